@@ -1,0 +1,98 @@
+"""Independent certificate checker: relative KKT residual of any primal-dual point.
+
+Test infrastructure only (see the package docstring).  It shares no code with the CUDA
+library and none with ``oracle.ipm`` either: it evaluates every product with its own
+sparse matrix-vector routines, so it can grade points at the full RT sizes where no dense
+matrix fits.
+
+Problem: min 0.5 x^T H x + c^T x  s.t.  A x <= b,  l <= x <= u  (Section 3.1 eq:qp with the
+bounds separated, Section 4).  The relative KKT residual (the paper defines none; this is
+the reading used for every parity claim) is the maximum of
+
+  primal : max(||max(A x - b, 0)||_inf, ||max(l - x, 0)||_inf, ||max(x - u, 0)||_inf) / (1 + ||b||_inf)
+  dual   : ||H x + c + A^T y - z_l + z_u||_inf / (1 + max(||c||_inf, ||H x||_inf, ||A^T y||_inf))
+  gap    : |pobj - dobj| / (1 + |pobj| + |dobj|)
+
+with pobj = 0.5 x^T H x + c^T x and the Lagrangian dual value
+dobj = -0.5 x^T H x - b^T y + l^T z_l - u^T z_u (y, z clipped at 0; z_l (z_u) counted only
+where l (u) is finite).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = ["Operators", "dense_ops", "rt_ops", "rel_kkt"]
+
+
+class Operators:
+    """H x, A x and A^T y for one QP, plus its vectors."""
+
+    def __init__(self, Hx, Ax, Aty, c, b, l, u):
+        self.Hx, self.Ax, self.Aty = Hx, Ax, Aty
+        self.c, self.b, self.l, self.u = (np.asarray(v, float) for v in (c, b, l, u))
+
+
+def _csr_mv(indptr, indices, data, x, nrows):
+    """y = M x for a CSR matrix, by a segmented sum of data * x[indices]."""
+    rows = np.repeat(np.arange(nrows), np.diff(indptr))
+    return np.bincount(rows, weights=data * x[indices], minlength=nrows)
+
+
+def _csr_tmv(indptr, indices, data, y, ncols):
+    """x = M^T y for a CSR matrix, by a scatter of data * y[row] into the columns."""
+    nz = np.diff(indptr)
+    rows = np.repeat(np.arange(nz.shape[0]), nz)
+    return np.bincount(indices, weights=data * y[rows], minlength=ncols)
+
+
+def dense_ops(p: dict) -> Operators:
+    H, A = np.asarray(p["H"], float), np.asarray(p["A"], float).reshape(-1, len(p["c"]))
+    return Operators(lambda x: H @ x, lambda x: A @ x, lambda y: A.T @ y, p["c"], p["b"], p["l"], p["u"])
+
+
+def rt_ops(p: dict) -> Operators:
+    """Operators of an RT-shaped QP: H x = D^T (w o (D x)) + h0 o x, A = D[a_rows]."""
+    ip, ix, dv = p["D_indptr"], p["D_indices"], p["D_data"]
+    V, n = p["V"], p["n"]
+    w, h0 = np.asarray(p["w"], float), np.asarray(p["h0"], float)
+    ar = np.asarray(p["a_rows"], dtype=np.int64)
+
+    def Hx(x):
+        return _csr_tmv(ip, ix, dv, w * _csr_mv(ip, ix, dv, x, V), n) + h0 * x
+
+    def Ax(x):
+        return _csr_mv(ip, ix, dv, x, V)[ar]
+
+    def Aty(y):
+        full = np.zeros(V)
+        np.add.at(full, ar, y)
+        return _csr_tmv(ip, ix, dv, full, n)
+
+    return Operators(Hx, Ax, Aty, p["c"], p["b"], p["l"], p["u"])
+
+
+def rel_kkt(ops: Operators, x, y, zl, zu, detail: bool = False):
+    """Relative KKT residual (max of the primal, dual and gap parts, see module docstring)."""
+    x = np.asarray(x, float)
+    y = np.maximum(np.asarray(y, float), 0.0)
+    fl, fu = np.isfinite(ops.l), np.isfinite(ops.u)
+    zl = np.where(fl, np.maximum(np.asarray(zl, float), 0.0), 0.0)
+    zu = np.where(fu, np.maximum(np.asarray(zu, float), 0.0), 0.0)
+    Hx, Ax, Aty = ops.Hx(x), ops.Ax(x), ops.Aty(y)
+    nb = np.max(np.abs(ops.b), initial=0.0)
+    viol = max(np.max(np.maximum(Ax - ops.b, 0.0), initial=0.0),
+               np.max(np.where(fl, np.maximum(np.where(fl, ops.l, 0.0) - x, 0.0), 0.0), initial=0.0),
+               np.max(np.where(fu, np.maximum(x - np.where(fu, ops.u, 0.0), 0.0), 0.0), initial=0.0))
+    primal = viol / (1.0 + nb)
+    rd = Hx + ops.c + Aty - zl + zu
+    dual = np.max(np.abs(rd), initial=0.0) / (1.0 + max(np.max(np.abs(ops.c), initial=0.0),
+                                                         np.max(np.abs(Hx), initial=0.0),
+                                                         np.max(np.abs(Aty), initial=0.0)))
+    pobj = 0.5 * x @ Hx + ops.c @ x
+    dobj = -0.5 * x @ Hx - ops.b @ y + np.sum(np.where(fl, np.where(fl, ops.l, 0.0) * zl, 0.0)) \
+        - np.sum(np.where(fu, np.where(fu, ops.u, 0.0) * zu, 0.0))
+    gap = abs(pobj - dobj) / (1.0 + abs(pobj) + abs(dobj))
+    val = float(max(primal, dual, gap))
+    if detail:
+        return val, dict(primal=float(primal), dual=float(dual), gap=float(gap), pobj=float(pobj), dobj=float(dobj))
+    return val

@@ -1,0 +1,195 @@
+"""Seeded synthetic QP generators shared by the tests, the bench and the oracle checks.
+
+This module only draws inputs: it holds none of the interior point method's arithmetic.
+Every problem has the form of the paper's QP (Section 3.1, eq:qp) written with a
+one-sided constraint block and separate variable bounds (Section 4, eq:2x2_reduced
+separates the bound rows):
+
+    min 0.5 x^T H x + c^T x   s.t.   A x <= b,   l <= x <= u.
+
+Two families are produced.
+
+* ``dense_qp``: a dense QP (H = Q diag(lam) Q^T, dense A).
+* ``rt_qp``: a radiation-therapy shaped QP.  The paper's own problems are exported
+  from a commercial planning system and are not available, so a dose-like matrix D
+  (voxels x beam spots) stands in: each voxel row holds a few contiguous bands of
+  spots, with lognormal values.  H = D^T diag(w) D + eps I is kept in factored form,
+  c = -D^T diag(w) d_presc, and the linear constraints are a subset of D's rows
+  (organ voxels, A = D[a_rows], b = 0.6).
+
+All arrays are numpy, float64 / int32 / int64.  Sparse matrices are CSR triplets
+``(indptr int64, indices int32, data float64)`` with sorted, unique column indices
+per row.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "dense_qp", "rt_qp", "rt_batch_sizes", "rt_batch", "perturb_chain_step",
+    "csr_to_dense", "random_iterate",
+]
+
+
+def dense_qp(n: int = 500, m: int = 1000, seed: int = 0, lam_lo: float = 1e-3,
+             lam_hi: float = 1e2, lo: float = 0.0, hi: float = 10.0) -> dict:
+    """Dense QP with a known eigen-decomposition of H.
+
+    A ~ N(0, 1/n); H = Q diag(lam) Q^T with Q a sign-fixed random orthogonal matrix and
+    lam log-uniform on [lam_lo, lam_hi]; c ~ N(0, 1); lo <= x <= hi;
+    b = A 1 + U(0.1, 1) so that x = 1 is strictly feasible.
+    The returned dict carries ``Q`` and ``lam`` as well, for closed-form checks.
+    """
+    rng = np.random.default_rng(seed)
+    A = rng.normal(0.0, 1.0 / np.sqrt(n), size=(m, n))
+    G = rng.normal(size=(n, n))
+    Q, R = np.linalg.qr(G)
+    Q = Q * np.sign(np.diag(R))[None, :]
+    lam = 10.0 ** rng.uniform(np.log10(lam_lo), np.log10(lam_hi), size=n)
+    H = (Q * lam[None, :]) @ Q.T
+    H = 0.5 * (H + H.T)
+    c = rng.normal(size=n)
+    b = A @ np.ones(n) + rng.uniform(0.1, 1.0, size=m)
+    l = np.full(n, lo)
+    u = np.full(n, hi)
+    return dict(kind="dense", n=n, m=m, H=H, c=c, A=A, b=b, l=l, u=u, Q=Q, lam=lam)
+
+
+def _band_rows(rng, V, n, density, main_sd_frac=0.02, max_extra=3):
+    """Column structure of a banded dose-like matrix, one block of rows at a time.
+
+    Row i holds k_i ~ Binomial(n, density) entries split into 1 + Binomial(max_extra, 0.5)
+    contiguous bands.  The first band is centred near i*n/V + N(0, main_sd_frac*n) (voxel
+    order follows spatial order); the extra bands are centred uniformly at random.
+    Returns (indptr, indices) with sorted unique columns per row.
+    """
+    k = rng.binomial(n, density, size=V).astype(np.int64)
+    k = np.clip(k, 1, n)
+    nb = 1 + rng.binomial(max_extra, 0.5, size=V)
+    # split k_i into nb_i band lengths (multinomial with equal weights, every band >= 1 where possible)
+    lens = np.zeros((V, max_extra + 1), dtype=np.int64)
+    u = rng.random((V, max_extra + 1))
+    u[np.arange(max_extra + 1)[None, :] >= nb[:, None]] = 0.0
+    u /= u.sum(axis=1, keepdims=True)
+    lens = np.floor(u * k[:, None]).astype(np.int64)
+    rem = k - lens.sum(axis=1)
+    lens[np.arange(V), 0] += rem
+    centres = np.empty((V, max_extra + 1))
+    centres[:, 0] = (np.arange(V) + 0.5) * (n / V) + rng.normal(0.0, main_sd_frac * n, size=V)
+    centres[:, 1:] = rng.uniform(0, n, size=(V, max_extra))
+    starts = np.rint(centres - lens / 2.0).astype(np.int64)
+    starts = np.clip(starts, 0, np.maximum(n - lens, 0))
+    # expand (row, col) pairs band by band
+    rows_l, cols_l = [], []
+    for bnd in range(max_extra + 1):
+        L = lens[:, bnd]
+        sel = L > 0
+        r = np.repeat(np.nonzero(sel)[0], L[sel])
+        off = np.arange(L[sel].sum()) - np.repeat(np.cumsum(L[sel]) - L[sel], L[sel])
+        cidx = np.repeat(starts[sel, bnd], L[sel]) + off
+        rows_l.append(r)
+        cols_l.append(cidx)
+    r = np.concatenate(rows_l)
+    cidx = np.concatenate(cols_l)
+    key = np.unique(r * np.int64(n) + cidx)           # sorted, duplicates (band overlap) removed
+    r = key // n
+    cidx = (key % n).astype(np.int32)
+    indptr = np.zeros(V + 1, dtype=np.int64)
+    np.cumsum(np.bincount(r, minlength=V), out=indptr[1:])
+    return indptr, cidx
+
+
+def rt_qp(n: int = 50_000, V: int | None = None, density: float = 0.005, seed: int = 1,
+          target_frac: float = 0.3, n_organ: int | None = None, b_organ: float = 0.6,
+          eps: float = 1e-4, lo: float = 0.0, hi: float = 5.0, w_lo: float = 0.1,
+          w_hi: float = 10.0) -> dict:
+    """Radiation-therapy shaped QP.
+
+    D: V x n dose-like CSR matrix (banded rows, lognormal(0, 1) values); w ~ U(w_lo, w_hi)
+    voxel weights; d_presc = 1 on a seeded target_frac of the voxels, else 0;
+    H = D^T diag(w) D + eps I (factored: F = D, weights w, diagonal h0 = eps);
+    c = -D^T (w * d_presc); A = D[a_rows] with a_rows = n_organ non-target voxels
+    (default 20000 when V = 200000, i.e. V/10), b = b_organ; lo <= x <= hi.
+    """
+    if V is None:
+        V = 4 * n
+    if n_organ is None:
+        n_organ = V // 10
+    rng = np.random.default_rng(seed)
+    indptr, indices = _band_rows(rng, V, n, density)
+    data = rng.lognormal(0.0, 1.0, size=indices.shape[0])
+    w = rng.uniform(w_lo, w_hi, size=V)
+    perm = rng.permutation(V)
+    n_target = int(round(target_frac * V))
+    target = np.sort(perm[:n_target])
+    d = np.zeros(V)
+    d[target] = 1.0
+    non_target = np.sort(perm[n_target:])
+    a_rows = np.sort(rng.choice(non_target, size=min(n_organ, non_target.size), replace=False)).astype(np.int32)
+    # c = -D^T (w * d): a scatter over the stored rows (a problem definition, not solver arithmetic)
+    wd = w * d
+    rowid = np.repeat(np.arange(V), np.diff(indptr))
+    c = -np.bincount(indices, weights=data * wd[rowid], minlength=n)
+    m = a_rows.shape[0]
+    return dict(kind="rt", n=n, V=V, m=m, D_indptr=indptr, D_indices=indices, D_data=data,
+                w=w, d=d, h0=np.full(n, eps), eps=eps, c=c, a_rows=a_rows,
+                b=np.full(m, b_organ), l=np.full(n, lo), u=np.full(n, hi))
+
+
+def rt_batch_sizes(count: int = 64, seed: int = 3, n_lo: int = 2000, n_hi: int = 40000,
+                   dens_lo: float = 0.002, dens_hi: float = 0.01):
+    """Per-instance (n, density, child seed) of the uneven batch: n ~ U[n_lo, n_hi],
+    density ~ U[dens_lo, dens_hi]; V = 4n and n/2 constraint rows are implied."""
+    ss = np.random.SeedSequence(seed)
+    kids = ss.spawn(count)
+    rng = np.random.default_rng(ss.spawn(1)[0])
+    ns = rng.integers(n_lo, n_hi + 1, size=count)
+    dens = rng.uniform(dens_lo, dens_hi, size=count)
+    return [(int(ns[i]), float(dens[i]), kids[i]) for i in range(count)]
+
+
+def rt_batch(count: int = 64, seed: int = 3, scale: float = 1.0, **kw):
+    """Uneven batch of RT-shaped QPs (optionally with every n scaled down by ``scale``)."""
+    out = []
+    for n, dens, kid in rt_batch_sizes(count, seed, **kw):
+        nn = max(16, int(round(n * scale)))
+        out.append(rt_qp(n=nn, V=4 * nn, density=dens, seed=kid, n_organ=nn // 2))
+    return out
+
+
+def perturb_chain_step(qp: dict, rng: np.random.Generator, rel: float = 0.01) -> dict:
+    """Next QP of an SQP-like chain: w <- w (1 + rel xi), c <- c (1 + rel xi), xi ~ N(0, 1).
+
+    w stays positive for rel * |xi| < 1, so H = D^T W D + eps I stays positive definite.
+    """
+    q = dict(qp)
+    q["w"] = qp["w"] * (1.0 + rel * rng.normal(size=qp["w"].shape))
+    q["w"] = np.maximum(q["w"], 1e-6)
+    q["c"] = qp["c"] * (1.0 + rel * rng.normal(size=qp["c"].shape))
+    return q
+
+
+def csr_to_dense(indptr, indices, data, shape):
+    """Plain CSR -> dense expansion (test helper)."""
+    M = np.zeros(shape)
+    rows = np.repeat(np.arange(shape[0]), np.diff(indptr))
+    np.add.at(M, (rows, indices), data)
+    return M
+
+
+def random_iterate(n: int, m: int, l: np.ndarray, u: np.ndarray, seed: int, spread: float = 1.0):
+    """A strictly interior primal-dual point (x, s, y, z_l, z_u) for operator/direction tests.
+
+    x lies strictly between finite bounds; s, y, z are log-normally spread positive numbers
+    (``spread`` sets the log-std, mimicking the widening of y/s late in a solve); z_l (z_u)
+    is zero where l (u) is infinite.
+    """
+    rng = np.random.default_rng(seed)
+    lo = np.where(np.isfinite(l), l, -10.0)
+    hi = np.where(np.isfinite(u), u, 10.0)
+    x = lo + (hi - lo) * rng.uniform(0.05, 0.95, size=n)
+    s = np.exp(rng.normal(0, spread, size=m))
+    y = np.exp(rng.normal(0, spread, size=m))
+    zl = np.where(np.isfinite(l), np.exp(rng.normal(0, spread, size=n)), 0.0)
+    zu = np.where(np.isfinite(u), np.exp(rng.normal(0, spread, size=n)), 0.0)
+    return x, s, y, zl, zu

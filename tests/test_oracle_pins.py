@@ -1,0 +1,288 @@
+"""Pins for the CPU oracle: each test checks it against something other than itself
+(closed forms, hand-solved fixtures, brute force, the paper's unreduced and doubly augmented
+Newton systems, exact identities), chosen so that a dropped term, a flipped sign or a
+transposed operand in oracle/ipm.py or oracle/kkt_check.py fails at least one of them."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import ipm, kkt_check
+from paper_2405_03584_gb300 import workloads as W
+from tests._bruteforce import solve_bruteforce
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "tiny_qps.json")
+
+
+def _rand_qp(n, m, seed, cond=1e2, free_frac=0.0):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.normal(size=(n, n)))
+    lam = 10 ** rng.uniform(0, np.log10(cond), size=n)
+    H = (Q * lam) @ Q.T
+    H = 0.5 * (H + H.T)
+    c = rng.normal(size=n) * 3
+    A = rng.normal(size=(m, n))
+    xf = rng.uniform(-0.5, 0.5, size=n)
+    b = A @ xf + rng.uniform(0.05, 1.0, size=m)
+    l = rng.uniform(-2, -0.6, size=n)
+    u = rng.uniform(0.6, 2, size=n)
+    free = rng.random(n) < free_frac
+    l[free & (rng.random(n) < 0.5)] = -np.inf
+    u[free & (rng.random(n) < 0.5)] = np.inf
+    return dict(H=H, c=c, A=A.reshape(m, n), b=b, l=l, u=u)
+
+
+def _qp_from_json(case):
+    n = len(case["c"])
+    A = np.array(case["A"], float).reshape(-1, n)
+    l = np.array([-np.inf if v is None else v for v in case["l"]], float)
+    u = np.array([np.inf if v is None else v for v in case["u"]], float)
+    return dict(H=np.array(case["H"], float), c=np.array(case["c"], float), A=A,
+                b=np.array(case["b"], float).reshape(-1), l=l, u=u)
+
+
+# ---------------------------------------------------------------- closed forms
+
+def test_unconstrained_closed_form():
+    """No rows, no bounds: the IPM must return x = -H^{-1} c, written here through the
+    generator's own eigen-decomposition H = Q diag(lam) Q^T (not through a solver)."""
+    p = W.dense_qp(n=60, m=0, seed=11)
+    p["A"] = np.zeros((0, 60))
+    p["b"] = np.zeros(0)
+    p["l"] = np.full(60, -np.inf)
+    p["u"] = np.full(60, np.inf)
+    x_star = -(p["Q"] @ ((p["Q"].T @ p["c"]) / p["lam"]))
+    it, info = ipm.solve(ipm.from_dense(p), tol=1e-12)
+    assert info.status == "optimal"
+    np.testing.assert_allclose(it.x, x_star, rtol=1e-9, atol=1e-9 * np.abs(x_star).max())
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_separable_box_clipping(seed):
+    """Diagonal H, no rows: x_j = clip(-c_j / h_j, l_j, u_j) coordinate by coordinate."""
+    rng = np.random.default_rng(100 + seed)
+    n = 40
+    h = 10 ** rng.uniform(-2, 2, size=n)
+    c = rng.normal(size=n) * 5
+    l = rng.uniform(-3, 0, size=n)
+    u = rng.uniform(0.1, 3, size=n)
+    l[rng.random(n) < 0.2] = -np.inf
+    u[rng.random(n) < 0.2] = np.inf
+    p = dict(H=np.diag(h), c=c, A=np.zeros((0, n)), b=np.zeros(0), l=l, u=u)
+    it, info = ipm.solve(ipm.from_dense(p), tol=1e-12)
+    assert info.status == "optimal"
+    np.testing.assert_allclose(it.x, np.clip(-c / h, l, u), rtol=1e-8, atol=1e-9)
+
+
+def test_hand_solved_fixtures():
+    """tests/golden/tiny_qps.json: KKT points derived by hand from eq:perturbed_KKT at mu = 0."""
+    cases = json.load(open(GOLD))["cases"]
+    for case in cases:
+        p = _qp_from_json(case)
+        it, info = ipm.solve(ipm.from_dense(p), tol=1e-12)
+        assert info.status == "optimal", case["name"]
+        np.testing.assert_allclose(it.x, case["x"], atol=1e-8, err_msg=case["name"])
+        np.testing.assert_allclose(it.y, case["y"], atol=1e-7, err_msg=case["name"])
+        fl, fu = np.isfinite(p["l"]), np.isfinite(p["u"])
+        np.testing.assert_allclose(np.where(fl, it.zl, 0), case["zl"], atol=1e-7, err_msg=case["name"])
+        np.testing.assert_allclose(np.where(fu, it.zu, 0), case["zu"], atol=1e-7, err_msg=case["name"])
+        assert abs(ipm.objective(ipm.from_dense(p), it.x) - case["obj"]) < 1e-9
+        # the stored multipliers certify the stored point with the independent checker
+        ops = kkt_check.dense_ops(p)
+        assert kkt_check.rel_kkt(ops, case["x"], case["y"], case["zl"], case["zu"]) < 1e-14
+
+
+# ---------------------------------------------------------------- brute force
+
+@pytest.mark.parametrize("n,m,seed", [(2, 1, 0), (3, 2, 1), (4, 3, 2), (5, 3, 3), (6, 4, 4), (6, 2, 5), (8, 2, 6)])
+def test_bruteforce_active_set(n, m, seed):
+    """Enumerate all 3^n 2^m active sets; the oracle's x must match the enumerated optimum,
+    and the enumerated KKT point must certify as optimal in the independent checker."""
+    p = _rand_qp(n, m, seed, free_frac=0.2)
+    bf = solve_bruteforce(p["H"], p["c"], p["A"], p["b"], p["l"], p["u"])
+    assert bf is not None
+    f, xb, yb, zlb, zub = bf
+    it, info = ipm.solve(ipm.from_dense(p), tol=1e-12)
+    assert info.status == "optimal"
+    np.testing.assert_allclose(it.x, xb, atol=1e-8)
+    assert abs(ipm.objective(ipm.from_dense(p), it.x) - f) <= 1e-9 * (1 + abs(f))
+    ops = kkt_check.dense_ops(p)
+    assert kkt_check.rel_kkt(ops, xb, yb, zlb, zub) < 1e-12
+    assert kkt_check.rel_kkt(ops, it.x, it.y, it.zl, it.zu) < 1e-11
+
+
+# ---------------------------------------------------------------- Newton systems
+
+def _interior_point(p, seed, spread=1.0):
+    n, m = len(p["c"]), len(p["b"])
+    return ipm.Iterate(*W.random_iterate(n, m, p["l"], p["u"], seed, spread))
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_newton_direction_solves_unreduced_system(seed):
+    """The condensed-Cholesky direction must satisfy the full, unreduced Newton system of
+    eq:newton_system (restated for A x + s = b and the separated bounds), assembled here
+    block by block in (dx, dy, dz_l, dz_u, ds) order."""
+    p = _rand_qp(12, 7, 20 + seed, cond=1e3, free_frac=0.3)
+    qp = ipm.from_dense(p)
+    it = _interior_point(p, seed, spread=2.0)
+    mu = 0.37
+    d = ipm.newton_direction(qp, it, mu)
+    rd, rp, rs, rl, ru = ipm.residuals(qp, it, mu)
+    n, m = qp.n, qp.m
+    fl, fu = qp.fl, qp.fu
+    tl = np.where(fl, it.x - np.where(fl, qp.l, 0), 1.0)
+    tu = np.where(fu, np.where(fu, qp.u, 0) - it.x, 1.0)
+    N = 3 * n + 2 * m
+    K = np.zeros((N, N))
+    ix, iy, izl, izu, isl = 0, n, n + m, 2 * n + m, 3 * n + m
+    K[ix:iy, ix:iy] = qp.H
+    K[ix:iy, iy:izl] = qp.A.T
+    K[ix:iy, izl:izu] = -np.eye(n)
+    K[ix:iy, izu:isl] = np.eye(n)
+    K[iy:izl, ix:iy] = qp.A                         # A dx + ds = -r_p
+    K[iy:izl, isl:] = np.eye(m)
+    K[izl:izu, ix:iy] = np.diag(np.where(fl, it.zl, 0))   # z_l dx + t_l dz_l = -r_l
+    K[izl:izu, izl:izu] = np.diag(np.where(fl, tl, 1.0))
+    K[izu:isl, ix:iy] = -np.diag(np.where(fu, it.zu, 0))  # -z_u dx + t_u dz_u = -r_u
+    K[izu:isl, izu:isl] = np.diag(np.where(fu, tu, 1.0))
+    K[isl:, iy:izl] = np.diag(it.s)                 # s dy + y ds = -r_s
+    K[isl:, isl:] = np.diag(it.y)
+    rhs = -np.concatenate([rd, rp, rl, ru, rs])
+    sol = np.linalg.solve(K, rhs)
+    np.testing.assert_allclose(d.x, sol[ix:iy], rtol=1e-9, atol=1e-10 * np.abs(sol).max())
+    np.testing.assert_allclose(d.y, sol[iy:izl], rtol=1e-9, atol=1e-10 * np.abs(sol).max())
+    np.testing.assert_allclose(d.zl, sol[izl:izu], rtol=1e-9, atol=1e-10 * np.abs(sol).max())
+    np.testing.assert_allclose(d.zu, sol[izu:isl], rtol=1e-9, atol=1e-10 * np.abs(sol).max())
+    np.testing.assert_allclose(d.s, sol[isl:], rtol=1e-9, atol=1e-10 * np.abs(sol).max())
+
+
+def test_newton_direction_matches_paper_two_sided_system():
+    """The paper's own 5x5 system (eq:newton_system, as printed, for l_A <= A x <= u_A with
+    residuals r_H = Hx + p - A^T lam_l + A^T lam_u, r_l = A x - s_l - l, r_u = -A x - s_u + u,
+    r_c = lam o s - mu) gives the same step as the oracle run on the one-sided stacking
+    [A; -A] x <= [u_A; -l_A], with y = (lam_u, lam_l) and s = (s_u, s_l)."""
+    rng = np.random.default_rng(7)
+    n, mA = 9, 5
+    p = _rand_qp(n, mA, 31, cond=1e2)
+    A, H, c = p["A"], p["H"], p["c"]
+    x = rng.normal(size=n) * 0.3
+    lA, uA = A @ x - rng.uniform(0.2, 1, mA), A @ x + rng.uniform(0.2, 1, mA)
+    sl, su = rng.uniform(0.1, 2, mA), rng.uniform(0.1, 2, mA)
+    ll, lu = rng.uniform(0.1, 2, mA), rng.uniform(0.1, 2, mA)
+    mu = 0.05
+    # paper form
+    rH = H @ x + c - A.T @ ll + A.T @ lu
+    rl = A @ x - sl - lA
+    ru = -A @ x - su + uA
+    rc1, rc2 = ll * sl - mu, lu * su - mu
+    N = n + 4 * mA
+    K = np.zeros((N, N))
+    o = np.cumsum([0, n, mA, mA, mA, mA])
+    K[o[0]:o[1], o[0]:o[1]] = H
+    K[o[0]:o[1], o[1]:o[2]] = -A.T
+    K[o[0]:o[1], o[2]:o[3]] = A.T
+    K[o[1]:o[2], o[0]:o[1]] = A
+    K[o[1]:o[2], o[3]:o[4]] = -np.eye(mA)
+    K[o[2]:o[3], o[0]:o[1]] = -A
+    K[o[2]:o[3], o[4]:o[5]] = -np.eye(mA)
+    K[o[3]:o[4], o[1]:o[2]] = np.diag(sl)
+    K[o[3]:o[4], o[3]:o[4]] = np.diag(ll)
+    K[o[4]:o[5], o[2]:o[3]] = np.diag(su)
+    K[o[4]:o[5], o[4]:o[5]] = np.diag(lu)
+    sol = np.linalg.solve(K, -np.concatenate([rH, rl, ru, rc1, rc2]))
+    dx_p, dll, dlu, dsl, dsu = (sol[o[i]:o[i + 1]] for i in range(5))
+    # oracle on the one-sided stacking, no variable bounds
+    q1 = dict(H=H, c=c, A=np.vstack([A, -A]), b=np.concatenate([uA, -lA]),
+              l=np.full(n, -np.inf), u=np.full(n, np.inf))
+    it = ipm.Iterate(x, np.concatenate([su, sl]), np.concatenate([lu, ll]), np.zeros(n), np.zeros(n))
+    d = ipm.newton_direction(ipm.from_dense(q1), it, mu)
+    np.testing.assert_allclose(d.x, dx_p, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(d.y, np.concatenate([dlu, dll]), rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(d.s, np.concatenate([dsu, dsl]), rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_doubly_augmented_matches_condensed(seed):
+    """The paper's doubly augmented form (eq:2x2_augmented) and the condensed form give the
+    same (dx, dy)."""
+    p = _rand_qp(10, 8, 40 + seed, cond=1e3, free_frac=0.2)
+    qp = ipm.from_dense(p)
+    it = _interior_point(p, 50 + seed, spread=1.5)
+    d = ipm.newton_direction(qp, it, 0.2)
+    dx, dy = ipm.doubly_augmented_direction(qp, it, 0.2)
+    np.testing.assert_allclose(d.x, dx, rtol=1e-8, atol=1e-10 * np.abs(dx).max())
+    np.testing.assert_allclose(d.y, dy, rtol=1e-8, atol=1e-10 * np.abs(dy).max())
+
+
+# ---------------------------------------------------------------- steps, invariants, identities
+
+def test_step_lengths_reach_boundary():
+    """alpha = tau * (largest feasible step): at alpha / tau some component sits on zero and
+    none is negative; a step with no blocking component is capped at 1."""
+    rng = np.random.default_rng(3)
+    n, m = 30, 20
+    p = _rand_qp(n, m, 9, free_frac=0.3)
+    qp = ipm.from_dense(p)
+    it = _interior_point(p, 4)
+    d = ipm.Iterate(rng.normal(size=n), rng.normal(size=m) * 3, rng.normal(size=m) * 3,
+                    rng.normal(size=n) * 3, rng.normal(size=n) * 3)
+    tau = 0.9
+    ap, ad = ipm.step_lengths(qp, it, d, tau)
+    assert 0 < ap < 1 and 0 < ad < 1
+    fl, fu = qp.fl, qp.fu
+    xs = it.x + ap / tau * d.x
+    prim = np.concatenate([it.s + ap / tau * d.s, (xs - qp.l)[fl], (qp.u - xs)[fu]])
+    dual = np.concatenate([it.y + ad / tau * d.y, (it.zl + ad / tau * d.zl)[fl], (it.zu + ad / tau * d.zu)[fu]])
+    assert prim.min() > -1e-12 and abs(prim.min()) < 1e-12
+    assert dual.min() > -1e-12 and abs(dual.min()) < 1e-12
+    up = ipm.Iterate(np.zeros(n), np.abs(d.s), np.abs(d.y), np.abs(d.zl), np.abs(d.zu))
+    assert ipm.step_lengths(qp, it, up, tau) == (1.0, 1.0)
+
+
+def test_iterates_stay_interior_and_gap_identity():
+    """Every oracle iterate keeps s, y, t_l, t_u, z_l, z_u > 0 (Section 3.1 line search), and at
+    any primal-dual feasible point pobj - dobj = s^T y + t_l^T z_l + t_u^T z_u."""
+    p = W.dense_qp(n=80, m=120, seed=5)
+    qp = ipm.from_dense(p)
+    it, info = ipm.solve(qp, tol=1e-9, record=True)
+    assert info.status == "optimal"
+    assert min(h["min_pos"] for h in info.history if "min_pos" in h) > 0
+    # feasible point: choose x, s, y, z, then define b and c so that r_p = r_d = 0
+    rng = np.random.default_rng(1)
+    n, m = 15, 9
+    q = _rand_qp(n, m, 77, free_frac=0.3)
+    x, s, y, zl, zu = W.random_iterate(n, m, q["l"], q["u"], 5)
+    q["b"] = q["A"] @ x + s
+    q["c"] = -(q["H"] @ x + q["A"].T @ y - zl + zu)
+    ops = kkt_check.dense_ops(q)
+    val, det = kkt_check.rel_kkt(ops, x, y, zl, zu, detail=True)
+    fl, fu = np.isfinite(q["l"]), np.isfinite(q["u"])
+    comp = s @ y + np.sum((x - q["l"])[fl] * zl[fl]) + np.sum((q["u"] - x)[fu] * zu[fu])
+    assert abs((det["pobj"] - det["dobj"]) - comp) < 1e-10 * (1 + abs(comp))
+    assert det["primal"] == 0.0 and det["dual"] < 1e-14
+
+
+def test_checker_rt_operators_match_dense():
+    """The checker's sparse RT operators agree with the dense expansion of the same QP."""
+    p = W.rt_qp(n=300, seed=2)
+    qp = ipm.from_rt(p)
+    ops = kkt_check.rt_ops(p)
+    rng = np.random.default_rng(0)
+    x, y = rng.normal(size=p["n"]), rng.normal(size=p["m"])
+    np.testing.assert_allclose(ops.Hx(x), qp.H @ x, rtol=1e-12, atol=1e-9)
+    np.testing.assert_allclose(ops.Ax(x), qp.A @ x, rtol=1e-12, atol=1e-10)
+    np.testing.assert_allclose(ops.Aty(y), qp.A.T @ y, rtol=1e-12, atol=1e-10)
+
+
+def test_oracle_solves_small_rt_and_dense():
+    """End-to-end oracle runs certify in the independent checker."""
+    p = W.rt_qp(n=400, seed=4)
+    it, info = ipm.solve(ipm.from_rt(p), tol=1e-9)
+    assert info.status == "optimal"
+    assert kkt_check.rel_kkt(kkt_check.rt_ops(p), it.x, it.y, it.zl, it.zu) < 1e-8
+    p = W.dense_qp(n=100, m=200, seed=8)
+    it, info = ipm.solve(ipm.from_dense(p), tol=1e-9)
+    assert info.status == "optimal"
+    assert kkt_check.rel_kkt(kkt_check.dense_ops(p), it.x, it.y, it.zl, it.zu) < 1e-8
