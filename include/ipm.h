@@ -1,0 +1,210 @@
+/*
+ * ipm.h -- C ABI of the GB300 (sm_103a) primal-dual interior point method for convex QPs
+ *
+ *     min 0.5 x^T H x + c^T x   s.t.   A x <= b,   l <= x <= u            (1)
+ *
+ * This is the paper's QP (Section 3.1, eq:qp) with a one-sided constraint block and the
+ * variable bounds kept apart from A, as Section 4 does before eq:2x2_reduced.  Each Newton
+ * step (eq:newton_system) is reduced to the normal-equations system
+ *
+ *     (H + A^T Theta A + Sigma) dx = r,  Theta = diag(y / s),  Sigma = diag(z_l/t_l + z_u/t_u)
+ *
+ * (the Schur complement of eq:2x2_reduced) and solved matrix-free by preconditioned
+ * conjugate gradients (Section 4.1, Algorithm 1 line "solve ... using PCG"), on the device.
+ *
+ * Conventions for every entry point:
+ *   - Return value: an ipm_status code; functions never abort and never print.
+ *     ipm_last_error(h) gives a one-line description of the last failure on a handle.
+ *   - Pointers are host or device memory as the `mem` argument says (IPM_MEM_HOST /
+ *     IPM_MEM_DEVICE).  Device pointers must be readable from the current CUDA device.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  The library orders its
+ *     work after everything already queued on `stream` and makes `stream` wait for it before
+ *     returning; calls that return data to host memory synchronise before returning.
+ *   - The library owns every device buffer it allocates (one arena per handle, allocated by
+ *     ipm_set_qp and freed by ipm_set_qp / ipm_destroy).  Inputs are deep-copied.
+ *   - Vectors are dense float64 arrays; sparse matrices are CSR with int64 row pointers and
+ *     int32 column indices (indices within a row in any order, no duplicates).
+ *   - A handle is not thread safe; different handles may be used concurrently.
+ */
+#ifndef IPM_H_
+#define IPM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum ipm_status {
+  IPM_OK = 0,
+  IPM_ERR_ARG = 1,               /* invalid argument (sizes, NULL, non-finite data, bad layout) */
+  IPM_ERR_OOM = 2,               /* device allocation failed or exceeds options.mem_budget      */
+  IPM_MAX_ITER = 3,              /* options.max_ipm iterations without reaching tol_kkt         */
+  IPM_CG_STALL = 4,              /* PCG hit options.max_cg without meeting its tolerance        */
+  IPM_NUMERICAL = 5,             /* NaN/Inf in an iterate, PCG breakdown or step length -> 0    */
+  IPM_INFEASIBLE_SUSPECTED = 6,  /* primal or dual residual stagnates while mu -> 0             */
+  IPM_ERR_TIMEOUT = 7,           /* host wall-clock limit options.timeout_ms exceeded           */
+  IPM_ERR_CUDA = 8,              /* a CUDA runtime call failed (see ipm_last_error)             */
+  IPM_ERR_STATE = 9              /* call out of order (e.g. ipm_solve before ipm_set_qp)        */
+};
+
+enum ipm_mem_space { IPM_MEM_HOST = 0, IPM_MEM_DEVICE = 1 };
+
+/* Preconditioner of the PCG solve (Section 4.1.2 computes the Jacobi diagonal).
+ *  JACOBI    : M = diag(H + A^T Theta A + Sigma), the paper's choice.
+ *  JACOBI_LR : Jacobi on the rows whose theta is moderate, plus an exact low-rank correction
+ *              (Woodbury) for the "stiff" rows whose theta_i sum_j a_ij^2 / M0_j > stiff_gamma;
+ *              keeps PCG iteration counts bounded as mu -> 0 (default).
+ *  DENSE     : the whole matrix, formed and Cholesky-factored on the device (one diagonal
+ *              block of size n); for n <= dense_max_n.                                       */
+enum ipm_precond { IPM_PRECOND_JACOBI = 0, IPM_PRECOND_JACOBI_LR = 1, IPM_PRECOND_DENSE = 2,
+                   IPM_PRECOND_AUTO = 3 };
+
+/* ipm_solve flags. */
+enum ipm_solve_flags { IPM_COLD = 0, IPM_WARM = 1 };
+
+typedef struct ipm_options {
+  double tol_kkt;        /* stop when the relative KKT residual <= tol_kkt (default 1e-6)      */
+  double tau;            /* fraction-to-boundary factor of the step lengths (0.995)            */
+  int max_ipm;           /* IPM iteration limit (200)                                          */
+  int max_cg;            /* PCG iteration limit per Newton step (2000)                         */
+  double cg_eta_max;     /* PCG relative tolerance eta = clamp(cg_eta_factor * relKKT, ...)    */
+  double cg_eta_min;     /*   ... between cg_eta_min (1e-10) and cg_eta_max (0.1)             */
+  double cg_eta_factor;  /*   (0.1)                                                            */
+  int precond;           /* enum ipm_precond (IPM_PRECOND_AUTO: DENSE if n <= 1024, else       */
+                         /* JACOBI_LR)                                                         */
+  double stiff_gamma;    /* JACOBI_LR threshold (1.0)                                          */
+  int stiff_max;         /* JACOBI_LR: at most this many stiff rows (256, <= 1024)             */
+  int dense_max_n;       /* DENSE allowed up to this n (2048, the maximum)                      */
+  double timeout_ms;     /* host wall-clock limit per ipm_solve, 0 = none                       */
+  double mem_budget;     /* bytes of device memory a handle may allocate, 0 = unlimited        */
+  int equal_steps;       /* 1: alpha_p = alpha_d = min of both (default 0: separate, Alg. 1)   */
+} ipm_options;
+
+/* Fills *opt with the defaults listed above. */
+void ipm_default_options(ipm_options* opt);
+
+/* The QP (1).  H = diag(h0) + H_dense + F^T diag(f_w) F, each term optional.
+ * Constraint rows come either from F (a_rows: row indices into F, the dose-matrix case where
+ * A is a subset of D's rows) or from a CSR matrix A; not both.  m = 0 is allowed (bounds only). */
+typedef struct ipm_qp {
+  int64_t n;                 /* variables, >= 1                                            */
+  int64_t m;                 /* linear inequality rows, >= 0                               */
+  int mem;                   /* ipm_mem_space of every pointer in this struct              */
+  const double* c;           /* n, linear cost (the paper's p)                             */
+  const double* b;           /* m, right-hand side of A x <= b (NULL iff m == 0)           */
+  const double* l;           /* n, lower bounds, -inf allowed; NULL = all -inf             */
+  const double* u;           /* n, upper bounds, +inf allowed; NULL = all +inf; l < u      */
+  const double* h0;          /* n, diagonal part of H (>= 0); NULL = 0                     */
+  const double* H_dense;     /* n*n row-major symmetric block of H; NULL = none            */
+  int64_t f_rows;            /* rows r of the factor F (0 = no factor term)                */
+  const int64_t* F_indptr;   /* r+1                                                        */
+  const int32_t* F_indices;  /* nnz(F), column indices in [0, n)                           */
+  const double* F_data;      /* nnz(F)                                                     */
+  const double* f_w;         /* r, weights >= 0                                            */
+  const int32_t* a_rows;     /* m row indices into F (or NULL)                             */
+  const int64_t* A_indptr;   /* m+1 (or NULL)                                              */
+  const int32_t* A_indices;  /* nnz(A)                                                     */
+  const double* A_data;      /* nnz(A)                                                     */
+} ipm_qp;
+
+typedef struct ipm_info {
+  int status;                /* ipm_status of the last ipm_solve                           */
+  int ipm_iters;             /* IPM iterations taken                                       */
+  int64_t cg_iters;          /* PCG iterations summed over all Newton steps                */
+  int max_cg_step;           /* most PCG iterations in one Newton step                     */
+  int max_stiff_rows;        /* most stiff rows in the JACOBI_LR correction                */
+  int precond;               /* preconditioner actually used                               */
+  double rel_kkt;            /* relative KKT residual of the returned point                */
+  double primal_res;         /* its primal, dual and gap parts                             */
+  double dual_res;
+  double gap_res;
+  double primal_obj;         /* 0.5 x^T H x + c^T x                                        */
+  double dual_obj;
+  double mu;                 /* final barrier parameter                                    */
+  double solve_ms;           /* wall time of the last ipm_solve                            */
+} ipm_info;
+
+/* Per-step result of ipm_newton_direction. */
+typedef struct ipm_cg_report {
+  int iters;                 /* PCG iterations                                             */
+  int converged;             /* 1 if ||r|| <= eta ||rhs|| was met                          */
+  int stiff_rows;            /* rows in the low-rank correction                            */
+  double rel_res;            /* final ||r|| / ||rhs||                                      */
+  double eta;                /* tolerance used                                             */
+} ipm_cg_report;
+
+typedef struct ipm_handle ipm_handle;
+
+/* Creates a solver handle on the current CUDA device.  opt may be NULL (defaults).
+ * Allocates no device memory.  Errors: IPM_ERR_ARG (out == NULL or invalid options). */
+int ipm_create(const ipm_options* opt, ipm_handle** out);
+
+/* Loads the QP (1) (deep copy into solver-owned device memory) and builds the stored
+ * transpose used by the matrix-free operator, the diagonal of H (computed once, as in
+ * Section 4.1.2) and the workspace.  Replaces any earlier QP on the handle.
+ * Errors: IPM_ERR_ARG (inconsistent sizes, index out of range, non-finite data, l >= u, both
+ * or neither of a_rows/A given with m > 0), IPM_ERR_OOM, IPM_ERR_CUDA. */
+int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream);
+
+/* Runs Algorithm 1 on the device from the start point (IPM_COLD) or from the last iterate
+ * (IPM_WARM: the previous solution, or one given by ipm_set_iterate).  Returns the solve
+ * status (IPM_OK when rel KKT <= tol_kkt). */
+int ipm_solve(ipm_handle* h, void* stream, int flags);
+
+/* Copies the current iterate to caller memory (any pointer may be NULL to skip it):
+ * x, z_l, z_u (n), y, s (m); fills *info if non-NULL. */
+int ipm_get_xyz(ipm_handle* h, double* x, double* y, double* z_l, double* z_u, double* s,
+                ipm_info* info, int mem, void* stream);
+
+/* Frees the handle and its device memory.  NULL-safe. */
+int ipm_destroy(ipm_handle* h);
+
+/* Static description of a status code. */
+const char* ipm_status_str(int status);
+
+/* Last error message recorded on h ("" if none). */
+const char* ipm_last_error(const ipm_handle* h);
+
+/* ---- Step-level entry points: one step of Algorithm 1 each, on the current iterate ---- */
+
+/* Sets the iterate (x, s, y, z_l, z_u) and mu; used for warm starts and to evaluate single
+ * steps.  x must lie strictly inside finite bounds; s, y, z_l, z_u > 0 where they apply. */
+int ipm_set_iterate(ipm_handle* h, const double* x, const double* s, const double* y,
+                    const double* z_l, const double* z_u, double mu, int mem, void* stream);
+
+/* Perturbed KKT residuals at the current iterate (Section 3.1, eq:perturbed_KKT, restated for
+ * (1)): r_d = Hx + c + A^T y - z_l + z_u (n), r_p = Ax + s - b (m), r_s = s o y - mu (m),
+ * r_l = t_l o z_l - mu, r_u = t_u o z_u - mu (n; 0 at infinite bounds).  NULL skips a vector.
+ * kkt (optional, 4 doubles) receives the relative KKT residual and its primal, dual and gap
+ * parts as defined for ipm_info. */
+int ipm_residuals(ipm_handle* h, double* r_d, double* r_p, double* r_s, double* r_l, double* r_u,
+                  double* kkt, int mem, void* stream);
+
+/* q = (H + A^T Theta A + Sigma) p at the current iterate: one matrix-free operator apply of
+ * the PCG (Section 4.1.1, the condensed counterpart of Listing 1's vec_mult_acc).  p, q: n. */
+int ipm_apply_kkt(ipm_handle* h, const double* p, double* q, int mem, void* stream);
+
+/* Jacobi diagonal diag(H + A^T Theta A + Sigma) at the current iterate (Section 4.1.2). */
+int ipm_precond_diag(ipm_handle* h, double* diag, int mem, void* stream);
+
+/* Newton direction at the current iterate and mu (Algorithm 1: PCG solve, then "assemble full
+ * search direction"): dx, dz_l, dz_u (n), ds, dy (m).  eta <= 0 selects the solver's own rule;
+ * otherwise PCG stops at ||r|| <= eta ||rhs||.  rep may be NULL. */
+int ipm_newton_direction(ipm_handle* h, double eta, double* dx, double* ds, double* dy,
+                         double* dz_l, double* dz_u, ipm_cg_report* rep, int mem, void* stream);
+
+/* Fraction-to-boundary step lengths for the given direction at the current iterate (Section
+ * 3.1 line search; Algorithm 1 "compute maximum step length"):
+ *   alpha_p = min(1, tau max{a: s + a ds >= 0, t_l + a dx >= 0, t_u - a dx >= 0}),
+ *   alpha_d = min(1, tau max{a: y + a dy >= 0, z_l + a dz_l >= 0, z_u + a dz_u >= 0}). */
+int ipm_step_lengths(ipm_handle* h, const double* dx, const double* ds, const double* dy,
+                     const double* dz_l, const double* dz_u, double tau, double* alpha_p,
+                     double* alpha_d, int mem, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IPM_H_ */

@@ -1,0 +1,844 @@
+// C ABI of the interior point library (declared in include/ipm.h): handle, problem ingest,
+// device arena, captured CUDA graphs of one IPM iteration and the host-side solve loop.
+//
+// Control flow of ipm_solve: one CUDA graph per IPM iteration (Algorithm 1 body, all on the
+// device): diagonal update -> preconditioner build -> right-hand side -> PCG as a
+// conditional-while graph node (one loop trip per PCG iteration; the loop condition is set by
+// the last kernel of the trip, so no host round trip per PCG iteration) -> direction
+// recovery -> ratio test -> update -> residual summary -> mu test / stop rule.  The host
+// reads a few device scalars once per IPM iteration to learn whether to stop.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/ipm.h"
+#include "state.h"
+
+using namespace ipmk;
+
+namespace {
+
+struct Graphs {
+  cudaGraphExec_t iter = nullptr;   // one full IPM iteration
+  cudaGraphExec_t dir = nullptr;    // Newton direction only (PCG + recovery)
+};
+
+}  // namespace
+
+struct ipm_handle {
+  ipm_options opt;
+  int device = 0;
+  cudaStream_t st = nullptr, st2 = nullptr;
+  cudaEvent_t ev = nullptr;
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  Dev d{};
+  Geo g{};
+  Scal* hs = nullptr;               // pinned host copy of the device scalars
+  bool loaded = false, have_iterate = false;
+  int precond = PC_JACOBI_LR;
+  Graphs graphs[3];
+  std::string err;
+  ipm_info info{};
+  double cnorm = 0, bnorm = 0;
+  int ncomp = 0;
+  int64_t sc_cap = 0;
+};
+
+namespace {
+
+int fail(ipm_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+#define CUDA_TRY(h, call)                                                                  \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail((h), IPM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// Copies n elements from host or device memory into a host vector.
+template <typename T>
+int fetch(ipm_handle* h, const T* src, int64_t n, int mem, std::vector<T>& out) {
+  out.resize((size_t)std::max<int64_t>(n, 0));
+  if (n <= 0) return IPM_OK;
+  if (!src) return fail(h, IPM_ERR_ARG, "missing array");
+  if (mem == IPM_MEM_DEVICE) {
+    CUDA_TRY(h, cudaMemcpy(out.data(), src, sizeof(T) * (size_t)n, cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(out.data(), src, sizeof(T) * (size_t)n);
+  }
+  return IPM_OK;
+}
+
+void destroy_graphs(ipm_handle* h) {
+  for (auto& g : h->graphs) {
+    if (g.iter) cudaGraphExecDestroy(g.iter);
+    if (g.dir) cudaGraphExecDestroy(g.dir);
+    g.iter = g.dir = nullptr;
+  }
+}
+
+void free_arena(ipm_handle* h) {
+  destroy_graphs(h);
+  if (h->arena) cudaFree(h->arena);
+  h->arena = nullptr;
+  h->arena_bytes = 0;
+  h->loaded = h->have_iterate = false;
+  h->d = Dev{};
+}
+
+// Bump allocator over one device allocation.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  bool count_only;
+  explicit Carver(char* b) : base(b), count_only(b == nullptr) {}
+  template <typename T>
+  T* take(int64_t n) {
+    off = (off + 255) & ~size_t(255);
+    T* p = count_only ? nullptr : reinterpret_cast<T*>(base + off);
+    off += sizeof(T) * (size_t)std::max<int64_t>(n, 1);
+    return p;
+  }
+};
+
+struct HostQP {
+  int64_t n = 0, m = 0, nR = 0, fr = 0;
+  std::vector<int64_t> Rp, RTp, Hp;
+  std::vector<int32_t> Ri, RTi, Hi, arow;
+  std::vector<double> Rv, RTv, Hv, wR, h0, c, b, l, u;
+  std::vector<unsigned char> fl, fu;
+};
+
+void carve(Carver& cv, Dev& d, const HostQP& q, int stiff_cap, int64_t sc_cap, bool dense) {
+  d.n = q.n; d.m = q.m; d.nR = q.nR;
+  d.nnzR = (int64_t)q.Rv.size();
+  d.nnzHs = (int64_t)q.Hv.size();
+  const int64_t n = q.n, m = q.m, nR = q.nR;
+  d.R_ptr = cv.take<int64_t>(nR + 1); d.R_idx = cv.take<int32_t>(d.nnzR); d.R_val = cv.take<double>(d.nnzR);
+  d.RT_ptr = cv.take<int64_t>(n + 1); d.RT_idx = cv.take<int32_t>(d.nnzR); d.RT_val = cv.take<double>(d.nnzR);
+  if (d.nnzHs) {
+    d.Hs_ptr = cv.take<int64_t>(n + 1); d.Hs_idx = cv.take<int32_t>(d.nnzHs); d.Hs_val = cv.take<double>(d.nnzHs);
+  } else {
+    d.Hs_ptr = nullptr; d.Hs_idx = nullptr; d.Hs_val = nullptr;
+  }
+  d.arow = cv.take<int32_t>(m);
+  d.wR = cv.take<double>(nR); d.h0 = cv.take<double>(n); d.c = cv.take<double>(n); d.b = cv.take<double>(m);
+  d.l = cv.take<double>(n); d.u = cv.take<double>(n);
+  d.fl = cv.take<unsigned char>(n); d.fu = cv.take<unsigned char>(n);
+  d.diagH = cv.take<double>(n);
+  d.x = cv.take<double>(n); d.s = cv.take<double>(m); d.y = cv.take<double>(m);
+  d.zl = cv.take<double>(n); d.zu = cv.take<double>(n);
+  d.theta = cv.take<double>(m); d.sigma = cv.take<double>(n); d.omega = cv.take<double>(nR);
+  d.M0 = cv.take<double>(n); d.Minv = cv.take<double>(n); d.thR = cv.take<double>(nR);
+  d.rd = cv.take<double>(n); d.rp = cv.take<double>(m); d.Hx = cv.take<double>(n); d.Aty = cv.take<double>(n);
+  d.tR = cv.take<double>(nR); d.vR = cv.take<double>(nR); d.vR2 = cv.take<double>(nR);
+  d.dx = cv.take<double>(n); d.r = cv.take<double>(n); d.z = cv.take<double>(n); d.p = cv.take<double>(n);
+  d.q = cv.take<double>(n); d.rhs = cv.take<double>(n);
+  d.ds = cv.take<double>(m); d.dy = cv.take<double>(m); d.dzl = cv.take<double>(n); d.dzu = cv.take<double>(n);
+  d.ratio = cv.take<double>(m); d.slotR = cv.take<int32_t>(nR); d.stiff_k = cv.take<int32_t>(stiff_cap);
+  d.sc_cnt = cv.take<int32_t>(n); d.sc_ptr = cv.take<int64_t>(n + 1);
+  d.sc_slot = cv.take<int32_t>(sc_cap); d.sc_val = cv.take<double>(sc_cap); d.sc_cap = sc_cap;
+  d.G = cv.take<double>((int64_t)stiff_cap * stiff_cap); d.Ginv = cv.take<double>((int64_t)stiff_cap * stiff_cap);
+  d.us = cv.take<double>(stiff_cap); d.ts = cv.take<double>(stiff_cap); d.stiff_cap = stiff_cap;
+  d.hist = cv.take<unsigned int>(kHistBins);
+  if (dense) { d.Kd = cv.take<double>(n * n); d.Kinv = cv.take<double>(n * n); } else { d.Kd = d.Kinv = nullptr; }
+  d.partials = cv.take<double>(32 * (int64_t)kMaxRedBlocks);
+  d.sc = cv.take<Scal>(1);
+}
+
+int validate_options(const ipm_options& o) {
+  if (!(o.tol_kkt > 0) || !(o.tau > 0 && o.tau < 1) || o.max_ipm < 1 || o.max_cg < 1) return IPM_ERR_ARG;
+  if (!(o.cg_eta_min > 0) || !(o.cg_eta_max >= o.cg_eta_min) || !(o.cg_eta_factor > 0)) return IPM_ERR_ARG;
+  if (o.precond < 0 || o.precond > 3 || o.stiff_max < 0 || o.stiff_max > 1024) return IPM_ERR_ARG;
+  if (o.dense_max_n < 0 || o.dense_max_n > 2048 || !(o.stiff_gamma > 0)) return IPM_ERR_ARG;
+  return IPM_OK;
+}
+
+// Host copy of the device scalars (one small D2H plus a synchronisation).
+int pull_scal(ipm_handle* h) {
+  CUDA_TRY(h, cudaMemcpyAsync(h->hs, h->d.sc, sizeof(Scal), cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return IPM_OK;
+}
+
+// Orders the internal stream after the caller's stream.
+int enter(ipm_handle* h, void* stream) {
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  CUDA_TRY(h, cudaEventRecord(h->ev, (cudaStream_t)stream));
+  CUDA_TRY(h, cudaStreamWaitEvent(h->st, h->ev, 0));
+  return IPM_OK;
+}
+
+// Orders the caller's stream after the internal stream.
+int leave(ipm_handle* h, void* stream) {
+  CUDA_TRY(h, cudaEventRecord(h->ev, h->st));
+  CUDA_TRY(h, cudaStreamWaitEvent((cudaStream_t)stream, h->ev, 0));
+  return IPM_OK;
+}
+
+// Captures one IPM iteration (full=true) or one Newton direction (full=false).
+int build_graph(ipm_handle* h, int pc, bool full, cudaGraphExec_t* out) {
+  const Dev& d = h->d;
+  const Geo& g = h->g;
+  cudaStream_t st = h->st;
+  CUDA_TRY(h, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t x) { if (e == cudaSuccess && x != cudaSuccess) e = x; };
+  chk(launch_diag_update(d, g, st));
+  chk(launch_precond_build(d, g, pc, st));
+  chk(launch_rhs(d, g, st));
+  chk(launch_cg_init(d, g, pc, st));
+  // PCG loop: a conditional while node whose body is one PCG iteration
+  cudaStreamCaptureStatus cs;
+  unsigned long long cid;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edata = nullptr;
+  size_t ndeps = 0;
+  if (e == cudaSuccess) chk(cudaStreamGetCaptureInfo(st, &cs, &cid, &cg, &deps, &edata, &ndeps));
+  cudaGraphNode_t cnode = nullptr;
+  cudaGraphConditionalHandle ch = 0;
+  if (e == cudaSuccess) {
+    std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
+    chk(cudaGraphConditionalHandleCreate(&ch, cg, 1u, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = ch;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if (e == cudaSuccess) chk(cudaGraphAddNode(&cnode, cg, dv.data(), nullptr, dv.size(), &cp));
+    if (e == cudaSuccess) chk(cudaStreamUpdateCaptureDependencies(st, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    if (e == cudaSuccess) {
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      chk(cudaStreamBeginCaptureToGraph(h->st2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      if (e == cudaSuccess) {
+        chk(launch_cg_body(d, g, pc, ch, h->st2));
+        cudaGraph_t bodyo = nullptr;
+        chk(cudaStreamEndCapture(h->st2, &bodyo));
+      }
+    }
+  }
+  chk(launch_recover(d, g, st));
+  if (full) {
+    chk(launch_ratio(d, g, st));
+    chk(launch_update(d, g, st));
+    chk(launch_residual_summary(d, g, st));
+    chk(launch_control(d, st));
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(st, &graph);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, IPM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  }
+  return IPM_OK;
+}
+
+int ensure_graph(ipm_handle* h, int pc, bool full, cudaGraphExec_t** gx) {
+  Graphs& gr = h->graphs[pc];
+  cudaGraphExec_t* slot = full ? &gr.iter : &gr.dir;
+  if (!*slot) {
+    int rc = build_graph(h, pc, full, slot);
+    if (rc) return rc;
+  }
+  *gx = slot;
+  return IPM_OK;
+}
+
+int choose_precond(const ipm_handle* h) {
+  const ipm_options& o = h->opt;
+  int pc = o.precond;
+  if (pc == IPM_PRECOND_AUTO) pc = (h->d.Kd && h->d.n <= 1024) ? PC_DENSE : PC_JACOBI_LR;
+  if (pc == PC_DENSE && !h->d.Kd) pc = PC_JACOBI_LR;
+  return pc;
+}
+
+// Writes the solver options into the device scalars (keeps the iterate state).
+int push_options(ipm_handle* h) {
+  Scal& s = *h->hs;
+  s.tol_kkt = h->opt.tol_kkt;
+  s.tau = h->opt.tau;
+  s.max_ipm = h->opt.max_ipm;
+  s.cg_max = h->opt.max_cg;
+  s.eta_factor = h->opt.cg_eta_factor;
+  s.eta_min = h->opt.cg_eta_min;
+  s.eta_max = h->opt.cg_eta_max;
+  s.stiff_gamma = h->opt.stiff_gamma;
+  s.stiff_max = std::min(h->opt.stiff_max, h->d.stiff_cap);
+  s.equal_steps = h->opt.equal_steps;
+  s.cnorm = h->cnorm;
+  s.bnorm = h->bnorm;
+  s.ncomp = h->ncomp;
+  return IPM_OK;
+}
+
+int copy_out(ipm_handle* h, double* dst, const double* src, int64_t n, int mem) {
+  if (!dst || n <= 0) return IPM_OK;
+  CUDA_TRY(h, cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)n,
+                              mem == IPM_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+  return IPM_OK;
+}
+
+int copy_in(ipm_handle* h, double* dst, const double* src, int64_t n, int mem) {
+  if (n <= 0) return IPM_OK;
+  if (!src) return fail(h, IPM_ERR_ARG, "missing vector");
+  CUDA_TRY(h, cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)n,
+                              mem == IPM_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+  return IPM_OK;
+}
+
+// Scalar fields of the device struct (written from the host between graph launches).
+int set_scal_double(ipm_handle* h, double* field_dev, double v) {
+  CUDA_TRY(h, cudaMemcpyAsync(field_dev, &v, sizeof(double), cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return IPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ipm_default_options(ipm_options* o) {
+  if (!o) return;
+  o->tol_kkt = 1e-6;
+  o->tau = 0.995;
+  o->max_ipm = 200;
+  o->max_cg = 2000;
+  o->cg_eta_max = 0.1;
+  o->cg_eta_min = 1e-10;
+  o->cg_eta_factor = 0.1;
+  o->precond = IPM_PRECOND_AUTO;
+  o->stiff_gamma = 1.0;
+  o->stiff_max = 256;
+  o->dense_max_n = 2048;
+  o->timeout_ms = 0.0;
+  o->mem_budget = 0.0;
+  o->equal_steps = 0;
+}
+
+const char* ipm_status_str(int s) {
+  switch (s) {
+    case IPM_OK: return "ok";
+    case IPM_ERR_ARG: return "invalid argument";
+    case IPM_ERR_OOM: return "out of device memory (or over budget)";
+    case IPM_MAX_ITER: return "IPM iteration limit reached";
+    case IPM_CG_STALL: return "PCG iteration limit reached";
+    case IPM_NUMERICAL: return "numerical failure (NaN/Inf or breakdown)";
+    case IPM_INFEASIBLE_SUSPECTED: return "problem looks infeasible";
+    case IPM_ERR_TIMEOUT: return "wall-clock limit exceeded";
+    case IPM_ERR_CUDA: return "CUDA error";
+    case IPM_ERR_STATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+const char* ipm_last_error(const ipm_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+int ipm_create(const ipm_options* opt, ipm_handle** out) {
+  if (!out) return IPM_ERR_ARG;
+  *out = nullptr;
+  ipm_options o;
+  ipm_default_options(&o);
+  if (opt) o = *opt;
+  if (validate_options(o) != IPM_OK) return IPM_ERR_ARG;
+  ipm_handle* h = new (std::nothrow) ipm_handle();
+  if (!h) return IPM_ERR_OOM;
+  h->opt = o;
+  if (cudaGetDevice(&h->device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMallocHost(&h->hs, sizeof(Scal)) != cudaSuccess) {
+    cudaGetLastError();
+    if (h->st) cudaStreamDestroy(h->st);
+    if (h->st2) cudaStreamDestroy(h->st2);
+    if (h->ev) cudaEventDestroy(h->ev);
+    delete h;
+    return IPM_ERR_CUDA;
+  }
+  std::memset(h->hs, 0, sizeof(Scal));
+  *out = h;
+  return IPM_OK;
+}
+
+int ipm_destroy(ipm_handle* h) {
+  if (!h) return IPM_OK;
+  cudaSetDevice(h->device);
+  if (h->st) cudaStreamSynchronize(h->st);
+  free_arena(h);
+  if (h->hs) cudaFreeHost(h->hs);
+  if (h->st) cudaStreamDestroy(h->st);
+  if (h->st2) cudaStreamDestroy(h->st2);
+  if (h->ev) cudaEventDestroy(h->ev);
+  delete h;
+  return IPM_OK;
+}
+
+int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
+  if (!h || !qp) return IPM_ERR_ARG;
+  h->err.clear();
+  const int64_t n = qp->n, m = qp->m, fr = qp->f_rows;
+  const int mem = qp->mem;
+  if (n < 1 || m < 0 || fr < 0 || (mem != IPM_MEM_HOST && mem != IPM_MEM_DEVICE))
+    return fail(h, IPM_ERR_ARG, "bad sizes or memory space");
+  if (n > INT32_MAX || fr + m > INT32_MAX) return fail(h, IPM_ERR_ARG, "sizes exceed int32 indexing");
+  const bool use_arows = qp->a_rows != nullptr;
+  const bool use_acsr = qp->A_indptr != nullptr;
+  if (m > 0 && use_arows == use_acsr) return fail(h, IPM_ERR_ARG, "give exactly one of a_rows or A (CSR)");
+  if (use_arows && fr == 0) return fail(h, IPM_ERR_ARG, "a_rows needs a factor F");
+  int rc;
+  HostQP q;
+  q.n = n; q.m = m; q.fr = fr;
+  // vectors
+  if ((rc = fetch(h, qp->c, n, mem, q.c))) return rc;
+  if (m && (rc = fetch(h, qp->b, m, mem, q.b))) return rc;
+  if (qp->l) { if ((rc = fetch(h, qp->l, n, mem, q.l))) return rc; } else q.l.assign(n, -INFINITY);
+  if (qp->u) { if ((rc = fetch(h, qp->u, n, mem, q.u))) return rc; } else q.u.assign(n, INFINITY);
+  if (qp->h0) { if ((rc = fetch(h, qp->h0, n, mem, q.h0))) return rc; } else q.h0.assign(n, 0.0);
+  for (int64_t j = 0; j < n; ++j) {
+    if (!std::isfinite(q.c[j]) || !std::isfinite(q.h0[j]) || q.h0[j] < 0) return fail(h, IPM_ERR_ARG, "c or h0 not finite / h0 < 0");
+    if (std::isnan(q.l[j]) || std::isnan(q.u[j]) || q.l[j] == INFINITY || q.u[j] == -INFINITY) return fail(h, IPM_ERR_ARG, "bad bound");
+    if (std::isfinite(q.l[j]) && std::isfinite(q.u[j]) && !(q.l[j] < q.u[j])) return fail(h, IPM_ERR_ARG, "l >= u");
+  }
+  for (int64_t k = 0; k < m; ++k) if (!std::isfinite(q.b[k])) return fail(h, IPM_ERR_ARG, "b not finite");
+  // R = [F; A_csr]
+  std::vector<int64_t> Fp, Ap;
+  std::vector<int32_t> Fi, Ai, arows_in;
+  std::vector<double> Fv, Av, fw;
+  if (fr) {
+    if ((rc = fetch(h, qp->F_indptr, fr + 1, mem, Fp))) return rc;
+    if (Fp[0] != 0) return fail(h, IPM_ERR_ARG, "F_indptr[0] != 0");
+    for (int64_t r = 0; r < fr; ++r) if (Fp[r + 1] < Fp[r]) return fail(h, IPM_ERR_ARG, "F_indptr not monotone");
+    if ((rc = fetch(h, qp->F_indices, Fp[fr], mem, Fi))) return rc;
+    if ((rc = fetch(h, qp->F_data, Fp[fr], mem, Fv))) return rc;
+    if ((rc = fetch(h, qp->f_w, fr, mem, fw))) return rc;
+    for (double w : fw) if (!std::isfinite(w) || w < 0) return fail(h, IPM_ERR_ARG, "f_w must be finite and >= 0");
+  }
+  if (m && use_acsr) {
+    if ((rc = fetch(h, qp->A_indptr, m + 1, mem, Ap))) return rc;
+    if (Ap[0] != 0) return fail(h, IPM_ERR_ARG, "A_indptr[0] != 0");
+    for (int64_t r = 0; r < m; ++r) if (Ap[r + 1] < Ap[r]) return fail(h, IPM_ERR_ARG, "A_indptr not monotone");
+    if ((rc = fetch(h, qp->A_indices, Ap[m], mem, Ai))) return rc;
+    if ((rc = fetch(h, qp->A_data, Ap[m], mem, Av))) return rc;
+  }
+  if (m && use_arows) {
+    if ((rc = fetch(h, qp->a_rows, m, mem, arows_in))) return rc;
+    std::vector<int32_t> srt(arows_in);
+    std::sort(srt.begin(), srt.end());
+    for (int64_t k = 0; k < m; ++k) {
+      if (srt[k] < 0 || srt[k] >= fr) return fail(h, IPM_ERR_ARG, "a_rows index out of range");
+      if (k && srt[k] == srt[k - 1]) return fail(h, IPM_ERR_ARG, "a_rows has duplicates");
+    }
+  }
+  q.nR = fr + (use_acsr ? m : 0);
+  const int64_t nnzF = fr ? Fp[fr] : 0, nnzA = (m && use_acsr) ? Ap[m] : 0;
+  q.Rp.resize(q.nR + 1);
+  q.Ri.resize(nnzF + nnzA);
+  q.Rv.resize(nnzF + nnzA);
+  q.wR.assign(q.nR, 0.0);
+  for (int64_t r = 0; r <= fr; ++r) q.Rp[r] = fr ? Fp[r] : 0;
+  if (nnzF) { std::memcpy(q.Ri.data(), Fi.data(), 4 * nnzF); std::memcpy(q.Rv.data(), Fv.data(), 8 * nnzF); }
+  for (int64_t r = 0; r < fr; ++r) q.wR[r] = fw[r];
+  if (use_acsr) {
+    for (int64_t k = 1; k <= m; ++k) q.Rp[fr + k] = nnzF + Ap[k];
+    if (nnzA) { std::memcpy(q.Ri.data() + nnzF, Ai.data(), 4 * nnzA); std::memcpy(q.Rv.data() + nnzF, Av.data(), 8 * nnzA); }
+  }
+  for (size_t e = 0; e < q.Ri.size(); ++e) {
+    if (q.Ri[e] < 0 || q.Ri[e] >= n) return fail(h, IPM_ERR_ARG, "column index out of range");
+    if (!std::isfinite(q.Rv[e])) return fail(h, IPM_ERR_ARG, "matrix value not finite");
+  }
+  q.arow.resize(m);
+  for (int64_t k = 0; k < m; ++k) q.arow[k] = use_arows ? arows_in[k] : (int32_t)(fr + k);
+  // R^T by a stable counting sort (rows increase within each column: deterministic order)
+  q.RTp.assign(n + 1, 0);
+  for (int32_t c : q.Ri) q.RTp[c + 1]++;
+  for (int64_t j = 0; j < n; ++j) q.RTp[j + 1] += q.RTp[j];
+  q.RTi.resize(q.Ri.size());
+  q.RTv.resize(q.Ri.size());
+  {
+    std::vector<int64_t> cur(q.RTp.begin(), q.RTp.end() - 1);
+    for (int64_t r = 0; r < q.nR; ++r)
+      for (int64_t e = q.Rp[r]; e < q.Rp[r + 1]; ++e) {
+        const int64_t pos = cur[q.Ri[e]]++;
+        q.RTi[pos] = (int32_t)r;
+        q.RTv[pos] = q.Rv[e];
+      }
+  }
+  // dense H block -> CSR of its non-zeros (symmetry checked)
+  if (qp->H_dense) {
+    std::vector<double> Hd;
+    if ((rc = fetch(h, qp->H_dense, n * n, mem, Hd))) return rc;
+    q.Hp.assign(n + 1, 0);
+    double scale = 0;
+    for (double v : Hd) { if (!std::isfinite(v)) return fail(h, IPM_ERR_ARG, "H_dense not finite"); scale = std::max(scale, std::fabs(v)); }
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t j = 0; j < n; ++j) {
+        const double v = Hd[i * n + j];
+        if (std::fabs(v - Hd[j * n + i]) > 1e-12 * (1 + scale)) return fail(h, IPM_ERR_ARG, "H_dense not symmetric");
+        if (v != 0.0) { q.Hi.push_back((int32_t)j); q.Hv.push_back(v); }
+      }
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      q.Hp[i] = cnt;
+      for (int64_t j = 0; j < n; ++j) if (Hd[i * n + j] != 0.0) ++cnt;
+    }
+    q.Hp[n] = cnt;
+  }
+  q.fl.resize(n);
+  q.fu.resize(n);
+  int ncomp = (int)m;
+  for (int64_t j = 0; j < n; ++j) {
+    q.fl[j] = std::isfinite(q.l[j]) ? 1 : 0;
+    q.fu[j] = std::isfinite(q.u[j]) ? 1 : 0;
+    ncomp += q.fl[j] + q.fu[j];
+  }
+  double cn = 0, bn = 0;
+  for (double v : q.c) cn = std::max(cn, std::fabs(v));
+  for (double v : q.b) bn = std::max(bn, std::fabs(v));
+  // stiff-row capacity: the stiff_cap longest constraint rows
+  const int stiff_cap = std::max(1, std::min<int>(h->opt.stiff_max > 0 ? h->opt.stiff_max : 1, (int)std::max<int64_t>(m, 1)));
+  std::vector<int64_t> lens(m);
+  for (int64_t k = 0; k < m; ++k) lens[k] = q.Rp[q.arow[k] + 1] - q.Rp[q.arow[k]];
+  std::sort(lens.begin(), lens.end(), std::greater<int64_t>());
+  int64_t sc_cap = 0;
+  for (int64_t k = 0; k < std::min<int64_t>(m, stiff_cap); ++k) sc_cap += lens[k];
+  sc_cap = std::max<int64_t>(sc_cap, 1);
+  const bool dense = h->opt.dense_max_n > 0 && n <= h->opt.dense_max_n &&
+                     (h->opt.precond == IPM_PRECOND_DENSE || h->opt.precond == IPM_PRECOND_AUTO);
+  // allocate
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  free_arena(h);
+  Dev dv{};
+  Carver cnt(nullptr);
+  carve(cnt, dv, q, stiff_cap, sc_cap, dense);
+  const size_t bytes = cnt.off + 256;
+  if (h->opt.mem_budget > 0 && (double)bytes > h->opt.mem_budget)
+    return fail(h, IPM_ERR_OOM, "QP needs " + std::to_string(bytes) + " bytes, over mem_budget");
+  if (cudaMalloc(&h->arena, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    h->arena = nullptr;
+    return fail(h, IPM_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  h->arena_bytes = bytes;
+  Carver cv((char*)h->arena);
+  carve(cv, dv, q, stiff_cap, sc_cap, dense);
+  h->d = dv;
+  h->g = make_geo(dv);
+  h->cnorm = cn; h->bnorm = bn; h->ncomp = ncomp; h->sc_cap = sc_cap;
+  if ((rc = enter(h, stream))) return rc;
+  auto up = [&](const void* dst, const void* src, size_t nbytes) -> int {
+    if (nbytes == 0) return IPM_OK;
+    CUDA_TRY(h, cudaMemcpyAsync((void*)dst, src, nbytes, cudaMemcpyHostToDevice, h->st));
+    return IPM_OK;
+  };
+  const Dev& d = h->d;
+  if ((rc = up(d.R_ptr, q.Rp.data(), 8 * q.Rp.size()))) return rc;
+  if ((rc = up(d.R_idx, q.Ri.data(), 4 * q.Ri.size()))) return rc;
+  if ((rc = up(d.R_val, q.Rv.data(), 8 * q.Rv.size()))) return rc;
+  if ((rc = up(d.RT_ptr, q.RTp.data(), 8 * q.RTp.size()))) return rc;
+  if ((rc = up(d.RT_idx, q.RTi.data(), 4 * q.RTi.size()))) return rc;
+  if ((rc = up(d.RT_val, q.RTv.data(), 8 * q.RTv.size()))) return rc;
+  if (d.Hs_ptr) {
+    if ((rc = up(d.Hs_ptr, q.Hp.data(), 8 * q.Hp.size()))) return rc;
+    if ((rc = up(d.Hs_idx, q.Hi.data(), 4 * q.Hi.size()))) return rc;
+    if ((rc = up(d.Hs_val, q.Hv.data(), 8 * q.Hv.size()))) return rc;
+  }
+  if ((rc = up(d.arow, q.arow.data(), 4 * q.arow.size()))) return rc;
+  if ((rc = up(d.wR, q.wR.data(), 8 * q.wR.size()))) return rc;
+  if ((rc = up(d.h0, q.h0.data(), 8 * n))) return rc;
+  if ((rc = up(d.c, q.c.data(), 8 * n))) return rc;
+  if ((rc = up(d.b, q.b.data(), 8 * m))) return rc;
+  if ((rc = up(d.l, q.l.data(), 8 * n))) return rc;
+  if ((rc = up(d.u, q.u.data(), 8 * n))) return rc;
+  if ((rc = up(d.fl, q.fl.data(), n))) return rc;
+  if ((rc = up(d.fu, q.fu.data(), n))) return rc;
+  CUDA_TRY(h, cudaMemsetAsync(d.hist, 0, sizeof(unsigned int) * kHistBins, h->st));
+  CUDA_TRY(h, cudaMemsetAsync(d.slotR, 0xff, sizeof(int32_t) * std::max<int64_t>(q.nR, 1), h->st));
+  std::memset(h->hs, 0, sizeof(Scal));
+  push_options(h);
+  h->hs->mu = h->hs->mu0 = 1.0;
+  h->hs->status = DS_RUNNING;
+  CUDA_TRY(h, cudaMemcpyAsync(d.sc, h->hs, sizeof(Scal), cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, launch_diagH(d, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));   // host staging buffers go out of scope
+  h->loaded = true;
+  h->have_iterate = false;
+  h->precond = choose_precond(h);
+  h->info = ipm_info{};
+  return leave(h, stream);
+}
+
+int ipm_solve(ipm_handle* h, void* stream, int flags) {
+  if (!h) return IPM_ERR_ARG;
+  if (!h->loaded) return fail(h, IPM_ERR_STATE, "ipm_solve before ipm_set_qp");
+  h->err.clear();
+  int rc;
+  const auto t0 = std::chrono::steady_clock::now();
+  if ((rc = enter(h, stream))) return rc;
+  // options may have been changed on the handle? (they cannot: ipm_options is fixed at create)
+  if ((rc = pull_scal(h))) return rc;
+  push_options(h);
+  h->hs->eta_override = 0;
+  CUDA_TRY(h, cudaMemcpyAsync(h->d.sc, h->hs, sizeof(Scal), cudaMemcpyHostToDevice, h->st));
+  if (!(flags & IPM_WARM) || !h->have_iterate) {
+    CUDA_TRY(h, launch_start_point(h->d, h->g, h->st));
+  } else {
+    CUDA_TRY(h, launch_residual_summary(h->d, h->g, h->st));
+    // warm start: mu0 = complementarity mean of the given point
+    CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    if ((rc = pull_scal(h))) return rc;
+    Scal& s = *h->hs;
+    s.mu0 = s.comp_mean > 0 ? s.comp_mean : 1.0;
+    s.mu = s.mu0;
+    s.ipm_iter = 0; s.stop = 0; s.status = DS_RUNNING;
+    double e = s.eta_factor * s.rel_kkt;
+    s.eta = std::min(s.eta_max, std::max(s.eta_min, std::isfinite(e) ? e : s.eta_max));
+    CUDA_TRY(h, cudaMemcpyAsync(h->d.sc, h->hs, sizeof(Scal), cudaMemcpyHostToDevice, h->st));
+  }
+  h->have_iterate = true;
+  const int pc = h->precond;
+  cudaGraphExec_t* gx = nullptr;
+  if ((rc = ensure_graph(h, pc, true, &gx))) return rc;
+  int64_t cg_total = 0;
+  int cg_max_step = 0;
+  int status = IPM_MAX_ITER;
+  for (int it = 0; it < h->opt.max_ipm; ++it) {
+    CUDA_TRY(h, cudaGraphLaunch(*gx, h->st));
+    CUDA_TRY(h, cudaMemcpyAsync(h->hs, h->d.sc, sizeof(Scal), cudaMemcpyDeviceToHost, h->st));
+    if (h->opt.timeout_ms > 0) {
+      CUDA_TRY(h, cudaEventRecord(h->ev, h->st));
+      while (true) {
+        cudaError_t q = cudaEventQuery(h->ev);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) return fail(h, IPM_ERR_CUDA, cudaGetErrorString(q));
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (ms > h->opt.timeout_ms) {
+          h->info.status = IPM_ERR_TIMEOUT;
+          leave(h, stream);
+          return fail(h, IPM_ERR_TIMEOUT, "timeout_ms exceeded");
+        }
+        std::this_thread::yield();
+      }
+    } else {
+      CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    }
+    const Scal& s = *h->hs;
+    cg_total += s.cg_iter;
+    cg_max_step = std::max(cg_max_step, s.cg_iter);
+    if (s.stop) {
+      status = s.status == DS_OK ? IPM_OK : s.status == DS_MAX_ITER ? IPM_MAX_ITER
+             : s.status == DS_CG_STALL ? IPM_CG_STALL : IPM_NUMERICAL;
+      break;
+    }
+  }
+  const Scal& s = *h->hs;
+  ipm_info& in = h->info;
+  in.status = status;
+  in.ipm_iters = s.ipm_iter;
+  in.cg_iters = cg_total;
+  in.max_cg_step = cg_max_step;
+  in.max_stiff_rows = s.max_stiff_seen;
+  in.precond = pc;
+  in.rel_kkt = s.rel_kkt;
+  in.primal_res = s.res_primal;
+  in.dual_res = s.res_dual;
+  in.gap_res = s.res_gap;
+  in.primal_obj = s.pobj;
+  in.dual_obj = s.dobj;
+  in.mu = s.mu;
+  in.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if ((rc = leave(h, stream))) return rc;
+  return status;
+}
+
+int ipm_get_xyz(ipm_handle* h, double* x, double* y, double* zl, double* zu, double* s, ipm_info* info, int mem, void* stream) {
+  if (!h) return IPM_ERR_ARG;
+  if (!h->loaded || !h->have_iterate) return fail(h, IPM_ERR_STATE, "no iterate");
+  int rc;
+  if ((rc = enter(h, stream))) return rc;
+  const Dev& d = h->d;
+  if ((rc = copy_out(h, x, d.x, d.n, mem))) return rc;
+  if ((rc = copy_out(h, y, d.y, d.m, mem))) return rc;
+  if ((rc = copy_out(h, zl, d.zl, d.n, mem))) return rc;
+  if ((rc = copy_out(h, zu, d.zu, d.n, mem))) return rc;
+  if ((rc = copy_out(h, s, d.s, d.m, mem))) return rc;
+  if (mem == IPM_MEM_HOST) CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  if (info) *info = h->info;
+  return leave(h, stream);
+}
+
+int ipm_set_iterate(ipm_handle* h, const double* x, const double* s, const double* y, const double* zl,
+                    const double* zu, double mu, int mem, void* stream) {
+  if (!h) return IPM_ERR_ARG;
+  if (!h->loaded) return fail(h, IPM_ERR_STATE, "ipm_set_iterate before ipm_set_qp");
+  if (!(mu > 0) || !std::isfinite(mu)) return fail(h, IPM_ERR_ARG, "mu must be positive");
+  int rc;
+  const Dev& d = h->d;
+  // validate strict interiority on a host copy
+  std::vector<double> hx, hs_, hy, hzl, hzu, hl(d.n), hu(d.n);
+  if ((rc = fetch(h, x, d.n, mem, hx)) || (rc = fetch(h, s, d.m, mem, hs_)) || (rc = fetch(h, y, d.m, mem, hy)) ||
+      (rc = fetch(h, zl, d.n, mem, hzl)) || (rc = fetch(h, zu, d.n, mem, hzu)))
+    return rc;
+  CUDA_TRY(h, cudaMemcpy(hl.data(), d.l, 8 * d.n, cudaMemcpyDeviceToHost));
+  CUDA_TRY(h, cudaMemcpy(hu.data(), d.u, 8 * d.n, cudaMemcpyDeviceToHost));
+  for (int64_t j = 0; j < d.n; ++j) {
+    if (!std::isfinite(hx[j])) return fail(h, IPM_ERR_ARG, "x not finite");
+    if (std::isfinite(hl[j]) && !(hx[j] > hl[j] && hzl[j] > 0)) return fail(h, IPM_ERR_ARG, "x/z_l not interior");
+    if (std::isfinite(hu[j]) && !(hx[j] < hu[j] && hzu[j] > 0)) return fail(h, IPM_ERR_ARG, "x/z_u not interior");
+    if (!std::isfinite(hl[j])) hzl[j] = 0.0;
+    if (!std::isfinite(hu[j])) hzu[j] = 0.0;
+  }
+  for (int64_t k = 0; k < d.m; ++k)
+    if (!(hs_[k] > 0 && hy[k] > 0) || !std::isfinite(hs_[k]) || !std::isfinite(hy[k])) return fail(h, IPM_ERR_ARG, "s/y not positive");
+  if ((rc = enter(h, stream))) return rc;
+  if ((rc = copy_in(h, d.x, hx.data(), d.n, IPM_MEM_HOST))) return rc;
+  if ((rc = copy_in(h, d.s, hs_.data(), d.m, IPM_MEM_HOST))) return rc;
+  if ((rc = copy_in(h, d.y, hy.data(), d.m, IPM_MEM_HOST))) return rc;
+  if ((rc = copy_in(h, d.zl, hzl.data(), d.n, IPM_MEM_HOST))) return rc;
+  if ((rc = copy_in(h, d.zu, hzu.data(), d.n, IPM_MEM_HOST))) return rc;
+  if ((rc = pull_scal(h))) return rc;
+  push_options(h);
+  h->hs->mu = mu;
+  h->hs->mu0 = mu;
+  h->hs->status = DS_RUNNING;
+  h->hs->stop = 0;
+  CUDA_TRY(h, cudaMemcpyAsync(d.sc, h->hs, sizeof(Scal), cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, launch_residual_summary(d, h->g, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  h->have_iterate = true;
+  return leave(h, stream);
+}
+
+int ipm_residuals(ipm_handle* h, double* rd, double* rp, double* rs, double* rl, double* ru, double* kkt, int mem, void* stream) {
+  if (!h) return IPM_ERR_ARG;
+  if (!h->loaded || !h->have_iterate) return fail(h, IPM_ERR_STATE, "no iterate");
+  int rc;
+  if ((rc = enter(h, stream))) return rc;
+  const Dev& d = h->d;
+  CUDA_TRY(h, launch_residual_summary(d, h->g, h->st));
+  // complementarity residuals into scratch vectors (ds: r_s, dzl: r_l, dzu: r_u)
+  CUDA_TRY(h, launch_comp_resid(d, h->g, h->st));
+  if ((rc = copy_out(h, rd, d.rd, d.n, mem))) return rc;
+  if ((rc = copy_out(h, rp, d.rp, d.m, mem))) return rc;
+  if ((rc = copy_out(h, rs, d.ds, d.m, mem))) return rc;
+  if ((rc = copy_out(h, rl, d.dzl, d.n, mem))) return rc;
+  if ((rc = copy_out(h, ru, d.dzu, d.n, mem))) return rc;
+  if ((rc = pull_scal(h))) return rc;
+  if (kkt) {
+    kkt[0] = h->hs->rel_kkt;
+    kkt[1] = h->hs->res_primal;
+    kkt[2] = h->hs->res_dual;
+    kkt[3] = h->hs->res_gap;
+  }
+  return leave(h, stream);
+}
+
+int ipm_apply_kkt(ipm_handle* h, const double* p, double* q, int mem, void* stream) {
+  if (!h || !p || !q) return IPM_ERR_ARG;
+  if (!h->loaded || !h->have_iterate) return fail(h, IPM_ERR_STATE, "no iterate");
+  int rc;
+  if ((rc = enter(h, stream))) return rc;
+  const Dev& d = h->d;
+  CUDA_TRY(h, launch_diag_update(d, h->g, h->st));
+  if ((rc = copy_in(h, d.p, p, d.n, mem))) return rc;
+  CUDA_TRY(h, launch_apply(d, h->g, h->st));
+  if ((rc = copy_out(h, q, d.q, d.n, mem))) return rc;
+  if (mem == IPM_MEM_HOST) CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return leave(h, stream);
+}
+
+int ipm_precond_diag(ipm_handle* h, double* diag, int mem, void* stream) {
+  if (!h || !diag) return IPM_ERR_ARG;
+  if (!h->loaded || !h->have_iterate) return fail(h, IPM_ERR_STATE, "no iterate");
+  int rc;
+  if ((rc = enter(h, stream))) return rc;
+  const Dev& d = h->d;
+  CUDA_TRY(h, launch_diag_update(d, h->g, h->st));
+  CUDA_TRY(h, launch_jacobi_full(d, h->g, d.q, h->st));
+  if ((rc = copy_out(h, diag, d.q, d.n, mem))) return rc;
+  if (mem == IPM_MEM_HOST) CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return leave(h, stream);
+}
+
+int ipm_newton_direction(ipm_handle* h, double eta, double* dx, double* ds, double* dy, double* dzl, double* dzu,
+                         ipm_cg_report* rep, int mem, void* stream) {
+  if (!h) return IPM_ERR_ARG;
+  if (!h->loaded || !h->have_iterate) return fail(h, IPM_ERR_STATE, "no iterate");
+  int rc;
+  if ((rc = enter(h, stream))) return rc;
+  const Dev& d = h->d;
+  // residual summary at the current iterate, then eta
+  CUDA_TRY(h, launch_residual_summary(d, h->g, h->st));
+  if ((rc = pull_scal(h))) return rc;
+  push_options(h);
+  Scal& s = *h->hs;
+  if (eta > 0) {
+    s.eta = eta;
+  } else {
+    double e = s.eta_factor * s.rel_kkt;
+    s.eta = std::min(s.eta_max, std::max(s.eta_min, std::isfinite(e) ? e : s.eta_max));
+  }
+  CUDA_TRY(h, cudaMemcpyAsync(d.sc, h->hs, sizeof(Scal), cudaMemcpyHostToDevice, h->st));
+  cudaGraphExec_t* gx = nullptr;
+  if ((rc = ensure_graph(h, h->precond, false, &gx))) return rc;
+  CUDA_TRY(h, cudaGraphLaunch(*gx, h->st));
+  if ((rc = copy_out(h, dx, d.dx, d.n, mem))) return rc;
+  if ((rc = copy_out(h, ds, d.ds, d.m, mem))) return rc;
+  if ((rc = copy_out(h, dy, d.dy, d.m, mem))) return rc;
+  if ((rc = copy_out(h, dzl, d.dzl, d.n, mem))) return rc;
+  if ((rc = copy_out(h, dzu, d.dzu, d.n, mem))) return rc;
+  if ((rc = pull_scal(h))) return rc;
+  if (rep) {
+    rep->iters = s.cg_iter;
+    rep->converged = s.cg_conv;
+    rep->stiff_rows = h->precond == PC_JACOBI_LR ? s.n_stiff : 0;
+    rep->rel_res = s.rhs2 > 0 ? std::sqrt(s.rr / s.rhs2) : 0.0;
+    rep->eta = s.eta;
+  }
+  return leave(h, stream);
+}
+
+int ipm_step_lengths(ipm_handle* h, const double* dx, const double* ds, const double* dy, const double* dzl,
+                     const double* dzu, double tau, double* alpha_p, double* alpha_d, int mem, void* stream) {
+  if (!h || !alpha_p || !alpha_d) return IPM_ERR_ARG;
+  if (!h->loaded || !h->have_iterate) return fail(h, IPM_ERR_STATE, "no iterate");
+  if (!(tau > 0 && tau <= 1)) return fail(h, IPM_ERR_ARG, "tau must be in (0, 1]");
+  int rc;
+  if ((rc = enter(h, stream))) return rc;
+  const Dev& d = h->d;
+  if ((rc = copy_in(h, d.dx, dx, d.n, mem))) return rc;
+  if ((rc = copy_in(h, d.ds, ds, d.m, mem))) return rc;
+  if ((rc = copy_in(h, d.dy, dy, d.m, mem))) return rc;
+  if ((rc = copy_in(h, d.dzl, dzl, d.n, mem))) return rc;
+  if ((rc = copy_in(h, d.dzu, dzu, d.n, mem))) return rc;
+  if ((rc = pull_scal(h))) return rc;
+  const double tau_keep = h->hs->tau;
+  const int eq_keep = h->hs->equal_steps;
+  if ((rc = set_scal_double(h, &d.sc->tau, tau))) return rc;
+  int zero = 0;
+  CUDA_TRY(h, cudaMemcpyAsync(&d.sc->equal_steps, &zero, sizeof(int), cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, launch_ratio(d, h->g, h->st));
+  if ((rc = pull_scal(h))) return rc;
+  *alpha_p = h->hs->alpha_p;
+  *alpha_d = h->hs->alpha_d;
+  if ((rc = set_scal_double(h, &d.sc->tau, tau_keep))) return rc;
+  CUDA_TRY(h, cudaMemcpyAsync(&d.sc->equal_steps, &eq_keep, sizeof(int), cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return leave(h, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,179 @@
+// Shared device-side definitions of the sm_103a interior point library.
+//
+// Layout in HBM (all float64 unless stated; one arena per handle, see api.cu):
+//   R    : the "row" matrix [F; A_csr] in CSR (int64 row pointers, int32 columns).  Every
+//          operator product goes through it: H's factor term is R^T diag(w_R) R (w_R = f_w on
+//          F rows, 0 on A rows) and the constraint block is A = R[arow].
+//   RT   : R^T in CSR (rows = variables), built once at ipm_set_qp, so that R^T v is a
+//          deterministic gather (Section 4.1.1 stores the constraint transposes for the same
+//          reason: transpose-free SpMV).
+//   Hs   : optional explicit symmetric part of H in CSR (a dense H block is stored this way).
+//   Scalars of the solve live in one device struct (Scal); kernels read and write them so
+//   that no scalar crosses to the host inside an IPM iteration.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ipmk {
+
+constexpr int kWarp = 32;
+constexpr int kBlock = 256;          // threads per block of the streaming kernels
+constexpr int kMaxRedBlocks = 1024;  // upper bound of blocks that write reduction partials
+constexpr int kHistBins = 64;        // stiff-row ratio histogram bins (two per octave)
+
+// Device scalars of one handle.
+struct Scal {
+  // barrier parameter and control
+  double mu, mu0, eta, tol_kkt, tau;
+  double cnorm, bnorm;               // ||c||_inf, ||b||_inf (set once)
+  int ipm_iter, max_ipm, status, stop;
+  int equal_steps, eta_override;     // eta_override: eta was set by the caller
+  double eta_factor, eta_min, eta_max;
+  // PCG
+  double rz, pq, alpha, beta, rr, rhs2, tol2;
+  int cg_iter, cg_done, cg_max, cg_conv;
+  // preconditioner
+  double stiff_gamma, stiff_thresh;
+  int n_stiff, stiff_max, max_stiff_seen, chol_fail;
+  // step
+  double alpha_p, alpha_d;
+  // residual summary at the current iterate (written by k_resid_final)
+  double rel_kkt, res_primal, res_dual, res_gap, pobj, dobj, rnorm_mu, comp_mean;
+  double rp_inf, rd_inf, rc_inf;
+  int ncomp;
+  // reduction tickets (last-block pattern); each is returned to 0 by its last block
+  unsigned int ticket[8];
+};
+
+enum ScalTicket { T_PQ = 0, T_UPD = 1, T_CORR = 2, T_INIT = 3, T_HIST = 4, T_STEP = 5, T_MISC = 6 };
+
+// Status values written by the device (mirror enum ipm_status).
+enum DevStatus { DS_RUNNING = -1, DS_OK = 0, DS_MAX_ITER = 3, DS_CG_STALL = 4, DS_NUMERICAL = 5 };
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide reductions in a fixed order (warp tree, then warp 0 over the warp results).
+// Every thread of the block must call them; the result is valid in every thread.
+template <int OP>  // 0 sum, 1 max, 2 min
+__device__ __forceinline__ double block_reduce(double v, double* sh /* >= 32 doubles */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = OP == 0 ? warp_sum(v) : (OP == 1 ? warp_max(v) : warp_min(v));
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    const double id = OP == 0 ? 0.0 : (OP == 1 ? -INFINITY : INFINITY);
+    double t = lane < nw ? sh[lane] : id;
+    t = OP == 0 ? warp_sum(t) : (OP == 1 ? warp_max(t) : warp_min(t));
+    if (lane == 0) sh[0] = t;
+  }
+  __syncthreads();
+  double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// Last-block-done grid reduction.  Each block stores its partial for each of NQ quantities
+// at partials[q * kMaxRedBlocks + blockIdx.x]; the last block to arrive reduces them in
+// block-index order and returns true (in all of its threads) with the totals in out[].
+// Deterministic for a fixed grid size.  ops[q]: 0 sum, 1 max, 2 min.
+template <int NQ>
+__device__ bool grid_reduce(const double (&v)[NQ], const int (&ops)[NQ], double* partials,
+                            unsigned int* ticket, double (&out)[NQ], double* sh) {
+  double r[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+    r[q] = ops[q] == 0 ? block_reduce<0>(v[q], sh) : (ops[q] == 1 ? block_reduce<1>(v[q], sh) : block_reduce<2>(v[q], sh));
+  __shared__ bool s_last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) partials[q * kMaxRedBlocks + blockIdx.x] = r[q];
+    __threadfence();
+    unsigned int t = atomicAdd(ticket, 1u);
+    s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const double id = ops[q] == 0 ? 0.0 : (ops[q] == 1 ? -INFINITY : INFINITY);
+    double acc = id;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+      double pv = __ldcg(partials + q * kMaxRedBlocks + b);
+      acc = ops[q] == 0 ? acc + pv : (ops[q] == 1 ? fmax(acc, pv) : fmin(acc, pv));
+    }
+    out[q] = ops[q] == 0 ? block_reduce<0>(acc, sh) : (ops[q] == 1 ? block_reduce<1>(acc, sh) : block_reduce<2>(acc, sh));
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
+// Dot product of one CSR row with a dense vector, computed by one warp (all lanes return the
+// sum).  Lanes take entries lane, lane+32, ...; four independent accumulators keep loads in
+// flight; the combination order is fixed.
+template <bool SQ>
+__device__ __forceinline__ double warp_row_dot(const int64_t beg, const int64_t end, const int32_t* __restrict__ idx,
+                                               const double* __restrict__ val, const double* __restrict__ x) {
+  const int lane = threadIdx.x & 31;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int64_t e = beg + lane;
+  for (; e + 96 < end; e += 128) {
+    double v0 = __ldg(val + e), v1 = __ldg(val + e + 32), v2 = __ldg(val + e + 64), v3 = __ldg(val + e + 96);
+    int i0 = __ldg(idx + e), i1 = __ldg(idx + e + 32), i2 = __ldg(idx + e + 64), i3 = __ldg(idx + e + 96);
+    if (SQ) { v0 *= v0; v1 *= v1; v2 *= v2; v3 *= v3; }
+    a0 = fma(v0, __ldg(x + i0), a0);
+    a1 = fma(v1, __ldg(x + i1), a1);
+    a2 = fma(v2, __ldg(x + i2), a2);
+    a3 = fma(v3, __ldg(x + i3), a3);
+  }
+  for (; e < end; e += 32) {
+    double v0 = __ldg(val + e);
+    if (SQ) v0 *= v0;
+    a0 = fma(v0, __ldg(x + __ldg(idx + e)), a0);
+  }
+  return warp_sum((a0 + a1) + (a2 + a3));
+}
+
+// Same, over two vectors at once (one pass over the matrix).
+__device__ __forceinline__ void warp_row_dot2(const int64_t beg, const int64_t end, const int32_t* __restrict__ idx,
+                                              const double* __restrict__ val, const double* __restrict__ x1,
+                                              const double* __restrict__ x2, double& o1, double& o2) {
+  const int lane = threadIdx.x & 31;
+  double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+  int64_t e = beg + lane;
+  for (; e + 32 < end; e += 64) {
+    double v0 = __ldg(val + e), v1 = __ldg(val + e + 32);
+    int i0 = __ldg(idx + e), i1 = __ldg(idx + e + 32);
+    a0 = fma(v0, __ldg(x1 + i0), a0);
+    b0 = fma(v0, __ldg(x2 + i0), b0);
+    a1 = fma(v1, __ldg(x1 + i1), a1);
+    b1 = fma(v1, __ldg(x2 + i1), b1);
+  }
+  for (; e < end; e += 32) {
+    double v0 = __ldg(val + e);
+    int i0 = __ldg(idx + e);
+    a0 = fma(v0, __ldg(x1 + i0), a0);
+    b0 = fma(v0, __ldg(x2 + i0), b0);
+  }
+  o1 = warp_sum(a0 + a1);
+  o2 = warp_sum(b0 + b1);
+}
+
+__device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
+
+}  // namespace ipmk

@@ -1,0 +1,1072 @@
+// sm_103a kernels of the interior point method: residuals, diagonal update, right-hand side,
+// the matrix-free PCG iteration, direction recovery, ratio test and update.
+//
+// Operator (the condensed form of the paper's KKT matvec, Section 4.1.1 / Listing 1):
+//     K p = R^T (omega o (R p)) + Hs p + (h0 + sigma) o p,
+// where R = [F; A_csr] and omega = w_R + theta placed on the constraint rows, so that
+// R^T diag(omega) R = F^T W F + A^T Theta A.  One PCG iteration is two streaming passes:
+// k_op_rows (row gather over R) and k_op_cols (row gather over the stored transpose R^T).
+// All reductions are block-tree + last-block sums in block order: results are bitwise
+// reproducible for a fixed problem size.
+#include <algorithm>
+#include <cmath>
+
+#include "state.h"
+
+namespace ipmk {
+
+static __device__ __forceinline__ int gwarp() { return (blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
+static __device__ __forceinline__ int nwarps() { return (gridDim.x * blockDim.x) >> 5; }
+
+Geo make_geo(const Dev& d) {
+  auto blocks_for = [](int64_t items, int per_block) -> int {
+    int64_t b = (items + per_block - 1) / per_block;
+    if (b > kMaxRedBlocks) b = kMaxRedBlocks;
+    return (int)b;
+  };
+  Geo g;
+  const int wpb = kBlock / kWarp;
+  g.gR = blocks_for(d.nR, wpb);
+  g.gM = blocks_for(d.m, wpb);
+  g.gN = blocks_for(d.n, wpb);
+  return g;
+}
+
+// ------------------------------------------------------------------------------ setup
+
+// diag(H)_j = h0_j + sum_i w_R,i R_ij^2 + Hs_jj  (computed once; Section 4.1.2 caches it).
+__global__ void k_diagH(Dev d) {
+  for (int64_t j = gwarp(); j < d.n; j += nwarps()) {
+    double acc = warp_row_dot<true>(d.RT_ptr[j], d.RT_ptr[j + 1], d.RT_idx, d.RT_val, d.wR);
+    double hjj = 0.0;
+    if (d.Hs_ptr) {
+      for (int64_t e = d.Hs_ptr[j] + (threadIdx.x & 31); e < d.Hs_ptr[j + 1]; e += 32)
+        if (d.Hs_idx[e] == j) hjj += d.Hs_val[e];
+      hjj = warp_sum(hjj);
+    }
+    if ((threadIdx.x & 31) == 0) d.diagH[j] = d.h0[j] + acc + hjj;
+  }
+}
+
+cudaError_t launch_diagH(const Dev& d, cudaStream_t st) {
+  Geo g = make_geo(d);
+  if (g.gN) k_diagH<<<g.gN, kBlock, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------ residuals
+
+// t = R x; v = w_R o t; partial sum of w_R t^2 (the factor part of x^T H x).
+__global__ void k_rows_resid(Dev d, double* part) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int64_t r = gwarp(); r < d.nR; r += nwarps()) {
+    double t = warp_row_dot<false>(d.R_ptr[r], d.R_ptr[r + 1], d.R_idx, d.R_val, d.x);
+    if ((threadIdx.x & 31) == 0) {
+      const double w = d.wR[r];
+      d.tR[r] = t;
+      d.vR[r] = w * t;
+      acc = fma(w * t, t, acc);
+    }
+  }
+  acc = block_reduce<0>(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// Constraint rows: r_p = A x + s - b, r_s = s o y - mu, and y placed on R rows (vR2).
+__global__ void k_cons_resid(Dev d, double* part) {
+  __shared__ double sh[32];
+  const double mu = d.sc->mu;
+  double rp_inf = 0.0, viol = 0.0, rs_inf = 0.0, by = 0.0, sy = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.m; k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t row = d.arow[k];
+    const double ax = d.tR[row];
+    const double rp = ax + d.s[k] - d.b[k];
+    const double rs = d.s[k] * d.y[k] - mu;
+    d.rp[k] = rp;
+    d.vR2[row] = d.y[k];
+    rp_inf = fmax(rp_inf, fabs(rp));
+    viol = fmax(viol, ax - d.b[k]);
+    rs_inf = fmax(rs_inf, fabs(rs));
+    by = fma(d.b[k], d.y[k], by);
+    sy = fma(d.s[k], d.y[k], sy);
+  }
+  const int K = kMaxRedBlocks;
+  double v;
+  v = block_reduce<1>(rp_inf, sh); if (threadIdx.x == 0) part[1 * K + blockIdx.x] = v;
+  v = block_reduce<1>(viol, sh);   if (threadIdx.x == 0) part[2 * K + blockIdx.x] = v;
+  v = block_reduce<1>(rs_inf, sh); if (threadIdx.x == 0) part[3 * K + blockIdx.x] = v;
+  v = block_reduce<0>(by, sh);     if (threadIdx.x == 0) part[4 * K + blockIdx.x] = v;
+  v = block_reduce<0>(sy, sh);     if (threadIdx.x == 0) part[5 * K + blockIdx.x] = v;
+}
+
+// Variables: Hx = R^T vR + Hs x + h0 o x, A^T y = R^T vR2, r_d, r_l, r_u and the scalar parts
+// of the objective, the dual objective and the complementarity sum.
+__global__ void k_cols_resid(Dev d, double* part) {
+  __shared__ double sh[32];
+  const double mu = d.sc->mu;
+  double rd_inf = 0.0, hx_inf = 0.0, aty_inf = 0.0, rc_inf = 0.0, xHsx = 0.0, cx = 0.0, lzl = 0.0,
+         uzu = 0.0, tz = 0.0, bviol = 0.0;
+  const int lane = threadIdx.x & 31;
+  for (int64_t j = gwarp(); j < d.n; j += nwarps()) {
+    double hx_f, aty;
+    warp_row_dot2(d.RT_ptr[j], d.RT_ptr[j + 1], d.RT_idx, d.RT_val, d.vR, d.vR2, hx_f, aty);
+    double hs = 0.0;
+    if (d.Hs_ptr) hs = warp_row_dot<false>(d.Hs_ptr[j], d.Hs_ptr[j + 1], d.Hs_idx, d.Hs_val, d.x);
+    if (lane == 0) {
+      const double xj = d.x[j];
+      const double hsx = hs + d.h0[j] * xj;
+      const double hx = hx_f + hsx;
+      const double zl = d.zl[j], zu = d.zu[j];
+      const double rd = hx + d.c[j] + aty - zl + zu;
+      d.Hx[j] = hx;
+      d.Aty[j] = aty;
+      d.rd[j] = rd;
+      rd_inf = fmax(rd_inf, fabs(rd));
+      hx_inf = fmax(hx_inf, fabs(hx));
+      aty_inf = fmax(aty_inf, fabs(aty));
+      xHsx = fma(xj, hsx, xHsx);
+      cx = fma(d.c[j], xj, cx);
+      if (d.fl[j]) {
+        const double tl = xj - d.l[j];
+        rc_inf = fmax(rc_inf, fabs(tl * zl - mu));
+        lzl = fma(d.l[j], zl, lzl);
+        tz = fma(tl, zl, tz);
+        bviol = fmax(bviol, -tl);
+      }
+      if (d.fu[j]) {
+        const double tu = d.u[j] - xj;
+        rc_inf = fmax(rc_inf, fabs(tu * zu - mu));
+        uzu = fma(d.u[j], zu, uzu);
+        tz = fma(tu, zu, tz);
+        bviol = fmax(bviol, -tu);
+      }
+    }
+  }
+  const int K = kMaxRedBlocks;
+  double v;
+  v = block_reduce<1>(rd_inf, sh);  if (threadIdx.x == 0) part[6 * K + blockIdx.x] = v;
+  v = block_reduce<1>(hx_inf, sh);  if (threadIdx.x == 0) part[7 * K + blockIdx.x] = v;
+  v = block_reduce<1>(aty_inf, sh); if (threadIdx.x == 0) part[8 * K + blockIdx.x] = v;
+  v = block_reduce<1>(rc_inf, sh);  if (threadIdx.x == 0) part[9 * K + blockIdx.x] = v;
+  v = block_reduce<0>(xHsx, sh);    if (threadIdx.x == 0) part[10 * K + blockIdx.x] = v;
+  v = block_reduce<0>(cx, sh);      if (threadIdx.x == 0) part[11 * K + blockIdx.x] = v;
+  v = block_reduce<0>(lzl, sh);     if (threadIdx.x == 0) part[12 * K + blockIdx.x] = v;
+  v = block_reduce<0>(uzu, sh);     if (threadIdx.x == 0) part[13 * K + blockIdx.x] = v;
+  v = block_reduce<0>(tz, sh);      if (threadIdx.x == 0) part[14 * K + blockIdx.x] = v;
+  v = block_reduce<1>(bviol, sh);   if (threadIdx.x == 0) part[15 * K + blockIdx.x] = v;
+}
+
+// One block: totals of the partials, then the relative KKT residual (primal, dual, gap), the
+// objective values and the norm of the mu test.
+//   primal = max(viol_A, viol_bounds) / (1 + ||b||), dual = ||r_d|| / (1 + max(||c||, ||Hx||, ||A^T y||)),
+//   gap = |pobj - dobj| / (1 + |pobj| + |dobj|),
+//   ||r||_mu = max(||r_s, r_l, r_u||, (1 + |pobj|) / N_c * max(||r_p|| / (1 + ||b||), ||r_d|| / (1 + ||c||))).
+__global__ void k_resid_final(Dev d, int gR, int gM, int gN, const double* part) {
+  __shared__ double sh[32];
+  const int K = kMaxRedBlocks;
+  auto tot = [&](int q, int nb, int op) -> double {
+    double acc = op == 0 ? 0.0 : -INFINITY;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+      double v = part[q * K + b];
+      acc = op == 0 ? acc + v : fmax(acc, v);
+    }
+    return op == 0 ? block_reduce<0>(acc, sh) : block_reduce<1>(acc, sh);
+  };
+  const double xFx = tot(0, gR, 0);
+  const double rp_inf = fmax(0.0, tot(1, gM, 1));
+  const double viol_a = fmax(0.0, tot(2, gM, 1));
+  const double rs_inf = fmax(0.0, tot(3, gM, 1));
+  const double by = tot(4, gM, 0);
+  const double sy = tot(5, gM, 0);
+  const double rd_inf = fmax(0.0, tot(6, gN, 1));
+  const double hx_inf = fmax(0.0, tot(7, gN, 1));
+  const double aty_inf = fmax(0.0, tot(8, gN, 1));
+  const double rc_inf = fmax(0.0, tot(9, gN, 1));
+  const double xHsx = tot(10, gN, 0);
+  const double cx = tot(11, gN, 0);
+  const double lzl = tot(12, gN, 0);
+  const double uzu = tot(13, gN, 0);
+  const double tz = tot(14, gN, 0);
+  const double viol_b = fmax(0.0, tot(15, gN, 1));
+  if (threadIdx.x == 0) {
+    Scal* sc = d.sc;
+    const double xHx = xFx + xHsx;
+    const double pobj = 0.5 * xHx + cx;
+    const double dobj = -0.5 * xHx - by + lzl - uzu;
+    const double bn = sc->bnorm, cn = sc->cnorm;
+    const double primal = fmax(viol_a, viol_b) / (1.0 + bn);
+    const double dual = rd_inf / (1.0 + fmax(cn, fmax(hx_inf, aty_inf)));
+    const double gap = fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj));
+    sc->res_primal = primal;
+    sc->res_dual = dual;
+    sc->res_gap = gap;
+    double rk = fmax(primal, fmax(dual, gap));
+    if (!isfinite(rk)) rk = INFINITY;
+    sc->rel_kkt = rk;
+    sc->pobj = pobj;
+    sc->dobj = dobj;
+    sc->rp_inf = rp_inf;
+    sc->rd_inf = rd_inf;
+    sc->rc_inf = fmax(rs_inf, rc_inf);
+    const int nc = sc->ncomp > 0 ? sc->ncomp : 1;
+    const double ep = rp_inf / (1.0 + bn), ed = rd_inf / (1.0 + cn);
+    sc->rnorm_mu = fmax(fmax(rs_inf, rc_inf), (1.0 + fabs(pobj)) / nc * fmax(ep, ed));
+    sc->comp_mean = (sy + tz) / nc;
+  }
+}
+
+cudaError_t launch_residual_summary(const Dev& d, const Geo& g, cudaStream_t st) {
+  double* part = d.partials;
+  if (d.nR) {
+    cudaMemsetAsync(d.vR2, 0, sizeof(double) * d.nR, st);
+    k_rows_resid<<<g.gR, kBlock, 0, st>>>(d, part);
+  }
+  if (d.m) k_cons_resid<<<g.gM, kBlock, 0, st>>>(d, part);
+  k_cols_resid<<<g.gN, kBlock, 0, st>>>(d, part);
+  k_resid_final<<<1, 1024, 0, st>>>(d, g.gR, g.gM, g.gN, part);
+  return cudaGetLastError();
+}
+
+// Complementarity residuals as vectors (for the step-level query): r_s into ds, r_l into dzl,
+// r_u into dzu.
+__global__ void k_comp_resid(Dev d) {
+  const double mu = d.sc->mu;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.m; k += (int64_t)gridDim.x * blockDim.x)
+    d.ds[k] = d.s[k] * d.y[k] - mu;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x) {
+    d.dzl[j] = d.fl[j] ? (d.x[j] - d.l[j]) * d.zl[j] - mu : 0.0;
+    d.dzu[j] = d.fu[j] ? (d.u[j] - d.x[j]) * d.zu[j] - mu : 0.0;
+  }
+}
+
+cudaError_t launch_comp_resid(const Dev& d, const Geo& g, cudaStream_t st) {
+  k_comp_resid<<<std::max(g.gN, g.gM), kBlock, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------ start point
+
+static __device__ void set_eta(Scal* sc);
+
+// x0 = 0 projected into the box shrunk by delta_j = 0.1 min(1, (u_j - l_j) / 2) (0.1 for a
+// one-sided bound; 0 for a free variable).
+__global__ void k_start_x(Dev d) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x) {
+    const bool fl = d.fl[j], fu = d.fu[j];
+    const double width = (fl && fu) ? d.u[j] - d.l[j] : 2.0;
+    const double delta = 0.1 * fmin(1.0, 0.5 * width);
+    double x = 0.0;
+    if (fl) x = fmax(x, d.l[j] + delta);
+    if (fu) x = fmin(x, d.u[j] - delta);
+    d.x[j] = x;
+  }
+}
+
+// s0 = max(b - A x0, 1)   (tR holds R x0)
+__global__ void k_start_s(Dev d) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.m; k += (int64_t)gridDim.x * blockDim.x)
+    d.s[k] = fmax(d.b[k] - d.tR[d.arow[k]], 1.0);
+}
+
+// g = H x0 + c; z_l0 = max(1, g), z_u0 = max(1, -g) on finite bounds; y0 = max(1, rms(g)).
+__global__ void k_start_z(Dev d) {
+  __shared__ double sh[32];
+  double g2 = 0.0;
+  const int lane = threadIdx.x & 31;
+  for (int64_t j = gwarp(); j < d.n; j += nwarps()) {
+    double hx = warp_row_dot<false>(d.RT_ptr[j], d.RT_ptr[j + 1], d.RT_idx, d.RT_val, d.vR);
+    double hs = 0.0;
+    if (d.Hs_ptr) hs = warp_row_dot<false>(d.Hs_ptr[j], d.Hs_ptr[j + 1], d.Hs_idx, d.Hs_val, d.x);
+    if (lane == 0) {
+      const double g = hx + hs + d.h0[j] * d.x[j] + d.c[j];
+      d.zl[j] = d.fl[j] ? fmax(1.0, g) : 0.0;
+      d.zu[j] = d.fu[j] ? fmax(1.0, -g) : 0.0;
+      g2 = fma(g, g, g2);
+    }
+  }
+  double v[1] = {g2};
+  const int ops[1] = {0};
+  double out[1];
+  if (grid_reduce<1>(v, ops, d.partials + 26 * kMaxRedBlocks, &d.sc->ticket[T_MISC], out, sh)) {
+    if (threadIdx.x == 0) d.sc->alpha = fmax(1.0, sqrt(out[0] / (double)d.n));  // y0 (scratch)
+  }
+}
+
+__global__ void k_start_y(Dev d) {
+  const double y0 = d.sc->alpha;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.m; k += (int64_t)gridDim.x * blockDim.x)
+    d.y[k] = y0;
+}
+
+__global__ void k_start_mu(Dev d) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    Scal* sc = d.sc;
+    sc->mu0 = sc->comp_mean > 0.0 ? sc->comp_mean : 1.0;
+    sc->mu = sc->mu0;
+    sc->ipm_iter = 0;
+    sc->stop = 0;
+    sc->status = DS_RUNNING;
+    set_eta(sc);
+  }
+}
+
+cudaError_t launch_start_point(const Dev& d, const Geo& g, cudaStream_t st) {
+  k_start_x<<<g.gN, kBlock, 0, st>>>(d);
+  if (d.nR) k_rows_resid<<<g.gR, kBlock, 0, st>>>(d, d.partials);
+  if (d.m) k_start_s<<<g.gM, kBlock, 0, st>>>(d);
+  k_start_z<<<g.gN, kBlock, 0, st>>>(d);
+  if (d.m) k_start_y<<<g.gM, kBlock, 0, st>>>(d);
+  cudaError_t e = launch_residual_summary(d, g, st);
+  if (e != cudaSuccess) return e;
+  k_start_mu<<<1, 32, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------ control
+
+// Inexact-Newton forcing term of the PCG solve: ||r|| <= eta ||rhs|| with
+// eta = clamp(eta_factor * relKKT, eta_min, eta_max) (reading; the paper states no tolerance).
+static __device__ void set_eta(Scal* sc) {
+  if (sc->eta_override) return;
+  double e = sc->eta_factor * sc->rel_kkt;
+  if (!(e <= sc->eta_max)) e = sc->eta_max;
+  if (e < sc->eta_min) e = sc->eta_min;
+  sc->eta = e;
+}
+
+// Algorithm 1's tail on the device: stop when rel KKT <= tol (reading of "mu <= mu_tol"),
+// else mu <- mu / 10 when ||r|| < mu; then the PCG tolerance eta for the next Newton step.
+__global__ void k_control(Dev d) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  Scal* sc = d.sc;
+  sc->ipm_iter += 1;
+  const double rk = sc->rel_kkt;
+  if (sc->status == DS_NUMERICAL || sc->status == DS_CG_STALL) {
+    sc->stop = 1;
+  } else if (!isfinite(rk) || !isfinite(sc->pobj)) {
+    sc->stop = 1;
+    sc->status = DS_NUMERICAL;
+  } else if (rk <= sc->tol_kkt) {
+    sc->stop = 1;
+    sc->status = DS_OK;
+  } else if (sc->ipm_iter >= sc->max_ipm) {
+    sc->stop = 1;
+    sc->status = DS_MAX_ITER;
+  } else if (sc->rnorm_mu < sc->mu) {
+    sc->mu = fmax(sc->mu * 0.1, sc->mu0 * 1e-16);
+  }
+  set_eta(sc);
+}
+
+cudaError_t launch_control(const Dev& d, cudaStream_t st) {
+  k_control<<<1, 32, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------ diagonal update
+
+// theta = y / s; omega = w_R + theta on the constraint rows (omega preset to w_R).
+__global__ void k_diag_m(Dev d) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.m; k += (int64_t)gridDim.x * blockDim.x) {
+    const double th = d.y[k] / d.s[k];
+    const int32_t row = d.arow[k];
+    d.theta[k] = th;
+    d.omega[row] = d.wR[row] + th;
+    d.thR[row] = th;
+  }
+}
+
+// sigma = z_l / t_l + z_u / t_u; M0 = diag(H) + sigma.
+__global__ void k_diag_n(Dev d) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x) {
+    double sg = 0.0;
+    if (d.fl[j]) sg += d.zl[j] / (d.x[j] - d.l[j]);
+    if (d.fu[j]) sg += d.zu[j] / (d.u[j] - d.x[j]);
+    d.sigma[j] = sg;
+    d.M0[j] = d.diagH[j] + sg;
+  }
+}
+
+cudaError_t launch_diag_update(const Dev& d, const Geo& g, cudaStream_t st) {
+  if (d.nR) {
+    cudaMemcpyAsync(d.omega, d.wR, sizeof(double) * d.nR, cudaMemcpyDeviceToDevice, st);
+    cudaMemsetAsync(d.thR, 0, sizeof(double) * d.nR, st);
+  }
+  if (d.m) k_diag_m<<<g.gM, kBlock, 0, st>>>(d);
+  k_diag_n<<<g.gN, kBlock, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------ Jacobi
+
+// M_j = M0_j + sum_i R_ij^2 thR_i  (thR: theta of the rows kept in the diagonal part).
+// Writes 1 / M_j to out (INV) or M_j.
+template <bool INV>
+__global__ void k_jacobi(Dev d, double* out) {
+  for (int64_t j = gwarp(); j < d.n; j += nwarps()) {
+    double a = warp_row_dot<true>(d.RT_ptr[j], d.RT_ptr[j + 1], d.RT_idx, d.RT_val, d.thR);
+    if ((threadIdx.x & 31) == 0) {
+      const double mj = d.M0[j] + a;
+      out[j] = INV ? 1.0 / mj : mj;
+    }
+  }
+}
+
+cudaError_t launch_jacobi_full(const Dev& d, const Geo& g, double* out, cudaStream_t st) {
+  k_jacobi<false><<<g.gN, kBlock, 0, st>>>(d, out);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------ stiff rows
+
+// ratio_k = theta_k sum_j A_kj^2 / M0_j; histogram of log2(ratio / gamma) in half-octave bins;
+// the last block picks the smallest threshold bin whose cumulative count from the top stays
+// <= stiff_max.  Rows with ratio >= stiff_thresh form the low-rank correction.
+__global__ void k_stiff_ratio(Dev d) {
+  __shared__ unsigned int h[kHistBins];
+  __shared__ bool s_last;
+  for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) h[i] = 0u;
+  __syncthreads();
+  const double gamma = d.sc->stiff_gamma;
+  for (int64_t k = gwarp(); k < d.m; k += nwarps()) {
+    const int32_t row = d.arow[k];
+    // 1 / M0 via the gather: sum_j R_ij^2 / M0_j; M0 inverted on the fly
+    const int64_t beg = d.R_ptr[row], end = d.R_ptr[row + 1];
+    double acc = 0.0;
+    for (int64_t e = beg + (threadIdx.x & 31); e < end; e += 32) {
+      const double v = d.R_val[e];
+      acc += v * v / d.M0[d.R_idx[e]];
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) {
+      const double ratio = d.theta[k] * acc;
+      d.ratio[k] = ratio;
+      if (ratio > gamma) {
+        int bin = (int)floor(2.0 * log2(ratio / gamma));
+        bin = bin < 0 ? 0 : (bin >= kHistBins ? kHistBins - 1 : bin);
+        atomicAdd(&h[bin], 1u);
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kHistBins; i += blockDim.x)
+    if (h[i]) atomicAdd(&d.hist[i], h[i]);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int t = atomicAdd(&d.sc->ticket[T_HIST], 1u);
+    s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    const int cap = d.sc->stiff_max;
+    unsigned int cum = 0;
+    int cut = kHistBins;  // no stiff rows
+    for (int b = kHistBins - 1; b >= 0; --b) {
+      unsigned int c = __ldcg(&d.hist[b]);
+      if (cum + c > (unsigned)cap) break;
+      cum += c;
+      cut = b;
+    }
+    // rows in bins >= cut are stiff: threshold = gamma * 2^(cut/2) (bins are half octaves)
+    d.sc->stiff_thresh = cut >= kHistBins ? INFINITY : (cut == 0 ? gamma : gamma * exp2(0.5 * cut));
+    for (int b = 0; b < kHistBins; ++b) d.hist[b] = 0u;
+    d.sc->ticket[T_HIST] = 0u;
+  }
+}
+
+// Ordered compaction (one block): slot of every stiff row, thR = 0 on stiff rows.
+__global__ void k_stiff_compact(Dev d) {
+  __shared__ int wsum[32];
+  __shared__ int base;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  const double thr = d.sc->stiff_thresh;
+  const double gamma = d.sc->stiff_gamma;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t k0 = 0; k0 < d.m; k0 += blockDim.x) {
+    const int64_t k = k0 + threadIdx.x;
+    int flag = 0;
+    if (k < d.m) {
+      const double rt = d.ratio[k];
+      flag = (rt > gamma && rt >= thr) ? 1 : 0;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, flag);
+    const int pre = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) wsum[wid] = __popc(bal);
+    __syncthreads();
+    int off = 0, total = 0;
+    for (int w = 0; w < nw; ++w) { if (w < wid) off += wsum[w]; total += wsum[w]; }
+    if (k < d.m) {
+      const int32_t row = d.arow[k];
+      const int slot = base + off + pre;
+      if (flag && slot < d.stiff_cap) {
+        d.stiff_k[slot] = (int32_t)k;
+        d.slotR[row] = slot;
+        d.thR[row] = 0.0;
+      } else {
+        d.slotR[row] = -1;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) base += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int ns = base < d.stiff_cap ? base : d.stiff_cap;
+    d.sc->n_stiff = ns;
+    if (ns > d.sc->max_stiff_seen) d.sc->max_stiff_seen = ns;
+  }
+}
+
+// Stiff entries per variable (count, then ordered fill) from the stored transpose.
+__global__ void k_sc_count(Dev d) {
+  if (d.sc->n_stiff == 0) return;
+  for (int64_t j = gwarp(); j < d.n; j += nwarps()) {
+    int cnt = 0;
+    for (int64_t e = d.RT_ptr[j] + (threadIdx.x & 31); e < d.RT_ptr[j + 1]; e += 32)
+      cnt += d.slotR[d.RT_idx[e]] >= 0 ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0) d.sc_cnt[j] = cnt;
+  }
+}
+
+// Exclusive scan of sc_cnt into sc_ptr (one block).
+__global__ void k_sc_scan(Dev d) {
+  if (d.sc->n_stiff == 0) return;
+  __shared__ long long wsum[32];
+  __shared__ long long base;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t j0 = 0; j0 < d.n; j0 += blockDim.x) {
+    const int64_t j = j0 + threadIdx.x;
+    long long v = j < d.n ? d.sc_cnt[j] : 0;
+    long long incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      long long t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    long long off = 0, total = 0;
+    for (int w = 0; w < nw; ++w) { if (w < wid) off += wsum[w]; total += wsum[w]; }
+    if (j < d.n) d.sc_ptr[j] = base + off + incl - v;
+    __syncthreads();
+    if (threadIdx.x == 0) base += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    d.sc_ptr[d.n] = base;
+    if (base > d.sc_cap) d.sc->n_stiff = 0;   // does not fit: fall back to plain Jacobi
+  }
+}
+
+__global__ void k_sc_fill(Dev d) {
+  if (d.sc->n_stiff == 0) return;
+  const int lane = threadIdx.x & 31;
+  for (int64_t j = gwarp(); j < d.n; j += nwarps()) {
+    int64_t out = d.sc_ptr[j];
+    for (int64_t e0 = d.RT_ptr[j]; e0 < d.RT_ptr[j + 1]; e0 += 32) {
+      const int64_t e = e0 + lane;
+      int slot = -1;
+      if (e < d.RT_ptr[j + 1]) slot = d.slotR[d.RT_idx[e]];
+      const unsigned bal = __ballot_sync(0xffffffffu, slot >= 0);
+      if (slot >= 0) {
+        const int64_t pos = out + __popc(bal & ((1u << lane) - 1u));
+        d.sc_slot[pos] = slot;
+        d.sc_val[pos] = d.RT_val[e];
+      }
+      out += __popc(bal);
+    }
+  }
+}
+
+// G = Theta_s^{-1} + A_s M^{-1} A_s^T (dense, n_stiff x n_stiff, leading dimension stiff_cap).
+// One block per stiff row a accumulates row a in shared memory: for every entry (j, R_aj) of
+// the row, add R_aj / M_j * (column j's stiff entries).  Entries of a column list are distinct
+// slots, so lanes never collide; the j order is fixed, hence deterministic.
+__global__ void k_gram_G(Dev d) {
+  extern __shared__ double grow[];
+  const int ns = d.sc->n_stiff;
+  const int cap = d.stiff_cap;
+  for (int a = blockIdx.x; a < ns; a += gridDim.x) {
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) grow[i] = 0.0;
+    __syncthreads();
+    const int32_t k = d.stiff_k[a];
+    const int32_t row = d.arow[k];
+    for (int64_t e = d.R_ptr[row]; e < d.R_ptr[row + 1]; ++e) {
+      const int32_t j = d.R_idx[e];
+      const double f = d.R_val[e] * d.Minv[j];
+      const int64_t b0 = d.sc_ptr[j], b1 = d.sc_ptr[j + 1];
+      for (int64_t t = b0 + threadIdx.x; t < b1; t += blockDim.x) grow[d.sc_slot[t]] += f * d.sc_val[t];
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+      double v = grow[i];
+      if (i == a) v += 1.0 / d.theta[k];
+      d.G[(int64_t)a * cap + i] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------ rhs
+
+// u = theta o r_p - r_s / s placed on R rows (vR2, pre-zeroed).
+__global__ void k_rhs_m(Dev d) {
+  const double mu = d.sc->mu;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.m; k += (int64_t)gridDim.x * blockDim.x) {
+    const double s = d.s[k];
+    const double rs = s * d.y[k] - mu;
+    d.vR2[d.arow[k]] = d.theta[k] * d.rp[k] - rs / s;
+  }
+}
+
+// rhs = -r_d - r_l / t_l + r_u / t_u - R^T vR2; PCG start r = rhs, dx = 0; ||rhs||^2.
+__global__ void k_rhs_n(Dev d) {
+  __shared__ double sh[32];
+  const double mu = d.sc->mu;
+  double r2 = 0.0;
+  for (int64_t j = gwarp(); j < d.n; j += nwarps()) {
+    double atu = 0.0;
+    if (d.nR) atu = warp_row_dot<false>(d.RT_ptr[j], d.RT_ptr[j + 1], d.RT_idx, d.RT_val, d.vR2);
+    if ((threadIdx.x & 31) == 0) {
+      double g = -d.rd[j] - atu;
+      const double xj = d.x[j];
+      if (d.fl[j]) { const double tl = xj - d.l[j]; g -= (tl * d.zl[j] - mu) / tl; }
+      if (d.fu[j]) { const double tu = d.u[j] - xj; g += (tu * d.zu[j] - mu) / tu; }
+      d.rhs[j] = g;
+      d.r[j] = g;
+      d.dx[j] = 0.0;
+      r2 = fma(g, g, r2);
+    }
+  }
+  double v[1] = {r2};
+  const int ops[1] = {0};
+  double out[1];
+  if (grid_reduce<1>(v, ops, d.partials + 20 * kMaxRedBlocks, &d.sc->ticket[T_INIT], out, sh)) {
+    if (threadIdx.x == 0) {
+      Scal* sc = d.sc;
+      sc->rhs2 = out[0];
+      sc->tol2 = sc->eta * sc->eta * out[0];
+      sc->cg_iter = 0;
+      sc->cg_conv = 0;
+      sc->cg_done = (out[0] == 0.0 || !isfinite(out[0])) ? 1 : 0;
+      if (!isfinite(out[0])) sc->status = DS_NUMERICAL;
+      else if (out[0] == 0.0) sc->cg_conv = 1;
+    }
+  }
+}
+
+cudaError_t launch_rhs(const Dev& d, const Geo& g, cudaStream_t st) {
+  if (d.nR) cudaMemsetAsync(d.vR2, 0, sizeof(double) * d.nR, st);
+  if (d.m) k_rhs_m<<<g.gM, kBlock, 0, st>>>(d);
+  k_rhs_n<<<g.gN, kBlock, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------ PCG
+
+// v = omega o (R p).  MODE 0: inside PCG (skips once converged); MODE 1: single apply.
+template <int MODE>
+__global__ void k_op_rows(Dev d) {
+  if (MODE == 0 && d.sc->cg_done) return;
+  for (int64_t r = gwarp(); r < d.nR; r += nwarps()) {
+    double t = warp_row_dot<false>(d.R_ptr[r], d.R_ptr[r + 1], d.R_idx, d.R_val, d.p);
+    if ((threadIdx.x & 31) == 0) d.vR[r] = d.omega[r] * t;
+  }
+}
+
+// q = R^T v + Hs p + (h0 + sigma) o p; p^T q -> alpha = rz / p^T q (last block).
+// MODE 0: inside PCG; MODE 1: a single operator apply (no scalars touched).
+template <int MODE>
+__global__ void k_op_cols(Dev d) {
+  __shared__ double sh[32];
+  if (MODE == 0 && d.sc->cg_done) return;
+  double pq = 0.0;
+  for (int64_t j = gwarp(); j < d.n; j += nwarps()) {
+    double acc = 0.0;
+    if (d.nR) acc = warp_row_dot<false>(d.RT_ptr[j], d.RT_ptr[j + 1], d.RT_idx, d.RT_val, d.vR);
+    if (d.Hs_ptr) acc += warp_row_dot<false>(d.Hs_ptr[j], d.Hs_ptr[j + 1], d.Hs_idx, d.Hs_val, d.p);
+    if ((threadIdx.x & 31) == 0) {
+      const double pj = d.p[j];
+      const double qj = acc + (d.h0[j] + d.sigma[j]) * pj;
+      d.q[j] = qj;
+      pq = fma(pj, qj, pq);
+    }
+  }
+  if (MODE == 1) return;
+  double v[1] = {pq};
+  const int ops[1] = {0};
+  double out[1];
+  if (grid_reduce<1>(v, ops, d.partials + 16 * kMaxRedBlocks, &d.sc->ticket[T_PQ], out, sh)) {
+    if (threadIdx.x == 0) {
+      Scal* sc = d.sc;
+      const double pqv = out[0];
+      if (!(pqv > 0.0) || !isfinite(pqv)) {
+        sc->cg_done = 1;                       // breakdown: keep the last iterate
+        if (!isfinite(pqv)) sc->status = DS_NUMERICAL;
+        sc->alpha = 0.0;
+      } else {
+        sc->alpha = sc->rz / pqv;
+      }
+      sc->pq = pqv;
+    }
+  }
+}
+
+// dx += alpha p; r -= alpha q; ||r||^2 -> convergence test.
+// ZM 0 (Jacobi): z = r / M, r^T z, beta.  ZM 1 (Jacobi + low rank): z0 = r / M only.
+// ZM 2 (dense): z is left to the dense apply.
+template <int ZM>
+__global__ void k_cg_update(Dev d) {
+  __shared__ double sh[32];
+  if (d.sc->cg_done) return;
+  const double alpha = d.sc->alpha;
+  double rr = 0.0, rz = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x) {
+    d.dx[j] = fma(alpha, d.p[j], d.dx[j]);
+    const double rj = fma(-alpha, d.q[j], d.r[j]);
+    d.r[j] = rj;
+    rr = fma(rj, rj, rr);
+    if (ZM < 2) {
+      const double zj = rj * d.Minv[j];
+      d.z[j] = zj;
+      rz = fma(rj, zj, rz);
+    }
+  }
+  double v[2] = {rr, rz};
+  const int ops[2] = {0, 0};
+  double out[2];
+  if (grid_reduce<2>(v, ops, d.partials + 17 * kMaxRedBlocks, &d.sc->ticket[T_UPD], out, sh)) {
+    if (threadIdx.x == 0) {
+      Scal* sc = d.sc;
+      sc->cg_iter += 1;
+      sc->rr = out[0];
+      if (!isfinite(out[0])) {
+        sc->cg_done = 1;
+        sc->status = DS_NUMERICAL;
+      } else if (out[0] <= sc->tol2) {
+        sc->cg_done = 1;
+        sc->cg_conv = 1;
+      } else if (sc->cg_iter >= sc->cg_max) {
+        sc->cg_done = 1;
+      }
+      if (ZM == 0 && !sc->cg_done) {
+        sc->beta = out[1] / sc->rz;
+        sc->rz = out[1];
+      }
+    }
+  }
+}
+
+// Low-rank correction (Woodbury): with z0 = M^{-1} r already in z,
+//   z = z0 - M^{-1} A_s^T G^{-1} A_s z0.
+// k_stiff_u: u_a = A_s z0 (one warp per stiff row).
+__global__ void k_stiff_u(Dev d, int init) {
+  if (!init && d.sc->cg_done) return;
+  const int ns = d.sc->n_stiff;
+  for (int a = gwarp(); a < ns; a += nwarps()) {
+    const int32_t row = d.arow[d.stiff_k[a]];
+    double u = warp_row_dot<false>(d.R_ptr[row], d.R_ptr[row + 1], d.R_idx, d.R_val, d.z);
+    if ((threadIdx.x & 31) == 0) d.us[a] = u;
+  }
+}
+
+// t = G^{-1} u (dense symmetric matvec, one warp per output).
+__global__ void k_stiff_t(Dev d, int init) {
+  if (!init && d.sc->cg_done) return;
+  const int ns = d.sc->n_stiff;
+  const int cap = d.stiff_cap;
+  const int lane = threadIdx.x & 31;
+  for (int a = gwarp(); a < ns; a += nwarps()) {
+    const double* g = d.Ginv + (int64_t)a * cap;
+    double acc = 0.0;
+    for (int b = lane; b < ns; b += 32) acc = fma(g[b], d.us[b], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) d.ts[a] = acc;
+  }
+}
+
+// z_j = z0_j - Minv_j sum_{(a, v) in column j} v t_a; r^T z -> beta (loop) or rz (init);
+// in init mode also p = z.
+__global__ void k_stiff_corr(Dev d, int init) {
+  __shared__ double sh[32];
+  if (!init && d.sc->cg_done) return;
+  const int ns = d.sc->n_stiff;
+  double rz = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x) {
+    double zj = d.z[j];
+    if (ns > 0) {
+      double acc = 0.0;
+      for (int64_t t = d.sc_ptr[j]; t < d.sc_ptr[j + 1]; ++t) acc = fma(d.sc_val[t], d.ts[d.sc_slot[t]], acc);
+      zj -= d.Minv[j] * acc;
+      d.z[j] = zj;
+    }
+    if (init) d.p[j] = zj;
+    rz = fma(d.r[j], zj, rz);
+  }
+  double v[1] = {rz};
+  const int ops[1] = {0};
+  double out[1];
+  if (grid_reduce<1>(v, ops, d.partials + 19 * kMaxRedBlocks, &d.sc->ticket[T_CORR], out, sh)) {
+    if (threadIdx.x == 0) {
+      Scal* sc = d.sc;
+      if (init) {
+        sc->rz = out[0];
+      } else {
+        sc->beta = out[0] / sc->rz;
+        sc->rz = out[0];
+      }
+    }
+  }
+}
+
+// Dense preconditioner apply: z = Kinv r (one warp per row); r^T z -> rz / beta; init: p = z.
+__global__ void k_dense_apply(Dev d, int init) {
+  __shared__ double sh[32];
+  if (!init && d.sc->cg_done) return;
+  const int lane = threadIdx.x & 31;
+  double rz = 0.0;
+  for (int64_t j = gwarp(); j < d.n; j += nwarps()) {
+    const double* kr = d.Kinv + j * d.n;
+    double acc = 0.0;
+    for (int64_t i = lane; i < d.n; i += 32) acc = fma(kr[i], d.r[i], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      d.z[j] = acc;
+      if (init) d.p[j] = acc;
+      rz = fma(d.r[j], acc, rz);
+    }
+  }
+  double v[1] = {rz};
+  const int ops[1] = {0};
+  double out[1];
+  if (grid_reduce<1>(v, ops, d.partials + 19 * kMaxRedBlocks, &d.sc->ticket[T_CORR], out, sh)) {
+    if (threadIdx.x == 0) {
+      Scal* sc = d.sc;
+      if (init) {
+        sc->rz = out[0];
+      } else {
+        sc->beta = out[0] / sc->rz;
+        sc->rz = out[0];
+      }
+    }
+  }
+}
+
+// Jacobi start: z = r / M, p = z, rz = r^T z.
+__global__ void k_cg_init_diag(Dev d) {
+  __shared__ double sh[32];
+  double rz = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x) {
+    const double zj = d.r[j] * d.Minv[j];
+    d.z[j] = zj;
+    d.p[j] = zj;
+    rz = fma(d.r[j], zj, rz);
+  }
+  double v[1] = {rz};
+  const int ops[1] = {0};
+  double out[1];
+  if (grid_reduce<1>(v, ops, d.partials + 21 * kMaxRedBlocks, &d.sc->ticket[T_CORR], out, sh)) {
+    if (threadIdx.x == 0) d.sc->rz = out[0];
+  }
+}
+
+// p = z + beta p; also sets the while-loop condition of the captured PCG graph.
+__global__ void k_cg_p(Dev d, cudaGraphConditionalHandle h, int set_cond) {
+  const int done = d.sc->cg_done;
+  if (set_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, done ? 0u : 1u);
+  if (done) return;
+  const double beta = d.sc->beta;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x)
+    d.p[j] = fma(beta, d.p[j], d.z[j]);
+}
+
+cudaError_t launch_cg_init(const Dev& d, const Geo& g, int precond, cudaStream_t st) {
+  if (precond == PC_DENSE) {
+    k_dense_apply<<<g.gN, kBlock, 0, st>>>(d, 1);
+  } else if (precond == PC_JACOBI_LR) {
+    k_cg_init_diag<<<g.gN, kBlock, 0, st>>>(d);
+    const int gs = (d.stiff_cap + 7) / 8;
+    k_stiff_u<<<gs, kBlock, 0, st>>>(d, 1);
+    k_stiff_t<<<gs, kBlock, 0, st>>>(d, 1);
+    k_stiff_corr<<<g.gN, kBlock, 0, st>>>(d, 1);
+  } else {
+    k_cg_init_diag<<<g.gN, kBlock, 0, st>>>(d);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_body(const Dev& d, const Geo& g, int precond, cudaGraphConditionalHandle h, cudaStream_t st) {
+  if (d.nR) k_op_rows<0><<<g.gR, kBlock, 0, st>>>(d);
+  k_op_cols<0><<<g.gN, kBlock, 0, st>>>(d);
+  if (precond == PC_DENSE) {
+    k_cg_update<2><<<g.gN, kBlock, 0, st>>>(d);
+    k_dense_apply<<<g.gN, kBlock, 0, st>>>(d, 0);
+  } else if (precond == PC_JACOBI_LR) {
+    k_cg_update<1><<<g.gN, kBlock, 0, st>>>(d);
+    const int gs = (d.stiff_cap + 7) / 8;
+    k_stiff_u<<<gs, kBlock, 0, st>>>(d, 0);
+    k_stiff_t<<<gs, kBlock, 0, st>>>(d, 0);
+    k_stiff_corr<<<g.gN, kBlock, 0, st>>>(d, 0);
+  } else {
+    k_cg_update<0><<<g.gN, kBlock, 0, st>>>(d);
+  }
+  k_cg_p<<<g.gN, kBlock, 0, st>>>(d, h, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply(const Dev& d, const Geo& g, cudaStream_t st) {
+  if (d.nR) k_op_rows<1><<<g.gR, kBlock, 0, st>>>(d);
+  k_op_cols<1><<<g.gN, kBlock, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------ recovery
+
+// A dx on the constraint rows; ds = -r_p - A dx; dy = theta (A dx + r_p) - r_s / s.
+__global__ void k_recover_m(Dev d) {
+  const double mu = d.sc->mu;
+  for (int64_t k = gwarp(); k < d.m; k += nwarps()) {
+    const int32_t row = d.arow[k];
+    double adx = warp_row_dot<false>(d.R_ptr[row], d.R_ptr[row + 1], d.R_idx, d.R_val, d.dx);
+    if ((threadIdx.x & 31) == 0) {
+      const double s = d.s[k];
+      const double rs = s * d.y[k] - mu;
+      d.ds[k] = -d.rp[k] - adx;
+      d.dy[k] = d.theta[k] * (adx + d.rp[k]) - rs / s;
+    }
+  }
+}
+
+// dz_l = (-r_l - z_l dx) / t_l, dz_u = (-r_u + z_u dx) / t_u.
+__global__ void k_recover_n(Dev d) {
+  const double mu = d.sc->mu;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x) {
+    const double xj = d.x[j], dxj = d.dx[j];
+    double dzl = 0.0, dzu = 0.0;
+    if (d.fl[j]) { const double tl = xj - d.l[j]; const double rl = tl * d.zl[j] - mu; dzl = (-rl - d.zl[j] * dxj) / tl; }
+    if (d.fu[j]) { const double tu = d.u[j] - xj; const double ru = tu * d.zu[j] - mu; dzu = (-ru + d.zu[j] * dxj) / tu; }
+    d.dzl[j] = dzl;
+    d.dzu[j] = dzu;
+  }
+}
+
+cudaError_t launch_recover(const Dev& d, const Geo& g, cudaStream_t st) {
+  if (d.m) k_recover_m<<<g.gM, kBlock, 0, st>>>(d);
+  k_recover_n<<<g.gN, kBlock, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------ ratio test
+
+static __device__ __forceinline__ double ratio_of(double v, double dv) { return dv < 0.0 ? -v / dv : INFINITY; }
+
+__global__ void k_ratio_m(Dev d, double* part) {
+  __shared__ double sh[32];
+  double ap = INFINITY, ad = INFINITY;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.m; k += (int64_t)gridDim.x * blockDim.x) {
+    ap = fmin(ap, ratio_of(d.s[k], d.ds[k]));
+    ad = fmin(ad, ratio_of(d.y[k], d.dy[k]));
+  }
+  double v = block_reduce<2>(ap, sh);
+  if (threadIdx.x == 0) part[0 * kMaxRedBlocks + blockIdx.x] = v;
+  v = block_reduce<2>(ad, sh);
+  if (threadIdx.x == 0) part[1 * kMaxRedBlocks + blockIdx.x] = v;
+}
+
+__global__ void k_ratio_n(Dev d, double* part) {
+  __shared__ double sh[32];
+  double ap = INFINITY, ad = INFINITY;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x) {
+    const double xj = d.x[j], dxj = d.dx[j];
+    if (d.fl[j]) { ap = fmin(ap, ratio_of(xj - d.l[j], dxj)); ad = fmin(ad, ratio_of(d.zl[j], d.dzl[j])); }
+    if (d.fu[j]) { ap = fmin(ap, ratio_of(d.u[j] - xj, -dxj)); ad = fmin(ad, ratio_of(d.zu[j], d.dzu[j])); }
+  }
+  double v = block_reduce<2>(ap, sh);
+  if (threadIdx.x == 0) part[2 * kMaxRedBlocks + blockIdx.x] = v;
+  v = block_reduce<2>(ad, sh);
+  if (threadIdx.x == 0) part[3 * kMaxRedBlocks + blockIdx.x] = v;
+}
+
+__global__ void k_ratio_final(Dev d, int gM, int gN, const double* part) {
+  __shared__ double sh[32];
+  auto mn = [&](int q, int nb) -> double {
+    double acc = INFINITY;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) acc = fmin(acc, part[q * kMaxRedBlocks + b]);
+    return block_reduce<2>(acc, sh);
+  };
+  const double ap = fmin(mn(0, gM), mn(2, gN));
+  const double ad = fmin(mn(1, gM), mn(3, gN));
+  if (threadIdx.x == 0) {
+    Scal* sc = d.sc;
+    double a_p = fmin(1.0, sc->tau * ap);
+    double a_d = fmin(1.0, sc->tau * ad);
+    if (sc->equal_steps) a_p = a_d = fmin(a_p, a_d);
+    sc->alpha_p = a_p;
+    sc->alpha_d = a_d;
+  }
+}
+
+cudaError_t launch_ratio(const Dev& d, const Geo& g, cudaStream_t st) {
+  double* part = d.partials + 22 * kMaxRedBlocks;
+  if (d.m) k_ratio_m<<<g.gM, kBlock, 0, st>>>(d, part);
+  k_ratio_n<<<g.gN, kBlock, 0, st>>>(d, part);
+  k_ratio_final<<<1, 256, 0, st>>>(d, d.m ? g.gM : 0, g.gN, part);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------ update
+
+__global__ void k_update_n(Dev d) {
+  const double ap = d.sc->alpha_p, ad = d.sc->alpha_d;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x) {
+    d.x[j] = fma(ap, d.dx[j], d.x[j]);
+    if (d.fl[j]) d.zl[j] = fma(ad, d.dzl[j], d.zl[j]);
+    if (d.fu[j]) d.zu[j] = fma(ad, d.dzu[j], d.zu[j]);
+  }
+}
+
+__global__ void k_update_m(Dev d) {
+  const double ap = d.sc->alpha_p, ad = d.sc->alpha_d;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.m; k += (int64_t)gridDim.x * blockDim.x) {
+    d.s[k] = fma(ap, d.ds[k], d.s[k]);
+    d.y[k] = fma(ad, d.dy[k], d.y[k]);
+  }
+}
+
+cudaError_t launch_update(const Dev& d, const Geo& g, cudaStream_t st) {
+  k_update_n<<<g.gN, kBlock, 0, st>>>(d);
+  if (d.m) k_update_m<<<g.gM, kBlock, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------ precond build
+
+cudaError_t launch_dense_build(const Dev& d, cudaStream_t st);       // dense.cu
+cudaError_t launch_stiff_factor(const Dev& d, cudaStream_t st);      // dense.cu
+
+cudaError_t launch_precond_build(const Dev& d, const Geo& g, int precond, cudaStream_t st) {
+  if (precond == PC_DENSE) return launch_dense_build(d, st);
+  if (precond == PC_JACOBI_LR && d.m) {
+    k_stiff_ratio<<<g.gM, kBlock, 0, st>>>(d);
+    k_stiff_compact<<<1, 1024, 0, st>>>(d);
+  }
+  k_jacobi<true><<<g.gN, kBlock, 0, st>>>(d, d.Minv);
+  if (precond == PC_JACOBI_LR && d.m) {
+    k_sc_count<<<g.gN, kBlock, 0, st>>>(d);
+    k_sc_scan<<<1, 1024, 0, st>>>(d);
+    k_sc_fill<<<g.gN, kBlock, 0, st>>>(d);
+    const size_t smem = sizeof(double) * (size_t)d.stiff_cap;
+    k_gram_G<<<d.stiff_cap, 256, smem, st>>>(d);
+    cudaError_t e = launch_stiff_factor(d, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ipmk

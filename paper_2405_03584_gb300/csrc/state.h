@@ -1,0 +1,84 @@
+// Device pointer bundle of one solver handle and the host-side launch interface of the kernels.
+// Every kernel takes the bundle by value; sizes are fixed per loaded QP, so a captured CUDA
+// graph stays valid until the next ipm_set_qp.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace ipmk {
+
+struct Dev {
+  int64_t n, m, nR;            // variables, constraint rows, rows of R = [F; A_csr]
+  int64_t nnzR, nnzHs;
+  // problem data
+  const int64_t* R_ptr; const int32_t* R_idx; const double* R_val;
+  const int64_t* RT_ptr; const int32_t* RT_idx; const double* RT_val;
+  const int64_t* Hs_ptr; const int32_t* Hs_idx; const double* Hs_val;   // nullptr if none
+  const int32_t* arow;         // m: row of R holding constraint k
+  const double *wR, *h0, *c, *b, *l, *u;
+  const unsigned char *fl, *fu;  // finite-bound masks (n)
+  double* diagH;               // n: diag(H), computed once
+  // iterate
+  double *x, *s, *y, *zl, *zu;
+  // per IPM iteration
+  double *theta, *sigma, *omega, *M0, *Minv, *thR;  // thR: theta placed on R rows (Jacobi part)
+  double *rd, *rp, *Hx, *Aty;
+  double *tR, *vR, *vR2;       // nR work vectors
+  // PCG and direction
+  double *dx, *r, *z, *p, *q, *rhs;
+  double *ds, *dy, *dzl, *dzu;
+  // stiff-row low-rank correction
+  double* ratio;               // m
+  int32_t* slotR;              // nR: slot of a stiff row, -1 otherwise
+  int32_t* stiff_k;            // stiff_cap: constraint index of each slot
+  int32_t* sc_cnt;             // n
+  int64_t* sc_ptr;             // n+1: stiff entries per variable (CSC of the stiff rows)
+  int32_t* sc_slot; double* sc_val;  // sc_cap
+  int64_t sc_cap;
+  double *G, *Ginv, *us, *ts;  // stiff_cap^2, stiff_cap^2, stiff_cap, stiff_cap
+  int stiff_cap;
+  unsigned int* hist;          // kHistBins
+  // dense preconditioner (n x n), nullptr if not allocated
+  double *Kd, *Kinv;
+  // reductions and scalars
+  double* partials;            // 32 * kMaxRedBlocks
+  Scal* sc;
+};
+
+// Launch geometry shared by the host code and the final reduction kernel.
+struct Geo {
+  int gR, gM, gN;              // blocks of the nR-row, m-row and n-column kernels
+};
+
+Geo make_geo(const Dev& d);
+
+// ---- setup and start point ----
+cudaError_t launch_diagH(const Dev& d, cudaStream_t st);
+cudaError_t launch_start_point(const Dev& d, const Geo& g, cudaStream_t st);
+// ---- residual summary at the current iterate and mu ----
+cudaError_t launch_residual_summary(const Dev& d, const Geo& g, cudaStream_t st);
+// ---- complementarity residual vectors r_s, r_l, r_u (into ds, dzl, dzu) ----
+cudaError_t launch_comp_resid(const Dev& d, const Geo& g, cudaStream_t st);
+// ---- IPM control (mu test, stop rule, eta) ----
+cudaError_t launch_control(const Dev& d, cudaStream_t st);
+// ---- diagonal update and preconditioner build ----
+cudaError_t launch_diag_update(const Dev& d, const Geo& g, cudaStream_t st);
+cudaError_t launch_precond_build(const Dev& d, const Geo& g, int precond, cudaStream_t st);
+// ---- right-hand side and PCG ----
+cudaError_t launch_rhs(const Dev& d, const Geo& g, cudaStream_t st);
+cudaError_t launch_cg_init(const Dev& d, const Geo& g, int precond, cudaStream_t st);
+cudaError_t launch_cg_body(const Dev& d, const Geo& g, int precond, cudaGraphConditionalHandle h, cudaStream_t st);
+// ---- direction recovery, ratio test, update ----
+cudaError_t launch_recover(const Dev& d, const Geo& g, cudaStream_t st);
+cudaError_t launch_ratio(const Dev& d, const Geo& g, cudaStream_t st);
+cudaError_t launch_update(const Dev& d, const Geo& g, cudaStream_t st);
+// ---- single operator apply (q = K p with the current theta, sigma) ----
+cudaError_t launch_apply(const Dev& d, const Geo& g, cudaStream_t st);
+// ---- full Jacobi diagonal into Minv's storage as M (not inverted) ----
+cudaError_t launch_jacobi_full(const Dev& d, const Geo& g, double* out, cudaStream_t st);
+
+enum Precond { PC_JACOBI = 0, PC_JACOBI_LR = 1, PC_DENSE = 2 };
+
+}  // namespace ipmk

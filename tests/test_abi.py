@@ -1,0 +1,62 @@
+"""C ABI checks that need no GPU: the library loads, exports every entry point that
+include/ipm.h declares, and its host-only calls behave (no compute calls here)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2405_03584_gb300 import build, ipm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ipm.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ipm_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return ipm.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(ipm.EXPORTS) <= set(names)
+
+
+def test_default_options(lib):
+    o = ipm.default_options()
+    assert o["tol_kkt"] == 1e-6 and o["tau"] == 0.995 and o["max_ipm"] == 200
+    assert o["precond"] == ipm.PRECOND["auto"] and o["stiff_max"] == 256
+
+
+def test_status_strings(lib):
+    for code in range(10):
+        assert lib.ipm_status_str(code)
+    assert lib.ipm_status_str(0) == b"ok"
+
+
+def test_null_arguments_rejected(lib):
+    assert lib.ipm_create(None, None) == ipm.IPM_ERR_ARG
+    assert lib.ipm_destroy(None) == ipm.IPM_OK
+    assert lib.ipm_set_qp(None, None, None) == ipm.IPM_ERR_ARG
+    assert lib.ipm_solve(None, None, 0) == ipm.IPM_ERR_ARG
+    bad = ipm.Options()
+    lib.ipm_default_options(C.byref(bad))
+    bad.tau = 1.5
+    h = C.c_void_p()
+    assert lib.ipm_create(C.byref(bad), C.byref(h)) == ipm.IPM_ERR_ARG
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    monkeypatch.setattr(ipm, "_lib", None)
+    with pytest.raises(ImportError):
+        ipm.load(str(tmp_path / "nope.so"))
