@@ -1,0 +1,318 @@
+#!/usr/bin/env python
+"""QP solves per second of the GPU interior point method on the RT-shaped workload.
+
+Workload (the configuration the headline metric is quoted on): an RT-shaped convex QP with a
+dose-like matrix D of V = 200000 voxels x n = 50000 beam spots (0.5 % density, lognormal
+values, contiguous spot bands per voxel row), H = D^T W D + 1e-4 I applied matrix-free,
+c = -D^T W d_presc, A = the 20000 D rows of organ voxels with b = 0.6, 0 <= x <= 5; FP64.
+Synthetic data from paper_2405_03584_gb300.workloads.rt_qp (seed 1).
+
+A step is one complete solve (start point, every IPM iteration with its PCG solve, to a
+relative KKT residual <= 1e-6) with the QP already resident in HBM; the operator's working
+set (about 1.2 GB) is larger than L2, so no explicit flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With torchrun (N > 1) every rank solves its own replica (the path does not shard a single
+QP); the value is the whole-job solves/s over the max-over-ranks time.  --impl reference
+times the CPU FP64 oracle (dense Cholesky IPM) on the host cores instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QP solves/sec & p50/p99 latency at rel. KKT <=1e-6; PCG SpMV HBM GB/s"
+N_FULL, SEED, TOL = 50_000, 1, 1e-6
+WORKLOAD = ("RT-shaped QP: D 200000 voxels x 50000 spots, 0.5% banded lognormal, H = D^T W D + 1e-4 I "
+            "matrix-free, A = 20000 organ rows (b = 0.6), 0 <= x <= 5, FP64, seed 1")
+SAMPLE_N = 4000                 # oracle sample: same generator at n = 4000 (V = 16000, m = 1600)
+FALLBACK_HBM_GBS = 6800.0
+FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 (non-tensor) nominal rate
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return float(d["hbm_gbs"]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def _cores_used():
+    try:
+        from threadpoolctl import threadpool_info
+        th = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if th:
+            return int(max(th))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = [l.strip().split(",") for l in open(self.path) if l.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower().startswith("active"):
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the summary was taken
+    on the current kernel source (its recorded source hash matches); else None."""
+    import hashlib
+    summ = os.path.join(ROOT, "profiles", "pcg_operator_rt_c1.md")
+    if not os.path.exists(summ):
+        return None
+    src = open(os.path.join(ROOT, "paper_2405_03584_gb300", "csrc", "kernels.cu"), "rb").read() + \
+        open(os.path.join(ROOT, "paper_2405_03584_gb300", "csrc", "common.cuh"), "rb").read()
+    h = hashlib.sha256(src).hexdigest()[:16]
+    txt = open(summ).read()
+    if ("source_hash: " + h) not in txt:
+        return None
+    for line in txt.splitlines():
+        if line.startswith("traffic_per_launch_bytes[%s]:" % kernel):
+            return float(line.split(":")[1])
+    return None
+
+
+def _oracle_sample():
+    """The CPU oracle as it stands: one full solve of the same generator at n = SAMPLE_N,
+    scaled to the full size by the O(n^3) cost of its dense Newton steps."""
+    from oracle import ipm as O
+    from paper_2405_03584_gb300 import workloads as W
+    p = W.rt_qp(n=SAMPLE_N, seed=SEED)
+    t0 = time.perf_counter()
+    qp = O.from_rt(p)
+    it, info = O.solve(qp, tol=TOL)
+    t = time.perf_counter() - t0
+    scale = (N_FULL / SAMPLE_N) ** 3
+    return dict(seconds=t, scale=scale, ipm_iters=info.iterations, status=info.status,
+                solves_per_s=1.0 / (t * scale))
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    cores = _cores_used()
+    times = []
+    for k in range(args.warmup + args.steps):
+        r = _oracle_sample()
+        if k >= args.warmup:
+            times.append(r["seconds"] * r["scale"])
+    tot = sum(times)
+    value = args.steps / tot
+    sample = ("oracle (dense-Cholesky FP64 IPM) full solve of the same RT generator at n=%d, V=%d, m=%d "
+              "(%.1f s each), scaled by (50000/%d)^3" % (SAMPLE_N, 4 * SAMPLE_N, 4 * SAMPLE_N // 10,
+                                                         statistics.mean([t / r["scale"] for t in times]), SAMPLE_N))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "l2": "host run"},
+           "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2405_03584_gb300 import build, ipm, workloads as W
+
+    rank, world, local = _env_rank()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    build.build()
+    dev = torch.cuda.current_device()
+    p = W.rt_qp(n=N_FULL, seed=SEED)
+    s = ipm.Solver(tol_kkt=TOL, precond="jacobi_lr")
+    s.set_qp_rt(p)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        st = s.solve()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches = 0
+    statuses, infos = [], []
+    for k in range(args.steps):
+        evs[k][0].record(stream)
+        st = s.solve()
+        evs[k][1].record(stream)
+        out_info = s.get()["info"]
+        statuses.append(st)
+        infos.append(out_info)
+        launches += out_info["kernel_launches"]
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    lat = [a.elapsed_time(b) for a, b in evs]
+    total_ms = evs[0][0].elapsed_time(evs[-1][1])
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = args.steps * world / (total_ms / 1000.0)
+    # correctness of the timed solves, certified on the host by the independent checker
+    from oracle import kkt_check
+    sol = s.get()
+    rk = kkt_check.rel_kkt(kkt_check.rt_ops(p), sol["x"], sol["y"], sol["zl"], sol["zu"])
+    # roofline of the dominant kernel (PCG operator pass), timed live with CUDA events
+    prof = s.profile_operator(reps=20)
+    kern = "k_op_rows" if prof["ms_rows"] >= prof["ms_cols"] else "k_op_cols"
+    key = "rows" if kern == "k_op_rows" else "cols"
+    ms, byts, flops = prof["ms_" + key], prof["bytes_" + key], prof["flops_" + key]
+    peak, peak_kind = _peaks()
+    achieved = byts / (ms / 1000.0) / 1e9
+    roof = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": _ncu_traffic(kern), "peak_kind": peak_kind + " hbm_gbs",
+            "algorithmic_bytes": byts, "ms_per_launch": ms,
+            "fp64_tflops": flops / (ms / 1000.0) / 1e12, "fp64_nominal_tflops": FP64_NOMINAL_TFLOPS,
+            "other_kernel": {"ms_per_launch": prof["ms_" + ("cols" if key == "rows" else "rows")],
+                             "gbs": prof["bytes_" + ("cols" if key == "rows" else "rows")] /
+                             (prof["ms_" + ("cols" if key == "rows" else "rows")] / 1000.0) / 1e9}}
+    s.close()
+    # end to end through the public API with host buffers (copies inside the timed region)
+    e2e = None
+    if args.e2e_steps > 0:
+        pin = {}
+        for k in ("D_indptr", "D_indices", "D_data", "w", "c", "b", "l", "u", "h0", "a_rows"):
+            t = torch.from_numpy(np.ascontiguousarray(p[k])).pin_memory()
+            pin[k] = t.numpy()
+        q = dict(p)
+        q.update(pin)
+        h2d = sum(v.nbytes for v in pin.values())
+        d2h = 8 * (3 * p["n"] + 2 * p["m"])
+        e2e_t = []
+        for k in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            se = ipm.Solver(tol_kkt=TOL, precond="jacobi_lr")
+            se.set_qp_rt(q)
+            se.solve()
+            se.get()
+            se.close()
+            torch.cuda.synchronize()
+            if k:
+                e2e_t.append(time.perf_counter() - t0)
+        e2e_val = len(e2e_t) / sum(e2e_t)
+        if world > 1:
+            t = torch.tensor([sum(e2e_t)], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_val = len(e2e_t) * world / float(t.item())
+        e2e = {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "steps": len(e2e_t), "includes": "ipm_create + ipm_set_qp (host arrays, pinned) + ipm_solve + ipm_get_xyz"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = _oracle_sample()
+        cpu = {"value": r["solves_per_s"], "unit": "solves/s", "cores": _cores_used(), "kind": "oracle",
+               "sample": "oracle (dense-Cholesky FP64 IPM) full solve of the same RT generator at n=%d, V=%d, m=%d "
+                         "in %.1f s (%d IPM iterations), scaled by (50000/%d)^3" %
+                         (SAMPLE_N, 4 * SAMPLE_N, 4 * SAMPLE_N // 10, r["seconds"], r["ipm_iters"], SAMPLE_N)}
+    if rank == 0:
+        lat_sorted = sorted(lat)
+        p99 = lat_sorted[min(len(lat_sorted) - 1, int(np.ceil(0.99 * len(lat_sorted))) - 1)]
+        out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": WORKLOAD, "n": p["n"], "V": p["V"], "m": p["m"], "nnz_D": int(p["D_indptr"][-1]),
+                          "tol_kkt": TOL, "precond": "jacobi_lr", "parallelism": "replicas" if world > 1 else "single",
+                          "l2": "no flush: operator working set (~1.2 GB) > 129 MB L2"},
+               "latency_ms": {"p50": statistics.median(lat), "p99": p99, "mean": statistics.mean(lat)},
+               "solve": {"status": [int(x) for x in statuses], "ipm_iters": [i["ipm_iters"] for i in infos],
+                         "cg_iters": [i["cg_iters"] for i in infos], "rel_kkt_device": infos[-1]["rel_kkt"],
+                         "rel_kkt_checker": rk, "max_stiff_rows": infos[-1]["max_stiff_rows"]},
+               "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -70,7 +70,7 @@ typedef struct ipm_options {
   int max_ipm;           /* IPM iteration limit (200)                                          */
   int max_cg;            /* PCG iteration limit per Newton step (2000)                         */
   double cg_eta_max;     /* PCG relative tolerance eta = clamp(cg_eta_factor * relKKT, ...)    */
-  double cg_eta_min;     /*   ... between cg_eta_min (1e-10) and cg_eta_max (0.1)             */
+  double cg_eta_min;     /*   ... between cg_eta_min (1e-10) and cg_eta_max (1e-3)            */
   double cg_eta_factor;  /*   (0.1)                                                            */
   int precond;           /* enum ipm_precond (IPM_PRECOND_AUTO: DENSE if n <= 1024, else       */
                          /* JACOBI_LR)                                                         */
@@ -124,6 +124,7 @@ typedef struct ipm_info {
   double dual_obj;
   double mu;                 /* final barrier parameter                                    */
   double solve_ms;           /* wall time of the last ipm_solve                            */
+  int64_t kernel_launches;   /* kernels of this library launched by the last ipm_solve     */
 } ipm_info;
 
 /* Per-step result of ipm_newton_direction. */
@@ -202,6 +203,24 @@ int ipm_newton_direction(ipm_handle* h, double eta, double* dx, double* ds, doub
 int ipm_step_lengths(ipm_handle* h, const double* dx, const double* ds, const double* dy,
                      const double* dz_l, const double* dz_u, double tau, double* alpha_p,
                      double* alpha_d, int mem, void* stream);
+
+/* Per-iteration trace of the last ipm_solve (metrics only): row k holds
+ *   {k+1, mu, rel_kkt, primal, dual, gap, alpha_p, alpha_d, pcg_iters, pcg_converged,
+ *    stiff_rows, pcg_rel_residual, eta}  (IPM_TRACE_COLS doubles).
+ * Copies at most max_rows rows into buf (host memory) and returns the number of rows the last
+ * solve recorded (so buf == NULL queries the count). */
+#define IPM_TRACE_COLS 13
+int ipm_get_trace(const ipm_handle* h, double* buf, int max_rows);
+
+/* Measurement hook for the PCG operator (Section 4.1.1's matvec, the loop that Section 5.1.2
+ * finds to take most of the run time): at the current iterate, launches the row-gather kernel
+ * over R and the gather over the stored transpose `reps` times each on the library's stream,
+ * timed with CUDA events around every launch.  Returns the mean milliseconds per launch and
+ * the algorithmic bytes and flops of one launch of each kernel (bytes: every matrix value,
+ * index and row pointer once, every dense vector once; flops: 2 per stored non-zero).
+ * Any output pointer may be NULL. */
+int ipm_profile_operator(ipm_handle* h, int reps, double* ms_rows, double* ms_cols, double* bytes_rows,
+                         double* bytes_cols, double* flops_rows, double* flops_cols);
 
 #ifdef __cplusplus
 }

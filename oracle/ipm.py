@@ -251,7 +251,8 @@ def start_point(qp: DenseQP):
           (delta_j = 0.1 for a one-sided bound; x0_j = 0 for a free variable);
     s0  = max(b - A x0, 1);
     with g = H x0 + c:  z_l0 = max(1, g), z_u0 = max(1, -g) on finite bounds (0 elsewhere),
-    y0  = max(1, median |g|) on every row;
+    y0  = 1 on every row (so that theta = y / s starts moderate and no constraint row begins
+          "stiff");
     mu0 = the average complementarity product of this point.
     Returns (Iterate, mu0).
     """
@@ -266,7 +267,7 @@ def start_point(qp: DenseQP):
     g = qp.H @ x0 + qp.c
     zl0 = np.where(qp.fl, np.maximum(1.0, g), 0.0)
     zu0 = np.where(qp.fu, np.maximum(1.0, -g), 0.0)
-    y0 = np.full(qp.m, max(1.0, float(np.median(np.abs(g))) if n else 1.0))
+    y0 = np.ones(qp.m)
     it = Iterate(x0, s0, y0, zl0, zu0)
     return it, complementarity_mean(qp, it)
 

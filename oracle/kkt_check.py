@@ -21,7 +21,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["Operators", "dense_ops", "rt_ops", "rel_kkt"]
+__all__ = ["Operators", "dense_ops", "rt_ops", "rel_kkt", "rt_condensed_entries", "rt_residual_dual"]
 
 
 class Operators:
@@ -96,3 +96,58 @@ def rel_kkt(ops: Operators, x, y, zl, zu, detail: bool = False):
     if detail:
         return val, dict(primal=float(primal), dual=float(dual), gap=float(gap), pobj=float(pobj), dobj=float(dobj))
     return val
+
+
+def rt_residual_dual(p: dict, x, y, zl, zu):
+    """r_d = H x + c + A^T y - z_l + z_u for an RT-shaped QP (eq:perturbed_KKT's r_H)."""
+    ops = rt_ops(p)
+    fl, fu = np.isfinite(ops.l), np.isfinite(ops.u)
+    return ops.Hx(x) + ops.c + ops.Aty(y) - np.where(fl, zl, 0.0) + np.where(fu, zu, 0.0)
+
+
+def rt_condensed_entries(p: dict, x, s, y, zl, zu, pvec, cols):
+    """Selected entries q_j, j in cols, of q = (H + A^T Theta A + Sigma) p for an RT-shaped QP,
+    each evaluated on its own from the definition (no full matrix product):
+
+        q_j = sum_{i : D_ij != 0} D_ij (w_i + theta~_i) (D_i . p) + (h0_j + sigma_j) p_j,
+
+    theta~_i = y_k / s_k when voxel row i is constraint k (a_rows[k] = i), else 0;
+    sigma_j = z_l,j / (x_j - l_j) + z_u,j / (u_j - x_j) over the finite bounds.
+    Used at full problem sizes, where only sampled entries are affordable on the host."""
+    ip, ix, dv = p["D_indptr"], p["D_indices"], p["D_data"]
+    V = p["V"]
+    theta_row = np.zeros(V)
+    theta_row[np.asarray(p["a_rows"], dtype=np.int64)] = np.asarray(y, float) / np.asarray(s, float)
+    l, u = np.asarray(p["l"], float), np.asarray(p["u"], float)
+    out = np.empty(len(cols))
+    for t, j in enumerate(cols):
+        acc = 0.0
+        # rows whose column list holds j: scan by binary search in each row's sorted columns
+        for i in _rows_with_col(ip, ix, j):
+            seg = slice(ip[i], ip[i + 1])
+            dij = dv[seg][np.searchsorted(ix[seg], j)]
+            acc += dij * (p["w"][i] + theta_row[i]) * (dv[seg] @ pvec[ix[seg]])
+        sig = 0.0
+        if np.isfinite(l[j]):
+            sig += zl[j] / (x[j] - l[j])
+        if np.isfinite(u[j]):
+            sig += zu[j] / (u[j] - x[j])
+        out[t] = acc + (p["h0"][j] + sig) * pvec[j]
+    return out
+
+
+_COL_CACHE = {}
+
+
+def _rows_with_col(ip, ix, j):
+    """Row indices i with column j present (cached column index of the matrix)."""
+    key = (id(ip), id(ix))
+    if key not in _COL_CACHE:
+        _COL_CACHE.clear()
+        rows = np.repeat(np.arange(ip.shape[0] - 1), np.diff(ip))
+        order = np.argsort(ix, kind="stable")
+        cnt = np.bincount(ix, minlength=int(ix.max()) + 1 if ix.size else 1)
+        ptr = np.concatenate([[0], np.cumsum(cnt)])
+        _COL_CACHE[key] = (rows[order], ptr)
+    rws, ptr = _COL_CACHE[key]
+    return rws[ptr[j]:ptr[j + 1]]

@@ -27,7 +27,23 @@ namespace {
 struct Graphs {
   cudaGraphExec_t iter = nullptr;   // one full IPM iteration
   cudaGraphExec_t dir = nullptr;    // Newton direction only (PCG + recovery)
+  int iter_kernels = 0, iter_body_kernels = 0;   // kernel nodes outside / inside the PCG loop
+  int dir_kernels = 0, dir_body_kernels = 0;
 };
+
+// Kernel nodes of a graph (not descending into child graphs).
+int count_kernel_nodes(cudaGraph_t g) {
+  size_t nn = 0;
+  if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess) return 0;
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (nn && cudaGraphGetNodes(g, nodes.data(), &nn) != cudaSuccess) return 0;
+  int k = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+  }
+  return k;
+}
 
 }  // namespace
 
@@ -49,6 +65,7 @@ struct ipm_handle {
   double cnorm = 0, bnorm = 0;
   int ncomp = 0;
   int64_t sc_cap = 0;
+  std::vector<double> trace;        // IPM_TRACE_COLS doubles per IPM iteration of the last solve
 };
 
 namespace {
@@ -152,6 +169,7 @@ void carve(Carver& cv, Dev& d, const HostQP& q, int stiff_cap, int64_t sc_cap, b
   d.us = cv.take<double>(stiff_cap); d.ts = cv.take<double>(stiff_cap); d.stiff_cap = stiff_cap;
   d.hist = cv.take<unsigned int>(kHistBins);
   if (dense) { d.Kd = cv.take<double>(n * n); d.Kinv = cv.take<double>(n * n); } else { d.Kd = d.Kinv = nullptr; }
+  d.chol_diag = cv.take<double>(std::max<int64_t>(dense ? n : 0, stiff_cap));
   d.partials = cv.take<double>(32 * (int64_t)kMaxRedBlocks);
   d.sc = cv.take<Scal>(1);
 }
@@ -187,7 +205,7 @@ int leave(ipm_handle* h, void* stream) {
 }
 
 // Captures one IPM iteration (full=true) or one Newton direction (full=false).
-int build_graph(ipm_handle* h, int pc, bool full, cudaGraphExec_t* out) {
+int build_graph(ipm_handle* h, int pc, bool full, cudaGraphExec_t* out, int* top_kernels, int* body_kernels) {
   const Dev& d = h->d;
   const Geo& g = h->g;
   cudaStream_t st = h->st;
@@ -225,6 +243,7 @@ int build_graph(ipm_handle* h, int pc, bool full, cudaGraphExec_t* out) {
         chk(launch_cg_body(d, g, pc, ch, h->st2));
         cudaGraph_t bodyo = nullptr;
         chk(cudaStreamEndCapture(h->st2, &bodyo));
+        if (e == cudaSuccess) *body_kernels = count_kernel_nodes(body);
       }
     }
   }
@@ -238,6 +257,7 @@ int build_graph(ipm_handle* h, int pc, bool full, cudaGraphExec_t* out) {
   cudaGraph_t graph = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(st, &graph);
   if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) *top_kernels = count_kernel_nodes(graph);
   if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
   if (graph) cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
@@ -251,7 +271,8 @@ int ensure_graph(ipm_handle* h, int pc, bool full, cudaGraphExec_t** gx) {
   Graphs& gr = h->graphs[pc];
   cudaGraphExec_t* slot = full ? &gr.iter : &gr.dir;
   if (!*slot) {
-    int rc = build_graph(h, pc, full, slot);
+    int rc = full ? build_graph(h, pc, full, slot, &gr.iter_kernels, &gr.iter_body_kernels)
+                  : build_graph(h, pc, full, slot, &gr.dir_kernels, &gr.dir_body_kernels);
     if (rc) return rc;
   }
   *gx = slot;
@@ -317,7 +338,7 @@ void ipm_default_options(ipm_options* o) {
   o->tau = 0.995;
   o->max_ipm = 200;
   o->max_cg = 2000;
-  o->cg_eta_max = 0.1;
+  o->cg_eta_max = 1e-3;
   o->cg_eta_min = 1e-10;
   o->cg_eta_factor = 0.1;
   o->precond = IPM_PRECOND_AUTO;
@@ -613,9 +634,11 @@ int ipm_solve(ipm_handle* h, void* stream, int flags) {
   const int pc = h->precond;
   cudaGraphExec_t* gx = nullptr;
   if ((rc = ensure_graph(h, pc, true, &gx))) return rc;
-  int64_t cg_total = 0;
+  int64_t cg_total = 0, launches = (flags & IPM_WARM) && h->have_iterate ? 4 : 13;
   int cg_max_step = 0;
   int status = IPM_MAX_ITER;
+  const Graphs& grs = h->graphs[pc];
+  h->trace.clear();
   for (int it = 0; it < h->opt.max_ipm; ++it) {
     CUDA_TRY(h, cudaGraphLaunch(*gx, h->st));
     CUDA_TRY(h, cudaMemcpyAsync(h->hs, h->d.sc, sizeof(Scal), cudaMemcpyDeviceToHost, h->st));
@@ -639,6 +662,12 @@ int ipm_solve(ipm_handle* h, void* stream, int flags) {
     const Scal& s = *h->hs;
     cg_total += s.cg_iter;
     cg_max_step = std::max(cg_max_step, s.cg_iter);
+    launches += grs.iter_kernels + (int64_t)std::max(1, s.cg_iter) * grs.iter_body_kernels;
+    const double row[IPM_TRACE_COLS] = {(double)s.ipm_iter, s.mu, s.rel_kkt, s.res_primal, s.res_dual, s.res_gap,
+                                        s.alpha_p, s.alpha_d, (double)s.cg_iter, (double)s.cg_conv,
+                                        (double)(pc == PC_JACOBI_LR ? s.n_stiff : 0),
+                                        s.rhs2 > 0 ? std::sqrt(s.rr / s.rhs2) : 0.0, s.eta_used};
+    h->trace.insert(h->trace.end(), row, row + IPM_TRACE_COLS);
     if (s.stop) {
       status = s.status == DS_OK ? IPM_OK : s.status == DS_MAX_ITER ? IPM_MAX_ITER
              : s.status == DS_CG_STALL ? IPM_CG_STALL : IPM_NUMERICAL;
@@ -661,6 +690,7 @@ int ipm_solve(ipm_handle* h, void* stream, int flags) {
   in.dual_obj = s.dobj;
   in.mu = s.mu;
   in.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  in.kernel_launches = launches;
   if ((rc = leave(h, stream))) return rc;
   return status;
 }
@@ -839,6 +869,58 @@ int ipm_step_lengths(ipm_handle* h, const double* dx, const double* ds, const do
   CUDA_TRY(h, cudaMemcpyAsync(&d.sc->equal_steps, &eq_keep, sizeof(int), cudaMemcpyHostToDevice, h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
   return leave(h, stream);
+}
+
+int ipm_get_trace(const ipm_handle* h, double* buf, int max_rows) {
+  if (!h) return 0;
+  const int rows = (int)(h->trace.size() / IPM_TRACE_COLS);
+  if (buf && max_rows > 0)
+    std::memcpy(buf, h->trace.data(), sizeof(double) * IPM_TRACE_COLS * (size_t)std::min(rows, max_rows));
+  return rows;
+}
+
+int ipm_profile_operator(ipm_handle* h, int reps, double* ms_rows, double* ms_cols, double* bytes_rows,
+                         double* bytes_cols, double* flops_rows, double* flops_cols) {
+  if (!h || reps < 1) return IPM_ERR_ARG;
+  if (!h->loaded || !h->have_iterate) return fail(h, IPM_ERR_STATE, "no iterate");
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  const Dev& d = h->d;
+  const Geo& g = h->g;
+  CUDA_TRY(h, launch_diag_update(d, g, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(d.p, d.x, sizeof(double) * d.n, cudaMemcpyDeviceToDevice, h->st));
+  std::vector<cudaEvent_t> ev(3 * reps);
+  for (auto& e : ev) CUDA_TRY(h, cudaEventCreate(&e));
+  // one untimed pair first
+  CUDA_TRY(h, launch_op_rows_only(d, g, h->st));
+  CUDA_TRY(h, launch_op_cols_only(d, g, h->st));
+  for (int r = 0; r < reps; ++r) {
+    CUDA_TRY(h, cudaEventRecord(ev[3 * r], h->st));
+    CUDA_TRY(h, launch_op_rows_only(d, g, h->st));
+    CUDA_TRY(h, cudaEventRecord(ev[3 * r + 1], h->st));
+    CUDA_TRY(h, launch_op_cols_only(d, g, h->st));
+    CUDA_TRY(h, cudaEventRecord(ev[3 * r + 2], h->st));
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  double tr = 0, tc = 0;
+  for (int r = 0; r < reps; ++r) {
+    float a = 0, b = 0;
+    CUDA_TRY(h, cudaEventElapsedTime(&a, ev[3 * r], ev[3 * r + 1]));
+    CUDA_TRY(h, cudaEventElapsedTime(&b, ev[3 * r + 1], ev[3 * r + 2]));
+    tr += a;
+    tc += b;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  const double nnz = (double)d.nnzR, nnzh = (double)d.nnzHs;
+  if (ms_rows) *ms_rows = tr / reps;
+  if (ms_cols) *ms_cols = tc / reps;
+  // rows: values + indices, row pointers, omega, v written, p read once
+  if (bytes_rows) *bytes_rows = 12.0 * nnz + 8.0 * (d.nR + 1) + 16.0 * d.nR + 8.0 * d.n;
+  // cols: values + indices, row pointers, v read once, p, h0, sigma read, q written (+ Hs)
+  if (bytes_cols) *bytes_cols = 12.0 * nnz + 8.0 * (d.n + 1) + 8.0 * d.nR + 32.0 * d.n +
+                                (d.Hs_ptr ? 12.0 * nnzh + 8.0 * (d.n + 1) : 0.0);
+  if (flops_rows) *flops_rows = 2.0 * nnz + d.nR;
+  if (flops_cols) *flops_cols = 2.0 * nnz + 2.0 * nnzh + 4.0 * d.n;
+  return IPM_OK;
 }
 
 }  // extern "C"

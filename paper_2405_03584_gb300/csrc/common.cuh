@@ -28,7 +28,7 @@ struct Scal {
   double cnorm, bnorm;               // ||c||_inf, ||b||_inf (set once)
   int ipm_iter, max_ipm, status, stop;
   int equal_steps, eta_override;     // eta_override: eta was set by the caller
-  double eta_factor, eta_min, eta_max;
+  double eta_factor, eta_min, eta_max, eta_used;
   // PCG
   double rz, pq, alpha, beta, rr, rhs2, tol2;
   int cg_iter, cg_done, cg_max, cg_conv;

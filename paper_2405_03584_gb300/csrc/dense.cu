@@ -1,7 +1,7 @@
 // Dense pieces of the preconditioners (sm_103a, float64):
 //   * k_gram_K   : K = Hs + R^T diag(omega) R + diag(h0 + sigma) as a dense n x n matrix
 //                  (the DENSE preconditioner: one diagonal block covering all variables);
-//   * k_chol     : in-place Cholesky factor (lower) with pivot flooring, one block;
+//   * k_chol_*   : in-place blocked Cholesky factor (lower) with pivot flooring;
 //   * k_mirror   : copies L into the upper triangle so both sweeps of the inverse read rows;
 //   * k_inv      : explicit inverse from the factor, columns spread over blocks.
 // The explicit inverse turns every preconditioner apply inside PCG into a parallel matvec;
@@ -39,48 +39,140 @@ __global__ void k_gram_K(Dev d) {
   }
 }
 
-// Right-looking Cholesky of the leading nn x nn block of A (row-major, leading dimension ld),
-// lower triangle overwritten by L.  A pivot below floor_rel * (original diagonal) is raised
-// to that floor (a modified factor; still symmetric positive definite, which is all a
-// preconditioner needs); the count of floored pivots goes to *nfloor.
-// Shared memory: 2 * nn doubles (column cache and original diagonal).
-__global__ void k_chol(double* A, int64_t ld, const int* nn_dev, int nn_fixed, double floor_rel, int* nfloor) {
-  extern __shared__ double shm[];
-  const int nn = nn_dev ? *nn_dev : nn_fixed;
-  double* colk = shm;
-  double* diag0 = shm + nn;
-  for (int i = threadIdx.x; i < nn; i += blockDim.x) diag0[i] = A[(int64_t)i * ld + i];
-  __shared__ double s_lkk;
-  __shared__ int s_floor;
-  if (threadIdx.x == 0) s_floor = 0;
+// Blocked right-looking Cholesky (lower, row-major, leading dimension ld) of the leading
+// nn x nn block of A, on 32 x 32 tiles spread over many blocks:
+//   for each tile column kb:  factor the diagonal tile (one block), solve the tiles below it
+//   (one block per tile), update the trailing lower triangle (one block per tile pair).
+// nn is read on the device (it may be the number of stiff rows).  A pivot below
+// floor_rel * (original diagonal) is raised to that floor (a modified factor; still symmetric
+// positive definite, which is all a preconditioner needs); the count goes to *nfloor.
+constexpr int kT = 32;
+
+__device__ __forceinline__ int dev_nn(const int* nn_dev, int nn_fixed) { return nn_dev ? *nn_dev : nn_fixed; }
+
+__global__ void k_chol_save_diag(const double* A, int64_t ld, const int* nn_dev, int nn_fixed, double* diag0, int* nfloor) {
+  const int nn = dev_nn(nn_dev, nn_fixed);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) diag0[i] = A[(int64_t)i * ld + i];
+  if (blockIdx.x == 0 && threadIdx.x == 0 && nfloor) *nfloor = 0;
+}
+
+// Diagonal tile kb: unblocked Cholesky in shared memory (rows/cols >= nn padded by identity).
+__global__ void k_chol_potrf(double* A, int64_t ld, const int* nn_dev, int nn_fixed, int kb, const double* diag0,
+                             double floor_rel, int* nfloor) {
+  const int nn = dev_nn(nn_dev, nn_fixed);
+  const int base = kb * kT;
+  if (base >= nn) return;
+  __shared__ double t[kT][kT + 1];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+  for (int r = ty; r < kT; r += 8) {
+    const int gi = base + r, gj = base + tx;
+    t[r][tx] = (gi < nn && gj < nn) ? A[(int64_t)gi * ld + gj] : (r == tx ? 1.0 : 0.0);
+  }
   __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int k = 0; k < nn; ++k) {
+  for (int k = 0; k < kT; ++k) {
     if (threadIdx.x == 0) {
-      double akk = A[(int64_t)k * ld + k];
-      const double fl = floor_rel * fabs(diag0[k]) + 1e-300;
-      if (!(akk > fl)) { akk = fl; s_floor += 1; }
-      const double lkk = sqrt(akk);
-      A[(int64_t)k * ld + k] = lkk;
-      s_lkk = lkk;
+      double akk = t[k][k];
+      if (base + k < nn) {
+        const double fl = floor_rel * fabs(diag0[base + k]) + 1e-300;
+        if (!(akk > fl)) { akk = fl; atomicAdd(nfloor, 1); }
+      }
+      t[k][k] = sqrt(akk);
     }
     __syncthreads();
-    const double inv = 1.0 / s_lkk;
-    for (int i = k + 1 + threadIdx.x; i < nn; i += blockDim.x) {
-      const double v = A[(int64_t)i * ld + k] * inv;
-      A[(int64_t)i * ld + k] = v;
-      colk[i] = v;
-    }
+    const double lkk = t[k][k];
+    if (threadIdx.x > k && threadIdx.x < kT) t[threadIdx.x][k] /= lkk;
     __syncthreads();
-    // trailing update of the lower triangle: A[i][j] -= L[i][k] L[j][k], k < j <= i
-    for (int i = k + 1 + wid; i < nn; i += nw) {
-      const double lik = colk[i];
-      double* ai = A + (int64_t)i * ld;
-      for (int j = k + 1 + lane; j <= i; j += 32) ai[j] = fma(-lik, colk[j], ai[j]);
-    }
+    for (int r = k + 1 + ty; r < kT; r += 8)
+      if (tx > k && tx <= r) t[r][tx] = fma(-t[r][k], t[tx][k], t[r][tx]);
     __syncthreads();
   }
-  if (threadIdx.x == 0 && nfloor) *nfloor = s_floor;
+  for (int r = ty; r < kT; r += 8) {
+    const int gi = base + r, gj = base + tx;
+    if (gi < nn && gj < nn && tx <= r) A[(int64_t)gi * ld + gj] = t[r][tx];
+  }
+}
+
+// Tiles (ib, kb), ib > kb: X = A_ib,kb L_kb,kb^{-T} (one block per tile, one thread per row).
+__global__ void k_chol_trsm(double* A, int64_t ld, const int* nn_dev, int nn_fixed, int kb) {
+  const int nn = dev_nn(nn_dev, nn_fixed);
+  const int nt = (nn + kT - 1) / kT;
+  const int ib = kb + 1 + blockIdx.x;
+  if (ib >= nt) return;
+  __shared__ double L[kT][kT + 1];
+  __shared__ double X[kT][kT + 1];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int kbase = kb * kT, ibase = ib * kT;
+  for (int r = ty; r < kT; r += 8) {
+    const int gk = kbase + r, gc = kbase + tx;
+    L[r][tx] = (gk < nn && gc < nn) ? (tx <= r ? A[(int64_t)gk * ld + gc] : 0.0) : (r == tx ? 1.0 : 0.0);
+    const int gi = ibase + r;
+    X[r][tx] = (gi < nn && gc < nn) ? A[(int64_t)gi * ld + gc] : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x < kT) {
+    const int r = threadIdx.x;
+    for (int j = 0; j < kT; ++j) {
+      double v = X[r][j];
+      for (int c = 0; c < j; ++c) v = fma(-X[r][c], L[j][c], v);
+      X[r][j] = v / L[j][j];
+    }
+  }
+  __syncthreads();
+  for (int r = ty; r < kT; r += 8) {
+    const int gi = ibase + r, gc = kbase + tx;
+    if (gi < nn && gc < nn) A[(int64_t)gi * ld + gc] = X[r][tx];
+  }
+}
+
+// Trailing update A_ib,jb -= L_ib,kb L_jb,kb^T for kb < jb <= ib (one block per tile pair).
+__global__ void k_chol_update(double* A, int64_t ld, const int* nn_dev, int nn_fixed, int kb) {
+  const int nn = dev_nn(nn_dev, nn_fixed);
+  const int nt = (nn + kT - 1) / kT;
+  const int mrem = nt - kb - 1;
+  const int64_t npairs = (int64_t)mrem * (mrem + 1) / 2;
+  if ((int64_t)blockIdx.x >= npairs) return;
+  // blockIdx -> (a, b), 0 <= b <= a < mrem, row-major over the lower triangle
+  int a = (int)((sqrt(8.0 * blockIdx.x + 1.0) - 1.0) * 0.5);
+  while ((int64_t)(a + 1) * (a + 2) / 2 <= (int64_t)blockIdx.x) ++a;
+  while ((int64_t)a * (a + 1) / 2 > (int64_t)blockIdx.x) --a;
+  const int b = (int)(blockIdx.x - (int64_t)a * (a + 1) / 2);
+  const int ib = kb + 1 + a, jb = kb + 1 + b;
+  __shared__ double Li[kT][kT + 1];
+  __shared__ double Lj[kT][kT + 1];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int kbase = kb * kT, ibase = ib * kT, jbase = jb * kT;
+  for (int r = ty; r < kT; r += 8) {
+    const int gc = kbase + tx;
+    Li[r][tx] = (ibase + r < nn && gc < nn) ? A[(int64_t)(ibase + r) * ld + gc] : 0.0;
+    Lj[r][tx] = (jbase + r < nn && gc < nn) ? A[(int64_t)(jbase + r) * ld + gc] : 0.0;
+  }
+  __syncthreads();
+  for (int r = ty; r < kT; r += 8) {
+    const int gi = ibase + r, gj = jbase + tx;
+    if (gi < nn && gj < nn && gj <= gi) {
+      double acc = 0.0;
+#pragma unroll 8
+      for (int c = 0; c < kT; ++c) acc = fma(Li[r][c], Lj[tx][c], acc);
+      A[(int64_t)gi * ld + gj] -= acc;
+    }
+  }
+}
+
+// Captures the whole factorisation for an nn of at most cap (tile columns beyond the device
+// nn exit immediately).
+static cudaError_t launch_chol(double* A, int64_t ld, const int* nn_dev, int nn_fixed, int cap, double* diag0,
+                               int* nfloor, cudaStream_t st) {
+  const int nt = (cap + kT - 1) / kT;
+  k_chol_save_diag<<<std::max(1, std::min(64, (cap + 255) / 256)), 256, 0, st>>>(A, ld, nn_dev, nn_fixed, diag0, nfloor);
+  for (int kb = 0; kb < nt; ++kb) {
+    k_chol_potrf<<<1, 256, 0, st>>>(A, ld, nn_dev, nn_fixed, kb, diag0, 1e-13, nfloor);
+    const int below = nt - kb - 1;
+    if (below > 0) {
+      k_chol_trsm<<<below, 256, 0, st>>>(A, ld, nn_dev, nn_fixed, kb);
+      k_chol_update<<<below * (below + 1) / 2, 256, 0, st>>>(A, ld, nn_dev, nn_fixed, kb);
+    }
+  }
+  return cudaGetLastError();
 }
 
 // Upper triangle <- L^T so that column p of L is row p of the upper part.
@@ -125,7 +217,8 @@ cudaError_t launch_dense_build(const Dev& d, cudaStream_t st) {
   const int n = (int)d.n;
   const size_t rowbytes = sizeof(double) * (size_t)n;
   k_gram_K<<<(int)std::min<int64_t>(d.n, 4 * 152), 256, rowbytes, st>>>(d);
-  k_chol<<<1, 1024, 2 * rowbytes, st>>>(d.Kd, d.n, nullptr, n, 1e-13, &d.sc->chol_fail);
+  cudaError_t e = launch_chol(d.Kd, d.n, nullptr, n, n, d.chol_diag, &d.sc->chol_fail, st);
+  if (e != cudaSuccess) return e;
   k_mirror<<<256, 256, 0, st>>>(d.Kd, d.n, nullptr, n);
   k_inv<<<(int)std::min<int64_t>(d.n, 4 * 152), 256, rowbytes, st>>>(d.Kd, d.n, nullptr, n, d.Kinv, d.n);
   return cudaGetLastError();
@@ -135,7 +228,8 @@ cudaError_t launch_stiff_factor(const Dev& d, cudaStream_t st) {
   const int cap = d.stiff_cap;
   const size_t rowbytes = sizeof(double) * (size_t)cap;
   const int* ns = &d.sc->n_stiff;
-  k_chol<<<1, 1024, 2 * rowbytes, st>>>(d.G, cap, ns, 0, 1e-13, &d.sc->chol_fail);
+  cudaError_t e = launch_chol(d.G, cap, ns, 0, cap, d.chol_diag, &d.sc->chol_fail, st);
+  if (e != cudaSuccess) return e;
   k_mirror<<<64, 256, 0, st>>>(d.G, cap, ns, 0);
   k_inv<<<std::min(cap, 4 * 152), 256, rowbytes, st>>>(d.G, cap, ns, 0, d.Ginv, cap);
   return cudaGetLastError();

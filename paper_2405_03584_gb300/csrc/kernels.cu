@@ -269,34 +269,26 @@ __global__ void k_start_s(Dev d) {
     d.s[k] = fmax(d.b[k] - d.tR[d.arow[k]], 1.0);
 }
 
-// g = H x0 + c; z_l0 = max(1, g), z_u0 = max(1, -g) on finite bounds; y0 = max(1, rms(g)).
+// g = H x0 + c; z_l0 = max(1, g), z_u0 = max(1, -g) on finite bounds.
 __global__ void k_start_z(Dev d) {
-  __shared__ double sh[32];
-  double g2 = 0.0;
   const int lane = threadIdx.x & 31;
   for (int64_t j = gwarp(); j < d.n; j += nwarps()) {
-    double hx = warp_row_dot<false>(d.RT_ptr[j], d.RT_ptr[j + 1], d.RT_idx, d.RT_val, d.vR);
+    double hx = 0.0;
+    if (d.nR) hx = warp_row_dot<false>(d.RT_ptr[j], d.RT_ptr[j + 1], d.RT_idx, d.RT_val, d.vR);
     double hs = 0.0;
     if (d.Hs_ptr) hs = warp_row_dot<false>(d.Hs_ptr[j], d.Hs_ptr[j + 1], d.Hs_idx, d.Hs_val, d.x);
     if (lane == 0) {
       const double g = hx + hs + d.h0[j] * d.x[j] + d.c[j];
       d.zl[j] = d.fl[j] ? fmax(1.0, g) : 0.0;
       d.zu[j] = d.fu[j] ? fmax(1.0, -g) : 0.0;
-      g2 = fma(g, g, g2);
     }
-  }
-  double v[1] = {g2};
-  const int ops[1] = {0};
-  double out[1];
-  if (grid_reduce<1>(v, ops, d.partials + 26 * kMaxRedBlocks, &d.sc->ticket[T_MISC], out, sh)) {
-    if (threadIdx.x == 0) d.sc->alpha = fmax(1.0, sqrt(out[0] / (double)d.n));  // y0 (scratch)
   }
 }
 
+// y0 = 1 on every row (theta starts moderate: no constraint row begins stiff).
 __global__ void k_start_y(Dev d) {
-  const double y0 = d.sc->alpha;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.m; k += (int64_t)gridDim.x * blockDim.x)
-    d.y[k] = y0;
+    d.y[k] = 1.0;
 }
 
 __global__ void k_start_mu(Dev d) {
@@ -651,6 +643,7 @@ __global__ void k_rhs_n(Dev d) {
     if (threadIdx.x == 0) {
       Scal* sc = d.sc;
       sc->rhs2 = out[0];
+      sc->eta_used = sc->eta;
       sc->tol2 = sc->eta * sc->eta * out[0];
       sc->cg_iter = 0;
       sc->cg_conv = 0;
@@ -917,6 +910,16 @@ cudaError_t launch_cg_body(const Dev& d, const Geo& g, int precond, cudaGraphCon
     k_cg_update<0><<<g.gN, kBlock, 0, st>>>(d);
   }
   k_cg_p<<<g.gN, kBlock, 0, st>>>(d, h, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_op_rows_only(const Dev& d, const Geo& g, cudaStream_t st) {
+  if (d.nR) k_op_rows<1><<<g.gR, kBlock, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_op_cols_only(const Dev& d, const Geo& g, cudaStream_t st) {
+  k_op_cols<1><<<g.gN, kBlock, 0, st>>>(d);
   return cudaGetLastError();
 }
 

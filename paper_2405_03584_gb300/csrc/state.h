@@ -42,6 +42,7 @@ struct Dev {
   unsigned int* hist;          // kHistBins
   // dense preconditioner (n x n), nullptr if not allocated
   double *Kd, *Kinv;
+  double* chol_diag;           // max(n_dense, stiff_cap): original diagonal during a factorisation
   // reductions and scalars
   double* partials;            // 32 * kMaxRedBlocks
   Scal* sc;
@@ -76,6 +77,9 @@ cudaError_t launch_ratio(const Dev& d, const Geo& g, cudaStream_t st);
 cudaError_t launch_update(const Dev& d, const Geo& g, cudaStream_t st);
 // ---- single operator apply (q = K p with the current theta, sigma) ----
 cudaError_t launch_apply(const Dev& d, const Geo& g, cudaStream_t st);
+// ---- the two operator kernels alone (measurement) ----
+cudaError_t launch_op_rows_only(const Dev& d, const Geo& g, cudaStream_t st);
+cudaError_t launch_op_cols_only(const Dev& d, const Geo& g, cudaStream_t st);
 // ---- full Jacobi diagonal into Minv's storage as M (not inverted) ----
 cudaError_t launch_jacobi_full(const Dev& d, const Geo& g, double* out, cudaStream_t st);
 

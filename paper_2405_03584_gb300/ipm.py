@@ -26,7 +26,10 @@ COLD, WARM = 0, 1
 
 EXPORTS = ["ipm_default_options", "ipm_create", "ipm_set_qp", "ipm_solve", "ipm_get_xyz", "ipm_destroy",
            "ipm_status_str", "ipm_last_error", "ipm_set_iterate", "ipm_residuals", "ipm_apply_kkt",
-           "ipm_precond_diag", "ipm_newton_direction", "ipm_step_lengths"]
+           "ipm_precond_diag", "ipm_newton_direction", "ipm_step_lengths", "ipm_profile_operator",
+           "ipm_get_trace"]
+TRACE_COLS = ("iter", "mu", "rel_kkt", "primal", "dual", "gap", "alpha_p", "alpha_d", "pcg_iters", "pcg_converged",
+              "stiff_rows", "pcg_rel_residual", "eta")
 
 
 class Options(C.Structure):
@@ -49,7 +52,8 @@ class Info(C.Structure):
     _fields_ = [("status", C.c_int), ("ipm_iters", C.c_int), ("cg_iters", C.c_int64), ("max_cg_step", C.c_int),
                 ("max_stiff_rows", C.c_int), ("precond", C.c_int), ("rel_kkt", C.c_double),
                 ("primal_res", C.c_double), ("dual_res", C.c_double), ("gap_res", C.c_double),
-                ("primal_obj", C.c_double), ("dual_obj", C.c_double), ("mu", C.c_double), ("solve_ms", C.c_double)]
+                ("primal_obj", C.c_double), ("dual_obj", C.c_double), ("mu", C.c_double), ("solve_ms", C.c_double),
+                ("kernel_launches", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -90,6 +94,8 @@ def load(path: str = LIB_PATH):
         "ipm_precond_diag": (I, [P, P, I, P]),
         "ipm_newton_direction": (I, [P, D, P, P, P, P, P, C.POINTER(CgReport), I, P]),
         "ipm_step_lengths": (I, [P, P, P, P, P, P, D, C.POINTER(C.c_double), C.POINTER(C.c_double), I, P]),
+        "ipm_profile_operator": (I, [P, I] + [C.POINTER(C.c_double)] * 6),
+        "ipm_get_trace": (I, [P, P, I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -301,6 +307,21 @@ class Solver:
                                                 C.byref(rep), MEM_HOST, _default_stream(stream)),
                     "ipm_newton_direction")
         return dict(dx=dx, ds=ds, dy=dy, dzl=dzl, dzu=dzu, report=rep.as_dict())
+
+    def trace(self):
+        """Per-IPM-iteration trace of the last solve as a list of dicts (keys TRACE_COLS)."""
+        L = load()
+        rows = L.ipm_get_trace(self._h, None, 0)
+        buf = np.empty((max(rows, 1), len(TRACE_COLS)))
+        L.ipm_get_trace(self._h, buf.ctypes.data, rows)
+        return [dict(zip(TRACE_COLS, r)) for r in buf[:rows]]
+
+    def profile_operator(self, reps=20):
+        """Mean ms per launch and algorithmic bytes / flops of the two PCG operator kernels."""
+        v = [C.c_double() for _ in range(6)]
+        self._check(load().ipm_profile_operator(self._h, int(reps), *[C.byref(x) for x in v]), "ipm_profile_operator")
+        keys = ("ms_rows", "ms_cols", "bytes_rows", "bytes_cols", "flops_rows", "flops_cols")
+        return {k: x.value for k, x in zip(keys, v)}
 
     def step_lengths(self, dx, ds, dy, dzl, dzu, tau, stream=None):
         mk = _Marshal(MEM_HOST)

@@ -79,23 +79,24 @@ def _band_rows(rng, V, n, density, main_sd_frac=0.02, max_extra=3):
     centres[:, 1:] = rng.uniform(0, n, size=(V, max_extra))
     starts = np.rint(centres - lens / 2.0).astype(np.int64)
     starts = np.clip(starts, 0, np.maximum(n - lens, 0))
-    # expand (row, col) pairs band by band
-    rows_l, cols_l = [], []
-    for bnd in range(max_extra + 1):
-        L = lens[:, bnd]
-        sel = L > 0
-        r = np.repeat(np.nonzero(sel)[0], L[sel])
-        off = np.arange(L[sel].sum()) - np.repeat(np.cumsum(L[sel]) - L[sel], L[sel])
-        cidx = np.repeat(starts[sel, bnd], L[sel]) + off
-        rows_l.append(r)
-        cols_l.append(cidx)
-    r = np.concatenate(rows_l)
-    cidx = np.concatenate(cols_l)
-    key = np.unique(r * np.int64(n) + cidx)           # sorted, duplicates (band overlap) removed
-    r = key // n
-    cidx = (key % n).astype(np.int32)
+    # union of each row's bands without a global sort: order the bands of a row by start,
+    # clip every band to begin after the previous bands end, then expand the pieces in order
+    ends = starts + lens
+    ends = np.where(lens > 0, ends, starts)
+    order = np.argsort(np.where(lens > 0, starts, n + 1), axis=1, kind="stable")
+    st = np.take_along_axis(starts, order, axis=1)
+    en = np.take_along_axis(ends, order, axis=1)
+    prev_end = np.maximum.accumulate(np.concatenate([np.zeros((V, 1), np.int64), en[:, :-1]], axis=1), axis=1)
+    st = np.maximum(st, prev_end)
+    ln = np.maximum(en - st, 0)
+    nnz_row = ln.sum(axis=1)
     indptr = np.zeros(V + 1, dtype=np.int64)
-    np.cumsum(np.bincount(r, minlength=V), out=indptr[1:])
+    np.cumsum(nnz_row, out=indptr[1:])
+    flat_len = ln.ravel()
+    sel = flat_len > 0
+    L = flat_len[sel]
+    off = np.arange(L.sum(), dtype=np.int64) - np.repeat(np.cumsum(L) - L, L)
+    cidx = (np.repeat(st.ravel()[sel], L) + off).astype(np.int32)
     return indptr, cidx
 
 

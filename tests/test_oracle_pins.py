@@ -286,3 +286,19 @@ def test_oracle_solves_small_rt_and_dense():
     it, info = ipm.solve(ipm.from_dense(p), tol=1e-9)
     assert info.status == "optimal"
     assert kkt_check.rel_kkt(kkt_check.dense_ops(p), it.x, it.y, it.zl, it.zu) < 1e-8
+
+
+def test_checker_sampled_entries_match_dense():
+    """The one-entry-at-a-time operator evaluation used at full size equals the dense
+    condensed matrix of the oracle applied to the same vector."""
+    p = W.rt_qp(n=250, seed=6)
+    qp = ipm.from_rt(p)
+    it = ipm.Iterate(*W.random_iterate(p["n"], p["m"], p["l"], p["u"], 3, 1.0))
+    res = ipm.residuals(qp, it, 0.1)
+    K, _, _, _ = ipm.condensed_system(qp, it, res)
+    pv = np.random.default_rng(2).normal(size=p["n"])
+    cols = np.array([0, 7, 100, 249])
+    q = kkt_check.rt_condensed_entries(p, it.x, it.s, it.y, it.zl, it.zu, pv, cols)
+    np.testing.assert_allclose(q, (K @ pv)[cols], rtol=1e-11)
+    rd = kkt_check.rt_residual_dual(p, it.x, it.y, it.zl, it.zu)
+    np.testing.assert_allclose(rd, res[0], rtol=1e-11, atol=1e-9)
