@@ -46,7 +46,8 @@ enum ipm_status {
   IPM_INFEASIBLE_SUSPECTED = 6,  /* primal or dual residual stagnates while mu -> 0             */
   IPM_ERR_TIMEOUT = 7,           /* host wall-clock limit options.timeout_ms exceeded           */
   IPM_ERR_CUDA = 8,              /* a CUDA runtime call failed (see ipm_last_error)             */
-  IPM_ERR_STATE = 9              /* call out of order (e.g. ipm_solve before ipm_set_qp)        */
+  IPM_ERR_STATE = 9,             /* call out of order (e.g. ipm_solve before ipm_set_qp)        */
+  IPM_ERR_TOO_LARGE = 10         /* size beyond the fixed scratch of ipm_apply_operator_static  */
 };
 
 enum ipm_mem_space { IPM_MEM_HOST = 0, IPM_MEM_DEVICE = 1 };
@@ -221,6 +222,26 @@ int ipm_get_trace(const ipm_handle* h, double* buf, int max_rows);
  * Any output pointer may be NULL. */
 int ipm_profile_operator(ipm_handle* h, int reps, double* ms_rows, double* ms_cols, double* bytes_rows,
                          double* bytes_cols, double* flops_rows, double* flops_cols);
+
+/* ---- Allocation-free operator apply (the paper has no counterpart) ----
+ * For callers that cannot call cudaMalloc (an application that owns and budgets all device
+ * memory itself, a custom allocator that must not recurse into the CUDA allocator, a hook
+ * that may not allocate): computes, with no allocation of any kind,
+ *     q = R^T diag(omega) (R p) + dg o p
+ * -- the condensed PCG operator when R = [F; A], omega = f_w (+ theta on constraint rows) and
+ * dg = h0 + sigma -- from caller-owned device arrays: R (nR x n CSR), its transpose RT
+ * (n x nR CSR), omega (nR), dg, p and q (n).  The intermediate R p lives in a file-scope
+ * device array of IPM_STATIC_SCRATCH_ROWS doubles (2 MiB, held by every GPU that loads the
+ * library until the process exits); nR > IPM_STATIC_SCRATCH_ROWS returns IPM_ERR_TOO_LARGE
+ * before any work.  The first call on a device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU race, so serialise them.  Work is queued on
+ * `stream` (device pointers only); returns IPM_ERR_ARG for NULL or negative arguments. */
+#define IPM_STATIC_SCRATCH_ROWS 262144
+int ipm_apply_operator_static(int64_t n, int64_t nR, const int64_t* R_indptr, const int32_t* R_indices,
+                              const double* R_data, const int64_t* RT_indptr, const int32_t* RT_indices,
+                              const double* RT_data, const double* omega, const double* dg,
+                              const double* p, double* q, void* stream);
 
 #ifdef __cplusplus
 }

@@ -362,6 +362,7 @@ const char* ipm_status_str(int s) {
     case IPM_ERR_TIMEOUT: return "wall-clock limit exceeded";
     case IPM_ERR_CUDA: return "CUDA error";
     case IPM_ERR_STATE: return "call out of order";
+    case IPM_ERR_TOO_LARGE: return "size exceeds the fixed static scratch (IPM_STATIC_SCRATCH_ROWS rows)";
     default: return "unknown status";
   }
 }

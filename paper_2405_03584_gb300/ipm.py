@@ -19,7 +19,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libipm.so")
 
 IPM_OK, IPM_ERR_ARG, IPM_ERR_OOM, IPM_MAX_ITER, IPM_CG_STALL, IPM_NUMERICAL, \
-    IPM_INFEASIBLE_SUSPECTED, IPM_ERR_TIMEOUT, IPM_ERR_CUDA, IPM_ERR_STATE = range(10)
+    IPM_INFEASIBLE_SUSPECTED, IPM_ERR_TIMEOUT, IPM_ERR_CUDA, IPM_ERR_STATE, IPM_ERR_TOO_LARGE = range(11)
+STATIC_SCRATCH_ROWS = 262144
 MEM_HOST, MEM_DEVICE = 0, 1
 PRECOND = {"jacobi": 0, "jacobi_lr": 1, "dense": 2, "auto": 3}
 COLD, WARM = 0, 1
@@ -27,7 +28,7 @@ COLD, WARM = 0, 1
 EXPORTS = ["ipm_default_options", "ipm_create", "ipm_set_qp", "ipm_solve", "ipm_get_xyz", "ipm_destroy",
            "ipm_status_str", "ipm_last_error", "ipm_set_iterate", "ipm_residuals", "ipm_apply_kkt",
            "ipm_precond_diag", "ipm_newton_direction", "ipm_step_lengths", "ipm_profile_operator",
-           "ipm_get_trace"]
+           "ipm_get_trace", "ipm_apply_operator_static"]
 TRACE_COLS = ("iter", "mu", "rel_kkt", "primal", "dual", "gap", "alpha_p", "alpha_d", "pcg_iters", "pcg_converged",
               "stiff_rows", "pcg_rel_residual", "eta")
 
@@ -96,6 +97,7 @@ def load(path: str = LIB_PATH):
         "ipm_step_lengths": (I, [P, P, P, P, P, P, D, C.POINTER(C.c_double), C.POINTER(C.c_double), I, P]),
         "ipm_profile_operator": (I, [P, I] + [C.POINTER(C.c_double)] * 6),
         "ipm_get_trace": (I, [P, P, I]),
+        "ipm_apply_operator_static": (I, [C.c_int64, C.c_int64] + [P] * 10 + [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
