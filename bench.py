@@ -116,21 +116,30 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _ncu_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the summary was taken
-    on the current kernel source (its recorded source hash matches); else None."""
+def operator_source_hash():
+    """Hash of the source of the two PCG operator kernels and the row-dot helper they use."""
     import hashlib
+    import re
+    k = open(os.path.join(ROOT, "paper_2405_03584_gb300", "csrc", "kernels.cu")).read()
+    c = open(os.path.join(ROOT, "paper_2405_03584_gb300", "csrc", "common.cuh")).read()
+    a = k.index("// v = omega o (R p).")
+    b = k.index("// dx += alpha p; r -= alpha q;")
+    m = re.search(r"template <int G, bool SQ>\n__device__ __forceinline__ double group_row_dot\(.*?\n}\n", c, re.S)
+    return hashlib.sha256((k[a:b] + (m.group(0) if m else "")).encode()).hexdigest()[:16]
+
+
+def _ncu_traffic(kernel, lanes):
+    """DRAM bytes per launch of `kernel` (with `lanes` lanes per row) from the committed ncu
+    summary, if it was taken on the current operator source (recorded hash matches); else None."""
     summ = os.path.join(ROOT, "profiles", "pcg_operator_rt_c1.md")
     if not os.path.exists(summ):
         return None
-    src = open(os.path.join(ROOT, "paper_2405_03584_gb300", "csrc", "kernels.cu"), "rb").read() + \
-        open(os.path.join(ROOT, "paper_2405_03584_gb300", "csrc", "common.cuh"), "rb").read()
-    h = hashlib.sha256(src).hexdigest()[:16]
     txt = open(summ).read()
-    if ("source_hash: " + h) not in txt:
+    if ("source_hash: " + operator_source_hash()) not in txt:
         return None
+    key = "traffic_per_launch_bytes[%s<%d>]:" % (kernel, lanes)
     for line in txt.splitlines():
-        if line.startswith("traffic_per_launch_bytes[%s]:" % kernel):
+        if line.strip().startswith(key):
             return float(line.split(":")[1])
     return None
 
@@ -175,6 +184,25 @@ def run_reference(args):
     return 0
 
 
+def run_operator_only(args):
+    """Small capture target for profilers: the RT workload, three IPM iterations, then the two
+    operator kernels three times each (ipm_profile_operator)."""
+    import torch
+    from paper_2405_03584_gb300 import build, ipm, workloads as W
+    torch.cuda.set_device(0)
+    build.build()
+    p = W.rt_qp(n=N_FULL, seed=SEED)
+    s = ipm.Solver(tol_kkt=TOL, precond="jacobi_lr", max_ipm=3, autotune=1)
+    s.set_qp_rt(p)
+    s.solve()
+    out = s.profile_operator(reps=3)
+    out["lanes"] = [s.get()["info"]["lanes_rows"], s.get()["info"]["lanes_cols"]]
+    out["operator_source_hash"] = operator_source_hash()
+    print(json.dumps(out), flush=True)
+    s.close()
+    return 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -190,7 +218,7 @@ def run_ours(args):
     build.build()
     dev = torch.cuda.current_device()
     p = W.rt_qp(n=N_FULL, seed=SEED)
-    s = ipm.Solver(tol_kkt=TOL, precond="jacobi_lr")
+    s = ipm.Solver(tol_kkt=TOL, precond="jacobi_lr", use_graphs=0 if args.no_graphs else 1, autotune=1)
     s.set_qp_rt(p)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -233,8 +261,10 @@ def run_ours(args):
     ms, byts, flops = prof["ms_" + key], prof["bytes_" + key], prof["flops_" + key]
     peak, peak_kind = _peaks()
     achieved = byts / (ms / 1000.0) / 1e9
-    roof = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": _ncu_traffic(kern), "peak_kind": peak_kind + " hbm_gbs",
+    lanes = infos[-1]["lanes_rows"] if kern == "k_op_rows" else infos[-1]["lanes_cols"]
+    roof = {"bound": "hbm", "kernel": "%s<%d lanes/row>" % (kern, lanes), "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": _ncu_traffic(kern, lanes),
+            "peak_kind": peak_kind + " hbm_gbs",
             "algorithmic_bytes": byts, "ms_per_launch": ms,
             "fp64_tflops": flops / (ms / 1000.0) / 1e12, "fp64_nominal_tflops": FP64_NOMINAL_TFLOPS,
             "other_kernel": {"ms_per_launch": prof["ms_" + ("cols" if key == "rows" else "rows")],
@@ -290,7 +320,8 @@ def run_ours(args):
                "latency_ms": {"p50": statistics.median(lat), "p99": p99, "mean": statistics.mean(lat)},
                "solve": {"status": [int(x) for x in statuses], "ipm_iters": [i["ipm_iters"] for i in infos],
                          "cg_iters": [i["cg_iters"] for i in infos], "rel_kkt_device": infos[-1]["rel_kkt"],
-                         "rel_kkt_checker": rk, "max_stiff_rows": infos[-1]["max_stiff_rows"]},
+                         "rel_kkt_checker": rk, "max_stiff_rows": infos[-1]["max_stiff_rows"],
+                         "lanes_per_row": [infos[-1]["lanes_rows"], infos[-1]["lanes_cols"]]},
                "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk}
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -306,11 +337,17 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--operator-only", action="store_true",
+                    help="profiler capture target: a few IPM iterations, then the operator kernels")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch every kernel directly (for per-kernel profilers; same kernels, slower)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.operator_only:
+        return run_operator_only(args)
     return run_ours(args)
 
 

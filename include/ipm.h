@@ -81,6 +81,13 @@ typedef struct ipm_options {
   double timeout_ms;     /* host wall-clock limit per ipm_solve, 0 = none                       */
   double mem_budget;     /* bytes of device memory a handle may allocate, 0 = unlimited        */
   int equal_steps;       /* 1: alpha_p = alpha_d = min of both (default 0: separate, Alg. 1)   */
+  int autotune;          /* 1: ipm_set_qp times the operator kernels for 4/8/16/32 lanes per   */
+                         /* row on the loaded matrices and keeps the fastest (kept per matrix  */
+                         /* signature for the process).  0 (default): lanes from the average   */
+                         /* row length, so results are bitwise reproducible across processes  */
+  int use_graphs;        /* 1: one CUDA graph per IPM iteration with PCG as a conditional-while */
+                         /* node (default); 0: the same kernels launched one by one with a host */
+                         /* loop over PCG iterations (for per-kernel profilers)                */
 } ipm_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -126,6 +133,8 @@ typedef struct ipm_info {
   double mu;                 /* final barrier parameter                                    */
   double solve_ms;           /* wall time of the last ipm_solve                            */
   int64_t kernel_launches;   /* kernels of this library launched by the last ipm_solve     */
+  int lanes_rows;            /* lanes per row of the kernels over R and over R^T (chosen   */
+  int lanes_cols;            /* by the autotuner at ipm_set_qp)                            */
 } ipm_info;
 
 /* Per-step result of ipm_newton_direction. */

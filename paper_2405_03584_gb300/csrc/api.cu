@@ -9,6 +9,9 @@
 // reads a few device scalars once per IPM iteration to learn whether to stop.
 #include <algorithm>
 #include <chrono>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -204,6 +207,71 @@ int leave(ipm_handle* h, void* stream) {
   return IPM_OK;
 }
 
+// Lanes per row from the average row length (used when autotuning is off): a group of G
+// lanes should see at least 32 entries per lane... rounded to 4, 8, 16 or 32.
+int heuristic_group(double avg_nnz) {
+  int g = 4;
+  while (g < 32 && avg_nnz / g > 32.0) g *= 2;
+  return g;
+}
+
+// Autotuner results per matrix signature (n, rows of R, non-zeros), process-wide, so that a
+// QP loaded again in the same process runs the same schedule (and gives the same bits).
+std::mutex g_tune_mu;
+std::map<std::tuple<int64_t, int64_t, int64_t>, std::pair<int, int>> g_tune_cache;
+
+// Times the two operator kernels for every lane-group size on the loaded matrices (three
+// launches each after one warm-up, CUDA events on the handle's stream) and keeps the fastest.
+int autotune_groups(ipm_handle* h) {
+  Dev& d = h->d;
+  const auto key = std::make_tuple(d.n, d.nR, d.nnzR);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      d.g_rows = it->second.first;
+      d.g_cols = it->second.second;
+      h->g = make_geo(d);
+      return IPM_OK;
+    }
+  }
+  CUDA_TRY(h, cudaMemsetAsync(d.p, 0, sizeof(double) * d.n, h->st));
+  CUDA_TRY(h, cudaMemsetAsync(d.sigma, 0, sizeof(double) * d.n, h->st));
+  if (d.nR) {
+    CUDA_TRY(h, cudaMemsetAsync(d.omega, 0, sizeof(double) * d.nR, h->st));
+    CUDA_TRY(h, cudaMemsetAsync(d.vR, 0, sizeof(double) * d.nR, h->st));
+  }
+  cudaEvent_t e0, e1;
+  CUDA_TRY(h, cudaEventCreate(&e0));
+  CUDA_TRY(h, cudaEventCreate(&e1));
+  const int cand[4] = {4, 8, 16, 32};
+  for (int which = 0; which < 2; ++which) {
+    if (which == 0 && d.nR == 0) continue;
+    float best = 1e30f;
+    int bestg = which == 0 ? d.g_rows : d.g_cols;
+    for (int gsz : cand) {
+      if (which == 0) d.g_rows = gsz; else d.g_cols = gsz;
+      const Geo g = make_geo(d);
+      auto run = [&]() { return which == 0 ? launch_op_rows_only(d, g, h->st) : launch_op_cols_only(d, g, h->st); };
+      CUDA_TRY(h, run());
+      CUDA_TRY(h, cudaEventRecord(e0, h->st));
+      for (int r = 0; r < 3; ++r) CUDA_TRY(h, run());
+      CUDA_TRY(h, cudaEventRecord(e1, h->st));
+      CUDA_TRY(h, cudaEventSynchronize(e1));
+      float ms = 0;
+      CUDA_TRY(h, cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) { best = ms; bestg = gsz; }
+    }
+    if (which == 0) d.g_rows = bestg; else d.g_cols = bestg;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->g = make_geo(d);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = std::make_pair(d.g_rows, d.g_cols);
+  return IPM_OK;
+}
+
 // Captures one IPM iteration (full=true) or one Newton direction (full=false).
 int build_graph(ipm_handle* h, int pc, bool full, cudaGraphExec_t* out, int* top_kernels, int* body_kernels) {
   const Dev& d = h->d;
@@ -214,7 +282,8 @@ int build_graph(ipm_handle* h, int pc, bool full, cudaGraphExec_t* out, int* top
   auto chk = [&](cudaError_t x) { if (e == cudaSuccess && x != cudaSuccess) e = x; };
   chk(launch_diag_update(d, g, st));
   chk(launch_precond_build(d, g, pc, st));
-  chk(launch_rhs(d, g, st));
+  chk(launch_rhs(d, g, pc, st));
+  chk(launch_precond_finish(d, g, pc, st));
   chk(launch_cg_init(d, g, pc, st));
   // PCG loop: a conditional while node whose body is one PCG iteration
   cudaStreamCaptureStatus cs;
@@ -264,6 +333,36 @@ int build_graph(ipm_handle* h, int pc, bool full, cudaGraphExec_t* out, int* top
     cudaGetLastError();
     return fail(h, IPM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
   }
+  return IPM_OK;
+}
+
+// One IPM iteration with every kernel launched directly (use_graphs = 0): the same sequence
+// as the captured graph, with the PCG loop driven from the host (one scalar read per PCG
+// iteration).  Adds the kernels it launched to *launches.
+int run_iteration_direct(ipm_handle* h, int pc, int64_t* launches) {
+  const Dev& d = h->d;
+  const Geo& g = h->g;
+  cudaStream_t st = h->st;
+  CUDA_TRY(h, launch_diag_update(d, g, st));
+  CUDA_TRY(h, launch_precond_build(d, g, pc, st));
+  CUDA_TRY(h, launch_rhs(d, g, pc, st));
+  CUDA_TRY(h, launch_precond_finish(d, g, pc, st));
+  CUDA_TRY(h, launch_cg_init(d, g, pc, st));
+  const Graphs& gr = h->graphs[pc];
+  int done = 0;
+  for (int k = 0; k < h->opt.max_cg + 1 && !done; ++k) {
+    CUDA_TRY(h, launch_cg_body(d, g, pc, 0, st, false));
+    CUDA_TRY(h, cudaMemcpyAsync(&h->hs->cg_done, &d.sc->cg_done, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(h, cudaStreamSynchronize(st));
+    done = h->hs->cg_done;
+    *launches += gr.iter_body_kernels;
+  }
+  CUDA_TRY(h, launch_recover(d, g, st));
+  CUDA_TRY(h, launch_ratio(d, g, st));
+  CUDA_TRY(h, launch_update(d, g, st));
+  CUDA_TRY(h, launch_residual_summary(d, g, st));
+  CUDA_TRY(h, launch_control(d, st));
+  *launches += gr.iter_kernels;
   return IPM_OK;
 }
 
@@ -348,6 +447,8 @@ void ipm_default_options(ipm_options* o) {
   o->timeout_ms = 0.0;
   o->mem_budget = 0.0;
   o->equal_steps = 0;
+  o->autotune = 0;
+  o->use_graphs = 1;
 }
 
 const char* ipm_status_str(int s) {
@@ -558,6 +659,8 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   h->arena_bytes = bytes;
   Carver cv((char*)h->arena);
   carve(cv, dv, q, stiff_cap, sc_cap, dense);
+  dv.g_rows = heuristic_group(q.nR ? (double)q.Rv.size() / (double)q.nR : 0.0);
+  dv.g_cols = heuristic_group((double)q.Rv.size() / (double)n);
   h->d = dv;
   h->g = make_geo(dv);
   h->cnorm = cn; h->bnorm = bn; h->ncomp = ncomp; h->sc_cap = sc_cap;
@@ -597,6 +700,7 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   CUDA_TRY(h, cudaMemcpyAsync(d.sc, h->hs, sizeof(Scal), cudaMemcpyHostToDevice, h->st));
   CUDA_TRY(h, launch_diagH(d, h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));   // host staging buffers go out of scope
+  if (h->opt.autotune && (rc = autotune_groups(h))) return rc;
   h->loaded = true;
   h->have_iterate = false;
   h->precond = choose_precond(h);
@@ -634,14 +738,19 @@ int ipm_solve(ipm_handle* h, void* stream, int flags) {
   h->have_iterate = true;
   const int pc = h->precond;
   cudaGraphExec_t* gx = nullptr;
-  if ((rc = ensure_graph(h, pc, true, &gx))) return rc;
+  if ((rc = ensure_graph(h, pc, true, &gx))) return rc;   // also counts the kernels per iteration
+  if (!h->opt.use_graphs) gx = nullptr;
   int64_t cg_total = 0, launches = (flags & IPM_WARM) && h->have_iterate ? 4 : 13;
   int cg_max_step = 0;
   int status = IPM_MAX_ITER;
   const Graphs& grs = h->graphs[pc];
   h->trace.clear();
   for (int it = 0; it < h->opt.max_ipm; ++it) {
-    CUDA_TRY(h, cudaGraphLaunch(*gx, h->st));
+    if (gx) {
+      CUDA_TRY(h, cudaGraphLaunch(*gx, h->st));
+    } else if ((rc = run_iteration_direct(h, pc, &launches))) {
+      return rc;
+    }
     CUDA_TRY(h, cudaMemcpyAsync(h->hs, h->d.sc, sizeof(Scal), cudaMemcpyDeviceToHost, h->st));
     if (h->opt.timeout_ms > 0) {
       CUDA_TRY(h, cudaEventRecord(h->ev, h->st));
@@ -663,7 +772,7 @@ int ipm_solve(ipm_handle* h, void* stream, int flags) {
     const Scal& s = *h->hs;
     cg_total += s.cg_iter;
     cg_max_step = std::max(cg_max_step, s.cg_iter);
-    launches += grs.iter_kernels + (int64_t)std::max(1, s.cg_iter) * grs.iter_body_kernels;
+    if (gx) launches += grs.iter_kernels + (int64_t)std::max(1, s.cg_iter) * grs.iter_body_kernels;
     const double row[IPM_TRACE_COLS] = {(double)s.ipm_iter, s.mu, s.rel_kkt, s.res_primal, s.res_dual, s.res_gap,
                                         s.alpha_p, s.alpha_d, (double)s.cg_iter, (double)s.cg_conv,
                                         (double)(pc == PC_JACOBI_LR ? s.n_stiff : 0),
@@ -692,6 +801,8 @@ int ipm_solve(ipm_handle* h, void* stream, int flags) {
   in.mu = s.mu;
   in.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   in.kernel_launches = launches;
+  in.lanes_rows = h->d.g_rows;
+  in.lanes_cols = h->d.g_cols;
   if ((rc = leave(h, stream))) return rc;
   return status;
 }

@@ -149,6 +149,60 @@ __device__ __forceinline__ double warp_row_dot(const int64_t beg, const int64_t 
   return warp_sum((a0 + a1) + (a2 + a3));
 }
 
+// Dot product of one CSR row with a dense vector by a group of G consecutive lanes (G divides
+// 32; all lanes of the warp must call it, each with its own row).  GB300 issues a float64
+// warp instruction over many cycles, so the reduction is the cost to minimise: with G lanes a
+// row costs nnz/G fused multiply-adds per lane plus log2(G) + 1 adds, against 5 + 3 adds for a
+// whole-warp row.  Lane gl of the group takes entries gl, gl + G, ...; two accumulators keep
+// loads in flight; the combination order is fixed.
+template <int G, bool SQ>
+__device__ __forceinline__ double group_row_dot(const int64_t beg, const int64_t end, const int gl,
+                                                const int32_t* __restrict__ idx, const double* __restrict__ val,
+                                                const double* __restrict__ x) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int64_t e = beg + gl;
+  for (; e + 3 * G < end; e += 4 * G) {
+    double v0 = __ldg(val + e), v1 = __ldg(val + e + G), v2 = __ldg(val + e + 2 * G), v3 = __ldg(val + e + 3 * G);
+    const int i0 = __ldg(idx + e), i1 = __ldg(idx + e + G), i2 = __ldg(idx + e + 2 * G), i3 = __ldg(idx + e + 3 * G);
+    if (SQ) { v0 *= v0; v1 *= v1; v2 *= v2; v3 *= v3; }
+    a0 = fma(v0, __ldg(x + i0), a0);
+    a1 = fma(v1, __ldg(x + i1), a1);
+    a2 = fma(v2, __ldg(x + i2), a2);
+    a3 = fma(v3, __ldg(x + i3), a3);
+  }
+  for (; e < end; e += G) {
+    double v0 = __ldg(val + e);
+    if (SQ) v0 *= v0;
+    a0 = fma(v0, __ldg(x + __ldg(idx + e)), a0);
+  }
+  double s = (a0 + a1) + (a2 + a3);
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// Two vectors through the same matrix row (one pass over the row), by a group of G lanes.
+template <int G>
+__device__ __forceinline__ void group_row_dot2(const int64_t beg, const int64_t end, const int gl,
+                                               const int32_t* __restrict__ idx, const double* __restrict__ val,
+                                               const double* __restrict__ x1, const double* __restrict__ x2,
+                                               double& o1, double& o2) {
+  double a = 0.0, b = 0.0;
+  for (int64_t e = beg + gl; e < end; e += G) {
+    const double v = __ldg(val + e);
+    const int i = __ldg(idx + e);
+    a = fma(v, __ldg(x1 + i), a);
+    b = fma(v, __ldg(x2 + i), b);
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  o1 = a;
+  o2 = b;
+}
+
 // Same, over two vectors at once (one pass over the matrix).
 __device__ __forceinline__ void warp_row_dot2(const int64_t beg, const int64_t end, const int32_t* __restrict__ idx,
                                               const double* __restrict__ val, const double* __restrict__ x1,

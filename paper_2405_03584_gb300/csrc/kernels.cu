@@ -18,6 +18,31 @@ namespace ipmk {
 static __device__ __forceinline__ int gwarp() { return (blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
 static __device__ __forceinline__ int nwarps() { return (gridDim.x * blockDim.x) >> 5; }
 
+// Lanes per row of the streaming row kernels (see group_row_dot): G is a template parameter,
+// picked per matrix at ipm_set_qp (Dev::g_rows for R, Dev::g_cols for R^T).
+template <int G>
+static __device__ __forceinline__ int glane() { return threadIdx.x & (G - 1); }
+
+// Grid-stride loop over rows, G lanes per row, with a warp-uniform trip count (the group
+// shuffles need every lane of the warp): the loop runs over the first row of each warp's
+// groups; a group whose row is past the end works on an empty row.
+#define FOR_GROUP_ROWS(G, r, ok, nrows)                                                                \
+  for (int64_t r##_0 = (int64_t)gwarp() * (32 / G); r##_0 < (nrows); r##_0 += (int64_t)nwarps() * (32 / G)) \
+    for (int64_t r = r##_0 + (threadIdx.x & 31) / G, r##_once = 0; r##_once == 0; r##_once = 1)           \
+      for (bool ok = r < (nrows), ok##_once = true; ok##_once; ok##_once = false)
+
+// Instantiates a launch for the lane-group size g (4, 8, 16 or 32) chosen at run time.
+#define DISPATCH_G(g, ...)                         \
+  do {                                             \
+    switch (g) {                                   \
+      case 4: { constexpr int G = 4; __VA_ARGS__; } break;   \
+      case 8: { constexpr int G = 8; __VA_ARGS__; } break;   \
+      case 16: { constexpr int G = 16; __VA_ARGS__; } break; \
+      default: { constexpr int G = 32; __VA_ARGS__; } break; \
+    }                                              \
+  } while (0)
+
+
 Geo make_geo(const Dev& d) {
   auto blocks_for = [](int64_t items, int per_block) -> int {
     int64_t b = (items + per_block - 1) / per_block;
@@ -25,10 +50,12 @@ Geo make_geo(const Dev& d) {
     return (int)b;
   };
   Geo g;
-  const int wpb = kBlock / kWarp;
-  g.gR = blocks_for(d.nR, wpb);
-  g.gM = blocks_for(d.m, wpb);
-  g.gN = blocks_for(d.n, wpb);
+  const int gr = d.g_rows > 0 ? d.g_rows : 32, gc = d.g_cols > 0 ? d.g_cols : 32;
+  g.gR = blocks_for(d.nR, kBlock / gr);
+  g.gM = blocks_for(d.m, kBlock / gr);
+  g.gN = blocks_for(d.n, kBlock / gc);
+  g.eM = blocks_for(d.m, kBlock);
+  g.eN = blocks_for(d.n, kBlock);
   return g;
 }
 
@@ -57,12 +84,14 @@ cudaError_t launch_diagH(const Dev& d, cudaStream_t st) {
 // ------------------------------------------------------------------------------ residuals
 
 // t = R x; v = w_R o t; partial sum of w_R t^2 (the factor part of x^T H x).
+template <int G>
 __global__ void k_rows_resid(Dev d, double* part) {
   __shared__ double sh[32];
   double acc = 0.0;
-  for (int64_t r = gwarp(); r < d.nR; r += nwarps()) {
-    double t = warp_row_dot<false>(d.R_ptr[r], d.R_ptr[r + 1], d.R_idx, d.R_val, d.x);
-    if ((threadIdx.x & 31) == 0) {
+  FOR_GROUP_ROWS(G, r, ok, d.nR) {
+    const int64_t beg = ok ? d.R_ptr[r] : 0, end = ok ? d.R_ptr[r + 1] : 0;
+    const double t = group_row_dot<G, false>(beg, end, glane<G>(), d.R_idx, d.R_val, d.x);
+    if (ok && glane<G>() == 0) {
       const double w = d.wR[r];
       d.tR[r] = t;
       d.vR[r] = w * t;
@@ -102,18 +131,22 @@ __global__ void k_cons_resid(Dev d, double* part) {
 
 // Variables: Hx = R^T vR + Hs x + h0 o x, A^T y = R^T vR2, r_d, r_l, r_u and the scalar parts
 // of the objective, the dual objective and the complementarity sum.
+template <int G>
 __global__ void k_cols_resid(Dev d, double* part) {
   __shared__ double sh[32];
   const double mu = d.sc->mu;
   double rd_inf = 0.0, hx_inf = 0.0, aty_inf = 0.0, rc_inf = 0.0, xHsx = 0.0, cx = 0.0, lzl = 0.0,
          uzu = 0.0, tz = 0.0, bviol = 0.0;
-  const int lane = threadIdx.x & 31;
-  for (int64_t j = gwarp(); j < d.n; j += nwarps()) {
+  FOR_GROUP_ROWS(G, j, ok, d.n) {
     double hx_f, aty;
-    warp_row_dot2(d.RT_ptr[j], d.RT_ptr[j + 1], d.RT_idx, d.RT_val, d.vR, d.vR2, hx_f, aty);
+    const int64_t beg = ok ? d.RT_ptr[j] : 0, end = ok ? d.RT_ptr[j + 1] : 0;
+    group_row_dot2<G>(beg, end, glane<G>(), d.RT_idx, d.RT_val, d.vR, d.vR2, hx_f, aty);
     double hs = 0.0;
-    if (d.Hs_ptr) hs = warp_row_dot<false>(d.Hs_ptr[j], d.Hs_ptr[j + 1], d.Hs_idx, d.Hs_val, d.x);
-    if (lane == 0) {
+    if (d.Hs_ptr) {
+      const int64_t hb = ok ? d.Hs_ptr[j] : 0, he = ok ? d.Hs_ptr[j + 1] : 0;
+      hs = group_row_dot<G, false>(hb, he, glane<G>(), d.Hs_idx, d.Hs_val, d.x);
+    }
+    if (ok && glane<G>() == 0) {
       const double xj = d.x[j];
       const double hsx = hs + d.h0[j] * xj;
       const double hx = hx_f + hsx;
@@ -220,11 +253,11 @@ cudaError_t launch_residual_summary(const Dev& d, const Geo& g, cudaStream_t st)
   double* part = d.partials;
   if (d.nR) {
     cudaMemsetAsync(d.vR2, 0, sizeof(double) * d.nR, st);
-    k_rows_resid<<<g.gR, kBlock, 0, st>>>(d, part);
+    DISPATCH_G(d.g_rows, k_rows_resid<G><<<g.gR, kBlock, 0, st>>>(d, part));
   }
-  if (d.m) k_cons_resid<<<g.gM, kBlock, 0, st>>>(d, part);
-  k_cols_resid<<<g.gN, kBlock, 0, st>>>(d, part);
-  k_resid_final<<<1, 1024, 0, st>>>(d, g.gR, g.gM, g.gN, part);
+  if (d.m) k_cons_resid<<<g.eM, kBlock, 0, st>>>(d, part);
+  DISPATCH_G(d.g_cols, k_cols_resid<G><<<g.gN, kBlock, 0, st>>>(d, part));
+  k_resid_final<<<1, 1024, 0, st>>>(d, g.gR, g.eM, g.gN, part);
   return cudaGetLastError();
 }
 
@@ -241,7 +274,7 @@ __global__ void k_comp_resid(Dev d) {
 }
 
 cudaError_t launch_comp_resid(const Dev& d, const Geo& g, cudaStream_t st) {
-  k_comp_resid<<<std::max(g.gN, g.gM), kBlock, 0, st>>>(d);
+  k_comp_resid<<<std::max(g.eN, g.eM), kBlock, 0, st>>>(d);
   return cudaGetLastError();
 }
 
@@ -270,14 +303,17 @@ __global__ void k_start_s(Dev d) {
 }
 
 // g = H x0 + c; z_l0 = max(1, g), z_u0 = max(1, -g) on finite bounds.
+template <int G>
 __global__ void k_start_z(Dev d) {
-  const int lane = threadIdx.x & 31;
-  for (int64_t j = gwarp(); j < d.n; j += nwarps()) {
-    double hx = 0.0;
-    if (d.nR) hx = warp_row_dot<false>(d.RT_ptr[j], d.RT_ptr[j + 1], d.RT_idx, d.RT_val, d.vR);
+  FOR_GROUP_ROWS(G, j, ok, d.n) {
+    const int64_t beg = ok ? d.RT_ptr[j] : 0, end = ok ? d.RT_ptr[j + 1] : 0;
+    const double hx = group_row_dot<G, false>(beg, end, glane<G>(), d.RT_idx, d.RT_val, d.vR);
     double hs = 0.0;
-    if (d.Hs_ptr) hs = warp_row_dot<false>(d.Hs_ptr[j], d.Hs_ptr[j + 1], d.Hs_idx, d.Hs_val, d.x);
-    if (lane == 0) {
+    if (d.Hs_ptr) {
+      const int64_t hb = ok ? d.Hs_ptr[j] : 0, he = ok ? d.Hs_ptr[j + 1] : 0;
+      hs = group_row_dot<G, false>(hb, he, glane<G>(), d.Hs_idx, d.Hs_val, d.x);
+    }
+    if (ok && glane<G>() == 0) {
       const double g = hx + hs + d.h0[j] * d.x[j] + d.c[j];
       d.zl[j] = d.fl[j] ? fmax(1.0, g) : 0.0;
       d.zu[j] = d.fu[j] ? fmax(1.0, -g) : 0.0;
@@ -304,11 +340,11 @@ __global__ void k_start_mu(Dev d) {
 }
 
 cudaError_t launch_start_point(const Dev& d, const Geo& g, cudaStream_t st) {
-  k_start_x<<<g.gN, kBlock, 0, st>>>(d);
-  if (d.nR) k_rows_resid<<<g.gR, kBlock, 0, st>>>(d, d.partials);
-  if (d.m) k_start_s<<<g.gM, kBlock, 0, st>>>(d);
-  k_start_z<<<g.gN, kBlock, 0, st>>>(d);
-  if (d.m) k_start_y<<<g.gM, kBlock, 0, st>>>(d);
+  k_start_x<<<g.eN, kBlock, 0, st>>>(d);
+  if (d.nR) DISPATCH_G(d.g_rows, k_rows_resid<G><<<g.gR, kBlock, 0, st>>>(d, d.partials));
+  if (d.m) k_start_s<<<g.eM, kBlock, 0, st>>>(d);
+  DISPATCH_G(d.g_cols, k_start_z<G><<<g.gN, kBlock, 0, st>>>(d));
+  if (d.m) k_start_y<<<g.eM, kBlock, 0, st>>>(d);
   cudaError_t e = launch_residual_summary(d, g, st);
   if (e != cudaSuccess) return e;
   k_start_mu<<<1, 32, 0, st>>>(d);
@@ -376,7 +412,9 @@ __global__ void k_diag_n(Dev d) {
     if (d.fl[j]) sg += d.zl[j] / (d.x[j] - d.l[j]);
     if (d.fu[j]) sg += d.zu[j] / (d.u[j] - d.x[j]);
     d.sigma[j] = sg;
-    d.M0[j] = d.diagH[j] + sg;
+    const double m0 = d.diagH[j] + sg;
+    d.M0[j] = m0;
+    d.Minv[j] = 1.0 / m0;   // 1 / M0 until the Jacobi diagonal of the moderate rows replaces it
   }
 }
 
@@ -385,8 +423,8 @@ cudaError_t launch_diag_update(const Dev& d, const Geo& g, cudaStream_t st) {
     cudaMemcpyAsync(d.omega, d.wR, sizeof(double) * d.nR, cudaMemcpyDeviceToDevice, st);
     cudaMemsetAsync(d.thR, 0, sizeof(double) * d.nR, st);
   }
-  if (d.m) k_diag_m<<<g.gM, kBlock, 0, st>>>(d);
-  k_diag_n<<<g.gN, kBlock, 0, st>>>(d);
+  if (d.m) k_diag_m<<<g.eM, kBlock, 0, st>>>(d);
+  k_diag_n<<<g.eN, kBlock, 0, st>>>(d);
   return cudaGetLastError();
 }
 
@@ -394,11 +432,12 @@ cudaError_t launch_diag_update(const Dev& d, const Geo& g, cudaStream_t st) {
 
 // M_j = M0_j + sum_i R_ij^2 thR_i  (thR: theta of the rows kept in the diagonal part).
 // Writes 1 / M_j to out (INV) or M_j.
-template <bool INV>
+template <bool INV, int G>
 __global__ void k_jacobi(Dev d, double* out) {
-  for (int64_t j = gwarp(); j < d.n; j += nwarps()) {
-    double a = warp_row_dot<true>(d.RT_ptr[j], d.RT_ptr[j + 1], d.RT_idx, d.RT_val, d.thR);
-    if ((threadIdx.x & 31) == 0) {
+  FOR_GROUP_ROWS(G, j, ok, d.n) {
+    const int64_t beg = ok ? d.RT_ptr[j] : 0, end = ok ? d.RT_ptr[j + 1] : 0;
+    const double a = group_row_dot<G, true>(beg, end, glane<G>(), d.RT_idx, d.RT_val, d.thR);
+    if (ok && glane<G>() == 0) {
       const double mj = d.M0[j] + a;
       out[j] = INV ? 1.0 / mj : mj;
     }
@@ -406,7 +445,7 @@ __global__ void k_jacobi(Dev d, double* out) {
 }
 
 cudaError_t launch_jacobi_full(const Dev& d, const Geo& g, double* out, cudaStream_t st) {
-  k_jacobi<false><<<g.gN, kBlock, 0, st>>>(d, out);
+  DISPATCH_G(d.g_cols, k_jacobi<false, G><<<g.gN, kBlock, 0, st>>>(d, out));
   return cudaGetLastError();
 }
 
@@ -415,23 +454,19 @@ cudaError_t launch_jacobi_full(const Dev& d, const Geo& g, double* out, cudaStre
 // ratio_k = theta_k sum_j A_kj^2 / M0_j; histogram of log2(ratio / gamma) in half-octave bins;
 // the last block picks the smallest threshold bin whose cumulative count from the top stays
 // <= stiff_max.  Rows with ratio >= stiff_thresh form the low-rank correction.
+template <int G>
 __global__ void k_stiff_ratio(Dev d) {
   __shared__ unsigned int h[kHistBins];
   __shared__ bool s_last;
   for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) h[i] = 0u;
   __syncthreads();
   const double gamma = d.sc->stiff_gamma;
-  for (int64_t k = gwarp(); k < d.m; k += nwarps()) {
-    const int32_t row = d.arow[k];
-    // 1 / M0 via the gather: sum_j R_ij^2 / M0_j; M0 inverted on the fly
-    const int64_t beg = d.R_ptr[row], end = d.R_ptr[row + 1];
-    double acc = 0.0;
-    for (int64_t e = beg + (threadIdx.x & 31); e < end; e += 32) {
-      const double v = d.R_val[e];
-      acc += v * v / d.M0[d.R_idx[e]];
-    }
-    acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) {
+  FOR_GROUP_ROWS(G, k, ok, d.m) {
+    const int32_t row = ok ? d.arow[k] : 0;
+    const int64_t beg = ok ? d.R_ptr[row] : 0, end = ok ? d.R_ptr[row + 1] : 0;
+    // sum_j R_kj^2 / M0_j with 1 / M0 precomputed in Minv
+    const double acc = group_row_dot<G, true>(beg, end, glane<G>(), d.R_idx, d.R_val, d.Minv);
+    if (ok && glane<G>() == 0) {
       const double ratio = d.theta[k] * acc;
       d.ratio[k] = ratio;
       if (ratio > gamma) {
@@ -469,45 +504,58 @@ __global__ void k_stiff_ratio(Dev d) {
   }
 }
 
-// Ordered compaction (one block): slot of every stiff row, thR = 0 on stiff rows.
-__global__ void k_stiff_compact(Dev d) {
-  __shared__ int wsum[32];
-  __shared__ int base;
-  if (threadIdx.x == 0) base = 0;
+// Exclusive scan of per-item 0/1 (or counts) by one block in two levels: every thread scans
+// a contiguous run serially, then the block scans the run totals.  Returns the total; calls
+// emit(i, offset) for every item i in order-preserving positions.
+template <typename Val, typename Emit>
+__device__ long long block_scan_runs(int64_t count, Val val, Emit emit) {
+  __shared__ long long tsum[1024];
+  const int t = threadIdx.x, nt = blockDim.x;
+  const int64_t run = (count + nt - 1) / nt;
+  const int64_t b0 = t * run, b1 = b0 + run < count ? b0 + run : count;
+  long long acc = 0;
+  for (int64_t i = b0; i < b1; ++i) acc += val(i);
+  tsum[t] = acc;
   __syncthreads();
-  const double thr = d.sc->stiff_thresh;
-  const double gamma = d.sc->stiff_gamma;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int64_t k0 = 0; k0 < d.m; k0 += blockDim.x) {
-    const int64_t k = k0 + threadIdx.x;
-    int flag = 0;
-    if (k < d.m) {
-      const double rt = d.ratio[k];
-      flag = (rt > gamma && rt >= thr) ? 1 : 0;
-    }
-    const unsigned bal = __ballot_sync(0xffffffffu, flag);
-    const int pre = __popc(bal & ((1u << lane) - 1u));
-    if (lane == 0) wsum[wid] = __popc(bal);
+  // Hillis-Steele inclusive scan of the nt run totals
+  for (int off = 1; off < nt; off <<= 1) {
+    long long v = t >= off ? tsum[t - off] : 0;
     __syncthreads();
-    int off = 0, total = 0;
-    for (int w = 0; w < nw; ++w) { if (w < wid) off += wsum[w]; total += wsum[w]; }
-    if (k < d.m) {
-      const int32_t row = d.arow[k];
-      const int slot = base + off + pre;
-      if (flag && slot < d.stiff_cap) {
-        d.stiff_k[slot] = (int32_t)k;
-        d.slotR[row] = slot;
-        d.thR[row] = 0.0;
-      } else {
-        d.slotR[row] = -1;
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) base += total;
+    tsum[t] += v;
     __syncthreads();
   }
+  long long base = t ? tsum[t - 1] : 0;
+  const long long total = tsum[nt - 1];
+  for (int64_t i = b0; i < b1; ++i) {
+    const long long v = val(i);
+    emit(i, base, v);
+    base += v;
+  }
+  __syncthreads();
+  return total;
+}
+
+// Ordered compaction (one block): slot of every stiff row, thR = 0 on stiff rows.
+__global__ void k_stiff_compact(Dev d) {
+  const double thr = d.sc->stiff_thresh;
+  const double gamma = d.sc->stiff_gamma;
+  const int cap = d.stiff_cap;
+  auto flag = [&](int64_t k) -> long long {
+    const double rt = d.ratio[k];
+    return (rt > gamma && rt >= thr) ? 1 : 0;
+  };
+  const long long total = block_scan_runs(d.m, flag, [&](int64_t k, long long off, long long v) {
+    const int32_t row = d.arow[k];
+    if (v && off < cap) {
+      d.stiff_k[off] = (int32_t)k;
+      d.slotR[row] = (int32_t)off;
+      d.thR[row] = 0.0;
+    } else {
+      d.slotR[row] = -1;
+    }
+  });
   if (threadIdx.x == 0) {
-    const int ns = base < d.stiff_cap ? base : d.stiff_cap;
+    const int ns = total < cap ? (int)total : cap;
     d.sc->n_stiff = ns;
     if (ns > d.sc->max_stiff_seen) d.sc->max_stiff_seen = ns;
   }
@@ -525,34 +573,14 @@ __global__ void k_sc_count(Dev d) {
   }
 }
 
-// Exclusive scan of sc_cnt into sc_ptr (one block).
+// Exclusive scan of sc_cnt into sc_ptr (one block, two levels).
 __global__ void k_sc_scan(Dev d) {
   if (d.sc->n_stiff == 0) return;
-  __shared__ long long wsum[32];
-  __shared__ long long base;
-  if (threadIdx.x == 0) base = 0;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int64_t j0 = 0; j0 < d.n; j0 += blockDim.x) {
-    const int64_t j = j0 + threadIdx.x;
-    long long v = j < d.n ? d.sc_cnt[j] : 0;
-    long long incl = v;
-    for (int o = 1; o < 32; o <<= 1) {
-      long long t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    if (lane == 31) wsum[wid] = incl;
-    __syncthreads();
-    long long off = 0, total = 0;
-    for (int w = 0; w < nw; ++w) { if (w < wid) off += wsum[w]; total += wsum[w]; }
-    if (j < d.n) d.sc_ptr[j] = base + off + incl - v;
-    __syncthreads();
-    if (threadIdx.x == 0) base += total;
-    __syncthreads();
-  }
+  const long long total = block_scan_runs(d.n, [&](int64_t j) -> long long { return d.sc_cnt[j]; },
+                                          [&](int64_t j, long long off, long long) { d.sc_ptr[j] = off; });
   if (threadIdx.x == 0) {
-    d.sc_ptr[d.n] = base;
-    if (base > d.sc_cap) d.sc->n_stiff = 0;   // does not fit: fall back to plain Jacobi
+    d.sc_ptr[d.n] = total;
+    if (total > d.sc_cap) d.sc->n_stiff = 0;   // does not fit: fall back to plain Jacobi
   }
 }
 
@@ -617,15 +645,28 @@ __global__ void k_rhs_m(Dev d) {
   }
 }
 
+// PCG start from ||rhs||^2: tolerance eta^2 ||rhs||^2, counters reset.
+static __device__ void finish_rhs(Scal* sc, double rhs2) {
+  sc->rhs2 = rhs2;
+  sc->eta_used = sc->eta;
+  sc->tol2 = sc->eta * sc->eta * rhs2;
+  sc->cg_iter = 0;
+  sc->cg_conv = 0;
+  sc->cg_done = (rhs2 == 0.0 || !isfinite(rhs2)) ? 1 : 0;
+  if (!isfinite(rhs2)) sc->status = DS_NUMERICAL;
+  else if (rhs2 == 0.0) sc->cg_conv = 1;
+}
+
 // rhs = -r_d - r_l / t_l + r_u / t_u - R^T vR2; PCG start r = rhs, dx = 0; ||rhs||^2.
+template <int G>
 __global__ void k_rhs_n(Dev d) {
   __shared__ double sh[32];
   const double mu = d.sc->mu;
   double r2 = 0.0;
-  for (int64_t j = gwarp(); j < d.n; j += nwarps()) {
-    double atu = 0.0;
-    if (d.nR) atu = warp_row_dot<false>(d.RT_ptr[j], d.RT_ptr[j + 1], d.RT_idx, d.RT_val, d.vR2);
-    if ((threadIdx.x & 31) == 0) {
+  FOR_GROUP_ROWS(G, j, ok, d.n) {
+    const int64_t beg = ok ? d.RT_ptr[j] : 0, end = ok ? d.RT_ptr[j + 1] : 0;
+    const double atu = group_row_dot<G, false>(beg, end, glane<G>(), d.RT_idx, d.RT_val, d.vR2);
+    if (ok && glane<G>() == 0) {
       double g = -d.rd[j] - atu;
       const double xj = d.x[j];
       if (d.fl[j]) { const double tl = xj - d.l[j]; g -= (tl * d.zl[j] - mu) / tl; }
@@ -640,51 +681,112 @@ __global__ void k_rhs_n(Dev d) {
   const int ops[1] = {0};
   double out[1];
   if (grid_reduce<1>(v, ops, d.partials + 20 * kMaxRedBlocks, &d.sc->ticket[T_INIT], out, sh)) {
-    if (threadIdx.x == 0) {
-      Scal* sc = d.sc;
-      sc->rhs2 = out[0];
-      sc->eta_used = sc->eta;
-      sc->tol2 = sc->eta * sc->eta * out[0];
-      sc->cg_iter = 0;
-      sc->cg_conv = 0;
-      sc->cg_done = (out[0] == 0.0 || !isfinite(out[0])) ? 1 : 0;
-      if (!isfinite(out[0])) sc->status = DS_NUMERICAL;
-      else if (out[0] == 0.0) sc->cg_conv = 1;
-    }
+    if (threadIdx.x == 0) finish_rhs(d.sc, out[0]);
   }
 }
 
-cudaError_t launch_rhs(const Dev& d, const Geo& g, cudaStream_t st) {
+// The right-hand side and the Jacobi diagonal in one pass over R^T: for each variable j the
+// same entries give sum_i R_ij u_i (plain) and sum_i R_ij^2 thR_i (squared).
+template <int G>
+__device__ __forceinline__ void group_row_dot_plain_sq(const int64_t beg, const int64_t end, const int gl,
+                                                       const int32_t* __restrict__ idx, const double* __restrict__ val,
+                                                       const double* __restrict__ xp, const double* __restrict__ xs,
+                                                       double& op, double& os) {
+  double a = 0.0, b = 0.0, a1 = 0.0, b1 = 0.0;
+  int64_t e = beg + gl;
+  for (; e + G < end; e += 2 * G) {
+    const double v0 = __ldg(val + e), v1 = __ldg(val + e + G);
+    const int i0 = __ldg(idx + e), i1 = __ldg(idx + e + G);
+    a = fma(v0, __ldg(xp + i0), a);
+    b = fma(v0 * v0, __ldg(xs + i0), b);
+    a1 = fma(v1, __ldg(xp + i1), a1);
+    b1 = fma(v1 * v1, __ldg(xs + i1), b1);
+  }
+  if (e < end) {
+    const double v0 = __ldg(val + e);
+    const int i0 = __ldg(idx + e);
+    a = fma(v0, __ldg(xp + i0), a);
+    b = fma(v0 * v0, __ldg(xs + i0), b);
+  }
+  a += a1;
+  b += b1;
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  op = a;
+  os = b;
+}
+
+template <int G>
+__global__ void k_rhs_jacobi(Dev d) {
+  __shared__ double sh[32];
+  const double mu = d.sc->mu;
+  double r2 = 0.0;
+  FOR_GROUP_ROWS(G, j, ok, d.n) {
+    const int64_t beg = ok ? d.RT_ptr[j] : 0, end = ok ? d.RT_ptr[j + 1] : 0;
+    double atu, dth;
+    group_row_dot_plain_sq<G>(beg, end, glane<G>(), d.RT_idx, d.RT_val, d.vR2, d.thR, atu, dth);
+    if (ok && glane<G>() == 0) {
+      d.Minv[j] = 1.0 / (d.M0[j] + dth);
+      double gj = -d.rd[j] - atu;
+      const double xj = d.x[j];
+      if (d.fl[j]) { const double tl = xj - d.l[j]; gj -= (tl * d.zl[j] - mu) / tl; }
+      if (d.fu[j]) { const double tu = d.u[j] - xj; gj += (tu * d.zu[j] - mu) / tu; }
+      d.rhs[j] = gj;
+      d.r[j] = gj;
+      d.dx[j] = 0.0;
+      r2 = fma(gj, gj, r2);
+    }
+  }
+  double v[1] = {r2};
+  const int ops[1] = {0};
+  double out[1];
+  if (grid_reduce<1>(v, ops, d.partials + 20 * kMaxRedBlocks, &d.sc->ticket[T_INIT], out, sh)) {
+    if (threadIdx.x == 0) finish_rhs(d.sc, out[0]);
+  }
+}
+
+cudaError_t launch_rhs(const Dev& d, const Geo& g, int precond, cudaStream_t st) {
   if (d.nR) cudaMemsetAsync(d.vR2, 0, sizeof(double) * d.nR, st);
-  if (d.m) k_rhs_m<<<g.gM, kBlock, 0, st>>>(d);
-  k_rhs_n<<<g.gN, kBlock, 0, st>>>(d);
+  if (d.m) k_rhs_m<<<g.eM, kBlock, 0, st>>>(d);
+  if (precond == PC_DENSE) {
+    DISPATCH_G(d.g_cols, k_rhs_n<G><<<g.gN, kBlock, 0, st>>>(d));
+  } else {
+    DISPATCH_G(d.g_cols, k_rhs_jacobi<G><<<g.gN, kBlock, 0, st>>>(d));
+  }
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------------ PCG
 
 // v = omega o (R p).  MODE 0: inside PCG (skips once converged); MODE 1: single apply.
-template <int MODE>
+template <int MODE, int G>
 __global__ void k_op_rows(Dev d) {
   if (MODE == 0 && d.sc->cg_done) return;
-  for (int64_t r = gwarp(); r < d.nR; r += nwarps()) {
-    double t = warp_row_dot<false>(d.R_ptr[r], d.R_ptr[r + 1], d.R_idx, d.R_val, d.p);
-    if ((threadIdx.x & 31) == 0) d.vR[r] = d.omega[r] * t;
+  FOR_GROUP_ROWS(G, r, ok, d.nR) {
+    const int64_t beg = ok ? d.R_ptr[r] : 0, end = ok ? d.R_ptr[r + 1] : 0;
+    const double t = group_row_dot<G, false>(beg, end, glane<G>(), d.R_idx, d.R_val, d.p);
+    if (ok && glane<G>() == 0) d.vR[r] = d.omega[r] * t;
   }
 }
 
 // q = R^T v + Hs p + (h0 + sigma) o p; p^T q -> alpha = rz / p^T q (last block).
 // MODE 0: inside PCG; MODE 1: a single operator apply (no scalars touched).
-template <int MODE>
+template <int MODE, int G>
 __global__ void k_op_cols(Dev d) {
   __shared__ double sh[32];
   if (MODE == 0 && d.sc->cg_done) return;
   double pq = 0.0;
-  for (int64_t j = gwarp(); j < d.n; j += nwarps()) {
-    double acc = 0.0;
-    if (d.nR) acc = warp_row_dot<false>(d.RT_ptr[j], d.RT_ptr[j + 1], d.RT_idx, d.RT_val, d.vR);
-    if (d.Hs_ptr) acc += warp_row_dot<false>(d.Hs_ptr[j], d.Hs_ptr[j + 1], d.Hs_idx, d.Hs_val, d.p);
-    if ((threadIdx.x & 31) == 0) {
+  FOR_GROUP_ROWS(G, j, ok, d.n) {
+    const int64_t beg = ok ? d.RT_ptr[j] : 0, end = ok ? d.RT_ptr[j + 1] : 0;
+    double acc = group_row_dot<G, false>(beg, end, glane<G>(), d.RT_idx, d.RT_val, d.vR);
+    if (d.Hs_ptr) {
+      const int64_t hb = ok ? d.Hs_ptr[j] : 0, he = ok ? d.Hs_ptr[j + 1] : 0;
+      acc += group_row_dot<G, false>(hb, he, glane<G>(), d.Hs_idx, d.Hs_val, d.p);
+    }
+    if (ok && glane<G>() == 0) {
       const double pj = d.p[j];
       const double qj = acc + (d.h0[j] + d.sigma[j]) * pj;
       d.q[j] = qj;
@@ -883,61 +985,64 @@ cudaError_t launch_cg_init(const Dev& d, const Geo& g, int precond, cudaStream_t
   if (precond == PC_DENSE) {
     k_dense_apply<<<g.gN, kBlock, 0, st>>>(d, 1);
   } else if (precond == PC_JACOBI_LR) {
-    k_cg_init_diag<<<g.gN, kBlock, 0, st>>>(d);
+    k_cg_init_diag<<<g.eN, kBlock, 0, st>>>(d);
     const int gs = (d.stiff_cap + 7) / 8;
     k_stiff_u<<<gs, kBlock, 0, st>>>(d, 1);
     k_stiff_t<<<gs, kBlock, 0, st>>>(d, 1);
-    k_stiff_corr<<<g.gN, kBlock, 0, st>>>(d, 1);
+    k_stiff_corr<<<g.eN, kBlock, 0, st>>>(d, 1);
   } else {
-    k_cg_init_diag<<<g.gN, kBlock, 0, st>>>(d);
+    k_cg_init_diag<<<g.eN, kBlock, 0, st>>>(d);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_body(const Dev& d, const Geo& g, int precond, cudaGraphConditionalHandle h, cudaStream_t st) {
-  if (d.nR) k_op_rows<0><<<g.gR, kBlock, 0, st>>>(d);
-  k_op_cols<0><<<g.gN, kBlock, 0, st>>>(d);
+cudaError_t launch_cg_body(const Dev& d, const Geo& g, int precond, cudaGraphConditionalHandle h, cudaStream_t st,
+                           bool in_graph) {
+  if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<0, G><<<g.gR, kBlock, 0, st>>>(d));
+  DISPATCH_G(d.g_cols, k_op_cols<0, G><<<g.gN, kBlock, 0, st>>>(d));
   if (precond == PC_DENSE) {
-    k_cg_update<2><<<g.gN, kBlock, 0, st>>>(d);
+    k_cg_update<2><<<g.eN, kBlock, 0, st>>>(d);
     k_dense_apply<<<g.gN, kBlock, 0, st>>>(d, 0);
   } else if (precond == PC_JACOBI_LR) {
-    k_cg_update<1><<<g.gN, kBlock, 0, st>>>(d);
+    k_cg_update<1><<<g.eN, kBlock, 0, st>>>(d);
     const int gs = (d.stiff_cap + 7) / 8;
     k_stiff_u<<<gs, kBlock, 0, st>>>(d, 0);
     k_stiff_t<<<gs, kBlock, 0, st>>>(d, 0);
-    k_stiff_corr<<<g.gN, kBlock, 0, st>>>(d, 0);
+    k_stiff_corr<<<g.eN, kBlock, 0, st>>>(d, 0);
   } else {
-    k_cg_update<0><<<g.gN, kBlock, 0, st>>>(d);
+    k_cg_update<0><<<g.eN, kBlock, 0, st>>>(d);
   }
-  k_cg_p<<<g.gN, kBlock, 0, st>>>(d, h, 1);
+  k_cg_p<<<g.eN, kBlock, 0, st>>>(d, h, in_graph ? 1 : 0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_op_rows_only(const Dev& d, const Geo& g, cudaStream_t st) {
-  if (d.nR) k_op_rows<1><<<g.gR, kBlock, 0, st>>>(d);
+  if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<1, G><<<g.gR, kBlock, 0, st>>>(d));
   return cudaGetLastError();
 }
 
 cudaError_t launch_op_cols_only(const Dev& d, const Geo& g, cudaStream_t st) {
-  k_op_cols<1><<<g.gN, kBlock, 0, st>>>(d);
+  DISPATCH_G(d.g_cols, k_op_cols<1, G><<<g.gN, kBlock, 0, st>>>(d));
   return cudaGetLastError();
 }
 
 cudaError_t launch_apply(const Dev& d, const Geo& g, cudaStream_t st) {
-  if (d.nR) k_op_rows<1><<<g.gR, kBlock, 0, st>>>(d);
-  k_op_cols<1><<<g.gN, kBlock, 0, st>>>(d);
+  if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<1, G><<<g.gR, kBlock, 0, st>>>(d));
+  DISPATCH_G(d.g_cols, k_op_cols<1, G><<<g.gN, kBlock, 0, st>>>(d));
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------------ recovery
 
 // A dx on the constraint rows; ds = -r_p - A dx; dy = theta (A dx + r_p) - r_s / s.
+template <int G>
 __global__ void k_recover_m(Dev d) {
   const double mu = d.sc->mu;
-  for (int64_t k = gwarp(); k < d.m; k += nwarps()) {
-    const int32_t row = d.arow[k];
-    double adx = warp_row_dot<false>(d.R_ptr[row], d.R_ptr[row + 1], d.R_idx, d.R_val, d.dx);
-    if ((threadIdx.x & 31) == 0) {
+  FOR_GROUP_ROWS(G, k, ok, d.m) {
+    const int32_t row = ok ? d.arow[k] : 0;
+    const int64_t beg = ok ? d.R_ptr[row] : 0, end = ok ? d.R_ptr[row + 1] : 0;
+    const double adx = group_row_dot<G, false>(beg, end, glane<G>(), d.R_idx, d.R_val, d.dx);
+    if (ok && glane<G>() == 0) {
       const double s = d.s[k];
       const double rs = s * d.y[k] - mu;
       d.ds[k] = -d.rp[k] - adx;
@@ -960,8 +1065,8 @@ __global__ void k_recover_n(Dev d) {
 }
 
 cudaError_t launch_recover(const Dev& d, const Geo& g, cudaStream_t st) {
-  if (d.m) k_recover_m<<<g.gM, kBlock, 0, st>>>(d);
-  k_recover_n<<<g.gN, kBlock, 0, st>>>(d);
+  if (d.m) DISPATCH_G(d.g_rows, k_recover_m<G><<<g.gM, kBlock, 0, st>>>(d));
+  k_recover_n<<<g.eN, kBlock, 0, st>>>(d);
   return cudaGetLastError();
 }
 
@@ -1017,9 +1122,9 @@ __global__ void k_ratio_final(Dev d, int gM, int gN, const double* part) {
 
 cudaError_t launch_ratio(const Dev& d, const Geo& g, cudaStream_t st) {
   double* part = d.partials + 22 * kMaxRedBlocks;
-  if (d.m) k_ratio_m<<<g.gM, kBlock, 0, st>>>(d, part);
-  k_ratio_n<<<g.gN, kBlock, 0, st>>>(d, part);
-  k_ratio_final<<<1, 256, 0, st>>>(d, d.m ? g.gM : 0, g.gN, part);
+  if (d.m) k_ratio_m<<<g.eM, kBlock, 0, st>>>(d, part);
+  k_ratio_n<<<g.eN, kBlock, 0, st>>>(d, part);
+  k_ratio_final<<<1, 256, 0, st>>>(d, d.m ? g.eM : 0, g.eN, part);
   return cudaGetLastError();
 }
 
@@ -1043,8 +1148,8 @@ __global__ void k_update_m(Dev d) {
 }
 
 cudaError_t launch_update(const Dev& d, const Geo& g, cudaStream_t st) {
-  k_update_n<<<g.gN, kBlock, 0, st>>>(d);
-  if (d.m) k_update_m<<<g.gM, kBlock, 0, st>>>(d);
+  k_update_n<<<g.eN, kBlock, 0, st>>>(d);
+  if (d.m) k_update_m<<<g.eM, kBlock, 0, st>>>(d);
   return cudaGetLastError();
 }
 
@@ -1053,13 +1158,19 @@ cudaError_t launch_update(const Dev& d, const Geo& g, cudaStream_t st) {
 cudaError_t launch_dense_build(const Dev& d, cudaStream_t st);       // dense.cu
 cudaError_t launch_stiff_factor(const Dev& d, cudaStream_t st);      // dense.cu
 
+// Before the right-hand side: stiff-row selection (JACOBI_LR).
 cudaError_t launch_precond_build(const Dev& d, const Geo& g, int precond, cudaStream_t st) {
-  if (precond == PC_DENSE) return launch_dense_build(d, st);
   if (precond == PC_JACOBI_LR && d.m) {
-    k_stiff_ratio<<<g.gM, kBlock, 0, st>>>(d);
+    DISPATCH_G(d.g_rows, k_stiff_ratio<G><<<g.gM, kBlock, 0, st>>>(d));
     k_stiff_compact<<<1, 1024, 0, st>>>(d);
   }
-  k_jacobi<true><<<g.gN, kBlock, 0, st>>>(d, d.Minv);
+  return cudaGetLastError();
+}
+
+// After the right-hand side (which also wrote the Jacobi diagonal): the low-rank factor
+// (JACOBI_LR) or the dense factor (DENSE).
+cudaError_t launch_precond_finish(const Dev& d, const Geo& g, int precond, cudaStream_t st) {
+  if (precond == PC_DENSE) return launch_dense_build(d, st);
   if (precond == PC_JACOBI_LR && d.m) {
     k_sc_count<<<g.gN, kBlock, 0, st>>>(d);
     k_sc_scan<<<1, 1024, 0, st>>>(d);

@@ -12,6 +12,7 @@ namespace ipmk {
 struct Dev {
   int64_t n, m, nR;            // variables, constraint rows, rows of R = [F; A_csr]
   int64_t nnzR, nnzHs;
+  int g_rows, g_cols;          // lanes per row of the kernels over R and over R^T (4, 8, 16, 32)
   // problem data
   const int64_t* R_ptr; const int32_t* R_idx; const double* R_val;
   const int64_t* RT_ptr; const int32_t* RT_idx; const double* RT_val;
@@ -50,7 +51,8 @@ struct Dev {
 
 // Launch geometry shared by the host code and the final reduction kernel.
 struct Geo {
-  int gR, gM, gN;              // blocks of the nR-row, m-row and n-column kernels
+  int gR, gM, gN;              // blocks of the row-group kernels over R rows, constraint rows, R^T rows
+  int eM, eN;                  // blocks of the one-thread-per-element kernels over m and n
 };
 
 Geo make_geo(const Dev& d);
@@ -66,11 +68,13 @@ cudaError_t launch_comp_resid(const Dev& d, const Geo& g, cudaStream_t st);
 cudaError_t launch_control(const Dev& d, cudaStream_t st);
 // ---- diagonal update and preconditioner build ----
 cudaError_t launch_diag_update(const Dev& d, const Geo& g, cudaStream_t st);
-cudaError_t launch_precond_build(const Dev& d, const Geo& g, int precond, cudaStream_t st);
+cudaError_t launch_precond_build(const Dev& d, const Geo& g, int precond, cudaStream_t st);   // before rhs
+cudaError_t launch_precond_finish(const Dev& d, const Geo& g, int precond, cudaStream_t st);  // after rhs
 // ---- right-hand side and PCG ----
-cudaError_t launch_rhs(const Dev& d, const Geo& g, cudaStream_t st);
+cudaError_t launch_rhs(const Dev& d, const Geo& g, int precond, cudaStream_t st);  // + Jacobi diagonal
 cudaError_t launch_cg_init(const Dev& d, const Geo& g, int precond, cudaStream_t st);
-cudaError_t launch_cg_body(const Dev& d, const Geo& g, int precond, cudaGraphConditionalHandle h, cudaStream_t st);
+cudaError_t launch_cg_body(const Dev& d, const Geo& g, int precond, cudaGraphConditionalHandle h, cudaStream_t st,
+                           bool in_graph = true);
 // ---- direction recovery, ratio test, update ----
 cudaError_t launch_recover(const Dev& d, const Geo& g, cudaStream_t st);
 cudaError_t launch_ratio(const Dev& d, const Geo& g, cudaStream_t st);

@@ -38,7 +38,7 @@ class Options(C.Structure):
                 ("cg_eta_max", C.c_double), ("cg_eta_min", C.c_double), ("cg_eta_factor", C.c_double),
                 ("precond", C.c_int), ("stiff_gamma", C.c_double), ("stiff_max", C.c_int),
                 ("dense_max_n", C.c_int), ("timeout_ms", C.c_double), ("mem_budget", C.c_double),
-                ("equal_steps", C.c_int)]
+                ("equal_steps", C.c_int), ("autotune", C.c_int), ("use_graphs", C.c_int)]
 
 
 class QP(C.Structure):
@@ -54,7 +54,7 @@ class Info(C.Structure):
                 ("max_stiff_rows", C.c_int), ("precond", C.c_int), ("rel_kkt", C.c_double),
                 ("primal_res", C.c_double), ("dual_res", C.c_double), ("gap_res", C.c_double),
                 ("primal_obj", C.c_double), ("dual_obj", C.c_double), ("mu", C.c_double), ("solve_ms", C.c_double),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("lanes_rows", C.c_int), ("lanes_cols", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

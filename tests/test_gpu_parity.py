@@ -213,6 +213,28 @@ def test_bitwise_deterministic():
     assert np.array_equal(xs[0], xs[1])
 
 
+def test_autotuned_schedule_solves():
+    p = W.rt_qp(n=1100, seed=16)
+    with ipm.Solver(tol_kkt=1e-8, precond="jacobi_lr", autotune=1) as s:
+        s.set_qp_rt(p)
+        assert s.solve() == ipm.IPM_OK
+        out = s.get()
+        assert out["info"]["lanes_rows"] in (4, 8, 16, 32) and out["info"]["lanes_cols"] in (4, 8, 16, 32)
+        assert kkt_check.rel_kkt(kkt_check.rt_ops(p), out["x"], out["y"], out["zl"], out["zu"]) <= 1e-8
+
+
+def test_direct_launch_mode_matches_graphs():
+    """use_graphs = 0 runs the same kernels one by one: the same bits as the graph path."""
+    p = W.rt_qp(n=600, seed=17)
+    xs = []
+    for ug in (1, 0):
+        with ipm.Solver(tol_kkt=1e-8, precond="jacobi_lr", use_graphs=ug) as s:
+            s.set_qp_rt(p)
+            assert s.solve() == ipm.IPM_OK
+            xs.append(s.get()["x"])
+    assert np.array_equal(xs[0], xs[1])
+
+
 def test_warm_start_from_solution():
     p = W.rt_qp(n=800, seed=15)
     with ipm.Solver(tol_kkt=1e-8, precond="jacobi_lr") as s:
