@@ -62,6 +62,13 @@ enum ipm_mem_space { IPM_MEM_HOST = 0, IPM_MEM_DEVICE = 1 };
 enum ipm_precond { IPM_PRECOND_JACOBI = 0, IPM_PRECOND_JACOBI_LR = 1, IPM_PRECOND_DENSE = 2,
                    IPM_PRECOND_AUTO = 3 };
 
+/* Storage of the matrix values inside PCG.  F64 (default): the FP64 operator throughout.
+ * F32 / BF16 / FP8_E4M3: a second copy of the values of R = [F; A] and R^T in that type with
+ * one FP32 scale per row, an FP32-accumulating operator inside PCG, and FP64 iterative
+ * refinement of every Newton step against the FP64 operator (residuals and reductions stay
+ * FP64).  Not part of the paper, which is FP64 throughout. */
+enum ipm_storage { IPM_STORAGE_F64 = 0, IPM_STORAGE_F32 = 1, IPM_STORAGE_BF16 = 2, IPM_STORAGE_FP8_E4M3 = 3 };
+
 /* ipm_solve flags. */
 enum ipm_solve_flags { IPM_COLD = 0, IPM_WARM = 1 };
 
@@ -88,6 +95,10 @@ typedef struct ipm_options {
   int use_graphs;        /* 1: one CUDA graph per IPM iteration with PCG as a conditional-while */
                          /* node (default); 0: the same kernels launched one by one with a host */
                          /* loop over PCG iterations (for per-kernel profilers)                */
+  int storage;           /* enum ipm_storage (default IPM_STORAGE_F64)                          */
+  int refine_max;        /* reduced precision: at most this many refinement passes per step (8) */
+  double refine_eta;     /* reduced precision: inner PCG tolerance relative to the current      */
+                         /* FP64 residual (0.1)                                                */
 } ipm_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -135,6 +146,8 @@ typedef struct ipm_info {
   int64_t kernel_launches;   /* kernels of this library launched by the last ipm_solve     */
   int lanes_rows;            /* lanes per row of the kernels over R and over R^T (chosen   */
   int lanes_cols;            /* by the autotuner at ipm_set_qp)                            */
+  int64_t refine_passes;     /* FP64 refinement passes summed over the Newton steps        */
+  int64_t fallback_steps;    /* Newton steps finished by FP64 PCG after refinement stalled */
 } ipm_info;
 
 /* Per-step result of ipm_newton_direction. */
@@ -216,10 +229,10 @@ int ipm_step_lengths(ipm_handle* h, const double* dx, const double* ds, const do
 
 /* Per-iteration trace of the last ipm_solve (metrics only): row k holds
  *   {k+1, mu, rel_kkt, primal, dual, gap, alpha_p, alpha_d, pcg_iters, pcg_converged,
- *    stiff_rows, pcg_rel_residual, eta}  (IPM_TRACE_COLS doubles).
+ *    stiff_rows, pcg_rel_residual, eta, refine_passes}  (IPM_TRACE_COLS doubles).
  * Copies at most max_rows rows into buf (host memory) and returns the number of rows the last
  * solve recorded (so buf == NULL queries the count). */
-#define IPM_TRACE_COLS 13
+#define IPM_TRACE_COLS 14
 int ipm_get_trace(const ipm_handle* h, double* buf, int max_rows);
 
 /* Measurement hook for the PCG operator (Section 4.1.1's matvec, the loop that Section 5.1.2

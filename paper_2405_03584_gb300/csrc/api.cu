@@ -31,7 +31,9 @@ struct Graphs {
   cudaGraphExec_t iter = nullptr;   // one full IPM iteration
   cudaGraphExec_t dir = nullptr;    // Newton direction only (PCG + recovery)
   int iter_kernels = 0, iter_body_kernels = 0;   // kernel nodes outside / inside the PCG loop
-  int dir_kernels = 0, dir_body_kernels = 0;
+  int iter_outer_kernels = 0;                      // inside the refinement loop, outside PCG
+  int iter_fb_kernels = 0;                         // one trip of the FP64 fallback loop
+  int dir_kernels = 0, dir_body_kernels = 0, dir_outer_kernels = 0, dir_fb_kernels = 0;
 };
 
 // Kernel nodes of a graph (not descending into child graphs).
@@ -53,7 +55,7 @@ int count_kernel_nodes(cudaGraph_t g) {
 struct ipm_handle {
   ipm_options opt;
   int device = 0;
-  cudaStream_t st = nullptr, st2 = nullptr;
+  cudaStream_t st = nullptr, st2 = nullptr, st3 = nullptr;
   cudaEvent_t ev = nullptr;
   void* arena = nullptr;
   size_t arena_bytes = 0;
@@ -139,7 +141,7 @@ struct HostQP {
   std::vector<unsigned char> fl, fu;
 };
 
-void carve(Carver& cv, Dev& d, const HostQP& q, int stiff_cap, int64_t sc_cap, bool dense) {
+void carve(Carver& cv, Dev& d, const HostQP& q, int stiff_cap, int64_t sc_cap, bool dense, int storage) {
   d.n = q.n; d.m = q.m; d.nR = q.nR;
   d.nnzR = (int64_t)q.Rv.size();
   d.nnzHs = (int64_t)q.Hv.size();
@@ -170,9 +172,24 @@ void carve(Carver& cv, Dev& d, const HostQP& q, int stiff_cap, int64_t sc_cap, b
   d.sc_slot = cv.take<int32_t>(sc_cap); d.sc_val = cv.take<double>(sc_cap); d.sc_cap = sc_cap;
   d.G = cv.take<double>((int64_t)stiff_cap * stiff_cap); d.Ginv = cv.take<double>((int64_t)stiff_cap * stiff_cap);
   d.us = cv.take<double>(stiff_cap); d.ts = cv.take<double>(stiff_cap); d.stiff_cap = stiff_cap;
+  d.us2 = cv.take<double>(stiff_cap);
   d.hist = cv.take<unsigned int>(kHistBins);
   if (dense) { d.Kd = cv.take<double>(n * n); d.Kinv = cv.take<double>(n * n); } else { d.Kd = d.Kinv = nullptr; }
   d.chol_diag = cv.take<double>(std::max<int64_t>(dense ? n : 0, stiff_cap));
+  d.storage = storage;
+  if (storage != ST_F64) {
+    const size_t vb = storage == ST_F32 ? 4 : (storage == ST_BF16 ? 2 : 1);
+    d.Rq = cv.take<unsigned char>((int64_t)vb * d.nnzR);
+    d.RTq = cv.take<unsigned char>((int64_t)vb * d.nnzR);
+    d.scaleR = cv.take<float>(nR);
+    d.p32 = cv.take<float>(n);
+    d.w32 = cv.take<float>(nR);
+    d.dxr = cv.take<double>(n);
+  } else {
+    d.Rq = d.RTq = nullptr;
+    d.scaleR = d.p32 = d.w32 = nullptr;
+    d.dxr = nullptr;
+  }
   d.partials = cv.take<double>(32 * (int64_t)kMaxRedBlocks);
   d.sc = cv.take<Scal>(1);
 }
@@ -182,6 +199,7 @@ int validate_options(const ipm_options& o) {
   if (!(o.cg_eta_min > 0) || !(o.cg_eta_max >= o.cg_eta_min) || !(o.cg_eta_factor > 0)) return IPM_ERR_ARG;
   if (o.precond < 0 || o.precond > 3 || o.stiff_max < 0 || o.stiff_max > 1024) return IPM_ERR_ARG;
   if (o.dense_max_n < 0 || o.dense_max_n > 2048 || !(o.stiff_gamma > 0)) return IPM_ERR_ARG;
+  if (o.storage < 0 || o.storage > 3 || o.refine_max < 1 || !(o.refine_eta > 0 && o.refine_eta < 1)) return IPM_ERR_ARG;
   return IPM_OK;
 }
 
@@ -272,11 +290,72 @@ int autotune_groups(ipm_handle* h) {
   return IPM_OK;
 }
 
-// Captures one IPM iteration (full=true) or one Newton direction (full=false).
-int build_graph(ipm_handle* h, int pc, bool full, cudaGraphExec_t* out, int* top_kernels, int* body_kernels) {
+// Adds a conditional while node at the current capture point of `st` (default condition 1,
+// reset at every graph launch) and captures its body on `body_st` with fill(handle, body_st).
+// A handle created here is reset to 1 at every launch of the top-level graph only; a loop
+// nested in another loop's body must have its condition set by a kernel before each entry
+// (pass that handle in `pre`, created with new_handle()).
+cudaError_t new_handle(cudaStream_t st, cudaGraphConditionalHandle* ch) {
+  cudaStreamCaptureStatus cs;
+  unsigned long long cid;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edata = nullptr;
+  size_t ndeps = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, &cid, &cg, &deps, &edata, &ndeps);
+  if (e != cudaSuccess) return e;
+  return cudaGraphConditionalHandleCreate(ch, cg, 1u, cudaGraphCondAssignDefault);
+}
+
+template <typename Fill>
+cudaError_t add_while(cudaStream_t st, cudaStream_t body_st, Fill fill, int* body_kernels,
+                      const cudaGraphConditionalHandle* pre = nullptr) {
+  cudaStreamCaptureStatus cs;
+  unsigned long long cid;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edata = nullptr;
+  size_t ndeps = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, &cid, &cg, &deps, &edata, &ndeps);
+  if (e != cudaSuccess) return e;
+  std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
+  cudaGraphConditionalHandle ch = 0;
+  if (pre) {
+    ch = *pre;
+  } else {
+    e = cudaGraphConditionalHandleCreate(&ch, cg, 1u, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return e;
+  }
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = ch;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode = nullptr;
+  e = cudaGraphAddNode(&cnode, cg, dv.data(), nullptr, dv.size(), &cp);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamUpdateCaptureDependencies(st, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(body_st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t ef = fill(ch, body_st);
+  cudaGraph_t bodyo = nullptr;
+  e = cudaStreamEndCapture(body_st, &bodyo);
+  if (ef != cudaSuccess) return ef;
+  if (e != cudaSuccess) return e;
+  if (body_kernels) *body_kernels = count_kernel_nodes(body);
+  return cudaSuccess;
+}
+
+// Captures one IPM iteration (full=true) or one Newton direction (full=false).  With a
+// reduced-precision store the PCG loop sits inside an FP64 refinement loop (nested while).
+int build_graph(ipm_handle* h, int pc, bool full, cudaGraphExec_t* out, int* top_kernels, int* body_kernels,
+                int* outer_kernels, int* fallback_kernels) {
   const Dev& d = h->d;
   const Geo& g = h->g;
   cudaStream_t st = h->st;
+  const bool lowp = d.storage != ST_F64;
   CUDA_TRY(h, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t x) { if (e == cudaSuccess && x != cudaSuccess) e = x; };
@@ -284,37 +363,37 @@ int build_graph(ipm_handle* h, int pc, bool full, cudaGraphExec_t* out, int* top
   chk(launch_precond_build(d, g, pc, st));
   chk(launch_rhs(d, g, pc, st));
   chk(launch_precond_finish(d, g, pc, st));
-  chk(launch_cg_init(d, g, pc, st));
-  // PCG loop: a conditional while node whose body is one PCG iteration
-  cudaStreamCaptureStatus cs;
-  unsigned long long cid;
-  cudaGraph_t cg = nullptr;
-  const cudaGraphNode_t* deps = nullptr;
-  const cudaGraphEdgeData* edata = nullptr;
-  size_t ndeps = 0;
-  if (e == cudaSuccess) chk(cudaStreamGetCaptureInfo(st, &cs, &cid, &cg, &deps, &edata, &ndeps));
-  cudaGraphNode_t cnode = nullptr;
-  cudaGraphConditionalHandle ch = 0;
-  if (e == cudaSuccess) {
-    std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
-    chk(cudaGraphConditionalHandleCreate(&ch, cg, 1u, cudaGraphCondAssignDefault));
-    cudaGraphNodeParams cp{};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = ch;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    if (e == cudaSuccess) chk(cudaGraphAddNode(&cnode, cg, dv.data(), nullptr, dv.size(), &cp));
-    if (e == cudaSuccess) chk(cudaStreamUpdateCaptureDependencies(st, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
-    if (e == cudaSuccess) {
-      cudaGraph_t body = cp.conditional.phGraph_out[0];
-      chk(cudaStreamBeginCaptureToGraph(h->st2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-      if (e == cudaSuccess) {
-        chk(launch_cg_body(d, g, pc, ch, h->st2));
-        cudaGraph_t bodyo = nullptr;
-        chk(cudaStreamEndCapture(h->st2, &bodyo));
-        if (e == cudaSuccess) *body_kernels = count_kernel_nodes(body);
-      }
-    }
+  *outer_kernels = 0;
+  *fallback_kernels = 0;
+  if (!lowp) {
+    chk(launch_cg_init(d, g, pc, st));
+    if (e == cudaSuccess)
+      chk(add_while(st, h->st2, [&](cudaGraphConditionalHandle ch, cudaStream_t bs) {
+            return launch_cg_body(d, g, pc, ch, bs, true, false);
+          }, body_kernels));
+  } else {
+    chk(launch_refine_start(d, g, st));
+    if (e == cudaSuccess)
+      chk(add_while(st, h->st2, [&](cudaGraphConditionalHandle ho, cudaStream_t bs) {
+            cudaGraphConditionalHandle hi = 0;
+            cudaError_t x = new_handle(bs, &hi);
+            if (x == cudaSuccess) x = launch_refine_inner(d, g, hi, bs);
+            if (x == cudaSuccess) x = launch_cg_init(d, g, pc, bs);
+            if (x == cudaSuccess)
+              x = add_while(bs, h->st3, [&](cudaGraphConditionalHandle hin, cudaStream_t bs2) {
+                    return launch_cg_body(d, g, pc, hin, bs2, true, true);
+                  }, body_kernels, &hi);
+            if (x == cudaSuccess) x = launch_refine_tail(d, g, ho, bs);
+            return x;
+          }, outer_kernels));
+    // FP64 fallback for a step the refinement could not finish (exits at once otherwise)
+    chk(launch_refine_fallback(d, g, st));
+    chk(launch_cg_init(d, g, pc, st));
+    if (e == cudaSuccess)
+      chk(add_while(st, h->st2, [&](cudaGraphConditionalHandle ch, cudaStream_t bs) {
+            return launch_cg_body(d, g, pc, ch, bs, true, false);
+          }, fallback_kernels));
+    chk(launch_refine_finish(d, g, st));
   }
   chk(launch_recover(d, g, st));
   if (full) {
@@ -337,25 +416,48 @@ int build_graph(ipm_handle* h, int pc, bool full, cudaGraphExec_t* out, int* top
 }
 
 // One IPM iteration with every kernel launched directly (use_graphs = 0): the same sequence
-// as the captured graph, with the PCG loop driven from the host (one scalar read per PCG
-// iteration).  Adds the kernels it launched to *launches.
+// as the captured graph, with the loops driven from the host (one scalar read per trip).
+// Adds the kernels it launched to *launches.
 int run_iteration_direct(ipm_handle* h, int pc, int64_t* launches) {
   const Dev& d = h->d;
   const Geo& g = h->g;
   cudaStream_t st = h->st;
+  const Graphs& gr = h->graphs[pc];
+  auto pcg = [&](bool lowp) -> int {
+    int done = 0;
+    for (int k = 0; k < h->opt.max_cg + 1 && !done; ++k) {
+      CUDA_TRY(h, launch_cg_body(d, g, pc, 0, st, false, lowp));
+      CUDA_TRY(h, cudaMemcpyAsync(&h->hs->cg_done, &d.sc->cg_done, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(h, cudaStreamSynchronize(st));
+      done = h->hs->cg_done;
+      *launches += gr.iter_body_kernels;
+    }
+    return IPM_OK;
+  };
   CUDA_TRY(h, launch_diag_update(d, g, st));
   CUDA_TRY(h, launch_precond_build(d, g, pc, st));
   CUDA_TRY(h, launch_rhs(d, g, pc, st));
   CUDA_TRY(h, launch_precond_finish(d, g, pc, st));
-  CUDA_TRY(h, launch_cg_init(d, g, pc, st));
-  const Graphs& gr = h->graphs[pc];
-  int done = 0;
-  for (int k = 0; k < h->opt.max_cg + 1 && !done; ++k) {
-    CUDA_TRY(h, launch_cg_body(d, g, pc, 0, st, false));
-    CUDA_TRY(h, cudaMemcpyAsync(&h->hs->cg_done, &d.sc->cg_done, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(h, cudaStreamSynchronize(st));
-    done = h->hs->cg_done;
-    *launches += gr.iter_body_kernels;
+  int rc;
+  if (d.storage == ST_F64) {
+    CUDA_TRY(h, launch_cg_init(d, g, pc, st));
+    if ((rc = pcg(false))) return rc;
+  } else {
+    CUDA_TRY(h, launch_refine_start(d, g, st));
+    for (int it = 0; it < h->opt.refine_max; ++it) {
+      CUDA_TRY(h, launch_refine_inner(d, g, 0, st));
+      CUDA_TRY(h, launch_cg_init(d, g, pc, st));
+      if ((rc = pcg(true))) return rc;
+      CUDA_TRY(h, launch_refine_tail(d, g, 0, st));
+      *launches += gr.iter_outer_kernels;
+      CUDA_TRY(h, cudaMemcpyAsync(h->hs, d.sc, sizeof(Scal), cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(h, cudaStreamSynchronize(st));
+      if (h->hs->cg_conv_outer || !std::isfinite(h->hs->rr_outer)) break;
+    }
+    CUDA_TRY(h, launch_refine_fallback(d, g, st));
+    CUDA_TRY(h, launch_cg_init(d, g, pc, st));
+    if ((rc = pcg(false))) return rc;
+    CUDA_TRY(h, launch_refine_finish(d, g, st));
   }
   CUDA_TRY(h, launch_recover(d, g, st));
   CUDA_TRY(h, launch_ratio(d, g, st));
@@ -370,8 +472,10 @@ int ensure_graph(ipm_handle* h, int pc, bool full, cudaGraphExec_t** gx) {
   Graphs& gr = h->graphs[pc];
   cudaGraphExec_t* slot = full ? &gr.iter : &gr.dir;
   if (!*slot) {
-    int rc = full ? build_graph(h, pc, full, slot, &gr.iter_kernels, &gr.iter_body_kernels)
-                  : build_graph(h, pc, full, slot, &gr.dir_kernels, &gr.dir_body_kernels);
+    int rc = full ? build_graph(h, pc, full, slot, &gr.iter_kernels, &gr.iter_body_kernels, &gr.iter_outer_kernels,
+                                &gr.iter_fb_kernels)
+                  : build_graph(h, pc, full, slot, &gr.dir_kernels, &gr.dir_body_kernels, &gr.dir_outer_kernels,
+                                &gr.dir_fb_kernels);
     if (rc) return rc;
   }
   *gx = slot;
@@ -399,6 +503,8 @@ int push_options(ipm_handle* h) {
   s.stiff_gamma = h->opt.stiff_gamma;
   s.stiff_max = std::min(h->opt.stiff_max, h->d.stiff_cap);
   s.equal_steps = h->opt.equal_steps;
+  s.refine_max = h->opt.refine_max;
+  s.refine_eta = h->opt.refine_eta;
   s.cnorm = h->cnorm;
   s.bnorm = h->bnorm;
   s.ncomp = h->ncomp;
@@ -449,6 +555,9 @@ void ipm_default_options(ipm_options* o) {
   o->equal_steps = 0;
   o->autotune = 0;
   o->use_graphs = 1;
+  o->storage = IPM_STORAGE_F64;
+  o->refine_max = 8;
+  o->refine_eta = 0.1;
 }
 
 const char* ipm_status_str(int s) {
@@ -483,11 +592,13 @@ int ipm_create(const ipm_options* opt, ipm_handle** out) {
   if (cudaGetDevice(&h->device) != cudaSuccess ||
       cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->st3, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming) != cudaSuccess ||
       cudaMallocHost(&h->hs, sizeof(Scal)) != cudaSuccess) {
     cudaGetLastError();
     if (h->st) cudaStreamDestroy(h->st);
     if (h->st2) cudaStreamDestroy(h->st2);
+    if (h->st3) cudaStreamDestroy(h->st3);
     if (h->ev) cudaEventDestroy(h->ev);
     delete h;
     return IPM_ERR_CUDA;
@@ -505,6 +616,7 @@ int ipm_destroy(ipm_handle* h) {
   if (h->hs) cudaFreeHost(h->hs);
   if (h->st) cudaStreamDestroy(h->st);
   if (h->st2) cudaStreamDestroy(h->st2);
+  if (h->st3) cudaStreamDestroy(h->st3);
   if (h->ev) cudaEventDestroy(h->ev);
   delete h;
   return IPM_OK;
@@ -647,7 +759,7 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   free_arena(h);
   Dev dv{};
   Carver cnt(nullptr);
-  carve(cnt, dv, q, stiff_cap, sc_cap, dense);
+  carve(cnt, dv, q, stiff_cap, sc_cap, dense, h->opt.storage);
   const size_t bytes = cnt.off + 256;
   if (h->opt.mem_budget > 0 && (double)bytes > h->opt.mem_budget)
     return fail(h, IPM_ERR_OOM, "QP needs " + std::to_string(bytes) + " bytes, over mem_budget");
@@ -658,7 +770,7 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   }
   h->arena_bytes = bytes;
   Carver cv((char*)h->arena);
-  carve(cv, dv, q, stiff_cap, sc_cap, dense);
+  carve(cv, dv, q, stiff_cap, sc_cap, dense, h->opt.storage);
   dv.g_rows = heuristic_group(q.nR ? (double)q.Rv.size() / (double)q.nR : 0.0);
   dv.g_cols = heuristic_group((double)q.Rv.size() / (double)n);
   h->d = dv;
@@ -699,6 +811,7 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   h->hs->status = DS_RUNNING;
   CUDA_TRY(h, cudaMemcpyAsync(d.sc, h->hs, sizeof(Scal), cudaMemcpyHostToDevice, h->st));
   CUDA_TRY(h, launch_diagH(d, h->st));
+  CUDA_TRY(h, launch_quantize(d, h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));   // host staging buffers go out of scope
   if (h->opt.autotune && (rc = autotune_groups(h))) return rc;
   h->loaded = true;
@@ -742,9 +855,14 @@ int ipm_solve(ipm_handle* h, void* stream, int flags) {
   if (!h->opt.use_graphs) gx = nullptr;
   int64_t cg_total = 0, launches = (flags & IPM_WARM) && h->have_iterate ? 4 : 13;
   int cg_max_step = 0;
+  int64_t refine_total = 0;
   int status = IPM_MAX_ITER;
   const Graphs& grs = h->graphs[pc];
   h->trace.clear();
+  if (h->d.storage != ST_F64) {
+    int zero = 0;
+    CUDA_TRY(h, cudaMemcpyAsync(&h->d.sc->fallback_total, &zero, sizeof(int), cudaMemcpyHostToDevice, h->st));
+  }
   for (int it = 0; it < h->opt.max_ipm; ++it) {
     if (gx) {
       CUDA_TRY(h, cudaGraphLaunch(*gx, h->st));
@@ -772,11 +890,14 @@ int ipm_solve(ipm_handle* h, void* stream, int flags) {
     const Scal& s = *h->hs;
     cg_total += s.cg_iter;
     cg_max_step = std::max(cg_max_step, s.cg_iter);
-    if (gx) launches += grs.iter_kernels + (int64_t)std::max(1, s.cg_iter) * grs.iter_body_kernels;
+    if (gx) launches += grs.iter_kernels + (int64_t)std::max(1, s.cg_iter) * grs.iter_body_kernels +
+                        (int64_t)s.refine_it * grs.iter_outer_kernels + (h->d.storage != ST_F64 ? grs.iter_fb_kernels : 0);
+    refine_total += h->d.storage != ST_F64 ? s.refine_it : 0;
     const double row[IPM_TRACE_COLS] = {(double)s.ipm_iter, s.mu, s.rel_kkt, s.res_primal, s.res_dual, s.res_gap,
                                         s.alpha_p, s.alpha_d, (double)s.cg_iter, (double)s.cg_conv,
                                         (double)(pc == PC_JACOBI_LR ? s.n_stiff : 0),
-                                        s.rhs2 > 0 ? std::sqrt(s.rr / s.rhs2) : 0.0, s.eta_used};
+                                        s.rhs2 > 0 ? std::sqrt(s.rr / s.rhs2) : 0.0, s.eta_used,
+                                        (double)(h->d.storage != ST_F64 ? s.refine_it : 0)};
     h->trace.insert(h->trace.end(), row, row + IPM_TRACE_COLS);
     if (s.stop) {
       status = s.status == DS_OK ? IPM_OK : s.status == DS_MAX_ITER ? IPM_MAX_ITER
@@ -803,6 +924,8 @@ int ipm_solve(ipm_handle* h, void* stream, int flags) {
   in.kernel_launches = launches;
   in.lanes_rows = h->d.g_rows;
   in.lanes_cols = h->d.g_cols;
+  in.refine_passes = refine_total;
+  in.fallback_steps = h->d.storage != ST_F64 ? s.fallback_total : 0;
   if ((rc = leave(h, stream))) return rc;
   return status;
 }

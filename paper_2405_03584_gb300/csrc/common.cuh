@@ -35,6 +35,9 @@ struct Scal {
   // preconditioner
   double stiff_gamma, stiff_thresh;
   int n_stiff, stiff_max, max_stiff_seen, chol_fail;
+  // FP64 refinement of a reduced-precision Newton step
+  double tol2_outer, rr_outer, refine_eta;
+  int refine_it, refine_max, cg_step_total, cg_conv_outer, fallback, fallback_total;
   // step
   double alpha_p, alpha_d;
   // residual summary at the current iterate (written by k_resid_final)
@@ -45,7 +48,10 @@ struct Scal {
   unsigned int ticket[8];
 };
 
-enum ScalTicket { T_PQ = 0, T_UPD = 1, T_CORR = 2, T_INIT = 3, T_HIST = 4, T_STEP = 5, T_MISC = 6 };
+enum ScalTicket { T_PQ = 0, T_UPD = 1, T_CORR = 2, T_INIT = 3, T_HIST = 4, T_STEP = 5, T_MISC = 6, T_REF = 7 };
+
+// Storage of the matrix values used inside PCG (mirrors enum ipm_storage).
+enum Storage { ST_F64 = 0, ST_F32 = 1, ST_BF16 = 2, ST_FP8 = 3 };
 
 // Status values written by the device (mirror enum ipm_status).
 enum DevStatus { DS_RUNNING = -1, DS_OK = 0, DS_MAX_ITER = 3, DS_CG_STALL = 4, DS_NUMERICAL = 5 };

@@ -901,7 +901,11 @@ __global__ void k_stiff_corr(Dev d, int init) {
       zj -= d.Minv[j] * acc;
       d.z[j] = zj;
     }
-    if (init) d.p[j] = zj;
+    if (init) {
+      d.p[j] = zj;
+    if (d.p32) d.p32[j] = (float)zj;
+      if (d.p32) d.p32[j] = (float)zj;
+    }
     rz = fma(d.r[j], zj, rz);
   }
   double v[1] = {rz};
@@ -933,7 +937,10 @@ __global__ void k_dense_apply(Dev d, int init) {
     acc = warp_sum(acc);
     if (lane == 0) {
       d.z[j] = acc;
-      if (init) d.p[j] = acc;
+      if (init) {
+        d.p[j] = acc;
+        if (d.p32) d.p32[j] = (float)acc;
+      }
       rz = fma(d.r[j], acc, rz);
     }
   }
@@ -978,7 +985,11 @@ __global__ void k_cg_p(Dev d, cudaGraphConditionalHandle h, int set_cond) {
   if (done) return;
   const double beta = d.sc->beta;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x)
-    d.p[j] = fma(beta, d.p[j], d.z[j]);
+  {
+    const double pj = fma(beta, d.p[j], d.z[j]);
+    d.p[j] = pj;
+    if (d.p32) d.p32[j] = (float)pj;
+  }
 }
 
 cudaError_t launch_cg_init(const Dev& d, const Geo& g, int precond, cudaStream_t st) {
@@ -997,9 +1008,14 @@ cudaError_t launch_cg_init(const Dev& d, const Geo& g, int precond, cudaStream_t
 }
 
 cudaError_t launch_cg_body(const Dev& d, const Geo& g, int precond, cudaGraphConditionalHandle h, cudaStream_t st,
-                           bool in_graph) {
-  if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<0, G><<<g.gR, kBlock, 0, st>>>(d));
-  DISPATCH_G(d.g_cols, k_op_cols<0, G><<<g.gN, kBlock, 0, st>>>(d));
+                           bool in_graph, bool lowp) {
+  if (lowp) {
+    cudaError_t e = launch_op_lp(d, g, st);
+    if (e != cudaSuccess) return e;
+  } else {
+    if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<0, G><<<g.gR, kBlock, 0, st>>>(d));
+    DISPATCH_G(d.g_cols, k_op_cols<0, G><<<g.gN, kBlock, 0, st>>>(d));
+  }
   if (precond == PC_DENSE) {
     k_cg_update<2><<<g.eN, kBlock, 0, st>>>(d);
     k_dense_apply<<<g.gN, kBlock, 0, st>>>(d, 0);

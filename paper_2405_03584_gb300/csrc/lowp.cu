@@ -1,0 +1,340 @@
+// Reduced-precision operator and FP64 iterative refinement of the Newton step.
+//
+// The matrix values of R and R^T are stored a second time in FP32, BF16 or FP8-E4M3 with one
+// FP32 scale per row of R (R~_ij = s_i q_ij, q_ij = round(R_ij / s_i)); the int32 index arrays
+// are shared with the FP64 copy.  Inside PCG the operator
+//     K~ p = R~^T (omega o (R~ p)) + Hs p + (h0 + sigma) o p
+// reads the narrow values and an FP32 mirror of p and accumulates in FP32 (the fast pipe);
+// K~ is exactly symmetric, so CG stays valid.  The Newton step keeps FP64 accuracy by
+// refinement: dx <- dx + K~^{-1}(rhs - K dx) with the residual formed by the FP64 operator,
+// until ||rhs - K dx|| <= eta ||rhs||.  Residuals, the refinement residual and every reduction
+// stay in FP64.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "state.h"
+
+namespace ipmk {
+
+static __device__ __forceinline__ int gwarp_l() { return (blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
+static __device__ __forceinline__ int nwarps_l() { return (gridDim.x * blockDim.x) >> 5; }
+
+template <int S> struct StorageT;
+template <> struct StorageT<ST_F32> {
+  using T = float;
+  static constexpr float qmax = 1.0f;
+  static __device__ __forceinline__ float dec(T v) { return v; }
+  static __device__ __forceinline__ T enc(float v) { return v; }
+};
+template <> struct StorageT<ST_BF16> {
+  using T = __nv_bfloat16;
+  static constexpr float qmax = 1.0f;
+  static __device__ __forceinline__ float dec(T v) { return __bfloat162float(v); }
+  static __device__ __forceinline__ T enc(float v) { return __float2bfloat16_rn(v); }
+};
+template <> struct StorageT<ST_FP8> {
+  using T = __nv_fp8_e4m3;
+  static constexpr float qmax = 448.0f;
+  static __device__ __forceinline__ float dec(T v) { return static_cast<float>(v); }
+  static __device__ __forceinline__ T enc(float v) { return T(v); }
+};
+
+// Per-row scale s_i = max_j |R_ij| / qmax (1 for an empty or zero row).
+template <int S>
+__global__ void k_quant_scale(Dev d) {
+  for (int64_t r = gwarp_l(); r < d.nR; r += nwarps_l()) {
+    double mx = 0.0;
+    for (int64_t e = d.R_ptr[r] + (threadIdx.x & 31); e < d.R_ptr[r + 1]; e += 32) mx = fmax(mx, fabs(d.R_val[e]));
+    mx = warp_max(mx);
+    if ((threadIdx.x & 31) == 0) d.scaleR[r] = mx > 0.0 ? (float)(mx / (double)StorageT<S>::qmax) : 1.0f;
+  }
+}
+
+template <int S>
+__global__ void k_quant_rows(Dev d) {
+  using T = typename StorageT<S>::T;
+  T* q = static_cast<T*>(d.Rq);
+  for (int64_t r = gwarp_l(); r < d.nR; r += nwarps_l()) {
+    const double s = (double)d.scaleR[r];
+    for (int64_t e = d.R_ptr[r] + (threadIdx.x & 31); e < d.R_ptr[r + 1]; e += 32)
+      q[e] = StorageT<S>::enc((float)(d.R_val[e] / s));
+  }
+}
+
+template <int S>
+__global__ void k_quant_rt(Dev d) {
+  using T = typename StorageT<S>::T;
+  T* q = static_cast<T*>(d.RTq);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < d.nnzR; e += (int64_t)gridDim.x * blockDim.x)
+    q[e] = StorageT<S>::enc((float)(d.RT_val[e] / (double)d.scaleR[d.RT_idx[e]]));
+}
+
+cudaError_t launch_quantize(const Dev& d, cudaStream_t st) {
+  if (d.storage == ST_F64 || d.nR == 0) return cudaSuccess;
+  const int gb = (int)std::min<int64_t>((d.nR + 7) / 8, 4096);
+  const int ge = (int)std::min<int64_t>((d.nnzR + 255) / 256, 8192);
+  switch (d.storage) {
+    case ST_F32: k_quant_scale<ST_F32><<<gb, 256, 0, st>>>(d); k_quant_rows<ST_F32><<<gb, 256, 0, st>>>(d); k_quant_rt<ST_F32><<<ge, 256, 0, st>>>(d); break;
+    case ST_BF16: k_quant_scale<ST_BF16><<<gb, 256, 0, st>>>(d); k_quant_rows<ST_BF16><<<gb, 256, 0, st>>>(d); k_quant_rt<ST_BF16><<<ge, 256, 0, st>>>(d); break;
+    default: k_quant_scale<ST_FP8><<<gb, 256, 0, st>>>(d); k_quant_rows<ST_FP8><<<gb, 256, 0, st>>>(d); k_quant_rt<ST_FP8><<<ge, 256, 0, st>>>(d); break;
+  }
+  return cudaGetLastError();
+}
+
+// FP32 dot of a stored row with an FP32 vector by a group of G lanes (four accumulators).
+template <int S, int G>
+__device__ __forceinline__ float group_row_dot_lp(const int64_t beg, const int64_t end, const int gl,
+                                                  const int32_t* __restrict__ idx,
+                                                  const typename StorageT<S>::T* __restrict__ val,
+                                                  const float* __restrict__ x) {
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+  int64_t e = beg + gl;
+  for (; e + 3 * G < end; e += 4 * G) {
+    const float v0 = StorageT<S>::dec(val[e]), v1 = StorageT<S>::dec(val[e + G]);
+    const float v2 = StorageT<S>::dec(val[e + 2 * G]), v3 = StorageT<S>::dec(val[e + 3 * G]);
+    const int i0 = __ldg(idx + e), i1 = __ldg(idx + e + G), i2 = __ldg(idx + e + 2 * G), i3 = __ldg(idx + e + 3 * G);
+    a0 = fmaf(v0, __ldg(x + i0), a0);
+    a1 = fmaf(v1, __ldg(x + i1), a1);
+    a2 = fmaf(v2, __ldg(x + i2), a2);
+    a3 = fmaf(v3, __ldg(x + i3), a3);
+  }
+  for (; e < end; e += G) a0 = fmaf(StorageT<S>::dec(val[e]), __ldg(x + __ldg(idx + e)), a0);
+  float s = (a0 + a1) + (a2 + a3);
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+#define FOR_GROUP_ROWS_L(G, r, ok, nrows)                                                                    \
+  for (int64_t r##_0 = (int64_t)gwarp_l() * (32 / G); r##_0 < (nrows); r##_0 += (int64_t)nwarps_l() * (32 / G)) \
+    for (int64_t r = r##_0 + (threadIdx.x & 31) / G, r##_once = 0; r##_once == 0; r##_once = 1)               \
+      for (bool ok = r < (nrows), ok##_once = true; ok##_once; ok##_once = false)
+
+// Exact FP64 part of the operator for the stiff rows (JACOBI_LR): u_a = theta_a (A_a . p).
+// Their narrow copy is left out of K~ (omega_lp = w_R + theta on moderate rows only), so the
+// rows whose theta dominates are never rounded: K~ = R~^T diag(w + theta_mod) R~ + A_s^T Theta_s A_s.
+__global__ void k_stiff_op_u(Dev d) {
+  if (d.sc->cg_done) return;
+  const int ns = d.sc->n_stiff;
+  for (int a = gwarp_l(); a < ns; a += nwarps_l()) {
+    const int32_t k = d.stiff_k[a];
+    const int32_t row = d.arow[k];
+    const double u = warp_row_dot<false>(d.R_ptr[row], d.R_ptr[row + 1], d.R_idx, d.R_val, d.p);
+    if ((threadIdx.x & 31) == 0) d.us2[a] = d.theta[k] * u;
+  }
+}
+
+// w_i = s_i^2 (w_R,i + thR_i) (q_i . p32)   (FP32 result; thR = theta on moderate rows)
+template <int S, int G>
+__global__ void k_op_rows_lp(Dev d) {
+  if (d.sc->cg_done) return;
+  using T = typename StorageT<S>::T;
+  const T* q = static_cast<const T*>(d.Rq);
+  const int gl = threadIdx.x & (G - 1);
+  FOR_GROUP_ROWS_L(G, r, ok, d.nR) {
+    const int64_t beg = ok ? d.R_ptr[r] : 0, end = ok ? d.R_ptr[r + 1] : 0;
+    const float t = group_row_dot_lp<S, G>(beg, end, gl, d.R_idx, q, d.p32);
+    if (ok && gl == 0) {
+      const double s = (double)d.scaleR[r];
+      d.w32[r] = (float)((d.wR[r] + d.thR[r]) * s * s * (double)t);
+    }
+  }
+}
+
+// q_j = sum_i q_ij w_i + Hs p + (h0 + sigma) p;  p^T q -> alpha (last block), as k_op_cols.
+template <int S, int G>
+__global__ void k_op_cols_lp(Dev d) {
+  __shared__ double sh[32];
+  if (d.sc->cg_done) return;
+  using T = typename StorageT<S>::T;
+  const T* q = static_cast<const T*>(d.RTq);
+  const int gl = threadIdx.x & (G - 1);
+  const bool stiff = d.sc->n_stiff > 0;
+  double pq = 0.0;
+  FOR_GROUP_ROWS_L(G, j, ok, d.n) {
+    const int64_t beg = ok ? d.RT_ptr[j] : 0, end = ok ? d.RT_ptr[j + 1] : 0;
+    const float acc = group_row_dot_lp<S, G>(beg, end, gl, d.RT_idx, q, d.w32);
+    double hs = 0.0;
+    if (d.Hs_ptr) {
+      const int64_t hb = ok ? d.Hs_ptr[j] : 0, he = ok ? d.Hs_ptr[j + 1] : 0;
+      hs = group_row_dot<G, false>(hb, he, gl, d.Hs_idx, d.Hs_val, d.p);
+    }
+    if (ok && gl == 0) {
+      const double pj = d.p[j];
+      double st = 0.0;
+      if (stiff)
+        for (int64_t t = d.sc_ptr[j]; t < d.sc_ptr[j + 1]; ++t) st = fma(d.sc_val[t], d.us2[d.sc_slot[t]], st);
+      const double qj = (double)acc + hs + st + (d.h0[j] + d.sigma[j]) * pj;
+      d.q[j] = qj;
+      pq = fma(pj, qj, pq);
+    }
+  }
+  double v[1] = {pq};
+  const int ops[1] = {0};
+  double out[1];
+  if (grid_reduce<1>(v, ops, d.partials + 16 * kMaxRedBlocks, &d.sc->ticket[T_PQ], out, sh)) {
+    if (threadIdx.x == 0) {
+      Scal* sc = d.sc;
+      const double pqv = out[0];
+      if (!(pqv > 0.0) || !isfinite(pqv)) {
+        sc->cg_done = 1;
+        if (!isfinite(pqv)) sc->status = DS_NUMERICAL;
+        sc->alpha = 0.0;
+      } else {
+        sc->alpha = sc->rz / pqv;
+      }
+      sc->pq = pqv;
+    }
+  }
+}
+
+#define DISPATCH_SG(s, g, ...)                                                                   \
+  do {                                                                                           \
+    if ((s) == ST_F32) { constexpr int S = ST_F32; DISPATCH_GL(g, __VA_ARGS__); }                \
+    else if ((s) == ST_BF16) { constexpr int S = ST_BF16; DISPATCH_GL(g, __VA_ARGS__); }         \
+    else { constexpr int S = ST_FP8; DISPATCH_GL(g, __VA_ARGS__); }                              \
+  } while (0)
+#define DISPATCH_GL(g, ...)                                   \
+  switch (g) {                                                \
+    case 4: { constexpr int G = 4; __VA_ARGS__; } break;      \
+    case 8: { constexpr int G = 8; __VA_ARGS__; } break;      \
+    case 16: { constexpr int G = 16; __VA_ARGS__; } break;    \
+    default: { constexpr int G = 32; __VA_ARGS__; } break;    \
+  }
+
+cudaError_t launch_op_lp(const Dev& d, const Geo& g, cudaStream_t st) {
+  k_stiff_op_u<<<(d.stiff_cap + 7) / 8, kBlock, 0, st>>>(d);
+  if (d.nR) DISPATCH_SG(d.storage, d.g_rows, k_op_rows_lp<S, G><<<g.gR, kBlock, 0, st>>>(d));
+  DISPATCH_SG(d.storage, d.g_cols, k_op_cols_lp<S, G><<<g.gN, kBlock, 0, st>>>(d));
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------- refinement
+
+// Start of a refined Newton step: dx_acc = 0; outer tolerance = the PCG tolerance of the step.
+__global__ void k_refine_start(Dev d) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x)
+    d.dxr[j] = 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    Scal* sc = d.sc;
+    sc->tol2_outer = sc->tol2;
+    sc->rr_outer = sc->rhs2;
+    sc->refine_it = 0;
+    sc->cg_step_total = 0;
+    sc->cg_conv_outer = sc->cg_done;   // rhs == 0: nothing to refine
+  }
+}
+
+// Inner solve setup: dx = 0; PCG tolerance relative to the current FP64 residual in r; the
+// inner loop's condition re-armed (a nested loop keeps its last value between outer trips).
+__global__ void k_refine_inner(Dev d, cudaGraphConditionalHandle hi, int set_cond) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x)
+    d.dx[j] = 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (set_cond) cudaGraphSetConditional(hi, 1u);
+    Scal* sc = d.sc;
+    sc->tol2 = sc->refine_eta * sc->refine_eta * sc->rr_outer;
+    sc->cg_iter = 0;
+    sc->cg_conv = 0;
+    sc->cg_done = (sc->rr_outer == 0.0) ? 1 : 0;
+  }
+}
+
+// dx_acc += dx; p = dx_acc (input of the FP64 operator apply that follows).
+__global__ void k_refine_acc(Dev d) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x) {
+    const double v = d.dxr[j] + d.dx[j];
+    d.dxr[j] = v;
+    d.p[j] = v;
+  }
+}
+
+// r = rhs - K dx_acc (q holds K dx_acc from the FP64 operator); ||r||^2; loop condition.
+__global__ void k_refine_resid(Dev d, cudaGraphConditionalHandle h, int set_cond) {
+  __shared__ double sh[32];
+  double rr = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x) {
+    const double rj = d.rhs[j] - d.q[j];
+    d.r[j] = rj;
+    rr = fma(rj, rj, rr);
+  }
+  double v[1] = {rr};
+  const int ops[1] = {0};
+  double out[1];
+  if (grid_reduce<1>(v, ops, d.partials + 27 * kMaxRedBlocks, &d.sc->ticket[T_REF], out, sh)) {
+    if (threadIdx.x == 0) {
+      Scal* sc = d.sc;
+      sc->refine_it += 1;
+      sc->cg_step_total += sc->cg_iter;
+      sc->rr_outer = out[0];
+      sc->rr = out[0];
+      const bool ok = isfinite(out[0]);
+      if (!ok) sc->status = DS_NUMERICAL;
+      sc->cg_conv_outer = ok && out[0] <= sc->tol2_outer;
+      const bool cont = ok && !sc->cg_conv_outer && sc->refine_it < sc->refine_max;
+      if (set_cond) cudaGraphSetConditional(h, cont ? 1u : 0u);
+    }
+  }
+}
+
+// Fallback when refinement did not reach the tolerance in refine_max passes: plain FP64 PCG
+// on the current residual (r = rhs - K dx_acc) to the step's absolute tolerance.  When the
+// refinement converged the loop that follows exits at once (cg_done = 1).
+__global__ void k_refine_fallback(Dev d) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x)
+    d.dx[j] = 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    Scal* sc = d.sc;
+    sc->tol2 = sc->tol2_outer;
+    sc->cg_iter = 0;
+    sc->cg_conv = 0;
+    sc->cg_done = (sc->cg_conv_outer || !isfinite(sc->rr_outer) || sc->rr_outer <= sc->tol2_outer) ? 1 : 0;
+    sc->fallback = sc->cg_done ? 0 : 1;
+  }
+}
+
+// End of a refined step: dx = dx_acc (+ the fallback's correction); totals in the PCG fields.
+__global__ void k_refine_finish(Dev d) {
+  const bool fb = d.sc->fallback;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x)
+    d.dx[j] = fb ? d.dxr[j] + d.dx[j] : d.dxr[j];
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    Scal* sc = d.sc;
+    if (fb) {
+      sc->cg_step_total += sc->cg_iter;
+      sc->fallback_total += 1;
+    } else {
+      sc->cg_conv = sc->cg_conv_outer;
+      sc->rr = sc->rr_outer;
+    }
+    sc->cg_iter = sc->cg_step_total;
+    sc->tol2 = sc->tol2_outer;
+  }
+}
+
+cudaError_t launch_refine_start(const Dev& d, const Geo& g, cudaStream_t st) {
+  k_refine_start<<<g.eN, kBlock, 0, st>>>(d);
+  return cudaGetLastError();
+}
+cudaError_t launch_refine_inner(const Dev& d, const Geo& g, cudaGraphConditionalHandle hi, cudaStream_t st) {
+  k_refine_inner<<<g.eN, kBlock, 0, st>>>(d, hi, hi != 0 ? 1 : 0);
+  return cudaGetLastError();
+}
+cudaError_t launch_refine_tail(const Dev& d, const Geo& g, cudaGraphConditionalHandle h, cudaStream_t st) {
+  k_refine_acc<<<g.eN, kBlock, 0, st>>>(d);
+  cudaError_t e = launch_apply(d, g, st);        // FP64 operator: q = K dx_acc
+  if (e != cudaSuccess) return e;
+  k_refine_resid<<<g.eN, kBlock, 0, st>>>(d, h, h != 0 ? 1 : 0);
+  return cudaGetLastError();
+}
+cudaError_t launch_refine_fallback(const Dev& d, const Geo& g, cudaStream_t st) {
+  k_refine_fallback<<<g.eN, kBlock, 0, st>>>(d);
+  return cudaGetLastError();
+}
+cudaError_t launch_refine_finish(const Dev& d, const Geo& g, cudaStream_t st) {
+  k_refine_finish<<<g.eN, kBlock, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+}  // namespace ipmk

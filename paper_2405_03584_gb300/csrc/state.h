@@ -39,11 +39,18 @@ struct Dev {
   int32_t* sc_slot; double* sc_val;  // sc_cap
   int64_t sc_cap;
   double *G, *Ginv, *us, *ts;  // stiff_cap^2, stiff_cap^2, stiff_cap, stiff_cap
+  double* us2;                 // stiff_cap: theta_a (A_a . p) for the exact stiff part of K~
   int stiff_cap;
   unsigned int* hist;          // kHistBins
   // dense preconditioner (n x n), nullptr if not allocated
   double *Kd, *Kinv;
   double* chol_diag;           // max(n_dense, stiff_cap): original diagonal during a factorisation
+  // reduced-precision copy of the matrix values (storage != ST_F64): R~_ij = scaleR_i * q_ij
+  int storage;
+  void *Rq, *RTq;              // nnzR values each (float / bf16 / fp8-e4m3), indices shared with R, R^T
+  float* scaleR;               // nR
+  float *p32, *w32;            // FP32 mirror of p (n) and the rows-pass result (nR)
+  double* dxr;                 // n: accumulated refined step
   // reductions and scalars
   double* partials;            // 32 * kMaxRedBlocks
   Scal* sc;
@@ -74,7 +81,15 @@ cudaError_t launch_precond_finish(const Dev& d, const Geo& g, int precond, cudaS
 cudaError_t launch_rhs(const Dev& d, const Geo& g, int precond, cudaStream_t st);  // + Jacobi diagonal
 cudaError_t launch_cg_init(const Dev& d, const Geo& g, int precond, cudaStream_t st);
 cudaError_t launch_cg_body(const Dev& d, const Geo& g, int precond, cudaGraphConditionalHandle h, cudaStream_t st,
-                           bool in_graph = true);
+                           bool in_graph = true, bool lowp = false);
+// ---- reduced-precision operator and FP64 refinement (lowp.cu) ----
+cudaError_t launch_quantize(const Dev& d, cudaStream_t st);
+cudaError_t launch_op_lp(const Dev& d, const Geo& g, cudaStream_t st);
+cudaError_t launch_refine_start(const Dev& d, const Geo& g, cudaStream_t st);
+cudaError_t launch_refine_inner(const Dev& d, const Geo& g, cudaGraphConditionalHandle hi, cudaStream_t st);
+cudaError_t launch_refine_tail(const Dev& d, const Geo& g, cudaGraphConditionalHandle h, cudaStream_t st);
+cudaError_t launch_refine_fallback(const Dev& d, const Geo& g, cudaStream_t st);
+cudaError_t launch_refine_finish(const Dev& d, const Geo& g, cudaStream_t st);
 // ---- direction recovery, ratio test, update ----
 cudaError_t launch_recover(const Dev& d, const Geo& g, cudaStream_t st);
 cudaError_t launch_ratio(const Dev& d, const Geo& g, cudaStream_t st);

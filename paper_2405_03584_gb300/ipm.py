@@ -23,6 +23,7 @@ IPM_OK, IPM_ERR_ARG, IPM_ERR_OOM, IPM_MAX_ITER, IPM_CG_STALL, IPM_NUMERICAL, \
 STATIC_SCRATCH_ROWS = 262144
 MEM_HOST, MEM_DEVICE = 0, 1
 PRECOND = {"jacobi": 0, "jacobi_lr": 1, "dense": 2, "auto": 3}
+STORAGE = {"f64": 0, "f32": 1, "bf16": 2, "fp8": 3, "fp8_e4m3": 3}
 COLD, WARM = 0, 1
 
 EXPORTS = ["ipm_default_options", "ipm_create", "ipm_set_qp", "ipm_solve", "ipm_get_xyz", "ipm_destroy",
@@ -30,7 +31,7 @@ EXPORTS = ["ipm_default_options", "ipm_create", "ipm_set_qp", "ipm_solve", "ipm_
            "ipm_precond_diag", "ipm_newton_direction", "ipm_step_lengths", "ipm_profile_operator",
            "ipm_get_trace", "ipm_apply_operator_static"]
 TRACE_COLS = ("iter", "mu", "rel_kkt", "primal", "dual", "gap", "alpha_p", "alpha_d", "pcg_iters", "pcg_converged",
-              "stiff_rows", "pcg_rel_residual", "eta")
+              "stiff_rows", "pcg_rel_residual", "eta", "refine_passes")
 
 
 class Options(C.Structure):
@@ -38,7 +39,8 @@ class Options(C.Structure):
                 ("cg_eta_max", C.c_double), ("cg_eta_min", C.c_double), ("cg_eta_factor", C.c_double),
                 ("precond", C.c_int), ("stiff_gamma", C.c_double), ("stiff_max", C.c_int),
                 ("dense_max_n", C.c_int), ("timeout_ms", C.c_double), ("mem_budget", C.c_double),
-                ("equal_steps", C.c_int), ("autotune", C.c_int), ("use_graphs", C.c_int)]
+                ("equal_steps", C.c_int), ("autotune", C.c_int), ("use_graphs", C.c_int),
+                ("storage", C.c_int), ("refine_max", C.c_int), ("refine_eta", C.c_double)]
 
 
 class QP(C.Structure):
@@ -54,7 +56,8 @@ class Info(C.Structure):
                 ("max_stiff_rows", C.c_int), ("precond", C.c_int), ("rel_kkt", C.c_double),
                 ("primal_res", C.c_double), ("dual_res", C.c_double), ("gap_res", C.c_double),
                 ("primal_obj", C.c_double), ("dual_obj", C.c_double), ("mu", C.c_double), ("solve_ms", C.c_double),
-                ("kernel_launches", C.c_int64), ("lanes_rows", C.c_int), ("lanes_cols", C.c_int)]
+                ("kernel_launches", C.c_int64), ("lanes_rows", C.c_int), ("lanes_cols", C.c_int),
+                ("refine_passes", C.c_int64), ("fallback_steps", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -169,6 +172,8 @@ class Solver:
         for k, v in opts.items():
             if k == "precond" and isinstance(v, str):
                 v = PRECOND[v]
+            if k == "storage" and isinstance(v, str):
+                v = STORAGE[v]
             if not hasattr(o, k):
                 raise TypeError("unknown option %s" % k)
             setattr(o, k, v)

@@ -265,3 +265,29 @@ def test_bad_inputs_rejected():
     with pytest.raises(ipm.IpmError):
         s.set_qp_rt(bad)
     s.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16", "fp8"])
+def test_reduced_precision_operator_refined_to_fp64(storage):
+    """D and A stored in FP32 / BF16 / FP8-E4M3 with per-row scales, FP32-accumulating PCG,
+    FP64 iterative refinement of each Newton step: the solve must still match the FP64
+    oracle at the spec bar (rel KKT <= tol, rel objective difference <= 1e-6)."""
+    p = W.rt_qp(n=1400, seed=19)
+    st, out, ref, qp = _solve_both(p, 1e-7, precond="jacobi_lr", storage=storage, max_cg=5000)
+    _check_solution(p, qp, st, out, ref, 1e-7)
+    assert out["info"]["refine_passes"] >= out["info"]["ipm_iters"]
+
+
+@pytest.mark.parametrize("storage", ["bf16", "fp8"])
+def test_reduced_precision_direction(storage):
+    """One refined Newton direction at a random iterate against the oracle's exact one."""
+    p = W.rt_qp(n=900, seed=21)
+    s, qp = _load(p, precond="jacobi_lr", storage=storage, max_cg=5000, refine_max=30)
+    it = _iterate(p, qp, 13, spread=1.0)
+    s.set_iterate(it.x, it.s, it.y, it.zl, it.zu, 0.05)
+    d = s.newton_direction(eta=1e-10)
+    ref = O.newton_direction(qp, it, 0.05)
+    assert d["report"]["converged"] == 1, d["report"]
+    err = np.abs(d["dx"] - ref.x).max() / np.abs(ref.x).max()
+    assert err <= 1e-6, err
+    s.close()
