@@ -192,7 +192,8 @@ def run_operator_only(args):
     torch.cuda.set_device(0)
     build.build()
     p = W.rt_qp(n=N_FULL, seed=SEED)
-    s = ipm.Solver(tol_kkt=TOL, precond="jacobi_lr", max_ipm=3, autotune=1)
+    lr, lc = (int(v) for v in args.lanes.split(","))
+    s = ipm.Solver(tol_kkt=TOL, precond="jacobi_lr", max_ipm=3, lanes_rows=lr, lanes_cols=lc)
     s.set_qp_rt(p)
     s.solve()
     out = s.profile_operator(reps=3)
@@ -339,6 +340,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--operator-only", action="store_true",
                     help="profiler capture target: a few IPM iterations, then the operator kernels")
+    ap.add_argument("--lanes", default="8,16", help="--operator-only: lanes per row over R and R^T")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every kernel directly (for per-kernel profilers; same kernels, slower)")
     args = ap.parse_args()

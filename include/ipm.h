@@ -47,7 +47,8 @@ enum ipm_status {
   IPM_ERR_TIMEOUT = 7,           /* host wall-clock limit options.timeout_ms exceeded           */
   IPM_ERR_CUDA = 8,              /* a CUDA runtime call failed (see ipm_last_error)             */
   IPM_ERR_STATE = 9,             /* call out of order (e.g. ipm_solve before ipm_set_qp)        */
-  IPM_ERR_TOO_LARGE = 10         /* size beyond the fixed scratch of ipm_apply_operator_static  */
+  IPM_ERR_TOO_LARGE = 10,        /* size beyond the fixed scratch of ipm_apply_operator_static  */
+  IPM_BUSY = 11                  /* ipm_solve_query: the solve is still running                 */
 };
 
 enum ipm_mem_space { IPM_MEM_HOST = 0, IPM_MEM_DEVICE = 1 };
@@ -99,6 +100,8 @@ typedef struct ipm_options {
   int refine_max;        /* reduced precision: at most this many refinement passes per step (8) */
   double refine_eta;     /* reduced precision: inner PCG tolerance relative to the current      */
                          /* FP64 residual (0.1)                                                */
+  int lanes_rows;        /* lanes per row of the kernels over R (4, 8, 16, 32; 0 = automatic)   */
+  int lanes_cols;        /* lanes per row of the kernels over R^T (same; overrides autotune)    */
 } ipm_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -176,6 +179,30 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream);
  * (IPM_WARM: the previous solution, or one given by ipm_set_iterate).  Returns the solve
  * status (IPM_OK when rel KKT <= tol_kkt). */
 int ipm_solve(ipm_handle* h, void* stream, int flags);
+
+/* Asynchronous form of ipm_solve: queues the whole solve (one CUDA graph launch) behind the
+ * work already on `stream` and returns at once; `stream` is made to wait for the solve.  At
+ * most one solve per handle is in flight.  Needs use_graphs = 1. */
+int ipm_solve_async(ipm_handle* h, void* stream, int flags);
+
+/* Waits for the solve started by ipm_solve_async (bounded by options.timeout_ms), returns its
+ * status and fills *info if non-NULL. */
+int ipm_solve_wait(ipm_handle* h, ipm_info* info);
+
+/* IPM_BUSY while the solve started by ipm_solve_async is running, IPM_OK when it has finished
+ * (or none is in flight); does not block. */
+int ipm_solve_query(ipm_handle* h);
+
+/* Batched solve (the uneven many-QP workload): every handle's whole solve captured as one
+ * branch of a single CUDA graph, so one launch runs all of them concurrently on the device;
+ * each handle keeps its own data, schedule and scalars.  ipm_batch_create captures the graph
+ * (after ipm_set_qp on every handle); ipm_batch_solve launches it behind `stream`, waits, and
+ * stores each handle's result (read it with ipm_get_xyz); statuses (count ints) may be NULL.
+ * A batch is invalidated by ipm_set_qp or ipm_destroy on any of its handles. */
+typedef struct ipm_batch ipm_batch;
+int ipm_batch_create(ipm_handle* const* handles, int count, int flags, ipm_batch** out);
+int ipm_batch_solve(ipm_batch* b, void* stream, int* statuses);
+int ipm_batch_destroy(ipm_batch* b);
 
 /* Copies the current iterate to caller memory (any pointer may be NULL to skip it):
  * x, z_l, z_u (n), y, s (m); fills *info if non-NULL. */

@@ -1,12 +1,12 @@
 // C ABI of the interior point library (declared in include/ipm.h): handle, problem ingest,
-// device arena, captured CUDA graphs of one IPM iteration and the host-side solve loop.
+// device arena, the captured CUDA graph of a whole solve, asynchronous and batched launches.
 //
-// Control flow of ipm_solve: one CUDA graph per IPM iteration (Algorithm 1 body, all on the
-// device): diagonal update -> preconditioner build -> right-hand side -> PCG as a
-// conditional-while graph node (one loop trip per PCG iteration; the loop condition is set by
-// the last kernel of the trip, so no host round trip per PCG iteration) -> direction
-// recovery -> ratio test -> update -> residual summary -> mu test / stop rule.  The host
-// reads a few device scalars once per IPM iteration to learn whether to stop.
+// Control flow of ipm_solve: one CUDA graph per solve, all on the device.  Start point, then a
+// conditional-while node over IPM iterations (Algorithm 1) whose body is: diagonal update ->
+// preconditioner build -> right-hand side -> PCG as a nested conditional-while node (one trip
+// per PCG iteration; the condition is set by the last kernel of the trip) -> direction
+// recovery -> ratio test -> update -> residual summary -> mu test / stop rule (which sets the
+// outer condition and appends a trace row).  The host launches the graph and waits once.
 #include <algorithm>
 #include <chrono>
 #include <map>
@@ -27,13 +27,20 @@ using namespace ipmk;
 
 namespace {
 
+// Kernel nodes at each loop level of a captured graph (for launch accounting).
+struct LoopCounts {
+  int top = 0;       // outside every loop
+  int ipm = 0;       // IPM-loop body, outside nested loops
+  int pcg = 0;       // one PCG trip
+  int refine = 0;    // refinement body, outside its PCG loop
+  int fallback = 0;  // one trip of the FP64 fallback loop
+};
+
 struct Graphs {
-  cudaGraphExec_t iter = nullptr;   // one full IPM iteration
-  cudaGraphExec_t dir = nullptr;    // Newton direction only (PCG + recovery)
-  int iter_kernels = 0, iter_body_kernels = 0;   // kernel nodes outside / inside the PCG loop
-  int iter_outer_kernels = 0;                      // inside the refinement loop, outside PCG
-  int iter_fb_kernels = 0;                         // one trip of the FP64 fallback loop
-  int dir_kernels = 0, dir_body_kernels = 0, dir_outer_kernels = 0, dir_fb_kernels = 0;
+  cudaGraphExec_t solve[2] = {nullptr, nullptr};   // whole solve: cold, warm
+  cudaGraph_t solve_g[2] = {nullptr, nullptr};     // its un-instantiated graph (batch capture)
+  cudaGraphExec_t dir = nullptr;                   // Newton direction only (PCG + recovery)
+  LoopCounts solve_c[2], dir_c;
 };
 
 // Kernel nodes of a graph (not descending into child graphs).
@@ -55,7 +62,7 @@ int count_kernel_nodes(cudaGraph_t g) {
 struct ipm_handle {
   ipm_options opt;
   int device = 0;
-  cudaStream_t st = nullptr, st2 = nullptr, st3 = nullptr;
+  cudaStream_t st = nullptr, st2 = nullptr, st3 = nullptr, st4 = nullptr;
   cudaEvent_t ev = nullptr;
   void* arena = nullptr;
   size_t arena_bytes = 0;
@@ -71,6 +78,11 @@ struct ipm_handle {
   int ncomp = 0;
   int64_t sc_cap = 0;
   std::vector<double> trace;        // IPM_TRACE_COLS doubles per IPM iteration of the last solve
+  double* htrace = nullptr;         // pinned: trace rows copied back after a solve
+  int trace_cap = 0;
+  int pending = 0;                  // an asynchronous solve was launched and not yet waited for
+  int pending_pc = 0, pending_warm = 0;
+  std::chrono::steady_clock::time_point t_launch;
 };
 
 namespace {
@@ -103,14 +115,22 @@ int fetch(ipm_handle* h, const T* src, int64_t n, int mem, std::vector<T>& out) 
 
 void destroy_graphs(ipm_handle* h) {
   for (auto& g : h->graphs) {
-    if (g.iter) cudaGraphExecDestroy(g.iter);
+    for (int w = 0; w < 2; ++w) {
+      if (g.solve[w]) cudaGraphExecDestroy(g.solve[w]);
+      if (g.solve_g[w]) cudaGraphDestroy(g.solve_g[w]);
+      g.solve[w] = nullptr;
+      g.solve_g[w] = nullptr;
+    }
     if (g.dir) cudaGraphExecDestroy(g.dir);
-    g.iter = g.dir = nullptr;
+    g.dir = nullptr;
   }
 }
 
 void free_arena(ipm_handle* h) {
   destroy_graphs(h);
+  if (h->htrace) cudaFreeHost(h->htrace);
+  h->htrace = nullptr;
+  h->trace_cap = 0;
   if (h->arena) cudaFree(h->arena);
   h->arena = nullptr;
   h->arena_bytes = 0;
@@ -141,7 +161,7 @@ struct HostQP {
   std::vector<unsigned char> fl, fu;
 };
 
-void carve(Carver& cv, Dev& d, const HostQP& q, int stiff_cap, int64_t sc_cap, bool dense, int storage) {
+void carve(Carver& cv, Dev& d, const HostQP& q, int stiff_cap, int64_t sc_cap, bool dense, int storage, int trace_cap) {
   d.n = q.n; d.m = q.m; d.nR = q.nR;
   d.nnzR = (int64_t)q.Rv.size();
   d.nnzHs = (int64_t)q.Hv.size();
@@ -190,6 +210,7 @@ void carve(Carver& cv, Dev& d, const HostQP& q, int stiff_cap, int64_t sc_cap, b
     d.scaleR = d.p32 = d.w32 = nullptr;
     d.dxr = nullptr;
   }
+  d.trace = cv.take<double>((int64_t)trace_cap * kTraceCols);
   d.partials = cv.take<double>(32 * (int64_t)kMaxRedBlocks);
   d.sc = cv.take<Scal>(1);
 }
@@ -200,6 +221,8 @@ int validate_options(const ipm_options& o) {
   if (o.precond < 0 || o.precond > 3 || o.stiff_max < 0 || o.stiff_max > 1024) return IPM_ERR_ARG;
   if (o.dense_max_n < 0 || o.dense_max_n > 2048 || !(o.stiff_gamma > 0)) return IPM_ERR_ARG;
   if (o.storage < 0 || o.storage > 3 || o.refine_max < 1 || !(o.refine_eta > 0 && o.refine_eta < 1)) return IPM_ERR_ARG;
+  auto lanes_ok = [](int g) { return g == 0 || g == 4 || g == 8 || g == 16 || g == 32; };
+  if (!lanes_ok(o.lanes_rows) || !lanes_ok(o.lanes_cols)) return IPM_ERR_ARG;
   return IPM_OK;
 }
 
@@ -226,10 +249,10 @@ int leave(ipm_handle* h, void* stream) {
 }
 
 // Lanes per row from the average row length (used when autotuning is off): a group of G
-// lanes should see at least 32 entries per lane... rounded to 4, 8, 16 or 32.
+// lanes keeps at most 64 entries per lane (4, 8, 16 or 32 lanes).
 int heuristic_group(double avg_nnz) {
   int g = 4;
-  while (g < 32 && avg_nnz / g > 32.0) g *= 2;
+  while (g < 32 && avg_nnz / g > 64.0) g *= 2;
   return g;
 }
 
@@ -348,51 +371,60 @@ cudaError_t add_while(cudaStream_t st, cudaStream_t body_st, Fill fill, int* bod
   return cudaSuccess;
 }
 
-// Captures one IPM iteration (full=true) or one Newton direction (full=false).  With a
-// reduced-precision store the PCG loop sits inside an FP64 refinement loop (nested while).
-int build_graph(ipm_handle* h, int pc, bool full, cudaGraphExec_t* out, int* top_kernels, int* body_kernels,
-                int* outer_kernels, int* fallback_kernels) {
+// Emits (into the capture running on `st`) one Newton step -- diagonal update, preconditioner,
+// right-hand side, PCG (nested while loops; with a reduced-precision store the PCG loop sits in
+// an FP64 refinement loop followed by an FP64 fallback loop) and direction recovery -- and,
+// when `full`, the ratio test, update, residual summary and control.  Nested loops are re-armed
+// by a kernel before each entry (their default is applied only at top-level graph launch).
+// Side streams s2, s3 capture the loop bodies.  `ipm_loop` is the handle the control kernel
+// sets (0: none).
+cudaError_t emit_step(ipm_handle* h, int pc, bool full, cudaStream_t st, cudaStream_t s2, cudaStream_t s3,
+                      cudaGraphConditionalHandle ipm_loop, LoopCounts* c) {
   const Dev& d = h->d;
   const Geo& g = h->g;
-  cudaStream_t st = h->st;
   const bool lowp = d.storage != ST_F64;
-  CUDA_TRY(h, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t x) { if (e == cudaSuccess && x != cudaSuccess) e = x; };
   chk(launch_diag_update(d, g, st));
   chk(launch_precond_build(d, g, pc, st));
   chk(launch_rhs(d, g, pc, st));
   chk(launch_precond_finish(d, g, pc, st));
-  *outer_kernels = 0;
-  *fallback_kernels = 0;
   if (!lowp) {
+    cudaGraphConditionalHandle hp = 0;
+    chk(new_handle(st, &hp));
+    chk(launch_set_cond(hp, 1u, st));
     chk(launch_cg_init(d, g, pc, st));
     if (e == cudaSuccess)
-      chk(add_while(st, h->st2, [&](cudaGraphConditionalHandle ch, cudaStream_t bs) {
+      chk(add_while(st, s2, [&](cudaGraphConditionalHandle ch, cudaStream_t bs) {
             return launch_cg_body(d, g, pc, ch, bs, true, false);
-          }, body_kernels));
+          }, &c->pcg, &hp));
   } else {
+    cudaGraphConditionalHandle hr = 0, hf = 0;
+    chk(new_handle(st, &hr));
+    chk(new_handle(st, &hf));
     chk(launch_refine_start(d, g, st));
+    chk(launch_set_cond(hr, 1u, st));
     if (e == cudaSuccess)
-      chk(add_while(st, h->st2, [&](cudaGraphConditionalHandle ho, cudaStream_t bs) {
+      chk(add_while(st, s2, [&](cudaGraphConditionalHandle ho, cudaStream_t bs) {
             cudaGraphConditionalHandle hi = 0;
             cudaError_t x = new_handle(bs, &hi);
             if (x == cudaSuccess) x = launch_refine_inner(d, g, hi, bs);
             if (x == cudaSuccess) x = launch_cg_init(d, g, pc, bs);
             if (x == cudaSuccess)
-              x = add_while(bs, h->st3, [&](cudaGraphConditionalHandle hin, cudaStream_t bs2) {
+              x = add_while(bs, s3, [&](cudaGraphConditionalHandle hin, cudaStream_t bs2) {
                     return launch_cg_body(d, g, pc, hin, bs2, true, true);
-                  }, body_kernels, &hi);
+                  }, &c->pcg, &hi);
             if (x == cudaSuccess) x = launch_refine_tail(d, g, ho, bs);
             return x;
-          }, outer_kernels));
+          }, &c->refine, &hr));
     // FP64 fallback for a step the refinement could not finish (exits at once otherwise)
     chk(launch_refine_fallback(d, g, st));
+    chk(launch_set_cond(hf, 1u, st));
     chk(launch_cg_init(d, g, pc, st));
     if (e == cudaSuccess)
-      chk(add_while(st, h->st2, [&](cudaGraphConditionalHandle ch, cudaStream_t bs) {
+      chk(add_while(st, s2, [&](cudaGraphConditionalHandle ch, cudaStream_t bs) {
             return launch_cg_body(d, g, pc, ch, bs, true, false);
-          }, fallback_kernels));
+          }, &c->fallback, &hf));
     chk(launch_refine_finish(d, g, st));
   }
   chk(launch_recover(d, g, st));
@@ -400,19 +432,59 @@ int build_graph(ipm_handle* h, int pc, bool full, cudaGraphExec_t* out, int* top
     chk(launch_ratio(d, g, st));
     chk(launch_update(d, g, st));
     chk(launch_residual_summary(d, g, st));
-    chk(launch_control(d, st));
+    chk(launch_control(d, st, ipm_loop));
   }
+  return e;
+}
+
+// Emits a whole solve into the capture on `st`: start point (cold) or residual summary +
+// warm mu (warm), totals reset, then the IPM while loop around emit_step.
+cudaError_t emit_solve(ipm_handle* h, int pc, bool warm, cudaStream_t st, LoopCounts* c) {
+  const Dev& d = h->d;
+  const Geo& g = h->g;
+  cudaError_t e = warm ? launch_warm_start(d, g, st) : launch_start_point(d, g, st);
+  if (e == cudaSuccess) e = launch_solve_begin(d, st);
+  if (e == cudaSuccess)
+    e = add_while(st, h->st2, [&](cudaGraphConditionalHandle hipm, cudaStream_t bs) {
+          return emit_step(h, pc, true, bs, h->st3, h->st4, hipm, c);
+        }, &c->ipm);
+  return e;
+}
+
+int finish_capture(ipm_handle* h, cudaError_t e, cudaStream_t st, cudaGraphExec_t* out, cudaGraph_t* keep, int* top) {
   cudaGraph_t graph = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(st, &graph);
   if (e == cudaSuccess) e = e2;
-  if (e == cudaSuccess) *top_kernels = count_kernel_nodes(graph);
+  if (e == cudaSuccess && top) *top = count_kernel_nodes(graph);
   if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
-  if (graph) cudaGraphDestroy(graph);
+  if (graph) {
+    if (keep && e == cudaSuccess) *keep = graph;
+    else cudaGraphDestroy(graph);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(h, IPM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
   }
   return IPM_OK;
+}
+
+int ensure_solve_graph(ipm_handle* h, int pc, bool warm) {
+  Graphs& gr = h->graphs[pc];
+  const int w = warm ? 1 : 0;
+  if (gr.solve[w]) return IPM_OK;
+  gr.solve_c[w] = LoopCounts{};
+  CUDA_TRY(h, cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = emit_solve(h, pc, warm, h->st, &gr.solve_c[w]);
+  return finish_capture(h, e, h->st, &gr.solve[w], &gr.solve_g[w], &gr.solve_c[w].top);
+}
+
+int ensure_dir_graph(ipm_handle* h, int pc) {
+  Graphs& gr = h->graphs[pc];
+  if (gr.dir) return IPM_OK;
+  gr.dir_c = LoopCounts{};
+  CUDA_TRY(h, cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = emit_step(h, pc, false, h->st, h->st2, h->st3, 0, &gr.dir_c);
+  return finish_capture(h, e, h->st, &gr.dir, nullptr, &gr.dir_c.top);
 }
 
 // One IPM iteration with every kernel launched directly (use_graphs = 0): the same sequence
@@ -422,7 +494,7 @@ int run_iteration_direct(ipm_handle* h, int pc, int64_t* launches) {
   const Dev& d = h->d;
   const Geo& g = h->g;
   cudaStream_t st = h->st;
-  const Graphs& gr = h->graphs[pc];
+  const LoopCounts& lc = h->graphs[pc].solve_c[0];
   auto pcg = [&](bool lowp) -> int {
     int done = 0;
     for (int k = 0; k < h->opt.max_cg + 1 && !done; ++k) {
@@ -430,7 +502,7 @@ int run_iteration_direct(ipm_handle* h, int pc, int64_t* launches) {
       CUDA_TRY(h, cudaMemcpyAsync(&h->hs->cg_done, &d.sc->cg_done, sizeof(int), cudaMemcpyDeviceToHost, st));
       CUDA_TRY(h, cudaStreamSynchronize(st));
       done = h->hs->cg_done;
-      *launches += gr.iter_body_kernels;
+      *launches += lowp ? lc.pcg : lc.pcg;
     }
     return IPM_OK;
   };
@@ -449,7 +521,7 @@ int run_iteration_direct(ipm_handle* h, int pc, int64_t* launches) {
       CUDA_TRY(h, launch_cg_init(d, g, pc, st));
       if ((rc = pcg(true))) return rc;
       CUDA_TRY(h, launch_refine_tail(d, g, 0, st));
-      *launches += gr.iter_outer_kernels;
+      *launches += lc.refine;
       CUDA_TRY(h, cudaMemcpyAsync(h->hs, d.sc, sizeof(Scal), cudaMemcpyDeviceToHost, st));
       CUDA_TRY(h, cudaStreamSynchronize(st));
       if (h->hs->cg_conv_outer || !std::isfinite(h->hs->rr_outer)) break;
@@ -464,21 +536,7 @@ int run_iteration_direct(ipm_handle* h, int pc, int64_t* launches) {
   CUDA_TRY(h, launch_update(d, g, st));
   CUDA_TRY(h, launch_residual_summary(d, g, st));
   CUDA_TRY(h, launch_control(d, st));
-  *launches += gr.iter_kernels;
-  return IPM_OK;
-}
-
-int ensure_graph(ipm_handle* h, int pc, bool full, cudaGraphExec_t** gx) {
-  Graphs& gr = h->graphs[pc];
-  cudaGraphExec_t* slot = full ? &gr.iter : &gr.dir;
-  if (!*slot) {
-    int rc = full ? build_graph(h, pc, full, slot, &gr.iter_kernels, &gr.iter_body_kernels, &gr.iter_outer_kernels,
-                                &gr.iter_fb_kernels)
-                  : build_graph(h, pc, full, slot, &gr.dir_kernels, &gr.dir_body_kernels, &gr.dir_outer_kernels,
-                                &gr.dir_fb_kernels);
-    if (rc) return rc;
-  }
-  *gx = slot;
+  *launches += lc.ipm;
   return IPM_OK;
 }
 
@@ -558,6 +616,8 @@ void ipm_default_options(ipm_options* o) {
   o->storage = IPM_STORAGE_F64;
   o->refine_max = 8;
   o->refine_eta = 0.1;
+  o->lanes_rows = 0;
+  o->lanes_cols = 0;
 }
 
 const char* ipm_status_str(int s) {
@@ -593,12 +653,14 @@ int ipm_create(const ipm_options* opt, ipm_handle** out) {
       cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&h->st3, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->st4, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming) != cudaSuccess ||
       cudaMallocHost(&h->hs, sizeof(Scal)) != cudaSuccess) {
     cudaGetLastError();
     if (h->st) cudaStreamDestroy(h->st);
     if (h->st2) cudaStreamDestroy(h->st2);
     if (h->st3) cudaStreamDestroy(h->st3);
+    if (h->st4) cudaStreamDestroy(h->st4);
     if (h->ev) cudaEventDestroy(h->ev);
     delete h;
     return IPM_ERR_CUDA;
@@ -617,6 +679,7 @@ int ipm_destroy(ipm_handle* h) {
   if (h->st) cudaStreamDestroy(h->st);
   if (h->st2) cudaStreamDestroy(h->st2);
   if (h->st3) cudaStreamDestroy(h->st3);
+  if (h->st4) cudaStreamDestroy(h->st4);
   if (h->ev) cudaEventDestroy(h->ev);
   delete h;
   return IPM_OK;
@@ -624,6 +687,7 @@ int ipm_destroy(ipm_handle* h) {
 
 int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   if (!h || !qp) return IPM_ERR_ARG;
+  if (h->pending) return fail(h, IPM_ERR_STATE, "a solve is in flight on this handle");
   h->err.clear();
   const int64_t n = qp->n, m = qp->m, fr = qp->f_rows;
   const int mem = qp->mem;
@@ -759,7 +823,7 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   free_arena(h);
   Dev dv{};
   Carver cnt(nullptr);
-  carve(cnt, dv, q, stiff_cap, sc_cap, dense, h->opt.storage);
+  carve(cnt, dv, q, stiff_cap, sc_cap, dense, h->opt.storage, h->opt.max_ipm);
   const size_t bytes = cnt.off + 256;
   if (h->opt.mem_budget > 0 && (double)bytes > h->opt.mem_budget)
     return fail(h, IPM_ERR_OOM, "QP needs " + std::to_string(bytes) + " bytes, over mem_budget");
@@ -770,11 +834,20 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   }
   h->arena_bytes = bytes;
   Carver cv((char*)h->arena);
-  carve(cv, dv, q, stiff_cap, sc_cap, dense, h->opt.storage);
+  carve(cv, dv, q, stiff_cap, sc_cap, dense, h->opt.storage, h->opt.max_ipm);
+  CUDA_TRY(h, cudaDeviceGetAttribute(&dv.sm_count, cudaDevAttrMultiProcessorCount, h->device));
   dv.g_rows = heuristic_group(q.nR ? (double)q.Rv.size() / (double)q.nR : 0.0);
   dv.g_cols = heuristic_group((double)q.Rv.size() / (double)n);
+  if (h->opt.lanes_rows) dv.g_rows = h->opt.lanes_rows;
+  if (h->opt.lanes_cols) dv.g_cols = h->opt.lanes_cols;
   h->d = dv;
   h->g = make_geo(dv);
+  h->trace_cap = h->opt.max_ipm;
+  if (cudaMallocHost(&h->htrace, sizeof(double) * kTraceCols * (size_t)h->trace_cap) != cudaSuccess) {
+    cudaGetLastError();
+    h->htrace = nullptr;
+    return fail(h, IPM_ERR_OOM, "pinned trace buffer");
+  }
   h->cnorm = cn; h->bnorm = bn; h->ncomp = ncomp; h->sc_cap = sc_cap;
   if ((rc = enter(h, stream))) return rc;
   auto up = [&](const void* dst, const void* src, size_t nbytes) -> int {
@@ -813,7 +886,7 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   CUDA_TRY(h, launch_diagH(d, h->st));
   CUDA_TRY(h, launch_quantize(d, h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));   // host staging buffers go out of scope
-  if (h->opt.autotune && (rc = autotune_groups(h))) return rc;
+  if (h->opt.autotune && !h->opt.lanes_rows && !h->opt.lanes_cols && (rc = autotune_groups(h))) return rc;
   h->loaded = true;
   h->have_iterate = false;
   h->precond = choose_precond(h);
@@ -821,96 +894,100 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   return leave(h, stream);
 }
 
-int ipm_solve(ipm_handle* h, void* stream, int flags) {
-  if (!h) return IPM_ERR_ARG;
-  if (!h->loaded) return fail(h, IPM_ERR_STATE, "ipm_solve before ipm_set_qp");
-  h->err.clear();
+}  // extern "C"
+
+// Launches a whole solve (one graph launch, or the direct-launch loop) and queues the copy
+// of the device scalars and trace back to pinned host memory; does not wait.
+static int solve_launch(ipm_handle* h, int flags, int64_t* direct_launches) {
   int rc;
-  const auto t0 = std::chrono::steady_clock::now();
-  if ((rc = enter(h, stream))) return rc;
-  // options may have been changed on the handle? (they cannot: ipm_options is fixed at create)
   if ((rc = pull_scal(h))) return rc;
   push_options(h);
   h->hs->eta_override = 0;
+  h->hs->trace_cap = h->trace_cap;
   CUDA_TRY(h, cudaMemcpyAsync(h->d.sc, h->hs, sizeof(Scal), cudaMemcpyHostToDevice, h->st));
-  if (!(flags & IPM_WARM) || !h->have_iterate) {
-    CUDA_TRY(h, launch_start_point(h->d, h->g, h->st));
-  } else {
-    CUDA_TRY(h, launch_residual_summary(h->d, h->g, h->st));
-    // warm start: mu0 = complementarity mean of the given point
-    CUDA_TRY(h, cudaStreamSynchronize(h->st));
-    if ((rc = pull_scal(h))) return rc;
-    Scal& s = *h->hs;
-    s.mu0 = s.comp_mean > 0 ? s.comp_mean : 1.0;
-    s.mu = s.mu0;
-    s.ipm_iter = 0; s.stop = 0; s.status = DS_RUNNING;
-    double e = s.eta_factor * s.rel_kkt;
-    s.eta = std::min(s.eta_max, std::max(s.eta_min, std::isfinite(e) ? e : s.eta_max));
-    CUDA_TRY(h, cudaMemcpyAsync(h->d.sc, h->hs, sizeof(Scal), cudaMemcpyHostToDevice, h->st));
-  }
-  h->have_iterate = true;
+  const bool warm = (flags & IPM_WARM) && h->have_iterate;
   const int pc = h->precond;
-  cudaGraphExec_t* gx = nullptr;
-  if ((rc = ensure_graph(h, pc, true, &gx))) return rc;   // also counts the kernels per iteration
-  if (!h->opt.use_graphs) gx = nullptr;
-  int64_t cg_total = 0, launches = (flags & IPM_WARM) && h->have_iterate ? 4 : 13;
-  int cg_max_step = 0;
-  int64_t refine_total = 0;
-  int status = IPM_MAX_ITER;
-  const Graphs& grs = h->graphs[pc];
-  h->trace.clear();
-  if (h->d.storage != ST_F64) {
-    int zero = 0;
-    CUDA_TRY(h, cudaMemcpyAsync(&h->d.sc->fallback_total, &zero, sizeof(int), cudaMemcpyHostToDevice, h->st));
-  }
-  for (int it = 0; it < h->opt.max_ipm; ++it) {
-    if (gx) {
-      CUDA_TRY(h, cudaGraphLaunch(*gx, h->st));
-    } else if ((rc = run_iteration_direct(h, pc, &launches))) {
-      return rc;
-    }
-    CUDA_TRY(h, cudaMemcpyAsync(h->hs, h->d.sc, sizeof(Scal), cudaMemcpyDeviceToHost, h->st));
-    if (h->opt.timeout_ms > 0) {
-      CUDA_TRY(h, cudaEventRecord(h->ev, h->st));
-      while (true) {
-        cudaError_t q = cudaEventQuery(h->ev);
-        if (q == cudaSuccess) break;
-        if (q != cudaErrorNotReady) return fail(h, IPM_ERR_CUDA, cudaGetErrorString(q));
-        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-        if (ms > h->opt.timeout_ms) {
-          h->info.status = IPM_ERR_TIMEOUT;
-          leave(h, stream);
-          return fail(h, IPM_ERR_TIMEOUT, "timeout_ms exceeded");
-        }
-        std::this_thread::yield();
-      }
-    } else {
+  h->have_iterate = true;
+  h->pending_pc = pc;
+  h->pending_warm = warm;
+  if ((rc = ensure_solve_graph(h, pc, warm))) return rc;
+  if (h->opt.use_graphs) {
+    CUDA_TRY(h, cudaGraphLaunch(h->graphs[pc].solve[warm ? 1 : 0], h->st));
+  } else {
+    // same kernels launched one by one, loops driven from the host
+    const Dev& d = h->d;
+    CUDA_TRY(h, warm ? launch_warm_start(d, h->g, h->st) : launch_start_point(d, h->g, h->st));
+    CUDA_TRY(h, launch_solve_begin(d, h->st));
+    for (int it = 0; it < h->opt.max_ipm; ++it) {
+      if ((rc = run_iteration_direct(h, pc, direct_launches))) return rc;
+      CUDA_TRY(h, cudaMemcpyAsync(h->hs, d.sc, sizeof(Scal), cudaMemcpyDeviceToHost, h->st));
       CUDA_TRY(h, cudaStreamSynchronize(h->st));
-    }
-    const Scal& s = *h->hs;
-    cg_total += s.cg_iter;
-    cg_max_step = std::max(cg_max_step, s.cg_iter);
-    if (gx) launches += grs.iter_kernels + (int64_t)std::max(1, s.cg_iter) * grs.iter_body_kernels +
-                        (int64_t)s.refine_it * grs.iter_outer_kernels + (h->d.storage != ST_F64 ? grs.iter_fb_kernels : 0);
-    refine_total += h->d.storage != ST_F64 ? s.refine_it : 0;
-    const double row[IPM_TRACE_COLS] = {(double)s.ipm_iter, s.mu, s.rel_kkt, s.res_primal, s.res_dual, s.res_gap,
-                                        s.alpha_p, s.alpha_d, (double)s.cg_iter, (double)s.cg_conv,
-                                        (double)(pc == PC_JACOBI_LR ? s.n_stiff : 0),
-                                        s.rhs2 > 0 ? std::sqrt(s.rr / s.rhs2) : 0.0, s.eta_used,
-                                        (double)(h->d.storage != ST_F64 ? s.refine_it : 0)};
-    h->trace.insert(h->trace.end(), row, row + IPM_TRACE_COLS);
-    if (s.stop) {
-      status = s.status == DS_OK ? IPM_OK : s.status == DS_MAX_ITER ? IPM_MAX_ITER
-             : s.status == DS_CG_STALL ? IPM_CG_STALL : IPM_NUMERICAL;
-      break;
+      if (h->hs->stop) break;
     }
   }
+  CUDA_TRY(h, cudaMemcpyAsync(h->hs, h->d.sc, sizeof(Scal), cudaMemcpyDeviceToHost, h->st));
+  if (h->trace_cap)
+    CUDA_TRY(h, cudaMemcpyAsync(h->htrace, h->d.trace, sizeof(double) * kTraceCols * (size_t)h->trace_cap,
+                                cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaEventRecord(h->ev, h->st));
+  h->pending = 1;
+  return IPM_OK;
+}
+
+static int fill_info(ipm_handle* h, int64_t direct_launches);
+
+// Waits for the launched solve (bounded by timeout_ms) and fills h->info and h->trace.
+static int solve_collect(ipm_handle* h, int64_t direct_launches) {
+  const auto t0 = h->t_launch;
+  if (h->opt.timeout_ms > 0) {
+    while (true) {
+      cudaError_t q = cudaEventQuery(h->ev);
+      if (q == cudaSuccess) break;
+      if (q != cudaErrorNotReady) return fail(h, IPM_ERR_CUDA, cudaGetErrorString(q));
+      const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      if (ms > h->opt.timeout_ms) {
+        h->info.status = IPM_ERR_TIMEOUT;
+        return fail(h, IPM_ERR_TIMEOUT, "timeout_ms exceeded (the solve keeps running to its iteration limit)");
+      }
+      std::this_thread::yield();
+    }
+  } else {
+    CUDA_TRY(h, cudaEventSynchronize(h->ev));
+  }
+  return fill_info(h, direct_launches);
+}
+
+// Result bookkeeping after a finished solve: info from the pinned scalars and trace rows.
+static int fill_info(ipm_handle* h, int64_t direct_launches) {
+  const auto t0 = h->t_launch;
+  h->pending = 0;
   const Scal& s = *h->hs;
+  const int pc = h->pending_pc;
+  const LoopCounts& lc = h->graphs[pc].solve_c[h->pending_warm ? 1 : 0];
+  const int rows = std::min(s.trace_rows, h->trace_cap);
+  h->trace.assign(h->htrace, h->htrace + (size_t)rows * kTraceCols);
+  int64_t launches = direct_launches;
+  if (h->opt.use_graphs) {
+    launches = lc.top;
+    const bool lowp = h->d.storage != ST_F64;
+    for (int r = 0; r < rows; ++r) {
+      const double* t = h->htrace + (size_t)r * kTraceCols;
+      const int64_t cg = (int64_t)t[8], ref = (int64_t)t[13];
+      launches += lc.ipm + 1;  // + the loop re-arm kernel counted in ipm
+      if (!lowp) {
+        launches += std::max<int64_t>(1, cg) * lc.pcg;
+      } else {
+        launches += (cg + ref) * lc.pcg + ref * lc.refine + lc.fallback;
+      }
+    }
+  }
+  int status = s.status == DS_OK ? IPM_OK : s.status == DS_MAX_ITER ? IPM_MAX_ITER
+             : s.status == DS_CG_STALL ? IPM_CG_STALL : s.status == DS_RUNNING ? IPM_MAX_ITER : IPM_NUMERICAL;
   ipm_info& in = h->info;
   in.status = status;
   in.ipm_iters = s.ipm_iter;
-  in.cg_iters = cg_total;
-  in.max_cg_step = cg_max_step;
+  in.cg_iters = s.cg_total;
+  in.max_cg_step = s.max_cg_step;
   in.max_stiff_rows = s.max_stiff_seen;
   in.precond = pc;
   in.rel_kkt = s.rel_kkt;
@@ -924,10 +1001,58 @@ int ipm_solve(ipm_handle* h, void* stream, int flags) {
   in.kernel_launches = launches;
   in.lanes_rows = h->d.g_rows;
   in.lanes_cols = h->d.g_cols;
-  in.refine_passes = refine_total;
+  in.refine_passes = h->d.storage != ST_F64 ? s.refine_total : 0;
   in.fallback_steps = h->d.storage != ST_F64 ? s.fallback_total : 0;
-  if ((rc = leave(h, stream))) return rc;
   return status;
+}
+
+extern "C" {
+
+int ipm_solve_async(ipm_handle* h, void* stream, int flags) {
+  if (!h) return IPM_ERR_ARG;
+  if (!h->loaded) return fail(h, IPM_ERR_STATE, "ipm_solve before ipm_set_qp");
+  if (h->pending) return fail(h, IPM_ERR_STATE, "a solve is already in flight on this handle");
+  if (!h->opt.use_graphs) return fail(h, IPM_ERR_STATE, "asynchronous solves need use_graphs = 1");
+  h->err.clear();
+  int rc;
+  h->t_launch = std::chrono::steady_clock::now();
+  if ((rc = enter(h, stream))) return rc;
+  int64_t dl = 0;
+  if ((rc = solve_launch(h, flags, &dl))) return rc;
+  return leave(h, stream);
+}
+
+int ipm_solve_wait(ipm_handle* h, ipm_info* info) {
+  if (!h) return IPM_ERR_ARG;
+  if (!h->pending) return fail(h, IPM_ERR_STATE, "no solve in flight");
+  int st = solve_collect(h, 0);
+  if (info) *info = h->info;
+  return st;
+}
+
+int ipm_solve_query(ipm_handle* h) {
+  if (!h) return IPM_ERR_ARG;
+  if (!h->pending) return IPM_OK;
+  cudaError_t q = cudaEventQuery(h->ev);
+  if (q == cudaErrorNotReady) return IPM_BUSY;
+  if (q != cudaSuccess) return fail(h, IPM_ERR_CUDA, cudaGetErrorString(q));
+  return IPM_OK;
+}
+
+int ipm_solve(ipm_handle* h, void* stream, int flags) {
+  if (!h) return IPM_ERR_ARG;
+  if (!h->loaded) return fail(h, IPM_ERR_STATE, "ipm_solve before ipm_set_qp");
+  if (h->pending) return fail(h, IPM_ERR_STATE, "a solve is already in flight on this handle");
+  h->err.clear();
+  int rc;
+  h->t_launch = std::chrono::steady_clock::now();
+  if ((rc = enter(h, stream))) return rc;
+  int64_t dl = 0;
+  if ((rc = solve_launch(h, flags, &dl))) return rc;
+  const int st = solve_collect(h, dl);
+  if (st == IPM_ERR_TIMEOUT || st == IPM_ERR_CUDA) return st;
+  if ((rc = leave(h, stream))) return rc;
+  return st;
 }
 
 int ipm_get_xyz(ipm_handle* h, double* x, double* y, double* zl, double* zu, double* s, ipm_info* info, int mem, void* stream) {
@@ -1058,9 +1183,8 @@ int ipm_newton_direction(ipm_handle* h, double eta, double* dx, double* ds, doub
     s.eta = std::min(s.eta_max, std::max(s.eta_min, std::isfinite(e) ? e : s.eta_max));
   }
   CUDA_TRY(h, cudaMemcpyAsync(d.sc, h->hs, sizeof(Scal), cudaMemcpyHostToDevice, h->st));
-  cudaGraphExec_t* gx = nullptr;
-  if ((rc = ensure_graph(h, h->precond, false, &gx))) return rc;
-  CUDA_TRY(h, cudaGraphLaunch(*gx, h->st));
+  if ((rc = ensure_dir_graph(h, h->precond))) return rc;
+  CUDA_TRY(h, cudaGraphLaunch(h->graphs[h->precond].dir, h->st));
   if ((rc = copy_out(h, dx, d.dx, d.n, mem))) return rc;
   if ((rc = copy_out(h, ds, d.ds, d.m, mem))) return rc;
   if ((rc = copy_out(h, dy, d.dy, d.m, mem))) return rc;
@@ -1104,6 +1228,118 @@ int ipm_step_lengths(ipm_handle* h, const double* dx, const double* ds, const do
   CUDA_TRY(h, cudaMemcpyAsync(&d.sc->equal_steps, &eq_keep, sizeof(int), cudaMemcpyHostToDevice, h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
   return leave(h, stream);
+}
+
+}  // extern "C"
+
+struct ipm_batch {
+  std::vector<ipm_handle*> hs;
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev = nullptr, fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraphExec_t exec = nullptr;
+};
+
+static void batch_free(ipm_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (auto e : b->join) if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->ev) cudaEventDestroy(b->ev);
+  if (b->st) cudaStreamDestroy(b->st);
+  delete b;
+}
+
+extern "C" {
+
+int ipm_batch_create(ipm_handle* const* handles, int count, int flags, ipm_batch** out) {
+  if (!handles || count < 1 || !out || flags != IPM_COLD) return IPM_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < count; ++i) {
+    if (!handles[i] || !handles[i]->loaded || handles[i]->pending || !handles[i]->opt.use_graphs) return IPM_ERR_STATE;
+    if (handles[i]->device != handles[0]->device) return IPM_ERR_ARG;
+    for (int j = 0; j < i; ++j) if (handles[j] == handles[i]) return IPM_ERR_ARG;
+  }
+  ipm_batch* b = new (std::nothrow) ipm_batch();
+  if (!b) return IPM_ERR_OOM;
+  b->hs.assign(handles, handles + count);
+  b->join.assign(count, nullptr);
+  auto bad = [&](ipm_handle* h, const std::string& m) {
+    if (h) h->err = m;
+    cudaGetLastError();
+    batch_free(b);
+    return IPM_ERR_CUDA;
+  };
+  if (cudaSetDevice(handles[0]->device) != cudaSuccess || cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+    return bad(handles[0], "batch stream/event");
+  for (auto& e : b->join)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return bad(handles[0], "batch event");
+  cudaError_t e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->st);
+  for (int i = 0; i < count && e == cudaSuccess; ++i) {
+    ipm_handle* h = b->hs[i];
+    const int pc = h->precond;
+    Graphs& gr = h->graphs[pc];
+    e = cudaStreamWaitEvent(h->st, b->fork, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d.sc, h->hs, sizeof(Scal), cudaMemcpyHostToDevice, h->st);
+    gr.solve_c[0] = LoopCounts{};
+    if (e == cudaSuccess) e = emit_solve(h, pc, false, h->st, &gr.solve_c[0]);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->hs, h->d.sc, sizeof(Scal), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess && h->trace_cap)
+      e = cudaMemcpyAsync(h->htrace, h->d.trace, sizeof(double) * kTraceCols * (size_t)h->trace_cap,
+                          cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaEventRecord(b->join[i], h->st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->st, b->join[i], 0);
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(b->st, &graph);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return bad(handles[0], std::string("batch capture: ") + cudaGetErrorString(e));
+  *out = b;
+  return IPM_OK;
+}
+
+int ipm_batch_solve(ipm_batch* b, void* stream, int* statuses) {
+  if (!b) return IPM_ERR_ARG;
+  ipm_handle* h0 = b->hs[0];
+  if (cudaSetDevice(h0->device) != cudaSuccess) return IPM_ERR_CUDA;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (ipm_handle* h : b->hs) {
+    if (h->pending || !h->loaded) return IPM_ERR_STATE;
+    push_options(h);
+    h->hs->eta_override = 0;
+    h->hs->trace_cap = h->trace_cap;
+  }
+  if (cudaEventRecord(b->ev, (cudaStream_t)stream) != cudaSuccess || cudaStreamWaitEvent(b->st, b->ev, 0) != cudaSuccess ||
+      cudaGraphLaunch(b->exec, b->st) != cudaSuccess || cudaEventRecord(b->ev, b->st) != cudaSuccess ||
+      cudaEventSynchronize(b->ev) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h0, IPM_ERR_CUDA, "batch launch failed");
+  }
+  int worst = IPM_OK;
+  for (size_t i = 0; i < b->hs.size(); ++i) {
+    ipm_handle* h = b->hs[i];
+    h->have_iterate = true;
+    h->pending_pc = h->precond;
+    h->pending_warm = 0;
+    h->t_launch = t0;
+    const int st = fill_info(h, 0);
+    if (statuses) statuses[i] = st;
+    if (st != IPM_OK && worst == IPM_OK) worst = st;
+  }
+  if (cudaStreamWaitEvent((cudaStream_t)stream, b->ev, 0) != cudaSuccess) return IPM_ERR_CUDA;
+  return worst;
+}
+
+int ipm_batch_destroy(ipm_batch* b) {
+  if (!b) return IPM_OK;
+  if (b->st) cudaStreamSynchronize(b->st);
+  batch_free(b);
+  return IPM_OK;
 }
 
 int ipm_get_trace(const ipm_handle* h, double* buf, int max_rows) {

@@ -18,7 +18,7 @@ namespace ipmk {
 
 constexpr int kWarp = 32;
 constexpr int kBlock = 256;          // threads per block of the streaming kernels
-constexpr int kMaxRedBlocks = 1024;  // upper bound of blocks that write reduction partials
+constexpr int kMaxRedBlocks = 2048;  // upper bound of blocks that write reduction partials
 constexpr int kHistBins = 64;        // stiff-row ratio histogram bins (two per octave)
 
 // Device scalars of one handle.
@@ -38,6 +38,9 @@ struct Scal {
   // FP64 refinement of a reduced-precision Newton step
   double tol2_outer, rr_outer, refine_eta;
   int refine_it, refine_max, cg_step_total, cg_conv_outer, fallback, fallback_total;
+  // totals of one solve (device-side IPM loop)
+  long long cg_total;
+  int refine_total, max_cg_step, trace_rows, trace_cap;
   // step
   double alpha_p, alpha_d;
   // residual summary at the current iterate (written by k_resid_final)
@@ -165,26 +168,31 @@ template <int G, bool SQ>
 __device__ __forceinline__ double group_row_dot(const int64_t beg, const int64_t end, const int gl,
                                                 const int32_t* __restrict__ idx, const double* __restrict__ val,
                                                 const double* __restrict__ x) {
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  // Eight entries per trip: all value and index loads first, then all gathers, then the
+  // multiply-adds into one accumulator (the float64 pipe, not the add latency, is the limit).
+  double a = 0.0;
   int64_t e = beg + gl;
-  for (; e + 3 * G < end; e += 4 * G) {
-    double v0 = __ldg(val + e), v1 = __ldg(val + e + G), v2 = __ldg(val + e + 2 * G), v3 = __ldg(val + e + 3 * G);
-    const int i0 = __ldg(idx + e), i1 = __ldg(idx + e + G), i2 = __ldg(idx + e + 2 * G), i3 = __ldg(idx + e + 3 * G);
-    if (SQ) { v0 *= v0; v1 *= v1; v2 *= v2; v3 *= v3; }
-    a0 = fma(v0, __ldg(x + i0), a0);
-    a1 = fma(v1, __ldg(x + i1), a1);
-    a2 = fma(v2, __ldg(x + i2), a2);
-    a3 = fma(v3, __ldg(x + i3), a3);
+  for (; e + 7 * G < end; e += 8 * G) {
+    double v[8];
+    int i[8];
+    double xv[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      v[k] = __ldg(val + e + k * G);
+      i[k] = __ldg(idx + e + k * G);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) xv[k] = __ldg(x + i[k]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a = fma(SQ ? v[k] * v[k] : v[k], xv[k], a);
   }
   for (; e < end; e += G) {
-    double v0 = __ldg(val + e);
-    if (SQ) v0 *= v0;
-    a0 = fma(v0, __ldg(x + __ldg(idx + e)), a0);
+    const double v0 = __ldg(val + e);
+    a = fma(SQ ? v0 * v0 : v0, __ldg(x + __ldg(idx + e)), a);
   }
-  double s = (a0 + a1) + (a2 + a3);
 #pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  return s;
+  for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  return a;
 }
 
 // Two vectors through the same matrix row (one pass over the row), by a group of G lanes.

@@ -44,9 +44,11 @@ static __device__ __forceinline__ int glane() { return threadIdx.x & (G - 1); }
 
 
 Geo make_geo(const Dev& d) {
-  auto blocks_for = [](int64_t items, int per_block) -> int {
+  // at most 8 blocks of 256 threads per SM (the row kernels are grid-stride loops)
+  const int cap = std::min(kMaxRedBlocks, 8 * (d.sm_count > 0 ? d.sm_count : 148));
+  auto blocks_for = [cap](int64_t items, int per_block) -> int {
     int64_t b = (items + per_block - 1) / per_block;
-    if (b > kMaxRedBlocks) b = kMaxRedBlocks;
+    if (b > cap) b = cap;
     return (int)b;
   };
   Geo g;
@@ -365,11 +367,16 @@ static __device__ void set_eta(Scal* sc) {
 
 // Algorithm 1's tail on the device: stop when rel KKT <= tol (reading of "mu <= mu_tol"),
 // else mu <- mu / 10 when ||r|| < mu; then the PCG tolerance eta for the next Newton step.
-__global__ void k_control(Dev d) {
+__global__ void k_control(Dev d, cudaGraphConditionalHandle h, int set_cond) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   Scal* sc = d.sc;
   sc->ipm_iter += 1;
   const double rk = sc->rel_kkt;
+  const double mu_step = sc->mu;
+  const int refine = d.storage != ST_F64 ? sc->refine_it : 0;
+  sc->cg_total += sc->cg_iter;
+  sc->refine_total += refine;
+  if (sc->cg_iter > sc->max_cg_step) sc->max_cg_step = sc->cg_iter;
   if (sc->status == DS_NUMERICAL || sc->status == DS_CG_STALL) {
     sc->stop = 1;
   } else if (!isfinite(rk) || !isfinite(sc->pobj)) {
@@ -385,10 +392,63 @@ __global__ void k_control(Dev d) {
     sc->mu = fmax(sc->mu * 0.1, sc->mu0 * 1e-16);
   }
   set_eta(sc);
+  if (d.trace && sc->trace_rows < sc->trace_cap) {
+    double* t = d.trace + (int64_t)sc->trace_rows * kTraceCols;
+    t[0] = sc->ipm_iter; t[1] = mu_step; t[2] = rk; t[3] = sc->res_primal; t[4] = sc->res_dual;
+    t[5] = sc->res_gap; t[6] = sc->alpha_p; t[7] = sc->alpha_d; t[8] = sc->cg_iter; t[9] = sc->cg_conv;
+    t[10] = sc->n_stiff; t[11] = sc->rhs2 > 0 ? sqrt(sc->rr / sc->rhs2) : 0.0; t[12] = sc->eta_used; t[13] = refine;
+    sc->trace_rows += 1;
+  }
+  if (set_cond) cudaGraphSetConditional(h, sc->stop ? 0u : 1u);
 }
 
-cudaError_t launch_control(const Dev& d, cudaStream_t st) {
-  k_control<<<1, 32, 0, st>>>(d);
+cudaError_t launch_control(const Dev& d, cudaStream_t st, cudaGraphConditionalHandle h) {
+  k_control<<<1, 32, 0, st>>>(d, h, h != 0 ? 1 : 0);
+  return cudaGetLastError();
+}
+
+// Start of a solve on the device: per-solve totals and the trace cleared.
+__global__ void k_solve_begin(Dev d) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  Scal* sc = d.sc;
+  sc->cg_total = 0;
+  sc->refine_total = 0;
+  sc->max_cg_step = 0;
+  sc->trace_rows = 0;
+  sc->max_stiff_seen = 0;
+  sc->fallback_total = 0;
+  sc->stop = 0;
+  sc->status = DS_RUNNING;
+}
+
+cudaError_t launch_solve_begin(const Dev& d, cudaStream_t st) {
+  k_solve_begin<<<1, 32, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+// Warm start from the current iterate: mu0 = its complementarity mean (after a residual summary).
+__global__ void k_warm_mu(Dev d) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  Scal* sc = d.sc;
+  sc->mu0 = sc->comp_mean > 0.0 ? sc->comp_mean : 1.0;
+  sc->mu = sc->mu0;
+  sc->ipm_iter = 0;
+  set_eta(sc);
+}
+
+cudaError_t launch_warm_start(const Dev& d, const Geo& g, cudaStream_t st) {
+  cudaError_t e = launch_residual_summary(d, g, st);
+  if (e != cudaSuccess) return e;
+  k_warm_mu<<<1, 32, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+__global__ void k_set_cond(cudaGraphConditionalHandle h, unsigned v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(h, v);
+}
+
+cudaError_t launch_set_cond(cudaGraphConditionalHandle h, unsigned v, cudaStream_t st) {
+  k_set_cond<<<1, 32, 0, st>>>(h, v);
   return cudaGetLastError();
 }
 

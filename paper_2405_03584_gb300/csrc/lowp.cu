@@ -87,22 +87,26 @@ __device__ __forceinline__ float group_row_dot_lp(const int64_t beg, const int64
                                                   const int32_t* __restrict__ idx,
                                                   const typename StorageT<S>::T* __restrict__ val,
                                                   const float* __restrict__ x) {
-  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+  float a = 0.f;
   int64_t e = beg + gl;
-  for (; e + 3 * G < end; e += 4 * G) {
-    const float v0 = StorageT<S>::dec(val[e]), v1 = StorageT<S>::dec(val[e + G]);
-    const float v2 = StorageT<S>::dec(val[e + 2 * G]), v3 = StorageT<S>::dec(val[e + 3 * G]);
-    const int i0 = __ldg(idx + e), i1 = __ldg(idx + e + G), i2 = __ldg(idx + e + 2 * G), i3 = __ldg(idx + e + 3 * G);
-    a0 = fmaf(v0, __ldg(x + i0), a0);
-    a1 = fmaf(v1, __ldg(x + i1), a1);
-    a2 = fmaf(v2, __ldg(x + i2), a2);
-    a3 = fmaf(v3, __ldg(x + i3), a3);
-  }
-  for (; e < end; e += G) a0 = fmaf(StorageT<S>::dec(val[e]), __ldg(x + __ldg(idx + e)), a0);
-  float s = (a0 + a1) + (a2 + a3);
+  for (; e + 7 * G < end; e += 8 * G) {
+    float v[8];
+    int i[8];
+    float xv[8];
 #pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  return s;
+    for (int k = 0; k < 8; ++k) {
+      v[k] = StorageT<S>::dec(val[e + k * G]);
+      i[k] = __ldg(idx + e + k * G);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) xv[k] = __ldg(x + i[k]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a = fmaf(v[k], xv[k], a);
+  }
+  for (; e < end; e += G) a = fmaf(StorageT<S>::dec(val[e]), __ldg(x + __ldg(idx + e)), a);
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  return a;
 }
 
 #define FOR_GROUP_ROWS_L(G, r, ok, nrows)                                                                    \

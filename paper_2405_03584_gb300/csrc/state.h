@@ -9,10 +9,13 @@
 
 namespace ipmk {
 
+constexpr int kTraceCols = 14;   // columns of one trace row (IPM_TRACE_COLS of the C header)
+
 struct Dev {
   int64_t n, m, nR;            // variables, constraint rows, rows of R = [F; A_csr]
   int64_t nnzR, nnzHs;
   int g_rows, g_cols;          // lanes per row of the kernels over R and over R^T (4, 8, 16, 32)
+  int sm_count;                // multiprocessors of the device (grid sizing)
   // problem data
   const int64_t* R_ptr; const int32_t* R_idx; const double* R_val;
   const int64_t* RT_ptr; const int32_t* RT_idx; const double* RT_val;
@@ -51,6 +54,7 @@ struct Dev {
   float* scaleR;               // nR
   float *p32, *w32;            // FP32 mirror of p (n) and the rows-pass result (nR)
   double* dxr;                 // n: accumulated refined step
+  double* trace;               // trace_cap rows of kTraceCols: per-IPM-iteration metrics
   // reductions and scalars
   double* partials;            // 32 * kMaxRedBlocks
   Scal* sc;
@@ -72,7 +76,11 @@ cudaError_t launch_residual_summary(const Dev& d, const Geo& g, cudaStream_t st)
 // ---- complementarity residual vectors r_s, r_l, r_u (into ds, dzl, dzu) ----
 cudaError_t launch_comp_resid(const Dev& d, const Geo& g, cudaStream_t st);
 // ---- IPM control (mu test, stop rule, eta) ----
-cudaError_t launch_control(const Dev& d, cudaStream_t st);
+cudaError_t launch_control(const Dev& d, cudaStream_t st, cudaGraphConditionalHandle h = 0);
+// ---- device-side IPM loop: solve start (totals reset), warm start, loop re-arming ----
+cudaError_t launch_solve_begin(const Dev& d, cudaStream_t st);
+cudaError_t launch_warm_start(const Dev& d, const Geo& g, cudaStream_t st);
+cudaError_t launch_set_cond(cudaGraphConditionalHandle h, unsigned v, cudaStream_t st);
 // ---- diagonal update and preconditioner build ----
 cudaError_t launch_diag_update(const Dev& d, const Geo& g, cudaStream_t st);
 cudaError_t launch_precond_build(const Dev& d, const Geo& g, int precond, cudaStream_t st);   // before rhs

@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libipm.so")
 
 IPM_OK, IPM_ERR_ARG, IPM_ERR_OOM, IPM_MAX_ITER, IPM_CG_STALL, IPM_NUMERICAL, \
-    IPM_INFEASIBLE_SUSPECTED, IPM_ERR_TIMEOUT, IPM_ERR_CUDA, IPM_ERR_STATE, IPM_ERR_TOO_LARGE = range(11)
+    IPM_INFEASIBLE_SUSPECTED, IPM_ERR_TIMEOUT, IPM_ERR_CUDA, IPM_ERR_STATE, IPM_ERR_TOO_LARGE, IPM_BUSY = range(12)
 STATIC_SCRATCH_ROWS = 262144
 MEM_HOST, MEM_DEVICE = 0, 1
 PRECOND = {"jacobi": 0, "jacobi_lr": 1, "dense": 2, "auto": 3}
@@ -29,7 +29,8 @@ COLD, WARM = 0, 1
 EXPORTS = ["ipm_default_options", "ipm_create", "ipm_set_qp", "ipm_solve", "ipm_get_xyz", "ipm_destroy",
            "ipm_status_str", "ipm_last_error", "ipm_set_iterate", "ipm_residuals", "ipm_apply_kkt",
            "ipm_precond_diag", "ipm_newton_direction", "ipm_step_lengths", "ipm_profile_operator",
-           "ipm_get_trace", "ipm_apply_operator_static"]
+           "ipm_get_trace", "ipm_apply_operator_static", "ipm_solve_async", "ipm_solve_wait", "ipm_solve_query",
+           "ipm_batch_create", "ipm_batch_solve", "ipm_batch_destroy"]
 TRACE_COLS = ("iter", "mu", "rel_kkt", "primal", "dual", "gap", "alpha_p", "alpha_d", "pcg_iters", "pcg_converged",
               "stiff_rows", "pcg_rel_residual", "eta", "refine_passes")
 
@@ -40,7 +41,8 @@ class Options(C.Structure):
                 ("precond", C.c_int), ("stiff_gamma", C.c_double), ("stiff_max", C.c_int),
                 ("dense_max_n", C.c_int), ("timeout_ms", C.c_double), ("mem_budget", C.c_double),
                 ("equal_steps", C.c_int), ("autotune", C.c_int), ("use_graphs", C.c_int),
-                ("storage", C.c_int), ("refine_max", C.c_int), ("refine_eta", C.c_double)]
+                ("storage", C.c_int), ("refine_max", C.c_int), ("refine_eta", C.c_double),
+                ("lanes_rows", C.c_int), ("lanes_cols", C.c_int)]
 
 
 class QP(C.Structure):
@@ -100,6 +102,12 @@ def load(path: str = LIB_PATH):
         "ipm_step_lengths": (I, [P, P, P, P, P, P, D, C.POINTER(C.c_double), C.POINTER(C.c_double), I, P]),
         "ipm_profile_operator": (I, [P, I] + [C.POINTER(C.c_double)] * 6),
         "ipm_get_trace": (I, [P, P, I]),
+        "ipm_solve_async": (I, [P, P, I]),
+        "ipm_solve_wait": (I, [P, C.POINTER(Info)]),
+        "ipm_solve_query": (I, [P]),
+        "ipm_batch_create": (I, [C.POINTER(P), I, I, C.POINTER(P)]),
+        "ipm_batch_solve": (I, [P, P, C.POINTER(C.c_int)]),
+        "ipm_batch_destroy": (I, [P]),
         "ipm_apply_operator_static": (I, [C.c_int64, C.c_int64] + [P] * 10 + [P]),
     }
     for name, (res, args) in sig.items():
@@ -260,6 +268,23 @@ class Solver:
         rc = load().ipm_solve(self._h, _default_stream(stream), WARM if warm else COLD)
         return self._check(rc, "ipm_solve", ok=(IPM_OK, IPM_MAX_ITER, IPM_CG_STALL, IPM_NUMERICAL))
 
+    def solve_async(self, warm=False, stream=None):
+        """Queues the whole solve (one graph launch) and returns at once."""
+        self._check(load().ipm_solve_async(self._h, _default_stream(stream), WARM if warm else COLD), "ipm_solve_async")
+
+    def wait(self):
+        """Waits for solve_async; returns the status."""
+        info = Info()
+        rc = load().ipm_solve_wait(self._h, C.byref(info))
+        return self._check(rc, "ipm_solve_wait", ok=(IPM_OK, IPM_MAX_ITER, IPM_CG_STALL, IPM_NUMERICAL))
+
+    def done(self):
+        """True once the solve started by solve_async has finished (non-blocking)."""
+        rc = load().ipm_solve_query(self._h)
+        if rc not in (IPM_OK, IPM_BUSY):
+            self._check(rc, "ipm_solve_query")
+        return rc == IPM_OK
+
     def get(self, stream=None, out=None):
         """Returns dict(x, y, zl, zu, s, info).  ``out`` may give preallocated device tensors."""
         n, m = self.n, self.m
@@ -338,3 +363,36 @@ class Solver:
                                             mk.ptr(dzu, np.float64), float(tau), C.byref(ap), C.byref(ad), MEM_HOST,
                                             _default_stream(stream)), "ipm_step_lengths")
         return ap.value, ad.value
+
+
+class Batch:
+    """Many solver handles solved by one CUDA graph launch (one graph branch per handle)."""
+
+    def __init__(self, solvers):
+        L = load()
+        self.solvers = list(solvers)
+        arr = (C.c_void_p * len(self.solvers))(*[s._h.value for s in self.solvers])
+        b = C.c_void_p()
+        rc = L.ipm_batch_create(arr, len(self.solvers), COLD, C.byref(b))
+        if rc != IPM_OK:
+            raise IpmError(rc, "ipm_batch_create: %s" % L.ipm_last_error(self.solvers[0]._h).decode())
+        self._b = b
+
+    def solve(self, stream=None):
+        """Runs every solve; returns the list of statuses."""
+        st = (C.c_int * len(self.solvers))()
+        rc = load().ipm_batch_solve(self._b, _default_stream(stream), st)
+        if rc in (IPM_ERR_ARG, IPM_ERR_CUDA, IPM_ERR_STATE):
+            raise IpmError(rc, "ipm_batch_solve")
+        return list(st)
+
+    def close(self):
+        if getattr(self, "_b", None):
+            load().ipm_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -291,3 +291,34 @@ def test_reduced_precision_direction(storage):
     err = np.abs(d["dx"] - ref.x).max() / np.abs(ref.x).max()
     assert err <= 1e-6, err
     s.close()
+
+
+def test_async_and_batch_match_sync():
+    """ipm_solve_async / ipm_solve_wait and one batched graph launch over several uneven QPs give
+    the same bits as solving each QP on its own."""
+    probs = [W.rt_qp(n=n, seed=40 + i, density=d, n_organ=n // 2) for i, (n, d) in
+             enumerate([(300, 0.01), (777, 0.004), (1200, 0.006), (450, 0.008)])]
+    ref = []
+    for p in probs:
+        with ipm.Solver(tol_kkt=1e-8, precond="jacobi_lr") as s:
+            s.set_qp_rt(p)
+            assert s.solve() == ipm.IPM_OK
+            ref.append(s.get()["x"])
+    with ipm.Solver(tol_kkt=1e-8, precond="jacobi_lr") as s:
+        s.set_qp_rt(probs[1])
+        s.solve_async()
+        assert s.wait() == ipm.IPM_OK
+        assert np.array_equal(s.get()["x"], ref[1])
+    solvers = []
+    for p in probs:
+        s = ipm.Solver(tol_kkt=1e-8, precond="jacobi_lr")
+        s.set_qp_rt(p)
+        solvers.append(s)
+    b = ipm.Batch(solvers)
+    for rep in range(2):
+        assert b.solve() == [ipm.IPM_OK] * len(probs)
+        for s, x in zip(solvers, ref):
+            assert np.array_equal(s.get()["x"], x)
+    b.close()
+    for s in solvers:
+        s.close()
