@@ -204,6 +204,71 @@ def run_operator_only(args):
     return 0
 
 
+def run_batch(args):
+    """The uneven batch: 64 RT-shaped QPs (n ~ U[2000, 40000], V = 4n, density U[0.2%, 1%],
+    n/2 constraint rows), FP32 operator storage with FP64 refinement and reductions, schedules
+    autotuned per instance, all solved by one graph launch; against the plain FP64 solver
+    running the same QPs one after another.  Prints one JSON line."""
+    import torch
+    from paper_2405_03584_gb300 import build, ipm, workloads as W
+    torch.cuda.set_device(0)
+    build.build()
+    count = args.batch_count
+    scale = args.batch_scale
+    t0 = time.perf_counter()
+    probs = W.rt_batch(count, seed=3, scale=scale)
+    t_gen = time.perf_counter() - t0
+    nnz = [int(p["D_indptr"][-1]) for p in probs]
+    t0 = time.perf_counter()
+    solvers = []
+    for p in probs:
+        sv = ipm.Solver(tol_kkt=TOL, precond="jacobi_lr", storage="f32", autotune=1)
+        sv.set_qp_rt(p)
+        solvers.append(sv)
+    t_load = time.perf_counter() - t0
+    b = ipm.Batch(solvers)
+    for _ in range(args.warmup):
+        st = b.solve()
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        st = b.solve()
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    infos = [sv.get()["info"] for sv in solvers]
+    b.close()
+    for sv in solvers:
+        sv.close()
+    # baseline: the plain FP64 solver, one QP at a time
+    seq_ms, seq_status = 0.0, []
+    for p in probs:
+        sv = ipm.Solver(tol_kkt=TOL, precond="jacobi_lr")
+        sv.set_qp_rt(p)
+        sv.solve()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        seq_status.append(sv.solve())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        seq_ms += e0.elapsed_time(e1)
+        sv.close()
+    out = {"mode": "batch", "metric": "QP solves/sec (64-QP uneven batch, rel. KKT <= 1e-6)",
+           "value": count / (ms / 1000.0), "unit": "solves/s", "ms_per_batch": ms, "steps": args.steps,
+           "warmup": args.warmup, "dtype": "f32 storage, f64 refinement and reductions",
+           "config": {"count": count, "scale": scale, "n": [p["n"] for p in probs], "nnz_total": int(sum(nnz)),
+                      "generator": "workloads.rt_batch(64, seed=3)"},
+           "status": [int(x) for x in st], "max_rel_kkt_device": max(i["rel_kkt"] for i in infos),
+           "ipm_iters": [i["ipm_iters"] for i in infos], "lanes": [[i["lanes_rows"], i["lanes_cols"]] for i in infos],
+           "baseline_sequential_f64": {"value": count / (seq_ms / 1000.0), "unit": "solves/s", "ms_total": seq_ms,
+                                       "status": [int(x) for x in seq_status]},
+           "speedup_vs_sequential_f64": seq_ms / ms, "setup_s": {"generate": t_gen, "load": t_load}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -341,6 +406,9 @@ def main():
     ap.add_argument("--operator-only", action="store_true",
                     help="profiler capture target: a few IPM iterations, then the operator kernels")
     ap.add_argument("--lanes", default="8,16", help="--operator-only: lanes per row over R and R^T")
+    ap.add_argument("--batch", action="store_true", help="the 64-QP uneven batch instead of the single RT QP")
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--batch-scale", type=float, default=1.0, help="scale every n of the batch (testing)")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every kernel directly (for per-kernel profilers; same kernels, slower)")
     args = ap.parse_args()
@@ -350,6 +418,8 @@ def main():
         return run_reference(args)
     if args.operator_only:
         return run_operator_only(args)
+    if args.batch:
+        return run_batch(args)
     return run_ours(args)
 
 
