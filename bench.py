@@ -269,6 +269,93 @@ def run_batch(args):
     return 0
 
 
+def _serve_once(plans, reqs, horizon, **kw):
+    from paper_2405_03584_gb300 import serve
+    srv = serve.Server(plans, **kw)
+    # one solve per plan handle before the clock starts (graph capture and instantiation)
+    for sl in srv.plan_slot:
+        sl.solver.solve(stream=sl.sid)
+    t0 = time.perf_counter()
+    qrec, rrec = srv.run(reqs)
+    wall = time.perf_counter() - t0
+    stats = dict(srv.stats)
+    srv.close()
+    summ = serve.latency_summary(qrec, rrec, horizon, stats["busy_s"])
+    summ.update(stats)
+    summ["wall_s"] = wall
+    return summ, qrec
+
+
+def run_serve(args):
+    """The serving workload: Poisson arrivals (lambda req/s) over a fixed horizon; 30 % of the
+    requests are chains of 20 related QPs (weights and cost perturbed by 1 % per step, each
+    warm-started from the previous solution), the rest single QPs; plans from the uneven
+    64-QP size mix; BF16 operator storage with FP64 refinement; admission against a 120 GB
+    HBM ledger with up to --serve-inflight solves in flight.  The baseline serves the same
+    stream with the plain FP64 solver, one solve at a time, cold starts.  One JSON line."""
+    import torch
+    from paper_2405_03584_gb300 import build, workloads as W
+    from oracle import kkt_check
+    torch.cuda.set_device(0)
+    build.build()
+    t0 = time.perf_counter()
+    plans = W.rt_batch(64, seed=3, scale=args.batch_scale)
+    t_gen = time.perf_counter() - t0
+    reqs = W.serving_stream(horizon=args.serve_horizon, lam=args.serve_lambda, chain_frac=0.3, chain_len=20,
+                            n_plans=len(plans), seed=4)
+    common = dict(budget_bytes=120e9, tol_kkt=TOL, precond="jacobi_lr")
+    t0 = time.perf_counter()
+    ours, qrec = _serve_once(plans, reqs, args.serve_horizon, max_inflight=args.serve_inflight, warm=True,
+                             keep_x=False, storage="bf16", **common)
+    t_ours = time.perf_counter() - t0
+    # independent check of sampled results (regenerated costs; the checker shares nothing with the GPU path)
+    rng = np.random.default_rng(0)
+    by_req = {r["rid"]: r for r in reqs}
+    checked = []
+    for rec in rng.choice(len(qrec), size=min(args.serve_check, len(qrec)), replace=False):
+        rec = qrec[int(rec)]
+        checked.append((rec["rid"], rec["step"]))
+    # re-solve the sampled QPs alone to get their iterates for the checker
+    from paper_2405_03584_gb300 import ipm
+    max_rk = 0.0
+    for rid, step in checked:
+        r = by_req[rid]
+        plan = plans[r["plan"]]
+        with ipm.Solver(storage="bf16", tol_kkt=TOL, precond="jacobi_lr") as sv:
+            sv.set_qp_rt(plan)
+            prev = None
+            for k in range(step + 1):
+                prev = W.request_costs(plan, r, prev)
+                sv.update_costs(f_w=prev[0], c=prev[1])
+                sv.solve(warm=k > 0)
+            out = sv.get()
+        pk = dict(plan)
+        pk["w"], pk["c"] = prev[0], prev[1]
+        max_rk = max(max_rk, kkt_check.rel_kkt(kkt_check.rt_ops(pk), out["x"], out["y"], out["zl"], out["zu"]))
+    base = None
+    if not args.serve_no_baseline:
+        t0 = time.perf_counter()
+        base, _ = _serve_once(plans, reqs, args.serve_horizon, max_inflight=1, warm=False, keep_x=False,
+                              storage="f64", **common)
+        base["run_s"] = time.perf_counter() - t0
+    out = {"mode": "serve", "metric": "QP solves/sec & p50/p99 latency at rel. KKT <=1e-6 (serving stream)",
+           "value": ours["solves_per_s"], "unit": "solves/s", "p50_ms": ours["p50_ms"], "p99_ms": ours["p99_ms"],
+           "dtype": "bf16 storage, f32 accumulate, f64 refinement and reductions",
+           "config": {"lambda": args.serve_lambda, "horizon_s": args.serve_horizon, "requests": len(reqs),
+                      "qps": sum(r["steps"] for r in reqs), "chain_frac": 0.3, "chain_len": 20,
+                      "plans": "workloads.rt_batch(64, seed=3, scale=%g)" % args.batch_scale,
+                      "stream": "workloads.serving_stream(seed=4)", "max_inflight": args.serve_inflight,
+                      "budget_bytes": 120e9},
+           "ours": ours, "checked_max_rel_kkt": max_rk, "checked": len(checked),
+           "baseline_f64_one_at_a_time": base,
+           "setup_s": {"generate": t_gen, "serve_run": t_ours}}
+    if base:
+        out["speedup_solves_per_s"] = ours["solves_per_s"] / base["solves_per_s"]
+        out["p99_ratio_baseline_over_ours"] = base["p99_ms"] / ours["p99_ms"]
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -409,6 +496,12 @@ def main():
     ap.add_argument("--batch", action="store_true", help="the 64-QP uneven batch instead of the single RT QP")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-scale", type=float, default=1.0, help="scale every n of the batch (testing)")
+    ap.add_argument("--serve", action="store_true", help="the serving stream (Poisson arrivals, chains, warm start)")
+    ap.add_argument("--serve-lambda", type=float, default=20.0)
+    ap.add_argument("--serve-horizon", type=float, default=60.0)
+    ap.add_argument("--serve-inflight", type=int, default=16)
+    ap.add_argument("--serve-check", type=int, default=6, help="results re-checked by the independent checker")
+    ap.add_argument("--serve-no-baseline", action="store_true")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every kernel directly (for per-kernel profilers; same kernels, slower)")
     args = ap.parse_args()
@@ -420,6 +513,10 @@ def main():
         return run_operator_only(args)
     if args.batch:
         return run_batch(args)
+    if args.serve:
+        # more hardware work queues than the default 8, so many slots' streams run side by side
+        os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+        return run_serve(args)
     return run_ours(args)
 
 

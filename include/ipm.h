@@ -102,6 +102,8 @@ typedef struct ipm_options {
                          /* FP64 residual (0.1)                                                */
   int lanes_rows;        /* lanes per row of the kernels over R (4, 8, 16, 32; 0 = automatic)   */
   int lanes_cols;        /* lanes per row of the kernels over R^T (same; overrides autotune)    */
+  double warm_rho;       /* IPM_WARM: complementarity pairs raised to >= warm_rho * mu0 of the  */
+                         /* last cold start (1e-5); 0 keeps the previous point as it is        */
 } ipm_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -208,6 +210,27 @@ int ipm_batch_destroy(ipm_batch* b);
  * x, z_l, z_u (n), y, s (m); fills *info if non-NULL. */
 int ipm_get_xyz(ipm_handle* h, double* x, double* y, double* z_l, double* z_u, double* s,
                 ipm_info* info, int mem, void* stream);
+
+/* Replaces the factor weights f_w (f_rows values) and/or the linear cost c (n values) of the
+ * loaded QP (NULL keeps the current one) without re-ingesting any matrix; diag(H) is updated.
+ * For SQP-like chains of related QPs (Section 3.2: each SQP iteration changes the QP's
+ * Hessian and cost, the constraints stay), followed by ipm_solve(..., IPM_WARM). */
+int ipm_update_costs(ipm_handle* h, const double* f_w, const double* c, int mem, void* stream);
+
+/* Loads into h the QP already loaded on src without copying its matrices: h references src's
+ * device copy of R, R^T (and its reduced-precision copies and dense H block), which stays
+ * alive until the last handle that uses it is destroyed or reloaded, and allocates only its
+ * own state (problem vectors, iterate, PCG and preconditioner work space; sizes in
+ * ipm_device_bytes).  c, f_w, b, l, u start as copies of src's and may then be changed with
+ * ipm_update_costs on either handle independently.  Both handles may solve at the same time.
+ * No counterpart in the paper: it lets several solves of one plan run concurrently (serving).
+ * Errors: IPM_ERR_STATE (src has no QP, or h has a solve in flight), IPM_ERR_ARG (different
+ * devices, or h's storage option differs from src's), IPM_ERR_OOM. */
+int ipm_share_qp(ipm_handle* h, ipm_handle* src, void* stream);
+
+/* Device bytes held by the handle: the matrix store (possibly shared; matrix_refs = number of
+ * handles referencing it) and the handle's own state.  Any output may be NULL. */
+int ipm_device_bytes(const ipm_handle* h, int64_t* matrix_bytes, int64_t* state_bytes, int* matrix_refs);
 
 /* Frees the handle and its device memory.  NULL-safe. */
 int ipm_destroy(ipm_handle* h);

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <chrono>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <tuple>
 #include <cmath>
@@ -57,6 +58,25 @@ int count_kernel_nodes(cudaGraph_t g) {
   return k;
 }
 
+// Read-only device copy of a QP's matrices.  Handles that share a QP hold a reference; the
+// memory is freed with the last one.
+struct MatStore {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  int device = 0;
+  int storage = 0;
+  std::vector<int64_t> sc_prefix;   // entries of the k longest constraint rows, k = 0..min(m, 1024)
+  ~MatStore() {
+    if (ptr) {
+      int cur = 0;
+      cudaGetDevice(&cur);
+      cudaSetDevice(device);
+      cudaFree(ptr);
+      cudaSetDevice(cur);
+    }
+  }
+};
+
 }  // namespace
 
 struct ipm_handle {
@@ -64,8 +84,9 @@ struct ipm_handle {
   int device = 0;
   cudaStream_t st = nullptr, st2 = nullptr, st3 = nullptr, st4 = nullptr;
   cudaEvent_t ev = nullptr;
-  void* arena = nullptr;
+  void* arena = nullptr;             // per-handle state: iterate, PCG and preconditioner work
   size_t arena_bytes = 0;
+  std::shared_ptr<MatStore> mat;    // matrices (R, R^T, H block, reduced copies); shared by ipm_share_qp
   Dev d{};
   Geo g{};
   Scal* hs = nullptr;               // pinned host copy of the device scalars
@@ -77,6 +98,7 @@ struct ipm_handle {
   double cnorm = 0, bnorm = 0;
   int ncomp = 0;
   int64_t sc_cap = 0;
+  bool f_acsr = false;              // constraint rows appended to R as an explicit CSR block
   std::vector<double> trace;        // IPM_TRACE_COLS doubles per IPM iteration of the last solve
   double* htrace = nullptr;         // pinned: trace rows copied back after a solve
   int trace_cap = 0;
@@ -134,6 +156,7 @@ void free_arena(ipm_handle* h) {
   if (h->arena) cudaFree(h->arena);
   h->arena = nullptr;
   h->arena_bytes = 0;
+  h->mat.reset();
   h->loaded = h->have_iterate = false;
   h->d = Dev{};
 }
@@ -161,19 +184,30 @@ struct HostQP {
   std::vector<unsigned char> fl, fu;
 };
 
-void carve(Carver& cv, Dev& d, const HostQP& q, int stiff_cap, int64_t sc_cap, bool dense, int storage, int trace_cap) {
-  d.n = q.n; d.m = q.m; d.nR = q.nR;
-  d.nnzR = (int64_t)q.Rv.size();
-  d.nnzHs = (int64_t)q.Hv.size();
-  const int64_t n = q.n, m = q.m, nR = q.nR;
-  d.R_ptr = cv.take<int64_t>(nR + 1); d.R_idx = cv.take<int32_t>(d.nnzR); d.R_val = cv.take<double>(d.nnzR);
-  d.RT_ptr = cv.take<int64_t>(n + 1); d.RT_idx = cv.take<int32_t>(d.nnzR); d.RT_val = cv.take<double>(d.nnzR);
-  if (d.nnzHs) {
-    d.Hs_ptr = cv.take<int64_t>(n + 1); d.Hs_idx = cv.take<int32_t>(d.nnzHs); d.Hs_val = cv.take<double>(d.nnzHs);
+// Matrix part of the device layout (shared between handles that share a QP).
+void carve_matrix(Carver& cv, Dev& d, int64_t n, int64_t m, int64_t nR, int64_t nnzR, int64_t nnzHs, int storage) {
+  d.R_ptr = cv.take<int64_t>(nR + 1); d.R_idx = cv.take<int32_t>(nnzR); d.R_val = cv.take<double>(nnzR);
+  d.RT_ptr = cv.take<int64_t>(n + 1); d.RT_idx = cv.take<int32_t>(nnzR); d.RT_val = cv.take<double>(nnzR);
+  if (nnzHs) {
+    d.Hs_ptr = cv.take<int64_t>(n + 1); d.Hs_idx = cv.take<int32_t>(nnzHs); d.Hs_val = cv.take<double>(nnzHs);
   } else {
     d.Hs_ptr = nullptr; d.Hs_idx = nullptr; d.Hs_val = nullptr;
   }
   d.arow = cv.take<int32_t>(m);
+  if (storage != ST_F64) {
+    const size_t vb = storage == ST_F32 ? 4 : (storage == ST_BF16 ? 2 : 1);
+    d.Rq = cv.take<unsigned char>((int64_t)vb * nnzR);
+    d.RTq = cv.take<unsigned char>((int64_t)vb * nnzR);
+    d.scaleR = cv.take<float>(nR);
+  } else {
+    d.Rq = d.RTq = nullptr;
+    d.scaleR = nullptr;
+  }
+}
+
+// Per-handle part: problem vectors (costs may change per handle), iterate and work space.
+void carve_state(Carver& cv, Dev& d, int64_t n, int64_t m, int64_t nR, int stiff_cap, int64_t sc_cap, bool dense,
+                 int storage, int trace_cap) {
   d.wR = cv.take<double>(nR); d.h0 = cv.take<double>(n); d.c = cv.take<double>(n); d.b = cv.take<double>(m);
   d.l = cv.take<double>(n); d.u = cv.take<double>(n);
   d.fl = cv.take<unsigned char>(n); d.fu = cv.take<unsigned char>(n);
@@ -198,21 +232,45 @@ void carve(Carver& cv, Dev& d, const HostQP& q, int stiff_cap, int64_t sc_cap, b
   d.chol_diag = cv.take<double>(std::max<int64_t>(dense ? n : 0, stiff_cap));
   d.storage = storage;
   if (storage != ST_F64) {
-    const size_t vb = storage == ST_F32 ? 4 : (storage == ST_BF16 ? 2 : 1);
-    d.Rq = cv.take<unsigned char>((int64_t)vb * d.nnzR);
-    d.RTq = cv.take<unsigned char>((int64_t)vb * d.nnzR);
-    d.scaleR = cv.take<float>(nR);
     d.p32 = cv.take<float>(n);
     d.w32 = cv.take<float>(nR);
     d.dxr = cv.take<double>(n);
   } else {
-    d.Rq = d.RTq = nullptr;
-    d.scaleR = d.p32 = d.w32 = nullptr;
+    d.p32 = d.w32 = nullptr;
     d.dxr = nullptr;
   }
   d.trace = cv.take<double>((int64_t)trace_cap * kTraceCols);
   d.partials = cv.take<double>(32 * (int64_t)kMaxRedBlocks);
   d.sc = cv.take<Scal>(1);
+}
+
+// Stiff-row capacity of a handle and the matching capacity of the stiff CSC lists.
+void stiff_caps(const ipm_options& o, int64_t m, const std::vector<int64_t>& sc_prefix, int* stiff_cap,
+                int64_t* sc_cap) {
+  *stiff_cap = std::max(1, std::min<int>(o.stiff_max > 0 ? o.stiff_max : 1, (int)std::max<int64_t>(m, 1)));
+  const int64_t k = std::min<int64_t>(*stiff_cap, (int64_t)sc_prefix.size() - 1);
+  *sc_cap = std::max<int64_t>(k > 0 ? sc_prefix[k] : 0, 1);
+}
+
+// One device allocation; IPM_ERR_OOM with a message on failure.
+int dev_alloc(ipm_handle* h, void** p, size_t bytes, const char* what) {
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(h, IPM_ERR_OOM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes (" + what + ") failed");
+  }
+  return IPM_OK;
+}
+
+// Pinned trace buffer for the rows copied back after each solve.
+int alloc_trace(ipm_handle* h) {
+  h->trace_cap = h->opt.max_ipm;
+  if (cudaMallocHost(&h->htrace, sizeof(double) * kTraceCols * (size_t)h->trace_cap) != cudaSuccess) {
+    cudaGetLastError();
+    h->htrace = nullptr;
+    return fail(h, IPM_ERR_OOM, "pinned trace buffer");
+  }
+  return IPM_OK;
 }
 
 int validate_options(const ipm_options& o) {
@@ -221,6 +279,7 @@ int validate_options(const ipm_options& o) {
   if (o.precond < 0 || o.precond > 3 || o.stiff_max < 0 || o.stiff_max > 1024) return IPM_ERR_ARG;
   if (o.dense_max_n < 0 || o.dense_max_n > 2048 || !(o.stiff_gamma > 0)) return IPM_ERR_ARG;
   if (o.storage < 0 || o.storage > 3 || o.refine_max < 1 || !(o.refine_eta > 0 && o.refine_eta < 1)) return IPM_ERR_ARG;
+  if (!(o.warm_rho >= 0 && o.warm_rho < 1)) return IPM_ERR_ARG;
   auto lanes_ok = [](int g) { return g == 0 || g == 4 || g == 8 || g == 16 || g == 32; };
   if (!lanes_ok(o.lanes_rows) || !lanes_ok(o.lanes_cols)) return IPM_ERR_ARG;
   return IPM_OK;
@@ -563,6 +622,7 @@ int push_options(ipm_handle* h) {
   s.equal_steps = h->opt.equal_steps;
   s.refine_max = h->opt.refine_max;
   s.refine_eta = h->opt.refine_eta;
+  s.warm_rho = h->opt.warm_rho;
   s.cnorm = h->cnorm;
   s.bnorm = h->bnorm;
   s.ncomp = h->ncomp;
@@ -618,6 +678,7 @@ void ipm_default_options(ipm_options* o) {
   o->refine_eta = 0.1;
   o->lanes_rows = 0;
   o->lanes_cols = 0;
+  o->warm_rho = 1e-5;
 }
 
 const char* ipm_status_str(int s) {
@@ -668,6 +729,31 @@ int ipm_create(const ipm_options* opt, ipm_handle** out) {
   std::memset(h->hs, 0, sizeof(Scal));
   *out = h;
   return IPM_OK;
+}
+
+int ipm_update_costs(ipm_handle* h, const double* f_w, const double* c, int mem, void* stream) {
+  if (!h) return IPM_ERR_ARG;
+  if (!h->loaded) return fail(h, IPM_ERR_STATE, "ipm_update_costs before ipm_set_qp");
+  if (h->pending) return fail(h, IPM_ERR_STATE, "a solve is in flight on this handle");
+  int rc;
+  const Dev& d = h->d;
+  const int64_t fr = h->d.nR - (h->f_acsr ? h->d.m : 0);
+  std::vector<double> hw, hc;
+  if (f_w && (rc = fetch(h, f_w, fr, mem, hw))) return rc;
+  if (c && (rc = fetch(h, c, d.n, mem, hc))) return rc;
+  for (double v : hw) if (!std::isfinite(v) || v < 0) return fail(h, IPM_ERR_ARG, "f_w must be finite and >= 0");
+  double cn = h->cnorm;
+  if (c) {
+    cn = 0;
+    for (double v : hc) { if (!std::isfinite(v)) return fail(h, IPM_ERR_ARG, "c not finite"); cn = std::max(cn, std::fabs(v)); }
+  }
+  if ((rc = enter(h, stream))) return rc;
+  if (f_w && fr) CUDA_TRY(h, cudaMemcpyAsync((void*)d.wR, hw.data(), 8 * fr, cudaMemcpyHostToDevice, h->st));
+  if (c) CUDA_TRY(h, cudaMemcpyAsync((void*)d.c, hc.data(), 8 * d.n, cudaMemcpyHostToDevice, h->st));
+  if (f_w) CUDA_TRY(h, launch_diagH(d, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));   // host staging buffers go out of scope
+  h->cnorm = cn;
+  return leave(h, stream);
 }
 
 int ipm_destroy(ipm_handle* h) {
@@ -808,13 +894,20 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   for (double v : q.c) cn = std::max(cn, std::fabs(v));
   for (double v : q.b) bn = std::max(bn, std::fabs(v));
   // stiff-row capacity: the stiff_cap longest constraint rows
-  const int stiff_cap = std::max(1, std::min<int>(h->opt.stiff_max > 0 ? h->opt.stiff_max : 1, (int)std::max<int64_t>(m, 1)));
-  std::vector<int64_t> lens(m);
-  for (int64_t k = 0; k < m; ++k) lens[k] = q.Rp[q.arow[k] + 1] - q.Rp[q.arow[k]];
-  std::sort(lens.begin(), lens.end(), std::greater<int64_t>());
-  int64_t sc_cap = 0;
-  for (int64_t k = 0; k < std::min<int64_t>(m, stiff_cap); ++k) sc_cap += lens[k];
-  sc_cap = std::max<int64_t>(sc_cap, 1);
+  auto store = std::make_shared<MatStore>();
+  store->device = h->device;
+  store->storage = h->opt.storage;
+  {
+    std::vector<int64_t> lens(m);
+    for (int64_t k = 0; k < m; ++k) lens[k] = q.Rp[q.arow[k] + 1] - q.Rp[q.arow[k]];
+    std::sort(lens.begin(), lens.end(), std::greater<int64_t>());
+    const int64_t kmax = std::min<int64_t>(m, 1024);
+    store->sc_prefix.assign(kmax + 1, 0);
+    for (int64_t k = 0; k < kmax; ++k) store->sc_prefix[k + 1] = store->sc_prefix[k] + lens[k];
+  }
+  int stiff_cap = 1;
+  int64_t sc_cap = 1;
+  stiff_caps(h->opt, m, store->sc_prefix, &stiff_cap, &sc_cap);
   const bool dense = h->opt.dense_max_n > 0 && n <= h->opt.dense_max_n &&
                      (h->opt.precond == IPM_PRECOND_DENSE || h->opt.precond == IPM_PRECOND_AUTO);
   // allocate
@@ -822,19 +915,22 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
   free_arena(h);
   Dev dv{};
-  Carver cnt(nullptr);
-  carve(cnt, dv, q, stiff_cap, sc_cap, dense, h->opt.storage, h->opt.max_ipm);
-  const size_t bytes = cnt.off + 256;
-  if (h->opt.mem_budget > 0 && (double)bytes > h->opt.mem_budget)
-    return fail(h, IPM_ERR_OOM, "QP needs " + std::to_string(bytes) + " bytes, over mem_budget");
-  if (cudaMalloc(&h->arena, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    h->arena = nullptr;
-    return fail(h, IPM_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
-  }
-  h->arena_bytes = bytes;
-  Carver cv((char*)h->arena);
-  carve(cv, dv, q, stiff_cap, sc_cap, dense, h->opt.storage, h->opt.max_ipm);
+  const int64_t nnzR = (int64_t)q.Rv.size(), nnzHs = (int64_t)q.Hv.size();
+  Carver cm(nullptr), cs(nullptr);
+  carve_matrix(cm, dv, n, m, q.nR, nnzR, nnzHs, h->opt.storage);
+  carve_state(cs, dv, n, m, q.nR, stiff_cap, sc_cap, dense, h->opt.storage, h->opt.max_ipm);
+  const size_t mbytes = cm.off + 256, sbytes = cs.off + 256;
+  if (h->opt.mem_budget > 0 && (double)(mbytes + sbytes) > h->opt.mem_budget)
+    return fail(h, IPM_ERR_OOM, "QP needs " + std::to_string(mbytes + sbytes) + " bytes, over mem_budget");
+  if ((rc = dev_alloc(h, &store->ptr, mbytes, "matrices"))) return rc;
+  store->bytes = mbytes;
+  if ((rc = dev_alloc(h, &h->arena, sbytes, "state"))) return rc;
+  h->arena_bytes = sbytes;
+  h->mat = store;
+  Carver cvm((char*)store->ptr), cvs((char*)h->arena);
+  carve_matrix(cvm, dv, n, m, q.nR, nnzR, nnzHs, h->opt.storage);
+  carve_state(cvs, dv, n, m, q.nR, stiff_cap, sc_cap, dense, h->opt.storage, h->opt.max_ipm);
+  dv.n = n; dv.m = m; dv.nR = q.nR; dv.nnzR = nnzR; dv.nnzHs = nnzHs;
   CUDA_TRY(h, cudaDeviceGetAttribute(&dv.sm_count, cudaDevAttrMultiProcessorCount, h->device));
   dv.g_rows = heuristic_group(q.nR ? (double)q.Rv.size() / (double)q.nR : 0.0);
   dv.g_cols = heuristic_group((double)q.Rv.size() / (double)n);
@@ -842,13 +938,9 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   if (h->opt.lanes_cols) dv.g_cols = h->opt.lanes_cols;
   h->d = dv;
   h->g = make_geo(dv);
-  h->trace_cap = h->opt.max_ipm;
-  if (cudaMallocHost(&h->htrace, sizeof(double) * kTraceCols * (size_t)h->trace_cap) != cudaSuccess) {
-    cudaGetLastError();
-    h->htrace = nullptr;
-    return fail(h, IPM_ERR_OOM, "pinned trace buffer");
-  }
+  if ((rc = alloc_trace(h))) return rc;
   h->cnorm = cn; h->bnorm = bn; h->ncomp = ncomp; h->sc_cap = sc_cap;
+  h->f_acsr = use_acsr;
   if ((rc = enter(h, stream))) return rc;
   auto up = [&](const void* dst, const void* src, size_t nbytes) -> int {
     if (nbytes == 0) return IPM_OK;
@@ -892,6 +984,85 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   h->precond = choose_precond(h);
   h->info = ipm_info{};
   return leave(h, stream);
+}
+
+int ipm_share_qp(ipm_handle* h, ipm_handle* src, void* stream) {
+  if (!h || !src || h == src) return IPM_ERR_ARG;
+  if (h->pending) return fail(h, IPM_ERR_STATE, "a solve is in flight on this handle");
+  if (!src->loaded || !src->mat) return fail(h, IPM_ERR_STATE, "source handle has no QP");
+  if (src->device != h->device) return fail(h, IPM_ERR_ARG, "handles on different devices");
+  if (src->opt.storage != h->opt.storage) return fail(h, IPM_ERR_ARG, "storage option differs from the source's");
+  h->err.clear();
+  int rc;
+  const Dev& sd = src->d;
+  const int64_t n = sd.n, m = sd.m, nR = sd.nR;
+  int stiff_cap = 1;
+  int64_t sc_cap = 1;
+  stiff_caps(h->opt, m, src->mat->sc_prefix, &stiff_cap, &sc_cap);
+  const bool use_dense = h->opt.dense_max_n > 0 && n <= h->opt.dense_max_n &&
+                         (h->opt.precond == IPM_PRECOND_DENSE || h->opt.precond == IPM_PRECOND_AUTO);
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  auto store = src->mat;            // keep the matrices alive before dropping our own
+  free_arena(h);
+  Dev dv = sd;                      // sizes, lane choices and matrix pointers of the source
+  Carver cs(nullptr);
+  carve_state(cs, dv, n, m, nR, stiff_cap, sc_cap, use_dense, h->opt.storage, h->opt.max_ipm);
+  const size_t sbytes = cs.off + 256;
+  if (h->opt.mem_budget > 0 && (double)sbytes > h->opt.mem_budget)
+    return fail(h, IPM_ERR_OOM, "state needs " + std::to_string(sbytes) + " bytes, over mem_budget");
+  if ((rc = dev_alloc(h, &h->arena, sbytes, "state"))) return rc;
+  h->arena_bytes = sbytes;
+  h->mat = store;
+  Carver cvs((char*)h->arena);
+  carve_state(cvs, dv, n, m, nR, stiff_cap, sc_cap, use_dense, h->opt.storage, h->opt.max_ipm);
+  if (h->opt.lanes_rows) dv.g_rows = h->opt.lanes_rows;
+  if (h->opt.lanes_cols) dv.g_cols = h->opt.lanes_cols;
+  h->d = dv;
+  h->g = make_geo(dv);
+  if ((rc = alloc_trace(h))) return rc;
+  h->cnorm = src->cnorm; h->bnorm = src->bnorm; h->ncomp = src->ncomp; h->sc_cap = sc_cap;
+  h->f_acsr = src->f_acsr;
+  // the source's problem vectors, ordered after its own stream and the caller's
+  CUDA_TRY(h, cudaEventRecord(src->ev, src->st));
+  CUDA_TRY(h, cudaStreamWaitEvent(h->st, src->ev, 0));
+  if ((rc = enter(h, stream))) return rc;
+  const Dev& d = h->d;
+  auto cp = [&](const void* dst, const void* from, size_t nbytes) -> int {
+    if (nbytes == 0) return IPM_OK;
+    CUDA_TRY(h, cudaMemcpyAsync((void*)dst, from, nbytes, cudaMemcpyDeviceToDevice, h->st));
+    return IPM_OK;
+  };
+  if ((rc = cp(d.wR, sd.wR, 8 * nR))) return rc;
+  if ((rc = cp(d.h0, sd.h0, 8 * n))) return rc;
+  if ((rc = cp(d.c, sd.c, 8 * n))) return rc;
+  if ((rc = cp(d.b, sd.b, 8 * m))) return rc;
+  if ((rc = cp(d.l, sd.l, 8 * n))) return rc;
+  if ((rc = cp(d.u, sd.u, 8 * n))) return rc;
+  if ((rc = cp(d.fl, sd.fl, n))) return rc;
+  if ((rc = cp(d.fu, sd.fu, n))) return rc;
+  if ((rc = cp(d.diagH, sd.diagH, 8 * n))) return rc;
+  CUDA_TRY(h, cudaMemsetAsync(d.hist, 0, sizeof(unsigned int) * kHistBins, h->st));
+  CUDA_TRY(h, cudaMemsetAsync(d.slotR, 0xff, sizeof(int32_t) * std::max<int64_t>(nR, 1), h->st));
+  std::memset(h->hs, 0, sizeof(Scal));
+  push_options(h);
+  h->hs->mu = h->hs->mu0 = 1.0;
+  h->hs->status = DS_RUNNING;
+  CUDA_TRY(h, cudaMemcpyAsync(d.sc, h->hs, sizeof(Scal), cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  h->loaded = true;
+  h->have_iterate = false;
+  h->precond = choose_precond(h);
+  h->info = ipm_info{};
+  return leave(h, stream);
+}
+
+int ipm_device_bytes(const ipm_handle* h, int64_t* matrix_bytes, int64_t* state_bytes, int* matrix_refs) {
+  if (!h) return IPM_ERR_ARG;
+  if (matrix_bytes) *matrix_bytes = h->mat ? (int64_t)h->mat->bytes : 0;
+  if (state_bytes) *state_bytes = (int64_t)h->arena_bytes;
+  if (matrix_refs) *matrix_refs = h->mat ? (int)h->mat.use_count() : 0;
+  return IPM_OK;
 }
 
 }  // extern "C"

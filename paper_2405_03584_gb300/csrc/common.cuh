@@ -37,6 +37,8 @@ struct Scal {
   int n_stiff, stiff_max, max_stiff_seen, chol_fail;
   // FP64 refinement of a reduced-precision Newton step
   double tol2_outer, rr_outer, refine_eta;
+  // warm start: pairs raised to at least warm_rho * mu0_cold (mu0 of the last cold start)
+  double mu0_cold, warm_rho;
   int refine_it, refine_max, cg_step_total, cg_conv_outer, fallback, fallback_total;
   // totals of one solve (device-side IPM loop)
   long long cg_total;

@@ -333,6 +333,7 @@ __global__ void k_start_mu(Dev d) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     Scal* sc = d.sc;
     sc->mu0 = sc->comp_mean > 0.0 ? sc->comp_mean : 1.0;
+    sc->mu0_cold = sc->mu0;
     sc->mu = sc->mu0;
     sc->ipm_iter = 0;
     sc->stop = 0;
@@ -436,7 +437,29 @@ __global__ void k_warm_mu(Dev d) {
   set_eta(sc);
 }
 
+// Warm start (reading; the paper warm-starts the SQP's QPs, Section 3.2, without a recipe):
+// every complementarity pair of the previous solution is raised to at least
+// mu_w = warm_rho * mu0_cold (mu0 of the last cold start on this handle): s and y scaled
+// together by sqrt(mu_w / (s y)), z_l, z_u raised to mu_w / t.  No shift before a cold start.
+__global__ void k_warm_shift(Dev d) {
+  const double muw = d.sc->warm_rho * d.sc->mu0_cold;
+  if (!(muw > 0.0)) return;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.m; k += (int64_t)gridDim.x * blockDim.x) {
+    const double sy = d.s[k] * d.y[k];
+    if (sy < muw) {
+      const double f = sqrt(muw / fmax(sy, 1e-300));
+      d.s[k] *= f;
+      d.y[k] *= f;
+    }
+  }
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x) {
+    if (d.fl[j]) d.zl[j] = fmax(d.zl[j], muw / (d.x[j] - d.l[j]));
+    if (d.fu[j]) d.zu[j] = fmax(d.zu[j], muw / (d.u[j] - d.x[j]));
+  }
+}
+
 cudaError_t launch_warm_start(const Dev& d, const Geo& g, cudaStream_t st) {
+  k_warm_shift<<<std::max(g.eN, g.eM), kBlock, 0, st>>>(d);
   cudaError_t e = launch_residual_summary(d, g, st);
   if (e != cudaSuccess) return e;
   k_warm_mu<<<1, 32, 0, st>>>(d);

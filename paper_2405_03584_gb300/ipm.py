@@ -30,7 +30,8 @@ EXPORTS = ["ipm_default_options", "ipm_create", "ipm_set_qp", "ipm_solve", "ipm_
            "ipm_status_str", "ipm_last_error", "ipm_set_iterate", "ipm_residuals", "ipm_apply_kkt",
            "ipm_precond_diag", "ipm_newton_direction", "ipm_step_lengths", "ipm_profile_operator",
            "ipm_get_trace", "ipm_apply_operator_static", "ipm_solve_async", "ipm_solve_wait", "ipm_solve_query",
-           "ipm_batch_create", "ipm_batch_solve", "ipm_batch_destroy"]
+           "ipm_batch_create", "ipm_batch_solve", "ipm_batch_destroy", "ipm_update_costs", "ipm_share_qp",
+           "ipm_device_bytes"]
 TRACE_COLS = ("iter", "mu", "rel_kkt", "primal", "dual", "gap", "alpha_p", "alpha_d", "pcg_iters", "pcg_converged",
               "stiff_rows", "pcg_rel_residual", "eta", "refine_passes")
 
@@ -42,7 +43,7 @@ class Options(C.Structure):
                 ("dense_max_n", C.c_int), ("timeout_ms", C.c_double), ("mem_budget", C.c_double),
                 ("equal_steps", C.c_int), ("autotune", C.c_int), ("use_graphs", C.c_int),
                 ("storage", C.c_int), ("refine_max", C.c_int), ("refine_eta", C.c_double),
-                ("lanes_rows", C.c_int), ("lanes_cols", C.c_int)]
+                ("lanes_rows", C.c_int), ("lanes_cols", C.c_int), ("warm_rho", C.c_double)]
 
 
 class QP(C.Structure):
@@ -108,6 +109,9 @@ def load(path: str = LIB_PATH):
         "ipm_batch_create": (I, [C.POINTER(P), I, I, C.POINTER(P)]),
         "ipm_batch_solve": (I, [P, P, C.POINTER(C.c_int)]),
         "ipm_batch_destroy": (I, [P]),
+        "ipm_update_costs": (I, [P, P, P, I, P]),
+        "ipm_share_qp": (I, [P, P, P]),
+        "ipm_device_bytes": (I, [P, P, P, P]),
         "ipm_apply_operator_static": (I, [C.c_int64, C.c_int64] + [P] * 10 + [P]),
     }
     for name, (res, args) in sig.items():
@@ -261,6 +265,24 @@ class Solver:
         return self.set_qp(p["n"], p["m"], p["c"], p["b"], p["l"], p["u"], h0=p["h0"],
                            F=(p["D_indptr"], p["D_indices"], p["D_data"]), f_w=p["w"],
                            a_rows=p["a_rows"] if p["m"] else None, stream=stream)
+
+    def update_costs(self, f_w=None, c=None, stream=None):
+        """New factor weights and/or linear cost for the loaded QP (matrices unchanged)."""
+        mk = _Marshal(MEM_HOST)
+        self._check(load().ipm_update_costs(self._h, mk.ptr(f_w, np.float64), mk.ptr(c, np.float64), MEM_HOST,
+                                            _default_stream(stream)), "ipm_update_costs")
+
+    def share_qp(self, src, stream=None):
+        """Loads the QP of Solver ``src`` without copying its matrices (own state only)."""
+        self._check(load().ipm_share_qp(self._h, src._h, _default_stream(stream)), "ipm_share_qp")
+        self.n, self.m = src.n, src.m
+        return self
+
+    def device_bytes(self):
+        """dict(matrix, state, matrix_refs): device bytes of the matrix store and of this handle's state."""
+        mb, sb, refs = C.c_int64(), C.c_int64(), C.c_int()
+        self._check(load().ipm_device_bytes(self._h, C.byref(mb), C.byref(sb), C.byref(refs)), "ipm_device_bytes")
+        return dict(matrix=mb.value, state=sb.value, matrix_refs=refs.value)
 
     # ---------------------------------------------------------------- solve
     def solve(self, warm=False, stream=None):

@@ -27,7 +27,7 @@ import numpy as np
 
 __all__ = [
     "dense_qp", "rt_qp", "rt_batch_sizes", "rt_batch", "perturb_chain_step",
-    "csr_to_dense", "random_iterate",
+    "serving_stream", "request_costs", "csr_to_dense", "random_iterate",
 ]
 
 
@@ -168,6 +168,35 @@ def perturb_chain_step(qp: dict, rng: np.random.Generator, rel: float = 0.01) ->
     q["w"] = np.maximum(q["w"], 1e-6)
     q["c"] = qp["c"] * (1.0 + rel * rng.normal(size=qp["c"].shape))
     return q
+
+
+def serving_stream(horizon: float = 60.0, lam: float = 20.0, chain_frac: float = 0.3, chain_len: int = 20,
+                   n_plans: int = 64, seed: int = 4) -> list[dict]:
+    """Request stream of the serving workload: Poisson arrivals of rate ``lam`` over
+    ``horizon`` seconds; each request names a plan (uniform over ``n_plans``) and is a single
+    QP or, with probability ``chain_frac``, an SQP-like chain of ``chain_len`` related QPs.
+    Each request carries its own seed for the cost perturbations of its QPs."""
+    rng = np.random.default_rng(seed)
+    out, t, rid = [], 0.0, 0
+    while True:
+        t += rng.exponential(1.0 / lam)
+        if t >= horizon:
+            break
+        steps = chain_len if rng.random() < chain_frac else 1
+        out.append(dict(rid=rid, t=t, plan=int(rng.integers(n_plans)), steps=steps,
+                        seed=int(rng.integers(2**62))))
+        rid += 1
+    return out
+
+
+def request_costs(plan: dict, req: dict, prev: tuple | None = None, rel: float = 0.01) -> tuple:
+    """(f_w, c) of a request's next QP: the first from the plan's own, each later one from
+    the previous QP of the chain, by ``perturb_chain_step`` with a generator keyed by the
+    request's seed and the step, so any step can be regenerated alone."""
+    step = 0 if prev is None else prev[2] + 1
+    base = dict(w=plan["w"], c=plan["c"]) if prev is None else dict(w=prev[0], c=prev[1])
+    q = perturb_chain_step(base, np.random.default_rng([req["seed"], step]), rel)
+    return q["w"], q["c"], step
 
 
 def csr_to_dense(indptr, indices, data, shape):
