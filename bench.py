@@ -371,7 +371,8 @@ def run_ours(args):
     build.build()
     dev = torch.cuda.current_device()
     p = W.rt_qp(n=N_FULL, seed=SEED)
-    s = ipm.Solver(tol_kkt=TOL, precond="jacobi_lr", use_graphs=0 if args.no_graphs else 1, autotune=1)
+    s = ipm.Solver(tol_kkt=TOL, precond="jacobi_lr", use_graphs=0 if args.no_graphs else 1, autotune=1,
+                   storage=args.storage)
     s.set_qp_rt(p)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -439,7 +440,7 @@ def run_ours(args):
         for k in range(args.e2e_steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            se = ipm.Solver(tol_kkt=TOL, precond="jacobi_lr")
+            se = ipm.Solver(tol_kkt=TOL, precond="jacobi_lr", storage=args.storage)
             se.set_qp_rt(q)
             se.solve()
             se.get()
@@ -466,8 +467,11 @@ def run_ours(args):
         p99 = lat_sorted[min(len(lat_sorted) - 1, int(np.ceil(0.99 * len(lat_sorted))) - 1)]
         out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-               "config": {"workload": WORKLOAD, "n": p["n"], "V": p["V"], "m": p["m"], "nnz_D": int(p["D_indptr"][-1]),
+               "scaling": "weak", "vs_baseline": None,
+               "dtype": "f64" if args.storage == "f64" else
+                        "%s operator storage, f32 accumulate, f64 refinement and reductions" % args.storage,
+               "data": "synthetic",
+               "config": {"workload": WORKLOAD, "storage": args.storage, "n": p["n"], "V": p["V"], "m": p["m"], "nnz_D": int(p["D_indptr"][-1]),
                           "tol_kkt": TOL, "precond": "jacobi_lr", "parallelism": "replicas" if world > 1 else "single",
                           "l2": "no flush: operator working set (~1.2 GB) > 129 MB L2"},
                "latency_ms": {"p50": statistics.median(lat), "p99": p99, "mean": statistics.mean(lat)},
@@ -502,6 +506,8 @@ def main():
     ap.add_argument("--serve-inflight", type=int, default=16)
     ap.add_argument("--serve-check", type=int, default=6, help="results re-checked by the independent checker")
     ap.add_argument("--serve-no-baseline", action="store_true")
+    ap.add_argument("--storage", choices=["f64", "f32", "bf16", "fp8"], default="f64",
+                    help="operator storage of the single RT QP (reduced ones add FP64 refinement)")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every kernel directly (for per-kernel profilers; same kernels, slower)")
     args = ap.parse_args()
