@@ -416,11 +416,14 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     achieved = byts / (ms / 1000.0) / 1e9
     lanes = infos[-1]["lanes_rows"] if kern == "k_op_rows" else infos[-1]["lanes_cols"]
-    roof = {"bound": "hbm", "kernel": "%s<%d lanes/row>" % (kern, lanes), "achieved": achieved, "peak": peak,
-            "unit": "GB/s", "frac": achieved / peak, "traffic": _ncu_traffic(kern, lanes),
+    lp = args.storage != "f64"
+    kname = "%s_lp<%s, %d lanes/row>" % (kern, args.storage, lanes) if lp else "%s<%d lanes/row>" % (kern, lanes)
+    roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": None if lp else _ncu_traffic(kern, lanes),
             "peak_kind": peak_kind + " hbm_gbs",
             "algorithmic_bytes": byts, "ms_per_launch": ms,
-            "fp64_tflops": flops / (ms / 1000.0) / 1e12, "fp64_nominal_tflops": FP64_NOMINAL_TFLOPS,
+            ("fp32_tflops" if lp else "fp64_tflops"): flops / (ms / 1000.0) / 1e12,
+            "fp64_nominal_tflops": FP64_NOMINAL_TFLOPS,
             "other_kernel": {"ms_per_launch": prof["ms_" + ("cols" if key == "rows" else "rows")],
                              "gbs": prof["bytes_" + ("cols" if key == "rows" else "rows")] /
                              (prof["ms_" + ("cols" if key == "rows" else "rows")] / 1000.0) / 1e9}}

@@ -288,9 +288,11 @@ int ipm_get_trace(const ipm_handle* h, double* buf, int max_rows);
 /* Measurement hook for the PCG operator (Section 4.1.1's matvec, the loop that Section 5.1.2
  * finds to take most of the run time): at the current iterate, launches the row-gather kernel
  * over R and the gather over the stored transpose `reps` times each on the library's stream,
- * timed with CUDA events around every launch.  Returns the mean milliseconds per launch and
- * the algorithmic bytes and flops of one launch of each kernel (bytes: every matrix value,
- * index and row pointer once, every dense vector once; flops: 2 per stored non-zero).
+ * timed with CUDA events around every launch: the FP64 kernels for IPM_STORAGE_F64, else the
+ * reduced-precision kernels of the handle's storage.  Returns the mean milliseconds per launch
+ * and the algorithmic bytes and flops of one launch of each kernel (bytes: every matrix value,
+ * index and row pointer once at its stored width, every dense vector once; flops: 2 per
+ * stored non-zero).
  * Any output pointer may be NULL. */
 int ipm_profile_operator(ipm_handle* h, int reps, double* ms_rows, double* ms_cols, double* bytes_rows,
                          double* bytes_cols, double* flops_rows, double* flops_cols);

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "../../include/ipm.h"
+#include "ingest.h"
 #include "state.h"
 
 using namespace ipmk;
@@ -135,6 +136,19 @@ int fetch(ipm_handle* h, const T* src, int64_t n, int mem, std::vector<T>& out) 
   return IPM_OK;
 }
 
+// Copies n elements from host or device memory into dst (host).
+template <typename T>
+int fetch_into(ipm_handle* h, const T* src, int64_t n, int mem, T* dst) {
+  if (n <= 0) return IPM_OK;
+  if (!src) return fail(h, IPM_ERR_ARG, "missing array");
+  if (mem == IPM_MEM_DEVICE) {
+    CUDA_TRY(h, cudaMemcpy(dst, src, sizeof(T) * (size_t)n, cudaMemcpyDeviceToHost));
+  } else {
+    par_copy(dst, src, sizeof(T) * (size_t)n);
+  }
+  return IPM_OK;
+}
+
 void destroy_graphs(ipm_handle* h) {
   for (auto& g : h->graphs) {
     for (int w = 0; w < 2; ++w) {
@@ -178,16 +192,18 @@ struct Carver {
 
 struct HostQP {
   int64_t n = 0, m = 0, nR = 0, fr = 0;
-  std::vector<int64_t> Rp, RTp, Hp;
-  std::vector<int32_t> Ri, RTi, Hi, arow;
-  std::vector<double> Rv, RTv, Hv, wR, h0, c, b, l, u;
+  std::vector<int64_t> Rp, RTp, ATp, Hp;
+  std::vector<int32_t> Ri, RTi, ATi, Hi, arow;
+  std::vector<double> Rv, RTv, ATv, Hv, wR, h0, c, b, l, u;
   std::vector<unsigned char> fl, fu;
 };
 
 // Matrix part of the device layout (shared between handles that share a QP).
-void carve_matrix(Carver& cv, Dev& d, int64_t n, int64_t m, int64_t nR, int64_t nnzR, int64_t nnzHs, int storage) {
+void carve_matrix(Carver& cv, Dev& d, int64_t n, int64_t m, int64_t nR, int64_t nnzR, int64_t nnzA, int64_t nnzHs,
+                  int storage) {
   d.R_ptr = cv.take<int64_t>(nR + 1); d.R_idx = cv.take<int32_t>(nnzR); d.R_val = cv.take<double>(nnzR);
   d.RT_ptr = cv.take<int64_t>(n + 1); d.RT_idx = cv.take<int32_t>(nnzR); d.RT_val = cv.take<double>(nnzR);
+  d.AT_ptr = cv.take<int64_t>(n + 1); d.AT_idx = cv.take<int32_t>(nnzA); d.AT_val = cv.take<double>(nnzA);
   if (nnzHs) {
     d.Hs_ptr = cv.take<int64_t>(n + 1); d.Hs_idx = cv.take<int32_t>(nnzHs); d.Hs_val = cv.take<double>(nnzHs);
   } else {
@@ -799,16 +815,14 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
     if (std::isfinite(q.l[j]) && std::isfinite(q.u[j]) && !(q.l[j] < q.u[j])) return fail(h, IPM_ERR_ARG, "l >= u");
   }
   for (int64_t k = 0; k < m; ++k) if (!std::isfinite(q.b[k])) return fail(h, IPM_ERR_ARG, "b not finite");
-  // R = [F; A_csr]
+  // R = [F; A_csr], copied straight into the host image of R
   std::vector<int64_t> Fp, Ap;
-  std::vector<int32_t> Fi, Ai, arows_in;
-  std::vector<double> Fv, Av, fw;
+  std::vector<int32_t> arows_in;
+  std::vector<double> fw;
   if (fr) {
     if ((rc = fetch(h, qp->F_indptr, fr + 1, mem, Fp))) return rc;
     if (Fp[0] != 0) return fail(h, IPM_ERR_ARG, "F_indptr[0] != 0");
     for (int64_t r = 0; r < fr; ++r) if (Fp[r + 1] < Fp[r]) return fail(h, IPM_ERR_ARG, "F_indptr not monotone");
-    if ((rc = fetch(h, qp->F_indices, Fp[fr], mem, Fi))) return rc;
-    if ((rc = fetch(h, qp->F_data, Fp[fr], mem, Fv))) return rc;
     if ((rc = fetch(h, qp->f_w, fr, mem, fw))) return rc;
     for (double w : fw) if (!std::isfinite(w) || w < 0) return fail(h, IPM_ERR_ARG, "f_w must be finite and >= 0");
   }
@@ -816,8 +830,6 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
     if ((rc = fetch(h, qp->A_indptr, m + 1, mem, Ap))) return rc;
     if (Ap[0] != 0) return fail(h, IPM_ERR_ARG, "A_indptr[0] != 0");
     for (int64_t r = 0; r < m; ++r) if (Ap[r + 1] < Ap[r]) return fail(h, IPM_ERR_ARG, "A_indptr not monotone");
-    if ((rc = fetch(h, qp->A_indices, Ap[m], mem, Ai))) return rc;
-    if ((rc = fetch(h, qp->A_data, Ap[m], mem, Av))) return rc;
   }
   if (m && use_arows) {
     if ((rc = fetch(h, qp->a_rows, m, mem, arows_in))) return rc;
@@ -835,32 +847,39 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   q.Rv.resize(nnzF + nnzA);
   q.wR.assign(q.nR, 0.0);
   for (int64_t r = 0; r <= fr; ++r) q.Rp[r] = fr ? Fp[r] : 0;
-  if (nnzF) { std::memcpy(q.Ri.data(), Fi.data(), 4 * nnzF); std::memcpy(q.Rv.data(), Fv.data(), 8 * nnzF); }
+  if (nnzF) {
+    if ((rc = fetch_into(h, qp->F_indices, nnzF, mem, q.Ri.data()))) return rc;
+    if ((rc = fetch_into(h, qp->F_data, nnzF, mem, q.Rv.data()))) return rc;
+  }
   for (int64_t r = 0; r < fr; ++r) q.wR[r] = fw[r];
   if (use_acsr) {
     for (int64_t k = 1; k <= m; ++k) q.Rp[fr + k] = nnzF + Ap[k];
-    if (nnzA) { std::memcpy(q.Ri.data() + nnzF, Ai.data(), 4 * nnzA); std::memcpy(q.Rv.data() + nnzF, Av.data(), 8 * nnzA); }
+    if (nnzA) {
+      if ((rc = fetch_into(h, qp->A_indices, nnzA, mem, q.Ri.data() + nnzF))) return rc;
+      if ((rc = fetch_into(h, qp->A_data, nnzA, mem, q.Rv.data() + nnzF))) return rc;
+    }
   }
-  for (size_t e = 0; e < q.Ri.size(); ++e) {
-    if (q.Ri[e] < 0 || q.Ri[e] >= n) return fail(h, IPM_ERR_ARG, "column index out of range");
-    if (!std::isfinite(q.Rv[e])) return fail(h, IPM_ERR_ARG, "matrix value not finite");
+  switch (check_csr_entries((int64_t)q.Ri.size(), q.Ri.data(), q.Rv.data(), n)) {
+    case 1: return fail(h, IPM_ERR_ARG, "column index out of range");
+    case 2: return fail(h, IPM_ERR_ARG, "matrix value not finite");
+    default: break;
   }
   q.arow.resize(m);
   for (int64_t k = 0; k < m; ++k) q.arow[k] = use_arows ? arows_in[k] : (int32_t)(fr + k);
   // R^T by a stable counting sort (rows increase within each column: deterministic order)
   q.RTp.assign(n + 1, 0);
-  for (int32_t c : q.Ri) q.RTp[c + 1]++;
-  for (int64_t j = 0; j < n; ++j) q.RTp[j + 1] += q.RTp[j];
   q.RTi.resize(q.Ri.size());
   q.RTv.resize(q.Ri.size());
+  transpose_csr(q.nR, n, q.Rp.data(), q.Ri.data(), q.Rv.data(), q.RTp.data(), q.RTi.data(), q.RTv.data());
+  // A^T: the R^T entries of constraint rows, in R^T's order
   {
-    std::vector<int64_t> cur(q.RTp.begin(), q.RTp.end() - 1);
-    for (int64_t r = 0; r < q.nR; ++r)
-      for (int64_t e = q.Rp[r]; e < q.Rp[r + 1]; ++e) {
-        const int64_t pos = cur[q.Ri[e]]++;
-        q.RTi[pos] = (int32_t)r;
-        q.RTv[pos] = q.Rv[e];
-      }
+    std::vector<unsigned char> is_con(q.nR, 0);
+    for (int64_t k = 0; k < m; ++k) is_con[q.arow[k]] = 1;
+    q.ATp.assign(n + 1, 0);
+    filter_rows(n, q.RTp.data(), q.RTi.data(), q.RTv.data(), is_con.data(), q.ATp.data(), nullptr, nullptr);
+    q.ATi.resize(q.ATp[n]);
+    q.ATv.resize(q.ATp[n]);
+    filter_rows(n, q.RTp.data(), q.RTi.data(), q.RTv.data(), is_con.data(), q.ATp.data(), q.ATi.data(), q.ATv.data());
   }
   // dense H block -> CSR of its non-zeros (symmetry checked)
   if (qp->H_dense) {
@@ -915,9 +934,9 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
   free_arena(h);
   Dev dv{};
-  const int64_t nnzR = (int64_t)q.Rv.size(), nnzHs = (int64_t)q.Hv.size();
+  const int64_t nnzR = (int64_t)q.Rv.size(), nnzHs = (int64_t)q.Hv.size(), nnzAT = (int64_t)q.ATv.size();
   Carver cm(nullptr), cs(nullptr);
-  carve_matrix(cm, dv, n, m, q.nR, nnzR, nnzHs, h->opt.storage);
+  carve_matrix(cm, dv, n, m, q.nR, nnzR, nnzAT, nnzHs, h->opt.storage);
   carve_state(cs, dv, n, m, q.nR, stiff_cap, sc_cap, dense, h->opt.storage, h->opt.max_ipm);
   const size_t mbytes = cm.off + 256, sbytes = cs.off + 256;
   if (h->opt.mem_budget > 0 && (double)(mbytes + sbytes) > h->opt.mem_budget)
@@ -928,9 +947,9 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   h->arena_bytes = sbytes;
   h->mat = store;
   Carver cvm((char*)store->ptr), cvs((char*)h->arena);
-  carve_matrix(cvm, dv, n, m, q.nR, nnzR, nnzHs, h->opt.storage);
+  carve_matrix(cvm, dv, n, m, q.nR, nnzR, nnzAT, nnzHs, h->opt.storage);
   carve_state(cvs, dv, n, m, q.nR, stiff_cap, sc_cap, dense, h->opt.storage, h->opt.max_ipm);
-  dv.n = n; dv.m = m; dv.nR = q.nR; dv.nnzR = nnzR; dv.nnzHs = nnzHs;
+  dv.n = n; dv.m = m; dv.nR = q.nR; dv.nnzR = nnzR; dv.nnzHs = nnzHs; dv.nnzA = nnzAT;
   CUDA_TRY(h, cudaDeviceGetAttribute(&dv.sm_count, cudaDevAttrMultiProcessorCount, h->device));
   dv.g_rows = heuristic_group(q.nR ? (double)q.Rv.size() / (double)q.nR : 0.0);
   dv.g_cols = heuristic_group((double)q.Rv.size() / (double)n);
@@ -954,6 +973,9 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   if ((rc = up(d.RT_ptr, q.RTp.data(), 8 * q.RTp.size()))) return rc;
   if ((rc = up(d.RT_idx, q.RTi.data(), 4 * q.RTi.size()))) return rc;
   if ((rc = up(d.RT_val, q.RTv.data(), 8 * q.RTv.size()))) return rc;
+  if ((rc = up(d.AT_ptr, q.ATp.data(), 8 * q.ATp.size()))) return rc;
+  if ((rc = up(d.AT_idx, q.ATi.data(), 4 * q.ATi.size()))) return rc;
+  if ((rc = up(d.AT_val, q.ATv.data(), 8 * q.ATv.size()))) return rc;
   if (d.Hs_ptr) {
     if ((rc = up(d.Hs_ptr, q.Hp.data(), 8 * q.Hp.size()))) return rc;
     if ((rc = up(d.Hs_idx, q.Hi.data(), 4 * q.Hi.size()))) return rc;
@@ -1530,16 +1552,21 @@ int ipm_profile_operator(ipm_handle* h, int reps, double* ms_rows, double* ms_co
   const Geo& g = h->g;
   CUDA_TRY(h, launch_diag_update(d, g, h->st));
   CUDA_TRY(h, cudaMemcpyAsync(d.p, d.x, sizeof(double) * d.n, cudaMemcpyDeviceToDevice, h->st));
+  // the passes the handle's PCG runs: FP64, or the reduced-precision ones of its storage
+  const bool lp = d.storage != ST_F64;
+  if (lp) CUDA_TRY(h, launch_mirror_p32(d, g, h->st));
+  auto rows = [&]() { return lp ? launch_op_rows_lp_only(d, g, h->st) : launch_op_rows_only(d, g, h->st); };
+  auto cols = [&]() { return lp ? launch_op_cols_lp_only(d, g, h->st) : launch_op_cols_only(d, g, h->st); };
   std::vector<cudaEvent_t> ev(3 * reps);
   for (auto& e : ev) CUDA_TRY(h, cudaEventCreate(&e));
   // one untimed pair first
-  CUDA_TRY(h, launch_op_rows_only(d, g, h->st));
-  CUDA_TRY(h, launch_op_cols_only(d, g, h->st));
+  CUDA_TRY(h, rows());
+  CUDA_TRY(h, cols());
   for (int r = 0; r < reps; ++r) {
     CUDA_TRY(h, cudaEventRecord(ev[3 * r], h->st));
-    CUDA_TRY(h, launch_op_rows_only(d, g, h->st));
+    CUDA_TRY(h, rows());
     CUDA_TRY(h, cudaEventRecord(ev[3 * r + 1], h->st));
-    CUDA_TRY(h, launch_op_cols_only(d, g, h->st));
+    CUDA_TRY(h, cols());
     CUDA_TRY(h, cudaEventRecord(ev[3 * r + 2], h->st));
   }
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
@@ -1555,6 +1582,17 @@ int ipm_profile_operator(ipm_handle* h, int reps, double* ms_rows, double* ms_co
   const double nnz = (double)d.nnzR, nnzh = (double)d.nnzHs;
   if (ms_rows) *ms_rows = tr / reps;
   if (ms_cols) *ms_cols = tc / reps;
+  if (lp) {
+    const double vb = d.storage == ST_F32 ? 4.0 : (d.storage == ST_BF16 ? 2.0 : 1.0);
+    // rows: narrow values + indices, row pointers, scale, w_R, thR read, w32 written, p32 read once
+    if (bytes_rows) *bytes_rows = (vb + 4.0) * nnz + 8.0 * (d.nR + 1) + 24.0 * d.nR + 4.0 * d.n;
+    // cols: narrow values + indices, row pointers, w32 read once, p, h0, sigma read, q written
+    if (bytes_cols) *bytes_cols = (vb + 4.0) * nnz + 8.0 * (d.n + 1) + 4.0 * d.nR + 32.0 * d.n +
+                                  (d.Hs_ptr ? 12.0 * nnzh + 8.0 * (d.n + 1) : 0.0);
+    if (flops_rows) *flops_rows = 2.0 * nnz + 4.0 * d.nR;
+    if (flops_cols) *flops_cols = 2.0 * nnz + 2.0 * nnzh + 4.0 * d.n;
+    return IPM_OK;
+  }
   // rows: values + indices, row pointers, omega, v written, p read once
   if (bytes_rows) *bytes_rows = 12.0 * nnz + 8.0 * (d.nR + 1) + 16.0 * d.nR + 8.0 * d.n;
   // cols: values + indices, row pointers, v read once, p, h0, sigma read, q written (+ Hs)

@@ -131,7 +131,8 @@ __global__ void k_cons_resid(Dev d, double* part) {
   v = block_reduce<0>(sy, sh);     if (threadIdx.x == 0) part[5 * K + blockIdx.x] = v;
 }
 
-// Variables: Hx = R^T vR + Hs x + h0 o x, A^T y = R^T vR2, r_d, r_l, r_u and the scalar parts
+// Variables: Hx = R^T vR + Hs x + h0 o x, A^T y (over the stored A^T, y placed on R rows in
+// vR2), r_d, r_l, r_u and the scalar parts
 // of the objective, the dual objective and the complementarity sum.
 template <int G>
 __global__ void k_cols_resid(Dev d, double* part) {
@@ -140,9 +141,10 @@ __global__ void k_cols_resid(Dev d, double* part) {
   double rd_inf = 0.0, hx_inf = 0.0, aty_inf = 0.0, rc_inf = 0.0, xHsx = 0.0, cx = 0.0, lzl = 0.0,
          uzu = 0.0, tz = 0.0, bviol = 0.0;
   FOR_GROUP_ROWS(G, j, ok, d.n) {
-    double hx_f, aty;
     const int64_t beg = ok ? d.RT_ptr[j] : 0, end = ok ? d.RT_ptr[j + 1] : 0;
-    group_row_dot2<G>(beg, end, glane<G>(), d.RT_idx, d.RT_val, d.vR, d.vR2, hx_f, aty);
+    const double hx_f = group_row_dot<G, false>(beg, end, glane<G>(), d.RT_idx, d.RT_val, d.vR);
+    const int64_t ab = ok ? d.AT_ptr[j] : 0, ae = ok ? d.AT_ptr[j + 1] : 0;
+    const double aty = group_row_dot<G, false>(ab, ae, glane<G>(), d.AT_idx, d.AT_val, d.vR2);
     double hs = 0.0;
     if (d.Hs_ptr) {
       const int64_t hb = ok ? d.Hs_ptr[j] : 0, he = ok ? d.Hs_ptr[j + 1] : 0;
@@ -513,13 +515,14 @@ cudaError_t launch_diag_update(const Dev& d, const Geo& g, cudaStream_t st) {
 
 // ------------------------------------------------------------------------------ Jacobi
 
-// M_j = M0_j + sum_i R_ij^2 thR_i  (thR: theta of the rows kept in the diagonal part).
+// M_j = M0_j + sum_k A_kj^2 thR_k  (thR: theta of the constraint rows kept in the diagonal part;
+// the factor rows' part w_R is already in M0 through diag(H)).
 // Writes 1 / M_j to out (INV) or M_j.
 template <bool INV, int G>
 __global__ void k_jacobi(Dev d, double* out) {
   FOR_GROUP_ROWS(G, j, ok, d.n) {
-    const int64_t beg = ok ? d.RT_ptr[j] : 0, end = ok ? d.RT_ptr[j + 1] : 0;
-    const double a = group_row_dot<G, true>(beg, end, glane<G>(), d.RT_idx, d.RT_val, d.thR);
+    const int64_t beg = ok ? d.AT_ptr[j] : 0, end = ok ? d.AT_ptr[j + 1] : 0;
+    const double a = group_row_dot<G, true>(beg, end, glane<G>(), d.AT_idx, d.AT_val, d.thR);
     if (ok && glane<G>() == 0) {
       const double mj = d.M0[j] + a;
       out[j] = INV ? 1.0 / mj : mj;
@@ -649,8 +652,8 @@ __global__ void k_sc_count(Dev d) {
   if (d.sc->n_stiff == 0) return;
   for (int64_t j = gwarp(); j < d.n; j += nwarps()) {
     int cnt = 0;
-    for (int64_t e = d.RT_ptr[j] + (threadIdx.x & 31); e < d.RT_ptr[j + 1]; e += 32)
-      cnt += d.slotR[d.RT_idx[e]] >= 0 ? 1 : 0;
+    for (int64_t e = d.AT_ptr[j] + (threadIdx.x & 31); e < d.AT_ptr[j + 1]; e += 32)
+      cnt += d.slotR[d.AT_idx[e]] >= 0 ? 1 : 0;
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
     if ((threadIdx.x & 31) == 0) d.sc_cnt[j] = cnt;
   }
@@ -672,15 +675,15 @@ __global__ void k_sc_fill(Dev d) {
   const int lane = threadIdx.x & 31;
   for (int64_t j = gwarp(); j < d.n; j += nwarps()) {
     int64_t out = d.sc_ptr[j];
-    for (int64_t e0 = d.RT_ptr[j]; e0 < d.RT_ptr[j + 1]; e0 += 32) {
+    for (int64_t e0 = d.AT_ptr[j]; e0 < d.AT_ptr[j + 1]; e0 += 32) {
       const int64_t e = e0 + lane;
       int slot = -1;
-      if (e < d.RT_ptr[j + 1]) slot = d.slotR[d.RT_idx[e]];
+      if (e < d.AT_ptr[j + 1]) slot = d.slotR[d.AT_idx[e]];
       const unsigned bal = __ballot_sync(0xffffffffu, slot >= 0);
       if (slot >= 0) {
         const int64_t pos = out + __popc(bal & ((1u << lane) - 1u));
         d.sc_slot[pos] = slot;
-        d.sc_val[pos] = d.RT_val[e];
+        d.sc_val[pos] = d.AT_val[e];
       }
       out += __popc(bal);
     }
@@ -740,15 +743,16 @@ static __device__ void finish_rhs(Scal* sc, double rhs2) {
   else if (rhs2 == 0.0) sc->cg_conv = 1;
 }
 
-// rhs = -r_d - r_l / t_l + r_u / t_u - R^T vR2; PCG start r = rhs, dx = 0; ||rhs||^2.
+// rhs = -r_d - r_l / t_l + r_u / t_u - A^T u (u = vR2 on the constraint rows); PCG start
+// r = rhs, dx = 0; ||rhs||^2.
 template <int G>
 __global__ void k_rhs_n(Dev d) {
   __shared__ double sh[32];
   const double mu = d.sc->mu;
   double r2 = 0.0;
   FOR_GROUP_ROWS(G, j, ok, d.n) {
-    const int64_t beg = ok ? d.RT_ptr[j] : 0, end = ok ? d.RT_ptr[j + 1] : 0;
-    const double atu = group_row_dot<G, false>(beg, end, glane<G>(), d.RT_idx, d.RT_val, d.vR2);
+    const int64_t beg = ok ? d.AT_ptr[j] : 0, end = ok ? d.AT_ptr[j + 1] : 0;
+    const double atu = group_row_dot<G, false>(beg, end, glane<G>(), d.AT_idx, d.AT_val, d.vR2);
     if (ok && glane<G>() == 0) {
       double g = -d.rd[j] - atu;
       const double xj = d.x[j];
@@ -768,8 +772,9 @@ __global__ void k_rhs_n(Dev d) {
   }
 }
 
-// The right-hand side and the Jacobi diagonal in one pass over R^T: for each variable j the
-// same entries give sum_i R_ij u_i (plain) and sum_i R_ij^2 thR_i (squared).
+// The right-hand side and the Jacobi diagonal in one pass over A^T (u and theta live on the
+// constraint rows only): for each variable j the same entries give sum_k A_kj u_k (plain) and
+// sum_k A_kj^2 thR_k (squared).
 template <int G>
 __device__ __forceinline__ void group_row_dot_plain_sq(const int64_t beg, const int64_t end, const int gl,
                                                        const int32_t* __restrict__ idx, const double* __restrict__ val,
@@ -808,9 +813,9 @@ __global__ void k_rhs_jacobi(Dev d) {
   const double mu = d.sc->mu;
   double r2 = 0.0;
   FOR_GROUP_ROWS(G, j, ok, d.n) {
-    const int64_t beg = ok ? d.RT_ptr[j] : 0, end = ok ? d.RT_ptr[j + 1] : 0;
+    const int64_t beg = ok ? d.AT_ptr[j] : 0, end = ok ? d.AT_ptr[j + 1] : 0;
     double atu, dth;
-    group_row_dot_plain_sq<G>(beg, end, glane<G>(), d.RT_idx, d.RT_val, d.vR2, d.thR, atu, dth);
+    group_row_dot_plain_sq<G>(beg, end, glane<G>(), d.AT_idx, d.AT_val, d.vR2, d.thR, atu, dth);
     if (ok && glane<G>() == 0) {
       d.Minv[j] = 1.0 / (d.M0[j] + dth);
       double gj = -d.rd[j] - atu;

@@ -81,29 +81,92 @@ cudaError_t launch_quantize(const Dev& d, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// FP32 dot of a stored row with an FP32 vector by a group of G lanes (four accumulators).
+// Eight stored values of type T decoded to FP32, from 16-byte aligned loads.
+template <int S> struct Chunk;
+template <> struct Chunk<ST_F32> {
+  static constexpr int C = 4;   // elements per 16-byte load
+  static __device__ __forceinline__ void load(const float* p, float* v) {
+    const float4 u = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w;
+  }
+};
+template <> struct Chunk<ST_BF16> {
+  static constexpr int C = 8;
+  static __device__ __forceinline__ void load(const __nv_bfloat16* p, float* v) {
+    const uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
+    const unsigned w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[2 * k] = __uint_as_float(w[k] << 16);          // bf16 = the high half of an fp32
+      v[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+    }
+  }
+};
+template <> struct Chunk<ST_FP8> {
+  static constexpr int C = 16;
+  static __device__ __forceinline__ void load(const __nv_fp8_e4m3* p, float* v) {
+    const uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
+    const unsigned w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const __nv_fp8x2_e4m3 lo = *reinterpret_cast<const __nv_fp8x2_e4m3*>(reinterpret_cast<const unsigned short*>(&w[k]));
+      const __nv_fp8x2_e4m3 hi = *reinterpret_cast<const __nv_fp8x2_e4m3*>(reinterpret_cast<const unsigned short*>(&w[k]) + 1);
+      const float2 a = static_cast<float2>(lo), b = static_cast<float2>(hi);
+      v[4 * k] = a.x; v[4 * k + 1] = a.y; v[4 * k + 2] = b.x; v[4 * k + 3] = b.y;
+    }
+  }
+};
+
+// FP32 dot of a stored row with an FP32 vector by a group of G lanes.  The row is split into
+// a head up to the first 16-byte boundary of the value array, whole chunks of C elements
+// (one 16-byte value load and C/4 16-byte index loads per chunk, chunk c taken by lane
+// c mod G, two chunks in flight per lane) and a tail; one accumulator per lane, then a
+// shuffle reduction over the group.  Value and index arrays are 256-byte aligned, so an
+// element offset that is a multiple of C (>= 4) is 16-byte aligned in both.
 template <int S, int G>
 __device__ __forceinline__ float group_row_dot_lp(const int64_t beg, const int64_t end, const int gl,
                                                   const int32_t* __restrict__ idx,
                                                   const typename StorageT<S>::T* __restrict__ val,
                                                   const float* __restrict__ x) {
+  constexpr int C = Chunk<S>::C;
   float a = 0.f;
-  int64_t e = beg + gl;
-  for (; e + 7 * G < end; e += 8 * G) {
-    float v[8];
-    int i[8];
-    float xv[8];
+  int64_t a0 = (beg + C - 1) & ~(int64_t)(C - 1);
+  if (a0 > end) a0 = end;
+  for (int64_t e = beg + gl; e < a0; e += G) a = fmaf(StorageT<S>::dec(val[e]), __ldg(x + __ldg(idx + e)), a);
+  const int64_t nch = (end - a0) / C;
+  int64_t c = gl;
+  for (; c + G < nch; c += 2 * G) {
+    const int64_t e0 = a0 + c * C, e1 = e0 + (int64_t)G * C;
+    float v0[C], v1[C];
+    int i0[C], i1[C];
+    Chunk<S>::load(val + e0, v0);
+    Chunk<S>::load(val + e1, v1);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      v[k] = StorageT<S>::dec(val[e + k * G]);
-      i[k] = __ldg(idx + e + k * G);
+    for (int k = 0; k < C / 4; ++k) {
+      const int4 t0 = __ldg(reinterpret_cast<const int4*>(idx + e0) + k);
+      const int4 t1 = __ldg(reinterpret_cast<const int4*>(idx + e1) + k);
+      i0[4 * k] = t0.x; i0[4 * k + 1] = t0.y; i0[4 * k + 2] = t0.z; i0[4 * k + 3] = t0.w;
+      i1[4 * k] = t1.x; i1[4 * k + 1] = t1.y; i1[4 * k + 2] = t1.z; i1[4 * k + 3] = t1.w;
     }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) xv[k] = __ldg(x + i[k]);
+    for (int k = 0; k < C; ++k) a = fmaf(v0[k], __ldg(x + i0[k]), a);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) a = fmaf(v[k], xv[k], a);
+    for (int k = 0; k < C; ++k) a = fmaf(v1[k], __ldg(x + i1[k]), a);
   }
-  for (; e < end; e += G) a = fmaf(StorageT<S>::dec(val[e]), __ldg(x + __ldg(idx + e)), a);
+  if (c < nch) {
+    const int64_t e0 = a0 + c * C;
+    float v0[C];
+    int i0[C];
+    Chunk<S>::load(val + e0, v0);
+#pragma unroll
+    for (int k = 0; k < C / 4; ++k) {
+      const int4 t0 = __ldg(reinterpret_cast<const int4*>(idx + e0) + k);
+      i0[4 * k] = t0.x; i0[4 * k + 1] = t0.y; i0[4 * k + 2] = t0.z; i0[4 * k + 3] = t0.w;
+    }
+#pragma unroll
+    for (int k = 0; k < C; ++k) a = fmaf(v0[k], __ldg(x + i0[k]), a);
+  }
+  for (int64_t e = a0 + nch * C + gl; e < end; e += G) a = fmaf(StorageT<S>::dec(val[e]), __ldg(x + __ldg(idx + e)), a);
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
   return a;
@@ -130,8 +193,8 @@ __global__ void k_stiff_op_u(Dev d) {
 
 // w_i = s_i^2 (w_R,i + thR_i) (q_i . p32)   (FP32 result; thR = theta on moderate rows)
 template <int S, int G>
-__global__ void k_op_rows_lp(Dev d) {
-  if (d.sc->cg_done) return;
+__global__ void k_op_rows_lp(Dev d, int standalone) {
+  if (!standalone && d.sc->cg_done) return;
   using T = typename StorageT<S>::T;
   const T* q = static_cast<const T*>(d.Rq);
   const int gl = threadIdx.x & (G - 1);
@@ -147,9 +210,9 @@ __global__ void k_op_rows_lp(Dev d) {
 
 // q_j = sum_i q_ij w_i + Hs p + (h0 + sigma) p;  p^T q -> alpha (last block), as k_op_cols.
 template <int S, int G>
-__global__ void k_op_cols_lp(Dev d) {
+__global__ void k_op_cols_lp(Dev d, int standalone) {
   __shared__ double sh[32];
-  if (d.sc->cg_done) return;
+  if (!standalone && d.sc->cg_done) return;
   using T = typename StorageT<S>::T;
   const T* q = static_cast<const T*>(d.RTq);
   const int gl = threadIdx.x & (G - 1);
@@ -173,6 +236,7 @@ __global__ void k_op_cols_lp(Dev d) {
       pq = fma(pj, qj, pq);
     }
   }
+  if (standalone) return;
   double v[1] = {pq};
   const int ops[1] = {0};
   double out[1];
@@ -208,8 +272,30 @@ __global__ void k_op_cols_lp(Dev d) {
 
 cudaError_t launch_op_lp(const Dev& d, const Geo& g, cudaStream_t st) {
   k_stiff_op_u<<<(d.stiff_cap + 7) / 8, kBlock, 0, st>>>(d);
-  if (d.nR) DISPATCH_SG(d.storage, d.g_rows, k_op_rows_lp<S, G><<<g.gR, kBlock, 0, st>>>(d));
-  DISPATCH_SG(d.storage, d.g_cols, k_op_cols_lp<S, G><<<g.gN, kBlock, 0, st>>>(d));
+  if (d.nR) DISPATCH_SG(d.storage, d.g_rows, k_op_rows_lp<S, G><<<g.gR, kBlock, 0, st>>>(d, 0));
+  DISPATCH_SG(d.storage, d.g_cols, k_op_cols_lp<S, G><<<g.gN, kBlock, 0, st>>>(d, 0));
+  return cudaGetLastError();
+}
+
+// The two reduced-precision passes alone (measurement): no scalars read or written; p32 must
+// hold the FP32 mirror of p.
+cudaError_t launch_op_rows_lp_only(const Dev& d, const Geo& g, cudaStream_t st) {
+  if (d.nR) DISPATCH_SG(d.storage, d.g_rows, k_op_rows_lp<S, G><<<g.gR, kBlock, 0, st>>>(d, 1));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_op_cols_lp_only(const Dev& d, const Geo& g, cudaStream_t st) {
+  DISPATCH_SG(d.storage, d.g_cols, k_op_cols_lp<S, G><<<g.gN, kBlock, 0, st>>>(d, 1));
+  return cudaGetLastError();
+}
+
+__global__ void k_mirror_p32(Dev d) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x)
+    d.p32[j] = (float)d.p[j];
+}
+
+cudaError_t launch_mirror_p32(const Dev& d, const Geo& g, cudaStream_t st) {
+  k_mirror_p32<<<g.eN, kBlock, 0, st>>>(d);
   return cudaGetLastError();
 }
 

@@ -19,6 +19,9 @@ struct Dev {
   // problem data
   const int64_t* R_ptr; const int32_t* R_idx; const double* R_val;
   const int64_t* RT_ptr; const int32_t* RT_idx; const double* RT_val;
+  // A^T alone: the entries of R^T whose row is a constraint row (same row indices, same order)
+  const int64_t* AT_ptr; const int32_t* AT_idx; const double* AT_val;
+  int64_t nnzA;
   const int64_t* Hs_ptr; const int32_t* Hs_idx; const double* Hs_val;   // nullptr if none
   const int32_t* arow;         // m: row of R holding constraint k
   const double *wR, *h0, *c, *b, *l, *u;
@@ -93,6 +96,9 @@ cudaError_t launch_cg_body(const Dev& d, const Geo& g, int precond, cudaGraphCon
 // ---- reduced-precision operator and FP64 refinement (lowp.cu) ----
 cudaError_t launch_quantize(const Dev& d, cudaStream_t st);
 cudaError_t launch_op_lp(const Dev& d, const Geo& g, cudaStream_t st);
+cudaError_t launch_op_rows_lp_only(const Dev& d, const Geo& g, cudaStream_t st);   // measurement
+cudaError_t launch_op_cols_lp_only(const Dev& d, const Geo& g, cudaStream_t st);
+cudaError_t launch_mirror_p32(const Dev& d, const Geo& g, cudaStream_t st);
 cudaError_t launch_refine_start(const Dev& d, const Geo& g, cudaStream_t st);
 cudaError_t launch_refine_inner(const Dev& d, const Geo& g, cudaGraphConditionalHandle hi, cudaStream_t st);
 cudaError_t launch_refine_tail(const Dev& d, const Geo& g, cudaGraphConditionalHandle h, cudaStream_t st);
