@@ -356,6 +356,71 @@ def run_serve(args):
     return 0
 
 
+def run_bfgs(args):
+    """The paper's quasi-Newton Hessian regime (Section 3.3, eq:bfgs_hessian; Table 1 sizes):
+    proton n = 77373, bounds only, 2k = 200 update columns; VMAT n = 13425 with 52867 upper
+    and 15751 lower sparse constraint rows, 2k = 66.  Synthetic (workloads.bfgs_qp).  Steps =
+    complete FP64 solves to rel. KKT <= 1e-6; roofline of the slower operator half."""
+    import torch
+    from paper_2405_03584_gb300 import build, ipm, workloads as W
+    from oracle import kkt_check
+    torch.cuda.set_device(0)
+    build.build()
+    if args.bfgs == "proton":
+        p = W.bfgs_qp(n=77373, k=100, seed=5)
+    else:
+        p = W.bfgs_qp(n=13425, k=33, m_ub=52867, m_lb=15751, density=0.01, seed=6, c_mode="target",
+                      ub_fac=1.1, lb_fac=0.9)
+    s = ipm.Solver(tol_kkt=TOL, precond="jacobi_lr", storage=args.storage,
+                   stiff_max=1024 if args.bfgs == "vmat" else 256)
+    s.set_qp_bfgs(p)
+    for _ in range(args.warmup):
+        s.solve()
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    torch.cuda.synchronize()
+    sts, infos = [], []
+    for k in range(args.steps):
+        evs[k][0].record(stream)
+        sts.append(s.solve())
+        evs[k][1].record(stream)
+        infos.append(s.get()["info"])
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    lat = [a.elapsed_time(b) for a, b in evs]
+    total = evs[0][0].elapsed_time(evs[-1][1])
+    out = s.get()
+    rk = kkt_check.rel_kkt(kkt_check.bfgs_ops(p), out["x"], out["y"], out["zl"], out["zu"])
+    prof = s.profile_operator(reps=20)
+    key = "rows" if prof["ms_rows"] >= prof["ms_cols"] else "cols"
+    peak, peak_kind = _peaks()
+    ach = prof["bytes_" + key] / (prof["ms_" + key] / 1000.0) / 1e9
+    other = "cols" if key == "rows" else "rows"
+    roof = {"bound": "hbm", "kernel": ("U^T p pass (k_lr_part + k_op_rows)" if key == "rows"
+                                       else "column pass (k_op_cols with U (W t))"),
+            "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+            "peak_kind": peak_kind + " hbm_gbs", "algorithmic_bytes": prof["bytes_" + key],
+            "ms_per_launch": prof["ms_" + key],
+            "fp64_tflops": prof["flops_" + key] / (prof["ms_" + key] / 1000.0) / 1e12,
+            "other_half": {"ms": prof["ms_" + other],
+                           "gbs": prof["bytes_" + other] / (prof["ms_" + other] / 1000.0) / 1e9}}
+    s.close()
+    res = {"mode": "bfgs", "metric": "QP solves/sec at rel. KKT <= 1e-6 (quasi-Newton Hessian, %s shape)" % args.bfgs,
+           "value": args.steps / (total / 1000.0), "unit": "solves/s", "ms_per_step": total / args.steps,
+           "steps": args.steps, "warmup": args.warmup, "dtype": "f64" if args.storage == "f64" else args.storage,
+           "config": {"workload": args.bfgs, "n": p["n"], "m": p["m"], "u_cols": int(p["U"].shape[1]),
+                      "nnz_A": int(p["A_indptr"][-1]) if p["m"] else 0,
+                      "generator": "workloads.bfgs_qp (synthetic; the paper's RayStation exports are not available)"},
+           "latency_ms": {"p50": statistics.median(lat), "max": max(lat)},
+           "solve": {"status": [int(x) for x in sts], "ipm_iters": [i["ipm_iters"] for i in infos],
+                     "cg_iters": [i["cg_iters"] for i in infos], "rel_kkt_checker": rk},
+           "gpu_launches": int(sum(i["kernel_launches"] for i in infos)), "roofline": roof, "clocks": clk}
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -503,6 +568,7 @@ def main():
     ap.add_argument("--batch", action="store_true", help="the 64-QP uneven batch instead of the single RT QP")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-scale", type=float, default=1.0, help="scale every n of the batch (testing)")
+    ap.add_argument("--bfgs", choices=["proton", "vmat"], help="the quasi-Newton Hessian shapes of the paper")
     ap.add_argument("--serve", action="store_true", help="the serving stream (Poisson arrivals, chains, warm start)")
     ap.add_argument("--serve-lambda", type=float, default=20.0)
     ap.add_argument("--serve-horizon", type=float, default=60.0)
@@ -522,6 +588,8 @@ def main():
         return run_operator_only(args)
     if args.batch:
         return run_batch(args)
+    if args.bfgs:
+        return run_bfgs(args)
     if args.serve:
         # more hardware work queues than the default 8, so many slots' streams run side by side
         os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")

@@ -109,7 +109,8 @@ typedef struct ipm_options {
 /* Fills *opt with the defaults listed above. */
 void ipm_default_options(ipm_options* opt);
 
-/* The QP (1).  H = diag(h0) + H_dense + F^T diag(f_w) F, each term optional.
+/* The QP (1).  H = diag(h0) + H_dense + F^T diag(f_w) F + U diag(u_w) U^T, each term optional
+ * (the last is the quasi-Newton Hessian of Section 3.3, eq:bfgs_hessian, applied matrix-free).
  * Constraint rows come either from F (a_rows: row indices into F, the dose-matrix case where
  * A is a subset of D's rows) or from a CSR matrix A; not both.  m = 0 is allowed (bounds only). */
 typedef struct ipm_qp {
@@ -131,6 +132,10 @@ typedef struct ipm_qp {
   const int64_t* A_indptr;   /* m+1 (or NULL)                                              */
   const int32_t* A_indices;  /* nnz(A)                                                     */
   const double* A_data;      /* nnz(A)                                                     */
+  int64_t u_cols;            /* columns of U in the low-rank term U diag(u_w) U^T of H     */
+                             /* (eq:bfgs_hessian; 0 = none, at most 65536)                  */
+  const double* U;           /* n x u_cols, row-major: variable j's u_cols values adjacent */
+  const double* u_w;         /* u_cols weights; may be negative (BFGS), H must stay PSD    */
 } ipm_qp;
 
 typedef struct ipm_info {

@@ -92,6 +92,21 @@ def from_rt(p: dict) -> DenseQP:
                    np.asarray(p["l"], float), np.asarray(p["u"], float))
 
 
+def from_bfgs(p: dict) -> DenseQP:
+    """Dense form of a QP with a quasi-Newton Hessian (Section 3.3, eq:bfgs_hessian):
+    H = diag(h0) + U diag(w) U^T; A from its CSR arrays (or none)."""
+    n, m = p["n"], p["m"]
+    U, w = np.asarray(p["U"], float), np.asarray(p["uw"], float)
+    H = np.diag(np.asarray(p["h0"], float)) + (U * w) @ U.T
+    H = 0.5 * (H + H.T)
+    A = np.zeros((m, n))
+    if m:
+        rows = np.repeat(np.arange(m), np.diff(p["A_indptr"]))
+        A[rows, p["A_indices"]] = p["A_data"]
+    return DenseQP(H, np.asarray(p["c"], float), A, np.asarray(p["b"], float),
+                   np.asarray(p["l"], float), np.asarray(p["u"], float))
+
+
 def _tl(qp, x):
     return np.where(qp.fl, x - np.where(qp.fl, qp.l, 0.0), 1.0)
 

@@ -21,7 +21,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["Operators", "dense_ops", "rt_ops", "rel_kkt", "rt_condensed_entries", "rt_residual_dual"]
+__all__ = ["Operators", "dense_ops", "rt_ops", "bfgs_ops", "rel_kkt", "rt_condensed_entries", "rt_residual_dual"]
 
 
 class Operators:
@@ -68,6 +68,24 @@ def rt_ops(p: dict) -> Operators:
         np.add.at(full, ar, y)
         return _csr_tmv(ip, ix, dv, full, n)
 
+    return Operators(Hx, Ax, Aty, p["c"], p["b"], p["l"], p["u"])
+
+
+def bfgs_ops(p: dict) -> Operators:
+    """Operators of a QP with a quasi-Newton Hessian: H x = h0 o x + U (w o (U^T x)), A in CSR."""
+    U, w, h0 = np.asarray(p["U"], float), np.asarray(p["uw"], float), np.asarray(p["h0"], float)
+    n, m = p["n"], p["m"]
+
+    def Hx(x):
+        return h0 * x + U @ (w * (U.T @ x))
+
+    if m:
+        ip, ix, dv = p["A_indptr"], p["A_indices"], p["A_data"]
+        Ax = lambda x: _csr_mv(ip, ix, dv, x, m)
+        Aty = lambda y: _csr_tmv(ip, ix, dv, y, n)
+    else:
+        Ax = lambda x: np.zeros(0)
+        Aty = lambda y: np.zeros(n)
     return Operators(Hx, Ax, Aty, p["c"], p["b"], p["l"], p["u"])
 
 

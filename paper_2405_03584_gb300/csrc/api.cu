@@ -8,6 +8,7 @@
 // recovery -> ratio test -> update -> residual summary -> mu test / stop rule (which sets the
 // outer condition and appends a trace row).  The host launches the graph and waits once.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <map>
 #include <memory>
@@ -195,6 +196,8 @@ struct HostQP {
   std::vector<int64_t> Rp, RTp, ATp, Hp;
   std::vector<int32_t> Ri, RTi, ATi, Hi, arow;
   std::vector<double> Rv, RTv, ATv, Hv, wR, h0, c, b, l, u;
+  int64_t ucols = 0;
+  std::vector<double> U, uw;        // low-rank Hessian term: n x ucols (row-major), ucols weights
   std::vector<unsigned char> fl, fu;
 };
 
@@ -210,6 +213,7 @@ void carve_matrix(Carver& cv, Dev& d, int64_t n, int64_t m, int64_t nR, int64_t 
     d.Hs_ptr = nullptr; d.Hs_idx = nullptr; d.Hs_val = nullptr;
   }
   d.arow = cv.take<int32_t>(m);
+  d.U = d.ucols ? cv.take<double>(n * d.ucols) : nullptr;
   if (storage != ST_F64) {
     const size_t vb = storage == ST_F32 ? 4 : (storage == ST_BF16 ? 2 : 1);
     d.Rq = cv.take<unsigned char>((int64_t)vb * nnzR);
@@ -254,6 +258,14 @@ void carve_state(Carver& cv, Dev& d, int64_t n, int64_t m, int64_t nR, int stiff
   } else {
     d.p32 = d.w32 = nullptr;
     d.dxr = nullptr;
+  }
+  if (d.ucols) {
+    d.uw = cv.take<double>(d.ucols);
+    d.lrs = cv.take<double>(d.ucols);
+    d.upart = cv.take<double>((int64_t)d.ublocks * d.ucols);
+    d.lrq = cv.take<double>(d.ucols);
+  } else {
+    d.uw = d.lrs = d.upart = d.lrq = nullptr;
   }
   d.trace = cv.take<double>((int64_t)trace_cap * kTraceCols);
   d.partials = cv.take<double>(32 * (int64_t)kMaxRedBlocks);
@@ -815,6 +827,22 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
     if (std::isfinite(q.l[j]) && std::isfinite(q.u[j]) && !(q.l[j] < q.u[j])) return fail(h, IPM_ERR_ARG, "l >= u");
   }
   for (int64_t k = 0; k < m; ++k) if (!std::isfinite(q.b[k])) return fail(h, IPM_ERR_ARG, "b not finite");
+  // low-rank Hessian term U diag(u_w) U^T
+  if (qp->u_cols < 0 || qp->u_cols > (1 << 16)) return fail(h, IPM_ERR_ARG, "u_cols out of range [0, 65536]");
+  q.ucols = qp->u_cols;
+  if (q.ucols) {
+    if (!qp->U || !qp->u_w) return fail(h, IPM_ERR_ARG, "u_cols > 0 needs U and u_w");
+    q.U.resize((size_t)(n * q.ucols));
+    if ((rc = fetch_into(h, qp->U, n * q.ucols, mem, q.U.data()))) return rc;
+    if ((rc = fetch(h, qp->u_w, q.ucols, mem, q.uw))) return rc;
+    for (double v : q.uw) if (!std::isfinite(v)) return fail(h, IPM_ERR_ARG, "u_w not finite");
+    std::atomic<int> bad{0};
+    parallel_ranges((int64_t)q.U.size(), q.U.size() < (1u << 20) ? 1 : host_threads(), [&](int, int64_t b, int64_t e) {
+      for (int64_t k = b; k < e; ++k)
+        if (!std::isfinite(q.U[k])) { bad.store(1); break; }
+    });
+    if (bad.load()) return fail(h, IPM_ERR_ARG, "U not finite");
+  }
   // R = [F; A_csr], copied straight into the host image of R
   std::vector<int64_t> Fp, Ap;
   std::vector<int32_t> arows_in;
@@ -934,6 +962,9 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
   free_arena(h);
   Dev dv{};
+  CUDA_TRY(h, cudaDeviceGetAttribute(&dv.sm_count, cudaDevAttrMultiProcessorCount, h->device));
+  dv.ucols = q.ucols;
+  dv.ublocks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * (int64_t)dv.sm_count, n / 32));
   const int64_t nnzR = (int64_t)q.Rv.size(), nnzHs = (int64_t)q.Hv.size(), nnzAT = (int64_t)q.ATv.size();
   Carver cm(nullptr), cs(nullptr);
   carve_matrix(cm, dv, n, m, q.nR, nnzR, nnzAT, nnzHs, h->opt.storage);
@@ -950,7 +981,6 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   carve_matrix(cvm, dv, n, m, q.nR, nnzR, nnzAT, nnzHs, h->opt.storage);
   carve_state(cvs, dv, n, m, q.nR, stiff_cap, sc_cap, dense, h->opt.storage, h->opt.max_ipm);
   dv.n = n; dv.m = m; dv.nR = q.nR; dv.nnzR = nnzR; dv.nnzHs = nnzHs; dv.nnzA = nnzAT;
-  CUDA_TRY(h, cudaDeviceGetAttribute(&dv.sm_count, cudaDevAttrMultiProcessorCount, h->device));
   dv.g_rows = heuristic_group(q.nR ? (double)q.Rv.size() / (double)q.nR : 0.0);
   dv.g_cols = heuristic_group((double)q.Rv.size() / (double)n);
   if (h->opt.lanes_rows) dv.g_rows = h->opt.lanes_rows;
@@ -982,6 +1012,10 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
     if ((rc = up(d.Hs_val, q.Hv.data(), 8 * q.Hv.size()))) return rc;
   }
   if ((rc = up(d.arow, q.arow.data(), 4 * q.arow.size()))) return rc;
+  if (q.ucols) {
+    if ((rc = up(d.U, q.U.data(), 8 * q.U.size()))) return rc;
+    if ((rc = up(d.uw, q.uw.data(), 8 * q.uw.size()))) return rc;
+  }
   if ((rc = up(d.wR, q.wR.data(), 8 * q.wR.size()))) return rc;
   if ((rc = up(d.h0, q.h0.data(), 8 * n))) return rc;
   if ((rc = up(d.c, q.c.data(), 8 * n))) return rc;
@@ -992,6 +1026,7 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   if ((rc = up(d.fu, q.fu.data(), n))) return rc;
   CUDA_TRY(h, cudaMemsetAsync(d.hist, 0, sizeof(unsigned int) * kHistBins, h->st));
   CUDA_TRY(h, cudaMemsetAsync(d.slotR, 0xff, sizeof(int32_t) * std::max<int64_t>(q.nR, 1), h->st));
+  if (d.ucols) CUDA_TRY(h, cudaMemsetAsync(d.lrs, 0, sizeof(double) * d.ucols, h->st));
   std::memset(h->hs, 0, sizeof(Scal));
   push_options(h);
   h->hs->mu = h->hs->mu0 = 1.0;
@@ -1064,8 +1099,10 @@ int ipm_share_qp(ipm_handle* h, ipm_handle* src, void* stream) {
   if ((rc = cp(d.fl, sd.fl, n))) return rc;
   if ((rc = cp(d.fu, sd.fu, n))) return rc;
   if ((rc = cp(d.diagH, sd.diagH, 8 * n))) return rc;
+  if (d.ucols && (rc = cp(d.uw, sd.uw, 8 * d.ucols))) return rc;
   CUDA_TRY(h, cudaMemsetAsync(d.hist, 0, sizeof(unsigned int) * kHistBins, h->st));
   CUDA_TRY(h, cudaMemsetAsync(d.slotR, 0xff, sizeof(int32_t) * std::max<int64_t>(nR, 1), h->st));
+  if (d.ucols) CUDA_TRY(h, cudaMemsetAsync(d.lrs, 0, sizeof(double) * d.ucols, h->st));
   std::memset(h->hs, 0, sizeof(Scal));
   push_options(h);
   h->hs->mu = h->hs->mu0 = 1.0;
@@ -1555,7 +1592,11 @@ int ipm_profile_operator(ipm_handle* h, int reps, double* ms_rows, double* ms_co
   // the passes the handle's PCG runs: FP64, or the reduced-precision ones of its storage
   const bool lp = d.storage != ST_F64;
   if (lp) CUDA_TRY(h, launch_mirror_p32(d, g, h->st));
-  auto rows = [&]() { return lp ? launch_op_rows_lp_only(d, g, h->st) : launch_op_rows_only(d, g, h->st); };
+  auto rows = [&]() {
+    cudaError_t e = lp ? launch_op_rows_lp_only(d, g, h->st) : launch_op_rows_only(d, g, h->st);
+    if (e == cudaSuccess && d.ucols) e = launch_lr(d, d.p, 0, h->st);   // U^T p belongs to the first half
+    return e;
+  };
   auto cols = [&]() { return lp ? launch_op_cols_lp_only(d, g, h->st) : launch_op_cols_only(d, g, h->st); };
   std::vector<cudaEvent_t> ev(3 * reps);
   for (auto& e : ev) CUDA_TRY(h, cudaEventCreate(&e));
@@ -1582,24 +1623,27 @@ int ipm_profile_operator(ipm_handle* h, int reps, double* ms_rows, double* ms_co
   const double nnz = (double)d.nnzR, nnzh = (double)d.nnzHs;
   if (ms_rows) *ms_rows = tr / reps;
   if (ms_cols) *ms_cols = tc / reps;
+  // low-rank term: U read once in each half (U^T p, then U (W t)), p and W t read once
+  const double lr_b = d.ucols ? 8.0 * (double)d.n * (double)d.ucols + 8.0 * (double)d.ucols : 0.0;
+  const double lr_f = d.ucols ? 2.0 * (double)d.n * (double)d.ucols : 0.0;
   if (lp) {
     const double vb = d.storage == ST_F32 ? 4.0 : (d.storage == ST_BF16 ? 2.0 : 1.0);
     // rows: narrow values + indices, row pointers, scale, w_R, thR read, w32 written, p32 read once
-    if (bytes_rows) *bytes_rows = (vb + 4.0) * nnz + 8.0 * (d.nR + 1) + 24.0 * d.nR + 4.0 * d.n;
+    if (bytes_rows) *bytes_rows = (vb + 4.0) * nnz + 8.0 * (d.nR + 1) + 24.0 * d.nR + 4.0 * d.n + lr_b;
     // cols: narrow values + indices, row pointers, w32 read once, p, h0, sigma read, q written
     if (bytes_cols) *bytes_cols = (vb + 4.0) * nnz + 8.0 * (d.n + 1) + 4.0 * d.nR + 32.0 * d.n +
-                                  (d.Hs_ptr ? 12.0 * nnzh + 8.0 * (d.n + 1) : 0.0);
-    if (flops_rows) *flops_rows = 2.0 * nnz + 4.0 * d.nR;
-    if (flops_cols) *flops_cols = 2.0 * nnz + 2.0 * nnzh + 4.0 * d.n;
+                                  (d.Hs_ptr ? 12.0 * nnzh + 8.0 * (d.n + 1) : 0.0) + lr_b;
+    if (flops_rows) *flops_rows = 2.0 * nnz + 4.0 * d.nR + lr_f;
+    if (flops_cols) *flops_cols = 2.0 * nnz + 2.0 * nnzh + 4.0 * d.n + lr_f;
     return IPM_OK;
   }
   // rows: values + indices, row pointers, omega, v written, p read once
-  if (bytes_rows) *bytes_rows = 12.0 * nnz + 8.0 * (d.nR + 1) + 16.0 * d.nR + 8.0 * d.n;
+  if (bytes_rows) *bytes_rows = 12.0 * nnz + 8.0 * (d.nR + 1) + 16.0 * d.nR + 8.0 * d.n + lr_b;
   // cols: values + indices, row pointers, v read once, p, h0, sigma read, q written (+ Hs)
   if (bytes_cols) *bytes_cols = 12.0 * nnz + 8.0 * (d.n + 1) + 8.0 * d.nR + 32.0 * d.n +
-                                (d.Hs_ptr ? 12.0 * nnzh + 8.0 * (d.n + 1) : 0.0);
-  if (flops_rows) *flops_rows = 2.0 * nnz + d.nR;
-  if (flops_cols) *flops_cols = 2.0 * nnz + 2.0 * nnzh + 4.0 * d.n;
+                                (d.Hs_ptr ? 12.0 * nnzh + 8.0 * (d.n + 1) : 0.0) + lr_b;
+  if (flops_rows) *flops_rows = 2.0 * nnz + d.nR + lr_f;
+  if (flops_cols) *flops_cols = 2.0 * nnz + 2.0 * nnzh + 4.0 * d.n + lr_f;
   return IPM_OK;
 }
 

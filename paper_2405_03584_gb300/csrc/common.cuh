@@ -37,6 +37,7 @@ struct Scal {
   int n_stiff, stiff_max, max_stiff_seen, chol_fail;
   // FP64 refinement of a reduced-precision Newton step
   double tol2_outer, rr_outer, refine_eta;
+  double lr_quad;               // x^T U W U^T x of the last residual summary
   // warm start: pairs raised to at least warm_rho * mu0_cold (mu0 of the last cold start)
   double mu0_cold, warm_rho;
   int refine_it, refine_max, cg_step_total, cg_conv_outer, fallback, fallback_total;

@@ -1,5 +1,5 @@
 // Dense pieces of the preconditioners (sm_103a, float64):
-//   * k_gram_K   : K = Hs + R^T diag(omega) R + diag(h0 + sigma) as a dense n x n matrix
+//   * k_gram_K   : K = Hs + R^T diag(omega) R + U W U^T + diag(h0 + sigma) as a dense n x n matrix
 //                  (the DENSE preconditioner: one diagonal block covering all variables);
 //   * k_chol_*   : in-place blocked Cholesky factor (lower) with pivot flooring;
 //   * k_mirror   : copies L into the upper triangle so both sweeps of the inverse read rows;
@@ -25,6 +25,17 @@ __global__ void k_gram_K(Dev d) {
     __syncthreads();
     if (d.Hs_ptr) {
       for (int64_t e = d.Hs_ptr[j] + threadIdx.x; e < d.Hs_ptr[j + 1]; e += blockDim.x) row[d.Hs_idx[e]] += d.Hs_val[e];
+      __syncthreads();
+    }
+    if (d.ucols) {
+      // (U W U^T)_ji = sum_r U_jr w_r U_ir, one column i per thread
+      const double* uj = d.U + j * d.ucols;
+      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const double* ui = d.U + i * d.ucols;
+        double a = 0.0;
+        for (int64_t r = 0; r < d.ucols; ++r) a = fma(uj[r] * d.uw[r], ui[r], a);
+        row[i] += a;
+      }
       __syncthreads();
     }
     for (int64_t e = d.RT_ptr[j]; e < d.RT_ptr[j + 1]; ++e) {

@@ -61,12 +61,97 @@ Geo make_geo(const Dev& d) {
   return g;
 }
 
+// ------------------------------------------------------------------------------ low-rank term
+
+// H's low-rank term U W U^T (eq:bfgs_hessian: H = H0 + U W U^T, U dense n x 2k, W diagonal) is
+// applied matrix-free in two dense passes over U: t = U^T v (this pair of kernels, a
+// reduction over the n rows of U split into row chunks, one partial vector per block, summed
+// in block order), then (U (W t))_j inside the column kernels (lr_row).  Row-major U makes
+// both passes read rows of U contiguously.
+__global__ void k_lr_part(Dev d, const double* __restrict__ v) {
+  const int64_t uc = d.ucols, n = d.n;
+  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t j0 = (int64_t)blockIdx.x * per, j1 = j0 + per < n ? j0 + per : n;
+  for (int64_t r = threadIdx.x; r < uc; r += blockDim.x) {
+    const double* col = d.U + r;
+    double a0 = 0.0, a1 = 0.0;
+    int64_t j = j0;
+    for (; j + 3 < j1; j += 4) {
+      const double u0 = __ldg(col + j * uc), u1 = __ldg(col + (j + 1) * uc);
+      const double u2 = __ldg(col + (j + 2) * uc), u3 = __ldg(col + (j + 3) * uc);
+      a0 = fma(u0, __ldg(v + j), a0);
+      a1 = fma(u1, __ldg(v + j + 1), a1);
+      a0 = fma(u2, __ldg(v + j + 2), a0);
+      a1 = fma(u3, __ldg(v + j + 3), a1);
+    }
+    for (; j < j1; ++j) a0 = fma(__ldg(col + j * uc), __ldg(v + j), a0);
+    d.upart[(int64_t)blockIdx.x * uc + r] = a0 + a1;
+  }
+}
+
+// lrs = uw o t, t_r = the sum of the block partials of column r (one warp per r: lane l adds
+// the partials of blocks l, l + 32, ..., then a fixed shuffle tree); quad: lrq_r = uw_r t_r^2.
+__global__ void k_lr_final(Dev d, int quad) {
+  const int64_t uc = d.ucols;
+  const int lane = threadIdx.x & 31;
+  for (int64_t r = gwarp(); r < uc; r += nwarps()) {
+    double t = 0.0;
+    for (int b = lane; b < d.ublocks; b += 32) t += d.upart[(int64_t)b * uc + r];
+    t = warp_sum(t);
+    if (lane == 0) {
+      const double sv = d.uw[r] * t;
+      d.lrs[r] = sv;
+      if (quad) d.lrq[r] = sv * t;
+    }
+  }
+}
+
+// v^T U W U^T v = sum_r lrq_r (one block, fixed order) into the device scalars.
+__global__ void k_lr_quad(Dev d) {
+  __shared__ double sh[32];
+  double q = 0.0;
+  for (int64_t r = threadIdx.x; r < d.ucols; r += blockDim.x) q += d.lrq[r];
+  q = block_reduce<0>(q, sh);
+  if (threadIdx.x == 0) d.sc->lr_quad = q;
+}
+
+cudaError_t launch_lr(const Dev& d, const double* v, int quad, cudaStream_t st) {
+  if (!d.ucols) return cudaSuccess;
+  const int th = (int)std::min<int64_t>(1024, ((d.ucols + 31) / 32) * 32);
+  k_lr_part<<<d.ublocks, th, 0, st>>>(d, v);
+  k_lr_final<<<(int)std::min<int64_t>((d.ucols + 7) / 8, 4096), 256, 0, st>>>(d, quad);
+  if (quad) k_lr_quad<<<1, 1024, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+// (U lrs)_j by a group of G lanes over the contiguous row j of U (all lanes of the group get it).
+template <int G>
+__device__ __forceinline__ double lr_row(const Dev& d, const int64_t j, const bool ok, const int gl) {
+  double a = 0.0;
+  if (ok) {
+    const double* row = d.U + j * d.ucols;
+    for (int64_t r = gl; r < d.ucols; r += G) a = fma(__ldg(row + r), __ldg(d.lrs + r), a);
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  return a;
+}
+
 // ------------------------------------------------------------------------------ setup
 
-// diag(H)_j = h0_j + sum_i w_R,i R_ij^2 + Hs_jj  (computed once; Section 4.1.2 caches it).
+// diag(H)_j = h0_j + sum_i w_R,i R_ij^2 + sum_r uw_r U_jr^2 + Hs_jj  (computed once; Section
+// 4.1.2 caches it).
 __global__ void k_diagH(Dev d) {
   for (int64_t j = gwarp(); j < d.n; j += nwarps()) {
     double acc = warp_row_dot<true>(d.RT_ptr[j], d.RT_ptr[j + 1], d.RT_idx, d.RT_val, d.wR);
+    if (d.ucols) {
+      double ul = 0.0;
+      for (int64_t r = threadIdx.x & 31; r < d.ucols; r += 32) {
+        const double u = d.U[j * d.ucols + r];
+        ul = fma(d.uw[r] * u, u, ul);
+      }
+      acc += warp_sum(ul);
+    }
     double hjj = 0.0;
     if (d.Hs_ptr) {
       for (int64_t e = d.Hs_ptr[j] + (threadIdx.x & 31); e < d.Hs_ptr[j + 1]; e += 32)
@@ -150,10 +235,11 @@ __global__ void k_cols_resid(Dev d, double* part) {
       const int64_t hb = ok ? d.Hs_ptr[j] : 0, he = ok ? d.Hs_ptr[j + 1] : 0;
       hs = group_row_dot<G, false>(hb, he, glane<G>(), d.Hs_idx, d.Hs_val, d.x);
     }
+    const double lr = d.ucols ? lr_row<G>(d, j, ok, glane<G>()) : 0.0;
     if (ok && glane<G>() == 0) {
       const double xj = d.x[j];
       const double hsx = hs + d.h0[j] * xj;
-      const double hx = hx_f + hsx;
+      const double hx = hx_f + hsx + lr;
       const double zl = d.zl[j], zu = d.zu[j];
       const double rd = hx + d.c[j] + aty - zl + zu;
       d.Hx[j] = hx;
@@ -228,7 +314,7 @@ __global__ void k_resid_final(Dev d, int gR, int gM, int gN, const double* part)
   const double viol_b = fmax(0.0, tot(15, gN, 1));
   if (threadIdx.x == 0) {
     Scal* sc = d.sc;
-    const double xHx = xFx + xHsx;
+    const double xHx = xFx + xHsx + (d.ucols ? sc->lr_quad : 0.0);
     const double pobj = 0.5 * xHx + cx;
     const double dobj = -0.5 * xHx - by + lzl - uzu;
     const double bn = sc->bnorm, cn = sc->cnorm;
@@ -260,6 +346,7 @@ cudaError_t launch_residual_summary(const Dev& d, const Geo& g, cudaStream_t st)
     DISPATCH_G(d.g_rows, k_rows_resid<G><<<g.gR, kBlock, 0, st>>>(d, part));
   }
   if (d.m) k_cons_resid<<<g.eM, kBlock, 0, st>>>(d, part);
+  launch_lr(d, d.x, 1, st);
   DISPATCH_G(d.g_cols, k_cols_resid<G><<<g.gN, kBlock, 0, st>>>(d, part));
   k_resid_final<<<1, 1024, 0, st>>>(d, g.gR, g.eM, g.gN, part);
   return cudaGetLastError();
@@ -317,6 +404,7 @@ __global__ void k_start_z(Dev d) {
       const int64_t hb = ok ? d.Hs_ptr[j] : 0, he = ok ? d.Hs_ptr[j + 1] : 0;
       hs = group_row_dot<G, false>(hb, he, glane<G>(), d.Hs_idx, d.Hs_val, d.x);
     }
+    if (d.ucols) hs += lr_row<G>(d, j, ok, glane<G>());
     if (ok && glane<G>() == 0) {
       const double g = hx + hs + d.h0[j] * d.x[j] + d.c[j];
       d.zl[j] = d.fl[j] ? fmax(1.0, g) : 0.0;
@@ -348,6 +436,7 @@ cudaError_t launch_start_point(const Dev& d, const Geo& g, cudaStream_t st) {
   k_start_x<<<g.eN, kBlock, 0, st>>>(d);
   if (d.nR) DISPATCH_G(d.g_rows, k_rows_resid<G><<<g.gR, kBlock, 0, st>>>(d, d.partials));
   if (d.m) k_start_s<<<g.eM, kBlock, 0, st>>>(d);
+  launch_lr(d, d.x, 0, st);
   DISPATCH_G(d.g_cols, k_start_z<G><<<g.gN, kBlock, 0, st>>>(d));
   if (d.m) k_start_y<<<g.eM, kBlock, 0, st>>>(d);
   cudaError_t e = launch_residual_summary(d, g, st);
@@ -874,6 +963,7 @@ __global__ void k_op_cols(Dev d) {
       const int64_t hb = ok ? d.Hs_ptr[j] : 0, he = ok ? d.Hs_ptr[j + 1] : 0;
       acc += group_row_dot<G, false>(hb, he, glane<G>(), d.Hs_idx, d.Hs_val, d.p);
     }
+    if (d.ucols) acc += lr_row<G>(d, j, ok, glane<G>());
     if (ok && glane<G>() == 0) {
       const double pj = d.p[j];
       const double qj = acc + (d.h0[j] + d.sigma[j]) * pj;
@@ -1102,6 +1192,7 @@ cudaError_t launch_cg_body(const Dev& d, const Geo& g, int precond, cudaGraphCon
     if (e != cudaSuccess) return e;
   } else {
     if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<0, G><<<g.gR, kBlock, 0, st>>>(d));
+    launch_lr(d, d.p, 0, st);
     DISPATCH_G(d.g_cols, k_op_cols<0, G><<<g.gN, kBlock, 0, st>>>(d));
   }
   if (precond == PC_DENSE) {
@@ -1126,12 +1217,14 @@ cudaError_t launch_op_rows_only(const Dev& d, const Geo& g, cudaStream_t st) {
 }
 
 cudaError_t launch_op_cols_only(const Dev& d, const Geo& g, cudaStream_t st) {
+  // (the low-rank term uses us from the last launch_lr; the measurement does not re-run it)
   DISPATCH_G(d.g_cols, k_op_cols<1, G><<<g.gN, kBlock, 0, st>>>(d));
   return cudaGetLastError();
 }
 
 cudaError_t launch_apply(const Dev& d, const Geo& g, cudaStream_t st) {
   if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<1, G><<<g.gR, kBlock, 0, st>>>(d));
+  launch_lr(d, d.p, 0, st);
   DISPATCH_G(d.g_cols, k_op_cols<1, G><<<g.gN, kBlock, 0, st>>>(d));
   return cudaGetLastError();
 }

@@ -172,6 +172,19 @@ __device__ __forceinline__ float group_row_dot_lp(const int64_t beg, const int64
   return a;
 }
 
+// (U lrs)_j by a group of G lanes (the FP64 low-rank Hessian term, as in the FP64 kernels).
+template <int G>
+__device__ __forceinline__ double lr_row_lp(const Dev& d, const int64_t j, const bool ok, const int gl) {
+  double a = 0.0;
+  if (ok) {
+    const double* row = d.U + j * d.ucols;
+    for (int64_t r = gl; r < d.ucols; r += G) a = fma(__ldg(row + r), __ldg(d.lrs + r), a);
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  return a;
+}
+
 #define FOR_GROUP_ROWS_L(G, r, ok, nrows)                                                                    \
   for (int64_t r##_0 = (int64_t)gwarp_l() * (32 / G); r##_0 < (nrows); r##_0 += (int64_t)nwarps_l() * (32 / G)) \
     for (int64_t r = r##_0 + (threadIdx.x & 31) / G, r##_once = 0; r##_once == 0; r##_once = 1)               \
@@ -226,6 +239,7 @@ __global__ void k_op_cols_lp(Dev d, int standalone) {
       const int64_t hb = ok ? d.Hs_ptr[j] : 0, he = ok ? d.Hs_ptr[j + 1] : 0;
       hs = group_row_dot<G, false>(hb, he, gl, d.Hs_idx, d.Hs_val, d.p);
     }
+    if (d.ucols) hs += lr_row_lp<G>(d, j, ok, gl);   // low-rank term kept in FP64
     if (ok && gl == 0) {
       const double pj = d.p[j];
       double st = 0.0;
@@ -272,6 +286,7 @@ __global__ void k_op_cols_lp(Dev d, int standalone) {
 
 cudaError_t launch_op_lp(const Dev& d, const Geo& g, cudaStream_t st) {
   k_stiff_op_u<<<(d.stiff_cap + 7) / 8, kBlock, 0, st>>>(d);
+  launch_lr(d, d.p, 0, st);
   if (d.nR) DISPATCH_SG(d.storage, d.g_rows, k_op_rows_lp<S, G><<<g.gR, kBlock, 0, st>>>(d, 0));
   DISPATCH_SG(d.storage, d.g_cols, k_op_cols_lp<S, G><<<g.gN, kBlock, 0, st>>>(d, 0));
   return cudaGetLastError();

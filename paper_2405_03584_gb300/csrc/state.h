@@ -24,6 +24,14 @@ struct Dev {
   int64_t nnzA;
   const int64_t* Hs_ptr; const int32_t* Hs_idx; const double* Hs_val;   // nullptr if none
   const int32_t* arow;         // m: row of R holding constraint k
+  // low-rank Hessian term U diag(uw) U^T (eq:bfgs_hessian): U is n x ucols, row-major
+  int64_t ucols;
+  const double* U;
+  double* uw;                  // ucols weights
+  double* lrs;                 // ucols: uw o (U^T v) for the vector v of the last launch_lr
+  double* upart;               // ublocks x ucols partial sums of U^T v
+  double* lrq;                 // ucols: uw o t^2 (terms of v^T U W U^T v)
+  int ublocks;
   const double *wR, *h0, *c, *b, *l, *u;
   const unsigned char *fl, *fu;  // finite-bound masks (n)
   double* diagH;               // n: diag(H), computed once
@@ -71,6 +79,8 @@ struct Geo {
 
 Geo make_geo(const Dev& d);
 
+// ---- low-rank Hessian term: lrs = uw o (U^T v); quad: also v^T U W U^T v into the scalars ----
+cudaError_t launch_lr(const Dev& d, const double* v, int quad, cudaStream_t st);
 // ---- setup and start point ----
 cudaError_t launch_diagH(const Dev& d, cudaStream_t st);
 cudaError_t launch_start_point(const Dev& d, const Geo& g, cudaStream_t st);

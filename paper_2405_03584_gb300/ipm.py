@@ -51,7 +51,8 @@ class QP(C.Structure):
                 ("c", C.c_void_p), ("b", C.c_void_p), ("l", C.c_void_p), ("u", C.c_void_p),
                 ("h0", C.c_void_p), ("H_dense", C.c_void_p), ("f_rows", C.c_int64),
                 ("F_indptr", C.c_void_p), ("F_indices", C.c_void_p), ("F_data", C.c_void_p), ("f_w", C.c_void_p),
-                ("a_rows", C.c_void_p), ("A_indptr", C.c_void_p), ("A_indices", C.c_void_p), ("A_data", C.c_void_p)]
+                ("a_rows", C.c_void_p), ("A_indptr", C.c_void_p), ("A_indices", C.c_void_p), ("A_data", C.c_void_p),
+                ("u_cols", C.c_int64), ("U", C.c_void_p), ("u_w", C.c_void_p)]
 
 
 class Info(C.Structure):
@@ -222,9 +223,10 @@ class Solver:
 
     # ---------------------------------------------------------------- problem
     def set_qp(self, n, m, c, b=None, l=None, u=None, h0=None, H_dense=None, F=None, f_w=None,
-               a_rows=None, A=None, stream=None):
-        """F and A are CSR triplets (indptr int64, indices int32, data float64)."""
-        arrays = [c, b, l, u, h0, H_dense, f_w, a_rows] + (list(F) if F else []) + (list(A) if A else [])
+               a_rows=None, A=None, U=None, u_w=None, stream=None):
+        """F and A are CSR triplets (indptr int64, indices int32, data float64); U is n x k
+        (row-major) with weights u_w: the low-rank Hessian term U diag(u_w) U^T."""
+        arrays = [c, b, l, u, h0, H_dense, f_w, a_rows, U, u_w] + (list(F) if F else []) + (list(A) if A else [])
         mem = MEM_DEVICE if any(_is_dev(a) for a in arrays if a is not None) else MEM_HOST
         mk = _Marshal(mem)
         q = QP()
@@ -245,6 +247,9 @@ class Solver:
         if A is not None and m:
             ip, ix, dv = A
             q.A_indptr, q.A_indices, q.A_data = mk.ptr(ip, np.int64), mk.ptr(ix, np.int32), mk.ptr(dv, np.float64)
+        if U is not None:
+            q.u_cols = int(U.shape[1]) if hasattr(U, "shape") else int(len(u_w))
+            q.U, q.u_w = mk.ptr(U, np.float64), mk.ptr(u_w, np.float64)
         self._check(load().ipm_set_qp(self._h, C.byref(q), _default_stream(stream)), "ipm_set_qp")
         self.n, self.m = int(n), int(m)
         return self
@@ -265,6 +270,13 @@ class Solver:
         return self.set_qp(p["n"], p["m"], p["c"], p["b"], p["l"], p["u"], h0=p["h0"],
                            F=(p["D_indptr"], p["D_indices"], p["D_data"]), f_w=p["w"],
                            a_rows=p["a_rows"] if p["m"] else None, stream=stream)
+
+    def set_qp_bfgs(self, p, stream=None):
+        """QP with a quasi-Newton Hessian from ``workloads.bfgs_qp``: H = diag(h0) + U diag(w) U^T,
+        constraints (if any) as a CSR matrix A."""
+        A = (p["A_indptr"], p["A_indices"], p["A_data"]) if p["m"] else None
+        return self.set_qp(p["n"], p["m"], p["c"], p["b"] if p["m"] else None, p["l"], p["u"], h0=p["h0"],
+                           A=A, U=p["U"], u_w=p["uw"], stream=stream)
 
     def update_costs(self, f_w=None, c=None, stream=None):
         """New factor weights and/or linear cost for the loaded QP (matrices unchanged)."""

@@ -27,7 +27,7 @@ import numpy as np
 
 __all__ = [
     "dense_qp", "rt_qp", "rt_batch_sizes", "rt_batch", "perturb_chain_step",
-    "serving_stream", "request_costs", "csr_to_dense", "random_iterate",
+    "serving_stream", "request_costs", "bfgs_qp", "csr_to_dense", "random_iterate",
 ]
 
 
@@ -197,6 +197,59 @@ def request_costs(plan: dict, req: dict, prev: tuple | None = None, rel: float =
     base = dict(w=plan["w"], c=plan["c"]) if prev is None else dict(w=prev[0], c=prev[1])
     q = perturb_chain_step(base, np.random.default_rng([req["seed"], step]), rel)
     return q["w"], q["c"], step
+
+
+def bfgs_qp(n: int = 77_373, k: int = 100, m_ub: int = 0, m_lb: int = 0, density: float = 0.01,
+            seed: int = 5, lam_lo: float = 1e-2, lam_hi: float = 1e2, c_mode: str = "random",
+            ub_fac: float = 1.2, lb_fac: float = 0.8) -> dict:
+    """QP sub-problem with a quasi-Newton Hessian in compact form (Section 3.3, eq:bfgs_hessian):
+    H = H0 + U diag(w) U^T, H0 = diag(h0), U n x 2k.
+
+    H0 = diag(U(0.5, 2)).  k BFGS updates H <- H - (H s)(H s)^T / (s^T H s) + y y^T / (y^T s)
+    from seeded pairs: s ~ N(0, 1/n), y = B s with B = diag(lam), lam log-uniform on
+    [lam_lo, lam_hi] (so y^T s > 0 and every H stays positive definite).  Each update appends
+    the columns H s (weight -1 / (s^T H s)) and y (weight 1 / (y^T s)) to U; H s is applied
+    through the compact form built so far.  c ~ N(0, 1) (c_mode "random"), or c = -H x_t +
+    0.1 N(0, 1) with x_t ~ U(0.5, 1.5) (c_mode "target": the objective pulls towards a plan
+    x_t); x >= 0 (one bound per variable, no upper bound).  Constraints (m = m_ub + m_lb rows
+    of a banded dose-like matrix G with lognormal values, as in ``rt_qp``): upper rows
+    G_i x <= ub_fac G_i 1, lower rows written as -G_i x <= -lb_fac G_i 1, so x = 1 is strictly
+    feasible.  A is returned as CSR.
+    Sizes of the paper's cases (Table 1): proton n = 77373, m = 0 (k up to 100 before spot
+    filtering); VMAT n = 13425, m = 52867 upper + 15751 lower rows (k up to 33).  The update
+    steps S (n x k) and lam are returned too (y_i = lam o s_i)."""
+    rng = np.random.default_rng(seed)
+    h0 = rng.uniform(0.5, 2.0, size=n)
+    lam = 10.0 ** rng.uniform(np.log10(lam_lo), np.log10(lam_hi), size=n)
+    U = np.zeros((n, 2 * k))
+    w = np.zeros(2 * k)
+    S = np.zeros((n, k))
+    for i in range(k):
+        sv = rng.normal(0.0, 1.0 / np.sqrt(n), size=n)
+        S[:, i] = sv
+        yv = lam * sv
+        Hs = h0 * sv + U[:, :2 * i] @ (w[:2 * i] * (U[:, :2 * i].T @ sv))
+        U[:, 2 * i] = Hs
+        w[2 * i] = -1.0 / float(sv @ Hs)
+        U[:, 2 * i + 1] = yv
+        w[2 * i + 1] = 1.0 / float(yv @ sv)
+    c = rng.normal(size=n)
+    if c_mode == "target":
+        xt = rng.uniform(0.5, 1.5, size=n)
+        c = -(h0 * xt + U @ (w * (U.T @ xt))) + 0.1 * c
+    m = m_ub + m_lb
+    out = dict(kind="bfgs", n=n, m=m, k=k, h0=h0, U=U, uw=w, c=c, l=np.zeros(n), u=np.full(n, np.inf),
+               b=np.zeros(m), S=S, lam=lam)
+    if m:
+        indptr, indices = _band_rows(rng, m, n, density)
+        data = rng.lognormal(0.0, 1.0, size=indices.shape[0])
+        rowid = np.repeat(np.arange(m), np.diff(indptr))
+        g1 = np.bincount(rowid, weights=data, minlength=m)      # G_i . 1
+        sign = np.ones(m)
+        sign[m_ub:] = -1.0
+        out["A_indptr"], out["A_indices"], out["A_data"] = indptr, indices, data * sign[rowid]
+        out["b"] = np.where(sign > 0, ub_fac * g1, -lb_fac * g1)
+    return out
 
 
 def csr_to_dense(indptr, indices, data, shape):

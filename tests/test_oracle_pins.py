@@ -302,3 +302,37 @@ def test_checker_sampled_entries_match_dense():
     np.testing.assert_allclose(q, (K @ pv)[cols], rtol=1e-11)
     rd = kkt_check.rt_residual_dual(p, it.x, it.y, it.zl, it.zu)
     np.testing.assert_allclose(rd, res[0], rtol=1e-11, atol=1e-9)
+
+
+def test_bfgs_compact_form_equals_dense_recursion():
+    """The quasi-Newton Hessian of Section 3.3 (eq:bfgs_hessian) in compact form H0 + U W U^T
+    against the BFGS recursion carried out on dense matrices; secant condition; definiteness."""
+    p = W.bfgs_qp(n=60, k=7, m_ub=5, m_lb=3, density=0.2, seed=9)
+    qp = ipm.from_bfgs(p)
+    Hd = np.diag(p["h0"])
+    for i in range(p["k"]):
+        s = p["S"][:, i]
+        y = p["lam"] * s
+        Hs = Hd @ s
+        Hd = Hd - np.outer(Hs, Hs) / (s @ Hs) + np.outer(y, y) / (y @ s)
+    np.testing.assert_allclose(qp.H, Hd, rtol=1e-12, atol=1e-12 * np.abs(Hd).max())
+    s_last = p["S"][:, -1]
+    np.testing.assert_allclose(qp.H @ s_last, p["lam"] * s_last, rtol=1e-10, atol=1e-13)
+    assert np.linalg.eigvalsh(qp.H).min() > 0
+    # constraints: upper rows G x <= 1.2 G 1, lower rows -G x <= -0.8 G 1; x = 1 strictly feasible
+    assert np.all(qp.A @ np.ones(p["n"]) < qp.b)
+    assert np.all(qp.b[:5] > 0) and np.all(qp.b[5:] < 0)
+
+
+def test_bfgs_qp_solution_kkt():
+    """Oracle solve of a small quasi-Newton QP satisfies the checker's KKT conditions and the
+    optimality of a bounds-only problem with a positive definite H (x >= 0)."""
+    p = W.bfgs_qp(n=40, k=4, seed=2)
+    qp = ipm.from_bfgs(p)
+    it, info = ipm.solve(qp, tol=1e-10)
+    assert info.status == "optimal"
+    rk = kkt_check.rel_kkt(kkt_check.bfgs_ops(p), it.x, it.y, it.zl, it.zu)
+    assert rk <= 1e-9
+    g = qp.H @ it.x + qp.c        # x >= 0: g >= 0 where x = 0, g = 0 where x > 0
+    act = it.x < 1e-7
+    assert np.all(g[act] >= -1e-6) and np.abs(g[~act]).max() <= 1e-6 * (1 + np.abs(qp.c).max())
