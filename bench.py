@@ -185,16 +185,20 @@ def run_reference(args):
 
 
 def run_operator_only(args):
-    """Small capture target for profilers: the RT workload, three IPM iterations, then the two
-    operator kernels three times each (ipm_profile_operator)."""
+    """Small capture target for profilers: the RT workload (or --bfgs), three IPM iterations,
+    then the two operator passes three times each (ipm_profile_operator), in the storage of
+    --storage."""
     import torch
     from paper_2405_03584_gb300 import build, ipm, workloads as W
     torch.cuda.set_device(0)
     build.build()
-    p = W.rt_qp(n=N_FULL, seed=SEED)
     lr, lc = (int(v) for v in args.lanes.split(","))
-    s = ipm.Solver(tol_kkt=TOL, precond="jacobi_lr", max_ipm=3, lanes_rows=lr, lanes_cols=lc)
-    s.set_qp_rt(p)
+    s = ipm.Solver(tol_kkt=TOL, precond="jacobi_lr", max_ipm=3, lanes_rows=lr, lanes_cols=lc,
+                   storage=args.storage)
+    if args.bfgs:
+        s.set_qp_bfgs(_bfgs_problem(args.bfgs))
+    else:
+        s.set_qp_rt(W.rt_qp(n=N_FULL, seed=SEED))
     s.solve()
     out = s.profile_operator(reps=3)
     out["lanes"] = [s.get()["info"]["lanes_rows"], s.get()["info"]["lanes_cols"]]
@@ -356,6 +360,14 @@ def run_serve(args):
     return 0
 
 
+def _bfgs_problem(case):
+    from paper_2405_03584_gb300 import workloads as W
+    if case == "proton":
+        return W.bfgs_qp(n=77373, k=100, seed=5)
+    return W.bfgs_qp(n=13425, k=33, m_ub=52867, m_lb=15751, density=0.01, seed=6, c_mode="target",
+                     ub_fac=1.1, lb_fac=0.9)
+
+
 def run_bfgs(args):
     """The paper's quasi-Newton Hessian regime (Section 3.3, eq:bfgs_hessian; Table 1 sizes):
     proton n = 77373, bounds only, 2k = 200 update columns; VMAT n = 13425 with 52867 upper
@@ -366,11 +378,7 @@ def run_bfgs(args):
     from oracle import kkt_check
     torch.cuda.set_device(0)
     build.build()
-    if args.bfgs == "proton":
-        p = W.bfgs_qp(n=77373, k=100, seed=5)
-    else:
-        p = W.bfgs_qp(n=13425, k=33, m_ub=52867, m_lb=15751, density=0.01, seed=6, c_mode="target",
-                      ub_fac=1.1, lb_fac=0.9)
+    p = _bfgs_problem(args.bfgs)
     s = ipm.Solver(tol_kkt=TOL, precond="jacobi_lr", storage=args.storage,
                    stiff_max=1024 if args.bfgs == "vmat" else 256)
     s.set_qp_bfgs(p)

@@ -68,35 +68,66 @@ Geo make_geo(const Dev& d) {
 // reduction over the n rows of U split into row chunks, one partial vector per block, summed
 // in block order), then (U (W t))_j inside the column kernels (lr_row).  Row-major U makes
 // both passes read rows of U contiguously.
-__global__ void k_lr_part(Dev d, const double* __restrict__ v) {
+__global__ void __launch_bounds__(256) k_lr_part(Dev d, const double* __restrict__ v) {
+  // 8 warps per block; warp w takes rows j0 + w, j0 + w + 8, ... of the block's chunk; lane l
+  // accumulates columns r0 + l + 32 c (c < 4) of a 128-column slice; the warps' sums are
+  // added in warp order through shared memory.
+  constexpr int RC = 4;
+  __shared__ double sh[8][32 * RC];
   const int64_t uc = d.ucols, n = d.n;
   const int64_t per = (n + gridDim.x - 1) / gridDim.x;
   const int64_t j0 = (int64_t)blockIdx.x * per, j1 = j0 + per < n ? j0 + per : n;
-  for (int64_t r = threadIdx.x; r < uc; r += blockDim.x) {
-    const double* col = d.U + r;
-    double a0 = 0.0, a1 = 0.0;
-    int64_t j = j0;
-    for (; j + 3 < j1; j += 4) {
-      const double u0 = __ldg(col + j * uc), u1 = __ldg(col + (j + 1) * uc);
-      const double u2 = __ldg(col + (j + 2) * uc), u3 = __ldg(col + (j + 3) * uc);
-      a0 = fma(u0, __ldg(v + j), a0);
-      a1 = fma(u1, __ldg(v + j + 1), a1);
-      a0 = fma(u2, __ldg(v + j + 2), a0);
-      a1 = fma(u3, __ldg(v + j + 3), a1);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int64_t r0 = 0; r0 < uc; r0 += 32 * RC) {
+    double acc[RC];
+#pragma unroll
+    for (int c = 0; c < RC; ++c) acc[c] = 0.0;
+    int64_t j = j0 + w;
+    for (; j + 8 < j1; j += 16) {
+      const double* u0 = d.U + j * uc + r0 + lane;
+      const double* u1 = u0 + 8 * uc;
+      const double x0 = __ldg(v + j), x1 = __ldg(v + j + 8);
+      double t0[RC], t1[RC];
+#pragma unroll
+      for (int c = 0; c < RC; ++c) {
+        const bool in = r0 + lane + 32 * c < uc;
+        t0[c] = in ? __ldg(u0 + 32 * c) : 0.0;
+        t1[c] = in ? __ldg(u1 + 32 * c) : 0.0;
+      }
+#pragma unroll
+      for (int c = 0; c < RC; ++c) acc[c] = fma(t1[c], x1, fma(t0[c], x0, acc[c]));
     }
-    for (; j < j1; ++j) a0 = fma(__ldg(col + j * uc), __ldg(v + j), a0);
-    d.upart[(int64_t)blockIdx.x * uc + r] = a0 + a1;
+    if (j < j1) {
+      const double* u0 = d.U + j * uc + r0 + lane;
+      const double x0 = __ldg(v + j);
+#pragma unroll
+      for (int c = 0; c < RC; ++c)
+        if (r0 + lane + 32 * c < uc) acc[c] = fma(__ldg(u0 + 32 * c), x0, acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < RC; ++c) sh[w][lane + 32 * c] = acc[c];
+    __syncthreads();
+    for (int t = threadIdx.x; t < 32 * RC; t += blockDim.x) {
+      if (r0 + t < uc) {
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s += sh[q][t];
+        d.upart[(r0 + t) * (int64_t)d.ublocks + blockIdx.x] = s;   // column-major: the final sum reads runs
+      }
+    }
+    __syncthreads();
   }
 }
 
-// lrs = uw o t, t_r = the sum of the block partials of column r (one warp per r: lane l adds
-// the partials of blocks l, l + 32, ..., then a fixed shuffle tree); quad: lrq_r = uw_r t_r^2.
+// lrs = uw o t, t_r = the sum of the block partials of column r (stored column-major; one warp
+// per r: lane l adds the partials of blocks l, l + 32, ..., then a fixed shuffle tree);
+// quad: lrq_r = uw_r t_r^2.
 __global__ void k_lr_final(Dev d, int quad) {
   const int64_t uc = d.ucols;
   const int lane = threadIdx.x & 31;
   for (int64_t r = gwarp(); r < uc; r += nwarps()) {
     double t = 0.0;
-    for (int b = lane; b < d.ublocks; b += 32) t += d.upart[(int64_t)b * uc + r];
+    for (int b = lane; b < d.ublocks; b += 32) t += d.upart[r * (int64_t)d.ublocks + b];
     t = warp_sum(t);
     if (lane == 0) {
       const double sv = d.uw[r] * t;
@@ -117,8 +148,7 @@ __global__ void k_lr_quad(Dev d) {
 
 cudaError_t launch_lr(const Dev& d, const double* v, int quad, cudaStream_t st) {
   if (!d.ucols) return cudaSuccess;
-  const int th = (int)std::min<int64_t>(1024, ((d.ucols + 31) / 32) * 32);
-  k_lr_part<<<d.ublocks, th, 0, st>>>(d, v);
+  k_lr_part<<<d.ublocks, 256, 0, st>>>(d, v);
   k_lr_final<<<(int)std::min<int64_t>((d.ucols + 7) / 8, 4096), 256, 0, st>>>(d, quad);
   if (quad) k_lr_quad<<<1, 1024, 0, st>>>(d);
   return cudaGetLastError();
@@ -130,7 +160,16 @@ __device__ __forceinline__ double lr_row(const Dev& d, const int64_t j, const bo
   double a = 0.0;
   if (ok) {
     const double* row = d.U + j * d.ucols;
-    for (int64_t r = gl; r < d.ucols; r += G) a = fma(__ldg(row + r), __ldg(d.lrs + r), a);
+    double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int64_t r = gl;
+    for (; r + 3 * G < d.ucols; r += 4 * G) {
+      a = fma(__ldg(row + r), __ldg(d.lrs + r), a);
+      a1 = fma(__ldg(row + r + G), __ldg(d.lrs + r + G), a1);
+      a2 = fma(__ldg(row + r + 2 * G), __ldg(d.lrs + r + 2 * G), a2);
+      a3 = fma(__ldg(row + r + 3 * G), __ldg(d.lrs + r + 3 * G), a3);
+    }
+    for (; r < d.ucols; r += G) a = fma(__ldg(row + r), __ldg(d.lrs + r), a);
+    a = (a + a1) + (a2 + a3);
   }
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);

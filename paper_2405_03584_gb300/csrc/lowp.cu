@@ -178,7 +178,16 @@ __device__ __forceinline__ double lr_row_lp(const Dev& d, const int64_t j, const
   double a = 0.0;
   if (ok) {
     const double* row = d.U + j * d.ucols;
-    for (int64_t r = gl; r < d.ucols; r += G) a = fma(__ldg(row + r), __ldg(d.lrs + r), a);
+    double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int64_t r = gl;
+    for (; r + 3 * G < d.ucols; r += 4 * G) {
+      a = fma(__ldg(row + r), __ldg(d.lrs + r), a);
+      a1 = fma(__ldg(row + r + G), __ldg(d.lrs + r + G), a1);
+      a2 = fma(__ldg(row + r + 2 * G), __ldg(d.lrs + r + 2 * G), a2);
+      a3 = fma(__ldg(row + r + 3 * G), __ldg(d.lrs + r + 3 * G), a3);
+    }
+    for (; r < d.ucols; r += G) a = fma(__ldg(row + r), __ldg(d.lrs + r), a);
+    a = (a + a1) + (a2 + a3);
   }
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
