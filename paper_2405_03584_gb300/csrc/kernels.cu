@@ -58,6 +58,10 @@ Geo make_geo(const Dev& d) {
   g.gN = blocks_for(d.n, kBlock / gc);
   g.eM = blocks_for(d.m, kBlock);
   g.eN = blocks_for(d.n, kBlock);
+  // the PCG column kernels are limited to 40 registers (6 blocks per SM): one full wave
+  g.gNc = (int)std::min<int64_t>(g.gN, 6 * (int64_t)(d.sm_count > 0 ? d.sm_count : 148));
+  // the residual and right-hand-side column kernels are limited to 64 registers (4 per SM)
+  g.gNr = (int)std::min<int64_t>(g.gN, 4 * (int64_t)(d.sm_count > 0 ? d.sm_count : 148));
   return g;
 }
 
@@ -259,7 +263,7 @@ __global__ void k_cons_resid(Dev d, double* part) {
 // vR2), r_d, r_l, r_u and the scalar parts
 // of the objective, the dual objective and the complementarity sum.
 template <int G>
-__global__ void k_cols_resid(Dev d, double* part) {
+__global__ void __launch_bounds__(256, 4) k_cols_resid(Dev d, double* part) {
   __shared__ double sh[32];
   const double mu = d.sc->mu;
   double rd_inf = 0.0, hx_inf = 0.0, aty_inf = 0.0, rc_inf = 0.0, xHsx = 0.0, cx = 0.0, lzl = 0.0,
@@ -386,8 +390,8 @@ cudaError_t launch_residual_summary(const Dev& d, const Geo& g, cudaStream_t st)
   }
   if (d.m) k_cons_resid<<<g.eM, kBlock, 0, st>>>(d, part);
   launch_lr(d, d.x, 1, st);
-  DISPATCH_G(d.g_cols, k_cols_resid<G><<<g.gN, kBlock, 0, st>>>(d, part));
-  k_resid_final<<<1, 1024, 0, st>>>(d, g.gR, g.eM, g.gN, part);
+  DISPATCH_G(d.g_cols, k_cols_resid<G><<<g.gNr, kBlock, 0, st>>>(d, part));
+  k_resid_final<<<1, 1024, 0, st>>>(d, g.gR, g.eM, g.gNr, part);
   return cudaGetLastError();
 }
 
@@ -936,7 +940,7 @@ __device__ __forceinline__ void group_row_dot_plain_sq(const int64_t beg, const 
 }
 
 template <int G>
-__global__ void k_rhs_jacobi(Dev d) {
+__global__ void __launch_bounds__(256, 4) k_rhs_jacobi(Dev d) {
   __shared__ double sh[32];
   const double mu = d.sc->mu;
   double r2 = 0.0;
@@ -970,7 +974,7 @@ cudaError_t launch_rhs(const Dev& d, const Geo& g, int precond, cudaStream_t st)
   if (precond == PC_DENSE) {
     DISPATCH_G(d.g_cols, k_rhs_n<G><<<g.gN, kBlock, 0, st>>>(d));
   } else {
-    DISPATCH_G(d.g_cols, k_rhs_jacobi<G><<<g.gN, kBlock, 0, st>>>(d));
+    DISPATCH_G(d.g_cols, k_rhs_jacobi<G><<<g.gNr, kBlock, 0, st>>>(d));
   }
   return cudaGetLastError();
 }
@@ -991,7 +995,7 @@ __global__ void k_op_rows(Dev d) {
 // q = R^T v + Hs p + (h0 + sigma) o p; p^T q -> alpha = rz / p^T q (last block).
 // MODE 0: inside PCG; MODE 1: a single operator apply (no scalars touched).
 template <int MODE, int G>
-__global__ void k_op_cols(Dev d) {
+__global__ void __launch_bounds__(256, 6) k_op_cols(Dev d) {
   __shared__ double sh[32];
   if (MODE == 0 && d.sc->cg_done) return;
   double pq = 0.0;
@@ -1232,7 +1236,7 @@ cudaError_t launch_cg_body(const Dev& d, const Geo& g, int precond, cudaGraphCon
   } else {
     if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<0, G><<<g.gR, kBlock, 0, st>>>(d));
     launch_lr(d, d.p, 0, st);
-    DISPATCH_G(d.g_cols, k_op_cols<0, G><<<g.gN, kBlock, 0, st>>>(d));
+    DISPATCH_G(d.g_cols, k_op_cols<0, G><<<g.gNc, kBlock, 0, st>>>(d));
   }
   if (precond == PC_DENSE) {
     k_cg_update<2><<<g.eN, kBlock, 0, st>>>(d);
@@ -1257,14 +1261,14 @@ cudaError_t launch_op_rows_only(const Dev& d, const Geo& g, cudaStream_t st) {
 
 cudaError_t launch_op_cols_only(const Dev& d, const Geo& g, cudaStream_t st) {
   // (the low-rank term uses us from the last launch_lr; the measurement does not re-run it)
-  DISPATCH_G(d.g_cols, k_op_cols<1, G><<<g.gN, kBlock, 0, st>>>(d));
+  DISPATCH_G(d.g_cols, k_op_cols<1, G><<<g.gNc, kBlock, 0, st>>>(d));
   return cudaGetLastError();
 }
 
 cudaError_t launch_apply(const Dev& d, const Geo& g, cudaStream_t st) {
   if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<1, G><<<g.gR, kBlock, 0, st>>>(d));
   launch_lr(d, d.p, 0, st);
-  DISPATCH_G(d.g_cols, k_op_cols<1, G><<<g.gN, kBlock, 0, st>>>(d));
+  DISPATCH_G(d.g_cols, k_op_cols<1, G><<<g.gNc, kBlock, 0, st>>>(d));
   return cudaGetLastError();
 }
 

@@ -81,7 +81,7 @@ cudaError_t launch_quantize(const Dev& d, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// Eight stored values of type T decoded to FP32, from 16-byte aligned loads.
+// C stored values of type T decoded to FP32 from one aligned vector load.
 template <int S> struct Chunk;
 template <> struct Chunk<ST_F32> {
   static constexpr int C = 4;   // elements per 16-byte load
@@ -103,12 +103,12 @@ template <> struct Chunk<ST_BF16> {
   }
 };
 template <> struct Chunk<ST_FP8> {
-  static constexpr int C = 16;
+  static constexpr int C = 8;   // 8-byte loads: as many elements per chunk as BF16
   static __device__ __forceinline__ void load(const __nv_fp8_e4m3* p, float* v) {
-    const uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
-    const unsigned w[4] = {u.x, u.y, u.z, u.w};
+    const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+    const unsigned w[2] = {u.x, u.y};
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 2; ++k) {
       const __nv_fp8x2_e4m3 lo = *reinterpret_cast<const __nv_fp8x2_e4m3*>(reinterpret_cast<const unsigned short*>(&w[k]));
       const __nv_fp8x2_e4m3 hi = *reinterpret_cast<const __nv_fp8x2_e4m3*>(reinterpret_cast<const unsigned short*>(&w[k]) + 1);
       const float2 a = static_cast<float2>(lo), b = static_cast<float2>(hi);
@@ -118,11 +118,11 @@ template <> struct Chunk<ST_FP8> {
 };
 
 // FP32 dot of a stored row with an FP32 vector by a group of G lanes.  The row is split into
-// a head up to the first 16-byte boundary of the value array, whole chunks of C elements
-// (one 16-byte value load and C/4 16-byte index loads per chunk, chunk c taken by lane
-// c mod G, two chunks in flight per lane) and a tail; one accumulator per lane, then a
-// shuffle reduction over the group.  Value and index arrays are 256-byte aligned, so an
-// element offset that is a multiple of C (>= 4) is 16-byte aligned in both.
+// a head up to the first chunk boundary, whole chunks of C elements (one vector load of the
+// C values, 16 bytes for F32 and BF16 and 8 for FP8, and C/4 16-byte index loads per chunk;
+// chunk c taken by lane c mod G, two chunks in flight per lane) and a tail; one accumulator
+// per lane, then a shuffle reduction over the group.  Value and index arrays are 256-byte
+// aligned, so an element offset that is a multiple of C (>= 4) aligns both loads.
 template <int S, int G>
 __device__ __forceinline__ float group_row_dot_lp(const int64_t beg, const int64_t end, const int gl,
                                                   const int32_t* __restrict__ idx,
@@ -232,7 +232,7 @@ __global__ void k_op_rows_lp(Dev d, int standalone) {
 
 // q_j = sum_i q_ij w_i + Hs p + (h0 + sigma) p;  p^T q -> alpha (last block), as k_op_cols.
 template <int S, int G>
-__global__ void k_op_cols_lp(Dev d, int standalone) {
+__global__ void __launch_bounds__(256, 6) k_op_cols_lp(Dev d, int standalone) {
   __shared__ double sh[32];
   if (!standalone && d.sc->cg_done) return;
   using T = typename StorageT<S>::T;
@@ -297,7 +297,7 @@ cudaError_t launch_op_lp(const Dev& d, const Geo& g, cudaStream_t st) {
   k_stiff_op_u<<<(d.stiff_cap + 7) / 8, kBlock, 0, st>>>(d);
   launch_lr(d, d.p, 0, st);
   if (d.nR) DISPATCH_SG(d.storage, d.g_rows, k_op_rows_lp<S, G><<<g.gR, kBlock, 0, st>>>(d, 0));
-  DISPATCH_SG(d.storage, d.g_cols, k_op_cols_lp<S, G><<<g.gN, kBlock, 0, st>>>(d, 0));
+  DISPATCH_SG(d.storage, d.g_cols, k_op_cols_lp<S, G><<<g.gNc, kBlock, 0, st>>>(d, 0));
   return cudaGetLastError();
 }
 
@@ -309,7 +309,7 @@ cudaError_t launch_op_rows_lp_only(const Dev& d, const Geo& g, cudaStream_t st) 
 }
 
 cudaError_t launch_op_cols_lp_only(const Dev& d, const Geo& g, cudaStream_t st) {
-  DISPATCH_SG(d.storage, d.g_cols, k_op_cols_lp<S, G><<<g.gN, kBlock, 0, st>>>(d, 1));
+  DISPATCH_SG(d.storage, d.g_cols, k_op_cols_lp<S, G><<<g.gNc, kBlock, 0, st>>>(d, 1));
   return cudaGetLastError();
 }
 

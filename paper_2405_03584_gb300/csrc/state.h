@@ -74,6 +74,8 @@ struct Dev {
 // Launch geometry shared by the host code and the final reduction kernel.
 struct Geo {
   int gR, gM, gN;              // blocks of the row-group kernels over R rows, constraint rows, R^T rows
+  int gNc;                     // blocks of the PCG column kernels (6 resident per SM: one wave)
+  int gNr;                     // blocks of the residual and right-hand-side column kernels (4 per SM)
   int eM, eN;                  // blocks of the one-thread-per-element kernels over m and n
 };
 
