@@ -60,6 +60,7 @@ Geo make_geo(const Dev& d) {
   g.eN = blocks_for(d.n, kBlock);
   // the PCG column kernels are limited to 40 registers (6 blocks per SM): one full wave
   g.gNc = (int)std::min<int64_t>(g.gN, 6 * (int64_t)(d.sm_count > 0 ? d.sm_count : 148));
+  g.gRc = (int)std::min<int64_t>(g.gR, 6 * (int64_t)(d.sm_count > 0 ? d.sm_count : 148));
   // the residual and right-hand-side column kernels are limited to 64 registers (4 per SM)
   g.gNr = (int)std::min<int64_t>(g.gN, 4 * (int64_t)(d.sm_count > 0 ? d.sm_count : 148));
   return g;
@@ -983,11 +984,11 @@ cudaError_t launch_rhs(const Dev& d, const Geo& g, int precond, cudaStream_t st)
 
 // v = omega o (R p).  MODE 0: inside PCG (skips once converged); MODE 1: single apply.
 template <int MODE, int G>
-__global__ void k_op_rows(Dev d) {
+__global__ void __launch_bounds__(256, 6) k_op_rows(Dev d) {
   if (MODE == 0 && d.sc->cg_done) return;
   FOR_GROUP_ROWS(G, r, ok, d.nR) {
     const int64_t beg = ok ? d.R_ptr[r] : 0, end = ok ? d.R_ptr[r + 1] : 0;
-    const double t = group_row_dot<G, false>(beg, end, glane<G>(), d.R_idx, d.R_val, d.p);
+    const double t = group_row_dot_u<G, 2>(beg, end, glane<G>(), d.R_idx, d.R_val, d.p);
     if (ok && glane<G>() == 0) d.vR[r] = d.omega[r] * t;
   }
 }
@@ -1234,7 +1235,7 @@ cudaError_t launch_cg_body(const Dev& d, const Geo& g, int precond, cudaGraphCon
     cudaError_t e = launch_op_lp(d, g, st);
     if (e != cudaSuccess) return e;
   } else {
-    if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<0, G><<<g.gR, kBlock, 0, st>>>(d));
+    if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<0, G><<<g.gRc, kBlock, 0, st>>>(d));
     launch_lr(d, d.p, 0, st);
     DISPATCH_G(d.g_cols, k_op_cols<0, G><<<g.gNc, kBlock, 0, st>>>(d));
   }
@@ -1255,7 +1256,7 @@ cudaError_t launch_cg_body(const Dev& d, const Geo& g, int precond, cudaGraphCon
 }
 
 cudaError_t launch_op_rows_only(const Dev& d, const Geo& g, cudaStream_t st) {
-  if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<1, G><<<g.gR, kBlock, 0, st>>>(d));
+  if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<1, G><<<g.gRc, kBlock, 0, st>>>(d));
   return cudaGetLastError();
 }
 
@@ -1266,7 +1267,7 @@ cudaError_t launch_op_cols_only(const Dev& d, const Geo& g, cudaStream_t st) {
 }
 
 cudaError_t launch_apply(const Dev& d, const Geo& g, cudaStream_t st) {
-  if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<1, G><<<g.gR, kBlock, 0, st>>>(d));
+  if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<1, G><<<g.gRc, kBlock, 0, st>>>(d));
   launch_lr(d, d.p, 0, st);
   DISPATCH_G(d.g_cols, k_op_cols<1, G><<<g.gNc, kBlock, 0, st>>>(d));
   return cudaGetLastError();
