@@ -104,6 +104,9 @@ typedef struct ipm_options {
   int lanes_cols;        /* lanes per row of the kernels over R^T (same; overrides autotune)    */
   double warm_rho;       /* IPM_WARM: complementarity pairs raised to >= warm_rho * mu0 of the  */
                          /* last cold start (1e-5); 0 keeps the previous point as it is        */
+  int u_cap;             /* columns reserved for the low-rank Hessian term U diag(u_w) U^T      */
+                         /* (0: as many as the loaded QP has); ipm_set_lowrank may use up to   */
+                         /* max(u_cap, u_cols of the QP)                                       */
 } ipm_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -221,6 +224,14 @@ int ipm_get_xyz(ipm_handle* h, double* x, double* y, double* z_l, double* z_u, d
  * For SQP-like chains of related QPs (Section 3.2: each SQP iteration changes the QP's
  * Hessian and cost, the constraints stay), followed by ipm_solve(..., IPM_WARM). */
 int ipm_update_costs(ipm_handle* h, const double* f_w, const double* c, int mem, void* stream);
+
+/* Replaces the low-rank Hessian term U diag(u_w) U^T of the loaded QP (Section 3.3: each SQP
+ * iteration appends two BFGS columns; u_cols = 0 drops the term, as the paper's reset after
+ * spot filtering does).  U is n x u_cols row-major, u_cols at most the capacity reserved at
+ * ipm_set_qp (IPM_ERR_TOO_LARGE otherwise).  diag(H) is recomputed; the handle's captured
+ * solve graphs are rebuilt at the next solve (a batch that contains the handle must be
+ * created again).  The iterate is kept, so IPM_WARM continues from the last solution. */
+int ipm_set_lowrank(ipm_handle* h, int64_t u_cols, const double* U, const double* u_w, int mem, void* stream);
 
 /* Loads into h the QP already loaded on src without copying its matrices: h references src's
  * device copy of R, R^T (and its reduced-precision copies and dense H block), which stays

@@ -213,7 +213,6 @@ void carve_matrix(Carver& cv, Dev& d, int64_t n, int64_t m, int64_t nR, int64_t 
     d.Hs_ptr = nullptr; d.Hs_idx = nullptr; d.Hs_val = nullptr;
   }
   d.arow = cv.take<int32_t>(m);
-  d.U = d.ucols ? cv.take<double>(n * d.ucols) : nullptr;
   if (storage != ST_F64) {
     const size_t vb = storage == ST_F32 ? 4 : (storage == ST_BF16 ? 2 : 1);
     d.Rq = cv.take<unsigned char>((int64_t)vb * nnzR);
@@ -259,13 +258,14 @@ void carve_state(Carver& cv, Dev& d, int64_t n, int64_t m, int64_t nR, int stiff
     d.p32 = d.w32 = nullptr;
     d.dxr = nullptr;
   }
-  if (d.ucols) {
-    d.uw = cv.take<double>(d.ucols);
-    d.lrs = cv.take<double>(d.ucols);
-    d.upart = cv.take<double>((int64_t)d.ublocks * d.ucols);
-    d.lrq = cv.take<double>(d.ucols);
+  if (d.ucap) {
+    d.U = cv.take<double>(n * d.ucap);
+    d.uw = cv.take<double>(d.ucap);
+    d.lrs = cv.take<double>(d.ucap);
+    d.upart = cv.take<double>((int64_t)d.ublocks * d.ucap);
+    d.lrq = cv.take<double>(d.ucap);
   } else {
-    d.uw = d.lrs = d.upart = d.lrq = nullptr;
+    d.U = d.uw = d.lrs = d.upart = d.lrq = nullptr;
   }
   d.trace = cv.take<double>((int64_t)trace_cap * kTraceCols);
   d.partials = cv.take<double>(32 * (int64_t)kMaxRedBlocks);
@@ -308,6 +308,7 @@ int validate_options(const ipm_options& o) {
   if (o.dense_max_n < 0 || o.dense_max_n > 2048 || !(o.stiff_gamma > 0)) return IPM_ERR_ARG;
   if (o.storage < 0 || o.storage > 3 || o.refine_max < 1 || !(o.refine_eta > 0 && o.refine_eta < 1)) return IPM_ERR_ARG;
   if (!(o.warm_rho >= 0 && o.warm_rho < 1)) return IPM_ERR_ARG;
+  if (o.u_cap < 0 || o.u_cap > (1 << 16)) return IPM_ERR_ARG;
   auto lanes_ok = [](int g) { return g == 0 || g == 4 || g == 8 || g == 16 || g == 32; };
   if (!lanes_ok(o.lanes_rows) || !lanes_ok(o.lanes_cols)) return IPM_ERR_ARG;
   return IPM_OK;
@@ -707,6 +708,7 @@ void ipm_default_options(ipm_options* o) {
   o->lanes_rows = 0;
   o->lanes_cols = 0;
   o->warm_rho = 1e-5;
+  o->u_cap = 0;
 }
 
 const char* ipm_status_str(int s) {
@@ -781,6 +783,37 @@ int ipm_update_costs(ipm_handle* h, const double* f_w, const double* c, int mem,
   if (f_w) CUDA_TRY(h, launch_diagH(d, h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));   // host staging buffers go out of scope
   h->cnorm = cn;
+  return leave(h, stream);
+}
+
+int ipm_set_lowrank(ipm_handle* h, int64_t u_cols, const double* U, const double* u_w, int mem, void* stream) {
+  if (!h) return IPM_ERR_ARG;
+  if (!h->loaded) return fail(h, IPM_ERR_STATE, "ipm_set_lowrank before ipm_set_qp");
+  if (h->pending) return fail(h, IPM_ERR_STATE, "a solve is in flight on this handle");
+  Dev& d = h->d;
+  if (u_cols < 0) return fail(h, IPM_ERR_ARG, "u_cols < 0");
+  if (u_cols > d.ucap)
+    return fail(h, IPM_ERR_TOO_LARGE, "u_cols " + std::to_string(u_cols) + " above the capacity " +
+                                          std::to_string(d.ucap) + " reserved at ipm_set_qp (options.u_cap)");
+  if (u_cols && (!U || !u_w)) return fail(h, IPM_ERR_ARG, "u_cols > 0 needs U and u_w");
+  int rc;
+  std::vector<double> hu, hw;
+  if (u_cols) {
+    hu.resize((size_t)(d.n * u_cols));
+    if ((rc = fetch_into(h, U, d.n * u_cols, mem, hu.data()))) return rc;
+    if ((rc = fetch(h, u_w, u_cols, mem, hw))) return rc;
+    for (double v : hw) if (!std::isfinite(v)) return fail(h, IPM_ERR_ARG, "u_w not finite");
+    for (double v : hu) if (!std::isfinite(v)) return fail(h, IPM_ERR_ARG, "U not finite");
+  }
+  if ((rc = enter(h, stream))) return rc;
+  if (u_cols) {
+    CUDA_TRY(h, cudaMemcpyAsync(d.U, hu.data(), 8 * hu.size(), cudaMemcpyHostToDevice, h->st));
+    CUDA_TRY(h, cudaMemcpyAsync(d.uw, hw.data(), 8 * hw.size(), cudaMemcpyHostToDevice, h->st));
+  }
+  d.ucols = u_cols;
+  destroy_graphs(h);                    // the captured kernels carry the old column count
+  CUDA_TRY(h, launch_diagH(d, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));   // host staging buffers go out of scope
   return leave(h, stream);
 }
 
@@ -964,6 +997,7 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   Dev dv{};
   CUDA_TRY(h, cudaDeviceGetAttribute(&dv.sm_count, cudaDevAttrMultiProcessorCount, h->device));
   dv.ucols = q.ucols;
+  dv.ucap = std::max<int64_t>(q.ucols, h->opt.u_cap);
   dv.ublocks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * (int64_t)dv.sm_count, n / 32));
   const int64_t nnzR = (int64_t)q.Rv.size(), nnzHs = (int64_t)q.Hv.size(), nnzAT = (int64_t)q.ATv.size();
   Carver cm(nullptr), cs(nullptr);
@@ -1026,7 +1060,7 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   if ((rc = up(d.fu, q.fu.data(), n))) return rc;
   CUDA_TRY(h, cudaMemsetAsync(d.hist, 0, sizeof(unsigned int) * kHistBins, h->st));
   CUDA_TRY(h, cudaMemsetAsync(d.slotR, 0xff, sizeof(int32_t) * std::max<int64_t>(q.nR, 1), h->st));
-  if (d.ucols) CUDA_TRY(h, cudaMemsetAsync(d.lrs, 0, sizeof(double) * d.ucols, h->st));
+  if (d.ucap) CUDA_TRY(h, cudaMemsetAsync(d.lrs, 0, sizeof(double) * d.ucap, h->st));
   std::memset(h->hs, 0, sizeof(Scal));
   push_options(h);
   h->hs->mu = h->hs->mu0 = 1.0;
@@ -1100,9 +1134,10 @@ int ipm_share_qp(ipm_handle* h, ipm_handle* src, void* stream) {
   if ((rc = cp(d.fu, sd.fu, n))) return rc;
   if ((rc = cp(d.diagH, sd.diagH, 8 * n))) return rc;
   if (d.ucols && (rc = cp(d.uw, sd.uw, 8 * d.ucols))) return rc;
+  if (d.ucols && (rc = cp(d.U, sd.U, 8 * n * d.ucols))) return rc;
   CUDA_TRY(h, cudaMemsetAsync(d.hist, 0, sizeof(unsigned int) * kHistBins, h->st));
   CUDA_TRY(h, cudaMemsetAsync(d.slotR, 0xff, sizeof(int32_t) * std::max<int64_t>(nR, 1), h->st));
-  if (d.ucols) CUDA_TRY(h, cudaMemsetAsync(d.lrs, 0, sizeof(double) * d.ucols, h->st));
+  if (d.ucap) CUDA_TRY(h, cudaMemsetAsync(d.lrs, 0, sizeof(double) * d.ucap, h->st));
   std::memset(h->hs, 0, sizeof(Scal));
   push_options(h);
   h->hs->mu = h->hs->mu0 = 1.0;

@@ -25,8 +25,9 @@ struct Dev {
   const int64_t* Hs_ptr; const int32_t* Hs_idx; const double* Hs_val;   // nullptr if none
   const int32_t* arow;         // m: row of R holding constraint k
   // low-rank Hessian term U diag(uw) U^T (eq:bfgs_hessian): U is n x ucols, row-major
-  int64_t ucols;
-  const double* U;
+  int64_t ucols;               // columns in use (<= ucap); U's row stride
+  int64_t ucap;                // columns allocated (per handle: U is part of the state)
+  double* U;
   double* uw;                  // ucols weights
   double* lrs;                 // ucols: uw o (U^T v) for the vector v of the last launch_lr
   double* upart;               // ublocks x ucols partial sums of U^T v

