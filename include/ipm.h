@@ -107,6 +107,8 @@ typedef struct ipm_options {
   int u_cap;             /* columns reserved for the low-rank Hessian term U diag(u_w) U^T      */
                          /* (0: as many as the loaded QP has); ipm_set_lowrank may use up to   */
                          /* max(u_cap, u_cols of the QP)                                       */
+  int ingest_host;       /* 1: ipm_set_qp builds R^T on the host (multi-threaded) instead of    */
+                         /* on the device; both give the same bytes (0)                        */
 } ipm_options;
 
 /* Fills *opt with the defaults listed above. */

@@ -25,6 +25,7 @@
 #include "../../include/ipm.h"
 #include "ingest.h"
 #include "state.h"
+#include "transpose.h"
 
 using namespace ipmk;
 
@@ -709,6 +710,7 @@ void ipm_default_options(ipm_options* o) {
   o->lanes_cols = 0;
   o->warm_rho = 1e-5;
   o->u_cap = 0;
+  o->ingest_host = 0;
 }
 
 const char* ipm_status_str(int s) {
@@ -904,36 +906,42 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   q.nR = fr + (use_acsr ? m : 0);
   const int64_t nnzF = fr ? Fp[fr] : 0, nnzA = (m && use_acsr) ? Ap[m] : 0;
   q.Rp.resize(q.nR + 1);
-  q.Ri.resize(nnzF + nnzA);
-  q.Rv.resize(nnzF + nnzA);
   q.wR.assign(q.nR, 0.0);
   for (int64_t r = 0; r <= fr; ++r) q.Rp[r] = fr ? Fp[r] : 0;
-  if (nnzF) {
-    if ((rc = fetch_into(h, qp->F_indices, nnzF, mem, q.Ri.data()))) return rc;
-    if ((rc = fetch_into(h, qp->F_data, nnzF, mem, q.Rv.data()))) return rc;
-  }
   for (int64_t r = 0; r < fr; ++r) q.wR[r] = fw[r];
-  if (use_acsr) {
+  if (use_acsr)
     for (int64_t k = 1; k <= m; ++k) q.Rp[fr + k] = nnzF + Ap[k];
-    if (nnzA) {
-      if ((rc = fetch_into(h, qp->A_indices, nnzA, mem, q.Ri.data() + nnzF))) return rc;
-      if ((rc = fetch_into(h, qp->A_data, nnzA, mem, q.Rv.data() + nnzF))) return rc;
-    }
-  }
-  switch (check_csr_entries((int64_t)q.Ri.size(), q.Ri.data(), q.Rv.data(), n)) {
-    case 1: return fail(h, IPM_ERR_ARG, "column index out of range");
-    case 2: return fail(h, IPM_ERR_ARG, "matrix value not finite");
-    default: break;
-  }
   q.arow.resize(m);
   for (int64_t k = 0; k < m; ++k) q.arow[k] = use_arows ? arows_in[k] : (int32_t)(fr + k);
-  // R^T by a stable counting sort (rows increase within each column: deterministic order)
-  q.RTp.assign(n + 1, 0);
-  q.RTi.resize(q.Ri.size());
-  q.RTv.resize(q.Ri.size());
-  transpose_csr(q.nR, n, q.Rp.data(), q.Ri.data(), q.Rv.data(), q.RTp.data(), q.RTi.data(), q.RTv.data());
-  // A^T: the R^T entries of constraint rows, in R^T's order
-  {
+  const int64_t nnzR = nnzF + nnzA;
+  // entries of A^T: the constraint rows' lengths
+  int64_t nnzAT = 0;
+  for (int64_t k = 0; k < m; ++k) nnzAT += q.Rp[q.arow[k] + 1] - q.Rp[q.arow[k]];
+  // R^T and A^T are built on the device (transpose.cu) unless options.ingest_host asks for
+  // the host transpose; the host path is also the fallback for very long columns
+  auto host_transpose = [&]() -> int {
+    int rc2;
+    q.Ri.resize(nnzR);
+    q.Rv.resize(nnzR);
+    if (nnzF) {
+      if ((rc2 = fetch_into(h, qp->F_indices, nnzF, mem, q.Ri.data()))) return rc2;
+      if ((rc2 = fetch_into(h, qp->F_data, nnzF, mem, q.Rv.data()))) return rc2;
+    }
+    if (nnzA) {
+      if ((rc2 = fetch_into(h, qp->A_indices, nnzA, mem, q.Ri.data() + nnzF))) return rc2;
+      if ((rc2 = fetch_into(h, qp->A_data, nnzA, mem, q.Rv.data() + nnzF))) return rc2;
+    }
+    switch (check_csr_entries(nnzR, q.Ri.data(), q.Rv.data(), n)) {
+      case 1: return fail(h, IPM_ERR_ARG, "column index out of range");
+      case 2: return fail(h, IPM_ERR_ARG, "matrix value not finite");
+      default: break;
+    }
+    // R^T by a stable counting sort (rows increase within each column: deterministic order)
+    q.RTp.assign(n + 1, 0);
+    q.RTi.resize(nnzR);
+    q.RTv.resize(nnzR);
+    transpose_csr(q.nR, n, q.Rp.data(), q.Ri.data(), q.Rv.data(), q.RTp.data(), q.RTi.data(), q.RTv.data());
+    // A^T: the R^T entries of constraint rows, in R^T's order
     std::vector<unsigned char> is_con(q.nR, 0);
     for (int64_t k = 0; k < m; ++k) is_con[q.arow[k]] = 1;
     q.ATp.assign(n + 1, 0);
@@ -941,7 +949,12 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
     q.ATi.resize(q.ATp[n]);
     q.ATv.resize(q.ATp[n]);
     filter_rows(n, q.RTp.data(), q.RTi.data(), q.RTv.data(), is_con.data(), q.ATp.data(), q.ATi.data(), q.ATv.data());
-  }
+    return IPM_OK;
+  };
+  if (nnzF && (!qp->F_indices || !qp->F_data)) return fail(h, IPM_ERR_ARG, "missing F arrays");
+  if (nnzA && (!qp->A_indices || !qp->A_data)) return fail(h, IPM_ERR_ARG, "missing A arrays");
+  bool host_path = h->opt.ingest_host != 0;
+  if (host_path && (rc = host_transpose())) return rc;
   // dense H block -> CSR of its non-zeros (symmetry checked)
   if (qp->H_dense) {
     std::vector<double> Hd;
@@ -999,7 +1012,7 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   dv.ucols = q.ucols;
   dv.ucap = std::max<int64_t>(q.ucols, h->opt.u_cap);
   dv.ublocks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * (int64_t)dv.sm_count, n / 32));
-  const int64_t nnzR = (int64_t)q.Rv.size(), nnzHs = (int64_t)q.Hv.size(), nnzAT = (int64_t)q.ATv.size();
+  const int64_t nnzHs = (int64_t)q.Hv.size();
   Carver cm(nullptr), cs(nullptr);
   carve_matrix(cm, dv, n, m, q.nR, nnzR, nnzAT, nnzHs, h->opt.storage);
   carve_state(cs, dv, n, m, q.nR, stiff_cap, sc_cap, dense, h->opt.storage, h->opt.max_ipm);
@@ -1015,8 +1028,8 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   carve_matrix(cvm, dv, n, m, q.nR, nnzR, nnzAT, nnzHs, h->opt.storage);
   carve_state(cvs, dv, n, m, q.nR, stiff_cap, sc_cap, dense, h->opt.storage, h->opt.max_ipm);
   dv.n = n; dv.m = m; dv.nR = q.nR; dv.nnzR = nnzR; dv.nnzHs = nnzHs; dv.nnzA = nnzAT;
-  dv.g_rows = heuristic_group(q.nR ? (double)q.Rv.size() / (double)q.nR : 0.0);
-  dv.g_cols = heuristic_group((double)q.Rv.size() / (double)n);
+  dv.g_rows = heuristic_group(q.nR ? (double)nnzR / (double)q.nR : 0.0);
+  dv.g_cols = heuristic_group((double)nnzR / (double)n);
   if (h->opt.lanes_rows) dv.g_rows = h->opt.lanes_rows;
   if (h->opt.lanes_cols) dv.g_cols = h->opt.lanes_cols;
   h->d = dv;
@@ -1032,20 +1045,49 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   };
   const Dev& d = h->d;
   if ((rc = up(d.R_ptr, q.Rp.data(), 8 * q.Rp.size()))) return rc;
-  if ((rc = up(d.R_idx, q.Ri.data(), 4 * q.Ri.size()))) return rc;
-  if ((rc = up(d.R_val, q.Rv.data(), 8 * q.Rv.size()))) return rc;
-  if ((rc = up(d.RT_ptr, q.RTp.data(), 8 * q.RTp.size()))) return rc;
-  if ((rc = up(d.RT_idx, q.RTi.data(), 4 * q.RTi.size()))) return rc;
-  if ((rc = up(d.RT_val, q.RTv.data(), 8 * q.RTv.size()))) return rc;
-  if ((rc = up(d.AT_ptr, q.ATp.data(), 8 * q.ATp.size()))) return rc;
-  if ((rc = up(d.AT_idx, q.ATi.data(), 4 * q.ATi.size()))) return rc;
-  if ((rc = up(d.AT_val, q.ATv.data(), 8 * q.ATv.size()))) return rc;
+  if ((rc = up(d.arow, q.arow.data(), 4 * q.arow.size()))) return rc;
+  if (!host_path) {
+    // R straight from the caller's arrays (host or device), then R^T and A^T on the device
+    auto in = [&](void* dst, const void* src, size_t nbytes) -> int {
+      if (nbytes == 0) return IPM_OK;
+      CUDA_TRY(h, cudaMemcpyAsync(dst, src, nbytes, cudaMemcpyDefault, h->st));
+      return IPM_OK;
+    };
+    if ((rc = in((void*)d.R_idx, qp->F_indices, 4 * (size_t)nnzF))) return rc;
+    if ((rc = in((void*)d.R_val, qp->F_data, 8 * (size_t)nnzF))) return rc;
+    if ((rc = in((void*)(d.R_idx + nnzF), qp->A_indices, 4 * (size_t)nnzA))) return rc;
+    if ((rc = in((void*)(d.R_val + nnzF), qp->A_data, 8 * (size_t)nnzA))) return rc;
+    void* scratch = nullptr;
+    if ((rc = dev_alloc(h, &scratch, device_transpose_scratch(n, q.nR), "transpose scratch"))) return rc;
+    cudaError_t terr = cudaSuccess;
+    const int tr = device_transpose(d.R_ptr, d.R_idx, d.R_val, q.nR, n, nnzR, d.arow, m, (int64_t*)d.RT_ptr,
+                                    (int32_t*)d.RT_idx, (double*)d.RT_val, (int64_t*)d.AT_ptr, (int32_t*)d.AT_idx,
+                                    (double*)d.AT_val, scratch, dv.sm_count, h->st, &terr);
+    cudaStreamSynchronize(h->st);
+    cudaFree(scratch);
+    if (tr < 0) return fail(h, IPM_ERR_CUDA, std::string("device transpose: ") + cudaGetErrorString(terr));
+    if (tr == 1) return fail(h, IPM_ERR_ARG, "column index out of range");
+    if (tr == 2) return fail(h, IPM_ERR_ARG, "matrix value not finite");
+    if (tr == 3) {
+      host_path = true;                 // a column too long for the device sort
+      if ((rc = host_transpose())) return rc;
+    }
+  }
+  if (host_path) {
+    if ((rc = up(d.R_idx, q.Ri.data(), 4 * q.Ri.size()))) return rc;
+    if ((rc = up(d.R_val, q.Rv.data(), 8 * q.Rv.size()))) return rc;
+    if ((rc = up(d.RT_ptr, q.RTp.data(), 8 * q.RTp.size()))) return rc;
+    if ((rc = up(d.RT_idx, q.RTi.data(), 4 * q.RTi.size()))) return rc;
+    if ((rc = up(d.RT_val, q.RTv.data(), 8 * q.RTv.size()))) return rc;
+    if ((rc = up(d.AT_ptr, q.ATp.data(), 8 * q.ATp.size()))) return rc;
+    if ((rc = up(d.AT_idx, q.ATi.data(), 4 * q.ATi.size()))) return rc;
+    if ((rc = up(d.AT_val, q.ATv.data(), 8 * q.ATv.size()))) return rc;
+  }
   if (d.Hs_ptr) {
     if ((rc = up(d.Hs_ptr, q.Hp.data(), 8 * q.Hp.size()))) return rc;
     if ((rc = up(d.Hs_idx, q.Hi.data(), 4 * q.Hi.size()))) return rc;
     if ((rc = up(d.Hs_val, q.Hv.data(), 8 * q.Hv.size()))) return rc;
   }
-  if ((rc = up(d.arow, q.arow.data(), 4 * q.arow.size()))) return rc;
   if (q.ucols) {
     if ((rc = up(d.U, q.U.data(), 8 * q.U.size()))) return rc;
     if ((rc = up(d.uw, q.uw.data(), 8 * q.uw.size()))) return rc;
