@@ -44,6 +44,22 @@ def _env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(value, device="cuda"):
+    """The largest of one float over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(units_per_rank, world, max_ms):
+    """Whole-job rate of independent replicas: all ranks' units over the slowest rank's time."""
+    return units_per_rank * world / (max_ms / 1000.0)
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -472,6 +488,53 @@ def run_sqp(args):
     return 0
 
 
+def run_dense(args):
+    """The dense QP (n = 500, m = 1000, seed 0, tol 1e-8; H = Q Lambda Q^T): FP64 solves with
+    the DENSE preconditioner (the condensed matrix formed and factored on the device once per
+    IPM iteration).  At about 10 MB per operator apply this case is L2- and launch-latency
+    bound, so it reports us per IPM and per PCG iteration rather than HBM bandwidth; beside it
+    the oracle's own solve of the same QP on the host cores."""
+    import torch
+    from paper_2405_03584_gb300 import build, ipm, workloads as W
+    from oracle import ipm as O, kkt_check
+    torch.cuda.set_device(0)
+    build.build()
+    p = W.dense_qp(n=500, m=1000, seed=0)
+    s = ipm.Solver(tol_kkt=1e-8)
+    s.set_qp_dense(p["H"], p["c"], p["A"], p["b"], p["l"], p["u"])
+    for _ in range(args.warmup):
+        s.solve()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sts = [s.solve() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    out = s.get()
+    info = out["info"]
+    rk = kkt_check.rel_kkt(kkt_check.dense_ops(p), out["x"], out["y"], out["zl"], out["zu"])
+    s.close()
+    qp = O.from_dense(p)
+    t0 = time.perf_counter()
+    ref, rinfo = O.solve(qp, tol=1e-8)
+    t_or = time.perf_counter() - t0
+    f, f0 = O.objective(qp, out["x"]), O.objective(qp, ref.x)
+    res = {"mode": "dense", "metric": "QP solves/sec at rel. KKT <= 1e-8 (dense QP)", "value": 1000.0 / ms,
+           "unit": "solves/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup, "dtype": "f64",
+           "config": {"workload": "dense QP n=500, m=1000, seed 0 (workloads.dense_qp)", "precond": "dense"},
+           "status": [int(x) for x in sts], "ipm_iters": info["ipm_iters"], "cg_iters": info["cg_iters"],
+           "us_per_ipm_iter": 1000.0 * ms / max(info["ipm_iters"], 1),
+           "us_per_pcg_iter_upper_bound": 1000.0 * ms / max(info["cg_iters"], 1),
+           "rel_kkt_checker": rk, "rel_obj_vs_oracle": abs(f - f0) / (1 + abs(f0)),
+           "gpu_launches": int(info["kernel_launches"]),
+           "cpu_baseline": {"value": 1.0 / t_or, "unit": "solves/s", "cores": _cores_used(), "kind": "oracle",
+                            "sample": "the whole oracle solve of the same QP (%d IPM iterations)" % rinfo.iterations}}
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -514,12 +577,8 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
     lat = [a.elapsed_time(b) for a, b in evs]
-    total_ms = evs[0][0].elapsed_time(evs[-1][1])
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = args.steps * world / (total_ms / 1000.0)
+    total_ms = max_over_ranks(evs[0][0].elapsed_time(evs[-1][1]))
+    value = replica_rate(args.steps, world, total_ms)
     # correctness of the timed solves, certified on the host by the independent checker
     from oracle import kkt_check
     sol = s.get()
@@ -569,9 +628,7 @@ def run_ours(args):
                 e2e_t.append(time.perf_counter() - t0)
         e2e_val = len(e2e_t) / sum(e2e_t)
         if world > 1:
-            t = torch.tensor([sum(e2e_t)], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_val = len(e2e_t) * world / float(t.item())
+            e2e_val = replica_rate(len(e2e_t), world, 1000.0 * max_over_ranks(sum(e2e_t)))
         e2e = {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "steps": len(e2e_t), "includes": "ipm_create + ipm_set_qp (host arrays, pinned) + ipm_solve + ipm_get_xyz"}
     cpu = None
@@ -621,6 +678,7 @@ def main():
     ap.add_argument("--batch-scale", type=float, default=1.0, help="scale every n of the batch (testing)")
     ap.add_argument("--bfgs", choices=["proton", "vmat"], help="the quasi-Newton Hessian shapes of the paper")
     ap.add_argument("--sqp", action="store_true", help="the SQP outer loop with GPU QP sub-problems")
+    ap.add_argument("--dense", action="store_true", help="the dense QP (n = 500, m = 1000)")
     ap.add_argument("--sqp-n", type=int, default=10000)
     ap.add_argument("--sqp-iters", type=int, default=150)
     ap.add_argument("--serve", action="store_true", help="the serving stream (Poisson arrivals, chains, warm start)")
@@ -646,6 +704,8 @@ def main():
         return run_bfgs(args)
     if args.sqp:
         return run_sqp(args)
+    if args.dense:
+        return run_dense(args)
     if args.serve:
         # more hardware work queues than the default 8, so many slots' streams run side by side
         os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
