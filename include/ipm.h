@@ -109,6 +109,10 @@ typedef struct ipm_options {
                          /* max(u_cap, u_cols of the QP)                                       */
   int ingest_host;       /* 1: ipm_set_qp builds R^T on the host (multi-threaded) instead of    */
                          /* on the device; both give the same bytes (0)                        */
+  int lp_stage;          /* reduced precision: stage the FP32 vector in shared memory by bulk   */
+                         /* copies (TMA) in the rows pass when n * 4 bytes fit (0: the staging */
+                         /* block holds 1024 threads per SM and measures slower, 105 against   */
+                         /* 72 us on the RT rows pass; same results bit for bit)               */
 } ipm_options;
 
 /* Fills *opt with the defaults listed above. */

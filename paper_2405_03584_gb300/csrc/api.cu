@@ -252,7 +252,7 @@ void carve_state(Carver& cv, Dev& d, int64_t n, int64_t m, int64_t nR, int stiff
   d.chol_diag = cv.take<double>(std::max<int64_t>(dense ? n : 0, stiff_cap));
   d.storage = storage;
   if (storage != ST_F64) {
-    d.p32 = cv.take<float>(n);
+    d.p32 = cv.take<float>((n + 3) & ~int64_t(3));   // whole 16-byte units (bulk copies)
     d.w32 = cv.take<float>(nR);
     d.dxr = cv.take<double>(n);
   } else {
@@ -711,6 +711,7 @@ void ipm_default_options(ipm_options* o) {
   o->warm_rho = 1e-5;
   o->u_cap = 0;
   o->ingest_host = 0;
+  o->lp_stage = 0;
 }
 
 const char* ipm_status_str(int s) {
@@ -1032,6 +1033,8 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   dv.g_cols = heuristic_group((double)nnzR / (double)n);
   if (h->opt.lanes_rows) dv.g_rows = h->opt.lanes_rows;
   if (h->opt.lanes_cols) dv.g_cols = h->opt.lanes_cols;
+  dv.lp_stage = (h->opt.storage != IPM_STORAGE_F64 && h->opt.lp_stage) ? 1 : 0;
+  if (dv.lp_stage) CUDA_TRY(h, prepare_lp_staging());
   h->d = dv;
   h->g = make_geo(dv);
   if ((rc = alloc_trace(h))) return rc;
@@ -1151,6 +1154,8 @@ int ipm_share_qp(ipm_handle* h, ipm_handle* src, void* stream) {
   carve_state(cvs, dv, n, m, nR, stiff_cap, sc_cap, use_dense, h->opt.storage, h->opt.max_ipm);
   if (h->opt.lanes_rows) dv.g_rows = h->opt.lanes_rows;
   if (h->opt.lanes_cols) dv.g_cols = h->opt.lanes_cols;
+  dv.lp_stage = (h->opt.storage != IPM_STORAGE_F64 && h->opt.lp_stage) ? 1 : 0;
+  if (dv.lp_stage) CUDA_TRY(h, prepare_lp_staging());
   h->d = dv;
   h->g = make_geo(dv);
   if ((rc = alloc_trace(h))) return rc;
@@ -1289,7 +1294,8 @@ static int fill_info(ipm_handle* h, int64_t direct_launches) {
     }
   }
   int status = s.status == DS_OK ? IPM_OK : s.status == DS_MAX_ITER ? IPM_MAX_ITER
-             : s.status == DS_CG_STALL ? IPM_CG_STALL : s.status == DS_RUNNING ? IPM_MAX_ITER : IPM_NUMERICAL;
+             : s.status == DS_CG_STALL ? IPM_CG_STALL : s.status == DS_RUNNING ? IPM_MAX_ITER
+             : s.status == DS_TIMEOUT ? IPM_ERR_TIMEOUT : IPM_NUMERICAL;
   ipm_info& in = h->info;
   in.status = status;
   in.ipm_iters = s.ipm_iter;

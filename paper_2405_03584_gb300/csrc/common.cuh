@@ -60,7 +60,7 @@ enum ScalTicket { T_PQ = 0, T_UPD = 1, T_CORR = 2, T_INIT = 3, T_HIST = 4, T_STE
 enum Storage { ST_F64 = 0, ST_F32 = 1, ST_BF16 = 2, ST_FP8 = 3 };
 
 // Status values written by the device (mirror enum ipm_status).
-enum DevStatus { DS_RUNNING = -1, DS_OK = 0, DS_MAX_ITER = 3, DS_CG_STALL = 4, DS_NUMERICAL = 5 };
+enum DevStatus { DS_RUNNING = -1, DS_OK = 0, DS_MAX_ITER = 3, DS_CG_STALL = 4, DS_NUMERICAL = 5, DS_TIMEOUT = 7 };
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

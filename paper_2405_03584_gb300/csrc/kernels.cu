@@ -513,7 +513,7 @@ __global__ void k_control(Dev d, cudaGraphConditionalHandle h, int set_cond) {
   sc->cg_total += sc->cg_iter;
   sc->refine_total += refine;
   if (sc->cg_iter > sc->max_cg_step) sc->max_cg_step = sc->cg_iter;
-  if (sc->status == DS_NUMERICAL || sc->status == DS_CG_STALL) {
+  if (sc->status == DS_NUMERICAL || sc->status == DS_CG_STALL || sc->status == DS_TIMEOUT) {
     sc->stop = 1;
   } else if (!isfinite(rk) || !isfinite(sc->pobj)) {
     sc->stop = 1;

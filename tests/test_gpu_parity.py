@@ -322,3 +322,18 @@ def test_async_and_batch_match_sync():
     b.close()
     for s in solvers:
         s.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16", "fp8"])
+def test_staged_rows_pass_equals_unstaged(storage):
+    """The reduced-precision rows pass with p32 staged in shared memory by bulk copies gives
+    the same bits as the pass that gathers from global memory."""
+    p = W.rt_qp(n=3001, seed=61)
+    xs = []
+    for stage in (1, 0):
+        with ipm.Solver(tol_kkt=1e-8, precond="jacobi_lr", storage=storage, lp_stage=stage) as s:
+            s.set_qp_rt(p)
+            assert s.solve() == ipm.IPM_OK
+            out = s.get()
+            xs.append((out["x"], out["info"]["cg_iters"], out["info"]["refine_passes"]))
+    assert np.array_equal(xs[0][0], xs[1][0]) and xs[0][1:] == xs[1][1:]
