@@ -550,8 +550,8 @@ def run_ours(args):
     build.build()
     dev = torch.cuda.current_device()
     p = W.rt_qp(n=N_FULL, seed=SEED)
-    s = ipm.Solver(tol_kkt=TOL, precond="jacobi_lr", use_graphs=0 if args.no_graphs else 1, autotune=1,
-                   storage=args.storage)
+    s = ipm.Solver(tol_kkt=TOL, precond="jacobi_lr" if args.system == "condensed" else "jacobi",
+                   use_graphs=0 if args.no_graphs else 1, autotune=1, storage=args.storage, system=args.system)
     s.set_qp_rt(p)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -647,7 +647,7 @@ def run_ours(args):
                "dtype": "f64" if args.storage == "f64" else
                         "%s operator storage, f32 accumulate, f64 refinement and reductions" % args.storage,
                "data": "synthetic",
-               "config": {"workload": WORKLOAD, "storage": args.storage, "n": p["n"], "V": p["V"], "m": p["m"], "nnz_D": int(p["D_indptr"][-1]),
+               "config": {"workload": WORKLOAD, "storage": args.storage, "system": args.system, "n": p["n"], "V": p["V"], "m": p["m"], "nnz_D": int(p["D_indptr"][-1]),
                           "tol_kkt": TOL, "precond": "jacobi_lr", "parallelism": "replicas" if world > 1 else "single",
                           "l2": "no flush: operator working set (~1.2 GB) > 129 MB L2"},
                "latency_ms": {"p50": statistics.median(lat), "p99": p99, "mean": statistics.mean(lat)},
@@ -687,6 +687,8 @@ def main():
     ap.add_argument("--serve-inflight", type=int, default=16)
     ap.add_argument("--serve-check", type=int, default=6, help="results re-checked by the independent checker")
     ap.add_argument("--serve-no-baseline", action="store_true")
+    ap.add_argument("--system", choices=["condensed", "augmented"], default="condensed",
+                    help="the linear system of the Newton step (augmented: the paper's eq:2x2_augmented, Jacobi PCG)")
     ap.add_argument("--storage", choices=["f64", "f32", "bf16", "fp8"], default="f64",
                     help="operator storage of the single RT QP (reduced ones add FP64 refinement)")
     ap.add_argument("--no-graphs", action="store_true",

@@ -68,6 +68,11 @@ enum ipm_precond { IPM_PRECOND_JACOBI = 0, IPM_PRECOND_JACOBI_LR = 1, IPM_PRECON
  * one FP32 scale per row, an FP32-accumulating operator inside PCG, and FP64 iterative
  * refinement of every Newton step against the FP64 operator (residuals and reductions stay
  * FP64).  Not part of the paper, which is FP64 throughout. */
+/* The linear system PCG solves for each Newton step (Section 4): the condensed (Schur
+ * complement) form (H + A^T Theta A + Sigma) dx = r, or the paper's doubly augmented form
+ * eq:2x2_augmented in (dx, dy) with its Jacobi preconditioner. */
+enum ipm_system { IPM_SYSTEM_CONDENSED = 0, IPM_SYSTEM_AUGMENTED = 1 };
+
 enum ipm_storage { IPM_STORAGE_F64 = 0, IPM_STORAGE_F32 = 1, IPM_STORAGE_BF16 = 2, IPM_STORAGE_FP8_E4M3 = 3 };
 
 /* ipm_solve flags. */
@@ -109,6 +114,8 @@ typedef struct ipm_options {
                          /* max(u_cap, u_cols of the QP)                                       */
   int ingest_host;       /* 1: ipm_set_qp builds R^T on the host (multi-threaded) instead of    */
                          /* on the device; both give the same bytes (0)                        */
+  int system;            /* enum ipm_system (IPM_SYSTEM_CONDENSED); AUGMENTED needs storage F64 */
+                         /* and precond JACOBI or AUTO (it always runs the Jacobi PCG)         */
   int lp_stage;          /* reduced precision: stage the FP32 vector in shared memory by bulk   */
                          /* copies (TMA) in the rows pass when n * 4 bytes fit (0: the staging */
                          /* block holds 1024 threads per SM and measures slower, 105 against   */

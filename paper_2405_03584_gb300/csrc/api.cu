@@ -235,13 +235,15 @@ void carve_state(Carver& cv, Dev& d, int64_t n, int64_t m, int64_t nR, int stiff
   d.x = cv.take<double>(n); d.s = cv.take<double>(m); d.y = cv.take<double>(m);
   d.zl = cv.take<double>(n); d.zu = cv.take<double>(n);
   d.theta = cv.take<double>(m); d.sigma = cv.take<double>(n); d.omega = cv.take<double>(nR);
-  d.M0 = cv.take<double>(n); d.Minv = cv.take<double>(n); d.thR = cv.take<double>(nR);
+  d.M0 = cv.take<double>(n); d.Minv = cv.take<double>(n + m); d.thR = cv.take<double>(nR);
   d.rd = cv.take<double>(n); d.rp = cv.take<double>(m); d.Hx = cv.take<double>(n); d.Aty = cv.take<double>(n);
   d.tR = cv.take<double>(nR); d.vR = cv.take<double>(nR); d.vR2 = cv.take<double>(nR);
-  d.dx = cv.take<double>(n); d.r = cv.take<double>(n); d.z = cv.take<double>(n); d.p = cv.take<double>(n);
-  d.q = cv.take<double>(n); d.rhs = cv.take<double>(n);
+  // PCG vectors hold n + m entries: the doubly augmented system appends the multipliers
+  d.dx = cv.take<double>(n + m); d.r = cv.take<double>(n + m); d.z = cv.take<double>(n + m);
+  d.p = cv.take<double>(n + m); d.q = cv.take<double>(n + m); d.rhs = cv.take<double>(n + m);
   d.ds = cv.take<double>(m); d.dy = cv.take<double>(m); d.dzl = cv.take<double>(n); d.dzu = cv.take<double>(n);
   d.ratio = cv.take<double>(m); d.slotR = cv.take<int32_t>(nR); d.stiff_k = cv.take<int32_t>(stiff_cap);
+  d.rowk = cv.take<int32_t>(nR);
   d.sc_cnt = cv.take<int32_t>(n); d.sc_ptr = cv.take<int64_t>(n + 1);
   d.sc_slot = cv.take<int32_t>(sc_cap); d.sc_val = cv.take<double>(sc_cap); d.sc_cap = sc_cap;
   d.G = cv.take<double>((int64_t)stiff_cap * stiff_cap); d.Ginv = cv.take<double>((int64_t)stiff_cap * stiff_cap);
@@ -310,6 +312,10 @@ int validate_options(const ipm_options& o) {
   if (o.storage < 0 || o.storage > 3 || o.refine_max < 1 || !(o.refine_eta > 0 && o.refine_eta < 1)) return IPM_ERR_ARG;
   if (!(o.warm_rho >= 0 && o.warm_rho < 1)) return IPM_ERR_ARG;
   if (o.u_cap < 0 || o.u_cap > (1 << 16)) return IPM_ERR_ARG;
+  if (o.system != IPM_SYSTEM_CONDENSED && o.system != IPM_SYSTEM_AUGMENTED) return IPM_ERR_ARG;
+  if (o.system == IPM_SYSTEM_AUGMENTED &&
+      (o.storage != IPM_STORAGE_F64 || (o.precond != IPM_PRECOND_JACOBI && o.precond != IPM_PRECOND_AUTO)))
+    return IPM_ERR_ARG;   // the doubly augmented system runs FP64 with the Jacobi preconditioner
   auto lanes_ok = [](int g) { return g == 0 || g == 4 || g == 8 || g == 16 || g == 32; };
   if (!lanes_ok(o.lanes_rows) || !lanes_ok(o.lanes_cols)) return IPM_ERR_ARG;
   return IPM_OK;
@@ -632,6 +638,7 @@ int run_iteration_direct(ipm_handle* h, int pc, int64_t* launches) {
 int choose_precond(const ipm_handle* h) {
   const ipm_options& o = h->opt;
   int pc = o.precond;
+  if (o.system == IPM_SYSTEM_AUGMENTED) return PC_JACOBI;   // the paper's Jacobi PCG on eq:2x2_augmented
   if (pc == IPM_PRECOND_AUTO) pc = (h->d.Kd && h->d.n <= 1024) ? PC_DENSE : PC_JACOBI_LR;
   if (pc == PC_DENSE && !h->d.Kd) pc = PC_JACOBI_LR;
   return pc;
@@ -712,6 +719,7 @@ void ipm_default_options(ipm_options* o) {
   o->u_cap = 0;
   o->ingest_host = 0;
   o->lp_stage = 0;
+  o->system = IPM_SYSTEM_CONDENSED;
 }
 
 const char* ipm_status_str(int s) {
@@ -1035,6 +1043,8 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   if (h->opt.lanes_cols) dv.g_cols = h->opt.lanes_cols;
   dv.lp_stage = (h->opt.storage != IPM_STORAGE_F64 && h->opt.lp_stage) ? 1 : 0;
   if (dv.lp_stage) CUDA_TRY(h, prepare_lp_staging());
+  dv.aug = h->opt.system == IPM_SYSTEM_AUGMENTED ? 1 : 0;
+  dv.nsys = dv.aug ? n + m : n;
   h->d = dv;
   h->g = make_geo(dv);
   if ((rc = alloc_trace(h))) return rc;
@@ -1105,6 +1115,7 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   if ((rc = up(d.fu, q.fu.data(), n))) return rc;
   CUDA_TRY(h, cudaMemsetAsync(d.hist, 0, sizeof(unsigned int) * kHistBins, h->st));
   CUDA_TRY(h, cudaMemsetAsync(d.slotR, 0xff, sizeof(int32_t) * std::max<int64_t>(q.nR, 1), h->st));
+  CUDA_TRY(h, launch_fill_rowk(d, h->st));
   if (d.ucap) CUDA_TRY(h, cudaMemsetAsync(d.lrs, 0, sizeof(double) * d.ucap, h->st));
   std::memset(h->hs, 0, sizeof(Scal));
   push_options(h);
@@ -1156,6 +1167,8 @@ int ipm_share_qp(ipm_handle* h, ipm_handle* src, void* stream) {
   if (h->opt.lanes_cols) dv.g_cols = h->opt.lanes_cols;
   dv.lp_stage = (h->opt.storage != IPM_STORAGE_F64 && h->opt.lp_stage) ? 1 : 0;
   if (dv.lp_stage) CUDA_TRY(h, prepare_lp_staging());
+  dv.aug = h->opt.system == IPM_SYSTEM_AUGMENTED ? 1 : 0;
+  dv.nsys = dv.aug ? n + m : n;
   h->d = dv;
   h->g = make_geo(dv);
   if ((rc = alloc_trace(h))) return rc;
@@ -1184,6 +1197,7 @@ int ipm_share_qp(ipm_handle* h, ipm_handle* src, void* stream) {
   if (d.ucols && (rc = cp(d.U, sd.U, 8 * n * d.ucols))) return rc;
   CUDA_TRY(h, cudaMemsetAsync(d.hist, 0, sizeof(unsigned int) * kHistBins, h->st));
   CUDA_TRY(h, cudaMemsetAsync(d.slotR, 0xff, sizeof(int32_t) * std::max<int64_t>(nR, 1), h->st));
+  CUDA_TRY(h, launch_fill_rowk(d, h->st));
   if (d.ucap) CUDA_TRY(h, cudaMemsetAsync(d.lrs, 0, sizeof(double) * d.ucap, h->st));
   std::memset(h->hs, 0, sizeof(Scal));
   push_options(h);

@@ -206,6 +206,25 @@ __global__ void k_diagH(Dev d) {
   }
 }
 
+__global__ void k_fill_rowk(Dev d) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < d.nR; r += (int64_t)gridDim.x * blockDim.x)
+    d.rowk[r] = -1;
+}
+
+__global__ void k_fill_rowk2(Dev d) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.m; k += (int64_t)gridDim.x * blockDim.x)
+    d.rowk[d.arow[k]] = (int32_t)k;
+}
+
+// rowk: the constraint index of each row of R (-1 for rows of the factor alone).
+cudaError_t launch_fill_rowk(const Dev& d, cudaStream_t st) {
+  if (!d.nR) return cudaSuccess;
+  const int b = (int)std::min<int64_t>((d.nR + kBlock - 1) / kBlock, 4096);
+  k_fill_rowk<<<b, kBlock, 0, st>>>(d);
+  if (d.m) k_fill_rowk2<<<(int)std::min<int64_t>((d.m + kBlock - 1) / kBlock, 4096), kBlock, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_diagH(const Dev& d, cudaStream_t st) {
   Geo g = make_geo(d);
   if (g.gN) k_diagH<<<g.gN, kBlock, 0, st>>>(d);
@@ -612,14 +631,17 @@ cudaError_t launch_set_cond(cudaGraphConditionalHandle h, unsigned v, cudaStream
 
 // ------------------------------------------------------------------------------ diagonal update
 
-// theta = y / s; omega = w_R + theta on the constraint rows (omega preset to w_R).
+// theta = y / s; omega = w_R + theta on the constraint rows (omega preset to w_R); twice
+// theta for the doubly augmented system.
 __global__ void k_diag_m(Dev d) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.m; k += (int64_t)gridDim.x * blockDim.x) {
     const double th = d.y[k] / d.s[k];
     const int32_t row = d.arow[k];
     d.theta[k] = th;
-    d.omega[row] = d.wR[row] + th;
-    d.thR[row] = th;
+    // doubly augmented system: its (1,1) block carries 2 B^T D^-1 B = 2 A^T Theta A
+    const double thf = d.aug ? 2.0 * th : th;
+    d.omega[row] = d.wR[row] + thf;
+    d.thR[row] = thf;
   }
 }
 
@@ -854,13 +876,26 @@ __global__ void k_gram_G(Dev d) {
 
 // ------------------------------------------------------------------------------ rhs
 
-// u = theta o r_p - r_s / s placed on R rows (vR2, pre-zeroed).
+// u = theta o r_p - r_s / s placed on R rows (vR2, pre-zeroed); the doubly augmented system
+// takes 2u there and its bottom block's right-hand side, start and Jacobi diagonal.
 __global__ void k_rhs_m(Dev d) {
   const double mu = d.sc->mu;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.m; k += (int64_t)gridDim.x * blockDim.x) {
     const double s = d.s[k];
     const double rs = s * d.y[k] - mu;
-    d.vR2[d.arow[k]] = d.theta[k] * d.rp[k] - rs / s;
+    const double u = d.theta[k] * d.rp[k] - rs / s;   // theta o r2, r2 = r_p - r_s / y
+    if (d.aug) {
+      // eq:2x2_augmented: top r1 + 2 B^T D^-1 r2 = r1 - 2 A^T (theta o r2); bottom r2;
+      // Jacobi on the bottom block D = s / y: 1 / D = theta
+      const double r2 = d.rp[k] - rs / d.y[k];
+      d.vR2[d.arow[k]] = 2.0 * u;
+      d.rhs[d.n + k] = r2;
+      d.r[d.n + k] = r2;
+      d.dx[d.n + k] = 0.0;
+      d.Minv[d.n + k] = d.theta[k];
+    } else {
+      d.vR2[d.arow[k]] = u;
+    }
   }
 }
 
@@ -961,6 +996,9 @@ __global__ void __launch_bounds__(256, 4) k_rhs_jacobi(Dev d) {
       r2 = fma(gj, gj, r2);
     }
   }
+  if (d.aug)   // the bottom block's right-hand side (written by k_rhs_m)
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.m; k += (int64_t)gridDim.x * blockDim.x)
+      r2 = fma(d.rhs[d.n + k], d.rhs[d.n + k], r2);
   double v[1] = {r2};
   const int ops[1] = {0};
   double out[1];
@@ -989,7 +1027,19 @@ __global__ void __launch_bounds__(256, 6) k_op_rows(Dev d) {
   FOR_GROUP_ROWS(G, r, ok, d.nR) {
     const int64_t beg = ok ? d.R_ptr[r] : 0, end = ok ? d.R_ptr[r + 1] : 0;
     const double t = group_row_dot_u<G, 2>(beg, end, glane<G>(), d.R_idx, d.R_val, d.p);
-    if (ok && glane<G>() == 0) d.vR[r] = d.omega[r] * t;
+    if (ok && glane<G>() == 0) {
+      double v = d.omega[r] * t;
+      if (MODE == 0 && d.aug) {
+        // doubly augmented: top gets -A^T p_bottom; bottom q = B p_top + D p_bottom
+        const int32_t k = d.rowk[r];
+        if (k >= 0) {
+          const double pb = d.p[d.n + k];
+          v -= pb;
+          d.q[d.n + k] = -t + pb * (d.s[k] / d.y[k]);
+        }
+      }
+      d.vR[r] = v;
+    }
   }
 }
 
@@ -1016,6 +1066,9 @@ __global__ void __launch_bounds__(256, 6) k_op_cols(Dev d) {
     }
   }
   if (MODE == 1) return;
+  if (d.aug)   // p^T q over the bottom block too (q's bottom written by the rows pass)
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.m; k += (int64_t)gridDim.x * blockDim.x)
+      pq = fma(d.p[d.n + k], d.q[d.n + k], pq);
   double v[1] = {pq};
   const int ops[1] = {0};
   double out[1];
@@ -1044,7 +1097,7 @@ __global__ void k_cg_update(Dev d) {
   if (d.sc->cg_done) return;
   const double alpha = d.sc->alpha;
   double rr = 0.0, rz = 0.0;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.nsys; j += (int64_t)gridDim.x * blockDim.x) {
     d.dx[j] = fma(alpha, d.p[j], d.dx[j]);
     const double rj = fma(-alpha, d.q[j], d.r[j]);
     d.r[j] = rj;
@@ -1186,7 +1239,7 @@ __global__ void k_dense_apply(Dev d, int init) {
 __global__ void k_cg_init_diag(Dev d) {
   __shared__ double sh[32];
   double rz = 0.0;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.nsys; j += (int64_t)gridDim.x * blockDim.x) {
     const double zj = d.r[j] * d.Minv[j];
     d.z[j] = zj;
     d.p[j] = zj;
@@ -1206,7 +1259,7 @@ __global__ void k_cg_p(Dev d, cudaGraphConditionalHandle h, int set_cond) {
   if (set_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, done ? 0u : 1u);
   if (done) return;
   const double beta = d.sc->beta;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x)
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.nsys; j += (int64_t)gridDim.x * blockDim.x)
   {
     const double pj = fma(beta, d.p[j], d.z[j]);
     d.p[j] = pj;
@@ -1287,7 +1340,8 @@ __global__ void k_recover_m(Dev d) {
       const double s = d.s[k];
       const double rs = s * d.y[k] - mu;
       d.ds[k] = -d.rp[k] - adx;
-      d.dy[k] = d.theta[k] * (adx + d.rp[k]) - rs / s;
+      // doubly augmented: dy is the solved bottom block
+      d.dy[k] = d.aug ? d.dx[d.n + k] : d.theta[k] * (adx + d.rp[k]) - rs / s;
     }
   }
 }

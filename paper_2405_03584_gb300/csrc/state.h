@@ -13,6 +13,8 @@ constexpr int kTraceCols = 14;   // columns of one trace row (IPM_TRACE_COLS of 
 
 struct Dev {
   int64_t n, m, nR;            // variables, constraint rows, rows of R = [F; A_csr]
+  int64_t nsys;                // PCG unknowns: n (condensed system), n + m (doubly augmented)
+  int aug;                     // 1: PCG on the doubly augmented system (Section 4, eq:2x2_augmented)
   int64_t nnzR, nnzHs;
   int g_rows, g_cols;          // lanes per row of the kernels over R and over R^T (4, 8, 16, 32)
   int sm_count;                // multiprocessors of the device (grid sizing)
@@ -48,6 +50,7 @@ struct Dev {
   // stiff-row low-rank correction
   double* ratio;               // m
   int32_t* slotR;              // nR: slot of a stiff row, -1 otherwise
+  int32_t* rowk;               // nR: constraint index of a row of R, -1 for the factor's rows
   int32_t* stiff_k;            // stiff_cap: constraint index of each slot
   int32_t* sc_cnt;             // n
   int64_t* sc_ptr;             // n+1: stiff entries per variable (CSC of the stiff rows)
@@ -88,6 +91,7 @@ Geo make_geo(const Dev& d);
 cudaError_t launch_lr(const Dev& d, const double* v, int quad, cudaStream_t st);
 // ---- setup and start point ----
 cudaError_t launch_diagH(const Dev& d, cudaStream_t st);
+cudaError_t launch_fill_rowk(const Dev& d, cudaStream_t st);
 cudaError_t launch_start_point(const Dev& d, const Geo& g, cudaStream_t st);
 // ---- residual summary at the current iterate and mu ----
 cudaError_t launch_residual_summary(const Dev& d, const Geo& g, cudaStream_t st);

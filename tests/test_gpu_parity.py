@@ -337,3 +337,45 @@ def test_staged_rows_pass_equals_unstaged(storage):
             out = s.get()
             xs.append((out["x"], out["info"]["cg_iters"], out["info"]["refine_passes"]))
     assert np.array_equal(xs[0][0], xs[1][0]) and xs[0][1:] == xs[1][1:]
+
+
+@pytest.mark.parametrize("name,make", CASES[:3], ids=[c[0] for c in CASES[:3]])
+def test_augmented_system_direction(name, make):
+    """PCG on the paper's doubly augmented system (Section 4, eq:2x2_augmented) gives the
+    oracle's direction of that system, which equals the condensed one."""
+    p = make()
+    s, qp = _load(p, system="augmented", max_cg=50000)
+    it = _iterate(p, qp, 13, spread=1.0)
+    mu = 0.05
+    s.set_iterate(it.x, it.s, it.y, it.zl, it.zu, mu)
+    d = s.newton_direction(eta=1e-12)
+    assert d["report"]["converged"] == 1, d["report"]
+    dx_ref, dy_ref = O.doubly_augmented_direction(qp, it, mu)
+    err = lambda a, b: np.abs(a - b).max() / (np.abs(b).max() + 1e-300)
+    assert err(d["dx"], dx_ref) <= 1e-6
+    if qp.m:
+        assert err(d["dy"], dy_ref) <= 1e-6
+    ref = O.newton_direction(qp, it, mu)
+    assert err(d["dx"], ref.x) <= 1e-6
+    s.close()
+
+
+@pytest.mark.parametrize("name,make", CASES[:3], ids=[c[0] for c in CASES[:3]])
+def test_augmented_system_solves(name, make):
+    p = make()
+    tol = 1e-8
+    s, qp = _load(p, system="augmented", tol_kkt=tol, max_cg=50000)
+    st = s.solve()
+    out = s.get()
+    s.close()
+    ref, info = O.solve(qp, tol=tol)
+    _check_solution(p, qp, st, out, ref, tol)
+    f, f0 = O.objective(qp, out["x"]), O.objective(qp, ref.x)
+    assert abs(f - f0) <= 1e-6 * (1 + abs(f0))
+
+
+def test_augmented_system_option_checks():
+    with pytest.raises(ipm.IpmError):
+        ipm.Solver(system="augmented", storage="bf16")
+    with pytest.raises(ipm.IpmError):
+        ipm.Solver(system="augmented", precond="jacobi_lr")
