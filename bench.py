@@ -500,7 +500,7 @@ def run_dense(args):
     torch.cuda.set_device(0)
     build.build()
     p = W.dense_qp(n=500, m=1000, seed=0)
-    s = ipm.Solver(tol_kkt=1e-8)
+    s = ipm.Solver(tol_kkt=1e-8, use_graphs=0 if args.no_graphs else 1)
     s.set_qp_dense(p["H"], p["c"], p["A"], p["b"], p["l"], p["u"])
     for _ in range(args.warmup):
         s.solve()
