@@ -250,7 +250,7 @@ void carve_state(Carver& cv, Dev& d, int64_t n, int64_t m, int64_t nR, int stiff
   d.us = cv.take<double>(stiff_cap); d.ts = cv.take<double>(stiff_cap); d.stiff_cap = stiff_cap;
   d.us2 = cv.take<double>(stiff_cap);
   d.hist = cv.take<unsigned int>(kHistBins);
-  if (dense) { d.Kd = cv.take<double>(n * n); d.Kinv = cv.take<double>(n * n); } else { d.Kd = d.Kinv = nullptr; }
+  d.Kd = dense ? cv.take<double>(n * n) : nullptr;
   d.chol_diag = cv.take<double>(std::max<int64_t>(dense ? n : 0, stiff_cap));
   d.storage = storage;
   if (storage != ST_F64) {

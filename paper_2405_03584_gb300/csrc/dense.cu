@@ -4,8 +4,10 @@
 //   * k_chol_*   : in-place blocked Cholesky factor (lower) with pivot flooring;
 //   * k_mirror   : copies L into the upper triangle so both sweeps of the inverse read rows;
 //   * k_inv      : explicit inverse from the factor, columns spread over blocks.
-// The explicit inverse turns every preconditioner apply inside PCG into a parallel matvec;
-// the factorisation runs once per IPM iteration.
+// The low-rank correction's G (up to 1024 rows) is inverted explicitly, so each of the many
+// PCG applies is a parallel matvec; the DENSE preconditioner, whose PCG takes one or two
+// iterations, is applied by triangular solves with the factor instead.  The factorisation
+// runs once per IPM iteration.
 #include <algorithm>
 #include <cmath>
 
@@ -231,7 +233,7 @@ cudaError_t launch_dense_build(const Dev& d, cudaStream_t st) {
   cudaError_t e = launch_chol(d.Kd, d.n, nullptr, n, n, d.chol_diag, &d.sc->chol_fail, st);
   if (e != cudaSuccess) return e;
   k_mirror<<<256, 256, 0, st>>>(d.Kd, d.n, nullptr, n);
-  k_inv<<<(int)std::min<int64_t>(d.n, 4 * 152), 256, rowbytes, st>>>(d.Kd, d.n, nullptr, n, d.Kinv, d.n);
+  (void)rowbytes;   // applied by triangular solves (k_dense_trsv), no explicit inverse
   return cudaGetLastError();
 }
 

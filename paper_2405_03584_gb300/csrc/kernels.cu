@@ -1199,38 +1199,82 @@ __global__ void k_stiff_corr(Dev d, int init) {
   }
 }
 
-// Dense preconditioner apply: z = Kinv r (one warp per row); r^T z -> rz / beta; init: p = z.
-__global__ void k_dense_apply(Dev d, int init) {
+// Dense preconditioner apply by triangular solves: z = K^{-1} r with K = L L^T (L in the
+// lower triangle of Kd, L^T mirrored into the upper triangle, both row-major), forward
+// L y = r then backward L^T z = y, in blocks of 32 rows: warp 0 solves the diagonal block
+// (lane i holds y_i, one shuffle per row), then all threads update the remaining rows with
+// the block's 32 columns.  One block of 1024 threads; y in shared memory (n <= 2048).
+// r^T z -> rz / beta; init: p = z.  (PCG with the exact factor converges in one or two
+// iterations, so this replaces forming K^{-1} once per IPM iteration.)
+__global__ void __launch_bounds__(1024) k_dense_trsv(Dev d, int init) {
+  extern __shared__ double y[];
   __shared__ double sh[32];
   if (!init && d.sc->cg_done) return;
-  const int lane = threadIdx.x & 31;
-  double rz = 0.0;
-  for (int64_t j = gwarp(); j < d.n; j += nwarps()) {
-    const double* kr = d.Kinv + j * d.n;
-    double acc = 0.0;
-    for (int64_t i = lane; i < d.n; i += 32) acc = fma(kr[i], d.r[i], acc);
-    acc = warp_sum(acc);
-    if (lane == 0) {
-      d.z[j] = acc;
-      if (init) {
-        d.p[j] = acc;
-        if (d.p32) d.p32[j] = (float)acc;
+  const int n = (int)d.n;
+  const double* K = d.Kd;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < n; i += blockDim.x) y[i] = d.r[i];
+  __syncthreads();
+  // forward: L y = r
+  for (int kb = 0; kb < n; kb += 32) {
+    const int bs = min(32, n - kb);
+    if (warp == 0) {
+      double yl = lane < bs ? y[kb + lane] : 0.0;
+      for (int c = 0; c < bs; ++c) {
+        if (lane == c) yl = yl / K[(int64_t)(kb + c) * n + kb + c];
+        const double v = __shfl_sync(0xffffffffu, yl, c);
+        if (lane > c && lane < bs) yl = fma(-K[(int64_t)(kb + lane) * n + kb + c], v, yl);
       }
-      rz = fma(d.r[j], acc, rz);
+      if (lane < bs) y[kb + lane] = yl;
     }
+    __syncthreads();
+    for (int r = kb + bs + tid; r < n; r += blockDim.x) {
+      const double* Lr = K + (int64_t)r * n + kb;
+      double acc = 0.0;
+      for (int c = 0; c < bs; ++c) acc = fma(Lr[c], y[kb + c], acc);
+      y[r] -= acc;
+    }
+    __syncthreads();
   }
-  double v[1] = {rz};
-  const int ops[1] = {0};
-  double out[1];
-  if (grid_reduce<1>(v, ops, d.partials + 19 * kMaxRedBlocks, &d.sc->ticket[T_CORR], out, sh)) {
-    if (threadIdx.x == 0) {
-      Scal* sc = d.sc;
-      if (init) {
-        sc->rz = out[0];
-      } else {
-        sc->beta = out[0] / sc->rz;
-        sc->rz = out[0];
+  // backward: L^T z = y, with L^T row i in the upper triangle of row i
+  for (int kb = ((n - 1) / 32) * 32; kb >= 0; kb -= 32) {
+    const int bs = min(32, n - kb);
+    if (warp == 0) {
+      double yl = lane < bs ? y[kb + lane] : 0.0;
+      for (int c = bs - 1; c >= 0; --c) {
+        if (lane == c) yl = yl / K[(int64_t)(kb + c) * n + kb + c];
+        const double v = __shfl_sync(0xffffffffu, yl, c);
+        if (lane < c) yl = fma(-K[(int64_t)(kb + lane) * n + kb + c], v, yl);
       }
+      if (lane < bs) y[kb + lane] = yl;
+    }
+    __syncthreads();
+    for (int r = tid; r < kb; r += blockDim.x) {
+      const double* Ur = K + (int64_t)r * n + kb;
+      double acc = 0.0;
+      for (int c = 0; c < bs; ++c) acc = fma(Ur[c], y[kb + c], acc);
+      y[r] -= acc;
+    }
+    __syncthreads();
+  }
+  double rz = 0.0;
+  for (int j = tid; j < n; j += blockDim.x) {
+    const double zj = y[j];
+    d.z[j] = zj;
+    if (init) {
+      d.p[j] = zj;
+      if (d.p32) d.p32[j] = (float)zj;
+    }
+    rz = fma(d.r[j], zj, rz);
+  }
+  rz = block_reduce<0>(rz, sh);
+  if (tid == 0) {
+    Scal* sc = d.sc;
+    if (init) {
+      sc->rz = rz;
+    } else {
+      sc->beta = rz / sc->rz;
+      sc->rz = rz;
     }
   }
 }
@@ -1269,7 +1313,7 @@ __global__ void k_cg_p(Dev d, cudaGraphConditionalHandle h, int set_cond) {
 
 cudaError_t launch_cg_init(const Dev& d, const Geo& g, int precond, cudaStream_t st) {
   if (precond == PC_DENSE) {
-    k_dense_apply<<<g.gN, kBlock, 0, st>>>(d, 1);
+    k_dense_trsv<<<1, 1024, sizeof(double) * d.n, st>>>(d, 1);
   } else if (precond == PC_JACOBI_LR) {
     k_cg_init_diag<<<g.eN, kBlock, 0, st>>>(d);
     const int gs = (d.stiff_cap + 7) / 8;
@@ -1294,7 +1338,7 @@ cudaError_t launch_cg_body(const Dev& d, const Geo& g, int precond, cudaGraphCon
   }
   if (precond == PC_DENSE) {
     k_cg_update<2><<<g.eN, kBlock, 0, st>>>(d);
-    k_dense_apply<<<g.gN, kBlock, 0, st>>>(d, 0);
+    k_dense_trsv<<<1, 1024, sizeof(double) * d.n, st>>>(d, 0);
   } else if (precond == PC_JACOBI_LR) {
     k_cg_update<1><<<g.eN, kBlock, 0, st>>>(d);
     const int gs = (d.stiff_cap + 7) / 8;

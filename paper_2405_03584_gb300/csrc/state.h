@@ -61,7 +61,7 @@ struct Dev {
   int stiff_cap;
   unsigned int* hist;          // kHistBins
   // dense preconditioner (n x n), nullptr if not allocated
-  double *Kd, *Kinv;
+  double* Kd;                  // n x n: the condensed matrix, then its Cholesky factor (L and L^T)
   double* chol_diag;           // max(n_dense, stiff_cap): original diagonal during a factorisation
   // reduced-precision copy of the matrix values (storage != ST_F64): R~_ij = scaleR_i * q_ij
   int storage;
