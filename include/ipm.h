@@ -84,8 +84,8 @@ typedef struct ipm_options {
   int max_ipm;           /* IPM iteration limit (200)                                          */
   int max_cg;            /* PCG iteration limit per Newton step (2000)                         */
   double cg_eta_max;     /* PCG relative tolerance eta = clamp(cg_eta_factor * relKKT, ...)    */
-  double cg_eta_min;     /*   ... between cg_eta_min (1e-10) and cg_eta_max (1e-3)            */
-  double cg_eta_factor;  /*   (0.1)                                                            */
+  double cg_eta_min;     /*   ... between cg_eta_min (1e-10) and cg_eta_max (1e-2)            */
+  double cg_eta_factor;  /*   (0.3)                                                            */
   int precond;           /* enum ipm_precond (IPM_PRECOND_AUTO: DENSE if n <= 1024, else       */
                          /* JACOBI_LR)                                                         */
   double stiff_gamma;    /* JACOBI_LR threshold (1.0)                                          */

@@ -698,9 +698,9 @@ void ipm_default_options(ipm_options* o) {
   o->tau = 0.995;
   o->max_ipm = 200;
   o->max_cg = 2000;
-  o->cg_eta_max = 1e-3;
+  o->cg_eta_max = 1e-2;
   o->cg_eta_min = 1e-10;
-  o->cg_eta_factor = 0.1;
+  o->cg_eta_factor = 0.3;
   o->precond = IPM_PRECOND_AUTO;
   o->stiff_gamma = 1.0;
   o->stiff_max = 256;
