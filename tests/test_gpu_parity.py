@@ -3,7 +3,7 @@
 Sizes span several blocks of every kernel and leave ragged tails (n, m not multiples of the
 warp or block size).  Floating-point tolerances follow from FP64 arithmetic with a different
 summation order: elementwise 1e-10 relative for single products and residuals; PCG
-directions within their requested tolerance; end-to-end results at the spec bar of
+directions within their requested tolerance; end-to-end results at the accuracy bar of
 relative KKT <= tol and relative objective difference <= 1e-6 against the oracle.
 """
 import numpy as np
@@ -271,7 +271,7 @@ def test_bad_inputs_rejected():
 def test_reduced_precision_operator_refined_to_fp64(storage):
     """D and A stored in FP32 / BF16 / FP8-E4M3 with per-row scales, FP32-accumulating PCG,
     FP64 iterative refinement of each Newton step: the solve must still match the FP64
-    oracle at the spec bar (rel KKT <= tol, rel objective difference <= 1e-6)."""
+    oracle at the accuracy bar (rel KKT <= tol, rel objective difference <= 1e-6)."""
     p = W.rt_qp(n=1400, seed=19)
     st, out, ref, qp = _solve_both(p, 1e-7, precond="jacobi_lr", storage=storage, max_cg=5000)
     _check_solution(p, qp, st, out, ref, 1e-7)
