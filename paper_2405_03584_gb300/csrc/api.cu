@@ -251,6 +251,9 @@ void carve_state(Carver& cv, Dev& d, int64_t n, int64_t m, int64_t nR, int stiff
   d.us2 = cv.take<double>(stiff_cap);
   d.hist = cv.take<unsigned int>(kHistBins);
   d.Kd = dense ? cv.take<double>(n * n) : nullptr;
+  // the dense preconditioner forms K by a tiled product over R stored densely when that
+  // copy stays below 256 MB (else it scans R's rows)
+  d.Rd = (dense && nR * n <= (int64_t)(32 << 20)) ? cv.take<double>(nR * n) : nullptr;
   d.chol_diag = cv.take<double>(std::max<int64_t>(dense ? n : 0, stiff_cap));
   d.storage = storage;
   if (storage != ST_F64) {
@@ -1116,6 +1119,7 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   CUDA_TRY(h, cudaMemsetAsync(d.hist, 0, sizeof(unsigned int) * kHistBins, h->st));
   CUDA_TRY(h, cudaMemsetAsync(d.slotR, 0xff, sizeof(int32_t) * std::max<int64_t>(q.nR, 1), h->st));
   CUDA_TRY(h, launch_fill_rowk(d, h->st));
+  CUDA_TRY(h, launch_densify_R(d, h->st));
   if (d.ucap) CUDA_TRY(h, cudaMemsetAsync(d.lrs, 0, sizeof(double) * d.ucap, h->st));
   std::memset(h->hs, 0, sizeof(Scal));
   push_options(h);
@@ -1198,6 +1202,7 @@ int ipm_share_qp(ipm_handle* h, ipm_handle* src, void* stream) {
   CUDA_TRY(h, cudaMemsetAsync(d.hist, 0, sizeof(unsigned int) * kHistBins, h->st));
   CUDA_TRY(h, cudaMemsetAsync(d.slotR, 0xff, sizeof(int32_t) * std::max<int64_t>(nR, 1), h->st));
   CUDA_TRY(h, launch_fill_rowk(d, h->st));
+  CUDA_TRY(h, launch_densify_R(d, h->st));
   if (d.ucap) CUDA_TRY(h, cudaMemsetAsync(d.lrs, 0, sizeof(double) * d.ucap, h->st));
   std::memset(h->hs, 0, sizeof(Scal));
   push_options(h);

@@ -1,8 +1,9 @@
 // Dense pieces of the preconditioners (sm_103a, float64):
-//   * k_gram_K   : K = Hs + R^T diag(omega) R + U W U^T + diag(h0 + sigma) as a dense n x n matrix
+//   * k_gram_tiles / k_gram_diag_hs : K = Hs + R^T diag(omega) R + U W U^T + diag(h0 + sigma) as a
+//                  dense n x n matrix
 //                  (the DENSE preconditioner: one diagonal block covering all variables);
 //   * k_chol_*   : in-place blocked Cholesky factor (lower) with pivot flooring;
-//   * k_mirror   : copies L into the upper triangle so both sweeps of the inverse read rows;
+//   * k_mirror   : copies L into the upper triangle so both triangular sweeps read rows;
 //   * k_inv      : explicit inverse from the factor, columns spread over blocks.
 // The low-rank correction's G (up to 1024 rows) is inverted explicitly, so each of the many
 // PCG applies is a parallel matvec; the DENSE preconditioner, whose PCG takes one or two
@@ -15,42 +16,6 @@
 
 namespace ipmk {
 
-// One block per row j of K.  Rows of R are summed in the fixed order of the stored
-// transpose; the entries of one row of R have distinct columns, so threads never collide.
-__global__ void k_gram_K(Dev d) {
-  extern __shared__ double row[];
-  const int64_t n = d.n;
-  for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) row[i] = 0.0;
-    __syncthreads();
-    if (threadIdx.x == 0) row[j] = d.h0[j] + d.sigma[j];
-    __syncthreads();
-    if (d.Hs_ptr) {
-      for (int64_t e = d.Hs_ptr[j] + threadIdx.x; e < d.Hs_ptr[j + 1]; e += blockDim.x) row[d.Hs_idx[e]] += d.Hs_val[e];
-      __syncthreads();
-    }
-    if (d.ucols) {
-      // (U W U^T)_ji = sum_r U_jr w_r U_ir, one column i per thread
-      const double* uj = d.U + j * d.ucols;
-      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const double* ui = d.U + i * d.ucols;
-        double a = 0.0;
-        for (int64_t r = 0; r < d.ucols; ++r) a = fma(uj[r] * d.uw[r], ui[r], a);
-        row[i] += a;
-      }
-      __syncthreads();
-    }
-    for (int64_t e = d.RT_ptr[j]; e < d.RT_ptr[j + 1]; ++e) {
-      const int32_t i = d.RT_idx[e];
-      const double f = d.RT_val[e] * d.omega[i];
-      if (f != 0.0)
-        for (int64_t t = d.R_ptr[i] + threadIdx.x; t < d.R_ptr[i + 1]; t += blockDim.x) row[d.R_idx[t]] += f * d.R_val[t];
-      __syncthreads();
-    }
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) d.Kd[j * n + i] = row[i];
-    __syncthreads();
-  }
-}
 
 // Blocked right-looking Cholesky (lower, row-major, leading dimension ld) of the leading
 // nn x nn block of A, on 32 x 32 tiles spread over many blocks:
@@ -226,10 +191,167 @@ __global__ void k_inv(const double* A, int64_t ld, const int* nn_dev, int nn_fix
   }
 }
 
+// K = R^T diag(omega) R + U W U^T + Hs + diag(h0 + sigma) by 32 x 32 tiles: one block per
+// tile of the lower triangle; for every row i of R (in order) the block gathers the row's
+// entries that fall in its two column ranges (scaled by omega_i on one side) and adds their
+// outer product (2 x 2 outputs per thread); the columns of U likewise.  Each output is a sum
+// in row order, so K is deterministic; off-diagonal tiles are written to both triangles.
+constexpr int kGT = 32;
+
+__global__ void __launch_bounds__(256) k_gram_tiles(Dev d) {
+  __shared__ double sJ[kGT], sL[kGT];
+  const int64_t n = d.n;
+  const int64_t b = blockIdx.x;
+  int64_t tj = (int64_t)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+  while ((tj + 1) * (tj + 2) / 2 <= b) ++tj;
+  while (tj * (tj + 1) / 2 > b) --tj;
+  const int64_t tl = b - tj * (tj + 1) / 2;
+  const int64_t J0 = tj * kGT, L0 = tl * kGT;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int64_t i = 0; i < d.nR; ++i) {
+    if (tid < kGT) { sJ[tid] = 0.0; sL[tid] = 0.0; }
+    __syncthreads();
+    const double w = d.omega[i];
+    int hj = 0, hl = 0;
+    if (w != 0.0) {
+      for (int64_t e = d.R_ptr[i] + tid; e < d.R_ptr[i + 1]; e += blockDim.x) {
+        const int64_t c = d.R_idx[e];
+        const double v = d.R_val[e];
+        if (c >= J0 && c < J0 + kGT) { sJ[c - J0] = w * v; hj = 1; }
+        if (c >= L0 && c < L0 + kGT) { sL[c - L0] = v; hl = 1; }
+      }
+    }
+    hj = __syncthreads_or(hj);
+    hl = __syncthreads_or(hl);
+    if (hj && hl) {
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) acc[a][c] = fma(sJ[2 * ty + a], sL[2 * tx + c], acc[a][c]);
+    }
+    __syncthreads();
+  }
+  for (int64_t r = 0; r < d.ucols; ++r) {
+    if (tid < kGT) {
+      sJ[tid] = J0 + tid < n ? d.U[(J0 + tid) * d.ucols + r] * d.uw[r] : 0.0;
+      sL[tid] = L0 + tid < n ? d.U[(L0 + tid) * d.ucols + r] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) acc[a][c] = fma(sJ[2 * ty + a], sL[2 * tx + c], acc[a][c]);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int64_t j = J0 + 2 * ty + a, l = L0 + 2 * tx + c;
+      if (j < n && l < n) {
+        d.Kd[j * n + l] = acc[a][c];
+        if (tj != tl) d.Kd[l * n + j] = acc[a][c];
+      }
+    }
+}
+
+// The same tiles from the dense copy of R: chunks of 32 rows of Rd staged in shared memory
+// (one side scaled by omega), 2 x 2 outputs per thread, rows summed in order; plus U W U^T.
+__global__ void __launch_bounds__(256) k_gram_gemm(Dev d) {
+  __shared__ double sA[kGT][kGT + 1], sB[kGT][kGT + 1];
+  const int64_t n = d.n;
+  const int64_t b = blockIdx.x;
+  int64_t tj = (int64_t)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+  while ((tj + 1) * (tj + 2) / 2 <= b) ++tj;
+  while (tj * (tj + 1) / 2 > b) --tj;
+  const int64_t tl = b - tj * (tj + 1) / 2;
+  const int64_t J0 = tj * kGT, L0 = tl * kGT;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int64_t i0 = 0; i0 < d.nR; i0 += kGT) {
+    for (int t = tid; t < kGT * kGT; t += blockDim.x) {
+      const int ii = t >> 5, cc = t & 31;
+      const int64_t i = i0 + ii;
+      const bool in = i < d.nR;
+      sA[ii][cc] = (in && J0 + cc < n) ? d.Rd[i * n + J0 + cc] * d.omega[i] : 0.0;
+      sB[ii][cc] = (in && L0 + cc < n) ? d.Rd[i * n + L0 + cc] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int ii = 0; ii < kGT; ++ii) {
+      const double a0 = sA[ii][2 * ty], a1 = sA[ii][2 * ty + 1];
+      const double b0 = sB[ii][2 * tx], b1 = sB[ii][2 * tx + 1];
+      acc[0][0] = fma(a0, b0, acc[0][0]);
+      acc[0][1] = fma(a0, b1, acc[0][1]);
+      acc[1][0] = fma(a1, b0, acc[1][0]);
+      acc[1][1] = fma(a1, b1, acc[1][1]);
+    }
+    __syncthreads();
+  }
+  for (int64_t r = 0; r < d.ucols; ++r) {
+    if (tid < kGT) {
+      sA[0][tid] = J0 + tid < n ? d.U[(J0 + tid) * d.ucols + r] * d.uw[r] : 0.0;
+      sB[0][tid] = L0 + tid < n ? d.U[(L0 + tid) * d.ucols + r] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) acc[a][c] = fma(sA[0][2 * ty + a], sB[0][2 * tx + c], acc[a][c]);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int64_t j = J0 + 2 * ty + a, l = L0 + 2 * tx + c;
+      if (j < n && l < n) {
+        d.Kd[j * n + l] = acc[a][c];
+        if (tj != tl) d.Kd[l * n + j] = acc[a][c];
+      }
+    }
+}
+
+__global__ void k_densify_zero(double* Rd, int64_t total) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
+    Rd[t] = 0.0;
+}
+
+__global__ void k_densify_fill(Dev d) {
+  for (int64_t r = blockIdx.x; r < d.nR; r += gridDim.x)
+    for (int64_t e = d.R_ptr[r] + threadIdx.x; e < d.R_ptr[r + 1]; e += blockDim.x) d.Rd[r * d.n + d.R_idx[e]] = d.R_val[e];
+}
+
+cudaError_t launch_densify_R(const Dev& d, cudaStream_t st) {
+  if (!d.Rd || !d.nR) return cudaSuccess;
+  k_densify_zero<<<1024, 256, 0, st>>>(d.Rd, d.nR * d.n);
+  k_densify_fill<<<(int)std::min<int64_t>(d.nR, 4096), 256, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+// Adds diag(h0 + sigma) and the explicit block Hs (each entry once: no conflicts).
+__global__ void k_gram_diag_hs(Dev d) {
+  const int64_t n = d.n;
+  for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
+    if (threadIdx.x == 0) d.Kd[j * n + j] += d.h0[j] + d.sigma[j];
+    if (d.Hs_ptr) {
+      __syncthreads();
+      for (int64_t e = d.Hs_ptr[j] + threadIdx.x; e < d.Hs_ptr[j + 1]; e += blockDim.x) d.Kd[j * n + d.Hs_idx[e]] += d.Hs_val[e];
+    }
+    __syncthreads();
+  }
+}
+
 cudaError_t launch_dense_build(const Dev& d, cudaStream_t st) {
   const int n = (int)d.n;
   const size_t rowbytes = sizeof(double) * (size_t)n;
-  k_gram_K<<<(int)std::min<int64_t>(d.n, 4 * 152), 256, rowbytes, st>>>(d);
+  const int64_t nt = (d.n + kGT - 1) / kGT;
+  if (d.Rd)
+    k_gram_gemm<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, st>>>(d);
+  else
+    k_gram_tiles<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, st>>>(d);
+  k_gram_diag_hs<<<(int)std::min<int64_t>(d.n, 4 * 152), 256, 0, st>>>(d);
   cudaError_t e = launch_chol(d.Kd, d.n, nullptr, n, n, d.chol_diag, &d.sc->chol_fail, st);
   if (e != cudaSuccess) return e;
   k_mirror<<<256, 256, 0, st>>>(d.Kd, d.n, nullptr, n);

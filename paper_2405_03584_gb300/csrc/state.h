@@ -62,6 +62,7 @@ struct Dev {
   unsigned int* hist;          // kHistBins
   // dense preconditioner (n x n), nullptr if not allocated
   double* Kd;                  // n x n: the condensed matrix, then its Cholesky factor (L and L^T)
+  double* Rd;                  // nR x n: R as a dense matrix (when it is small enough), or nullptr
   double* chol_diag;           // max(n_dense, stiff_cap): original diagonal during a factorisation
   // reduced-precision copy of the matrix values (storage != ST_F64): R~_ij = scaleR_i * q_ij
   int storage;
@@ -92,6 +93,7 @@ cudaError_t launch_lr(const Dev& d, const double* v, int quad, cudaStream_t st);
 // ---- setup and start point ----
 cudaError_t launch_diagH(const Dev& d, cudaStream_t st);
 cudaError_t launch_fill_rowk(const Dev& d, cudaStream_t st);
+cudaError_t launch_densify_R(const Dev& d, cudaStream_t st);   // dense.cu: Rd from R (once per QP)
 cudaError_t launch_start_point(const Dev& d, const Geo& g, cudaStream_t st);
 // ---- residual summary at the current iterate and mu ----
 cudaError_t launch_residual_summary(const Dev& d, const Geo& g, cudaStream_t st);
