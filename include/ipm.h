@@ -261,6 +261,11 @@ int ipm_share_qp(ipm_handle* h, ipm_handle* src, void* stream);
  * handles referencing it) and the handle's own state.  Any output may be NULL. */
 int ipm_device_bytes(const ipm_handle* h, int64_t* matrix_bytes, int64_t* state_bytes, int* matrix_refs);
 
+/* Sizes in bytes of the interface structs as this library was compiled (ipm_options,
+ * ipm_qp, ipm_info, ipm_cg_report), for bindings to check their own layouts.  Any pointer
+ * may be NULL.  No counterpart in the paper. */
+int ipm_abi_sizes(int64_t* options, int64_t* qp, int64_t* info, int64_t* cg_report);
+
 /* Frees the handle and its device memory.  NULL-safe. */
 int ipm_destroy(ipm_handle* h);
 

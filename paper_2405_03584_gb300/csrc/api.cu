@@ -831,6 +831,14 @@ int ipm_set_lowrank(ipm_handle* h, int64_t u_cols, const double* U, const double
   return leave(h, stream);
 }
 
+int ipm_abi_sizes(int64_t* options, int64_t* qp, int64_t* info, int64_t* cg_report) {
+  if (options) *options = (int64_t)sizeof(ipm_options);
+  if (qp) *qp = (int64_t)sizeof(ipm_qp);
+  if (info) *info = (int64_t)sizeof(ipm_info);
+  if (cg_report) *cg_report = (int64_t)sizeof(ipm_cg_report);
+  return IPM_OK;
+}
+
 int ipm_destroy(ipm_handle* h) {
   if (!h) return IPM_OK;
   cudaSetDevice(h->device);

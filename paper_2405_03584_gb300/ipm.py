@@ -31,7 +31,7 @@ EXPORTS = ["ipm_default_options", "ipm_create", "ipm_set_qp", "ipm_solve", "ipm_
            "ipm_precond_diag", "ipm_newton_direction", "ipm_step_lengths", "ipm_profile_operator",
            "ipm_get_trace", "ipm_apply_operator_static", "ipm_solve_async", "ipm_solve_wait", "ipm_solve_query",
            "ipm_batch_create", "ipm_batch_solve", "ipm_batch_destroy", "ipm_update_costs", "ipm_share_qp",
-           "ipm_device_bytes", "ipm_set_lowrank"]
+           "ipm_device_bytes", "ipm_set_lowrank", "ipm_abi_sizes"]
 TRACE_COLS = ("iter", "mu", "rel_kkt", "primal", "dual", "gap", "alpha_p", "alpha_d", "pcg_iters", "pcg_converged",
               "stiff_rows", "pcg_rel_residual", "eta", "refine_passes")
 
@@ -115,6 +115,7 @@ def load(path: str = LIB_PATH):
         "ipm_share_qp": (I, [P, P, P]),
         "ipm_device_bytes": (I, [P, P, P, P]),
         "ipm_set_lowrank": (I, [P, C.c_int64, P, P, I, P]),
+        "ipm_abi_sizes": (I, [P, P, P, P]),
         "ipm_apply_operator_static": (I, [C.c_int64, C.c_int64] + [P] * 10 + [P]),
     }
     for name, (res, args) in sig.items():

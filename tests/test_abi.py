@@ -60,3 +60,11 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(ipm, "_lib", None)
     with pytest.raises(ImportError):
         ipm.load(str(tmp_path / "nope.so"))
+
+
+def test_struct_layouts_match_the_library(lib):
+    """The binding's ctypes structs have the sizes the library was compiled with."""
+    sizes = [C.c_int64() for _ in range(4)]
+    assert lib.ipm_abi_sizes(*[C.byref(v) for v in sizes]) == ipm.IPM_OK
+    ours = [C.sizeof(ipm.Options), C.sizeof(ipm.QP), C.sizeof(ipm.Info), C.sizeof(ipm.CgReport)]
+    assert [v.value for v in sizes] == ours
