@@ -43,7 +43,9 @@ enum ipm_status {
   IPM_MAX_ITER = 3,              /* options.max_ipm iterations without reaching tol_kkt         */
   IPM_CG_STALL = 4,              /* PCG hit options.max_cg without meeting its tolerance        */
   IPM_NUMERICAL = 5,             /* NaN/Inf in an iterate, PCG breakdown or step length -> 0    */
-  IPM_INFEASIBLE_SUSPECTED = 6,  /* primal or dual residual stagnates while mu -> 0             */
+  IPM_INFEASIBLE_SUSPECTED = 6,  /* the multipliers diverge along a Farkas certificate of primal */
+                                 /* infeasibility (y, z >= 0, A^T y - z_l + z_u ~ 0,            */
+                                 /* b^T y - l^T z_l + u^T z_u < 0 after scaling)               */
   IPM_ERR_TIMEOUT = 7,           /* host wall-clock limit options.timeout_ms exceeded           */
   IPM_ERR_CUDA = 8,              /* a CUDA runtime call failed (see ipm_last_error)             */
   IPM_ERR_STATE = 9,             /* call out of order (e.g. ipm_solve before ipm_set_qp)        */

@@ -1322,7 +1322,8 @@ static int fill_info(ipm_handle* h, int64_t direct_launches) {
   }
   int status = s.status == DS_OK ? IPM_OK : s.status == DS_MAX_ITER ? IPM_MAX_ITER
              : s.status == DS_CG_STALL ? IPM_CG_STALL : s.status == DS_RUNNING ? IPM_MAX_ITER
-             : s.status == DS_TIMEOUT ? IPM_ERR_TIMEOUT : IPM_NUMERICAL;
+             : s.status == DS_TIMEOUT ? IPM_ERR_TIMEOUT : s.status == DS_INFEASIBLE ? IPM_INFEASIBLE_SUSPECTED
+             : IPM_NUMERICAL;
   ipm_info& in = h->info;
   in.status = status;
   in.ipm_iters = s.ipm_iter;

@@ -38,6 +38,9 @@ struct Scal {
   // FP64 refinement of a reduced-precision Newton step
   double tol2_outer, rr_outer, refine_eta;
   double lr_quad;               // x^T U W U^T x of the last residual summary
+  // primal infeasibility certificate (Farkas): with (y, z) scaled by its largest entry,
+  // |A^T y - z_l + z_u|_inf and b^T y - l^T z_l + u^T z_u
+  double cert_res, cert_gap, mult_inf;
   // warm start: pairs raised to at least warm_rho * mu0_cold (mu0 of the last cold start)
   double mu0_cold, warm_rho;
   int refine_it, refine_max, cg_step_total, cg_conv_outer, fallback, fallback_total;
@@ -60,7 +63,8 @@ enum ScalTicket { T_PQ = 0, T_UPD = 1, T_CORR = 2, T_INIT = 3, T_HIST = 4, T_STE
 enum Storage { ST_F64 = 0, ST_F32 = 1, ST_BF16 = 2, ST_FP8 = 3 };
 
 // Status values written by the device (mirror enum ipm_status).
-enum DevStatus { DS_RUNNING = -1, DS_OK = 0, DS_MAX_ITER = 3, DS_CG_STALL = 4, DS_NUMERICAL = 5, DS_TIMEOUT = 7 };
+enum DevStatus { DS_RUNNING = -1, DS_OK = 0, DS_MAX_ITER = 3, DS_CG_STALL = 4, DS_NUMERICAL = 5, DS_INFEASIBLE = 6,
+                 DS_TIMEOUT = 7 };
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

@@ -256,7 +256,7 @@ __global__ void k_rows_resid(Dev d, double* part) {
 __global__ void k_cons_resid(Dev d, double* part) {
   __shared__ double sh[32];
   const double mu = d.sc->mu;
-  double rp_inf = 0.0, viol = 0.0, rs_inf = 0.0, by = 0.0, sy = 0.0;
+  double rp_inf = 0.0, viol = 0.0, rs_inf = 0.0, by = 0.0, sy = 0.0, ymax = 0.0;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.m; k += (int64_t)gridDim.x * blockDim.x) {
     const int32_t row = d.arow[k];
     const double ax = d.tR[row];
@@ -268,6 +268,7 @@ __global__ void k_cons_resid(Dev d, double* part) {
     viol = fmax(viol, ax - d.b[k]);
     rs_inf = fmax(rs_inf, fabs(rs));
     by = fma(d.b[k], d.y[k], by);
+    ymax = fmax(ymax, fabs(d.y[k]));
     sy = fma(d.s[k], d.y[k], sy);
   }
   const int K = kMaxRedBlocks;
@@ -277,6 +278,7 @@ __global__ void k_cons_resid(Dev d, double* part) {
   v = block_reduce<1>(rs_inf, sh); if (threadIdx.x == 0) part[3 * K + blockIdx.x] = v;
   v = block_reduce<0>(by, sh);     if (threadIdx.x == 0) part[4 * K + blockIdx.x] = v;
   v = block_reduce<0>(sy, sh);     if (threadIdx.x == 0) part[5 * K + blockIdx.x] = v;
+  v = block_reduce<1>(ymax, sh);   if (threadIdx.x == 0) part[28 * K + blockIdx.x] = v;
 }
 
 // Variables: Hx = R^T vR + Hs x + h0 o x, A^T y (over the stored A^T, y placed on R rows in
@@ -287,7 +289,7 @@ __global__ void __launch_bounds__(256, 4) k_cols_resid(Dev d, double* part) {
   __shared__ double sh[32];
   const double mu = d.sc->mu;
   double rd_inf = 0.0, hx_inf = 0.0, aty_inf = 0.0, rc_inf = 0.0, xHsx = 0.0, cx = 0.0, lzl = 0.0,
-         uzu = 0.0, tz = 0.0, bviol = 0.0;
+         uzu = 0.0, tz = 0.0, bviol = 0.0, cert = 0.0, zmax = 0.0;
   FOR_GROUP_ROWS(G, j, ok, d.n) {
     const int64_t beg = ok ? d.RT_ptr[j] : 0, end = ok ? d.RT_ptr[j + 1] : 0;
     const double hx_f = group_row_dot<G, false>(beg, end, glane<G>(), d.RT_idx, d.RT_val, d.vR);
@@ -308,6 +310,8 @@ __global__ void __launch_bounds__(256, 4) k_cols_resid(Dev d, double* part) {
       d.Hx[j] = hx;
       d.Aty[j] = aty;
       d.rd[j] = rd;
+      cert = fmax(cert, fabs(aty - zl + zu));
+      zmax = fmax(zmax, fmax(fabs(zl), fabs(zu)));
       rd_inf = fmax(rd_inf, fabs(rd));
       hx_inf = fmax(hx_inf, fabs(hx));
       aty_inf = fmax(aty_inf, fabs(aty));
@@ -341,6 +345,8 @@ __global__ void __launch_bounds__(256, 4) k_cols_resid(Dev d, double* part) {
   v = block_reduce<0>(uzu, sh);     if (threadIdx.x == 0) part[13 * K + blockIdx.x] = v;
   v = block_reduce<0>(tz, sh);      if (threadIdx.x == 0) part[14 * K + blockIdx.x] = v;
   v = block_reduce<1>(bviol, sh);   if (threadIdx.x == 0) part[15 * K + blockIdx.x] = v;
+  v = block_reduce<1>(cert, sh);    if (threadIdx.x == 0) part[29 * K + blockIdx.x] = v;
+  v = block_reduce<1>(zmax, sh);    if (threadIdx.x == 0) part[30 * K + blockIdx.x] = v;
 }
 
 // One block: totals of the partials, then the relative KKT residual (primal, dual, gap), the
@@ -375,6 +381,9 @@ __global__ void k_resid_final(Dev d, int gR, int gM, int gN, const double* part)
   const double uzu = tot(13, gN, 0);
   const double tz = tot(14, gN, 0);
   const double viol_b = fmax(0.0, tot(15, gN, 1));
+  const double ymax = d.m ? fmax(0.0, tot(28, gM, 1)) : 0.0;
+  const double cert = fmax(0.0, tot(29, gN, 1));
+  const double zmax = fmax(0.0, tot(30, gN, 1));
   if (threadIdx.x == 0) {
     Scal* sc = d.sc;
     const double xHx = xFx + xHsx + (d.ucols ? sc->lr_quad : 0.0);
@@ -399,6 +408,10 @@ __global__ void k_resid_final(Dev d, int gR, int gM, int gN, const double* part)
     const double ep = rp_inf / (1.0 + bn), ed = rd_inf / (1.0 + cn);
     sc->rnorm_mu = fmax(fmax(rs_inf, rc_inf), (1.0 + fabs(pobj)) / nc * fmax(ep, ed));
     sc->comp_mean = (sy + tz) / nc;
+    const double mi = fmax(ymax, zmax);
+    sc->mult_inf = mi;
+    sc->cert_res = mi > 0.0 ? cert / mi : INFINITY;
+    sc->cert_gap = mi > 0.0 ? (by - lzl + uzu) / mi : 0.0;
   }
 }
 
@@ -534,6 +547,12 @@ __global__ void k_control(Dev d, cudaGraphConditionalHandle h, int set_cond) {
   if (sc->cg_iter > sc->max_cg_step) sc->max_cg_step = sc->cg_iter;
   if (sc->status == DS_NUMERICAL || sc->status == DS_CG_STALL || sc->status == DS_TIMEOUT) {
     sc->stop = 1;
+  } else if (sc->ipm_iter >= 5 && !(sc->res_primal <= sc->tol_kkt) && sc->mult_inf > 1e10 &&
+             isfinite(sc->mult_inf) && sc->cert_res <= 1e-8 && sc->cert_gap < -1e-8) {
+    // the multipliers diverge along a Farkas certificate of primal infeasibility:
+    // y >= 0, z >= 0 with A^T y - z_l + z_u ~ 0 and b^T y - l^T z_l + u^T z_u < 0
+    sc->stop = 1;
+    sc->status = DS_INFEASIBLE;
   } else if (!isfinite(rk) || !isfinite(sc->pobj)) {
     sc->stop = 1;
     sc->status = DS_NUMERICAL;

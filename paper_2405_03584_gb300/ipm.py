@@ -313,7 +313,8 @@ class Solver:
     def solve(self, warm=False, stream=None):
         """Runs the IPM; returns the status code (IPM_OK on convergence)."""
         rc = load().ipm_solve(self._h, _default_stream(stream), WARM if warm else COLD)
-        return self._check(rc, "ipm_solve", ok=(IPM_OK, IPM_MAX_ITER, IPM_CG_STALL, IPM_NUMERICAL))
+        return self._check(rc, "ipm_solve", ok=(IPM_OK, IPM_MAX_ITER, IPM_CG_STALL, IPM_NUMERICAL,
+                                                IPM_INFEASIBLE_SUSPECTED))
 
     def solve_async(self, warm=False, stream=None):
         """Queues the whole solve (one graph launch) and returns at once."""
@@ -323,7 +324,8 @@ class Solver:
         """Waits for solve_async; returns the status."""
         info = Info()
         rc = load().ipm_solve_wait(self._h, C.byref(info))
-        return self._check(rc, "ipm_solve_wait", ok=(IPM_OK, IPM_MAX_ITER, IPM_CG_STALL, IPM_NUMERICAL))
+        return self._check(rc, "ipm_solve_wait", ok=(IPM_OK, IPM_MAX_ITER, IPM_CG_STALL, IPM_NUMERICAL,
+                                                     IPM_INFEASIBLE_SUSPECTED))
 
     def done(self):
         """True once the solve started by solve_async has finished (non-blocking)."""

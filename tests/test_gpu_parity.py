@@ -379,3 +379,39 @@ def test_augmented_system_option_checks():
         ipm.Solver(system="augmented", storage="bf16")
     with pytest.raises(ipm.IpmError):
         ipm.Solver(system="augmented", precond="jacobi_lr")
+
+
+def _farkas_ok(A, b, l, u, y, zl, zu):
+    """y, z >= 0 with A^T y - z_l + z_u = 0 and b^T y - l^T z_l + u^T z_u < 0 (after scaling)."""
+    fl, fu = np.isfinite(l), np.isfinite(u)
+    zl = np.where(fl, zl, 0.0)
+    zu = np.where(fu, zu, 0.0)
+    sc = max(np.abs(y).max(initial=0.0), np.abs(zl).max(), np.abs(zu).max())
+    y, zl, zu = y / sc, zl / sc, zu / sc
+    res = np.abs(A.T @ y - zl + zu).max()
+    gap = b @ y - np.where(fl, l, 0.0) @ zl + np.where(fu, u, 0.0) @ zu
+    return y.min(initial=0.0) >= -1e-12 and res <= 1e-6 and gap < -1e-6
+
+
+@pytest.mark.parametrize("case", ["dense_box", "rt_negative_limit"])
+def test_primal_infeasibility_detected(case):
+    if case == "dense_box":
+        n = 7
+        A = np.ones((2, n))
+        A[1, :3] = 2.0
+        b = np.array([-1.0, 5.0])                 # sum(x) <= -1 with 0 <= x <= 1
+        l, u = np.zeros(n), np.ones(n)
+        s = ipm.Solver(tol_kkt=1e-8)
+        s.set_qp_dense(np.eye(n), np.ones(n), A, b, l, u)
+    else:
+        p = W.rt_qp(n=700, seed=71, b_organ=-0.5)  # dose <= -0.5 with D >= 0, x >= 0
+        qp = O.from_rt(p)
+        A, b, l, u = qp.A, qp.b, qp.l, qp.u
+        s = ipm.Solver(tol_kkt=1e-8)
+        s.set_qp_rt(p)
+    st = s.solve()
+    out = s.get()
+    s.close()
+    assert st == ipm.IPM_INFEASIBLE_SUSPECTED, out["info"]
+    assert out["info"]["ipm_iters"] < 200
+    assert _farkas_ok(A, b, l, u, out["y"], out["zl"], out["zu"])
