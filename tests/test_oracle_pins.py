@@ -336,3 +336,16 @@ def test_bfgs_qp_solution_kkt():
     g = qp.H @ it.x + qp.c        # x >= 0: g >= 0 where x = 0, g = 0 where x > 0
     act = it.x < 1e-7
     assert np.all(g[act] >= -1e-6) and np.abs(g[~act]).max() <= 1e-6 * (1 + np.abs(qp.c).max())
+
+
+def test_bfgs_checker_operators_match_dense_form():
+    """The checker's matrix-free quasi-Newton operators against the dense H, A of the
+    (separately pinned) dense form."""
+    p = W.bfgs_qp(n=50, k=5, m_ub=7, m_lb=4, density=0.2, seed=12)
+    qp = ipm.from_bfgs(p)
+    ops = kkt_check.bfgs_ops(p)
+    rng = np.random.default_rng(0)
+    x, y = rng.normal(size=p["n"]), rng.normal(size=p["m"])
+    np.testing.assert_allclose(ops.Hx(x), qp.H @ x, rtol=1e-12, atol=1e-12 * np.abs(qp.H).max())
+    np.testing.assert_allclose(ops.Ax(x), qp.A @ x, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(ops.Aty(y), qp.A.T @ y, rtol=1e-12, atol=1e-13)

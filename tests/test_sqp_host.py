@@ -97,3 +97,21 @@ def test_sqp_bfgs_secant_and_reset():
         y_last = U[:, -1]
         s_last = np.linalg.lstsq(H, y_last, rcond=None)[0]
         np.testing.assert_allclose(H @ s_last, y_last, rtol=1e-8, atol=1e-10)
+
+
+def test_dose_objective_gradient_and_h0():
+    """The objective's gradient against central differences; H0 against the Gauss-Newton
+    diagonal written out densely."""
+    p = W.sqp_problem(n=25, density=0.2, seed=5)
+    obj, _ = _objective(p)
+    rng = np.random.default_rng(1)
+    x = rng.uniform(0.0, 1.5, size=p["n"])
+    f, g = obj.value_grad(x)
+    h = 1e-6
+    fd = np.array([(obj.value_grad(x + h * e)[0] - obj.value_grad(x - h * e)[0]) / (2 * h) for e in np.eye(p["n"])])
+    np.testing.assert_allclose(g, fd, rtol=1e-5, atol=1e-6 * (1 + np.abs(g).max()))
+    D = obj.D.toarray()
+    wv = np.zeros(D.shape[0])
+    wv[p["target"]] += p["w_target"]
+    wv[p["organ"]] += p["w_organ"]
+    np.testing.assert_allclose(obj.gauss_newton_diag(), 2.0 * (D ** 2).T @ wv + obj.eps, rtol=1e-12)
