@@ -1043,7 +1043,9 @@ cudaError_t launch_rhs(const Dev& d, const Geo& g, int precond, cudaStream_t st)
 template <int MODE, int G>
 __global__ void __launch_bounds__(256, 6) k_op_rows(Dev d) {
   if (MODE == 0 && d.sc->cg_done) return;
-  FOR_GROUP_ROWS(G, r, ok, d.nR) {
+  FOR_GROUP_ROWS(G, ri, ok, d.nR) {
+    // rows in windows ordered by length (rperm), so the groups of one warp run equal trips
+    const int64_t r = (ok && d.rperm) ? (int64_t)d.rperm[ri] : ri;
     const int64_t beg = ok ? d.R_ptr[r] : 0, end = ok ? d.R_ptr[r + 1] : 0;
     const double t = group_row_dot_u<G, 2>(beg, end, glane<G>(), d.R_idx, d.R_val, d.p);
     if (ok && glane<G>() == 0) {

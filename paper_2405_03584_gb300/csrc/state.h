@@ -26,6 +26,7 @@ struct Dev {
   int64_t nnzA;
   const int64_t* Hs_ptr; const int32_t* Hs_idx; const double* Hs_val;   // nullptr if none
   const int32_t* arow;         // m: row of R holding constraint k
+  const int32_t* rperm;        // nR: order of the rows in the PCG rows pass (nullptr: natural)
   // low-rank Hessian term U diag(uw) U^T (eq:bfgs_hessian): U is n x ucols, row-major
   int64_t ucols;               // columns in use (<= ucap); U's row stride
   int64_t ucap;                // columns allocated (per handle: U is part of the state)
