@@ -1051,6 +1051,7 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   dv.n = n; dv.m = m; dv.nR = q.nR; dv.nnzR = nnzR; dv.nnzHs = nnzHs; dv.nnzA = nnzAT;
   dv.g_rows = heuristic_group(q.nR ? (double)nnzR / (double)q.nR : 0.0);
   dv.g_cols = heuristic_group((double)nnzR / (double)n);
+  dv.g_at = heuristic_group((double)nnzAT / (double)n);
   if (h->opt.lanes_rows) dv.g_rows = h->opt.lanes_rows;
   if (h->opt.lanes_cols) dv.g_cols = h->opt.lanes_cols;
   dv.lp_stage = (h->opt.storage != IPM_STORAGE_F64 && h->opt.lp_stage) ? 1 : 0;

@@ -355,35 +355,58 @@ __global__ void __launch_bounds__(256, 4) k_cols_resid(Dev d, double* part) {
 //   gap = |pobj - dobj| / (1 + |pobj| + |dobj|),
 //   ||r||_mu = max(||r_s, r_l, r_u||, (1 + |pobj|) / N_c * max(||r_p|| / (1 + ||b||), ||r_d|| / (1 + ||c||))).
 __global__ void k_resid_final(Dev d, int gR, int gM, int gN, const double* part) {
-  __shared__ double sh[32];
+  // all 19 block partials reduced in one pass: per thread over its blocks, then per warp by
+  // shuffles, then across warps (fixed order); sums (op 0) and maxima (op 1)
+  constexpr int NQ = 19;
+  const int slot[NQ] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 28, 29, 30};
+  const int opq[NQ] = {0, 1, 1, 1, 0, 0, 1, 1, 1, 1, 0, 0, 0, 0, 0, 1, 1, 1, 1};
+  const int nbq[NQ] = {gR, gM, gM, gM, gM, gM, gN, gN, gN, gN, gN, gN, gN, gN, gN, gN, gM, gN, gN};
+  __shared__ double red[32][NQ];
+  __shared__ double res[NQ];
   const int K = kMaxRedBlocks;
-  auto tot = [&](int q, int nb, int op) -> double {
-    double acc = op == 0 ? 0.0 : -INFINITY;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-      double v = part[q * K + b];
-      acc = op == 0 ? acc + v : fmax(acc, v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    acc[q] = opq[q] == 0 ? 0.0 : -INFINITY;
+    for (int b = threadIdx.x; b < nbq[q]; b += blockDim.x) {
+      const double v = part[slot[q] * K + b];
+      acc[q] = opq[q] == 0 ? acc[q] + v : fmax(acc[q], v);
     }
-    return op == 0 ? block_reduce<0>(acc, sh) : block_reduce<1>(acc, sh);
-  };
-  const double xFx = tot(0, gR, 0);
-  const double rp_inf = fmax(0.0, tot(1, gM, 1));
-  const double viol_a = fmax(0.0, tot(2, gM, 1));
-  const double rs_inf = fmax(0.0, tot(3, gM, 1));
-  const double by = tot(4, gM, 0);
-  const double sy = tot(5, gM, 0);
-  const double rd_inf = fmax(0.0, tot(6, gN, 1));
-  const double hx_inf = fmax(0.0, tot(7, gN, 1));
-  const double aty_inf = fmax(0.0, tot(8, gN, 1));
-  const double rc_inf = fmax(0.0, tot(9, gN, 1));
-  const double xHsx = tot(10, gN, 0);
-  const double cx = tot(11, gN, 0);
-  const double lzl = tot(12, gN, 0);
-  const double uzu = tot(13, gN, 0);
-  const double tz = tot(14, gN, 0);
-  const double viol_b = fmax(0.0, tot(15, gN, 1));
-  const double ymax = d.m ? fmax(0.0, tot(28, gM, 1)) : 0.0;
-  const double cert = fmax(0.0, tot(29, gN, 1));
-  const double zmax = fmax(0.0, tot(30, gN, 1));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double w = __shfl_xor_sync(0xffffffffu, acc[q], o);
+      acc[q] = opq[q] == 0 ? acc[q] + w : fmax(acc[q], w);
+    }
+    if (lane == 0) red[warp][q] = acc[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < NQ) {
+    const int q = threadIdx.x;
+    double t = opq[q] == 0 ? 0.0 : -INFINITY;
+    for (int w = 0; w < nw; ++w) t = opq[q] == 0 ? t + red[w][q] : fmax(t, red[w][q]);
+    res[q] = t;
+  }
+  __syncthreads();
+  const double xFx = res[0];
+  const double rp_inf = fmax(0.0, res[1]);
+  const double viol_a = fmax(0.0, res[2]);
+  const double rs_inf = fmax(0.0, res[3]);
+  const double by = res[4];
+  const double sy = res[5];
+  const double rd_inf = fmax(0.0, res[6]);
+  const double hx_inf = fmax(0.0, res[7]);
+  const double aty_inf = fmax(0.0, res[8]);
+  const double rc_inf = fmax(0.0, res[9]);
+  const double xHsx = res[10];
+  const double cx = res[11];
+  const double lzl = res[12];
+  const double uzu = res[13];
+  const double tz = res[14];
+  const double viol_b = fmax(0.0, res[15]);
+  const double ymax = d.m ? fmax(0.0, res[16]) : 0.0;
+  const double cert = fmax(0.0, res[17]);
+  const double zmax = fmax(0.0, res[18]);
   if (threadIdx.x == 0) {
     Scal* sc = d.sc;
     const double xHx = xFx + xHsx + (d.ucols ? sc->lr_quad : 0.0);
@@ -424,7 +447,7 @@ cudaError_t launch_residual_summary(const Dev& d, const Geo& g, cudaStream_t st)
   if (d.m) k_cons_resid<<<g.eM, kBlock, 0, st>>>(d, part);
   launch_lr(d, d.x, 1, st);
   DISPATCH_G(d.g_cols, k_cols_resid<G><<<g.gNr, kBlock, 0, st>>>(d, part));
-  k_resid_final<<<1, 1024, 0, st>>>(d, g.gR, g.eM, g.gNr, part);
+  k_resid_final<<<1, 512, 0, st>>>(d, g.gR, g.eM, g.gNr, part);
   return cudaGetLastError();
 }
 
@@ -705,7 +728,7 @@ __global__ void k_jacobi(Dev d, double* out) {
 }
 
 cudaError_t launch_jacobi_full(const Dev& d, const Geo& g, double* out, cudaStream_t st) {
-  DISPATCH_G(d.g_cols, k_jacobi<false, G><<<g.gN, kBlock, 0, st>>>(d, out));
+  DISPATCH_G(d.g_at, k_jacobi<false, G><<<g.gN, kBlock, 0, st>>>(d, out));
   return cudaGetLastError();
 }
 
@@ -1030,9 +1053,9 @@ cudaError_t launch_rhs(const Dev& d, const Geo& g, int precond, cudaStream_t st)
   if (d.nR) cudaMemsetAsync(d.vR2, 0, sizeof(double) * d.nR, st);
   if (d.m) k_rhs_m<<<g.eM, kBlock, 0, st>>>(d);
   if (precond == PC_DENSE) {
-    DISPATCH_G(d.g_cols, k_rhs_n<G><<<g.gN, kBlock, 0, st>>>(d));
+    DISPATCH_G(d.g_at, k_rhs_n<G><<<g.gN, kBlock, 0, st>>>(d));
   } else {
-    DISPATCH_G(d.g_cols, k_rhs_jacobi<G><<<g.gNr, kBlock, 0, st>>>(d));
+    DISPATCH_G(d.g_at, k_rhs_jacobi<G><<<g.gNr, kBlock, 0, st>>>(d));
   }
   return cudaGetLastError();
 }

@@ -213,7 +213,9 @@ __global__ void k_stiff_op_u(Dev d) {
   }
 }
 
-// w_i = s_i^2 (w_R,i + thR_i) (q_i . p32)   (FP32 result; thR = theta on moderate rows)
+// w_i = s_i^2 (w_R,i + thR_i) (q_i . p32)   (FP32 result; thR = theta on moderate rows).
+// Rows in natural order: the length order of the FP64 rows pass made this L1-bound pass
+// slower (72 -> 90 us on the RT rows, BF16), the gathers of neighbouring rows sharing lines.
 template <int S, int G>
 __global__ void k_op_rows_lp(Dev d, int standalone) {
   if (!standalone && d.sc->cg_done) return;

@@ -17,6 +17,7 @@ struct Dev {
   int aug;                     // 1: PCG on the doubly augmented system (Section 4, eq:2x2_augmented)
   int64_t nnzR, nnzHs;
   int g_rows, g_cols;          // lanes per row of the kernels over R and over R^T (4, 8, 16, 32)
+  int g_at;                    // lanes per row of the kernels over A^T alone
   int sm_count;                // multiprocessors of the device (grid sizing)
   // problem data
   const int64_t* R_ptr; const int32_t* R_idx; const double* R_val;
