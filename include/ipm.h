@@ -193,16 +193,18 @@ typedef struct ipm_handle ipm_handle;
  * Allocates no device memory.  Errors: IPM_ERR_ARG (out == NULL or invalid options). */
 int ipm_create(const ipm_options* opt, ipm_handle** out);
 
-/* Loads the QP (1) (deep copy into solver-owned device memory) and builds the stored
- * transpose used by the matrix-free operator, the diagonal of H (computed once, as in
- * Section 4.1.2) and the workspace.  Replaces any earlier QP on the handle.
+/* Loads the QP (1) (deep copy into solver-owned device memory) and builds, on the device, the
+ * stored transposes R^T and A^T used by the matrix-free operator (rows ascending within each
+ * column, so every product is a deterministic gather), the diagonal of H (computed once, as
+ * in Section 4.1.2) and the workspace.  Replaces any earlier QP on the handle.
  * Errors: IPM_ERR_ARG (inconsistent sizes, index out of range, non-finite data, l >= u, both
  * or neither of a_rows/A given with m > 0), IPM_ERR_OOM, IPM_ERR_CUDA. */
 int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream);
 
 /* Runs Algorithm 1 on the device from the start point (IPM_COLD) or from the last iterate
  * (IPM_WARM: the previous solution, or one given by ipm_set_iterate).  Returns the solve
- * status (IPM_OK when rel KKT <= tol_kkt). */
+ * status: IPM_OK when rel KKT <= tol_kkt; IPM_MAX_ITER, IPM_INFEASIBLE_SUSPECTED,
+ * IPM_NUMERICAL or IPM_ERR_TIMEOUT otherwise (the iterate is kept either way). */
 int ipm_solve(ipm_handle* h, void* stream, int flags);
 
 /* Asynchronous form of ipm_solve: queues the whole solve (one CUDA graph launch) behind the
@@ -293,7 +295,9 @@ int ipm_residuals(ipm_handle* h, double* r_d, double* r_p, double* r_s, double* 
                   double* kkt, int mem, void* stream);
 
 /* q = (H + A^T Theta A + Sigma) p at the current iterate: one matrix-free operator apply of
- * the PCG (Section 4.1.1, the condensed counterpart of Listing 1's vec_mult_acc).  p, q: n. */
+ * the PCG (Section 4.1.1; the condensed counterpart of the operator of Listing 1).  p, q: n.
+ * With options.system = IPM_SYSTEM_AUGMENTED it applies that system's (1,1) block,
+ * H + Sigma + 2 A^T Theta A. */
 int ipm_apply_kkt(ipm_handle* h, const double* p, double* q, int mem, void* stream);
 
 /* Jacobi diagonal diag(H + A^T Theta A + Sigma) at the current iterate (Section 4.1.2). */
