@@ -17,10 +17,14 @@ single step.  Each function names the passage it follows.  Readings of points th
 leaves open (the sign of the upper-row residual, the norm in the mu test, the start point,
 tau, the stop rule) are stated where they are used.
 
+Two-sided rows l_A <= A x <= u_A (the paper's form before eq:2x2_reduced) enter through
+``two_sided``: the stack B = [A; -A] turns them into the one-sided rows above.
+
 Parity pins: the closed form x = -H^{-1} c (unconstrained), per-coordinate clipping
-(separable box QP), brute-force active-set enumeration (n <= 8), the full unreduced Newton
-system (eq:newton_system), the doubly augmented system (eq:2x2_augmented) and the
-complementarity / duality-gap identities; see tests/test_oracle_pins.py.
+(separable box QP, also with two-sided single-variable rows), brute-force active-set
+enumeration (n <= 8; three states per two-sided row), the full unreduced Newton system
+(eq:newton_system), the doubly augmented system (eq:2x2_augmented) and the complementarity /
+duality-gap identities; see tests/test_oracle_pins.py.
 """
 from __future__ import annotations
 
@@ -32,7 +36,7 @@ import scipy.linalg as sla
 __all__ = [
     "DenseQP", "Iterate", "from_dense", "from_rt", "residuals", "scaled_residual_norm",
     "condensed_system", "newton_direction", "doubly_augmented_direction", "step_lengths",
-    "start_point", "solve", "objective", "complementarity_mean",
+    "start_point", "solve", "objective", "complementarity_mean", "two_sided", "row_multipliers",
 ]
 
 
@@ -105,6 +109,30 @@ def from_bfgs(p: dict) -> DenseQP:
         A[rows, p["A_indices"]] = p["A_data"]
     return DenseQP(H, np.asarray(p["c"], float), A, np.asarray(p["b"], float),
                    np.asarray(p["l"], float), np.asarray(p["u"], float))
+
+
+def two_sided(H, c, A, bl, bu, l, u):
+    """One-sided form of two-sided rows bl <= A x <= bu (Section 4, before eq:2x2_reduced:
+    B = [A; -A] with the upper and lower row bounds).  Rows whose upper side is +inf drop out
+    of the first block, rows whose lower side is -inf out of the second.  Returns
+    (DenseQP, upper, lower): the original indices of the rows in each block."""
+    A = np.asarray(A, float)
+    bl, bu = np.asarray(bl, float), np.asarray(bu, float)
+    upper = np.flatnonzero(np.isfinite(bu))
+    lower = np.flatnonzero(np.isfinite(bl))
+    B = np.vstack([A[upper], -A[lower]]).reshape(-1, A.shape[1])
+    b = np.concatenate([bu[upper], -bl[lower]])
+    return DenseQP(np.asarray(H, float), np.asarray(c, float), B, b, np.asarray(l, float),
+                   np.asarray(u, float)), upper, lower
+
+
+def row_multipliers(y, upper, lower, m):
+    """Multiplier of each original two-sided row from the stacked ones: the upper row's minus
+    the lower row's (the row's own sign convention: > 0 at its upper side, < 0 at its lower)."""
+    out = np.zeros(m)
+    np.add.at(out, upper, y[:upper.shape[0]])
+    np.add.at(out, lower, -y[upper.shape[0]:])
+    return out
 
 
 def _tl(qp, x):

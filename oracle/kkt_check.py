@@ -16,6 +16,12 @@ the reading used for every parity claim) is the maximum of
 with pobj = 0.5 x^T H x + c^T x and the Lagrangian dual value
 dobj = -0.5 x^T H x - b^T y + l^T z_l - u^T z_u (y, z clipped at 0; z_l (z_u) counted only
 where l (u) is finite).
+
+Two-sided rows bl <= A x <= b (the paper's l_A <= A x <= u_A; either side may be infinite)
+carry one signed multiplier y per row: y_u = max(y, 0) belongs to the upper side, y_l =
+max(-y, 0) to the lower side, each counted only where its side is finite.  Then A^T y above
+is A^T (y_u - y_l), the primal part also measures max(bl - A x, 0), ||b||_inf runs over both
+sides' finite values and dobj has -b^T y_u + bl^T y_l in place of -b^T y.
 """
 from __future__ import annotations
 
@@ -27,9 +33,10 @@ __all__ = ["Operators", "dense_ops", "rt_ops", "bfgs_ops", "rel_kkt", "rt_conden
 class Operators:
     """H x, A x and A^T y for one QP, plus its vectors."""
 
-    def __init__(self, Hx, Ax, Aty, c, b, l, u):
+    def __init__(self, Hx, Ax, Aty, c, b, l, u, bl=None):
         self.Hx, self.Ax, self.Aty = Hx, Ax, Aty
         self.c, self.b, self.l, self.u = (np.asarray(v, float) for v in (c, b, l, u))
+        self.bl = None if bl is None else np.asarray(bl, float)
 
 
 def _csr_mv(indptr, indices, data, x, nrows):
@@ -47,7 +54,8 @@ def _csr_tmv(indptr, indices, data, y, ncols):
 
 def dense_ops(p: dict) -> Operators:
     H, A = np.asarray(p["H"], float), np.asarray(p["A"], float).reshape(-1, len(p["c"]))
-    return Operators(lambda x: H @ x, lambda x: A @ x, lambda y: A.T @ y, p["c"], p["b"], p["l"], p["u"])
+    return Operators(lambda x: H @ x, lambda x: A @ x, lambda y: A.T @ y, p["c"], p["b"], p["l"], p["u"],
+                     p.get("bl"))
 
 
 def rt_ops(p: dict) -> Operators:
@@ -68,7 +76,7 @@ def rt_ops(p: dict) -> Operators:
         np.add.at(full, ar, y)
         return _csr_tmv(ip, ix, dv, full, n)
 
-    return Operators(Hx, Ax, Aty, p["c"], p["b"], p["l"], p["u"])
+    return Operators(Hx, Ax, Aty, p["c"], p["b"], p["l"], p["u"], p.get("bl"))
 
 
 def bfgs_ops(p: dict) -> Operators:
@@ -92,13 +100,22 @@ def bfgs_ops(p: dict) -> Operators:
 def rel_kkt(ops: Operators, x, y, zl, zu, detail: bool = False):
     """Relative KKT residual (max of the primal, dual and gap parts, see module docstring)."""
     x = np.asarray(x, float)
-    y = np.maximum(np.asarray(y, float), 0.0)
+    y = np.asarray(y, float)
+    if ops.bl is None:                       # one-sided rows A x <= b
+        fb, fbl = np.ones(y.shape[0], bool), np.zeros(y.shape[0], bool)
+    else:
+        fb, fbl = np.isfinite(ops.b), np.isfinite(ops.bl)
+    bu = np.where(fb, ops.b, 0.0)
+    bl = np.where(fbl, ops.bl, 0.0) if ops.bl is not None else np.zeros(y.shape[0])
+    yu = np.where(fb, np.maximum(y, 0.0), 0.0)
+    yl = np.where(fbl, np.maximum(-y, 0.0), 0.0)
     fl, fu = np.isfinite(ops.l), np.isfinite(ops.u)
     zl = np.where(fl, np.maximum(np.asarray(zl, float), 0.0), 0.0)
     zu = np.where(fu, np.maximum(np.asarray(zu, float), 0.0), 0.0)
-    Hx, Ax, Aty = ops.Hx(x), ops.Ax(x), ops.Aty(y)
-    nb = np.max(np.abs(ops.b), initial=0.0)
-    viol = max(np.max(np.maximum(Ax - ops.b, 0.0), initial=0.0),
+    Hx, Ax, Aty = ops.Hx(x), ops.Ax(x), ops.Aty(yu - yl)
+    nb = max(np.max(np.abs(bu), initial=0.0), np.max(np.abs(bl), initial=0.0))
+    viol = max(np.max(np.where(fb, np.maximum(Ax - bu, 0.0), 0.0), initial=0.0),
+               np.max(np.where(fbl, np.maximum(bl - Ax, 0.0), 0.0), initial=0.0),
                np.max(np.where(fl, np.maximum(np.where(fl, ops.l, 0.0) - x, 0.0), 0.0), initial=0.0),
                np.max(np.where(fu, np.maximum(x - np.where(fu, ops.u, 0.0), 0.0), 0.0), initial=0.0))
     primal = viol / (1.0 + nb)
@@ -107,7 +124,7 @@ def rel_kkt(ops: Operators, x, y, zl, zu, detail: bool = False):
                                                          np.max(np.abs(Hx), initial=0.0),
                                                          np.max(np.abs(Aty), initial=0.0)))
     pobj = 0.5 * x @ Hx + ops.c @ x
-    dobj = -0.5 * x @ Hx - ops.b @ y + np.sum(np.where(fl, np.where(fl, ops.l, 0.0) * zl, 0.0)) \
+    dobj = -0.5 * x @ Hx - bu @ yu + bl @ yl + np.sum(np.where(fl, np.where(fl, ops.l, 0.0) * zl, 0.0)) \
         - np.sum(np.where(fu, np.where(fu, ops.u, 0.0) * zu, 0.0))
     gap = abs(pobj - dobj) / (1.0 + abs(pobj) + abs(dobj))
     val = float(max(primal, dual, gap))

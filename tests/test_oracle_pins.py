@@ -10,7 +10,7 @@ import pytest
 
 from oracle import ipm, kkt_check
 from paper_2405_03584_gb300 import workloads as W
-from tests._bruteforce import solve_bruteforce
+from tests._bruteforce import solve_bruteforce, solve_bruteforce_two_sided
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden", "tiny_qps.json")
 
@@ -349,3 +349,135 @@ def test_bfgs_checker_operators_match_dense_form():
     np.testing.assert_allclose(ops.Hx(x), qp.H @ x, rtol=1e-12, atol=1e-12 * np.abs(qp.H).max())
     np.testing.assert_allclose(ops.Ax(x), qp.A @ x, rtol=1e-12, atol=1e-13)
     np.testing.assert_allclose(ops.Aty(y), qp.A.T @ y, rtol=1e-12, atol=1e-13)
+
+
+# ---------------------------------------------------------------- two-sided rows
+
+def _two_sided_case(n, m, seed, inf_frac=0.25):
+    """Random two-sided rows around a feasible point: windows bl < A x_f < bu, with some
+    sides (never both of a row) at infinity."""
+    p = _rand_qp(n, m, seed, free_frac=0.2)
+    rng = np.random.default_rng(500 + seed)
+    xf = rng.uniform(-0.4, 0.4, size=n)
+    Ax = p["A"] @ xf
+    bu = Ax + rng.uniform(0.05, 0.6, size=m)
+    bl = Ax - rng.uniform(0.05, 0.6, size=m)
+    drop = rng.random(m) < inf_frac
+    side = rng.random(m) < 0.5
+    bu[drop & side] = np.inf
+    bl[drop & ~side] = -np.inf
+    p["bl"], p["b"] = bl, bu
+    return p
+
+
+def test_two_sided_single_variable_rows_closed_form():
+    """Diagonal H with rows a_k x_{j_k} (distinct j_k, both signs of a_k): every variable's
+    window is the intersection of its bounds and its row's [bl/a, bu/a] (flipped for a < 0),
+    so x_j = clip(-c_j / h_j, window) and, where the row side is the binding one, the row's
+    signed multiplier is -(h_j x_j + c_j) / a_k."""
+    rng = np.random.default_rng(77)
+    n, m = 30, 20
+    h = 10 ** rng.uniform(-1, 1, size=n)
+    c = rng.normal(size=n) * 3
+    l = np.full(n, -4.0)
+    u = np.full(n, 4.0)
+    cols = rng.permutation(n)[:m]
+    a = rng.uniform(0.5, 2.0, size=m) * np.where(rng.random(m) < 0.5, -1.0, 1.0)
+    A = np.zeros((m, n))
+    A[np.arange(m), cols] = a
+    bl = rng.uniform(-1.5, -0.2, size=m)
+    bu = rng.uniform(0.2, 1.5, size=m)
+    bl[:3] = -np.inf
+    bu[3:6] = np.inf
+    lo, hi = l.copy(), u.copy()
+    for k, j in enumerate(cols):
+        r1, r2 = bl[k] / a[k], bu[k] / a[k]
+        rlo, rhi = (r1, r2) if a[k] > 0 else (r2, r1)
+        lo[j] = max(lo[j], rlo)
+        hi[j] = min(hi[j], rhi)
+    x_star = np.clip(-c / h, lo, hi)
+    qp, up, lw = ipm.two_sided(np.diag(h), c, A, bl, bu, l, u)
+    it, info = ipm.solve(qp, tol=1e-12)
+    assert info.status == "optimal"
+    np.testing.assert_allclose(it.x, x_star, rtol=1e-8, atol=1e-9)
+    y = ipm.row_multipliers(it.y, up, lw, m)
+    for k, j in enumerate(cols):
+        g = h[j] * x_star[j] + c[j]
+        at_row = (x_star[j] == lo[j] and lo[j] > l[j]) or (x_star[j] == hi[j] and hi[j] < u[j])
+        want = -g / a[k] if at_row else 0.0
+        assert abs(y[k] - want) <= 1e-7 * (1 + abs(want)), (k, y[k], want)
+    p = dict(H=np.diag(h), c=c, A=A, b=bu, bl=bl, l=l, u=u)
+    assert kkt_check.rel_kkt(kkt_check.dense_ops(p), it.x, y, it.zl, it.zu) < 1e-11
+
+
+@pytest.mark.parametrize("n,m,seed", [(2, 2, 0), (3, 2, 1), (4, 3, 2), (5, 3, 3), (4, 4, 4)])
+def test_two_sided_bruteforce(n, m, seed):
+    """Three states per row (inactive, at bu, at bl) and per variable: the oracle on the
+    stacked rows [A; -A] reaches the enumerated optimum, its signed row multipliers match the
+    enumerated ones, and both points certify in the checker's two-sided mode."""
+    p = _two_sided_case(n, m, seed)
+    bf = solve_bruteforce_two_sided(p["H"], p["c"], p["A"], p["bl"], p["b"], p["l"], p["u"])
+    assert bf is not None
+    f, xb, yb, zlb, zub = bf
+    qp, up, lw = ipm.two_sided(p["H"], p["c"], p["A"], p["bl"], p["b"], p["l"], p["u"])
+    it, info = ipm.solve(qp, tol=1e-12)
+    assert info.status == "optimal"
+    np.testing.assert_allclose(it.x, xb, atol=1e-8)
+    y = ipm.row_multipliers(it.y, up, lw, m)
+    np.testing.assert_allclose(y, yb, atol=1e-6 * (1 + np.abs(yb).max()))
+    ops = kkt_check.dense_ops(p)
+    assert kkt_check.rel_kkt(ops, xb, yb, zlb, zub) < 1e-12
+    assert kkt_check.rel_kkt(ops, it.x, y, it.zl, it.zu) < 1e-11
+
+
+def test_two_sided_stack_matches_paper_newton_system():
+    """ipm.two_sided's stack, at the paper's variables of eq:newton_system (stacked as
+    y = (lam_u, lam_l), s = (s_u, s_l)), gives the step of the paper's own 5x5 system."""
+    rng = np.random.default_rng(8)
+    n, mA = 7, 4
+    p = _rand_qp(n, mA, 32, cond=1e2)
+    A, H, c = p["A"], p["H"], p["c"]
+    x = rng.normal(size=n) * 0.3
+    lA, uA = A @ x - rng.uniform(0.2, 1, mA), A @ x + rng.uniform(0.2, 1, mA)
+    sl, su = rng.uniform(0.1, 2, mA), rng.uniform(0.1, 2, mA)
+    ll, lu = rng.uniform(0.1, 2, mA), rng.uniform(0.1, 2, mA)
+    mu = 0.03
+    N = n + 4 * mA
+    K = np.zeros((N, N))
+    o = np.cumsum([0, n, mA, mA, mA, mA])
+    K[o[0]:o[1], o[0]:o[1]] = H
+    K[o[0]:o[1], o[1]:o[2]] = -A.T
+    K[o[0]:o[1], o[2]:o[3]] = A.T
+    K[o[1]:o[2], o[0]:o[1]] = A
+    K[o[1]:o[2], o[3]:o[4]] = -np.eye(mA)
+    K[o[2]:o[3], o[0]:o[1]] = -A
+    K[o[2]:o[3], o[4]:o[5]] = -np.eye(mA)
+    K[o[3]:o[4], o[1]:o[2]] = np.diag(sl)
+    K[o[3]:o[4], o[3]:o[4]] = np.diag(ll)
+    K[o[4]:o[5], o[2]:o[3]] = np.diag(su)
+    K[o[4]:o[5], o[4]:o[5]] = np.diag(lu)
+    rhs = np.concatenate([H @ x + c - A.T @ ll + A.T @ lu, A @ x - sl - lA, -A @ x - su + uA,
+                          ll * sl - mu, lu * su - mu])
+    sol = np.linalg.solve(K, -rhs)
+    qp, up, lw = ipm.two_sided(H, c, A, lA, uA, np.full(n, -np.inf), np.full(n, np.inf))
+    assert list(up) == list(range(mA)) and list(lw) == list(range(mA))
+    it = ipm.Iterate(x, np.concatenate([su, sl]), np.concatenate([lu, ll]), np.zeros(n), np.zeros(n))
+    d = ipm.newton_direction(qp, it, mu)
+    np.testing.assert_allclose(d.x, sol[o[0]:o[1]], rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(d.y, np.concatenate([sol[o[2]:o[3]], sol[o[1]:o[2]]]), rtol=1e-10, atol=1e-12)
+
+
+def test_checker_two_sided_catches_wrong_sign_and_lower_violation():
+    """The checker's two-sided mode: the enumerated KKT point scores ~0, the same point with
+    its row multipliers negated fails the dual part, and a point below a finite lower side
+    fails the primal part (planted mistakes on the CPU)."""
+    p = _two_sided_case(4, 3, 11, inf_frac=0.0)
+    f, xb, yb, zlb, zub = solve_bruteforce_two_sided(p["H"], p["c"], p["A"], p["bl"], p["b"], p["l"], p["u"])
+    ops = kkt_check.dense_ops(p)
+    assert kkt_check.rel_kkt(ops, xb, yb, zlb, zub) < 1e-12
+    assert np.abs(yb).max() > 1e-3, "the case needs an active row"
+    assert kkt_check.rel_kkt(ops, xb, -yb, zlb, zub) > 1e-4
+    k = int(np.argmax(np.abs(p["A"]).sum(axis=1)))
+    x_bad = xb - p["A"][k] * ((p["A"][k] @ xb - p["bl"][k]) + 0.5) / (p["A"][k] @ p["A"][k])
+    val, parts = kkt_check.rel_kkt(ops, x_bad, yb, zlb, zub, detail=True)
+    assert parts["primal"] >= 0.5 / (1 + max(np.abs(p["b"]).max(), np.abs(p["bl"]).max())) - 1e-12
