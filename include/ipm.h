@@ -88,8 +88,8 @@ typedef struct ipm_options {
   double cg_eta_max;     /* PCG relative tolerance eta = clamp(cg_eta_factor * relKKT, ...)    */
   double cg_eta_min;     /*   ... between cg_eta_min (1e-10) and cg_eta_max (1e-2)            */
   double cg_eta_factor;  /*   (0.3)                                                            */
-  int precond;           /* enum ipm_precond (IPM_PRECOND_AUTO: DENSE if n <= 1024, else       */
-                         /* JACOBI_LR)                                                         */
+  int precond;           /* enum ipm_precond (IPM_PRECOND_AUTO: DENSE if n <= 1024 and storage */
+                         /* is F64, else JACOBI_LR); DENSE needs storage F64 (IPM_ERR_ARG)     */
   double stiff_gamma;    /* JACOBI_LR threshold (1.0)                                          */
   int stiff_max;         /* JACOBI_LR: at most this many stiff rows (256, <= 1024)             */
   int dense_max_n;       /* DENSE allowed up to this n (2048, the maximum)                      */
@@ -130,7 +130,16 @@ void ipm_default_options(ipm_options* opt);
 /* The QP (1).  H = diag(h0) + H_dense + F^T diag(f_w) F + U diag(u_w) U^T, each term optional
  * (the last is the quasi-Newton Hessian of Section 3.3, eq:bfgs_hessian, applied matrix-free).
  * Constraint rows come either from F (a_rows: row indices into F, the dose-matrix case where
- * A is a subset of D's rows) or from a CSR matrix A; not both.  m = 0 is allowed (bounds only). */
+ * A is a subset of D's rows) or from a CSR matrix A; not both.  m = 0 is allowed (bounds only).
+ *
+ * Two-sided rows bl <= A x <= b (the paper's l_A <= A x <= u_A, Section 4 before
+ * eq:2x2_reduced) are given by bl.  The solver stores them as the paper's stack B = [A; -A]:
+ * the "stored rows" are first A_k x <= b_k for every k with finite b_k, in order, then
+ * -A_k x <= -bl_k for every k with finite bl_k, in order (a_rows rows with a lower side get a
+ * negated copy in the matrix store).  ipm_get_xyz reports per caller row k the signed
+ * multiplier y_k = y_upper - y_lower and the slack b_k - A_k x (A_k x - bl_k where b_k is
+ * +inf; +inf for a row with neither side); the step-level entry points work on the stored
+ * rows, whose count ipm_get_sizes gives.  Without bl the stored rows are the caller's rows. */
 typedef struct ipm_qp {
   int64_t n;                 /* variables, >= 1                                            */
   int64_t m;                 /* linear inequality rows, >= 0                               */
@@ -154,6 +163,8 @@ typedef struct ipm_qp {
                              /* (eq:bfgs_hessian; 0 = none, at most 65536)                  */
   const double* U;           /* n x u_cols, row-major: variable j's u_cols values adjacent */
   const double* u_w;         /* u_cols weights; may be negative (BFGS), H must stay PSD    */
+  const double* bl;          /* m, lower sides of the rows (-inf = none); NULL = one-sided */
+                             /* rows A x <= b.  With bl, b may hold +inf; bl < b           */
 } ipm_qp;
 
 typedef struct ipm_info {
@@ -197,9 +208,13 @@ int ipm_create(const ipm_options* opt, ipm_handle** out);
  * stored transposes R^T and A^T used by the matrix-free operator (rows ascending within each
  * column, so every product is a deterministic gather), the diagonal of H (computed once, as
  * in Section 4.1.2) and the workspace.  Replaces any earlier QP on the handle.
- * Errors: IPM_ERR_ARG (inconsistent sizes, index out of range, non-finite data, l >= u, both
- * or neither of a_rows/A given with m > 0), IPM_ERR_OOM, IPM_ERR_CUDA. */
+ * Errors: IPM_ERR_ARG (inconsistent sizes, index out of range, non-finite data, l >= u,
+ * bl >= b, both or neither of a_rows/A given with m > 0), IPM_ERR_OOM, IPM_ERR_CUDA. */
 int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream);
+
+/* Sizes of the loaded QP: n, the caller's rows m and the stored rows m_rows (equal to m
+ * unless bl was given; see ipm_qp).  Any output may be NULL.  Errors: IPM_ERR_STATE (no QP). */
+int ipm_get_sizes(const ipm_handle* h, int64_t* n, int64_t* m, int64_t* m_rows);
 
 /* Runs Algorithm 1 on the device from the start point (IPM_COLD) or from the last iterate
  * (IPM_WARM: the previous solution, or one given by ipm_set_iterate).  Returns the solve
@@ -232,7 +247,8 @@ int ipm_batch_solve(ipm_batch* b, void* stream, int* statuses);
 int ipm_batch_destroy(ipm_batch* b);
 
 /* Copies the current iterate to caller memory (any pointer may be NULL to skip it):
- * x, z_l, z_u (n), y, s (m); fills *info if non-NULL. */
+ * x, z_l, z_u (n), y, s (m: the caller's rows; for two-sided rows the signed multiplier and
+ * slack described at ipm_qp); fills *info if non-NULL. */
 int ipm_get_xyz(ipm_handle* h, double* x, double* y, double* z_l, double* z_u, double* s,
                 ipm_info* info, int mem, void* stream);
 
@@ -282,7 +298,9 @@ const char* ipm_last_error(const ipm_handle* h);
 /* ---- Step-level entry points: one step of Algorithm 1 each, on the current iterate ---- */
 
 /* Sets the iterate (x, s, y, z_l, z_u) and mu; used for warm starts and to evaluate single
- * steps.  x must lie strictly inside finite bounds; s, y, z_l, z_u > 0 where they apply. */
+ * steps.  x must lie strictly inside finite bounds; s, y, z_l, z_u > 0 where they apply.
+ * Here and in the step-level calls below, s, y, r_p, r_s, ds and dy have one value per
+ * stored row (ipm_get_sizes' m_rows). */
 int ipm_set_iterate(ipm_handle* h, const double* x, const double* s, const double* y,
                     const double* z_l, const double* z_u, double mu, int mem, void* stream);
 

@@ -101,7 +101,11 @@ struct ipm_handle {
   double cnorm = 0, bnorm = 0;
   int ncomp = 0;
   int64_t sc_cap = 0;
-  bool f_acsr = false;              // constraint rows appended to R as an explicit CSR block
+  int64_t fr = 0;                   // rows of the factor F (the first rows of R)
+  // two-sided rows (ipm_qp.bl): the caller's row of every stored row, upper sides first
+  // (stored rows [0, rows_up)), then lower sides; empty when the stored rows are the caller's
+  int64_t m_user = 0, rows_up = 0;
+  std::vector<int32_t> row_of;
   std::vector<double> trace;        // IPM_TRACE_COLS doubles per IPM iteration of the last solve
   double* htrace = nullptr;         // pinned: trace rows copied back after a solve
   int trace_cap = 0;
@@ -320,6 +324,9 @@ int validate_options(const ipm_options& o) {
   if (o.system == IPM_SYSTEM_AUGMENTED &&
       (o.storage != IPM_STORAGE_F64 || (o.precond != IPM_PRECOND_JACOBI && o.precond != IPM_PRECOND_AUTO)))
     return IPM_ERR_ARG;   // the doubly augmented system runs FP64 with the Jacobi preconditioner
+  // the dense factor is an FP64 preconditioner for the FP64 operator: with a reduced-precision
+  // operator the refinement's inner PCG under it stalled near convergence (RT n = 900, FP8)
+  if (o.precond == IPM_PRECOND_DENSE && o.storage != IPM_STORAGE_F64) return IPM_ERR_ARG;
   auto lanes_ok = [](int g) { return g == 0 || g == 4 || g == 8 || g == 16 || g == 32; };
   if (!lanes_ok(o.lanes_rows) || !lanes_ok(o.lanes_cols)) return IPM_ERR_ARG;
   return IPM_OK;
@@ -782,7 +789,7 @@ int ipm_update_costs(ipm_handle* h, const double* f_w, const double* c, int mem,
   if (h->pending) return fail(h, IPM_ERR_STATE, "a solve is in flight on this handle");
   int rc;
   const Dev& d = h->d;
-  const int64_t fr = h->d.nR - (h->f_acsr ? h->d.m : 0);
+  const int64_t fr = h->fr;
   std::vector<double> hw, hc;
   if (f_w && (rc = fetch(h, f_w, fr, mem, hw))) return rc;
   if (c && (rc = fetch(h, c, d.n, mem, hc))) return rc;
@@ -855,18 +862,19 @@ int ipm_destroy(ipm_handle* h) {
   return IPM_OK;
 }
 
-int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
-  if (!h || !qp) return IPM_ERR_ARG;
-  if (h->pending) return fail(h, IPM_ERR_STATE, "a solve is in flight on this handle");
-  h->err.clear();
+// Loads a one-sided QP whose m rows are the m_ar rows of F listed in a_rows followed by the
+// m - m_ar rows of the CSR matrix A (either part may be empty); qp->bl is ignored.
+static int load_qp(ipm_handle* h, const ipm_qp* qp, int64_t m_ar, void* stream) {
   const int64_t n = qp->n, m = qp->m, fr = qp->f_rows;
   const int mem = qp->mem;
   if (n < 1 || m < 0 || fr < 0 || (mem != IPM_MEM_HOST && mem != IPM_MEM_DEVICE))
     return fail(h, IPM_ERR_ARG, "bad sizes or memory space");
   if (n > INT32_MAX || fr + m > INT32_MAX) return fail(h, IPM_ERR_ARG, "sizes exceed int32 indexing");
-  const bool use_arows = qp->a_rows != nullptr;
-  const bool use_acsr = qp->A_indptr != nullptr;
-  if (m > 0 && use_arows == use_acsr) return fail(h, IPM_ERR_ARG, "give exactly one of a_rows or A (CSR)");
+  const int64_t m_c = m - m_ar;
+  const bool use_arows = m_ar > 0;
+  const bool use_acsr = m_c > 0;
+  if (m_ar < 0 || m_c < 0 || (use_arows && !qp->a_rows) || (use_acsr && !qp->A_indptr))
+    return fail(h, IPM_ERR_ARG, "missing constraint rows");
   if (use_arows && fr == 0) return fail(h, IPM_ERR_ARG, "a_rows needs a factor F");
   int rc;
   HostQP q;
@@ -910,30 +918,29 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
     if ((rc = fetch(h, qp->f_w, fr, mem, fw))) return rc;
     for (double w : fw) if (!std::isfinite(w) || w < 0) return fail(h, IPM_ERR_ARG, "f_w must be finite and >= 0");
   }
-  if (m && use_acsr) {
-    if ((rc = fetch(h, qp->A_indptr, m + 1, mem, Ap))) return rc;
+  if (use_acsr) {
+    if ((rc = fetch(h, qp->A_indptr, m_c + 1, mem, Ap))) return rc;
     if (Ap[0] != 0) return fail(h, IPM_ERR_ARG, "A_indptr[0] != 0");
-    for (int64_t r = 0; r < m; ++r) if (Ap[r + 1] < Ap[r]) return fail(h, IPM_ERR_ARG, "A_indptr not monotone");
+    for (int64_t r = 0; r < m_c; ++r) if (Ap[r + 1] < Ap[r]) return fail(h, IPM_ERR_ARG, "A_indptr not monotone");
   }
-  if (m && use_arows) {
-    if ((rc = fetch(h, qp->a_rows, m, mem, arows_in))) return rc;
+  if (use_arows) {
+    if ((rc = fetch(h, qp->a_rows, m_ar, mem, arows_in))) return rc;
     std::vector<int32_t> srt(arows_in);
     std::sort(srt.begin(), srt.end());
-    for (int64_t k = 0; k < m; ++k) {
+    for (int64_t k = 0; k < m_ar; ++k) {
       if (srt[k] < 0 || srt[k] >= fr) return fail(h, IPM_ERR_ARG, "a_rows index out of range");
       if (k && srt[k] == srt[k - 1]) return fail(h, IPM_ERR_ARG, "a_rows has duplicates");
     }
   }
-  q.nR = fr + (use_acsr ? m : 0);
-  const int64_t nnzF = fr ? Fp[fr] : 0, nnzA = (m && use_acsr) ? Ap[m] : 0;
+  q.nR = fr + m_c;
+  const int64_t nnzF = fr ? Fp[fr] : 0, nnzA = use_acsr ? Ap[m_c] : 0;
   q.Rp.resize(q.nR + 1);
   q.wR.assign(q.nR, 0.0);
   for (int64_t r = 0; r <= fr; ++r) q.Rp[r] = fr ? Fp[r] : 0;
   for (int64_t r = 0; r < fr; ++r) q.wR[r] = fw[r];
-  if (use_acsr)
-    for (int64_t k = 1; k <= m; ++k) q.Rp[fr + k] = nnzF + Ap[k];
+  for (int64_t k = 1; k <= m_c; ++k) q.Rp[fr + k] = nnzF + Ap[k];
   q.arow.resize(m);
-  for (int64_t k = 0; k < m; ++k) q.arow[k] = use_arows ? arows_in[k] : (int32_t)(fr + k);
+  for (int64_t k = 0; k < m; ++k) q.arow[k] = k < m_ar ? arows_in[k] : (int32_t)(fr + (k - m_ar));
   const int64_t nnzR = nnzF + nnzA;
   // entries of A^T: the constraint rows' lengths
   int64_t nnzAT = 0;
@@ -1022,7 +1029,7 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   int stiff_cap = 1;
   int64_t sc_cap = 1;
   stiff_caps(h->opt, m, store->sc_prefix, &stiff_cap, &sc_cap);
-  const bool dense = h->opt.dense_max_n > 0 && n <= h->opt.dense_max_n &&
+  const bool dense = h->opt.dense_max_n > 0 && n <= h->opt.dense_max_n && h->opt.storage == IPM_STORAGE_F64 &&
                      (h->opt.precond == IPM_PRECOND_DENSE || h->opt.precond == IPM_PRECOND_AUTO);
   // allocate
   CUDA_TRY(h, cudaSetDevice(h->device));
@@ -1062,7 +1069,7 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   h->g = make_geo(dv);
   if ((rc = alloc_trace(h))) return rc;
   h->cnorm = cn; h->bnorm = bn; h->ncomp = ncomp; h->sc_cap = sc_cap;
-  h->f_acsr = use_acsr;
+  h->fr = fr;
   if ((rc = enter(h, stream))) return rc;
   auto up = [&](const void* dst, const void* src, size_t nbytes) -> int {
     if (nbytes == 0) return IPM_OK;
@@ -1162,6 +1169,156 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   return leave(h, stream);
 }
 
+// Two-sided rows bl <= A x <= b are loaded as the paper's stack B = [A; -A] (Section 4,
+// before eq:2x2_reduced): the upper sides A_k x <= b_k (finite b_k), then the lower sides
+// -A_k x <= -bl_k (finite bl_k).  Rows of F named by a_rows keep their fused form for the
+// upper side; a lower side becomes a negated copy of its row in the explicit CSR block.
+int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
+  if (!h || !qp) return IPM_ERR_ARG;
+  if (h->pending) return fail(h, IPM_ERR_STATE, "a solve is in flight on this handle");
+  h->err.clear();
+  const int64_t m = qp->m, fr = qp->f_rows;
+  const int mem = qp->mem;
+  if (m < 0 || fr < 0 || (mem != IPM_MEM_HOST && mem != IPM_MEM_DEVICE))
+    return fail(h, IPM_ERR_ARG, "bad sizes or memory space");
+  const bool use_arows = qp->a_rows != nullptr;
+  if (m > 0 && use_arows == (qp->A_indptr != nullptr)) return fail(h, IPM_ERR_ARG, "give exactly one of a_rows or A (CSR)");
+  int rc;
+  if (!qp->bl || m == 0) {
+    if ((rc = load_qp(h, qp, use_arows ? m : 0, stream))) return rc;
+    h->m_user = m;
+    h->rows_up = m;
+    h->row_of.clear();
+    return IPM_OK;
+  }
+  std::vector<double> b, bl;
+  if ((rc = fetch(h, qp->b, m, mem, b)) || (rc = fetch(h, qp->bl, m, mem, bl))) return rc;
+  std::vector<int32_t> row_of;
+  for (int64_t k = 0; k < m; ++k) {
+    if (std::isnan(b[k]) || std::isnan(bl[k]) || b[k] == -INFINITY || bl[k] == INFINITY)
+      return fail(h, IPM_ERR_ARG, "b or bl is not a valid row bound");
+    // an equality row (bl = b) would drive both sides' slacks to zero together: refused,
+    // like l = u for a variable
+    if (!(bl[k] < b[k])) return fail(h, IPM_ERR_ARG, "bl >= b");
+    if (std::isfinite(b[k])) row_of.push_back((int32_t)k);
+  }
+  const int64_t up = (int64_t)row_of.size();
+  for (int64_t k = 0; k < m; ++k)
+    if (std::isfinite(bl[k])) row_of.push_back((int32_t)k);
+  const int64_t mr = (int64_t)row_of.size();
+  if (fr + mr > INT32_MAX) return fail(h, IPM_ERR_ARG, "sizes exceed int32 indexing");
+  std::vector<double> bs(mr);
+  for (int64_t r = 0; r < mr; ++r) bs[r] = r < up ? b[row_of[r]] : -bl[row_of[r]];
+  // host view of the source rows: F (a_rows) or the caller's A
+  const int64_t srows = use_arows ? fr : m;
+  std::vector<int64_t> sp;
+  std::vector<int32_t> ar, si_h;
+  std::vector<double> sv_h;
+  if ((rc = fetch(h, use_arows ? qp->F_indptr : qp->A_indptr, srows + 1, mem, sp))) return rc;
+  if (sp[0] != 0) return fail(h, IPM_ERR_ARG, "indptr[0] != 0");
+  for (int64_t r = 0; r < srows; ++r) if (sp[r + 1] < sp[r]) return fail(h, IPM_ERR_ARG, "indptr not monotone");
+  const int32_t* s_idx = use_arows ? qp->F_indices : qp->A_indices;
+  const double* s_val = use_arows ? qp->F_data : qp->A_data;
+  if (sp[srows] && (!s_idx || !s_val)) return fail(h, IPM_ERR_ARG, "missing matrix arrays");
+  const bool need_entries = use_arows ? mr > up : mr > 0;     // rows copied into the CSR block
+  if (mem == IPM_MEM_DEVICE && sp[srows] && need_entries) {
+    si_h.resize(sp[srows]);
+    sv_h.resize(sp[srows]);
+    if ((rc = fetch_into(h, s_idx, sp[srows], mem, si_h.data())) || (rc = fetch_into(h, s_val, sp[srows], mem, sv_h.data())))
+      return rc;
+    s_idx = si_h.data();
+    s_val = sv_h.data();
+  }
+  if (use_arows) {
+    if ((rc = fetch(h, qp->a_rows, m, mem, ar))) return rc;
+    for (int32_t r : ar) if (r < 0 || r >= fr) return fail(h, IPM_ERR_ARG, "a_rows index out of range");
+  }
+  // stored rows: a_rows of the upper sides, then the CSR block (negated rows for lower sides)
+  std::vector<int32_t> ar_up;
+  std::vector<int64_t> Cp(1, 0);
+  int64_t cnnz = 0;
+  for (int64_t r = 0; r < mr; ++r) {
+    const int64_t k = row_of[r];
+    if (use_arows && r < up) continue;
+    const int64_t src = use_arows ? ar[k] : k;
+    cnnz += sp[src + 1] - sp[src];
+  }
+  std::vector<int32_t> Ci((size_t)cnnz);
+  std::vector<double> Cv((size_t)cnnz);
+  for (int64_t r = 0, o = 0; r < mr; ++r) {
+    const int64_t k = row_of[r];
+    if (use_arows && r < up) {
+      ar_up.push_back(ar[k]);
+      continue;
+    }
+    const int64_t src = use_arows ? ar[k] : k;
+    const double sign = r < up ? 1.0 : -1.0;
+    for (int64_t e = sp[src]; e < sp[src + 1]; ++e, ++o) {
+      Ci[o] = s_idx[e];
+      Cv[o] = sign * s_val[e];
+    }
+    Cp.push_back(o);
+  }
+  const int64_t m_ar = (int64_t)ar_up.size(), mc = mr - m_ar;
+  ipm_qp q2 = *qp;
+  q2.m = mr;
+  q2.bl = nullptr;
+  q2.b = mr ? bs.data() : nullptr;
+  q2.a_rows = m_ar ? ar_up.data() : nullptr;
+  q2.A_indptr = mc ? Cp.data() : nullptr;
+  q2.A_indices = cnnz ? Ci.data() : nullptr;
+  q2.A_data = cnnz ? Cv.data() : nullptr;
+  void* tmp = nullptr;
+  if (mem == IPM_MEM_DEVICE) {
+    // the stacked arrays join the caller's device arrays: one temporary device buffer
+    const size_t ob = 0, oa = ob + 8 * (size_t)mr, op = oa + ((4 * (size_t)m_ar + 7) & ~(size_t)7),
+                 oi = op + 8 * Cp.size(), ov = oi + ((4 * (size_t)cnnz + 7) & ~(size_t)7), tot = ov + 8 * (size_t)cnnz;
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    if ((rc = dev_alloc(h, &tmp, tot + 8, "stacked rows"))) return rc;
+    char* t = static_cast<char*>(tmp);
+    const cudaError_t e = [&]() {
+      cudaError_t r = cudaSuccess;
+      if (mr && r == cudaSuccess) r = cudaMemcpy(t + ob, bs.data(), 8 * (size_t)mr, cudaMemcpyHostToDevice);
+      if (m_ar && r == cudaSuccess) r = cudaMemcpy(t + oa, ar_up.data(), 4 * (size_t)m_ar, cudaMemcpyHostToDevice);
+      if (mc && r == cudaSuccess) r = cudaMemcpy(t + op, Cp.data(), 8 * Cp.size(), cudaMemcpyHostToDevice);
+      if (cnnz && r == cudaSuccess) r = cudaMemcpy(t + oi, Ci.data(), 4 * (size_t)cnnz, cudaMemcpyHostToDevice);
+      if (cnnz && r == cudaSuccess) r = cudaMemcpy(t + ov, Cv.data(), 8 * (size_t)cnnz, cudaMemcpyHostToDevice);
+      return r;
+    }();
+    if (e != cudaSuccess) {
+      cudaFree(tmp);
+      return fail(h, IPM_ERR_CUDA, std::string("stacked rows upload: ") + cudaGetErrorString(e));
+    }
+    if (mr) q2.b = reinterpret_cast<const double*>(t + ob);
+    if (m_ar) q2.a_rows = reinterpret_cast<const int32_t*>(t + oa);
+    if (mc) q2.A_indptr = reinterpret_cast<const int64_t*>(t + op);
+    if (cnnz) {
+      q2.A_indices = reinterpret_cast<const int32_t*>(t + oi);
+      q2.A_data = reinterpret_cast<const double*>(t + ov);
+    }
+  }
+  rc = load_qp(h, &q2, m_ar, stream);
+  if (tmp) {
+    cudaStreamSynchronize(h->st);
+    cudaFree(tmp);
+  }
+  if (rc) return rc;
+  h->m_user = m;
+  h->rows_up = up;
+  if (up == m && mr == m) row_of.clear();      // one-sided after all: the caller's rows
+  h->row_of = std::move(row_of);
+  return IPM_OK;
+}
+
+int ipm_get_sizes(const ipm_handle* h, int64_t* n, int64_t* m, int64_t* m_rows) {
+  if (!h) return IPM_ERR_ARG;
+  if (!h->loaded) return IPM_ERR_STATE;
+  if (n) *n = h->d.n;
+  if (m) *m = h->m_user;
+  if (m_rows) *m_rows = h->d.m;
+  return IPM_OK;
+}
+
 int ipm_share_qp(ipm_handle* h, ipm_handle* src, void* stream) {
   if (!h || !src || h == src) return IPM_ERR_ARG;
   if (h->pending) return fail(h, IPM_ERR_STATE, "a solve is in flight on this handle");
@@ -1175,7 +1332,7 @@ int ipm_share_qp(ipm_handle* h, ipm_handle* src, void* stream) {
   int stiff_cap = 1;
   int64_t sc_cap = 1;
   stiff_caps(h->opt, m, src->mat->sc_prefix, &stiff_cap, &sc_cap);
-  const bool use_dense = h->opt.dense_max_n > 0 && n <= h->opt.dense_max_n &&
+  const bool use_dense = h->opt.dense_max_n > 0 && n <= h->opt.dense_max_n && h->opt.storage == IPM_STORAGE_F64 &&
                          (h->opt.precond == IPM_PRECOND_DENSE || h->opt.precond == IPM_PRECOND_AUTO);
   CUDA_TRY(h, cudaSetDevice(h->device));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
@@ -1202,7 +1359,10 @@ int ipm_share_qp(ipm_handle* h, ipm_handle* src, void* stream) {
   h->g = make_geo(dv);
   if ((rc = alloc_trace(h))) return rc;
   h->cnorm = src->cnorm; h->bnorm = src->bnorm; h->ncomp = src->ncomp; h->sc_cap = sc_cap;
-  h->f_acsr = src->f_acsr;
+  h->fr = src->fr;
+  h->m_user = src->m_user;
+  h->rows_up = src->rows_up;
+  h->row_of = src->row_of;
   // the source's problem vectors, ordered after its own stream and the caller's
   CUDA_TRY(h, cudaEventRecord(src->ev, src->st));
   CUDA_TRY(h, cudaStreamWaitEvent(h->st, src->ev, 0));
@@ -1420,10 +1580,34 @@ int ipm_get_xyz(ipm_handle* h, double* x, double* y, double* zl, double* zu, dou
   if ((rc = enter(h, stream))) return rc;
   const Dev& d = h->d;
   if ((rc = copy_out(h, x, d.x, d.n, mem))) return rc;
-  if ((rc = copy_out(h, y, d.y, d.m, mem))) return rc;
   if ((rc = copy_out(h, zl, d.zl, d.n, mem))) return rc;
   if ((rc = copy_out(h, zu, d.zu, d.n, mem))) return rc;
-  if ((rc = copy_out(h, s, d.s, d.m, mem))) return rc;
+  if (h->row_of.empty()) {
+    if ((rc = copy_out(h, y, d.y, d.m, mem))) return rc;
+    if ((rc = copy_out(h, s, d.s, d.m, mem))) return rc;
+  } else if (y || s) {
+    // stored rows -> caller rows: y_k = y_upper - y_lower; s_k = the upper slack, else the lower
+    const int64_t mr = d.m, mu = h->m_user;
+    std::vector<double> yi(mr), si(mr), yo(mu, 0.0), so(mu, INFINITY);
+    if (mr) {
+      CUDA_TRY(h, cudaMemcpyAsync(yi.data(), d.y, 8 * (size_t)mr, cudaMemcpyDeviceToHost, h->st));
+      CUDA_TRY(h, cudaMemcpyAsync(si.data(), d.s, 8 * (size_t)mr, cudaMemcpyDeviceToHost, h->st));
+      CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    }
+    for (int64_t r = 0; r < mr; ++r) {
+      const int32_t k = h->row_of[r];
+      if (r < h->rows_up) {
+        yo[k] += yi[r];
+        so[k] = si[r];
+      } else {
+        yo[k] -= yi[r];
+        if (so[k] == INFINITY) so[k] = si[r];
+      }
+    }
+    if (y && mu) CUDA_TRY(h, cudaMemcpyAsync(y, yo.data(), 8 * (size_t)mu, cudaMemcpyDefault, h->st));
+    if (s && mu) CUDA_TRY(h, cudaMemcpyAsync(s, so.data(), 8 * (size_t)mu, cudaMemcpyDefault, h->st));
+    CUDA_TRY(h, cudaStreamSynchronize(h->st));   // yo, so go out of scope
+  }
   if (mem == IPM_MEM_HOST) CUDA_TRY(h, cudaStreamSynchronize(h->st));
   if (info) *info = h->info;
   return leave(h, stream);

@@ -31,7 +31,7 @@ EXPORTS = ["ipm_default_options", "ipm_create", "ipm_set_qp", "ipm_solve", "ipm_
            "ipm_precond_diag", "ipm_newton_direction", "ipm_step_lengths", "ipm_profile_operator",
            "ipm_get_trace", "ipm_apply_operator_static", "ipm_solve_async", "ipm_solve_wait", "ipm_solve_query",
            "ipm_batch_create", "ipm_batch_solve", "ipm_batch_destroy", "ipm_update_costs", "ipm_share_qp",
-           "ipm_device_bytes", "ipm_set_lowrank", "ipm_abi_sizes"]
+           "ipm_device_bytes", "ipm_set_lowrank", "ipm_abi_sizes", "ipm_get_sizes"]
 TRACE_COLS = ("iter", "mu", "rel_kkt", "primal", "dual", "gap", "alpha_p", "alpha_d", "pcg_iters", "pcg_converged",
               "stiff_rows", "pcg_rel_residual", "eta", "refine_passes")
 
@@ -53,7 +53,7 @@ class QP(C.Structure):
                 ("h0", C.c_void_p), ("H_dense", C.c_void_p), ("f_rows", C.c_int64),
                 ("F_indptr", C.c_void_p), ("F_indices", C.c_void_p), ("F_data", C.c_void_p), ("f_w", C.c_void_p),
                 ("a_rows", C.c_void_p), ("A_indptr", C.c_void_p), ("A_indices", C.c_void_p), ("A_data", C.c_void_p),
-                ("u_cols", C.c_int64), ("U", C.c_void_p), ("u_w", C.c_void_p)]
+                ("u_cols", C.c_int64), ("U", C.c_void_p), ("u_w", C.c_void_p), ("bl", C.c_void_p)]
 
 
 class Info(C.Structure):
@@ -116,6 +116,7 @@ def load(path: str = LIB_PATH):
         "ipm_device_bytes": (I, [P, P, P, P]),
         "ipm_set_lowrank": (I, [P, C.c_int64, P, P, I, P]),
         "ipm_abi_sizes": (I, [P, P, P, P]),
+        "ipm_get_sizes": (I, [P, P, P, P]),
         "ipm_apply_operator_static": (I, [C.c_int64, C.c_int64] + [P] * 10 + [P]),
     }
     for name, (res, args) in sig.items():
@@ -201,7 +202,7 @@ class Solver:
             raise IpmError(rc, "ipm_create")
         self._h = h
         self.opts = o
-        self.n = self.m = 0
+        self.n = self.m = self.m_rows = 0
 
     # ---------------------------------------------------------------- lifecycle
     def close(self):
@@ -228,10 +229,12 @@ class Solver:
 
     # ---------------------------------------------------------------- problem
     def set_qp(self, n, m, c, b=None, l=None, u=None, h0=None, H_dense=None, F=None, f_w=None,
-               a_rows=None, A=None, U=None, u_w=None, stream=None):
+               a_rows=None, A=None, U=None, u_w=None, bl=None, stream=None):
         """F and A are CSR triplets (indptr int64, indices int32, data float64); U is n x k
-        (row-major) with weights u_w: the low-rank Hessian term U diag(u_w) U^T."""
-        arrays = [c, b, l, u, h0, H_dense, f_w, a_rows, U, u_w] + (list(F) if F else []) + (list(A) if A else [])
+        (row-major) with weights u_w: the low-rank Hessian term U diag(u_w) U^T.  bl gives
+        two-sided rows bl <= A x <= b (-inf: no lower side; b may then hold +inf); get()
+        then returns per row the signed multiplier y_upper - y_lower."""
+        arrays = [c, b, l, u, h0, H_dense, f_w, a_rows, U, u_w, bl] + (list(F) if F else []) + (list(A) if A else [])
         mem = MEM_DEVICE if any(_is_dev(a) for a in arrays if a is not None) else MEM_HOST
         mk = _Marshal(mem)
         q = QP()
@@ -255,9 +258,18 @@ class Solver:
         if U is not None:
             q.u_cols = int(U.shape[1]) if hasattr(U, "shape") else int(len(u_w))
             q.U, q.u_w = mk.ptr(U, np.float64), mk.ptr(u_w, np.float64)
+        if bl is not None and m:
+            q.bl = mk.ptr(bl, np.float64)
         self._check(load().ipm_set_qp(self._h, C.byref(q), _default_stream(stream)), "ipm_set_qp")
         self.n, self.m = int(n), int(m)
+        self.m_rows = self.sizes()["m_rows"]
         return self
+
+    def sizes(self):
+        """dict(n, m, m_rows): m_rows counts the stored rows (two-sided rows stacked as [A; -A])."""
+        n, m, mr = C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(load().ipm_get_sizes(self._h, C.byref(n), C.byref(m), C.byref(mr)), "ipm_get_sizes")
+        return dict(n=n.value, m=m.value, m_rows=mr.value)
 
     def set_qp_dense(self, H, c, A, b, l=None, u=None, stream=None):
         """Dense QP: H as a dense symmetric block, A passed as CSR of its non-zeros."""
@@ -300,7 +312,7 @@ class Solver:
     def share_qp(self, src, stream=None):
         """Loads the QP of Solver ``src`` without copying its matrices (own state only)."""
         self._check(load().ipm_share_qp(self._h, src._h, _default_stream(stream)), "ipm_share_qp")
-        self.n, self.m = src.n, src.m
+        self.n, self.m, self.m_rows = src.n, src.m, src.m_rows
         return self
 
     def device_bytes(self):
@@ -353,13 +365,13 @@ class Solver:
     # ---------------------------------------------------------------- single steps
     def set_iterate(self, x, s, y, zl, zu, mu, stream=None):
         mk = _Marshal(MEM_HOST)
-        self._check(load().ipm_set_iterate(self._h, mk.ptr(x, np.float64), mk.ptr(s, np.float64) if self.m else None,
-                                           mk.ptr(y, np.float64) if self.m else None, mk.ptr(zl, np.float64),
+        self._check(load().ipm_set_iterate(self._h, mk.ptr(x, np.float64), mk.ptr(s, np.float64) if self.m_rows else None,
+                                           mk.ptr(y, np.float64) if self.m_rows else None, mk.ptr(zl, np.float64),
                                            mk.ptr(zu, np.float64), float(mu), MEM_HOST, _default_stream(stream)),
                     "ipm_set_iterate")
 
     def residuals(self, stream=None):
-        n, m = self.n, self.m
+        n, m = self.n, self.m_rows
         rd, rp, rs, rl, ru, kkt = np.empty(n), np.empty(m), np.empty(m), np.empty(n), np.empty(n), np.empty(4)
         p = lambda a: a.ctypes.data if a.size else None
         self._check(load().ipm_residuals(self._h, p(rd), p(rp), p(rs), p(rl), p(ru), p(kkt), MEM_HOST,
@@ -380,7 +392,7 @@ class Solver:
         return dg
 
     def newton_direction(self, eta=0.0, stream=None):
-        n, m = self.n, self.m
+        n, m = self.n, self.m_rows
         dx, ds, dy, dzl, dzu = np.empty(n), np.empty(m), np.empty(m), np.empty(n), np.empty(n)
         rep = CgReport()
         p = lambda a: a.ctypes.data if a.size else None
@@ -407,8 +419,8 @@ class Solver:
     def step_lengths(self, dx, ds, dy, dzl, dzu, tau, stream=None):
         mk = _Marshal(MEM_HOST)
         ap, ad = C.c_double(), C.c_double()
-        self._check(load().ipm_step_lengths(self._h, mk.ptr(dx, np.float64), mk.ptr(ds, np.float64) if self.m else None,
-                                            mk.ptr(dy, np.float64) if self.m else None, mk.ptr(dzl, np.float64),
+        self._check(load().ipm_step_lengths(self._h, mk.ptr(dx, np.float64), mk.ptr(ds, np.float64) if self.m_rows else None,
+                                            mk.ptr(dy, np.float64) if self.m_rows else None, mk.ptr(dzl, np.float64),
                                             mk.ptr(dzu, np.float64), float(tau), C.byref(ap), C.byref(ad), MEM_HOST,
                                             _default_stream(stream)), "ipm_step_lengths")
         return ap.value, ad.value

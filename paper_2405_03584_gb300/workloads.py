@@ -26,7 +26,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = [
-    "dense_qp", "rt_qp", "rt_batch_sizes", "rt_batch", "perturb_chain_step",
+    "dense_qp", "rt_qp", "rt_two_sided", "rt_batch_sizes", "rt_batch", "perturb_chain_step",
     "serving_stream", "request_costs", "bfgs_qp", "sqp_problem", "csr_to_dense", "random_iterate",
 ]
 
@@ -135,6 +135,43 @@ def rt_qp(n: int = 50_000, V: int | None = None, density: float = 0.005, seed: i
     return dict(kind="rt", n=n, V=V, m=m, D_indptr=indptr, D_indices=indices, D_data=data,
                 w=w, d=d, h0=np.full(n, eps), eps=eps, c=c, a_rows=a_rows,
                 b=np.full(m, b_organ), l=np.full(n, lo), u=np.full(n, hi))
+
+
+def rt_two_sided(p: dict, n_window: int | None = None, delta: float = 0.2, lower_only_frac: float = 0.125,
+                 seed: int = 5) -> dict:
+    """Adds two-sided rows to an RT-shaped QP from ``rt_qp``: the paper's l_A <= A x <= u_A
+    (Section 4, before eq:2x2_reduced).  x_f = alpha 1 with alpha = min_k b_k / (2 rowsum_k)
+    over the organ rows is strictly feasible; n_window target voxels and as many other
+    voxels (none of them organ rows) get the window (1 -/+ delta) (D x_f)_t, where the cost
+    pulls target doses up (upper sides bind) and the others down (lower sides bind); a
+    fraction lower_only_frac of the window rows keeps only the lower side (b = +inf).  The
+    organ rows keep their upper limit only (bl = -inf); the window rows follow them in a_rows."""
+    rng = np.random.default_rng(seed)
+    V = p["V"]
+    rowsum = np.add.reduceat(p["D_data"], p["D_indptr"][:-1]) * (np.diff(p["D_indptr"]) > 0)
+    organ = np.asarray(p["a_rows"], dtype=np.int64)
+    alpha = 0.5 * float(np.min(p["b"] / np.maximum(rowsum[organ], 1e-300))) if organ.size else 1.0
+    dose_f = alpha * rowsum
+    taken = np.zeros(V, bool)
+    taken[organ] = True
+    cand_t = np.flatnonzero((p["d"] > 0) & ~taken & (dose_f > 0))
+    cand_o = np.flatnonzero((p["d"] == 0) & ~taken & (dose_f > 0))
+    if n_window is None:
+        n_window = max(1, cand_t.size // 10)
+    win = np.concatenate([rng.choice(cand_t, size=min(n_window, cand_t.size), replace=False),
+                          rng.choice(cand_o, size=min(n_window, cand_o.size), replace=False)])
+    win = np.sort(win).astype(np.int32)
+    lo = (1.0 - delta) * dose_f[win]
+    hi = (1.0 + delta) * dose_f[win]
+    hi[rng.random(win.size) < lower_only_frac] = np.inf
+    m0 = p["m"]
+    q = dict(p)
+    q["a_rows"] = np.concatenate([organ, win]).astype(np.int32)
+    q["m"] = m0 + win.size
+    q["b"] = np.concatenate([p["b"], hi])
+    q["bl"] = np.concatenate([np.full(m0, -np.inf), lo])
+    q["x_feasible"] = np.full(p["n"], alpha)
+    return q
 
 
 def rt_batch_sizes(count: int = 64, seed: int = 3, n_lo: int = 2000, n_hi: int = 40000,

@@ -374,6 +374,19 @@ def test_augmented_system_solves(name, make):
     assert abs(f - f0) <= 1e-6 * (1 + abs(f0))
 
 
+def test_dense_preconditioner_needs_f64_storage():
+    """DENSE is an FP64 factor for the FP64 operator: refused with a reduced-precision
+    operator; AUTO then picks JACOBI_LR even for small n."""
+    for storage in ("f32", "bf16", "fp8"):
+        with pytest.raises(ipm.IpmError):
+            ipm.Solver(precond="dense", storage=storage)
+    p = W.rt_qp(n=300, seed=2)
+    with ipm.Solver(tol_kkt=1e-7, storage="bf16") as s:
+        s.set_qp_rt(p)
+        assert s.solve() == ipm.IPM_OK
+        assert s.get()["info"]["precond"] == ipm.PRECOND["jacobi_lr"]
+
+
 def test_augmented_system_option_checks():
     with pytest.raises(ipm.IpmError):
         ipm.Solver(system="augmented", storage="bf16")

@@ -40,3 +40,23 @@ def test_rt_batch_sizes_mix():
     ds = np.array([s[1] for s in sizes])
     assert len(sizes) == 64 and ns.min() >= 2000 and ns.max() <= 40000
     assert ds.min() >= 0.002 and ds.max() <= 0.01
+
+
+def test_rt_two_sided_structure():
+    """Window rows: distinct from the organ rows and from each other, half targets, windows
+    around the stated strictly feasible point, some rows lower-only, organ rows upper-only."""
+    p = W.rt_qp(n=1200, seed=7)
+    q = W.rt_two_sided(p, seed=2)
+    m0 = p["m"]
+    ar = q["a_rows"]
+    assert q["m"] == ar.size and np.unique(ar).size == ar.size and np.array_equal(ar[:m0], p["a_rows"])
+    win = ar[m0:]
+    assert (p["d"][win] > 0).sum() == (p["d"][win] == 0).sum()
+    assert np.all(np.isneginf(q["bl"][:m0])) and np.array_equal(q["b"][:m0], p["b"])
+    assert np.all(np.isfinite(q["bl"][m0:])) and 0 < np.isinf(q["b"][m0:]).sum() < win.size
+    # A x_f strictly inside every row's window, x_f inside the box
+    xf = q["x_feasible"]
+    rows = np.repeat(np.arange(p["V"]), np.diff(p["D_indptr"]))
+    dose = np.bincount(rows, weights=p["D_data"] * xf[p["D_indices"]], minlength=p["V"])[ar]
+    assert np.all(dose < q["b"]) and np.all(dose > q["bl"])
+    assert np.all(xf > p["l"]) and np.all(xf < p["u"])
