@@ -540,6 +540,64 @@ def run_dense(args):
     return 0
 
 
+def run_two_sided(args):
+    """The RT workload with the paper's two-sided rows (Section 4: l_A <= A x <= u_A, stacked
+    as B = [A; -A]): the 20000 organ rows keep their upper limit and dose windows
+    (1 -/+ 0.2) D x_f around a strictly feasible x_f are added on --window-rows targets and as
+    many other voxels, 1/8 of them lower-only (workloads.rt_two_sided).  Nearly every window
+    binds (the cost pulls target doses far above the window and the others to zero), so the
+    stiff-row correction is widened to 1024 rows; with thousands of binding rows it cannot
+    cover them and PCG runs to its limits.  Solves/s at rel. KKT <= 1e-6 beside the one-sided
+    workload solved with the same options (the cost of the stacked rows), each certified by
+    the independent checker."""
+    import torch
+    from paper_2405_03584_gb300 import build, ipm, workloads as W
+    from oracle import kkt_check
+    torch.cuda.set_device(0)
+    build.build()
+    base = W.rt_qp(n=N_FULL, seed=SEED)
+    two = W.rt_two_sided(base, n_window=args.window_rows)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    res = {}
+    for name, q in (("two_sided", two), ("one_sided", base)):
+        s = ipm.Solver(tol_kkt=TOL, precond="jacobi_lr", autotune=1, storage=args.storage, stiff_max=1024)
+        s.set_qp(q["n"], q["m"], q["c"], q["b"], q["l"], q["u"], h0=q["h0"],
+                 F=(q["D_indptr"], q["D_indices"], q["D_data"]), f_w=q["w"], a_rows=q["a_rows"], bl=q.get("bl"))
+        for _ in range(args.warmup):
+            s.solve()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sts = [s.solve() for _ in range(args.steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        out = s.get()
+        info = out["info"]
+        rk = kkt_check.rel_kkt(kkt_check.rt_ops(q), out["x"], out["y"], out["zl"], out["zu"])
+        y = out["y"][base["m"]:]
+        res[name] = {"solves_per_s": 1000.0 / ms, "ms_per_solve": ms, "status": [int(x) for x in sts],
+                     "ipm_iters": info["ipm_iters"], "cg_iters": info["cg_iters"], "rel_kkt_device": info["rel_kkt"],
+                     "rel_kkt_checker": rk, "m": q["m"], "m_rows": s.sizes()["m_rows"],
+                     "gpu_launches": int(info["kernel_launches"])}
+        if name == "two_sided":
+            res[name]["window_rows_binding"] = {"upper": int((y > 0).sum()), "lower": int((y < 0).sum()),
+                                                "of": int(y.size)}
+        s.close()
+    clk = clocks.stop()
+    out = {"mode": "two_sided", "metric": "QP solves/sec at rel. KKT <= 1e-6 (two-sided rows)",
+           "value": res["two_sided"]["solves_per_s"], "unit": "solves/s", "steps": args.steps, "warmup": args.warmup,
+           "dtype": "f64" if args.storage == "f64" else "%s storage, f64 refinement" % args.storage,
+           "config": {"workload": WORKLOAD + "; plus two-sided dose windows on %d target and %d other voxels "
+                                             "(workloads.rt_two_sided)" % (args.window_rows, args.window_rows),
+                      "storage": args.storage, "precond": "jacobi_lr", "stiff_max": 1024},
+           "two_sided": res["two_sided"], "one_sided": res["one_sided"], "clocks": clk}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -684,6 +742,8 @@ def main():
     ap.add_argument("--bfgs", choices=["proton", "vmat"], help="the quasi-Newton Hessian shapes of the paper")
     ap.add_argument("--sqp", action="store_true", help="the SQP outer loop with GPU QP sub-problems")
     ap.add_argument("--dense", action="store_true", help="the dense QP (n = 500, m = 1000)")
+    ap.add_argument("--two-sided", action="store_true", help="the RT workload with two-sided dose-window rows")
+    ap.add_argument("--window-rows", type=int, default=200, help="--two-sided: window rows per voxel class")
     ap.add_argument("--sqp-n", type=int, default=10000)
     ap.add_argument("--sqp-iters", type=int, default=150)
     ap.add_argument("--serve", action="store_true", help="the serving stream (Poisson arrivals, chains, warm start)")
@@ -713,6 +773,8 @@ def main():
         return run_sqp(args)
     if args.dense:
         return run_dense(args)
+    if args.two_sided:
+        return run_two_sided(args)
     if args.serve:
         # more hardware work queues than the default 8, so many slots' streams run side by side
         os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
