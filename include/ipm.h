@@ -10,7 +10,7 @@
  *     (H + A^T Theta A + Sigma) dx = r,  Theta = diag(y / s),  Sigma = diag(z_l/t_l + z_u/t_u)
  *
  * (the Schur complement of eq:2x2_reduced) and solved matrix-free by preconditioned
- * conjugate gradients (Section 4.1, Algorithm 1 line "solve ... using PCG"), on the device.
+ * conjugate gradients (Section 4.1; the linear solve of Algorithm 1), on the device.
  *
  * Conventions for every entry point:
  *   - Return value: an ipm_status code; functions never abort and never print.
@@ -321,14 +321,14 @@ int ipm_apply_kkt(ipm_handle* h, const double* p, double* q, int mem, void* stre
 /* Jacobi diagonal diag(H + A^T Theta A + Sigma) at the current iterate (Section 4.1.2). */
 int ipm_precond_diag(ipm_handle* h, double* diag, int mem, void* stream);
 
-/* Newton direction at the current iterate and mu (Algorithm 1: PCG solve, then "assemble full
- * search direction"): dx, dz_l, dz_u (n), ds, dy (m).  eta <= 0 selects the solver's own rule;
+/* Newton direction at the current iterate and mu (Algorithm 1: the PCG solve, then the
+ * recovery of the full direction): dx, dz_l, dz_u (n), ds, dy (m).  eta <= 0 selects the solver's own rule;
  * otherwise PCG stops at ||r|| <= eta ||rhs||.  rep may be NULL. */
 int ipm_newton_direction(ipm_handle* h, double eta, double* dx, double* ds, double* dy,
                          double* dz_l, double* dz_u, ipm_cg_report* rep, int mem, void* stream);
 
 /* Fraction-to-boundary step lengths for the given direction at the current iterate (Section
- * 3.1 line search; Algorithm 1 "compute maximum step length"):
+ * 3.1 line search; Algorithm 1's step lengths):
  *   alpha_p = min(1, tau max{a: s + a ds >= 0, t_l + a dx >= 0, t_u - a dx >= 0}),
  *   alpha_d = min(1, tau max{a: y + a dy >= 0, z_l + a dz_l >= 0, z_u + a dz_u >= 0}). */
 int ipm_step_lengths(ipm_handle* h, const double* dx, const double* ds, const double* dy,

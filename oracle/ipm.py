@@ -208,8 +208,8 @@ def condensed_system(qp: DenseQP, it: Iterate, res):
 
 
 def recover_direction(qp: DenseQP, it: Iterate, res, dx):
-    """Back-substitution for (ds, dy, dz_l, dz_u) from dx (Algorithm 1, "assemble full
-    search direction"): the last four block rows of eq:newton_system solved for them."""
+    """Back-substitution for (ds, dy, dz_l, dz_u) from dx (Algorithm 1's recovery of
+    the full direction): the last four block rows of eq:newton_system solved for them."""
     rd, rp, rs, rl, ru = res
     tl, tu = _tl(qp, it.x), _tu(qp, it.x)
     Adx = qp.A @ dx
@@ -268,8 +268,8 @@ def _max_ratio(v, dv, mask=None):
 
 
 def step_lengths(qp: DenseQP, it: Iterate, d: Iterate, tau: float = 0.995, equal: bool = False):
-    """Fraction-to-boundary step lengths (Section 3.1 line search; Algorithm 1 "compute
-    maximum step length alpha_x, alpha_lambda").
+    """Fraction-to-boundary step lengths (Section 3.1 line search; Algorithm 1's
+    separate primal and dual step lengths).
 
     alpha_p = min(1, tau * max{a : s + a ds >= 0, t_l + a dx >= 0, t_u - a dx >= 0})
     alpha_d = min(1, tau * max{a : y + a dy >= 0, z_l + a dz_l >= 0, z_u + a dz_u >= 0})
