@@ -87,10 +87,13 @@ def _hx(h0, U, w, v):
 
 
 def sqp_solve(obj: DoseObjective, A, b, l, u, x0, solver, max_iter=50, tol=1e-6, u_cap=200, warm=True,
-              armijo=1e-4):
+              armijo=1e-4, bl=None):
     """Runs the SQP loop.  ``solver`` is a loaded handle-like object (``ipm.Solver`` with
     ``u_cap`` columns reserved) offering set_qp, update_costs, set_lowrank, solve and get.
-    A is a scipy CSR matrix (m x n).  Returns an SQPResult; history has one dict per iteration."""
+    A is a scipy CSR matrix (m x n); bl, if given, makes the rows two-sided (bl <= A x <= b,
+    the paper's l_A <= A x <= u_A; b may then hold +inf) and the returned y signed (upper
+    side minus lower side).  x0 must be feasible (the line search stays on the segment to
+    the sub-problem's solution).  Returns an SQPResult; history has one dict per iteration."""
     n = x0.shape[0]
     x = np.asarray(x0, float).copy()
     h0 = obj.gauss_newton_diag()
@@ -99,8 +102,10 @@ def sqp_solve(obj: DoseObjective, A, b, l, u, x0, solver, max_iter=50, tol=1e-6,
     f, g = obj.value_grad(x)
     A = A.tocsr()
     m = A.shape[0]
+    two = {} if bl is None else {"bl": np.asarray(bl, float)}
     solver.set_qp(n, m, g - _hx(h0, U, w, x), b if m else None, l, u, h0=h0,
-                  A=(A.indptr.astype(np.int64), A.indices.astype(np.int32), A.data.astype(np.float64)) if m else None)
+                  A=(A.indptr.astype(np.int64), A.indices.astype(np.int32), A.data.astype(np.float64)) if m else None,
+                  **two)
     hist = []
     converged = False
     for k in range(max_iter):

@@ -35,6 +35,26 @@ def test_sqp_gpu_matches_oracle_subproblems():
     assert warm < cold
 
 
+def test_sqp_gpu_two_sided_rows():
+    """The SQP loop with two-sided rows (dose windows beside the hard organ limits, the
+    paper's l_A <= A x <= u_A): GPU sub-problems against the oracle's, signed multipliers."""
+    from tests.test_sqp_host import OracleQP, two_sided_rows
+    p = W.sqp_problem(n=120, density=0.05, seed=5)
+    obj, A = _objective(p)
+    A2, b2, bl2, xf = two_sided_rows(p, obj, A, 5, 12)
+    with ipm.Solver(tol_kkt=1e-9, precond="jacobi_lr", u_cap=120) as s:
+        res = sqp.sqp_solve(obj, A2, b2, p["l"], p["u"], xf, s, max_iter=150, tol=1e-6, u_cap=120, bl=bl2)
+    assert res.converged, res.history[-1]
+    assert all(h["qp_status"] == ipm.IPM_OK for h in res.history)
+    obj2, _ = _objective(p)
+    ref = sqp.sqp_solve(obj2, A2, b2, p["l"], p["u"], xf, OracleQP(), max_iter=150, tol=1e-6, u_cap=120, bl=bl2)
+    assert ref.converged
+    assert abs(res.f - ref.f) <= 1e-6 * (1 + abs(ref.f))
+    assert np.abs(res.x - ref.x).max() <= 1e-3 * (1 + np.abs(ref.x).max())
+    big = np.abs(ref.y) > 1e-3 * np.abs(ref.y).max()
+    assert (ref.y[big] < 0).any() and np.all(np.sign(res.y[big]) == np.sign(ref.y[big]))
+
+
 def test_set_lowrank_capacity_and_reset():
     p = W.bfgs_qp(n=300, k=6, seed=31)
     with ipm.Solver(tol_kkt=1e-8, u_cap=16) as s:

@@ -17,8 +17,9 @@ class OracleQP:
         self.U = None
         self.w = None
 
-    def set_qp(self, n, m, c, b=None, l=None, u=None, h0=None, A=None, **kw):
+    def set_qp(self, n, m, c, b=None, l=None, u=None, h0=None, A=None, bl=None, **kw):
         self.n, self.m, self.c, self.b, self.l, self.u, self.h0 = n, m, c, b, l, u, h0
+        self.bl = bl
         self.A = np.zeros((m, n))
         if m:
             ip, ix, dv = A
@@ -36,8 +37,14 @@ class OracleQP:
 
     def solve(self, warm=False):
         H = np.diag(self.h0) + (self.U * self.w) @ self.U.T
-        qp = O.DenseQP(0.5 * (H + H.T), self.c, self.A, self.b if self.m else np.zeros(0), self.l, self.u)
+        H = 0.5 * (H + H.T)
+        if self.bl is None:
+            qp = O.DenseQP(H, self.c, self.A, self.b if self.m else np.zeros(0), self.l, self.u)
+        else:
+            qp, up, lo = O.two_sided(H, self.c, self.A, self.bl, self.b, self.l, self.u)
         self.it, info = O.solve(qp, tol=1e-10)
+        if self.bl is not None:
+            self.it.y = O.row_multipliers(self.it.y, up, lo, self.m)
         self.info = info
         return 0 if info.status == "optimal" else 3
 
@@ -115,3 +122,48 @@ def test_dose_objective_gradient_and_h0():
     wv[p["target"]] += p["w_target"]
     wv[p["organ"]] += p["w_organ"]
     np.testing.assert_allclose(obj.gauss_newton_diag(), 2.0 * (D ** 2).T @ wv + obj.eps, rtol=1e-12)
+
+
+def two_sided_rows(p, obj, A, seed, k):
+    """The hard organ rows plus dose windows (0.8, 1.2) x (D x_f) on k non-target voxels,
+    the last one lower-only, around x_f = alpha 1 (alpha: half the tightest organ limit),
+    which is strictly feasible and serves as the start.  Returns (A, b, bl, x_f)."""
+    D = obj.D
+    rowsum = np.asarray(abs(D).sum(axis=1)).ravel()
+    ar = np.asarray(p["a_rows"])
+    xf = np.full(p["n"], 0.5 * np.min(p["b"] / rowsum[ar]))
+    taken = np.zeros(p["V"], bool)
+    taken[ar] = True
+    cand = np.flatnonzero(~taken & (rowsum > 0) & np.isin(np.arange(p["V"]), obj.organ))
+    other = np.sort(np.random.default_rng(seed).choice(cand, k, replace=False))
+    A2 = sp.vstack([A, D[other]]).tocsr()
+    dxf = D[other] @ xf
+    b2 = np.concatenate([p["b"], 1.2 * dxf])
+    bl2 = np.concatenate([np.full(ar.size, -np.inf), 0.8 * dxf])
+    b2[-1] = np.inf
+    return A2, b2, bl2, xf
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+def test_sqp_two_sided_rows_match_slsqp(seed):
+    """Two-sided rows (the paper's l_A <= A x <= u_A) through the SQP loop: dose windows
+    (0.8, 1.2) x (D x_f) on six non-target voxels around the feasible start x_f (one of them
+    lower-only) beside the hard organ limits; the result matches SLSQP with both sides as
+    inequalities, some lower sides bind, and stationarity holds with the signed multipliers."""
+    p = W.sqp_problem(n=30, density=0.1, seed=seed)
+    obj, A = _objective(p)
+    A2, b2, bl2, xf = two_sided_rows(p, obj, A, seed, 6)
+    res = sqp.sqp_solve(obj, A2, b2, p["l"], p["u"], xf, OracleQP(), max_iter=200, tol=1e-6, bl=bl2)
+    assert res.converged
+    fu, fl = np.isfinite(b2), np.isfinite(bl2)
+    cons = [{"type": "ineq", "fun": lambda x: (b2 - A2 @ x)[fu]},
+            {"type": "ineq", "fun": lambda x: (A2 @ x - bl2)[fl]}]
+    ref = so.minimize(lambda x: obj.value_grad(x), xf, jac=True, method="SLSQP",
+                      bounds=list(zip(p["l"], p["u"])), constraints=cons, options=dict(ftol=1e-14, maxiter=2000))
+    assert abs(res.f - ref.fun) <= 1e-7 * (1 + abs(ref.fun))
+    Ax = A2 @ res.x
+    assert np.all(Ax[fu] <= b2[fu] + 1e-7) and np.all(Ax[fl] >= bl2[fl] - 1e-7)
+    assert (res.y < -1e-8).any(), "a lower side must bind"
+    _, g = obj.value_grad(res.x)
+    r = g + A2.T @ res.y - res.zl + res.zu
+    assert np.abs(r).max() <= 1e-4 * (1 + np.abs(g).max())
