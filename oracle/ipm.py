@@ -25,6 +25,11 @@ Parity pins: the closed form x = -H^{-1} c (unconstrained), per-coordinate clipp
 enumeration (n <= 8; three states per two-sided row), the full unreduced Newton system
 (eq:newton_system), the doubly augmented system (eq:2x2_augmented) and the complementarity /
 duality-gap identities; see tests/test_oracle_pins.py.
+
+Parity unpinned: the iteration path.  The start point, the norm of the mu test, and with
+them the step-length sequence and the iteration counts follow readings of points the paper
+leaves open; the pins fix those readings' invariants (a strictly interior start, a norm
+that vanishes exactly on the central path) and the results the path reaches, not the path.
 """
 from __future__ import annotations
 

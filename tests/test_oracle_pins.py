@@ -481,3 +481,45 @@ def test_checker_two_sided_catches_wrong_sign_and_lower_violation():
     x_bad = xb - p["A"][k] * ((p["A"][k] @ xb - p["bl"][k]) + 0.5) / (p["A"][k] @ p["A"][k])
     val, parts = kkt_check.rel_kkt(ops, x_bad, yb, zlb, zub, detail=True)
     assert parts["primal"] >= 0.5 / (1 + max(np.abs(p["b"]).max(), np.abs(p["bl"]).max())) - 1e-12
+
+
+# ---------------------------------------------------------------- readings: invariants
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_start_point_strictly_interior(seed):
+    """The start point (a reading: the paper only asks for positive slacks) is strictly
+    inside every finite bound, with s, y and the finite-bound z positive and mu0 their mean
+    complementarity; z is zero at infinite bounds."""
+    p = _rand_qp(12, 7, 300 + seed, free_frac=0.5)
+    qp = ipm.from_dense(p)
+    it, mu0 = ipm.start_point(qp)
+    fl, fu = qp.fl, qp.fu
+    assert np.all(it.x[fl] > qp.l[fl]) and np.all(it.x[fu] < qp.u[fu])
+    assert np.all(it.s > 0) and np.all(it.y > 0)
+    assert np.all(it.zl[fl] > 0) and np.all(it.zu[fu] > 0)
+    assert np.all(it.zl[~fl] == 0) and np.all(it.zu[~fu] == 0)
+    pairs = np.concatenate([it.s * it.y, (it.x - qp.l)[fl] * it.zl[fl], (qp.u - it.x)[fu] * it.zu[fu]])
+    assert mu0 == pytest.approx(pairs.mean(), rel=1e-14)
+
+
+def test_mu_test_norm_vanishes_only_on_the_central_path():
+    """The mu test's ||r|| (a reading: the paper leaves the norm open) is zero at a point
+    that is primal and dual feasible with every complementarity product equal to mu, and
+    positive as soon as one residual block (r_p, r_d, r_s, r_l, r_u) is planted."""
+    n, m, mu = 10, 6, 0.3
+    q = _rand_qp(n, m, 55)
+    rng = np.random.default_rng(3)
+    x = rng.uniform(-0.5, 0.5, size=n)
+    s = rng.uniform(0.2, 2.0, size=m)
+    y = mu / s
+    zl, zu = mu / (x - q["l"]), mu / (q["u"] - x)
+    q["b"] = q["A"] @ x + s
+    q["c"] = -(q["H"] @ x + q["A"].T @ y - zl + zu)
+    qp = ipm.from_dense(q)
+    it = ipm.Iterate(x, s, y, zl, zu)
+    assert ipm.scaled_residual_norm(qp, it, ipm.residuals(qp, it, mu)) < 1e-13
+    for k in range(5):
+        res = list(ipm.residuals(qp, it, mu))
+        res[k] = res[k].copy()
+        res[k][0] += 1e-3
+        assert ipm.scaled_residual_norm(qp, it, tuple(res)) > 1e-6, k
