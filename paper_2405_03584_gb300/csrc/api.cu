@@ -102,8 +102,10 @@ struct ipm_handle {
   int ncomp = 0;
   int64_t sc_cap = 0;
   int64_t fr = 0;                   // rows of the factor F (the first rows of R)
-  // two-sided rows (ipm_qp.bl): the caller's row of every stored row, upper sides first
-  // (stored rows [0, rows_up)), then lower sides; empty when the stored rows are the caller's
+  // two-sided rows (ipm_qp.bl): stacked = the stored rows differ from the caller's; then
+  // row_of gives the caller's row of every stored row, upper sides first (stored rows
+  // [0, rows_up)), then lower sides
+  bool stacked = false;
   int64_t m_user = 0, rows_up = 0;
   std::vector<int32_t> row_of;
   std::vector<double> trace;        // IPM_TRACE_COLS doubles per IPM iteration of the last solve
@@ -1188,6 +1190,7 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
     if ((rc = load_qp(h, qp, use_arows ? m : 0, stream))) return rc;
     h->m_user = m;
     h->rows_up = m;
+    h->stacked = false;
     h->row_of.clear();
     return IPM_OK;
   }
@@ -1305,7 +1308,8 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   if (rc) return rc;
   h->m_user = m;
   h->rows_up = up;
-  if (up == m && mr == m) row_of.clear();      // one-sided after all: the caller's rows
+  h->stacked = !(up == m && mr == m);          // else one-sided after all: the caller's rows
+  if (!h->stacked) row_of.clear();
   h->row_of = std::move(row_of);
   return IPM_OK;
 }
@@ -1360,6 +1364,7 @@ int ipm_share_qp(ipm_handle* h, ipm_handle* src, void* stream) {
   if ((rc = alloc_trace(h))) return rc;
   h->cnorm = src->cnorm; h->bnorm = src->bnorm; h->ncomp = src->ncomp; h->sc_cap = sc_cap;
   h->fr = src->fr;
+  h->stacked = src->stacked;
   h->m_user = src->m_user;
   h->rows_up = src->rows_up;
   h->row_of = src->row_of;
@@ -1582,7 +1587,7 @@ int ipm_get_xyz(ipm_handle* h, double* x, double* y, double* zl, double* zu, dou
   if ((rc = copy_out(h, x, d.x, d.n, mem))) return rc;
   if ((rc = copy_out(h, zl, d.zl, d.n, mem))) return rc;
   if ((rc = copy_out(h, zu, d.zu, d.n, mem))) return rc;
-  if (h->row_of.empty()) {
+  if (!h->stacked) {
     if ((rc = copy_out(h, y, d.y, d.m, mem))) return rc;
     if ((rc = copy_out(h, s, d.s, d.m, mem))) return rc;
   } else if (y || s) {

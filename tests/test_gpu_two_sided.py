@@ -217,3 +217,21 @@ def test_bad_row_bounds_rejected():
     with pytest.raises(ipm.IpmError):
         s.set_qp(**_args(q))
     s.close()
+
+
+def test_all_rows_free():
+    """Rows with neither side finite drop out: the QP is the bounds-only one (bit-identical
+    solution), y = 0 and s = +inf for every caller row."""
+    p = _dense_two_sided(40, 12, 9)
+    p["b"], p["bl"] = np.full(12, np.inf), np.full(12, -np.inf)
+    with ipm.Solver(tol_kkt=1e-8) as s1:
+        s1.set_qp(**_args(p))
+        assert s1.sizes()["m_rows"] == 0
+        assert s1.solve() == ipm.IPM_OK
+        o1 = s1.get()
+    with ipm.Solver(tol_kkt=1e-8) as s2:
+        s2.set_qp(n=40, m=0, c=p["c"], l=p["l"], u=p["u"], H_dense=p["H"])
+        assert s2.solve() == ipm.IPM_OK
+        o2 = s2.get()
+    assert np.array_equal(o1["x"], o2["x"])
+    assert np.all(o1["y"] == 0) and np.all(np.isinf(o1["s"]))
