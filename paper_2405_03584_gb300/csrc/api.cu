@@ -1235,6 +1235,9 @@ int ipm_set_qp(ipm_handle* h, const ipm_qp* qp, void* stream) {
   if (use_arows) {
     if ((rc = fetch(h, qp->a_rows, m, mem, ar))) return rc;
     for (int32_t r : ar) if (r < 0 || r >= fr) return fail(h, IPM_ERR_ARG, "a_rows index out of range");
+    std::vector<int32_t> srt(ar);
+    std::sort(srt.begin(), srt.end());
+    if (std::adjacent_find(srt.begin(), srt.end()) != srt.end()) return fail(h, IPM_ERR_ARG, "a_rows has duplicates");
   }
   // stored rows: a_rows of the upper sides, then the CSR block (negated rows for lower sides)
   std::vector<int32_t> ar_up;

@@ -235,3 +235,16 @@ def test_all_rows_free():
         o2 = s2.get()
     assert np.array_equal(o1["x"], o2["x"])
     assert np.all(o1["y"] == 0) and np.all(np.isinf(o1["s"]))
+
+
+def test_duplicate_a_rows_rejected():
+    """As for one-sided rows, a row of F may be named once (its two sides are bl and b)."""
+    p = W.rt_two_sided(W.rt_qp(n=300, seed=4))
+    q = dict(p)
+    q["a_rows"] = p["a_rows"].copy()
+    q["a_rows"][-1] = q["a_rows"][-2]
+    s = ipm.Solver()
+    with pytest.raises(ipm.IpmError) as e:
+        s.set_qp(**_args(q))
+    assert e.value.status == ipm.IPM_ERR_ARG
+    s.close()
