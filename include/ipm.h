@@ -3,8 +3,9 @@
  *
  *     min 0.5 x^T H x + c^T x   s.t.   A x <= b,   l <= x <= u            (1)
  *
- * This is the paper's QP (Section 3.1, eq:qp) with a one-sided constraint block and the
- * variable bounds kept apart from A, as Section 4 does before eq:2x2_reduced.  Each Newton
+ * This is the paper's QP (Section 3.1, eq:qp) with the variable bounds kept apart from A, as
+ * Section 4 does before eq:2x2_reduced; the paper's two-sided rows l_A <= A x <= u_A are
+ * taken as its stack B = [A; -A] of one-sided rows (ipm_qp.bl).  Each Newton
  * step (eq:newton_system) is reduced to the normal-equations system
  *
  *     (H + A^T Theta A + Sigma) dx = r,  Theta = diag(y / s),  Sigma = diag(z_l/t_l + z_u/t_u)
@@ -61,7 +62,7 @@ enum ipm_mem_space { IPM_MEM_HOST = 0, IPM_MEM_DEVICE = 1 };
  *              (Woodbury) for the "stiff" rows whose theta_i sum_j a_ij^2 / M0_j > stiff_gamma;
  *              keeps PCG iteration counts bounded as mu -> 0 (default).
  *  DENSE     : the whole matrix, formed and Cholesky-factored on the device (one diagonal
- *              block of size n); for n <= dense_max_n.                                       */
+ *              block of size n); for n <= dense_max_n and FP64 storage.                      */
 enum ipm_precond { IPM_PRECOND_JACOBI = 0, IPM_PRECOND_JACOBI_LR = 1, IPM_PRECOND_DENSE = 2,
                    IPM_PRECOND_AUTO = 3 };
 
@@ -100,9 +101,9 @@ typedef struct ipm_options {
                          /* row on the loaded matrices and keeps the fastest (kept per matrix  */
                          /* signature for the process).  0 (default): lanes from the average   */
                          /* row length, so results are bitwise reproducible across processes  */
-  int use_graphs;        /* 1: one CUDA graph per IPM iteration with PCG as a conditional-while */
-                         /* node (default); 0: the same kernels launched one by one with a host */
-                         /* loop over PCG iterations (for per-kernel profilers)                */
+  int use_graphs;        /* 1: the whole solve as one CUDA graph, the IPM and PCG loops as      */
+                         /* nested conditional-while nodes (default); 0: the same kernels      */
+                         /* launched one by one from host loops (for per-kernel profilers)     */
   int storage;           /* enum ipm_storage (default IPM_STORAGE_F64)                          */
   int refine_max;        /* reduced precision: at most this many refinement passes per step (8) */
   double refine_eta;     /* reduced precision: inner PCG tolerance relative to the current      */
