@@ -160,17 +160,17 @@ def _ncu_traffic(kernel, lanes):
     return None
 
 
-def _oracle_sample():
-    """The CPU oracle as it stands: one full solve of the same generator at n = SAMPLE_N,
+def _oracle_sample(sample_n=SAMPLE_N):
+    """The CPU oracle as it stands: one full solve of the same generator at n = sample_n,
     scaled to the full size by the O(n^3) cost of its dense Newton steps."""
     from oracle import ipm as O
     from paper_2405_03584_gb300 import workloads as W
-    p = W.rt_qp(n=SAMPLE_N, seed=SEED)
+    p = W.rt_qp(n=sample_n, seed=SEED)
     t0 = time.perf_counter()
     qp = O.from_rt(p)
     it, info = O.solve(qp, tol=TOL)
     t = time.perf_counter() - t0
-    scale = (N_FULL / SAMPLE_N) ** 3
+    scale = (N_FULL / sample_n) ** 3
     return dict(seconds=t, scale=scale, ipm_iters=info.iterations, status=info.status,
                 solves_per_s=1.0 / (t * scale))
 
@@ -182,14 +182,14 @@ def run_reference(args):
     cores = _cores_used()
     times = []
     for k in range(args.warmup + args.steps):
-        r = _oracle_sample()
+        r = _oracle_sample(args.sample_n)
         if k >= args.warmup:
             times.append(r["seconds"] * r["scale"])
     tot = sum(times)
     value = args.steps / tot
     sample = ("oracle (dense-Cholesky FP64 IPM) full solve of the same RT generator at n=%d, V=%d, m=%d "
-              "(%.1f s each), scaled by (50000/%d)^3" % (SAMPLE_N, 4 * SAMPLE_N, 4 * SAMPLE_N // 10,
-                                                         statistics.mean([t / r["scale"] for t in times]), SAMPLE_N))
+              "(%.1f s each), scaled by (50000/%d)^3" % (args.sample_n, 4 * args.sample_n, 4 * args.sample_n // 10,
+                                                         statistics.mean([t / r["scale"] for t in times]), args.sample_n))
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -696,11 +696,12 @@ def run_ours(args):
                "steps": len(e2e_t), "includes": "ipm_create + ipm_set_qp (host arrays, pinned) + ipm_solve + ipm_get_xyz"}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r = _oracle_sample()
+        r = _oracle_sample(args.sample_n)
         cpu = {"value": r["solves_per_s"], "unit": "solves/s", "cores": _cores_used(), "kind": "oracle",
                "sample": "oracle (dense-Cholesky FP64 IPM) full solve of the same RT generator at n=%d, V=%d, m=%d "
                          "in %.1f s (%d IPM iterations), scaled by (50000/%d)^3" %
-                         (SAMPLE_N, 4 * SAMPLE_N, 4 * SAMPLE_N // 10, r["seconds"], r["ipm_iters"], SAMPLE_N)}
+                         (args.sample_n, 4 * args.sample_n, 4 * args.sample_n // 10, r["seconds"], r["ipm_iters"],
+                          args.sample_n)}
     if rank == 0:
         lat_sorted = sorted(lat)
         p99 = lat_sorted[min(len(lat_sorted) - 1, int(np.ceil(0.99 * len(lat_sorted))) - 1)]
@@ -733,6 +734,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sample-n", type=int, default=SAMPLE_N,
+                    help="n of the oracle sample behind cpu_baseline and --impl reference")
     ap.add_argument("--operator-only", action="store_true",
                     help="profiler capture target: a few IPM iterations, then the operator kernels")
     ap.add_argument("--lanes", default="8,16", help="--operator-only: lanes per row over R and R^T")
