@@ -271,8 +271,9 @@ class Solver:
         self._check(load().ipm_get_sizes(self._h, C.byref(n), C.byref(m), C.byref(mr)), "ipm_get_sizes")
         return dict(n=n.value, m=m.value, m_rows=mr.value)
 
-    def set_qp_dense(self, H, c, A, b, l=None, u=None, stream=None):
-        """Dense QP: H as a dense symmetric block, A passed as CSR of its non-zeros."""
+    def set_qp_dense(self, H, c, A, b, l=None, u=None, bl=None, stream=None):
+        """Dense QP: H as a dense symmetric block, A passed as CSR of its non-zeros (bl: lower
+        sides of two-sided rows, as in set_qp)."""
         A = np.asarray(A, dtype=np.float64).reshape(-1, len(c))
         m, n = A.shape
         rows, cols = np.nonzero(A)
@@ -280,13 +281,14 @@ class Solver:
         np.cumsum(np.bincount(rows, minlength=m), out=indptr[1:])
         Acsr = (indptr, cols.astype(np.int32), A[rows, cols]) if m else None
         return self.set_qp(n, m, c, b if m else None, l, u, H_dense=np.asarray(H, dtype=np.float64),
-                           A=Acsr, stream=stream)
+                           A=Acsr, bl=bl, stream=stream)
 
     def set_qp_rt(self, p, stream=None):
-        """RT-shaped QP from ``workloads.rt_qp``: H = D^T diag(w) D + diag(h0), A = D[a_rows]."""
+        """RT-shaped QP from ``workloads.rt_qp``: H = D^T diag(w) D + diag(h0), A = D[a_rows]
+        (two-sided rows when p has "bl", as ``workloads.rt_two_sided`` gives)."""
         return self.set_qp(p["n"], p["m"], p["c"], p["b"], p["l"], p["u"], h0=p["h0"],
                            F=(p["D_indptr"], p["D_indices"], p["D_data"]), f_w=p["w"],
-                           a_rows=p["a_rows"] if p["m"] else None, stream=stream)
+                           a_rows=p["a_rows"] if p["m"] else None, bl=p.get("bl"), stream=stream)
 
     def set_qp_bfgs(self, p, stream=None):
         """QP with a quasi-Newton Hessian from ``workloads.bfgs_qp``: H = diag(h0) + U diag(w) U^T,
