@@ -56,6 +56,22 @@ def test_null_arguments_rejected(lib):
     assert lib.ipm_create(C.byref(bad), C.byref(h)) == ipm.IPM_ERR_ARG
 
 
+@pytest.mark.parametrize("field,value", [
+    ("precond", 2), ("system", 1), ("stiff_max", 1025), ("lanes_rows", 12), ("dense_max_n", 4096),
+    ("refine_eta", 1.0), ("warm_rho", 1.0), ("u_cap", 1 << 17), ("storage", 4)])
+def test_invalid_option_combinations_rejected(lib, field, value):
+    """ipm_create validates the options before touching the device: with BF16 storage the
+    DENSE preconditioner and the doubly augmented system are refused, and so are values
+    outside their documented ranges."""
+    o = ipm.Options()
+    lib.ipm_default_options(C.byref(o))
+    o.storage = ipm.STORAGE["bf16"]
+    setattr(o, field, value)
+    h = C.c_void_p()
+    assert lib.ipm_create(C.byref(o), C.byref(h)) == ipm.IPM_ERR_ARG
+    assert not h.value
+
+
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(ipm, "_lib", None)
     with pytest.raises(ImportError):
