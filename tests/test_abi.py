@@ -72,6 +72,20 @@ def test_invalid_option_combinations_rejected(lib, field, value):
     assert not h.value
 
 
+def test_static_operator_argument_checks(lib):
+    """The allocation-free operator refuses bad arguments and sizes beyond its fixed scratch
+    before any device work (the pointers below are never dereferenced)."""
+    f = lib.ipm_apply_operator_static
+    dummy = C.c_void_p(16)
+    assert f(0, 0, None, None, None, dummy, None, None, None, dummy, dummy, dummy, None) == ipm.IPM_ERR_ARG
+    assert f(10, -1, None, None, None, dummy, None, None, None, dummy, dummy, dummy, None) == ipm.IPM_ERR_ARG
+    assert f(10, 5, None, None, None, dummy, None, None, None, dummy, dummy, dummy, None) == ipm.IPM_ERR_ARG
+    assert f(10, 5, dummy, None, None, dummy, None, None, dummy, dummy, dummy, None, None) == ipm.IPM_ERR_ARG
+    too_many = (1 << 18) + 1
+    assert f(10, too_many, dummy, None, None, dummy, None, None, dummy, dummy, dummy, dummy, None) == \
+        ipm.IPM_ERR_TOO_LARGE
+
+
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(ipm, "_lib", None)
     with pytest.raises(ImportError):
