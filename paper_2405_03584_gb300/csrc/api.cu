@@ -1087,13 +1087,7 @@ static int load_qp(ipm_handle* h, const ipm_qp* qp, int64_t m_ar, void* stream) 
     // sharing a warp run equal trip counts (RT rows pass: 133 -> 129 us; windows of 128
     // gained nothing, one global order 131 us)
     std::vector<int32_t> perm(q.nR);
-    for (int64_t r = 0; r < q.nR; ++r) perm[r] = (int32_t)r;
-    for (int64_t w0 = 0; w0 < q.nR; w0 += 1024) {
-      const int64_t w1 = std::min<int64_t>(q.nR, w0 + 1024);
-      std::stable_sort(perm.begin() + w0, perm.begin() + w1, [&](int32_t a, int32_t b) {
-        return q.Rp[a + 1] - q.Rp[a] > q.Rp[b + 1] - q.Rp[b];
-      });
-    }
+    order_rows_by_length(q.nR, q.Rp.data(), 1024, perm.data());
     if ((rc = up(d.rperm, perm.data(), 4 * perm.size()))) return rc;
   }
   if (!host_path) {

@@ -133,4 +133,20 @@ void filter_rows(int64_t ncols, const int64_t* tp, const int32_t* ti, const doub
   });
 }
 
+void order_rows_by_length(int64_t nrows, const int64_t* rp, int window, int32_t* perm) {
+  if (nrows <= 0) return;
+  const int64_t nw = (nrows + window - 1) / window;
+  const int T = nrows < (1 << 16) ? 1 : host_threads();
+  parallel_ranges(nw, T, [&](int, int64_t wb, int64_t we) {
+    std::vector<std::pair<int64_t, int32_t>> key;    // (-length, row): ascending = longest first, stable
+    for (int64_t w = wb; w < we; ++w) {
+      const int64_t r0 = w * window, r1 = std::min<int64_t>(nrows, r0 + window);
+      key.clear();
+      for (int64_t r = r0; r < r1; ++r) key.emplace_back(-(rp[r + 1] - rp[r]), (int32_t)r);
+      std::sort(key.begin(), key.end());
+      for (int64_t r = r0; r < r1; ++r) perm[r] = key[r - r0].second;
+    }
+  });
+}
+
 }  // namespace ipmk

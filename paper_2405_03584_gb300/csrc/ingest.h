@@ -31,4 +31,8 @@ void transpose_csr(int64_t nrows, int64_t ncols, const int64_t* rp, const int32_
 void filter_rows(int64_t ncols, const int64_t* tp, const int32_t* ti, const double* tv, const unsigned char* keep,
                  int64_t* op, int32_t* oi, double* ov);
 
+// Row order of the rows pass: windows of `window` consecutive rows, each ordered by row
+// length, longest first, ties in row order (a stable sort).  perm: nrows entries.
+void order_rows_by_length(int64_t nrows, const int64_t* rp, int window, int32_t* perm);
+
 }  // namespace ipmk

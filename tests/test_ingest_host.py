@@ -1,5 +1,5 @@
 """The host-side ingest routines (csrc/ingest.cu: the transpose fallback of ipm_set_qp and
-options.ingest_host) on the CPU: compiled with the host compiler into a small driver and
+options.ingest_host, the row order of the rows pass) on the CPU: compiled with the host compiler into a small driver and
 compared with scipy's transpose, on a matrix large enough for the multi-threaded paths.
 The results must be those of the sequential definitions, whatever the thread count."""
 import os
@@ -60,6 +60,9 @@ int main(int argc, char** argv) {
   std::vector<double> cp(nnz);
   ipmk::par_copy(cp.data(), rv.data(), sizeof(double) * nnz);
   codes.push_back(cp == rv ? 1 : 0);
+  std::vector<int32_t> perm(nr);
+  ipmk::order_rows_by_length(nr, rp.data(), 1024, perm.data());
+  wr(d + "/perm", perm);
   wr(d + "/tp", tp); wr(d + "/ti", ti); wr(d + "/tv", tv);
   wr(d + "/op", op); wr(d + "/oi", oi); wr(d + "/ov", ov); wr(d + "/codes", codes);
   return 0;
@@ -113,3 +116,7 @@ def test_host_transpose_filter_and_checks(driver, tmp_path, n, density, seed):
     assert np.array_equal(ld("oi", np.int32), T.indices[mask])
     assert np.array_equal(ld("ov", np.float64), T.data[mask])
     assert list(ld("codes", np.int64)) == [0, 1, 2, 1]
+    # rows-pass order: windows of 1024 rows, longest first, ties in row order
+    lens = np.diff(rp)
+    want = np.concatenate([w0 + np.argsort(-lens[w0:w0 + 1024], kind="stable") for w0 in range(0, nr, 1024)])
+    assert np.array_equal(ld("perm", np.int32), want)
