@@ -119,10 +119,6 @@ typedef struct ipm_options {
                          /* on the device; both give the same bytes (0)                        */
   int system;            /* enum ipm_system (IPM_SYSTEM_CONDENSED); AUGMENTED needs storage F64 */
                          /* and precond JACOBI or AUTO (it always runs the Jacobi PCG)         */
-  int lp_stage;          /* reduced precision: stage the FP32 vector in shared memory by bulk   */
-                         /* copies (TMA) in the rows pass when n * 4 bytes fit (0: the staging */
-                         /* block holds 1024 threads per SM and measures slower, 105 against   */
-                         /* 72 us on the RT rows pass; same results bit for bit)               */
 } ipm_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -241,7 +237,10 @@ int ipm_solve_query(ipm_handle* h);
  * each handle keeps its own data, schedule and scalars.  ipm_batch_create captures the graph
  * (after ipm_set_qp on every handle); ipm_batch_solve launches it behind `stream`, waits, and
  * stores each handle's result (read it with ipm_get_xyz); statuses (count ints) may be NULL.
- * A batch is invalidated by ipm_set_qp or ipm_destroy on any of its handles. */
+ * A batch is invalidated by ipm_set_qp, ipm_share_qp, ipm_set_lowrank or ipm_destroy on any of
+ * its handles: after the first three ipm_batch_solve returns IPM_ERR_STATE without launching
+ * anything (each handle carries a generation count that the batch checks); after
+ * ipm_destroy of a member the batch must not be used at all. */
 typedef struct ipm_batch ipm_batch;
 int ipm_batch_create(ipm_handle* const* handles, int count, int flags, ipm_batch** out);
 int ipm_batch_solve(ipm_batch* b, void* stream, int* statuses);
@@ -369,7 +368,9 @@ int ipm_profile_operator(ipm_handle* h, int reps, double* ms_rows, double* ms_co
  * before any work.  The first call on a device looks up the array's device address (with
  * that device current); make that first call before any stream capture.  All calls share
  * the array: calls that overlap on the GPU race, so serialise them.  Work is queued on
- * `stream` (device pointers only); returns IPM_ERR_ARG for NULL or negative arguments. */
+ * `stream` (device pointers only).  IPM_ERR_ARG for n < 1, nR < 0 or any NULL pointer (R's three
+ * arrays and omega may be NULL only when nR = 0), checked before the size limit, so no call
+ * with a NULL pointer launches anything. */
 #define IPM_STATIC_SCRATCH_ROWS 262144
 int ipm_apply_operator_static(int64_t n, int64_t nR, const int64_t* R_indptr, const int32_t* R_indices,
                               const double* R_data, const int64_t* RT_indptr, const int32_t* RT_indices,

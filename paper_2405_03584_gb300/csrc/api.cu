@@ -112,6 +112,10 @@ struct ipm_handle {
   double* htrace = nullptr;         // pinned: trace rows copied back after a solve
   int trace_cap = 0;
   int pending = 0;                  // an asynchronous solve was launched and not yet waited for
+  // Bumped whenever the buffers or kernel parameters that a captured solve graph holds change
+  // (arena freed, QP reloaded or shared, low-rank column count changed); a batch records it
+  // per member at ipm_batch_create and refuses to launch on a mismatch.
+  uint64_t gen = 0;
   int pending_pc = 0, pending_warm = 0;
   std::chrono::steady_clock::time_point t_launch;
 };
@@ -158,6 +162,7 @@ int fetch_into(ipm_handle* h, const T* src, int64_t n, int mem, T* dst) {
 }
 
 void destroy_graphs(ipm_handle* h) {
+  h->gen++;
   for (auto& g : h->graphs) {
     for (int w = 0; w < 2; ++w) {
       if (g.solve[w]) cudaGraphExecDestroy(g.solve[w]);
@@ -731,7 +736,6 @@ void ipm_default_options(ipm_options* o) {
   o->warm_rho = 1e-5;
   o->u_cap = 0;
   o->ingest_host = 0;
-  o->lp_stage = 0;
   o->system = IPM_SYSTEM_CONDENSED;
 }
 
@@ -1063,8 +1067,6 @@ static int load_qp(ipm_handle* h, const ipm_qp* qp, int64_t m_ar, void* stream) 
   dv.g_at = heuristic_group((double)nnzAT / (double)n);
   if (h->opt.lanes_rows) dv.g_rows = h->opt.lanes_rows;
   if (h->opt.lanes_cols) dv.g_cols = h->opt.lanes_cols;
-  dv.lp_stage = (h->opt.storage != IPM_STORAGE_F64 && h->opt.lp_stage) ? 1 : 0;
-  if (dv.lp_stage) CUDA_TRY(h, prepare_lp_staging());
   dv.aug = h->opt.system == IPM_SYSTEM_AUGMENTED ? 1 : 0;
   dv.nsys = dv.aug ? n + m : n;
   h->d = dv;
@@ -1352,8 +1354,6 @@ int ipm_share_qp(ipm_handle* h, ipm_handle* src, void* stream) {
   carve_state(cvs, dv, n, m, nR, stiff_cap, sc_cap, use_dense, h->opt.storage, h->opt.max_ipm);
   if (h->opt.lanes_rows) dv.g_rows = h->opt.lanes_rows;
   if (h->opt.lanes_cols) dv.g_cols = h->opt.lanes_cols;
-  dv.lp_stage = (h->opt.storage != IPM_STORAGE_F64 && h->opt.lp_stage) ? 1 : 0;
-  if (dv.lp_stage) CUDA_TRY(h, prepare_lp_staging());
   dv.aug = h->opt.system == IPM_SYSTEM_AUGMENTED ? 1 : 0;
   dv.nsys = dv.aug ? n + m : n;
   h->d = dv;
@@ -1778,6 +1778,7 @@ int ipm_step_lengths(ipm_handle* h, const double* dx, const double* ds, const do
 
 struct ipm_batch {
   std::vector<ipm_handle*> hs;
+  std::vector<uint64_t> gens;       // each member's ipm_handle::gen when the graph was captured
   cudaStream_t st = nullptr;
   cudaEvent_t ev = nullptr, fork = nullptr;
   std::vector<cudaEvent_t> join;
@@ -1807,6 +1808,7 @@ int ipm_batch_create(ipm_handle* const* handles, int count, int flags, ipm_batch
   ipm_batch* b = new (std::nothrow) ipm_batch();
   if (!b) return IPM_ERR_OOM;
   b->hs.assign(handles, handles + count);
+  for (int i = 0; i < count; ++i) b->gens.push_back(handles[i]->gen);
   b->join.assign(count, nullptr);
   auto bad = [&](ipm_handle* h, const std::string& m) {
     if (h) h->err = m;
@@ -1852,8 +1854,15 @@ int ipm_batch_solve(ipm_batch* b, void* stream, int* statuses) {
   ipm_handle* h0 = b->hs[0];
   if (cudaSetDevice(h0->device) != cudaSuccess) return IPM_ERR_CUDA;
   const auto t0 = std::chrono::steady_clock::now();
+  for (size_t i = 0; i < b->hs.size(); ++i) {
+    ipm_handle* h = b->hs[i];
+    if (h->pending || !h->loaded) return fail(h, IPM_ERR_STATE, "batch member busy or without a QP");
+    // the captured graph holds this member's buffers and kernel parameters as they were at
+    // ipm_batch_create; after a reload, ipm_share_qp or ipm_set_lowrank they are gone or stale
+    if (h->gen != b->gens[i])
+      return fail(h, IPM_ERR_STATE, "batch member changed since ipm_batch_create (create the batch again)");
+  }
   for (ipm_handle* h : b->hs) {
-    if (h->pending || !h->loaded) return IPM_ERR_STATE;
     push_options(h);
     h->hs->eta_override = 0;
     h->hs->trace_cap = h->trace_cap;

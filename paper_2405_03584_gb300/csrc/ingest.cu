@@ -40,20 +40,20 @@ void par_copy(void* dst, const void* src, size_t nbytes) {
 }
 
 int check_csr_entries(int64_t nnz, const int32_t* idx, const double* val, int64_t ncols) {
-  std::atomic<int> bad{0};
+  // each thread finds the first bad entry of its range; the answer is the code of the first
+  // bad entry overall, as the sequential scan would report it
   const int T = nnz < (1 << 20) ? 1 : host_threads();
-  parallel_ranges(nnz, T, [&](int, int64_t b, int64_t e) {
-    int my = 0;
+  std::vector<int64_t> first((size_t)T, -1);
+  std::vector<int> code((size_t)T, 0);
+  parallel_ranges(nnz, T, [&](int t, int64_t b, int64_t e) {
     for (int64_t k = b; k < e; ++k) {
-      if (idx[k] < 0 || idx[k] >= ncols) { my = 1; break; }
-      if (!std::isfinite(val[k])) { my = 2; break; }
-    }
-    if (my) {
-      int z = 0;
-      bad.compare_exchange_strong(z, my);
+      if (idx[k] < 0 || idx[k] >= ncols) { first[t] = k; code[t] = 1; break; }
+      if (!std::isfinite(val[k])) { first[t] = k; code[t] = 2; break; }
     }
   });
-  return bad.load();
+  for (int t = 0; t < T; ++t)   // ranges are in order: the first thread with a bad entry wins
+    if (first[t] >= 0) return code[t];
+  return 0;
 }
 
 void transpose_csr(int64_t nrows, int64_t ncols, const int64_t* rp, const int32_t* ri, const double* rv,

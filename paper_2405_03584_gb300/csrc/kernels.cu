@@ -1222,7 +1222,6 @@ __global__ void k_stiff_corr(Dev d, int init) {
     }
     if (init) {
       d.p[j] = zj;
-    if (d.p32) d.p32[j] = (float)zj;
       if (d.p32) d.p32[j] = (float)zj;
     }
     rz = fma(d.r[j], zj, rz);

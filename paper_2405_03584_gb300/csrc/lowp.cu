@@ -232,139 +232,6 @@ __global__ void k_op_rows_lp(Dev d, int standalone) {
   }
 }
 
-// ---------------------------------------------------------------- staged rows pass
-//
-// The same rows pass with the FP32 vector p32 staged in shared memory by the bulk-copy (TMA)
-// engine: one block of 1024 threads per SM, thread 0 arms an mbarrier with the byte count
-// and issues cp.async.bulk copies of p32 (16-byte aligned, whole 16-byte units) into dynamic
-// shared memory; every thread waits on the barrier's phase (bounded: after kLpWaitLimit
-// polls the block records DS_TIMEOUT, stops the PCG loop and waits once more, bounded, for
-// its copies before leaving), then the gathers of the row dots read shared memory instead
-// of L1/L2.  Used when options.lp_stage is set and n * 4 bytes fit the block's shared
-// memory.  Measured on the RT rows pass (BF16): 105 us staged against 72 us for the gathers
-// from L1/L2 -- the 224 KB staging buffer allows one block of 1024 threads per SM, half the
-// resident warps of the unstaged pass, and this pass is bound by load latency; so the
-// option is off by default.
-constexpr int kLpWaitLimit = 1 << 22;
-constexpr int kLpStageMaxBytes = 224 * 1024;   // dynamic shared memory of the staging block
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  uint32_t done = 0;
-  for (int it = 0; it < kLpWaitLimit && !done; ++it) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-  }
-  return done != 0;
-}
-
-// Copies nbytes (a multiple of 16, 16-byte aligned at both ends) from global src into shared
-// dst, completing on the mbarrier bar; called by one thread.
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t nbytes, uint32_t bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(nbytes) : "memory");
-  constexpr uint32_t kChunk = 32768;
-  for (uint32_t off = 0; off < nbytes; off += kChunk) {
-    const uint32_t sz = nbytes - off < kChunk ? nbytes - off : kChunk;
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(static_cast<char*>(dst) + off)),
-        "l"(static_cast<const char*>(src) + off), "r"(sz), "r"(bar)
-        : "memory");
-  }
-}
-
-// FP32 dot of a stored row with the staged vector (as group_row_dot_lp, gathers from shared).
-template <int S, int G>
-__device__ __forceinline__ float group_row_dot_lp_s(const int64_t beg, const int64_t end, const int gl,
-                                                    const int32_t* __restrict__ idx,
-                                                    const typename StorageT<S>::T* __restrict__ val,
-                                                    const float* __restrict__ xs) {
-  constexpr int C = Chunk<S>::C;
-  float a = 0.f;
-  int64_t a0 = (beg + C - 1) & ~(int64_t)(C - 1);
-  if (a0 > end) a0 = end;
-  for (int64_t e = beg + gl; e < a0; e += G) a = fmaf(StorageT<S>::dec(val[e]), xs[__ldg(idx + e)], a);
-  const int64_t nch = (end - a0) / C;
-  int64_t c = gl;
-  for (; c + G < nch; c += 2 * G) {
-    const int64_t e0 = a0 + c * C, e1 = e0 + (int64_t)G * C;
-    float v0[C], v1[C];
-    int i0[C], i1[C];
-    Chunk<S>::load(val + e0, v0);
-    Chunk<S>::load(val + e1, v1);
-#pragma unroll
-    for (int k = 0; k < C / 4; ++k) {
-      const int4 t0 = __ldg(reinterpret_cast<const int4*>(idx + e0) + k);
-      const int4 t1 = __ldg(reinterpret_cast<const int4*>(idx + e1) + k);
-      i0[4 * k] = t0.x; i0[4 * k + 1] = t0.y; i0[4 * k + 2] = t0.z; i0[4 * k + 3] = t0.w;
-      i1[4 * k] = t1.x; i1[4 * k + 1] = t1.y; i1[4 * k + 2] = t1.z; i1[4 * k + 3] = t1.w;
-    }
-#pragma unroll
-    for (int k = 0; k < C; ++k) a = fmaf(v0[k], xs[i0[k]], a);
-#pragma unroll
-    for (int k = 0; k < C; ++k) a = fmaf(v1[k], xs[i1[k]], a);
-  }
-  if (c < nch) {
-    const int64_t e0 = a0 + c * C;
-    float v0[C];
-    int i0[C];
-    Chunk<S>::load(val + e0, v0);
-#pragma unroll
-    for (int k = 0; k < C / 4; ++k) {
-      const int4 t0 = __ldg(reinterpret_cast<const int4*>(idx + e0) + k);
-      i0[4 * k] = t0.x; i0[4 * k + 1] = t0.y; i0[4 * k + 2] = t0.z; i0[4 * k + 3] = t0.w;
-    }
-#pragma unroll
-    for (int k = 0; k < C; ++k) a = fmaf(v0[k], xs[i0[k]], a);
-  }
-  for (int64_t e = a0 + nch * C + gl; e < end; e += G) a = fmaf(StorageT<S>::dec(val[e]), xs[__ldg(idx + e)], a);
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-  return a;
-}
-
-template <int S, int G>
-__global__ void __launch_bounds__(1024, 1) k_op_rows_lp_staged(Dev d, int standalone) {
-  extern __shared__ __align__(16) float xs[];
-  __shared__ __align__(8) uint64_t bar;
-  if (!standalone && d.sc->cg_done) return;
-  const uint32_t nbytes = (uint32_t)(((d.n + 3) & ~int64_t(3)) * 4);
-  const uint32_t b = smem_addr(&bar);
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) bulk_load(xs, d.p32, nbytes, b);
-  if (!mbar_wait(b, 0)) {
-    if (threadIdx.x == 0) {
-      d.sc->status = DS_TIMEOUT;
-      d.sc->cg_done = 1;
-    }
-    mbar_wait(b, 0);                   // the copies may still land: wait once more, bounded
-    return;
-  }
-  using T = typename StorageT<S>::T;
-  const T* q = static_cast<const T*>(d.Rq);
-  const int gl = threadIdx.x & (G - 1);
-  FOR_GROUP_ROWS_L(G, r, ok, d.nR) {
-    const int64_t beg = ok ? d.R_ptr[r] : 0, end = ok ? d.R_ptr[r + 1] : 0;
-    const float t = group_row_dot_lp_s<S, G>(beg, end, gl, d.R_idx, q, xs);
-    if (ok && gl == 0) {
-      const double s = (double)d.scaleR[r];
-      d.w32[r] = (float)((d.wR[r] + d.thR[r]) * s * s * (double)t);
-    }
-  }
-}
-
 // q_j = sum_i q_ij w_i + Hs p + (h0 + sigma) p;  p^T q -> alpha (last block), as k_op_cols.
 template <int S, int G>
 __global__ void __launch_bounds__(256, 6) k_op_cols_lp(Dev d, int standalone) {
@@ -428,39 +295,9 @@ __global__ void __launch_bounds__(256, 6) k_op_cols_lp(Dev d, int standalone) {
     default: { constexpr int G = 32; __VA_ARGS__; } break;    \
   }
 
-// Whether the rows pass stages p32 in shared memory, and the launch of either form.
-static bool lp_staged(const Dev& d) {
-  return d.lp_stage && ((d.n + 3) & ~int64_t(3)) * 4 <= kLpStageMaxBytes;
-}
-
 static void launch_rows_lp(const Dev& d, const Geo& g, int standalone, cudaStream_t st) {
   if (!d.nR) return;
-  if (lp_staged(d)) {
-    const int smem = (int)(((d.n + 3) & ~int64_t(3)) * 4);
-    const int grid = d.sm_count > 0 ? d.sm_count : 148;
-    DISPATCH_SG(d.storage, d.g_rows, k_op_rows_lp_staged<S, G><<<grid, 1024, smem, st>>>(d, standalone));
-  } else {
-    DISPATCH_SG(d.storage, d.g_rows, k_op_rows_lp<S, G><<<g.gR, kBlock, 0, st>>>(d, standalone));
-  }
-}
-
-cudaError_t prepare_lp_staging() {
-  // the staged rows kernels need more than the default 48 KB of dynamic shared memory
-  cudaError_t e = cudaSuccess;
-  auto set = [&](const void* f) {
-    const cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kLpStageMaxBytes);
-    if (r != cudaSuccess && e == cudaSuccess) e = r;
-  };
-#define IPMK_SET_STAGED(S)                                             \
-  set((const void*)k_op_rows_lp_staged<S, 4>);                          \
-  set((const void*)k_op_rows_lp_staged<S, 8>);                          \
-  set((const void*)k_op_rows_lp_staged<S, 16>);                         \
-  set((const void*)k_op_rows_lp_staged<S, 32>);
-  IPMK_SET_STAGED(ST_F32)
-  IPMK_SET_STAGED(ST_BF16)
-  IPMK_SET_STAGED(ST_FP8)
-#undef IPMK_SET_STAGED
-  return e;
+  DISPATCH_SG(d.storage, d.g_rows, k_op_rows_lp<S, G><<<g.gR, kBlock, 0, st>>>(d, standalone));
 }
 
 cudaError_t launch_op_lp(const Dev& d, const Geo& g, cudaStream_t st) {

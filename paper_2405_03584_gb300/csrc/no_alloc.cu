@@ -77,8 +77,10 @@ extern "C" int ipm_apply_operator_static(int64_t n, int64_t nR, const int64_t* R
                                          const double* R_data, const int64_t* RT_indptr, const int32_t* RT_indices,
                                          const double* RT_data, const double* omega, const double* dg,
                                          const double* p, double* q, void* stream) {
-  if (n < 1 || nR < 0 || !RT_indptr || !dg || !p || !q) return IPM_ERR_ARG;
-  if (nR > 0 && (!R_indptr || !omega)) return IPM_ERR_ARG;
+  // every pointer a launch below would dereference is checked before the size check, so a
+  // NULL never reaches the device
+  if (n < 1 || nR < 0 || !RT_indptr || !RT_indices || !RT_data || !dg || !p || !q) return IPM_ERR_ARG;
+  if (nR > 0 && (!R_indptr || !R_indices || !R_data || !omega)) return IPM_ERR_ARG;
   if (nR > kStaticRows) return IPM_ERR_TOO_LARGE;
   double* v = nullptr;
   int rc = static_scratch(&v);

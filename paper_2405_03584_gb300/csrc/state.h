@@ -68,7 +68,6 @@ struct Dev {
   double* chol_diag;           // max(n_dense, stiff_cap): original diagonal during a factorisation
   // reduced-precision copy of the matrix values (storage != ST_F64): R~_ij = scaleR_i * q_ij
   int storage;
-  int lp_stage;                // stage p32 in shared memory in the reduced-precision rows pass
   void *Rq, *RTq;              // nnzR values each (float / bf16 / fp8-e4m3), indices shared with R, R^T
   float* scaleR;               // nR
   float *p32, *w32;            // FP32 mirror of p (n) and the rows-pass result (nR)
@@ -119,7 +118,6 @@ cudaError_t launch_cg_body(const Dev& d, const Geo& g, int precond, cudaGraphCon
 // ---- reduced-precision operator and FP64 refinement (lowp.cu) ----
 cudaError_t launch_quantize(const Dev& d, cudaStream_t st);
 cudaError_t launch_op_lp(const Dev& d, const Geo& g, cudaStream_t st);
-cudaError_t prepare_lp_staging();   // once per process: shared-memory limit of the staged kernels
 cudaError_t launch_op_rows_lp_only(const Dev& d, const Geo& g, cudaStream_t st);   // measurement
 cudaError_t launch_op_cols_lp_only(const Dev& d, const Geo& g, cudaStream_t st);
 cudaError_t launch_mirror_p32(const Dev& d, const Geo& g, cudaStream_t st);

@@ -44,7 +44,7 @@ class Options(C.Structure):
                 ("equal_steps", C.c_int), ("autotune", C.c_int), ("use_graphs", C.c_int),
                 ("storage", C.c_int), ("refine_max", C.c_int), ("refine_eta", C.c_double),
                 ("lanes_rows", C.c_int), ("lanes_cols", C.c_int), ("warm_rho", C.c_double),
-                ("u_cap", C.c_int), ("ingest_host", C.c_int), ("system", C.c_int), ("lp_stage", C.c_int)]
+                ("u_cap", C.c_int), ("ingest_host", C.c_int), ("system", C.c_int)]
 
 
 class QP(C.Structure):

@@ -76,14 +76,26 @@ def test_static_operator_argument_checks(lib):
     """The allocation-free operator refuses bad arguments and sizes beyond its fixed scratch
     before any device work (the pointers below are never dereferenced)."""
     f = lib.ipm_apply_operator_static
-    dummy = C.c_void_p(16)
-    assert f(0, 0, None, None, None, dummy, None, None, None, dummy, dummy, dummy, None) == ipm.IPM_ERR_ARG
-    assert f(10, -1, None, None, None, dummy, None, None, None, dummy, dummy, dummy, None) == ipm.IPM_ERR_ARG
-    assert f(10, 5, None, None, None, dummy, None, None, None, dummy, dummy, dummy, None) == ipm.IPM_ERR_ARG
-    assert f(10, 5, dummy, None, None, dummy, None, None, dummy, dummy, dummy, None, None) == ipm.IPM_ERR_ARG
+    d = C.c_void_p(16)
+    ok = [d] * 10          # R_indptr, R_indices, R_data, RT_indptr, RT_indices, RT_data, omega, dg, p, q
+    assert f(0, 0, *ok, None) == ipm.IPM_ERR_ARG
+    assert f(10, -1, *ok, None) == ipm.IPM_ERR_ARG
+    # each pointer NULL in turn, at a small nR: refused before any launch
+    for k in range(10):
+        args = list(ok)
+        args[k] = None
+        assert f(10, 5, *args, None) == ipm.IPM_ERR_ARG, k
+    # with nR = 0 the arrays of R and omega are not needed; those of R^T still are
+    for k in range(10):
+        args = list(ok)
+        args[k] = None
+        want = ipm.IPM_ERR_ARG if k in (3, 4, 5, 7, 8, 9) else None
+        if want is not None:
+            assert f(10, 0, *args, None) == want, k
     too_many = (1 << 18) + 1
-    assert f(10, too_many, dummy, None, None, dummy, None, None, dummy, dummy, dummy, dummy, None) == \
-        ipm.IPM_ERR_TOO_LARGE
+    assert f(10, too_many, *ok, None) == ipm.IPM_ERR_TOO_LARGE
+    # a NULL pointer is reported as such even beyond the size limit
+    assert f(10, too_many, d, None, d, d, d, d, d, d, d, d, None) == ipm.IPM_ERR_ARG
 
 
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):

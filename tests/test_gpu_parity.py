@@ -324,21 +324,6 @@ def test_async_and_batch_match_sync():
         s.close()
 
 
-@pytest.mark.parametrize("storage", ["f32", "bf16", "fp8"])
-def test_staged_rows_pass_equals_unstaged(storage):
-    """The reduced-precision rows pass with p32 staged in shared memory by bulk copies gives
-    the same bits as the pass that gathers from global memory."""
-    p = W.rt_qp(n=3001, seed=61)
-    xs = []
-    for stage in (1, 0):
-        with ipm.Solver(tol_kkt=1e-8, precond="jacobi_lr", storage=storage, lp_stage=stage) as s:
-            s.set_qp_rt(p)
-            assert s.solve() == ipm.IPM_OK
-            out = s.get()
-            xs.append((out["x"], out["info"]["cg_iters"], out["info"]["refine_passes"]))
-    assert np.array_equal(xs[0][0], xs[1][0]) and xs[0][1:] == xs[1][1:]
-
-
 @pytest.mark.parametrize("name,make", CASES[:3], ids=[c[0] for c in CASES[:3]])
 def test_augmented_system_direction(name, make):
     """PCG on the paper's doubly augmented system (Section 4, eq:2x2_augmented) gives the

@@ -57,6 +57,18 @@ int main(int argc, char** argv) {
   auto bad_v = rv;
   bad_v[nnz - 1] = NAN;
   codes[2] = ipmk::check_csr_entries(nnz, ri.data(), bad_v.data(), nc);
+  // a NaN early and a bad index late (different thread ranges), and the other way round: the
+  // code of the first bad entry, whatever thread finishes first
+  auto both_i = ri;
+  auto both_v = rv;
+  both_v[1] = NAN;
+  both_i[nnz - 2] = -1;
+  codes.push_back(ipmk::check_csr_entries(nnz, both_i.data(), both_v.data(), nc));
+  both_v[1] = rv[1];
+  both_v[nnz - 2] = NAN;
+  both_i[nnz - 2] = ri[nnz - 2];
+  both_i[2] = (int32_t)nc + 7;
+  codes.push_back(ipmk::check_csr_entries(nnz, both_i.data(), both_v.data(), nc));
   std::vector<double> cp(nnz);
   ipmk::par_copy(cp.data(), rv.data(), sizeof(double) * nnz);
   codes.push_back(cp == rv ? 1 : 0);
@@ -115,7 +127,7 @@ def test_host_transpose_filter_and_checks(driver, tmp_path, n, density, seed):
     assert np.array_equal(ld("op", np.int64), op)
     assert np.array_equal(ld("oi", np.int32), T.indices[mask])
     assert np.array_equal(ld("ov", np.float64), T.data[mask])
-    assert list(ld("codes", np.int64)) == [0, 1, 2, 1]
+    assert list(ld("codes", np.int64)) == [0, 1, 2, 2, 1, 1]
     # rows-pass order: windows of 1024 rows, longest first, ties in row order
     lens = np.diff(rp)
     want = np.concatenate([w0 + np.argsort(-lens[w0:w0 + 1024], kind="stable") for w0 in range(0, nr, 1024)])
