@@ -35,7 +35,7 @@ METRIC = "QP solves/sec & p50/p99 latency at rel. KKT <=1e-6; PCG SpMV HBM GB/s"
 N_FULL, SEED, TOL = 50_000, 1, 1e-6
 WORKLOAD = ("RT-shaped QP: D 200000 voxels x 50000 spots, 0.5% banded lognormal, H = D^T W D + 1e-4 I "
             "matrix-free, A = 20000 organ rows (b = 0.6), 0 <= x <= 5, FP64, seed 1")
-SAMPLE_N = 4000                 # oracle sample: same generator at n = 4000 (V = 16000, m = 1600)
+SAMPLE_SIZES = (2000, 3000, 4000)   # oracle samples: the same generator at these n (V = 4n)
 FALLBACK_HBM_GBS = 6800.0
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 (non-tensor) nominal rate
 
@@ -160,19 +160,44 @@ def _ncu_traffic(kernel, lanes):
     return None
 
 
-def _oracle_sample(sample_n=SAMPLE_N):
-    """The CPU oracle as it stands: one full solve of the same generator at n = sample_n,
-    scaled to the full size by the O(n^3) cost of its dense Newton steps."""
+def _oracle_time(n):
+    """The CPU oracle as it stands: one full solve of the same generator at n variables
+    (V = 4n voxels, m = n/2.5 organ rows), wall-clock seconds of the oracle alone."""
     from oracle import ipm as O
     from paper_2405_03584_gb300 import workloads as W
-    p = W.rt_qp(n=sample_n, seed=SEED)
+    p = W.rt_qp(n=n, seed=SEED)
     t0 = time.perf_counter()
     qp = O.from_rt(p)
     it, info = O.solve(qp, tol=TOL)
     t = time.perf_counter() - t0
-    scale = (N_FULL / sample_n) ** 3
-    return dict(seconds=t, scale=scale, ipm_iters=info.iterations, status=info.status,
-                solves_per_s=1.0 / (t * scale))
+    return dict(n=n, seconds=t, ipm_iters=info.iterations, status=info.status)
+
+
+def power_law(points):
+    """Least-squares fit of log t = log a + b log n over measured (n, seconds) points; with
+    one size only the exponent of the oracle's dense Cholesky steps (3) is assumed."""
+    ns = np.array([float(q[0]) for q in points])
+    ts = np.array([float(q[1]) for q in points])
+    if len(set(ns.tolist())) < 2:
+        b = 3.0
+        a = float(np.exp(np.mean(np.log(ts) - b * np.log(ns))))
+        return a, b, False
+    b, la = np.polyfit(np.log(ns), np.log(ts), 1)
+    return float(np.exp(la)), float(b), True
+
+
+def _cpu_law(points):
+    """Full-size oracle rate from the measured points and its description."""
+    a, b, fitted = power_law([(q["n"], q["seconds"]) for q in points])
+    t_full = a * N_FULL ** b
+    by_n = {}
+    for q in points:
+        by_n.setdefault(q["n"], []).append(q["seconds"])
+    pts = ", ".join("n=%d: %.2f s" % (n, statistics.mean(v)) for n, v in sorted(by_n.items()))
+    law = ("t(n) = %.3g * n^%.2f s, %s over the measured sizes (%s)" %
+           (a, b, "least-squares fit" if fitted else "exponent 3 assumed (one size)", pts))
+    return 1.0 / t_full, law, {"coef": a, "exponent": b, "fitted": fitted, "t_full_s": t_full,
+                                "points": [[q["n"], q["seconds"], q["ipm_iters"]] for q in points]}
 
 
 def run_reference(args):
@@ -180,21 +205,25 @@ def run_reference(args):
     if rank != 0:
         return 0
     cores = _cores_used()
-    times = []
+    sizes = args.sample_sizes
+    pts, step_s = [], []
     for k in range(args.warmup + args.steps):
-        r = _oracle_sample(args.sample_n)
+        n = sizes[k % len(sizes)]
+        r = _oracle_time(n)
         if k >= args.warmup:
-            times.append(r["seconds"] * r["scale"])
-    tot = sum(times)
-    value = args.steps / tot
-    sample = ("oracle (dense-Cholesky FP64 IPM) full solve of the same RT generator at n=%d, V=%d, m=%d "
-              "(%.1f s each), scaled by (50000/%d)^3" % (args.sample_n, 4 * args.sample_n, 4 * args.sample_n // 10,
-                                                         statistics.mean([t / r["scale"] for t in times]), args.sample_n))
+            pts.append(r)
+            step_s.append(r["seconds"])
+    value, law, fit = _cpu_law(pts)
+    sample = ("oracle (dense-Cholesky FP64 IPM) full solves of the same RT generator at n in %s (V = 4n, "
+              "m = n/2.5), one size per step; full-size rate from %s" % (list(sizes), law))
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(step_s),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "l2": "host run"},
-           "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
+           "config": {"workload": WORKLOAD, "l2": "host run",
+                      "step": "one oracle solve at a sample size (ms_per_step is the measured mean); value is "
+                              "the full-size rate from the fitted law"},
+           "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample,
+                            "fit": fit},
            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0
@@ -251,12 +280,15 @@ def run_batch(args):
         st = b.solve()
     stream = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     torch.cuda.synchronize()
     ev[0].record(stream)
     for _ in range(args.steps):
         st = b.solve()
     ev[1].record(stream)
     torch.cuda.synchronize()
+    clk = clocks.stop()
     ms = ev[0].elapsed_time(ev[1]) / args.steps
     infos = [sv.get()["info"] for sv in solvers]
     b.close()
@@ -284,7 +316,8 @@ def run_batch(args):
            "ipm_iters": [i["ipm_iters"] for i in infos], "lanes": [[i["lanes_rows"], i["lanes_cols"]] for i in infos],
            "baseline_sequential_f64": {"value": count / (seq_ms / 1000.0), "unit": "solves/s", "ms_total": seq_ms,
                                        "status": [int(x) for x in seq_status]},
-           "speedup_vs_sequential_f64": seq_ms / ms, "setup_s": {"generate": t_gen, "load": t_load}}
+           "speedup_vs_sequential_f64": seq_ms / ms, "setup_s": {"generate": t_gen, "load": t_load},
+           "clocks": clk}
     print(json.dumps(out), flush=True)
     return 0
 
@@ -324,8 +357,11 @@ def run_serve(args):
                             n_plans=len(plans), seed=4)
     common = dict(budget_bytes=120e9, tol_kkt=TOL, precond="jacobi_lr")
     t0 = time.perf_counter()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     ours, qrec = _serve_once(plans, reqs, args.serve_horizon, max_inflight=args.serve_inflight, warm=True,
                              keep_x=False, storage="bf16", **common)
+    clk = clocks.stop()
     t_ours = time.perf_counter() - t0
     base = None
     if not args.serve_no_baseline:
@@ -343,7 +379,7 @@ def run_serve(args):
                       "budget_bytes": 120e9},
            "ours": ours,
            "baseline_f64_one_at_a_time": base,
-           "setup_s": {"generate": t_gen, "serve_run": t_ours}}
+           "setup_s": {"generate": t_gen, "serve_run": t_ours}, "clocks": clk}
     if base:
         out["speedup_solves_per_s"] = ours["solves_per_s"] / base["solves_per_s"]
         out["p99_ratio_baseline_over_ours"] = base["p99_ms"] / ours["p99_ms"]
@@ -431,6 +467,8 @@ def run_sqp(args):
     D = sp.csr_matrix((p["D_data"], p["D_indices"], p["D_indptr"]), shape=(p["V"], p["n"]))
     A = D[p["a_rows"]]
     runs = {}
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     for warm in (True, False):
         obj = sqp.DoseObjective(D, p["target"], p["presc"], p["organ"], p["soft_max"], p["w_target"], p["w_organ"])
         with ipm.Solver(tol_kkt=TOL, precond="jacobi_lr", u_cap=200, stiff_max=1024) as s:
@@ -448,8 +486,9 @@ def run_sqp(args):
             "qp_cg_iters_mean": float(np.mean([r["qp_cg_iters"] for r in h])),
             "max_u_cols": max(r["u_cols"] for r in h), "qp_not_ok": int(sum(r["qp_status"] != 0 for r in h)),
             "objective_evals": obj.evals}
+    clk = clocks.stop()
     w, c = runs["warm"], runs["cold"]
-    out = {"mode": "sqp", "metric": "QP sub-problems solved per second inside the SQP loop (rel. KKT <= 1e-6)",
+    out = {"mode": "sqp", "clocks": clk, "metric": "QP sub-problems solved per second inside the SQP loop (rel. KKT <= 1e-6)",
            "value": w["sqp_iterations"] / w["qp_s_total"], "unit": "QP/s", "dtype": "f64",
            "config": {"n": p["n"], "V": p["V"], "m": int(p["a_rows"].size), "nnz_D": int(p["D_indptr"][-1]),
                       "u_cap": 200, "sqp_tol": 1e-4,
@@ -478,11 +517,14 @@ def run_dense(args):
         s.solve()
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     torch.cuda.synchronize()
     e0.record(stream)
     sts = [s.solve() for _ in range(args.steps)]
     e1.record(stream)
     torch.cuda.synchronize()
+    clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     out = s.get()
     info = out["info"]
@@ -502,7 +544,7 @@ def run_dense(args):
            "us_per_ipm_iter": 1000.0 * ms / max(info["ipm_iters"], 1),
            "us_per_pcg_iter_upper_bound": 1000.0 * ms / max(info["cg_iters"], 1),
            "rel_kkt_device": info["rel_kkt"],
-           "gpu_launches": int(info["kernel_launches"]),
+           "gpu_launches": int(info["kernel_launches"]), "clocks": clk,
            "cpu_baseline": {"value": 1.0 / t_or, "unit": "solves/s", "cores": _cores_used(), "kind": "oracle",
                             "sample": "the whole oracle solve of the same QP (%d IPM iterations), best of 3 "
                                       "after a warm-up solve" % rinfo.iterations}}
@@ -569,7 +611,7 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2405_03584_gb300 import build, ipm, workloads as W
+    from paper_2405_03584_gb300 import build, ipm, presets, workloads as W
 
     rank, world, local = _env_rank()
     if world > 1:
@@ -580,8 +622,10 @@ def run_ours(args):
     build.build()
     dev = torch.cuda.current_device()
     p = W.rt_qp(n=N_FULL, seed=SEED)
-    s = ipm.Solver(tol_kkt=TOL, precond="jacobi_lr" if args.system == "condensed" else "jacobi",
-                   use_graphs=0 if args.no_graphs else 1, autotune=1, storage=args.storage, system=args.system)
+    opts = presets.rt(args.storage)
+    if args.system != "condensed":
+        opts.update(system=args.system, precond="jacobi")
+    s = ipm.Solver(use_graphs=0 if args.no_graphs else 1, **opts)
     s.set_qp_rt(p)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -640,32 +684,38 @@ def run_ours(args):
         q.update(pin)
         h2d = sum(v.nbytes for v in pin.values())
         d2h = 8 * (3 * p["n"] + 2 * p["m"])
-        e2e_t = []
-        for k in range(args.e2e_steps + 1):
+        def e2e_once():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            se = ipm.Solver(tol_kkt=TOL, precond="jacobi_lr", autotune=1, storage=args.storage)
+            se = ipm.Solver(**opts)
             se.set_qp_rt(q)
             se.solve()
             se.get()
             se.close()
             torch.cuda.synchronize()
-            if k:
-                e2e_t.append(time.perf_counter() - t0)
+            return time.perf_counter() - t0
+
+        e2e_once()                                   # untimed: first-call costs of the process
+        e2e_t = [e2e_once() for _ in range(args.e2e_steps)]
+        ipm.autotune_reset()                         # one more with the autotuner's cache emptied
+        t_cold = e2e_once()
         e2e_val = len(e2e_t) / sum(e2e_t)
         if world > 1:
             e2e_val = replica_rate(len(e2e_t), world, 1000.0 * max_over_ranks(sum(e2e_t)))
         e2e = {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "steps": len(e2e_t), "includes": "ipm_create + ipm_set_qp (host arrays, pinned) + ipm_solve + ipm_get_xyz",
-               "options": "as the device-timed solve (autotuned lanes, cached per matrix signature by the untimed first pass)"}
+               "options": "as the device-timed solve; lanes from the autotuner's per-process cache (filled by the "
+                          "untimed first pass)",
+               "cold_autotune": {"value": 1.0 / t_cold, "unit": "solves/s", "seconds": t_cold,
+                                 "note": "one more step after ipm_autotune_reset: ipm_set_qp times the lane widths again"}}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r = _oracle_sample(args.sample_n)
-        cpu = {"value": r["solves_per_s"], "unit": "solves/s", "cores": _cores_used(), "kind": "oracle",
-               "sample": "oracle (dense-Cholesky FP64 IPM) full solve of the same RT generator at n=%d, V=%d, m=%d "
-                         "in %.1f s (%d IPM iterations), scaled by (50000/%d)^3" %
-                         (args.sample_n, 4 * args.sample_n, 4 * args.sample_n // 10, r["seconds"], r["ipm_iters"],
-                          args.sample_n)}
+        pts = [_oracle_time(n) for n in args.sample_sizes]
+        v, law, fit = _cpu_law(pts)
+        cpu = {"value": v, "unit": "solves/s", "cores": _cores_used(), "kind": "oracle",
+               "sample": "oracle (dense-Cholesky FP64 IPM) full solves of the same RT generator at n in %s "
+                         "(V = 4n, m = n/2.5); full-size rate from %s" % (list(args.sample_sizes), law),
+               "fit": fit}
     if rank == 0:
         lat_sorted = sorted(lat)
         p99 = lat_sorted[min(len(lat_sorted) - 1, int(np.ceil(0.99 * len(lat_sorted))) - 1)]
@@ -696,10 +746,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--sample-n", type=int, default=SAMPLE_N,
-                    help="n of the oracle sample behind cpu_baseline and --impl reference")
+    ap.add_argument("--sample-n", default=",".join(str(v) for v in SAMPLE_SIZES),
+                    help="comma-separated n of the oracle samples behind cpu_baseline and --impl reference")
     ap.add_argument("--operator-only", action="store_true",
                     help="profiler capture target: a few IPM iterations, then the operator kernels")
     ap.add_argument("--lanes", default="8,16", help="--operator-only: lanes per row over R and R^T")
@@ -727,6 +777,7 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    args.sample_sizes = tuple(int(v) for v in str(args.sample_n).split(",") if v.strip())
     if args.impl == "reference":
         return run_reference(args)
     if args.operator_only:

@@ -42,12 +42,16 @@ enum ipm_status {
   IPM_ERR_ARG = 1,               /* invalid argument (sizes, NULL, non-finite data, bad layout) */
   IPM_ERR_OOM = 2,               /* device allocation failed or exceeds options.mem_budget      */
   IPM_MAX_ITER = 3,              /* options.max_ipm iterations without reaching tol_kkt         */
-  IPM_CG_STALL = 4,              /* PCG hit options.max_cg without meeting its tolerance        */
+  IPM_CG_STALL = 4,              /* PCG hit options.max_cg without meeting its tolerance in two */
+                                 /* consecutive Newton steps (the solve stops there)            */
   IPM_NUMERICAL = 5,             /* NaN/Inf in an iterate, PCG breakdown or step length -> 0    */
   IPM_INFEASIBLE_SUSPECTED = 6,  /* the multipliers diverge along a Farkas certificate of primal */
                                  /* infeasibility (y, z >= 0, A^T y - z_l + z_u ~ 0,            */
                                  /* b^T y - l^T z_l + u^T z_u < 0 after scaling)               */
-  IPM_ERR_TIMEOUT = 7,           /* host wall-clock limit options.timeout_ms exceeded           */
+  IPM_ERR_TIMEOUT = 7,           /* host wall-clock limit options.timeout_ms exceeded: the     */
+                                 /* solve keeps running on the device; collect it with         */
+                                 /* ipm_solve_wait (ipm_solve_query polls) before the handle's */
+                                 /* next call, which is refused with IPM_ERR_STATE until then  */
   IPM_ERR_CUDA = 8,              /* a CUDA runtime call failed (see ipm_last_error)             */
   IPM_ERR_STATE = 9,             /* call out of order (e.g. ipm_solve before ipm_set_qp)        */
   IPM_ERR_TOO_LARGE = 10,        /* size beyond the fixed scratch of ipm_apply_operator_static  */
@@ -119,6 +123,9 @@ typedef struct ipm_options {
                          /* on the device; both give the same bytes (0)                        */
   int system;            /* enum ipm_system (IPM_SYSTEM_CONDENSED); AUGMENTED needs storage F64 */
                          /* and precond JACOBI or AUTO (it always runs the Jacobi PCG)         */
+  int lanes_at;          /* lanes per row of the kernels over the stored A^T alone (right-hand  */
+                         /* side with the Jacobi diagonal, Jacobi diagonal): 4, 8, 16, 32; 0 =  */
+                         /* from its average row length                                        */
 } ipm_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -285,6 +292,12 @@ int ipm_device_bytes(const ipm_handle* h, int64_t* matrix_bytes, int64_t* state_
  * ipm_qp, ipm_info, ipm_cg_report), for bindings to check their own layouts.  Any pointer
  * may be NULL.  No counterpart in the paper. */
 int ipm_abi_sizes(int64_t* options, int64_t* qp, int64_t* info, int64_t* cg_report);
+
+/* Forgets the lane widths the autotuner (options.autotune) chose per matrix signature in this
+ * process, so that the next ipm_set_qp with autotune = 1 times the kernels again (a cold start,
+ * as in a fresh process).  Handles already loaded keep their widths.  No counterpart in the
+ * paper. */
+int ipm_autotune_reset(void);
 
 /* Frees the handle and its device memory.  NULL-safe. */
 int ipm_destroy(ipm_handle* h);

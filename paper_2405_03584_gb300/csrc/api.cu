@@ -335,7 +335,7 @@ int validate_options(const ipm_options& o) {
   // operator the refinement's inner PCG under it stalled near convergence (RT n = 900, FP8)
   if (o.precond == IPM_PRECOND_DENSE && o.storage != IPM_STORAGE_F64) return IPM_ERR_ARG;
   auto lanes_ok = [](int g) { return g == 0 || g == 4 || g == 8 || g == 16 || g == 32; };
-  if (!lanes_ok(o.lanes_rows) || !lanes_ok(o.lanes_cols)) return IPM_ERR_ARG;
+  if (!lanes_ok(o.lanes_rows) || !lanes_ok(o.lanes_cols) || !lanes_ok(o.lanes_at)) return IPM_ERR_ARG;
   return IPM_OK;
 }
 
@@ -733,6 +733,7 @@ void ipm_default_options(ipm_options* o) {
   o->refine_eta = 0.1;
   o->lanes_rows = 0;
   o->lanes_cols = 0;
+  o->lanes_at = 0;
   o->warm_rho = 1e-5;
   o->u_cap = 0;
   o->ingest_host = 0;
@@ -843,6 +844,12 @@ int ipm_set_lowrank(ipm_handle* h, int64_t u_cols, const double* U, const double
   CUDA_TRY(h, launch_diagH(d, h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));   // host staging buffers go out of scope
   return leave(h, stream);
+}
+
+int ipm_autotune_reset(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache.clear();
+  return IPM_OK;
 }
 
 int ipm_abi_sizes(int64_t* options, int64_t* qp, int64_t* info, int64_t* cg_report) {
@@ -1067,6 +1074,7 @@ static int load_qp(ipm_handle* h, const ipm_qp* qp, int64_t m_ar, void* stream) 
   dv.g_at = heuristic_group((double)nnzAT / (double)n);
   if (h->opt.lanes_rows) dv.g_rows = h->opt.lanes_rows;
   if (h->opt.lanes_cols) dv.g_cols = h->opt.lanes_cols;
+  if (h->opt.lanes_at) dv.g_at = h->opt.lanes_at;
   dv.aug = h->opt.system == IPM_SYSTEM_AUGMENTED ? 1 : 0;
   dv.nsys = dv.aug ? n + m : n;
   h->d = dv;
@@ -1354,6 +1362,7 @@ int ipm_share_qp(ipm_handle* h, ipm_handle* src, void* stream) {
   carve_state(cvs, dv, n, m, nR, stiff_cap, sc_cap, use_dense, h->opt.storage, h->opt.max_ipm);
   if (h->opt.lanes_rows) dv.g_rows = h->opt.lanes_rows;
   if (h->opt.lanes_cols) dv.g_cols = h->opt.lanes_cols;
+  if (h->opt.lanes_at) dv.g_at = h->opt.lanes_at;
   dv.aug = h->opt.system == IPM_SYSTEM_AUGMENTED ? 1 : 0;
   dv.nsys = dv.aug ? n + m : n;
   h->d = dv;
@@ -1578,6 +1587,7 @@ int ipm_solve(ipm_handle* h, void* stream, int flags) {
 int ipm_get_xyz(ipm_handle* h, double* x, double* y, double* zl, double* zu, double* s, ipm_info* info, int mem, void* stream) {
   if (!h) return IPM_ERR_ARG;
   if (!h->loaded || !h->have_iterate) return fail(h, IPM_ERR_STATE, "no iterate");
+  if (h->pending) return fail(h, IPM_ERR_STATE, "a solve is in flight on this handle (collect it with ipm_solve_wait)");
   int rc;
   if ((rc = enter(h, stream))) return rc;
   const Dev& d = h->d;
@@ -1619,6 +1629,7 @@ int ipm_set_iterate(ipm_handle* h, const double* x, const double* s, const doubl
                     const double* zu, double mu, int mem, void* stream) {
   if (!h) return IPM_ERR_ARG;
   if (!h->loaded) return fail(h, IPM_ERR_STATE, "ipm_set_iterate before ipm_set_qp");
+  if (h->pending) return fail(h, IPM_ERR_STATE, "a solve is in flight on this handle (collect it with ipm_solve_wait)");
   if (!(mu > 0) || !std::isfinite(mu)) return fail(h, IPM_ERR_ARG, "mu must be positive");
   int rc;
   const Dev& d = h->d;
@@ -1660,6 +1671,7 @@ int ipm_set_iterate(ipm_handle* h, const double* x, const double* s, const doubl
 int ipm_residuals(ipm_handle* h, double* rd, double* rp, double* rs, double* rl, double* ru, double* kkt, int mem, void* stream) {
   if (!h) return IPM_ERR_ARG;
   if (!h->loaded || !h->have_iterate) return fail(h, IPM_ERR_STATE, "no iterate");
+  if (h->pending) return fail(h, IPM_ERR_STATE, "a solve is in flight on this handle (collect it with ipm_solve_wait)");
   int rc;
   if ((rc = enter(h, stream))) return rc;
   const Dev& d = h->d;
@@ -1684,6 +1696,7 @@ int ipm_residuals(ipm_handle* h, double* rd, double* rp, double* rs, double* rl,
 int ipm_apply_kkt(ipm_handle* h, const double* p, double* q, int mem, void* stream) {
   if (!h || !p || !q) return IPM_ERR_ARG;
   if (!h->loaded || !h->have_iterate) return fail(h, IPM_ERR_STATE, "no iterate");
+  if (h->pending) return fail(h, IPM_ERR_STATE, "a solve is in flight on this handle (collect it with ipm_solve_wait)");
   int rc;
   if ((rc = enter(h, stream))) return rc;
   const Dev& d = h->d;
@@ -1698,6 +1711,7 @@ int ipm_apply_kkt(ipm_handle* h, const double* p, double* q, int mem, void* stre
 int ipm_precond_diag(ipm_handle* h, double* diag, int mem, void* stream) {
   if (!h || !diag) return IPM_ERR_ARG;
   if (!h->loaded || !h->have_iterate) return fail(h, IPM_ERR_STATE, "no iterate");
+  if (h->pending) return fail(h, IPM_ERR_STATE, "a solve is in flight on this handle (collect it with ipm_solve_wait)");
   int rc;
   if ((rc = enter(h, stream))) return rc;
   const Dev& d = h->d;
@@ -1712,6 +1726,7 @@ int ipm_newton_direction(ipm_handle* h, double eta, double* dx, double* ds, doub
                          ipm_cg_report* rep, int mem, void* stream) {
   if (!h) return IPM_ERR_ARG;
   if (!h->loaded || !h->have_iterate) return fail(h, IPM_ERR_STATE, "no iterate");
+  if (h->pending) return fail(h, IPM_ERR_STATE, "a solve is in flight on this handle (collect it with ipm_solve_wait)");
   int rc;
   if ((rc = enter(h, stream))) return rc;
   const Dev& d = h->d;
@@ -1749,6 +1764,7 @@ int ipm_step_lengths(ipm_handle* h, const double* dx, const double* ds, const do
                      const double* dzu, double tau, double* alpha_p, double* alpha_d, int mem, void* stream) {
   if (!h || !alpha_p || !alpha_d) return IPM_ERR_ARG;
   if (!h->loaded || !h->have_iterate) return fail(h, IPM_ERR_STATE, "no iterate");
+  if (h->pending) return fail(h, IPM_ERR_STATE, "a solve is in flight on this handle (collect it with ipm_solve_wait)");
   if (!(tau > 0 && tau <= 1)) return fail(h, IPM_ERR_ARG, "tau must be in (0, 1]");
   int rc;
   if ((rc = enter(h, stream))) return rc;
@@ -1907,6 +1923,7 @@ int ipm_profile_operator(ipm_handle* h, int reps, double* ms_rows, double* ms_co
                          double* bytes_cols, double* flops_rows, double* flops_cols) {
   if (!h || reps < 1) return IPM_ERR_ARG;
   if (!h->loaded || !h->have_iterate) return fail(h, IPM_ERR_STATE, "no iterate");
+  if (h->pending) return fail(h, IPM_ERR_STATE, "a solve is in flight on this handle (collect it with ipm_solve_wait)");
   CUDA_TRY(h, cudaSetDevice(h->device));
   const Dev& d = h->d;
   const Geo& g = h->g;

@@ -44,6 +44,7 @@ struct Scal {
   // warm start: pairs raised to at least warm_rho * mu0_cold (mu0 of the last cold start)
   double mu0_cold, warm_rho;
   int refine_it, refine_max, cg_step_total, cg_conv_outer, fallback, fallback_total;
+  int cg_fail_run;                   // consecutive Newton steps whose PCG ended unconverged
   // totals of one solve (device-side IPM loop)
   long long cg_total;
   int refine_total, max_cg_step, trace_rows, trace_cap;

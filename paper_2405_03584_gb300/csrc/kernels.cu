@@ -568,6 +568,10 @@ __global__ void k_control(Dev d, cudaGraphConditionalHandle h, int set_cond) {
   sc->cg_total += sc->cg_iter;
   sc->refine_total += refine;
   if (sc->cg_iter > sc->max_cg_step) sc->max_cg_step = sc->cg_iter;
+  // PCG stall: the direction of two consecutive Newton steps ended at the iteration limit
+  // without meeting its tolerance (one inexact direction is tolerated, inexact Newton)
+  sc->cg_fail_run = sc->cg_conv ? 0 : sc->cg_fail_run + 1;
+  if (sc->status == DS_RUNNING && sc->cg_fail_run >= 2) sc->status = DS_CG_STALL;
   if (sc->status == DS_NUMERICAL || sc->status == DS_CG_STALL || sc->status == DS_TIMEOUT) {
     sc->stop = 1;
   } else if (sc->ipm_iter >= 5 && !(sc->res_primal <= sc->tol_kkt) && sc->mult_inf > 1e10 &&
@@ -614,6 +618,7 @@ __global__ void k_solve_begin(Dev d) {
   sc->trace_rows = 0;
   sc->max_stiff_seen = 0;
   sc->fallback_total = 0;
+  sc->cg_fail_run = 0;
   sc->stop = 0;
   sc->status = DS_RUNNING;
 }

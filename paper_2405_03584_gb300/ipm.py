@@ -31,7 +31,7 @@ EXPORTS = ["ipm_default_options", "ipm_create", "ipm_set_qp", "ipm_solve", "ipm_
            "ipm_precond_diag", "ipm_newton_direction", "ipm_step_lengths", "ipm_profile_operator",
            "ipm_get_trace", "ipm_apply_operator_static", "ipm_solve_async", "ipm_solve_wait", "ipm_solve_query",
            "ipm_batch_create", "ipm_batch_solve", "ipm_batch_destroy", "ipm_update_costs", "ipm_share_qp",
-           "ipm_device_bytes", "ipm_set_lowrank", "ipm_abi_sizes", "ipm_get_sizes"]
+           "ipm_device_bytes", "ipm_set_lowrank", "ipm_abi_sizes", "ipm_get_sizes", "ipm_autotune_reset"]
 TRACE_COLS = ("iter", "mu", "rel_kkt", "primal", "dual", "gap", "alpha_p", "alpha_d", "pcg_iters", "pcg_converged",
               "stiff_rows", "pcg_rel_residual", "eta", "refine_passes")
 
@@ -44,7 +44,8 @@ class Options(C.Structure):
                 ("equal_steps", C.c_int), ("autotune", C.c_int), ("use_graphs", C.c_int),
                 ("storage", C.c_int), ("refine_max", C.c_int), ("refine_eta", C.c_double),
                 ("lanes_rows", C.c_int), ("lanes_cols", C.c_int), ("warm_rho", C.c_double),
-                ("u_cap", C.c_int), ("ingest_host", C.c_int), ("system", C.c_int)]
+                ("u_cap", C.c_int), ("ingest_host", C.c_int), ("system", C.c_int),
+                ("lanes_at", C.c_int)]
 
 
 class QP(C.Structure):
@@ -117,6 +118,7 @@ def load(path: str = LIB_PATH):
         "ipm_set_lowrank": (I, [P, C.c_int64, P, P, I, P]),
         "ipm_abi_sizes": (I, [P, P, P, P]),
         "ipm_get_sizes": (I, [P, P, P, P]),
+        "ipm_autotune_reset": (I, []),
         "ipm_apply_operator_static": (I, [C.c_int64, C.c_int64] + [P] * 10 + [P]),
     }
     for name, (res, args) in sig.items():
@@ -171,6 +173,11 @@ def _default_stream(stream):
     except Exception:
         pass
     return 0
+
+
+def autotune_reset():
+    """Forgets the autotuner's per-matrix choices of this process (ipm_autotune_reset)."""
+    return load().ipm_autotune_reset()
 
 
 def default_options() -> dict:

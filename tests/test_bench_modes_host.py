@@ -122,5 +122,9 @@ def test_every_bench_mode_runs_to_its_json_line(tmp_path):
     assert res["serve"]["speedup_solves_per_s"] == 1.0
     assert res["batch"]["config"]["count"] == 4
     assert res["sqp"]["warm"]["converged"]
+    # every mode records the SM clocks of its timed region (None here: no nvidia-smi)
+    for mode, line in res.items():
+        assert "clocks" in line, mode
+    assert d["e2e"]["steps"] == 5 and "cold_autotune" in d["e2e"]
     # outside the CPU-baseline legs no mode reports anything computed by oracle/
     assert not any("checker" in k for m in res.values() for k in m)

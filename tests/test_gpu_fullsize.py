@@ -1,5 +1,6 @@
 """Parity at the benchmark's full size (RT-shaped QP, V = 200000, n = 50000, m = 20000) in the
-launch configuration bench.py times (tol_kkt = 1e-6, JACOBI_LR).  The dense oracle cannot run
+launch configuration bench.py times (the same option set, ``presets.rt()``: tol_kkt = 1e-6,
+JACOBI_LR, lanes per row picked by the autotuner).  The dense oracle cannot run
 at this size, so the checks are the properties that hold at any size plus sampled outputs
 evaluated one by one on the host:
 
@@ -14,7 +15,7 @@ import pytest
 
 from oracle import ipm as O
 from oracle import kkt_check
-from paper_2405_03584_gb300 import ipm, workloads as W
+from paper_2405_03584_gb300 import ipm, presets, workloads as W
 
 pytestmark = pytest.mark.gpu
 
@@ -24,7 +25,7 @@ def full():
     from paper_2405_03584_gb300 import build
     build.build()
     p = W.rt_qp(n=50_000, seed=1)
-    s = ipm.Solver(tol_kkt=1e-6, precond="jacobi_lr")
+    s = ipm.Solver(**presets.rt())
     s.set_qp_rt(p)
     st = s.solve()
     out = s.get()
@@ -55,16 +56,46 @@ def test_full_size_residual_and_operator_samples(full):
     np.testing.assert_allclose(q[cols], ref, rtol=1e-9, atol=1e-12 * np.abs(ref).max())
 
 
-def test_mid_size_matches_oracle():
+@pytest.fixture(scope="module")
+def mid():
+    """The same generator at n = 4000 (V = 16000, m = 1600) and the oracle's solution."""
     p = W.rt_qp(n=4000, seed=1)
+    qp = O.from_rt(p)
+    ref, info = O.solve(qp, tol=1e-9)
+    assert info.status == "optimal"
+    return p, qp, ref
+
+
+def test_mid_size_matches_oracle(mid):
+    p, qp, ref = mid
     with ipm.Solver(tol_kkt=1e-7, precond="jacobi_lr") as s:
         s.set_qp_rt(p)
         assert s.solve() == ipm.IPM_OK
         out = s.get()
-    qp = O.from_rt(p)
-    ref, info = O.solve(qp, tol=1e-8)
-    assert info.status == "optimal"
     f, f_ref = O.objective(qp, out["x"]), O.objective(qp, ref.x)
     assert abs(f - f_ref) / (1 + abs(f_ref)) <= 1e-6
     assert kkt_check.rel_kkt(kkt_check.rt_ops(p), out["x"], out["y"], out["zl"], out["zu"]) <= 1e-7
     assert np.abs(out["x"] - ref.x).max() / (1 + np.abs(ref.x).max()) <= 1e-3
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16", "fp8"])
+def test_mid_size_error_per_storage(mid, storage):
+    """Each operator storage in the benchmark's option set, against the FP64 oracle: the
+    error in x, in the objective and the relative KKT residual of the returned point (the
+    precision configuration reports these per dtype).  Bars: rel. KKT <= 1e-6 and relative
+    objective error <= 1e-6; the x error is printed (x* is unique, its distance follows the
+    KKT residual through the conditioning of the problem)."""
+    p, qp, ref = mid
+    with ipm.Solver(**presets.rt(storage)) as s:
+        s.set_qp_rt(p)
+        assert s.solve() == ipm.IPM_OK
+        out = s.get()
+    rk = kkt_check.rel_kkt(kkt_check.rt_ops(p), out["x"], out["y"], out["zl"], out["zu"])
+    f, f_ref = O.objective(qp, out["x"]), O.objective(qp, ref.x)
+    ex = np.abs(out["x"] - ref.x).max() / np.abs(ref.x).max()
+    e2 = np.linalg.norm(out["x"] - ref.x) / np.linalg.norm(ref.x)
+    ef = abs(f - f_ref) / abs(f_ref)
+    print("\nstorage-accuracy %s: x_err_inf=%.3e x_err_2=%.3e obj_rel_err=%.3e rel_kkt=%.3e ipm=%d pcg=%d refine=%d"
+          % (storage, ex, e2, ef, rk, out["info"]["ipm_iters"], out["info"]["cg_iters"], out["info"]["refine_passes"]))
+    assert rk <= 1e-6
+    assert ef <= 1e-6

@@ -1,10 +1,12 @@
 """The allocation-free operator apply (ipm_apply_operator_static), for callers that cannot
 allocate device memory, against the handle-based operator apply (ipm_apply_kkt) on the same
-QP and iterate: two calls in a row, each checked element by element with the tolerance of
-the other operator tests (1e-10 relative).  Collected last on purpose (file name)."""
+QP and iterate, and against the oracle's condensed matrix at that iterate: two calls in a
+row, each checked element by element with the tolerance of the other operator tests (1e-10
+relative).  Collected last on purpose (file name)."""
 import numpy as np
 import pytest
 
+from oracle import ipm as O
 from paper_2405_03584_gb300 import ipm, workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -43,6 +45,9 @@ def test_static_scratch_operator_matches_apply_kkt():
     RT = (dev(tp, i64), dev(ti, i32), dev(tv, f64))
     om, dgd = dev(omega, f64), dev(dg, f64)
     stream = torch.cuda.current_stream().cuda_stream
+    qp = O.from_rt(p)
+    it = O.Iterate(x, s, y, zl, zu)
+    K, _, _, _ = O.condensed_system(qp, it, O.residuals(qp, it, 0.3))
     rng = np.random.default_rng(8)
     for call in range(2):
         pv = rng.normal(size=n)
@@ -56,6 +61,9 @@ def test_static_scratch_operator_matches_apply_kkt():
         torch.cuda.synchronize()
         qh = q.cpu().numpy()
         np.testing.assert_allclose(qh, q_ref, rtol=1e-10, atol=1e-12 * np.abs(q_ref).max(), err_msg="call %d" % call)
+        kp = K @ pv
+        np.testing.assert_allclose(qh, kp, rtol=1e-10, atol=1e-12 * np.abs(K).max() * np.abs(pv).max() * n,
+                                   err_msg="oracle, call %d" % call)
     # more rows than the fixed scratch holds: refused before any work
     rc = L.ipm_apply_operator_static(n, ipm.STATIC_SCRATCH_ROWS + 1, R[0].data_ptr(), R[1].data_ptr(),
                                      R[2].data_ptr(), RT[0].data_ptr(), RT[1].data_ptr(), RT[2].data_ptr(),
