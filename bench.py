@@ -133,15 +133,16 @@ class ClockSampler:
 
 
 def operator_source_hash():
-    """Hash of the source of the two PCG operator kernels and the row-dot helper they use."""
+    """Hash of the library's device sources (every csrc file): an ncu figure recorded under
+    another hash was taken on other kernels and is not reported."""
+    import glob
     import hashlib
-    import re
-    k = open(os.path.join(ROOT, "paper_2405_03584_gb300", "csrc", "kernels.cu")).read()
-    c = open(os.path.join(ROOT, "paper_2405_03584_gb300", "csrc", "common.cuh")).read()
-    a = k.index("// v = omega o (R p).")
-    b = k.index("// dx += alpha p; r -= alpha q;")
-    m = re.search(r"template <int G, bool SQ>\n__device__ __forceinline__ double group_row_dot\(.*?\n}\n", c, re.S)
-    return hashlib.sha256((k[a:b] + (m.group(0) if m else "")).encode()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2405_03584_gb300", "csrc", "*"))):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(os.path.basename(f).encode())
+            h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
 
 
 def _ncu_traffic(kernel, lanes):
@@ -229,6 +230,16 @@ def run_reference(args):
     return 0
 
 
+def _operator_opts(args):
+    """Operator arithmetic and rows format given on the command line (else the preset's)."""
+    o = {}
+    if args.op_arith:
+        o["op_arith"] = args.op_arith
+    if args.rows_format:
+        o["rows_format"] = args.rows_format
+    return o
+
+
 def run_operator_only(args):
     """Small capture target for profilers: the RT workload (or --bfgs), three IPM iterations,
     then the two operator passes three times each (ipm_profile_operator), in the storage of
@@ -239,7 +250,7 @@ def run_operator_only(args):
     build.build()
     lr, lc = (int(v) for v in args.lanes.split(","))
     s = ipm.Solver(tol_kkt=TOL, precond="jacobi_lr", max_ipm=3, lanes_rows=lr, lanes_cols=lc,
-                   storage=args.storage)
+                   storage=args.storage, **_operator_opts(args))
     if args.bfgs:
         s.set_qp_bfgs(_bfgs_problem(args.bfgs))
     else:
@@ -622,7 +633,7 @@ def run_ours(args):
     build.build()
     dev = torch.cuda.current_device()
     p = W.rt_qp(n=N_FULL, seed=SEED)
-    opts = presets.rt(args.storage)
+    opts = presets.rt(args.storage, **_operator_opts(args))
     if args.system != "condensed":
         opts.update(system=args.system, precond="jacobi")
     s = ipm.Solver(use_graphs=0 if args.no_graphs else 1, **opts)
@@ -662,12 +673,15 @@ def run_ours(args):
     achieved = byts / (ms / 1000.0) / 1e9
     lanes = infos[-1]["lanes_rows"] if kern == "k_op_rows" else infos[-1]["lanes_cols"]
     lp = args.storage != "f64"
-    kname = "%s_lp<%s, %d lanes/row>" % (kern, args.storage, lanes) if lp else "%s<%d lanes/row>" % (kern, lanes)
+    df = infos[-1]["op_arith"] == 1
+    runs = infos[-1]["rows_runs"] == 1 and kern == "k_op_rows"
+    base = kern + ("_lp" if lp else "") + ("_df" if df and not lp else "") + ("_runs" if runs else "")
+    kname = "%s<%s%d lanes/row>" % (base, (args.storage + ", ") if lp else "", lanes)
     roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
-            "unit": "GB/s", "frac": achieved / peak, "traffic": None if lp else _ncu_traffic(kern, lanes),
+            "unit": "GB/s", "frac": achieved / peak, "traffic": _ncu_traffic(base, lanes),
             "peak_kind": peak_kind + " hbm_gbs",
             "algorithmic_bytes": byts, "ms_per_launch": ms,
-            ("fp32_tflops" if lp else "fp64_tflops"): flops / (ms / 1000.0) / 1e12,
+            ("fp32_tflops" if lp or df else "fp64_tflops"): flops / (ms / 1000.0) / 1e12,
             "fp64_nominal_tflops": FP64_NOMINAL_TFLOPS,
             "other_kernel": {"ms_per_launch": prof["ms_" + ("cols" if key == "rows" else "rows")],
                              "gbs": prof["bytes_" + ("cols" if key == "rows" else "rows")] /
@@ -732,7 +746,8 @@ def run_ours(args):
                "solve": {"status": [int(x) for x in statuses], "ipm_iters": [i["ipm_iters"] for i in infos],
                          "cg_iters": [i["cg_iters"] for i in infos], "rel_kkt_device": infos[-1]["rel_kkt"],
                          "max_stiff_rows": infos[-1]["max_stiff_rows"],
-                         "lanes_per_row": [infos[-1]["lanes_rows"], infos[-1]["lanes_cols"]]},
+                         "lanes_per_row": [infos[-1]["lanes_rows"], infos[-1]["lanes_cols"]],
+                         "op_arith": ["f64", "df32"][infos[-1]["op_arith"]], "rows_runs": infos[-1]["rows_runs"]},
                "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk}
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -772,6 +787,10 @@ def main():
                     help="the linear system of the Newton step (augmented: the paper's eq:2x2_augmented, Jacobi PCG)")
     ap.add_argument("--storage", choices=["f64", "f32", "bf16", "fp8"], default="f64",
                     help="operator storage of the single RT QP (reduced ones add FP64 refinement)")
+    ap.add_argument("--op-arith", choices=["f64", "df32"], default=None,
+                    help="PCG operator arithmetic with f64 storage (default: the preset's)")
+    ap.add_argument("--rows-format", choices=["auto", "csr", "runs"], default=None,
+                    help="format of the PCG rows pass (default: the preset's)")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every kernel directly (for per-kernel profilers; same kernels, slower)")
     args = ap.parse_args()

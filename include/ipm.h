@@ -42,8 +42,9 @@ enum ipm_status {
   IPM_ERR_ARG = 1,               /* invalid argument (sizes, NULL, non-finite data, bad layout) */
   IPM_ERR_OOM = 2,               /* device allocation failed or exceeds options.mem_budget      */
   IPM_MAX_ITER = 3,              /* options.max_ipm iterations without reaching tol_kkt         */
-  IPM_CG_STALL = 4,              /* PCG hit options.max_cg without meeting its tolerance in two */
-                                 /* consecutive Newton steps (the solve stops there)            */
+  IPM_CG_STALL = 4,              /* PCG hit options.max_cg with its residual above 1e-2 of the  */
+                                 /* right-hand side in two consecutive Newton steps (the solve */
+                                 /* stops there)                                               */
   IPM_NUMERICAL = 5,             /* NaN/Inf in an iterate, PCG breakdown or step length -> 0    */
   IPM_INFEASIBLE_SUSPECTED = 6,  /* the multipliers diverge along a Farkas certificate of primal */
                                  /* infeasibility (y, z >= 0, A^T y - z_l + z_u ~ 0,            */
@@ -81,6 +82,23 @@ enum ipm_precond { IPM_PRECOND_JACOBI = 0, IPM_PRECOND_JACOBI_LR = 1, IPM_PRECON
 enum ipm_system { IPM_SYSTEM_CONDENSED = 0, IPM_SYSTEM_AUGMENTED = 1 };
 
 enum ipm_storage { IPM_STORAGE_F64 = 0, IPM_STORAGE_F32 = 1, IPM_STORAGE_BF16 = 2, IPM_STORAGE_FP8_E4M3 = 3 };
+
+/* Arithmetic of the PCG operator with F64 storage (not part of the paper, which uses FP64).
+ *  F64  : float64 multiply-adds (GB300 issues two per SM per clock, which bounds the passes).
+ *  DF32 : double-float: every value of R, R^T and of the vectors the operator reads is carried
+ *         as a (hi, lo) pair of float32 (48 significant bits, the same 8 bytes), products and
+ *         sums by error-free transformations on the float32 pipe; row sums within about 1e-13
+ *         of sum |a x|.  Residuals, reductions and the rest of the iteration stay float64.
+ *         Needs the non-zero values of R within [2^-90, 2^90]; otherwise ipm_set_qp keeps F64
+ *         (ipm_info.op_arith tells which ran).  An extra copy of R and R^T (8 bytes per entry
+ *         each) is stored. */
+enum ipm_arith { IPM_ARITH_F64 = 0, IPM_ARITH_DF32 = 1 };
+
+/* Format of R's rows in the PCG rows pass.  CSR: one int32 column index per entry.  RUNS: the
+ * maximal stretches of consecutive entries with consecutive columns (a dose row's contiguous
+ * spot bands) as (first column, first entry) pairs, so no per-entry index is read.  AUTO: RUNS
+ * when R has at least 8 entries per run on average (the row order is the caller's). */
+enum ipm_rows_format { IPM_ROWS_AUTO = 0, IPM_ROWS_CSR = 1, IPM_ROWS_RUNS = 2 };
 
 /* ipm_solve flags. */
 enum ipm_solve_flags { IPM_COLD = 0, IPM_WARM = 1 };
@@ -126,6 +144,8 @@ typedef struct ipm_options {
   int lanes_at;          /* lanes per row of the kernels over the stored A^T alone (right-hand  */
                          /* side with the Jacobi diagonal, Jacobi diagonal): 4, 8, 16, 32; 0 =  */
                          /* from its average row length                                        */
+  int op_arith;          /* enum ipm_arith: PCG operator arithmetic with F64 storage (F64)      */
+  int rows_format;       /* enum ipm_rows_format of the PCG rows pass (AUTO)                    */
 } ipm_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -191,6 +211,8 @@ typedef struct ipm_info {
   int lanes_cols;            /* by the autotuner at ipm_set_qp)                            */
   int64_t refine_passes;     /* FP64 refinement passes summed over the Newton steps        */
   int64_t fallback_steps;    /* Newton steps finished by FP64 PCG after refinement stalled */
+  int op_arith;              /* enum ipm_arith the F64-storage PCG operator ran in         */
+  int rows_runs;             /* 1 if the PCG rows pass read R's rows as runs               */
 } ipm_info;
 
 /* Per-step result of ipm_newton_direction. */
@@ -252,6 +274,11 @@ typedef struct ipm_batch ipm_batch;
 int ipm_batch_create(ipm_handle* const* handles, int count, int flags, ipm_batch** out);
 int ipm_batch_solve(ipm_batch* b, void* stream, int* statuses);
 int ipm_batch_destroy(ipm_batch* b);
+
+/* Fills *info: the last solve's results (zero before the first solve) and the operator
+ * configuration chosen at ipm_set_qp (op_arith, rows_runs, lanes_rows, lanes_cols).
+ * Errors: IPM_ERR_ARG (NULL), IPM_ERR_STATE (no QP loaded). */
+int ipm_get_info(ipm_handle* h, ipm_info* info);
 
 /* Copies the current iterate to caller memory (any pointer may be NULL to skip it):
  * x, z_l, z_u (n), y, s (m: the caller's rows; for two-sided rows the signed multiplier and

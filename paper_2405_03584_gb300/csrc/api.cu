@@ -65,6 +65,7 @@ int count_kernel_nodes(cudaGraph_t g) {
 // memory is freed with the last one.
 struct MatStore {
   void* ptr = nullptr;
+  void* aux = nullptr;              // runs of R's rows (sized only once R is on the device)
   size_t bytes = 0;
   int device = 0;
   int storage = 0;
@@ -75,6 +76,7 @@ struct MatStore {
       cudaGetDevice(&cur);
       cudaSetDevice(device);
       cudaFree(ptr);
+      if (aux) cudaFree(aux);
       cudaSetDevice(cur);
     }
   }
@@ -215,7 +217,7 @@ struct HostQP {
 
 // Matrix part of the device layout (shared between handles that share a QP).
 void carve_matrix(Carver& cv, Dev& d, int64_t n, int64_t m, int64_t nR, int64_t nnzR, int64_t nnzA, int64_t nnzHs,
-                  int storage) {
+                  int storage, bool df) {
   d.R_ptr = cv.take<int64_t>(nR + 1); d.R_idx = cv.take<int32_t>(nnzR); d.R_val = cv.take<double>(nnzR);
   d.RT_ptr = cv.take<int64_t>(n + 1); d.RT_idx = cv.take<int32_t>(nnzR); d.RT_val = cv.take<double>(nnzR);
   d.AT_ptr = cv.take<int64_t>(n + 1); d.AT_idx = cv.take<int32_t>(nnzA); d.AT_val = cv.take<double>(nnzA);
@@ -235,11 +237,17 @@ void carve_matrix(Carver& cv, Dev& d, int64_t n, int64_t m, int64_t nR, int64_t 
     d.Rq = d.RTq = nullptr;
     d.scaleR = nullptr;
   }
+  if (df) {
+    d.R_df = cv.take<float2>(nnzR);
+    d.RT_df = cv.take<float2>(nnzR);
+  } else {
+    d.R_df = d.RT_df = nullptr;
+  }
 }
 
 // Per-handle part: problem vectors (costs may change per handle), iterate and work space.
 void carve_state(Carver& cv, Dev& d, int64_t n, int64_t m, int64_t nR, int stiff_cap, int64_t sc_cap, bool dense,
-                 int storage, int trace_cap) {
+                 int storage, int trace_cap, bool df) {
   d.wR = cv.take<double>(nR); d.h0 = cv.take<double>(n); d.c = cv.take<double>(n); d.b = cv.take<double>(m);
   d.l = cv.take<double>(n); d.u = cv.take<double>(n);
   d.fl = cv.take<unsigned char>(n); d.fu = cv.take<unsigned char>(n);
@@ -268,8 +276,14 @@ void carve_state(Carver& cv, Dev& d, int64_t n, int64_t m, int64_t nR, int stiff
   d.Rd = (dense && nR * n <= (int64_t)(32 << 20)) ? cv.take<double>(nR * n) : nullptr;
   d.chol_diag = cv.take<double>(std::max<int64_t>(dense ? n : 0, stiff_cap));
   d.storage = storage;
+  if (df) {
+    d.p_df = cv.take<float2>(n);
+    d.v_df = cv.take<float2>(nR);
+  } else {
+    d.p_df = d.v_df = nullptr;
+  }
   if (storage != ST_F64) {
-    d.p32 = cv.take<float>((n + 3) & ~int64_t(3));   // whole 16-byte units (bulk copies)
+    d.p32 = cv.take<float>((n + 3) & ~int64_t(3));
     d.w32 = cv.take<float>(nR);
     d.dxr = cv.take<double>(n);
   } else {
@@ -328,6 +342,8 @@ int validate_options(const ipm_options& o) {
   if (!(o.warm_rho >= 0 && o.warm_rho < 1)) return IPM_ERR_ARG;
   if (o.u_cap < 0 || o.u_cap > (1 << 16)) return IPM_ERR_ARG;
   if (o.system != IPM_SYSTEM_CONDENSED && o.system != IPM_SYSTEM_AUGMENTED) return IPM_ERR_ARG;
+  if (o.op_arith != IPM_ARITH_F64 && o.op_arith != IPM_ARITH_DF32) return IPM_ERR_ARG;
+  if (o.rows_format < IPM_ROWS_AUTO || o.rows_format > IPM_ROWS_RUNS) return IPM_ERR_ARG;
   if (o.system == IPM_SYSTEM_AUGMENTED &&
       (o.storage != IPM_STORAGE_F64 || (o.precond != IPM_PRECOND_JACOBI && o.precond != IPM_PRECOND_AUTO)))
     return IPM_ERR_ARG;   // the doubly augmented system runs FP64 with the Jacobi preconditioner
@@ -374,6 +390,60 @@ int heuristic_group(double avg_nnz) {
 std::mutex g_tune_mu;
 std::map<std::tuple<int64_t, int64_t, int64_t>, std::pair<int, int>> g_tune_cache;
 
+// Operator formats decided once R and R^T are on the device: the double-float copies of the
+// values (asked for by options.op_arith, kept only when every value is in the float32 range
+// the pairs need) and the runs of R's rows (options.rows_format; AUTO takes them when they
+// average at least 8 entries).  The runs get a device allocation of their own, sized here.
+int prepare_operator_formats(ipm_handle* h) {
+  Dev& d = h->d;
+  d.df = 0;
+  if (d.R_df) {
+    int* flag = reinterpret_cast<int*>(d.partials);   // reduction scratch, free at set-up
+    CUDA_TRY(h, cudaMemsetAsync(flag, 0, sizeof(int), h->st));
+    CUDA_TRY(h, launch_df_split(d, flag, h->st));
+    int bad = 0;
+    CUDA_TRY(h, cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    d.df = bad ? 0 : 1;
+  }
+  d.runs = 0;
+  d.nruns = 0;
+  d.run_ptr = nullptr;
+  d.run_col = nullptr;
+  d.run_beg = nullptr;
+  if (h->opt.rows_format == IPM_ROWS_CSR || d.nR == 0 || d.nnzR == 0) return IPM_OK;
+  int32_t* cnt = reinterpret_cast<int32_t*>(d.tR);     // nR doubles of iteration work space
+  CUDA_TRY(h, launch_runs_count(d, cnt, h->st));
+  std::vector<int32_t> hc((size_t)d.nR);
+  CUDA_TRY(h, cudaMemcpyAsync(hc.data(), cnt, sizeof(int32_t) * (size_t)d.nR, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  std::vector<int64_t> rp((size_t)d.nR + 1, 0);
+  for (int64_t r = 0; r < d.nR; ++r) rp[r + 1] = rp[r] + hc[r];
+  const int64_t nruns = rp[d.nR];
+  const bool use = nruns > 0 && (h->opt.rows_format == IPM_ROWS_RUNS || (double)d.nnzR >= 8.0 * (double)nruns);
+  if (!use) return IPM_OK;
+  Carver cc(nullptr);
+  cc.take<int64_t>(d.nR + 1);
+  cc.take<int32_t>(nruns);
+  cc.take<int64_t>(nruns + 1);
+  const size_t bytes = cc.off + 256;
+  if (h->opt.mem_budget > 0 && (double)(h->mat->bytes + h->arena_bytes + bytes) > h->opt.mem_budget)
+    return IPM_OK;                                     // within the budget the rows pass stays CSR
+  int rc;
+  if ((rc = dev_alloc(h, &h->mat->aux, bytes, "runs of R's rows"))) return rc;
+  h->mat->bytes += bytes;
+  Carver cv((char*)h->mat->aux);
+  d.run_ptr = cv.take<int64_t>(d.nR + 1);
+  d.run_col = cv.take<int32_t>(nruns);
+  d.run_beg = cv.take<int64_t>(nruns + 1);
+  d.nruns = nruns;
+  CUDA_TRY(h, cudaMemcpyAsync((void*)d.run_ptr, rp.data(), sizeof(int64_t) * rp.size(), cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, launch_runs_fill(d, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  d.runs = 1;
+  return IPM_OK;
+}
+
 // Times the two operator kernels for every lane-group size on the loaded matrices (three
 // launches each after one warm-up, CUDA events on the handle's stream) and keeps the fastest.
 int autotune_groups(ipm_handle* h) {
@@ -390,6 +460,8 @@ int autotune_groups(ipm_handle* h) {
     }
   }
   CUDA_TRY(h, cudaMemsetAsync(d.p, 0, sizeof(double) * d.n, h->st));
+  if (d.p_df) CUDA_TRY(h, cudaMemsetAsync(d.p_df, 0, sizeof(float2) * d.n, h->st));
+  if (d.v_df && d.nR) CUDA_TRY(h, cudaMemsetAsync(d.v_df, 0, sizeof(float2) * d.nR, h->st));
   CUDA_TRY(h, cudaMemsetAsync(d.sigma, 0, sizeof(double) * d.n, h->st));
   if (d.nR) {
     CUDA_TRY(h, cudaMemsetAsync(d.omega, 0, sizeof(double) * d.nR, h->st));
@@ -734,6 +806,8 @@ void ipm_default_options(ipm_options* o) {
   o->lanes_rows = 0;
   o->lanes_cols = 0;
   o->lanes_at = 0;
+  o->op_arith = IPM_ARITH_F64;
+  o->rows_format = IPM_ROWS_AUTO;
   o->warm_rho = 1e-5;
   o->u_cap = 0;
   o->ingest_host = 0;
@@ -1055,8 +1129,9 @@ static int load_qp(ipm_handle* h, const ipm_qp* qp, int64_t m_ar, void* stream) 
   dv.ublocks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * (int64_t)dv.sm_count, n / 32));
   const int64_t nnzHs = (int64_t)q.Hv.size();
   Carver cm(nullptr), cs(nullptr);
-  carve_matrix(cm, dv, n, m, q.nR, nnzR, nnzAT, nnzHs, h->opt.storage);
-  carve_state(cs, dv, n, m, q.nR, stiff_cap, sc_cap, dense, h->opt.storage, h->opt.max_ipm);
+  const bool want_df = h->opt.op_arith == IPM_ARITH_DF32 && h->opt.storage == IPM_STORAGE_F64;
+  carve_matrix(cm, dv, n, m, q.nR, nnzR, nnzAT, nnzHs, h->opt.storage, want_df);
+  carve_state(cs, dv, n, m, q.nR, stiff_cap, sc_cap, dense, h->opt.storage, h->opt.max_ipm, want_df);
   const size_t mbytes = cm.off + 256, sbytes = cs.off + 256;
   if (h->opt.mem_budget > 0 && (double)(mbytes + sbytes) > h->opt.mem_budget)
     return fail(h, IPM_ERR_OOM, "QP needs " + std::to_string(mbytes + sbytes) + " bytes, over mem_budget");
@@ -1066,8 +1141,8 @@ static int load_qp(ipm_handle* h, const ipm_qp* qp, int64_t m_ar, void* stream) 
   h->arena_bytes = sbytes;
   h->mat = store;
   Carver cvm((char*)store->ptr), cvs((char*)h->arena);
-  carve_matrix(cvm, dv, n, m, q.nR, nnzR, nnzAT, nnzHs, h->opt.storage);
-  carve_state(cvs, dv, n, m, q.nR, stiff_cap, sc_cap, dense, h->opt.storage, h->opt.max_ipm);
+  carve_matrix(cvm, dv, n, m, q.nR, nnzR, nnzAT, nnzHs, h->opt.storage, want_df);
+  carve_state(cvs, dv, n, m, q.nR, stiff_cap, sc_cap, dense, h->opt.storage, h->opt.max_ipm, want_df);
   dv.n = n; dv.m = m; dv.nR = q.nR; dv.nnzR = nnzR; dv.nnzHs = nnzHs; dv.nnzA = nnzAT;
   dv.g_rows = heuristic_group(q.nR ? (double)nnzR / (double)q.nR : 0.0);
   dv.g_cols = heuristic_group((double)nnzR / (double)n);
@@ -1167,6 +1242,7 @@ static int load_qp(ipm_handle* h, const ipm_qp* qp, int64_t m_ar, void* stream) 
   CUDA_TRY(h, launch_diagH(d, h->st));
   CUDA_TRY(h, launch_quantize(d, h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));   // host staging buffers go out of scope
+  if ((rc = prepare_operator_formats(h))) return rc;
   if (h->opt.autotune && !h->opt.lanes_rows && !h->opt.lanes_cols && (rc = autotune_groups(h))) return rc;
   h->loaded = true;
   h->have_iterate = false;
@@ -1351,7 +1427,7 @@ int ipm_share_qp(ipm_handle* h, ipm_handle* src, void* stream) {
   free_arena(h);
   Dev dv = sd;                      // sizes, lane choices and matrix pointers of the source
   Carver cs(nullptr);
-  carve_state(cs, dv, n, m, nR, stiff_cap, sc_cap, use_dense, h->opt.storage, h->opt.max_ipm);
+  carve_state(cs, dv, n, m, nR, stiff_cap, sc_cap, use_dense, h->opt.storage, h->opt.max_ipm, sd.R_df != nullptr);
   const size_t sbytes = cs.off + 256;
   if (h->opt.mem_budget > 0 && (double)sbytes > h->opt.mem_budget)
     return fail(h, IPM_ERR_OOM, "state needs " + std::to_string(sbytes) + " bytes, over mem_budget");
@@ -1359,7 +1435,7 @@ int ipm_share_qp(ipm_handle* h, ipm_handle* src, void* stream) {
   h->arena_bytes = sbytes;
   h->mat = store;
   Carver cvs((char*)h->arena);
-  carve_state(cvs, dv, n, m, nR, stiff_cap, sc_cap, use_dense, h->opt.storage, h->opt.max_ipm);
+  carve_state(cvs, dv, n, m, nR, stiff_cap, sc_cap, use_dense, h->opt.storage, h->opt.max_ipm, sd.R_df != nullptr);
   if (h->opt.lanes_rows) dv.g_rows = h->opt.lanes_rows;
   if (h->opt.lanes_cols) dv.g_cols = h->opt.lanes_cols;
   if (h->opt.lanes_at) dv.g_at = h->opt.lanes_at;
@@ -1532,6 +1608,8 @@ static int fill_info(ipm_handle* h, int64_t direct_launches) {
   in.lanes_cols = h->d.g_cols;
   in.refine_passes = h->d.storage != ST_F64 ? s.refine_total : 0;
   in.fallback_steps = h->d.storage != ST_F64 ? s.fallback_total : 0;
+  in.op_arith = h->d.df ? IPM_ARITH_DF32 : IPM_ARITH_F64;
+  in.rows_runs = h->d.runs;
   return status;
 }
 
@@ -1584,6 +1662,18 @@ int ipm_solve(ipm_handle* h, void* stream, int flags) {
   return st;
 }
 
+int ipm_get_info(ipm_handle* h, ipm_info* info) {
+  if (!h || !info) return IPM_ERR_ARG;
+  if (!h->loaded) return fail(h, IPM_ERR_STATE, "no QP loaded");
+  // the operator's configuration is known from ipm_set_qp on, solved or not
+  h->info.op_arith = h->d.df ? IPM_ARITH_DF32 : IPM_ARITH_F64;
+  h->info.rows_runs = h->d.runs;
+  h->info.lanes_rows = h->d.g_rows;
+  h->info.lanes_cols = h->d.g_cols;
+  *info = h->info;
+  return IPM_OK;
+}
+
 int ipm_get_xyz(ipm_handle* h, double* x, double* y, double* zl, double* zu, double* s, ipm_info* info, int mem, void* stream) {
   if (!h) return IPM_ERR_ARG;
   if (!h->loaded || !h->have_iterate) return fail(h, IPM_ERR_STATE, "no iterate");
@@ -1621,7 +1711,7 @@ int ipm_get_xyz(ipm_handle* h, double* x, double* y, double* zl, double* zu, dou
     CUDA_TRY(h, cudaStreamSynchronize(h->st));   // yo, so go out of scope
   }
   if (mem == IPM_MEM_HOST) CUDA_TRY(h, cudaStreamSynchronize(h->st));
-  if (info) *info = h->info;
+  if (info) ipm_get_info(h, info);
   return leave(h, stream);
 }
 
@@ -1932,6 +2022,7 @@ int ipm_profile_operator(ipm_handle* h, int reps, double* ms_rows, double* ms_co
   // the passes the handle's PCG runs: FP64, or the reduced-precision ones of its storage
   const bool lp = d.storage != ST_F64;
   if (lp) CUDA_TRY(h, launch_mirror_p32(d, g, h->st));
+  if (d.df) CUDA_TRY(h, launch_mirror_df(d, g, h->st));
   auto rows = [&]() {
     cudaError_t e = lp ? launch_op_rows_lp_only(d, g, h->st) : launch_op_rows_only(d, g, h->st);
     if (e == cudaSuccess && d.ucols) e = launch_lr(d, d.p, 0, h->st);   // U^T p belongs to the first half
@@ -1960,30 +2051,32 @@ int ipm_profile_operator(ipm_handle* h, int reps, double* ms_rows, double* ms_co
     tc += b;
   }
   for (auto& e : ev) cudaEventDestroy(e);
-  const double nnz = (double)d.nnzR, nnzh = (double)d.nnzHs;
+  const double nnz = (double)d.nnzR, nnzh = (double)d.nnzHs, nR = (double)d.nR, n = (double)d.n;
   if (ms_rows) *ms_rows = tr / reps;
   if (ms_cols) *ms_cols = tc / reps;
   // low-rank term: U read once in each half (U^T p, then U (W t)), p and W t read once
-  const double lr_b = d.ucols ? 8.0 * (double)d.n * (double)d.ucols + 8.0 * (double)d.ucols : 0.0;
-  const double lr_f = d.ucols ? 2.0 * (double)d.n * (double)d.ucols : 0.0;
+  const double lr_b = d.ucols ? 8.0 * n * (double)d.ucols + 8.0 * (double)d.ucols : 0.0;
+  const double lr_f = d.ucols ? 2.0 * n * (double)d.ucols : 0.0;
+  // the rows pass reads, per row, its row pointers (CSR) or its run pointers and runs
+  const double row_index = d.runs ? 8.0 * (nR + 1) + 12.0 * (double)d.nruns + 8.0 : 4.0 * nnz + 8.0 * (nR + 1);
+  const double hs_b = d.Hs_ptr ? 12.0 * nnzh + 8.0 * (n + 1) : 0.0;
   if (lp) {
     const double vb = d.storage == ST_F32 ? 4.0 : (d.storage == ST_BF16 ? 2.0 : 1.0);
-    // rows: narrow values + indices, row pointers, scale, w_R, thR read, w32 written, p32 read once
-    if (bytes_rows) *bytes_rows = (vb + 4.0) * nnz + 8.0 * (d.nR + 1) + 24.0 * d.nR + 4.0 * d.n + lr_b;
+    // rows: narrow values, the index data, scale, w_R, thR read, w32 written, p32 read once
+    if (bytes_rows) *bytes_rows = vb * nnz + row_index + 24.0 * nR + 4.0 * n + lr_b;
     // cols: narrow values + indices, row pointers, w32 read once, p, h0, sigma read, q written
-    if (bytes_cols) *bytes_cols = (vb + 4.0) * nnz + 8.0 * (d.n + 1) + 4.0 * d.nR + 32.0 * d.n +
-                                  (d.Hs_ptr ? 12.0 * nnzh + 8.0 * (d.n + 1) : 0.0) + lr_b;
-    if (flops_rows) *flops_rows = 2.0 * nnz + 4.0 * d.nR + lr_f;
-    if (flops_cols) *flops_cols = 2.0 * nnz + 2.0 * nnzh + 4.0 * d.n + lr_f;
+    if (bytes_cols) *bytes_cols = (vb + 4.0) * nnz + 8.0 * (n + 1) + 4.0 * nR + 32.0 * n + hs_b + lr_b;
+    if (flops_rows) *flops_rows = 2.0 * nnz + 4.0 * nR + lr_f;
+    if (flops_cols) *flops_cols = 2.0 * nnz + 2.0 * nnzh + 4.0 * n + lr_f;
     return IPM_OK;
   }
-  // rows: values + indices, row pointers, omega, v written, p read once
-  if (bytes_rows) *bytes_rows = 12.0 * nnz + 8.0 * (d.nR + 1) + 16.0 * d.nR + 8.0 * d.n + lr_b;
+  // FP64 and double-float alike (8 bytes per value and per vector entry):
+  // rows: values, the index data, the row order, omega, v written, p read once
+  if (bytes_rows) *bytes_rows = 8.0 * nnz + row_index + 4.0 * nR + 16.0 * nR + 8.0 * n + lr_b;
   // cols: values + indices, row pointers, v read once, p, h0, sigma read, q written (+ Hs)
-  if (bytes_cols) *bytes_cols = 12.0 * nnz + 8.0 * (d.n + 1) + 8.0 * d.nR + 32.0 * d.n +
-                                (d.Hs_ptr ? 12.0 * nnzh + 8.0 * (d.n + 1) : 0.0) + lr_b;
-  if (flops_rows) *flops_rows = 2.0 * nnz + d.nR + lr_f;
-  if (flops_cols) *flops_cols = 2.0 * nnz + 2.0 * nnzh + 4.0 * d.n + lr_f;
+  if (bytes_cols) *bytes_cols = 12.0 * nnz + 8.0 * (n + 1) + 8.0 * nR + 32.0 * n + hs_b + lr_b;
+  if (flops_rows) *flops_rows = 2.0 * nnz + nR + lr_f;
+  if (flops_cols) *flops_cols = 2.0 * nnz + 2.0 * nnzh + 4.0 * n + lr_f;
   return IPM_OK;
 }
 

@@ -286,4 +286,58 @@ __device__ __forceinline__ void warp_row_dot2(const int64_t beg, const int64_t e
 
 __device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
 
+// ---------------------------------------------------------------- double-float arithmetic
+//
+// A float64 value x is carried as an unevaluated pair of float32 (hi, lo) with hi = fl32(x)
+// and lo = fl32(x - hi): 48 significant bits, the same 8 bytes as the double.  Products and
+// sums of such pairs are formed on the float32 pipe with error-free transformations:
+// Dekker's product (the rounding error of a * b is fma(a, b, -fl(a * b)) exactly; Dekker
+// 1971, with the fused multiply-add in place of his splitting) and Knuth's two-sum (s =
+// fl(a + b), e = (a - (s - bb)) + (b - bb) with bb = s - a gives a + b = s + e exactly; Knuth,
+// TAOCP vol. 2, 4.2.2).  The _rn intrinsics are never contracted into fused operations, which
+// the transformations rely on.
+__device__ __forceinline__ float2 df_split(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
+
+__device__ __forceinline__ double df_value(float h, float l) { return (double)h + (double)l; }
+
+// s + e = a + b exactly (Knuth's two-sum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (h, l) += a * x for double-float a, x: the high product and its exact error (Dekker), the
+// two cross terms into the error (the lo * lo term is below the pair's precision), the high
+// product added to h by two-sum, every error term into l.
+__device__ __forceinline__ void df_mac(const float2 a, const float2 x, float& h, float& l) {
+  const float p = __fmul_rn(a.x, x.x);
+  float e = __fmaf_rn(a.x, x.x, -p);
+  e = __fmaf_rn(a.x, x.y, e);
+  e = __fmaf_rn(a.y, x.x, e);
+  float s, t;
+  two_sum(h, p, s, t);
+  h = s;
+  l = __fadd_rn(l, __fadd_rn(t, e));
+}
+
+// Sum of the pairs of a group of G lanes (fixed butterfly order; every lane gets the total).
+template <int G>
+__device__ __forceinline__ double df_group_sum(float h, float l) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+    // both partners form the same pair: s and the exact error of h + oh do not depend on the
+    // operand order, and a float32 addition is commutative
+    float s, t;
+    two_sum(h, oh, s, t);
+    h = s;
+    l = __fadd_rn(__fadd_rn(l, ol), t);
+  }
+  return df_value(h, l);
+}
+
 }  // namespace ipmk

@@ -1,0 +1,266 @@
+// Double-float PCG operator and the runs of R's rows.
+//
+// GB300 issues two float64 fused multiply-adds per SM per clock: at the RT size the FP64
+// operator passes (one multiply-add per stored entry) are bound by that pipe before HBM.  The
+// double-float passes carry every value of R, R^T, p and v as a (hi, lo) pair of float32 (the
+// same 8 bytes as the double) and form each product and the row sums with error-free
+// transformations on the float32 pipe (common.cuh), which is 64 times wider, leaving HBM as
+// the bound.  The row sums are exact to about 2^-44 relative to sum |a x| (48-bit operands,
+// compensated sums), far below the smallest PCG tolerance; the operator stays exactly
+// symmetric (the column pass forms R^T diag(omega) R with the same stored values as the rows
+// pass, and every sum has a fixed order), so conjugate gradients remain valid.  Residuals,
+// the start point, the right-hand side and the preconditioner keep the FP64 copies.
+//
+// Runs: the columns of a dose row come in a few contiguous spot bands.  A run is a maximal
+// stretch of consecutive stored entries of a row whose columns increase by one; the rows pass
+// over runs reads (first column, first entry) per run instead of one int32 index per entry,
+// and gathers p at consecutive addresses.
+#include "state.h"
+
+namespace ipmk {
+
+static __device__ __forceinline__ int gwarp_d() { return (blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
+static __device__ __forceinline__ int nwarps_d() { return (gridDim.x * blockDim.x) >> 5; }
+
+#define FOR_GROUP_ROWS_D(G, r, ok, nrows)                                                                    \
+  for (int64_t r##_0 = (int64_t)gwarp_d() * (32 / G); r##_0 < (nrows); r##_0 += (int64_t)nwarps_d() * (32 / G)) \
+    for (int64_t r = r##_0 + (threadIdx.x & 31) / G, r##_once = 0; r##_once == 0; r##_once = 1)               \
+      for (bool ok = r < (nrows), ok##_once = true; ok##_once; ok##_once = false)
+
+#define DISPATCH_GD(g, ...)                                  \
+  switch (g) {                                               \
+    case 4: { constexpr int G = 4; __VA_ARGS__; } break;     \
+    case 8: { constexpr int G = 8; __VA_ARGS__; } break;     \
+    case 16: { constexpr int G = 16; __VA_ARGS__; } break;   \
+    default: { constexpr int G = 32; __VA_ARGS__; } break;   \
+  }
+
+// ---------------------------------------------------------------- set-up
+
+// out = (hi, lo) pairs of a; *flag |= 1 if a non-zero value lies outside [2^-90, 2^90], where
+// the pair would lose bits to the float32 exponent range (the caller then keeps FP64).
+__global__ void k_df_split(const double* __restrict__ a, float2* __restrict__ out, int64_t n, int* flag) {
+  bool bad = false;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double v = a[e];
+    const double av = fabs(v);
+    if (v != 0.0 && !(av >= 0x1p-90 && av <= 0x1p90)) bad = true;
+    out[e] = df_split(v);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+cudaError_t launch_df_split(const Dev& d, int* out_of_range, cudaStream_t st) {
+  if (!d.R_df || d.nnzR == 0) return cudaSuccess;
+  const int gb = (int)std::min<int64_t>((d.nnzR + 255) / 256, 8 * (int64_t)(d.sm_count > 0 ? d.sm_count : 148));
+  k_df_split<<<gb, 256, 0, st>>>(d.R_val, const_cast<float2*>(d.R_df), d.nnzR, out_of_range);
+  k_df_split<<<gb, 256, 0, st>>>(d.RT_val, const_cast<float2*>(d.RT_df), d.nnzR, out_of_range);
+  return cudaGetLastError();
+}
+
+__global__ void k_mirror_df(Dev d) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x)
+    d.p_df[j] = df_split(d.p[j]);
+}
+
+cudaError_t launch_mirror_df(const Dev& d, const Geo& g, cudaStream_t st) {
+  k_mirror_df<<<g.eN, kBlock, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- row sums
+
+// Double-float dot of one CSR row with a double-float vector by a group of G lanes (lane gl
+// takes entries gl, gl + G, ...; two in flight), summed over the group.
+template <int G>
+__device__ __forceinline__ double group_row_dot_df(const int64_t beg, const int64_t end, const int gl,
+                                                   const int32_t* __restrict__ idx, const float2* __restrict__ val,
+                                                   const float2* __restrict__ x) {
+  float h = 0.f, l = 0.f;
+  int64_t e = beg + gl;
+  for (; e + G < end; e += 2 * G) {
+    const float2 a0 = __ldg(val + e), a1 = __ldg(val + e + G);
+    const int i0 = __ldg(idx + e), i1 = __ldg(idx + e + G);
+    const float2 x0 = __ldg(x + i0), x1 = __ldg(x + i1);
+    df_mac(a0, x0, h, l);
+    df_mac(a1, x1, h, l);
+  }
+  if (e < end) df_mac(__ldg(val + e), __ldg(x + __ldg(idx + e)), h, l);
+  return df_group_sum<G>(h, l);
+}
+
+// The same over the runs [k0, k1) of a row: entry e of run k sits in column
+// run_col[k] + (e - run_beg[k]), so the gathers of a group read consecutive addresses.
+template <int G>
+__device__ __forceinline__ double group_runs_dot_df(const int64_t k0, const int64_t k1, const int gl,
+                                                    const int32_t* __restrict__ run_col,
+                                                    const int64_t* __restrict__ run_beg,
+                                                    const float2* __restrict__ val, const float2* __restrict__ x) {
+  float h = 0.f, l = 0.f;
+  for (int64_t k = k0; k < k1; ++k) {
+    const int64_t b = __ldg(run_beg + k), en = __ldg(run_beg + k + 1);
+    const int64_t off = (int64_t)__ldg(run_col + k) - b;   // column of entry e = off + e
+    int64_t e = b + gl;
+    for (; e + G < en; e += 2 * G) {
+      const float2 a0 = __ldg(val + e), a1 = __ldg(val + e + G);
+      const float2 x0 = __ldg(x + (off + e)), x1 = __ldg(x + (off + e + G));
+      df_mac(a0, x0, h, l);
+      df_mac(a1, x1, h, l);
+    }
+    if (e < en) df_mac(__ldg(val + e), __ldg(x + (off + e)), h, l);
+  }
+  return df_group_sum<G>(h, l);
+}
+
+// ---------------------------------------------------------------- operator passes
+
+// v = omega o (R p), double-float products, v stored as pairs.  MODE 0: inside PCG (skips once
+// converged; the doubly augmented system's bottom block as in the FP64 pass); MODE 1: one apply.
+template <int MODE, int G, bool RUNS>
+__global__ void __launch_bounds__(256, 6) k_op_rows_df(Dev d) {
+  if (MODE == 0 && d.sc->cg_done) return;
+  const int gl = threadIdx.x & (G - 1);
+  FOR_GROUP_ROWS_D(G, ri, ok, d.nR) {
+    const int64_t r = (ok && d.rperm) ? (int64_t)d.rperm[ri] : ri;
+    double t;
+    if (RUNS) {
+      const int64_t k0 = ok ? d.run_ptr[r] : 0, k1 = ok ? d.run_ptr[r + 1] : 0;
+      t = group_runs_dot_df<G>(k0, k1, gl, d.run_col, d.run_beg, d.R_df, d.p_df);
+    } else {
+      const int64_t beg = ok ? d.R_ptr[r] : 0, end = ok ? d.R_ptr[r + 1] : 0;
+      t = group_row_dot_df<G>(beg, end, gl, d.R_idx, d.R_df, d.p_df);
+    }
+    if (ok && gl == 0) {
+      double v = d.omega[r] * t;
+      if (MODE == 0 && d.aug) {
+        const int32_t k = d.rowk[r];
+        if (k >= 0) {
+          const double pb = d.p[d.n + k];
+          v -= pb;
+          d.q[d.n + k] = -t + pb * (d.s[k] / d.y[k]);
+        }
+      }
+      d.v_df[r] = df_split(v);
+    }
+  }
+}
+
+// q = R^T v + Hs p + U (W t) + (h0 + sigma) o p with the R^T v sums in double-float; p^T q ->
+// alpha = rz / p^T q (last block), exactly as the FP64 column pass.
+template <int MODE, int G>
+__global__ void __launch_bounds__(256, 6) k_op_cols_df(Dev d) {
+  __shared__ double sh[32];
+  if (MODE == 0 && d.sc->cg_done) return;
+  const int gl = threadIdx.x & (G - 1);
+  double pq = 0.0;
+  FOR_GROUP_ROWS_D(G, j, ok, d.n) {
+    const int64_t beg = ok ? d.RT_ptr[j] : 0, end = ok ? d.RT_ptr[j + 1] : 0;
+    double acc = group_row_dot_df<G>(beg, end, gl, d.RT_idx, d.RT_df, d.v_df);
+    if (d.Hs_ptr) {
+      const int64_t hb = ok ? d.Hs_ptr[j] : 0, he = ok ? d.Hs_ptr[j + 1] : 0;
+      acc += group_row_dot<G, false>(hb, he, gl, d.Hs_idx, d.Hs_val, d.p);
+    }
+    if (d.ucols) acc += lr_row<G>(d, j, ok, gl);
+    if (ok && gl == 0) {
+      const double pj = d.p[j];
+      const double qj = acc + (d.h0[j] + d.sigma[j]) * pj;
+      d.q[j] = qj;
+      pq = fma(pj, qj, pq);
+    }
+  }
+  if (MODE == 1) return;
+  if (d.aug)
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.m; k += (int64_t)gridDim.x * blockDim.x)
+      pq = fma(d.p[d.n + k], d.q[d.n + k], pq);
+  double v[1] = {pq};
+  const int ops[1] = {0};
+  double out[1];
+  if (grid_reduce<1>(v, ops, d.partials + 16 * kMaxRedBlocks, &d.sc->ticket[T_PQ], out, sh)) {
+    if (threadIdx.x == 0) {
+      Scal* sc = d.sc;
+      const double pqv = out[0];
+      if (!(pqv > 0.0) || !isfinite(pqv)) {
+        sc->cg_done = 1;
+        if (!isfinite(pqv)) sc->status = DS_NUMERICAL;
+        sc->alpha = 0.0;
+      } else {
+        sc->alpha = sc->rz / pqv;
+      }
+      sc->pq = pqv;
+    }
+  }
+}
+
+cudaError_t launch_op_rows_df(const Dev& d, const Geo& g, int mode, cudaStream_t st) {
+  if (!d.nR) return cudaSuccess;
+  if (d.runs) {
+    if (mode == 0) { DISPATCH_GD(d.g_rows, k_op_rows_df<0, G, true><<<g.gRc, kBlock, 0, st>>>(d)); }
+    else { DISPATCH_GD(d.g_rows, k_op_rows_df<1, G, true><<<g.gRc, kBlock, 0, st>>>(d)); }
+  } else {
+    if (mode == 0) { DISPATCH_GD(d.g_rows, k_op_rows_df<0, G, false><<<g.gRc, kBlock, 0, st>>>(d)); }
+    else { DISPATCH_GD(d.g_rows, k_op_rows_df<1, G, false><<<g.gRc, kBlock, 0, st>>>(d)); }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_op_cols_df(const Dev& d, const Geo& g, int mode, cudaStream_t st) {
+  if (mode == 0) { DISPATCH_GD(d.g_cols, k_op_cols_df<0, G><<<g.gNc, kBlock, 0, st>>>(d)); }
+  else { DISPATCH_GD(d.g_cols, k_op_cols_df<1, G><<<g.gNc, kBlock, 0, st>>>(d)); }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- runs of R's rows
+
+// An entry starts a run if it is the first of its row or its column is not one more than the
+// previous entry's.  One warp per row; count[r] = runs of row r.
+__global__ void k_runs_count(Dev d, int32_t* __restrict__ count) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t r = gwarp_d(); r < d.nR; r += nwarps_d()) {
+    const int64_t beg = d.R_ptr[r], end = d.R_ptr[r + 1];
+    int c = 0;
+    for (int64_t e = beg + lane; e < end; e += 32)
+      c += (e == beg || d.R_idx[e] != d.R_idx[e - 1] + 1) ? 1 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) count[r] = c;
+  }
+}
+
+// run_col, run_beg from run_ptr (the exclusive scan of the counts): the starts of a row are
+// written in entry order by a ballot over each 32-entry stretch.
+__global__ void k_runs_fill(Dev d) {
+  const int lane = threadIdx.x & 31;
+  int32_t* col = const_cast<int32_t*>(d.run_col);
+  int64_t* rb = const_cast<int64_t*>(d.run_beg);
+  for (int64_t r = gwarp_d(); r < d.nR; r += nwarps_d()) {
+    const int64_t beg = d.R_ptr[r], end = d.R_ptr[r + 1];
+    int64_t k = d.run_ptr[r];
+    for (int64_t e0 = beg; e0 < end; e0 += 32) {
+      const int64_t e = e0 + lane;
+      const bool start = e < end && (e == beg || d.R_idx[e] != d.R_idx[e - 1] + 1);
+      const unsigned m = __ballot_sync(0xffffffffu, start);
+      if (start) {
+        const int64_t slot = k + __popc(m & ((1u << lane) - 1u));
+        col[slot] = d.R_idx[e];
+        rb[slot] = e;
+      }
+      k += __popc(m);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) rb[d.nruns] = d.nnzR;
+}
+
+cudaError_t launch_runs_count(const Dev& d, int32_t* count, cudaStream_t st) {
+  if (!d.nR) return cudaSuccess;
+  const int gb = (int)std::min<int64_t>((d.nR + 7) / 8, 8 * (int64_t)(d.sm_count > 0 ? d.sm_count : 148));
+  k_runs_count<<<gb, 256, 0, st>>>(d, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_runs_fill(const Dev& d, cudaStream_t st) {
+  const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((d.nR + 7) / 8, 8 * (int64_t)(d.sm_count > 0 ? d.sm_count : 148)));
+  k_runs_fill<<<gb, 256, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+}  // namespace ipmk

@@ -159,28 +159,6 @@ cudaError_t launch_lr(const Dev& d, const double* v, int quad, cudaStream_t st) 
   return cudaGetLastError();
 }
 
-// (U lrs)_j by a group of G lanes over the contiguous row j of U (all lanes of the group get it).
-template <int G>
-__device__ __forceinline__ double lr_row(const Dev& d, const int64_t j, const bool ok, const int gl) {
-  double a = 0.0;
-  if (ok) {
-    const double* row = d.U + j * d.ucols;
-    double a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    int64_t r = gl;
-    for (; r + 3 * G < d.ucols; r += 4 * G) {
-      a = fma(__ldg(row + r), __ldg(d.lrs + r), a);
-      a1 = fma(__ldg(row + r + G), __ldg(d.lrs + r + G), a1);
-      a2 = fma(__ldg(row + r + 2 * G), __ldg(d.lrs + r + 2 * G), a2);
-      a3 = fma(__ldg(row + r + 3 * G), __ldg(d.lrs + r + 3 * G), a3);
-    }
-    for (; r < d.ucols; r += G) a = fma(__ldg(row + r), __ldg(d.lrs + r), a);
-    a = (a + a1) + (a2 + a3);
-  }
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-  return a;
-}
-
 // ------------------------------------------------------------------------------ setup
 
 // diag(H)_j = h0_j + sum_i w_R,i R_ij^2 + sum_r uw_r U_jr^2 + Hs_jj  (computed once; Section
@@ -568,9 +546,12 @@ __global__ void k_control(Dev d, cudaGraphConditionalHandle h, int set_cond) {
   sc->cg_total += sc->cg_iter;
   sc->refine_total += refine;
   if (sc->cg_iter > sc->max_cg_step) sc->max_cg_step = sc->cg_iter;
-  // PCG stall: the direction of two consecutive Newton steps ended at the iteration limit
-  // without meeting its tolerance (one inexact direction is tolerated, inexact Newton)
-  sc->cg_fail_run = sc->cg_conv ? 0 : sc->cg_fail_run + 1;
+  // PCG stall: the PCG of two consecutive Newton steps ended at the iteration limit with a
+  // residual above 1e-2 of its right-hand side (worse than the loosest tolerance the method
+  // asks for).  A direction that misses a tight tolerance but is otherwise accurate is kept
+  // (inexact Newton): the paper's doubly augmented system under Jacobi PCG lives there.
+  const double cg_rel = sc->rhs2 > 0.0 ? sqrt(sc->rr / sc->rhs2) : 0.0;
+  sc->cg_fail_run = (sc->cg_conv || cg_rel <= 1e-2) ? 0 : sc->cg_fail_run + 1;
   if (sc->status == DS_RUNNING && sc->cg_fail_run >= 2) sc->status = DS_CG_STALL;
   if (sc->status == DS_NUMERICAL || sc->status == DS_CG_STALL || sc->status == DS_TIMEOUT) {
     sc->stop = 1;
@@ -1092,6 +1073,62 @@ __global__ void __launch_bounds__(256, 6) k_op_rows(Dev d) {
   }
 }
 
+// FP64 dot over the runs [k0, k1) of a row by a group of G lanes: entry e of run k sits in
+// column run_col[k] + (e - run_beg[k]), so no index is loaded and the gathers of a group read
+// consecutive addresses.
+template <int G>
+__device__ __forceinline__ double group_runs_dot(const int64_t k0, const int64_t k1, const int gl,
+                                                 const int32_t* __restrict__ run_col,
+                                                 const int64_t* __restrict__ run_beg,
+                                                 const double* __restrict__ val, const double* __restrict__ x) {
+  double a = 0.0;
+  for (int64_t k = k0; k < k1; ++k) {
+    const int64_t b = __ldg(run_beg + k), en = __ldg(run_beg + k + 1);
+    const int64_t off = (int64_t)__ldg(run_col + k) - b;
+    int64_t e = b + gl;
+    for (; e + G < en; e += 2 * G) {
+      const double v0 = __ldg(val + e), v1 = __ldg(val + e + G);
+      const double x0 = __ldg(x + (off + e)), x1 = __ldg(x + (off + e + G));
+      a = fma(v0, x0, a);
+      a = fma(v1, x1, a);
+    }
+    if (e < en) a = fma(__ldg(val + e), __ldg(x + (off + e)), a);
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  return a;
+}
+
+// v = omega o (R p) over the runs of R's rows (FP64); otherwise as k_op_rows.
+template <int MODE, int G>
+__global__ void __launch_bounds__(256, 6) k_op_rows_runs(Dev d) {
+  if (MODE == 0 && d.sc->cg_done) return;
+  FOR_GROUP_ROWS(G, ri, ok, d.nR) {
+    const int64_t r = (ok && d.rperm) ? (int64_t)d.rperm[ri] : ri;
+    const int64_t k0 = ok ? d.run_ptr[r] : 0, k1 = ok ? d.run_ptr[r + 1] : 0;
+    const double t = group_runs_dot<G>(k0, k1, glane<G>(), d.run_col, d.run_beg, d.R_val, d.p);
+    if (ok && glane<G>() == 0) {
+      double v = d.omega[r] * t;
+      if (MODE == 0 && d.aug) {
+        const int32_t k = d.rowk[r];
+        if (k >= 0) {
+          const double pb = d.p[d.n + k];
+          v -= pb;
+          d.q[d.n + k] = -t + pb * (d.s[k] / d.y[k]);
+        }
+      }
+      d.vR[r] = v;
+    }
+  }
+}
+
+cudaError_t launch_op_rows_runs(const Dev& d, const Geo& g, int mode, cudaStream_t st) {
+  if (!d.nR) return cudaSuccess;
+  if (mode == 0) DISPATCH_G(d.g_rows, k_op_rows_runs<0, G><<<g.gRc, kBlock, 0, st>>>(d));
+  else DISPATCH_G(d.g_rows, k_op_rows_runs<1, G><<<g.gRc, kBlock, 0, st>>>(d));
+  return cudaGetLastError();
+}
+
 // q = R^T v + Hs p + (h0 + sigma) o p; p^T q -> alpha = rz / p^T q (last block).
 // MODE 0: inside PCG; MODE 1: a single operator apply (no scalars touched).
 template <int MODE, int G>
@@ -1228,6 +1265,7 @@ __global__ void k_stiff_corr(Dev d, int init) {
     if (init) {
       d.p[j] = zj;
       if (d.p32) d.p32[j] = (float)zj;
+      if (d.p_df) d.p_df[j] = df_split(zj);
     }
     rz = fma(d.r[j], zj, rz);
   }
@@ -1312,6 +1350,7 @@ __global__ void __launch_bounds__(1024) k_dense_trsv(Dev d, int init) {
     if (init) {
       d.p[j] = zj;
       if (d.p32) d.p32[j] = (float)zj;
+      if (d.p_df) d.p_df[j] = df_split(zj);
     }
     rz = fma(d.r[j], zj, rz);
   }
@@ -1335,6 +1374,7 @@ __global__ void k_cg_init_diag(Dev d) {
     const double zj = d.r[j] * d.Minv[j];
     d.z[j] = zj;
     d.p[j] = zj;
+    if (d.p_df && j < d.n) d.p_df[j] = df_split(zj);
     rz = fma(d.r[j], zj, rz);
   }
   double v[1] = {rz};
@@ -1356,6 +1396,7 @@ __global__ void k_cg_p(Dev d, cudaGraphConditionalHandle h, int set_cond) {
     const double pj = fma(beta, d.p[j], d.z[j]);
     d.p[j] = pj;
     if (d.p32) d.p32[j] = (float)pj;
+    if (d.p_df && j < d.n) d.p_df[j] = df_split(pj);
   }
 }
 
@@ -1379,8 +1420,13 @@ cudaError_t launch_cg_body(const Dev& d, const Geo& g, int precond, cudaGraphCon
   if (lowp) {
     cudaError_t e = launch_op_lp(d, g, st);
     if (e != cudaSuccess) return e;
+  } else if (d.df) {
+    launch_op_rows_df(d, g, 0, st);
+    launch_lr(d, d.p, 0, st);
+    launch_op_cols_df(d, g, 0, st);
   } else {
-    if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<0, G><<<g.gRc, kBlock, 0, st>>>(d));
+    if (d.runs) launch_op_rows_runs(d, g, 0, st);
+    else if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<0, G><<<g.gRc, kBlock, 0, st>>>(d));
     launch_lr(d, d.p, 0, st);
     DISPATCH_G(d.g_cols, k_op_cols<0, G><<<g.gNc, kBlock, 0, st>>>(d));
   }
@@ -1400,19 +1446,33 @@ cudaError_t launch_cg_body(const Dev& d, const Geo& g, int precond, cudaGraphCon
   return cudaGetLastError();
 }
 
+// The rows and the column pass of the handle's FP64-storage PCG operator alone (measurement,
+// autotuning); the double-float passes read p_df, which the caller keeps current.
 cudaError_t launch_op_rows_only(const Dev& d, const Geo& g, cudaStream_t st) {
+  if (d.df) return launch_op_rows_df(d, g, 1, st);
+  if (d.runs) return launch_op_rows_runs(d, g, 1, st);
   if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<1, G><<<g.gRc, kBlock, 0, st>>>(d));
   return cudaGetLastError();
 }
 
 cudaError_t launch_op_cols_only(const Dev& d, const Geo& g, cudaStream_t st) {
   // (the low-rank term uses us from the last launch_lr; the measurement does not re-run it)
+  if (d.df) return launch_op_cols_df(d, g, 1, st);
   DISPATCH_G(d.g_cols, k_op_cols<1, G><<<g.gNc, kBlock, 0, st>>>(d));
   return cudaGetLastError();
 }
 
+// q = K p, one apply of the handle's FP64-storage PCG operator (FP64 or double-float).
 cudaError_t launch_apply(const Dev& d, const Geo& g, cudaStream_t st) {
-  if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<1, G><<<g.gRc, kBlock, 0, st>>>(d));
+  if (d.df) {
+    launch_mirror_df(d, g, st);
+    launch_op_rows_df(d, g, 1, st);
+    launch_lr(d, d.p, 0, st);
+    launch_op_cols_df(d, g, 1, st);
+    return cudaGetLastError();
+  }
+  if (d.runs) launch_op_rows_runs(d, g, 1, st);
+  else if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<1, G><<<g.gRc, kBlock, 0, st>>>(d));
   launch_lr(d, d.p, 0, st);
   DISPATCH_G(d.g_cols, k_op_cols<1, G><<<g.gNc, kBlock, 0, st>>>(d));
   return cudaGetLastError();

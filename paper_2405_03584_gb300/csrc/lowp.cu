@@ -172,28 +172,6 @@ __device__ __forceinline__ float group_row_dot_lp(const int64_t beg, const int64
   return a;
 }
 
-// (U lrs)_j by a group of G lanes (the FP64 low-rank Hessian term, as in the FP64 kernels).
-template <int G>
-__device__ __forceinline__ double lr_row_lp(const Dev& d, const int64_t j, const bool ok, const int gl) {
-  double a = 0.0;
-  if (ok) {
-    const double* row = d.U + j * d.ucols;
-    double a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    int64_t r = gl;
-    for (; r + 3 * G < d.ucols; r += 4 * G) {
-      a = fma(__ldg(row + r), __ldg(d.lrs + r), a);
-      a1 = fma(__ldg(row + r + G), __ldg(d.lrs + r + G), a1);
-      a2 = fma(__ldg(row + r + 2 * G), __ldg(d.lrs + r + 2 * G), a2);
-      a3 = fma(__ldg(row + r + 3 * G), __ldg(d.lrs + r + 3 * G), a3);
-    }
-    for (; r < d.ucols; r += G) a = fma(__ldg(row + r), __ldg(d.lrs + r), a);
-    a = (a + a1) + (a2 + a3);
-  }
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-  return a;
-}
-
 #define FOR_GROUP_ROWS_L(G, r, ok, nrows)                                                                    \
   for (int64_t r##_0 = (int64_t)gwarp_l() * (32 / G); r##_0 < (nrows); r##_0 += (int64_t)nwarps_l() * (32 / G)) \
     for (int64_t r = r##_0 + (threadIdx.x & 31) / G, r##_once = 0; r##_once == 0; r##_once = 1)               \
@@ -250,7 +228,7 @@ __global__ void __launch_bounds__(256, 6) k_op_cols_lp(Dev d, int standalone) {
       const int64_t hb = ok ? d.Hs_ptr[j] : 0, he = ok ? d.Hs_ptr[j + 1] : 0;
       hs = group_row_dot<G, false>(hb, he, gl, d.Hs_idx, d.Hs_val, d.p);
     }
-    if (d.ucols) hs += lr_row_lp<G>(d, j, ok, gl);   // low-rank term kept in FP64
+    if (d.ucols) hs += lr_row<G>(d, j, ok, gl);   // low-rank term kept in FP64
     if (ok && gl == 0) {
       const double pj = d.p[j];
       double st = 0.0;
@@ -295,9 +273,64 @@ __global__ void __launch_bounds__(256, 6) k_op_cols_lp(Dev d, int standalone) {
     default: { constexpr int G = 32; __VA_ARGS__; } break;    \
   }
 
+// FP32 dot over the runs [k0, k1) of a stored row by a group of G lanes: lane gl takes
+// entries gl, gl + G, ... of each run, so a group reads consecutive values and gathers the
+// FP32 vector at consecutive addresses; no index array is read.
+template <int S, int G>
+__device__ __forceinline__ float group_runs_dot_lp(const int64_t k0, const int64_t k1, const int gl,
+                                                   const int32_t* __restrict__ run_col,
+                                                   const int64_t* __restrict__ run_beg,
+                                                   const typename StorageT<S>::T* __restrict__ val,
+                                                   const float* __restrict__ x) {
+  float a = 0.f, b = 0.f;
+  for (int64_t k = k0; k < k1; ++k) {
+    const int64_t rb = __ldg(run_beg + k), en = __ldg(run_beg + k + 1);
+    const int64_t off = (int64_t)__ldg(run_col + k) - rb;
+    int64_t e = rb + gl;
+    for (; e + 3 * G < en; e += 4 * G) {
+      const float v0 = StorageT<S>::dec(val[e]), v1 = StorageT<S>::dec(val[e + G]);
+      const float v2 = StorageT<S>::dec(val[e + 2 * G]), v3 = StorageT<S>::dec(val[e + 3 * G]);
+      const float x0 = __ldg(x + (off + e)), x1 = __ldg(x + (off + e + G));
+      const float x2 = __ldg(x + (off + e + 2 * G)), x3 = __ldg(x + (off + e + 3 * G));
+      a = fmaf(v0, x0, a);
+      b = fmaf(v1, x1, b);
+      a = fmaf(v2, x2, a);
+      b = fmaf(v3, x3, b);
+    }
+    for (; e < en; e += G) a = fmaf(StorageT<S>::dec(val[e]), __ldg(x + (off + e)), a);
+  }
+  a += b;
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  return a;
+}
+
+// The reduced-precision rows pass over the runs of R's rows (otherwise as k_op_rows_lp).
+template <int S, int G>
+__global__ void __launch_bounds__(256, 6) k_op_rows_lp_runs(Dev d, int standalone) {
+  if (!standalone && d.sc->cg_done) return;
+  using T = typename StorageT<S>::T;
+  const T* q = static_cast<const T*>(d.Rq);
+  const int gl = threadIdx.x & (G - 1);
+  FOR_GROUP_ROWS_L(G, r, ok, d.nR) {
+    const int64_t k0 = ok ? d.run_ptr[r] : 0, k1 = ok ? d.run_ptr[r + 1] : 0;
+    const float t = group_runs_dot_lp<S, G>(k0, k1, gl, d.run_col, d.run_beg, q, d.p32);
+    if (ok && gl == 0) {
+      const double s = (double)d.scaleR[r];
+      d.w32[r] = (float)((d.wR[r] + d.thR[r]) * s * s * (double)t);
+    }
+  }
+}
+
 static void launch_rows_lp(const Dev& d, const Geo& g, int standalone, cudaStream_t st) {
   if (!d.nR) return;
-  DISPATCH_SG(d.storage, d.g_rows, k_op_rows_lp<S, G><<<g.gR, kBlock, 0, st>>>(d, standalone));
+  if (d.runs) DISPATCH_SG(d.storage, d.g_rows, k_op_rows_lp_runs<S, G><<<g.gRc, kBlock, 0, st>>>(d, standalone));
+  else DISPATCH_SG(d.storage, d.g_rows, k_op_rows_lp<S, G><<<g.gR, kBlock, 0, st>>>(d, standalone));
+}
+
+cudaError_t launch_op_rows_lp_runs(const Dev& d, const Geo& g, int standalone, cudaStream_t st) {
+  if (d.nR) DISPATCH_SG(d.storage, d.g_rows, k_op_rows_lp_runs<S, G><<<g.gRc, kBlock, 0, st>>>(d, standalone));
+  return cudaGetLastError();
 }
 
 cudaError_t launch_op_lp(const Dev& d, const Geo& g, cudaStream_t st) {

@@ -66,6 +66,20 @@ struct Dev {
   double* Kd;                  // n x n: the condensed matrix, then its Cholesky factor (L and L^T)
   double* Rd;                  // nR x n: R as a dense matrix (when it is small enough), or nullptr
   double* chol_diag;           // max(n_dense, stiff_cap): original diagonal during a factorisation
+  // double-float operator (storage ST_F64 with options.op_arith = DF32): the values of R and
+  // R^T as (hi, lo) float32 pairs, the PCG direction p and the rows-pass result v likewise;
+  // the FP64 copies stay for the residuals, the start point and the stiff-row correction
+  int df;
+  const float2 *R_df, *RT_df;  // nnzR each
+  float2 *p_df, *v_df;         // n, nR
+  // runs of R's rows: maximal stretches of consecutive entries whose columns increase by one
+  // (the contiguous spot bands of a dose row); the rows pass reads columns from them instead
+  // of the index array when `runs` is set
+  int runs;
+  int64_t nruns;
+  const int64_t* run_ptr;      // nR + 1: runs of row r are [run_ptr[r], run_ptr[r+1])
+  const int32_t* run_col;      // nruns: first column of each run
+  const int64_t* run_beg;      // nruns + 1: first entry of each run; run_beg[nruns] = nnzR
   // reduced-precision copy of the matrix values (storage != ST_F64): R~_ij = scaleR_i * q_ij
   int storage;
   void *Rq, *RTq;              // nnzR values each (float / bf16 / fp8-e4m3), indices shared with R, R^T
@@ -77,6 +91,28 @@ struct Dev {
   double* partials;            // 32 * kMaxRedBlocks
   Scal* sc;
 };
+
+// (U lrs)_j by a group of G lanes over the contiguous row j of U (all lanes of the group get it).
+template <int G>
+__device__ __forceinline__ double lr_row(const Dev& d, const int64_t j, const bool ok, const int gl) {
+  double a = 0.0;
+  if (ok) {
+    const double* row = d.U + j * d.ucols;
+    double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int64_t r = gl;
+    for (; r + 3 * G < d.ucols; r += 4 * G) {
+      a = fma(__ldg(row + r), __ldg(d.lrs + r), a);
+      a1 = fma(__ldg(row + r + G), __ldg(d.lrs + r + G), a1);
+      a2 = fma(__ldg(row + r + 2 * G), __ldg(d.lrs + r + 2 * G), a2);
+      a3 = fma(__ldg(row + r + 3 * G), __ldg(d.lrs + r + 3 * G), a3);
+    }
+    for (; r < d.ucols; r += G) a = fma(__ldg(row + r), __ldg(d.lrs + r), a);
+    a = (a + a1) + (a2 + a3);
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  return a;
+}
 
 // Launch geometry shared by the host code and the final reduction kernel.
 struct Geo {
@@ -121,6 +157,16 @@ cudaError_t launch_op_lp(const Dev& d, const Geo& g, cudaStream_t st);
 cudaError_t launch_op_rows_lp_only(const Dev& d, const Geo& g, cudaStream_t st);   // measurement
 cudaError_t launch_op_cols_lp_only(const Dev& d, const Geo& g, cudaStream_t st);
 cudaError_t launch_mirror_p32(const Dev& d, const Geo& g, cudaStream_t st);
+// ---- double-float operator (df.cu) ----
+cudaError_t launch_df_split(const Dev& d, int* out_of_range, cudaStream_t st);   // R_df, RT_df from the FP64 values
+cudaError_t launch_mirror_df(const Dev& d, const Geo& g, cudaStream_t st);        // p_df from p
+cudaError_t launch_op_rows_df(const Dev& d, const Geo& g, int mode, cudaStream_t st);
+cudaError_t launch_op_cols_df(const Dev& d, const Geo& g, int mode, cudaStream_t st);
+// ---- runs of R's rows (df.cu) ----
+cudaError_t launch_runs_count(const Dev& d, int32_t* count, cudaStream_t st);     // runs per row
+cudaError_t launch_runs_fill(const Dev& d, cudaStream_t st);                      // run_col, run_beg
+cudaError_t launch_op_rows_runs(const Dev& d, const Geo& g, int mode, cudaStream_t st);   // FP64 (kernels.cu)
+cudaError_t launch_op_rows_lp_runs(const Dev& d, const Geo& g, int standalone, cudaStream_t st);  // lowp.cu
 cudaError_t launch_refine_start(const Dev& d, const Geo& g, cudaStream_t st);
 cudaError_t launch_refine_inner(const Dev& d, const Geo& g, cudaGraphConditionalHandle hi, cudaStream_t st);
 cudaError_t launch_refine_tail(const Dev& d, const Geo& g, cudaGraphConditionalHandle h, cudaStream_t st);

@@ -24,6 +24,8 @@ STATIC_SCRATCH_ROWS = 262144
 MEM_HOST, MEM_DEVICE = 0, 1
 PRECOND = {"jacobi": 0, "jacobi_lr": 1, "dense": 2, "auto": 3}
 STORAGE = {"f64": 0, "f32": 1, "bf16": 2, "fp8": 3, "fp8_e4m3": 3}
+ARITH = {"f64": 0, "df32": 1}
+ROWS_FORMAT = {"auto": 0, "csr": 1, "runs": 2}
 COLD, WARM = 0, 1
 
 EXPORTS = ["ipm_default_options", "ipm_create", "ipm_set_qp", "ipm_solve", "ipm_get_xyz", "ipm_destroy",
@@ -31,7 +33,8 @@ EXPORTS = ["ipm_default_options", "ipm_create", "ipm_set_qp", "ipm_solve", "ipm_
            "ipm_precond_diag", "ipm_newton_direction", "ipm_step_lengths", "ipm_profile_operator",
            "ipm_get_trace", "ipm_apply_operator_static", "ipm_solve_async", "ipm_solve_wait", "ipm_solve_query",
            "ipm_batch_create", "ipm_batch_solve", "ipm_batch_destroy", "ipm_update_costs", "ipm_share_qp",
-           "ipm_device_bytes", "ipm_set_lowrank", "ipm_abi_sizes", "ipm_get_sizes", "ipm_autotune_reset"]
+           "ipm_device_bytes", "ipm_set_lowrank", "ipm_abi_sizes", "ipm_get_sizes", "ipm_autotune_reset",
+           "ipm_get_info"]
 TRACE_COLS = ("iter", "mu", "rel_kkt", "primal", "dual", "gap", "alpha_p", "alpha_d", "pcg_iters", "pcg_converged",
               "stiff_rows", "pcg_rel_residual", "eta", "refine_passes")
 
@@ -45,7 +48,7 @@ class Options(C.Structure):
                 ("storage", C.c_int), ("refine_max", C.c_int), ("refine_eta", C.c_double),
                 ("lanes_rows", C.c_int), ("lanes_cols", C.c_int), ("warm_rho", C.c_double),
                 ("u_cap", C.c_int), ("ingest_host", C.c_int), ("system", C.c_int),
-                ("lanes_at", C.c_int)]
+                ("lanes_at", C.c_int), ("op_arith", C.c_int), ("rows_format", C.c_int)]
 
 
 class QP(C.Structure):
@@ -63,7 +66,8 @@ class Info(C.Structure):
                 ("primal_res", C.c_double), ("dual_res", C.c_double), ("gap_res", C.c_double),
                 ("primal_obj", C.c_double), ("dual_obj", C.c_double), ("mu", C.c_double), ("solve_ms", C.c_double),
                 ("kernel_launches", C.c_int64), ("lanes_rows", C.c_int), ("lanes_cols", C.c_int),
-                ("refine_passes", C.c_int64), ("fallback_steps", C.c_int64)]
+                ("refine_passes", C.c_int64), ("fallback_steps", C.c_int64), ("op_arith", C.c_int),
+                ("rows_runs", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -119,6 +123,7 @@ def load(path: str = LIB_PATH):
         "ipm_abi_sizes": (I, [P, P, P, P]),
         "ipm_get_sizes": (I, [P, P, P, P]),
         "ipm_autotune_reset": (I, []),
+        "ipm_get_info": (I, [P, C.POINTER(Info)]),
         "ipm_apply_operator_static": (I, [C.c_int64, C.c_int64] + [P] * 10 + [P]),
     }
     for name, (res, args) in sig.items():
@@ -200,6 +205,10 @@ class Solver:
                 v = STORAGE[v]
             if k == "system" and isinstance(v, str):
                 v = {"condensed": 0, "augmented": 1}[v]
+            if k == "op_arith" and isinstance(v, str):
+                v = ARITH[v]
+            if k == "rows_format" and isinstance(v, str):
+                v = ROWS_FORMAT[v]
             if not hasattr(o, k):
                 raise TypeError("unknown option %s" % k)
             setattr(o, k, v)
@@ -354,6 +363,17 @@ class Solver:
         if rc not in (IPM_OK, IPM_BUSY):
             self._check(rc, "ipm_solve_query")
         return rc == IPM_OK
+
+    def info(self):
+        """ipm_info: the last solve's results and the operator configuration of the loaded QP."""
+        info = Info()
+        self._check(load().ipm_get_info(self._h, C.byref(info)), "ipm_get_info")
+        return info.as_dict()
+
+    def get_config(self):
+        """The operator configuration chosen at set_qp: op_arith, rows_runs, lanes_rows, lanes_cols."""
+        i = self.info()
+        return {k: i[k] for k in ("op_arith", "rows_runs", "lanes_rows", "lanes_cols")}
 
     def get(self, stream=None, out=None):
         """Returns dict(x, y, zl, zu, s, info).  ``out`` may give preallocated device tensors."""

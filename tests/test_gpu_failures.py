@@ -35,14 +35,15 @@ def test_max_iter():
 @pytest.mark.parametrize("storage", ["f64", "bf16"])
 def test_cg_stall(storage):
     """One PCG iteration per Newton step against a tolerance of 1e-12: the first direction
-    is inexact and tolerated, the second ends the solve with IPM_CG_STALL."""
+    (residual far above 1e-2 of its right-hand side) is tolerated, the second ends the solve
+    with IPM_CG_STALL."""
     p = W.rt_qp(n=1200, seed=82)
     with ipm.Solver(tol_kkt=1e-8, max_cg=1, cg_eta_min=1e-12, cg_eta_max=1e-12, storage=storage, refine_max=1) as s:
         s.set_qp_rt(p)
         assert s.solve() == ipm.IPM_CG_STALL
         info = s.get()["info"]
         assert info["ipm_iters"] == 2, info
-        assert all(t["pcg_converged"] == 0 for t in s.trace())
+        assert all(t["pcg_converged"] == 0 and t["pcg_rel_residual"] > 1e-2 for t in s.trace())
         # the iterate is kept and stays strictly interior
         out = s.get()
         assert np.all(out["x"] > p["l"]) and np.all(out["x"] < p["u"]) and np.all(out["s"] > 0)

@@ -1,0 +1,139 @@
+"""The PCG operator's arithmetic (float64 or double-float) and the format of its rows pass
+(CSR or runs) on every problem family, against the CPU oracle: whole solves at the accuracy
+bar (checker rel. KKT <= tol, relative objective difference <= 1e-6 against the oracle's),
+bitwise reproducibility, the graph and direct-launch paths, and the fallbacks (double-float
+refused for values outside the float32 pair's range; runs not taken by AUTO when rows are
+scattered)."""
+import numpy as np
+import pytest
+
+from oracle import ipm as O
+from oracle import kkt_check
+from paper_2405_03584_gb300 import ipm, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = [("f64", "runs"), ("df32", "csr"), ("df32", "runs")]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2405_03584_gb300 import build
+    build.build()
+    ipm.load()
+
+
+def _check(p, qp, st, out, tol, ops):
+    assert st == ipm.IPM_OK, out["info"]
+    rk = kkt_check.rel_kkt(ops, out["x"], out["y"], out["zl"], out["zu"])
+    assert rk <= tol * 1.0001, rk
+    ref, info = O.solve(qp, tol=min(tol, 1e-9))
+    assert info.status == "optimal"
+    f, f0 = O.objective(qp, out["x"]), O.objective(qp, ref.x)
+    assert abs(f - f0) / (1 + abs(f0)) <= 1e-6
+
+
+@pytest.mark.parametrize("arith,fmt", VARIANTS, ids=["%s-%s" % v for v in VARIANTS])
+@pytest.mark.parametrize("precond", ["jacobi_lr", "jacobi"])
+def test_rt_solves(arith, fmt, precond):
+    p = W.rt_qp(n=1500, seed=9)
+    with ipm.Solver(tol_kkt=1e-7, precond=precond, op_arith=arith, rows_format=fmt, max_cg=20000) as s:
+        s.set_qp_rt(p)
+        st = s.solve()
+        out = s.get()
+    assert out["info"]["op_arith"] == ipm.ARITH[arith] and out["info"]["rows_runs"] == (fmt == "runs")
+    _check(p, O.from_rt(p), st, out, 1e-7, kkt_check.rt_ops(p))
+
+
+@pytest.mark.parametrize("arith,fmt", VARIANTS, ids=["%s-%s" % v for v in VARIANTS])
+def test_dense_h_block_solves(arith, fmt):
+    """A dense H block (its FP64 part of the column pass) and dense rows of A (one run each)."""
+    p = W.dense_qp(n=300, m=700, seed=2)
+    with ipm.Solver(tol_kkt=1e-8, precond="jacobi_lr", op_arith=arith, rows_format=fmt, max_cg=20000) as s:
+        s.set_qp_dense(p["H"], p["c"], p["A"], p["b"], p["l"], p["u"])
+        st = s.solve()
+        out = s.get()
+    _check(p, O.from_dense(p), st, out, 1e-8, kkt_check.dense_ops(p))
+
+
+@pytest.mark.parametrize("arith,fmt", VARIANTS, ids=["%s-%s" % v for v in VARIANTS])
+def test_lowrank_hessian_solves(arith, fmt):
+    """The quasi-Newton term U W U^T (FP64 inside the double-float column pass) with CSR rows."""
+    q = W.bfgs_qp(n=3000, k=20, m_ub=900, m_lb=300, density=0.01, seed=6, c_mode="target", ub_fac=1.1, lb_fac=0.9)
+    with ipm.Solver(tol_kkt=1e-7, precond="jacobi_lr", op_arith=arith, rows_format=fmt, stiff_max=1024) as s:
+        s.set_qp_bfgs(q)
+        st = s.solve()
+        out = s.get()
+    qp = O.from_bfgs(q)
+    _check(q, qp, st, out, 1e-7, kkt_check.bfgs_ops(q))
+
+
+@pytest.mark.parametrize("arith,fmt", VARIANTS, ids=["%s-%s" % v for v in VARIANTS])
+def test_augmented_and_two_sided_solves(arith, fmt):
+    """The paper's doubly augmented system (the rows pass also forms its bottom block) and
+    two-sided rows (negated copies of rows appended to R)."""
+    p = W.rt_qp(n=900, seed=13)
+    with ipm.Solver(tol_kkt=1e-8, system="augmented", op_arith=arith, rows_format=fmt, max_cg=50000) as s:
+        s.set_qp_rt(p)
+        st = s.solve()
+        out = s.get()
+    _check(p, O.from_rt(p), st, out, 1e-8, kkt_check.rt_ops(p))
+    t = W.rt_two_sided(W.rt_qp(n=1100, seed=5), n_window=40)
+    with ipm.Solver(tol_kkt=1e-8, precond="jacobi_lr", op_arith=arith, rows_format=fmt, stiff_max=1024) as s:
+        s.set_qp_rt(t)
+        st = s.solve()
+        out = s.get()
+    assert st == ipm.IPM_OK, out["info"]
+    dq = O.from_rt(t)
+    qp, _, _ = O.two_sided(dq.H, dq.c, dq.A, t["bl"], t["b"], dq.l, dq.u)
+    ref, info = O.solve(qp, tol=1e-9)
+    f, f0 = O.objective(qp, out["x"]), O.objective(qp, ref.x)
+    assert abs(f - f0) / (1 + abs(f0)) <= 1e-6
+
+
+@pytest.mark.parametrize("arith,fmt", VARIANTS, ids=["%s-%s" % v for v in VARIANTS])
+def test_bitwise_reproducible_and_direct_launches(arith, fmt):
+    p = W.rt_qp(n=900, seed=14)
+    xs = []
+    for ug in (1, 1, 0):
+        with ipm.Solver(tol_kkt=1e-8, precond="jacobi_lr", op_arith=arith, rows_format=fmt, use_graphs=ug) as s:
+            s.set_qp_rt(p)
+            assert s.solve() == ipm.IPM_OK
+            xs.append(s.get()["x"])
+    assert np.array_equal(xs[0], xs[1]) and np.array_equal(xs[0], xs[2])
+
+
+def test_double_float_refused_out_of_range():
+    """Values beyond 2^90 would lose bits in a float32 pair: the handle keeps float64."""
+    p = W.rt_qp(n=400, seed=15)
+    big = dict(p)
+    big["D_data"] = p["D_data"] * 2.0 ** 95
+    big["w"] = p["w"] * 2.0 ** -190
+    with ipm.Solver(tol_kkt=1e-8, op_arith="df32") as s:
+        s.set_qp_rt(big)
+        assert s.get_config()["op_arith"] == ipm.ARITH["f64"]
+    with ipm.Solver(tol_kkt=1e-8, op_arith="df32") as s:
+        s.set_qp_rt(p)
+        assert s.get_config()["op_arith"] == ipm.ARITH["df32"]
+
+
+def test_runs_auto_detection():
+    """AUTO takes runs for banded dose rows and keeps CSR for rows of scattered columns."""
+    p = W.rt_qp(n=700, seed=16)
+    with ipm.Solver() as s:
+        s.set_qp_rt(p)
+        assert s.get_config()["rows_runs"] == 1
+    rng = np.random.default_rng(3)
+    n, m = 400, 300
+    A = np.where(rng.random((m, n)) < 0.05, rng.normal(size=(m, n)), 0.0)
+    with ipm.Solver() as s:
+        s.set_qp(n, m, rng.normal(size=n), np.abs(A).sum(1) + 1.0, np.zeros(n), np.ones(n), h0=np.ones(n),
+                 A=_csr(A))
+        assert s.get_config()["rows_runs"] == 0
+
+
+def _csr(A):
+    rows, cols = np.nonzero(A)
+    ip = np.zeros(A.shape[0] + 1, np.int64)
+    np.cumsum(np.bincount(rows, minlength=A.shape[0]), out=ip[1:])
+    return ip, cols.astype(np.int32), A[rows, cols]
