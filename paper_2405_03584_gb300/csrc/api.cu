@@ -407,37 +407,47 @@ int prepare_operator_formats(ipm_handle* h) {
     d.df = bad ? 0 : 1;
   }
   d.runs = 0;
-  d.nruns = 0;
-  d.run_ptr = nullptr;
-  d.run_col = nullptr;
-  d.run_beg = nullptr;
+  d.npieces = 0;
+  d.pc_ptr = nullptr;
+  d.pc_col = nullptr;
+  d.pc_ol = nullptr;
   if (h->opt.rows_format == IPM_ROWS_CSR || d.nR == 0 || d.nnzR == 0) return IPM_OK;
-  int32_t* cnt = reinterpret_cast<int32_t*>(d.tR);     // nR doubles of iteration work space
-  CUDA_TRY(h, launch_runs_count(d, cnt, h->st));
-  std::vector<int32_t> hc((size_t)d.nR);
-  CUDA_TRY(h, cudaMemcpyAsync(hc.data(), cnt, sizeof(int32_t) * (size_t)d.nR, cudaMemcpyDeviceToHost, h->st));
+  // per row: runs and pieces (two int32 per row in the nR doubles of iteration work space tR)
+  int32_t* cnt = reinterpret_cast<int32_t*>(d.tR);
+  CUDA_TRY(h, launch_runs_count(d, cnt, cnt + d.nR, h->st));
+  std::vector<int32_t> hc(2 * (size_t)d.nR);
+  std::vector<int64_t> rows(d.nR + 1);
+  CUDA_TRY(h, cudaMemcpyAsync(hc.data(), cnt, sizeof(int32_t) * hc.size(), cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(rows.data(), d.R_ptr, sizeof(int64_t) * rows.size(), cudaMemcpyDeviceToHost, h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
-  std::vector<int64_t> rp((size_t)d.nR + 1, 0);
-  for (int64_t r = 0; r < d.nR; ++r) rp[r + 1] = rp[r] + hc[r];
-  const int64_t nruns = rp[d.nR];
-  const bool use = nruns > 0 && (h->opt.rows_format == IPM_ROWS_RUNS || (double)d.nnzR >= 8.0 * (double)nruns);
+  std::vector<int64_t> pp((size_t)d.nR + 1, 0);
+  int64_t nruns = 0, longest = 0;
+  for (int64_t r = 0; r < d.nR; ++r) {
+    nruns += hc[r];
+    pp[r + 1] = pp[r] + hc[d.nR + r];
+    longest = std::max<int64_t>(longest, rows[r + 1] - rows[r]);
+  }
+  const int64_t npieces = pp[d.nR];
+  // a piece records its offset in the row in 26 bits
+  if (nruns == 0 || longest >= ((int64_t)1 << 26)) return IPM_OK;
+  const bool use = h->opt.rows_format == IPM_ROWS_RUNS || (double)d.nnzR >= 8.0 * (double)nruns;
   if (!use) return IPM_OK;
   Carver cc(nullptr);
   cc.take<int64_t>(d.nR + 1);
-  cc.take<int32_t>(nruns);
-  cc.take<int64_t>(nruns + 1);
+  cc.take<int32_t>(npieces);
+  cc.take<uint32_t>(npieces);
   const size_t bytes = cc.off + 256;
   if (h->opt.mem_budget > 0 && (double)(h->mat->bytes + h->arena_bytes + bytes) > h->opt.mem_budget)
     return IPM_OK;                                     // within the budget the rows pass stays CSR
   int rc;
-  if ((rc = dev_alloc(h, &h->mat->aux, bytes, "runs of R's rows"))) return rc;
+  if ((rc = dev_alloc(h, &h->mat->aux, bytes, "pieces of R's runs"))) return rc;
   h->mat->bytes += bytes;
   Carver cv((char*)h->mat->aux);
-  d.run_ptr = cv.take<int64_t>(d.nR + 1);
-  d.run_col = cv.take<int32_t>(nruns);
-  d.run_beg = cv.take<int64_t>(nruns + 1);
-  d.nruns = nruns;
-  CUDA_TRY(h, cudaMemcpyAsync((void*)d.run_ptr, rp.data(), sizeof(int64_t) * rp.size(), cudaMemcpyHostToDevice, h->st));
+  d.pc_ptr = cv.take<int64_t>(d.nR + 1);
+  d.pc_col = cv.take<int32_t>(npieces);
+  d.pc_ol = cv.take<uint32_t>(npieces);
+  d.npieces = npieces;
+  CUDA_TRY(h, cudaMemcpyAsync((void*)d.pc_ptr, pp.data(), sizeof(int64_t) * pp.size(), cudaMemcpyHostToDevice, h->st));
   CUDA_TRY(h, launch_runs_fill(d, h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
   d.runs = 1;
@@ -2058,7 +2068,8 @@ int ipm_profile_operator(ipm_handle* h, int reps, double* ms_rows, double* ms_co
   const double lr_b = d.ucols ? 8.0 * n * (double)d.ucols + 8.0 * (double)d.ucols : 0.0;
   const double lr_f = d.ucols ? 2.0 * n * (double)d.ucols : 0.0;
   // the rows pass reads, per row, its row pointers (CSR) or its run pointers and runs
-  const double row_index = d.runs ? 8.0 * (nR + 1) + 12.0 * (double)d.nruns + 8.0 : 4.0 * nnz + 8.0 * (nR + 1);
+  // (pieces: the row pointers of R for the entry offsets, the piece pointers, 8 bytes a piece)
+  const double row_index = d.runs ? 16.0 * (nR + 1) + 8.0 * (double)d.npieces : 4.0 * nnz + 8.0 * (nR + 1);
   const double hs_b = d.Hs_ptr ? 12.0 * nnzh + 8.0 * (n + 1) : 0.0;
   if (lp) {
     const double vb = d.storage == ST_F32 ? 4.0 : (d.storage == ST_BF16 ? 2.0 : 1.0);

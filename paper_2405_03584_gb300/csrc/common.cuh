@@ -324,7 +324,21 @@ __device__ __forceinline__ void df_mac(const float2 a, const float2 x, float& h,
   l = __fadd_rn(l, __fadd_rn(t, e));
 }
 
-// Sum of the pairs of a group of G lanes (fixed butterfly order; every lane gets the total).
+// Sum of the pairs of a group of G lanes in place (fixed butterfly order; every lane of the
+// group gets the total pair).
+template <int G>
+__device__ __forceinline__ void df_group_pair(float& h, float& l) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+    float s, t;
+    two_sum(h, oh, s, t);
+    h = s;
+    l = __fadd_rn(__fadd_rn(l, ol), t);
+  }
+}
+
+// The same, returned as one float64 value.
 template <int G>
 __device__ __forceinline__ double df_group_sum(float h, float l) {
 #pragma unroll

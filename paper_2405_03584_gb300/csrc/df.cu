@@ -12,9 +12,10 @@
 // the start point, the right-hand side and the preconditioner keep the FP64 copies.
 //
 // Runs: the columns of a dose row come in a few contiguous spot bands.  A run is a maximal
-// stretch of consecutive stored entries of a row whose columns increase by one; the rows pass
-// over runs reads (first column, first entry) per run instead of one int32 index per entry,
-// and gathers p at consecutive addresses.
+// stretch of consecutive stored entries of a row whose columns increase by one; runs are cut
+// into pieces of at most 32 entries, and the rows pass over pieces reads one 8-byte
+// descriptor per piece instead of one int32 index per entry, with the values and the gathers
+// of p at consecutive addresses and no load waiting for an index.
 #include "state.h"
 
 namespace ipmk {
@@ -73,43 +74,20 @@ cudaError_t launch_mirror_df(const Dev& d, const Geo& g, cudaStream_t st) {
 // Double-float dot of one CSR row with a double-float vector by a group of G lanes (lane gl
 // takes entries gl, gl + G, ...; two in flight), summed over the group.
 template <int G>
-__device__ __forceinline__ double group_row_dot_df(const int64_t beg, const int64_t end, const int gl,
-                                                   const int32_t* __restrict__ idx, const float2* __restrict__ val,
-                                                   const float2* __restrict__ x) {
-  float h = 0.f, l = 0.f;
+__device__ __forceinline__ void group_row_mac_df(const int64_t beg, const int64_t end, const int gl,
+                                                 const int32_t* __restrict__ idx, const float2* __restrict__ val,
+                                                 const float2* __restrict__ x, float& h, float& l) {
   int64_t e = beg + gl;
-  for (; e + G < end; e += 2 * G) {
-    const float2 a0 = __ldg(val + e), a1 = __ldg(val + e + G);
-    const int i0 = __ldg(idx + e), i1 = __ldg(idx + e + G);
-    const float2 x0 = __ldg(x + i0), x1 = __ldg(x + i1);
+  for (; e + 3 * G < end; e += 4 * G) {
+    const float2 a0 = __ldg(val + e), a1 = __ldg(val + e + G), a2 = __ldg(val + e + 2 * G), a3 = __ldg(val + e + 3 * G);
+    const int i0 = __ldg(idx + e), i1 = __ldg(idx + e + G), i2 = __ldg(idx + e + 2 * G), i3 = __ldg(idx + e + 3 * G);
+    const float2 x0 = __ldg(x + i0), x1 = __ldg(x + i1), x2 = __ldg(x + i2), x3 = __ldg(x + i3);
     df_mac(a0, x0, h, l);
     df_mac(a1, x1, h, l);
+    df_mac(a2, x2, h, l);
+    df_mac(a3, x3, h, l);
   }
-  if (e < end) df_mac(__ldg(val + e), __ldg(x + __ldg(idx + e)), h, l);
-  return df_group_sum<G>(h, l);
-}
-
-// The same over the runs [k0, k1) of a row: entry e of run k sits in column
-// run_col[k] + (e - run_beg[k]), so the gathers of a group read consecutive addresses.
-template <int G>
-__device__ __forceinline__ double group_runs_dot_df(const int64_t k0, const int64_t k1, const int gl,
-                                                    const int32_t* __restrict__ run_col,
-                                                    const int64_t* __restrict__ run_beg,
-                                                    const float2* __restrict__ val, const float2* __restrict__ x) {
-  float h = 0.f, l = 0.f;
-  for (int64_t k = k0; k < k1; ++k) {
-    const int64_t b = __ldg(run_beg + k), en = __ldg(run_beg + k + 1);
-    const int64_t off = (int64_t)__ldg(run_col + k) - b;   // column of entry e = off + e
-    int64_t e = b + gl;
-    for (; e + G < en; e += 2 * G) {
-      const float2 a0 = __ldg(val + e), a1 = __ldg(val + e + G);
-      const float2 x0 = __ldg(x + (off + e)), x1 = __ldg(x + (off + e + G));
-      df_mac(a0, x0, h, l);
-      df_mac(a1, x1, h, l);
-    }
-    if (e < en) df_mac(__ldg(val + e), __ldg(x + (off + e)), h, l);
-  }
-  return df_group_sum<G>(h, l);
+  for (; e < end; e += G) df_mac(__ldg(val + e), __ldg(x + __ldg(idx + e)), h, l);
 }
 
 // ---------------------------------------------------------------- operator passes
@@ -122,25 +100,34 @@ __global__ void __launch_bounds__(256, 6) k_op_rows_df(Dev d) {
   const int gl = threadIdx.x & (G - 1);
   FOR_GROUP_ROWS_D(G, ri, ok, d.nR) {
     const int64_t r = (ok && d.rperm) ? (int64_t)d.rperm[ri] : ri;
-    double t;
+    float th = 0.f, tl = 0.f;
     if (RUNS) {
-      const int64_t k0 = ok ? d.run_ptr[r] : 0, k1 = ok ? d.run_ptr[r + 1] : 0;
-      t = group_runs_dot_df<G>(k0, k1, gl, d.run_col, d.run_beg, d.R_df, d.p_df);
+      for_row_pieces<G>(d, r, ok, gl, [&](int64_t e, int c) { df_mac(__ldg(d.R_df + e), __ldg(d.p_df + c), th, tl); });
     } else {
       const int64_t beg = ok ? d.R_ptr[r] : 0, end = ok ? d.R_ptr[r + 1] : 0;
-      t = group_row_dot_df<G>(beg, end, gl, d.R_idx, d.R_df, d.p_df);
+      group_row_mac_df<G>(beg, end, gl, d.R_idx, d.R_df, d.p_df, th, tl);
     }
+    df_group_pair<G>(th, tl);
     if (ok && gl == 0) {
-      double v = d.omega[r] * t;
       if (MODE == 0 && d.aug) {
+        const double t = df_value(th, tl);
+        double v = d.omega[r] * t;
         const int32_t k = d.rowk[r];
         if (k >= 0) {
           const double pb = d.p[d.n + k];
           v -= pb;
           d.q[d.n + k] = -t + pb * (d.s[k] / d.y[k]);
         }
+        d.v_df[r] = df_split(v);
+      } else {
+        // v = omega t as a double-float product (no float64 arithmetic per row)
+        const float2 w = df_split(d.omega[r]);
+        float vh = 0.f, vl = 0.f;
+        df_mac(w, make_float2(th, tl), vh, vl);
+        float s, e;
+        two_sum(vh, vl, s, e);
+        d.v_df[r] = make_float2(s, e);
       }
-      d.v_df[r] = df_split(v);
     }
   }
 }
@@ -155,7 +142,10 @@ __global__ void __launch_bounds__(256, 6) k_op_cols_df(Dev d) {
   double pq = 0.0;
   FOR_GROUP_ROWS_D(G, j, ok, d.n) {
     const int64_t beg = ok ? d.RT_ptr[j] : 0, end = ok ? d.RT_ptr[j + 1] : 0;
-    double acc = group_row_dot_df<G>(beg, end, gl, d.RT_idx, d.RT_df, d.v_df);
+    float ah = 0.f, al = 0.f;
+    group_row_mac_df<G>(beg, end, gl, d.RT_idx, d.RT_df, d.v_df, ah, al);
+    df_group_pair<G>(ah, al);
+    double acc = gl == 0 ? df_value(ah, al) : 0.0;   // float64 once per row (lane 0 keeps it)
     if (d.Hs_ptr) {
       const int64_t hb = ok ? d.Hs_ptr[j] : 0, he = ok ? d.Hs_ptr[j + 1] : 0;
       acc += group_row_dot<G, false>(hb, he, gl, d.Hs_idx, d.Hs_val, d.p);
@@ -212,54 +202,62 @@ cudaError_t launch_op_cols_df(const Dev& d, const Geo& g, int mode, cudaStream_t
 // ---------------------------------------------------------------- runs of R's rows
 
 // An entry starts a run if it is the first of its row or its column is not one more than the
-// previous entry's.  One warp per row; count[r] = runs of row r.
-__global__ void k_runs_count(Dev d, int32_t* __restrict__ count) {
+// previous entry's; a run of L entries is cut into ceil(L / kPiece) pieces.  One warp per row
+// walks the run starts found by a ballot over each 32-entry stretch (the same walk in every
+// lane).  EMIT 0: count runs and pieces per row; EMIT 1: write the piece descriptors.
+template <int EMIT>
+__global__ void k_runs_walk(Dev d, int32_t* __restrict__ nruns, int32_t* __restrict__ npieces) {
   const int lane = threadIdx.x & 31;
+  int32_t* pcol = const_cast<int32_t*>(d.pc_col);
+  uint32_t* pol = const_cast<uint32_t*>(d.pc_ol);
   for (int64_t r = gwarp_d(); r < d.nR; r += nwarps_d()) {
     const int64_t beg = d.R_ptr[r], end = d.R_ptr[r + 1];
-    int c = 0;
-    for (int64_t e = beg + lane; e < end; e += 32)
-      c += (e == beg || d.R_idx[e] != d.R_idx[e - 1] + 1) ? 1 : 0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if (lane == 0) count[r] = c;
-  }
-}
-
-// run_col, run_beg from run_ptr (the exclusive scan of the counts): the starts of a row are
-// written in entry order by a ballot over each 32-entry stretch.
-__global__ void k_runs_fill(Dev d) {
-  const int lane = threadIdx.x & 31;
-  int32_t* col = const_cast<int32_t*>(d.run_col);
-  int64_t* rb = const_cast<int64_t*>(d.run_beg);
-  for (int64_t r = gwarp_d(); r < d.nR; r += nwarps_d()) {
-    const int64_t beg = d.R_ptr[r], end = d.R_ptr[r + 1];
-    int64_t k = d.run_ptr[r];
+    int64_t cur = beg;                           // first entry of the open run
+    int64_t k = EMIT ? d.pc_ptr[r] : 0;          // next piece slot
+    int nr = 0, np = 0;
+    auto close = [&](int64_t stop) {             // the run [cur, stop) -> its pieces
+      const int32_t c0 = d.R_idx[cur];
+      for (int64_t s = cur; s < stop; s += kPiece) {
+        const int64_t len = stop - s < kPiece ? stop - s : kPiece;
+        if (EMIT && lane == 0) {
+          pcol[k] = c0 + (int32_t)(s - cur);
+          pol[k] = ((uint32_t)(s - beg) << 6) | (uint32_t)len;
+        }
+        ++k;
+        ++np;
+      }
+    };
     for (int64_t e0 = beg; e0 < end; e0 += 32) {
       const int64_t e = e0 + lane;
       const bool start = e < end && (e == beg || d.R_idx[e] != d.R_idx[e - 1] + 1);
-      const unsigned m = __ballot_sync(0xffffffffu, start);
-      if (start) {
-        const int64_t slot = k + __popc(m & ((1u << lane) - 1u));
-        col[slot] = d.R_idx[e];
-        rb[slot] = e;
+      unsigned m = __ballot_sync(0xffffffffu, start);
+      while (m) {
+        const int64_t pos = e0 + (__ffs(m) - 1);
+        m &= m - 1;
+        if (pos > beg) close(pos);
+        cur = pos;
+        ++nr;
       }
-      k += __popc(m);
+    }
+    if (end > beg) close(end);
+    if (!EMIT && lane == 0) {
+      nruns[r] = nr;
+      npieces[r] = np;
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) rb[d.nruns] = d.nnzR;
 }
 
-cudaError_t launch_runs_count(const Dev& d, int32_t* count, cudaStream_t st) {
+cudaError_t launch_runs_count(const Dev& d, int32_t* runs, int32_t* pieces, cudaStream_t st) {
   if (!d.nR) return cudaSuccess;
   const int gb = (int)std::min<int64_t>((d.nR + 7) / 8, 8 * (int64_t)(d.sm_count > 0 ? d.sm_count : 148));
-  k_runs_count<<<gb, 256, 0, st>>>(d, count);
+  k_runs_walk<0><<<gb, 256, 0, st>>>(d, runs, pieces);
   return cudaGetLastError();
 }
 
 cudaError_t launch_runs_fill(const Dev& d, cudaStream_t st) {
-  const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((d.nR + 7) / 8, 8 * (int64_t)(d.sm_count > 0 ? d.sm_count : 148)));
-  k_runs_fill<<<gb, 256, 0, st>>>(d);
+  if (!d.nR) return cudaSuccess;
+  const int gb = (int)std::min<int64_t>((d.nR + 7) / 8, 8 * (int64_t)(d.sm_count > 0 ? d.sm_count : 148));
+  k_runs_walk<1><<<gb, 256, 0, st>>>(d, nullptr, nullptr);
   return cudaGetLastError();
 }
 

@@ -1073,40 +1073,18 @@ __global__ void __launch_bounds__(256, 6) k_op_rows(Dev d) {
   }
 }
 
-// FP64 dot over the runs [k0, k1) of a row by a group of G lanes: entry e of run k sits in
-// column run_col[k] + (e - run_beg[k]), so no index is loaded and the gathers of a group read
-// consecutive addresses.
-template <int G>
-__device__ __forceinline__ double group_runs_dot(const int64_t k0, const int64_t k1, const int gl,
-                                                 const int32_t* __restrict__ run_col,
-                                                 const int64_t* __restrict__ run_beg,
-                                                 const double* __restrict__ val, const double* __restrict__ x) {
-  double a = 0.0;
-  for (int64_t k = k0; k < k1; ++k) {
-    const int64_t b = __ldg(run_beg + k), en = __ldg(run_beg + k + 1);
-    const int64_t off = (int64_t)__ldg(run_col + k) - b;
-    int64_t e = b + gl;
-    for (; e + G < en; e += 2 * G) {
-      const double v0 = __ldg(val + e), v1 = __ldg(val + e + G);
-      const double x0 = __ldg(x + (off + e)), x1 = __ldg(x + (off + e + G));
-      a = fma(v0, x0, a);
-      a = fma(v1, x1, a);
-    }
-    if (e < en) a = fma(__ldg(val + e), __ldg(x + (off + e)), a);
-  }
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-  return a;
-}
-
-// v = omega o (R p) over the runs of R's rows (FP64); otherwise as k_op_rows.
+// v = omega o (R p) over the pieces of R's rows (FP64; one descriptor per piece of a run
+// instead of one index per entry); otherwise as k_op_rows.
 template <int MODE, int G>
 __global__ void __launch_bounds__(256, 6) k_op_rows_runs(Dev d) {
   if (MODE == 0 && d.sc->cg_done) return;
   FOR_GROUP_ROWS(G, ri, ok, d.nR) {
     const int64_t r = (ok && d.rperm) ? (int64_t)d.rperm[ri] : ri;
-    const int64_t k0 = ok ? d.run_ptr[r] : 0, k1 = ok ? d.run_ptr[r + 1] : 0;
-    const double t = group_runs_dot<G>(k0, k1, glane<G>(), d.run_col, d.run_beg, d.R_val, d.p);
+    double a = 0.0;
+    for_row_pieces<G>(d, r, ok, glane<G>(), [&](int64_t e, int c) { a = fma(__ldg(d.R_val + e), __ldg(d.p + c), a); });
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    const double t = a;
     if (ok && glane<G>() == 0) {
       double v = d.omega[r] * t;
       if (MODE == 0 && d.aug) {

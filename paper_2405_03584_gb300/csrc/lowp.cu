@@ -273,39 +273,9 @@ __global__ void __launch_bounds__(256, 6) k_op_cols_lp(Dev d, int standalone) {
     default: { constexpr int G = 32; __VA_ARGS__; } break;    \
   }
 
-// FP32 dot over the runs [k0, k1) of a stored row by a group of G lanes: lane gl takes
-// entries gl, gl + G, ... of each run, so a group reads consecutive values and gathers the
-// FP32 vector at consecutive addresses; no index array is read.
-template <int S, int G>
-__device__ __forceinline__ float group_runs_dot_lp(const int64_t k0, const int64_t k1, const int gl,
-                                                   const int32_t* __restrict__ run_col,
-                                                   const int64_t* __restrict__ run_beg,
-                                                   const typename StorageT<S>::T* __restrict__ val,
-                                                   const float* __restrict__ x) {
-  float a = 0.f, b = 0.f;
-  for (int64_t k = k0; k < k1; ++k) {
-    const int64_t rb = __ldg(run_beg + k), en = __ldg(run_beg + k + 1);
-    const int64_t off = (int64_t)__ldg(run_col + k) - rb;
-    int64_t e = rb + gl;
-    for (; e + 3 * G < en; e += 4 * G) {
-      const float v0 = StorageT<S>::dec(val[e]), v1 = StorageT<S>::dec(val[e + G]);
-      const float v2 = StorageT<S>::dec(val[e + 2 * G]), v3 = StorageT<S>::dec(val[e + 3 * G]);
-      const float x0 = __ldg(x + (off + e)), x1 = __ldg(x + (off + e + G));
-      const float x2 = __ldg(x + (off + e + 2 * G)), x3 = __ldg(x + (off + e + 3 * G));
-      a = fmaf(v0, x0, a);
-      b = fmaf(v1, x1, b);
-      a = fmaf(v2, x2, a);
-      b = fmaf(v3, x3, b);
-    }
-    for (; e < en; e += G) a = fmaf(StorageT<S>::dec(val[e]), __ldg(x + (off + e)), a);
-  }
-  a += b;
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-  return a;
-}
-
-// The reduced-precision rows pass over the runs of R's rows (otherwise as k_op_rows_lp).
+// The reduced-precision rows pass over the pieces of R's rows: one descriptor per piece of a
+// run instead of one index per entry, the narrow values and the FP32 vector at consecutive
+// addresses (otherwise as k_op_rows_lp).
 template <int S, int G>
 __global__ void __launch_bounds__(256, 6) k_op_rows_lp_runs(Dev d, int standalone) {
   if (!standalone && d.sc->cg_done) return;
@@ -313,11 +283,13 @@ __global__ void __launch_bounds__(256, 6) k_op_rows_lp_runs(Dev d, int standalon
   const T* q = static_cast<const T*>(d.Rq);
   const int gl = threadIdx.x & (G - 1);
   FOR_GROUP_ROWS_L(G, r, ok, d.nR) {
-    const int64_t k0 = ok ? d.run_ptr[r] : 0, k1 = ok ? d.run_ptr[r + 1] : 0;
-    const float t = group_runs_dot_lp<S, G>(k0, k1, gl, d.run_col, d.run_beg, q, d.p32);
+    float a = 0.f;
+    for_row_pieces<G>(d, r, ok, gl, [&](int64_t e, int c) { a = fmaf(StorageT<S>::dec(q[e]), __ldg(d.p32 + c), a); });
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
     if (ok && gl == 0) {
       const double s = (double)d.scaleR[r];
-      d.w32[r] = (float)((d.wR[r] + d.thR[r]) * s * s * (double)t);
+      d.w32[r] = (float)((d.wR[r] + d.thR[r]) * s * s * (double)a);
     }
   }
 }

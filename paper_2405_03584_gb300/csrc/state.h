@@ -73,13 +73,14 @@ struct Dev {
   const float2 *R_df, *RT_df;  // nnzR each
   float2 *p_df, *v_df;         // n, nR
   // runs of R's rows: maximal stretches of consecutive entries whose columns increase by one
-  // (the contiguous spot bands of a dose row); the rows pass reads columns from them instead
-  // of the index array when `runs` is set
+  // (the contiguous spot bands of a dose row), cut into pieces of at most kPiece entries; the
+  // rows pass reads one descriptor per piece instead of one column index per entry when
+  // `runs` is set
   int runs;
-  int64_t nruns;
-  const int64_t* run_ptr;      // nR + 1: runs of row r are [run_ptr[r], run_ptr[r+1])
-  const int32_t* run_col;      // nruns: first column of each run
-  const int64_t* run_beg;      // nruns + 1: first entry of each run; run_beg[nruns] = nnzR
+  int64_t npieces;
+  const int64_t* pc_ptr;       // nR + 1: pieces of row r are [pc_ptr[r], pc_ptr[r+1])
+  const int32_t* pc_col;       // npieces: column of the piece's first entry
+  const uint32_t* pc_ol;       // npieces: (entry offset within the row) << 6 | length
   // reduced-precision copy of the matrix values (storage != ST_F64): R~_ij = scaleR_i * q_ij
   int storage;
   void *Rq, *RTq;              // nnzR values each (float / bf16 / fp8-e4m3), indices shared with R, R^T
@@ -112,6 +113,44 @@ __device__ __forceinline__ double lr_row(const Dev& d, const int64_t j, const bo
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
   return a;
+}
+
+constexpr int kPiece = 32;      // entries per piece of a run (at most)
+
+// Calls f(e, c) for every stored entry e of row r of R, with its column c, by a group of G
+// lanes, walking the row's pieces: the group loads G piece descriptors at a time (one per
+// lane) and takes the pieces one after another, broadcast by shuffles; lane gl handles the
+// piece's entries gl, gl + G, ... .  The trip counts are uniform over the warp (the most
+// pieces any of its groups has; a group past its own count sees empty pieces), so every
+// lane executes the same instruction stream and only masks differ.  Two pieces per trip keep
+// 2 * kPiece / G entries per lane in flight; no per-entry index is read.
+template <int G, typename F>
+__device__ __forceinline__ void for_row_pieces(const Dev& d, const int64_t r, const bool ok, const int gl, F f) {
+  const int64_t kb = ok ? d.pc_ptr[r] : 0, ke = ok ? d.pc_ptr[r + 1] : 0;
+  const int64_t rb = ok ? d.R_ptr[r] : 0;
+  const unsigned np = (unsigned)(ke - kb);
+  const unsigned npmax = __reduce_max_sync(0xffffffffu, np);
+  for (unsigned tb = 0; tb < npmax; tb += G) {
+    int col = 0;
+    unsigned ol = 0;
+    if (tb + gl < np) {
+      col = __ldg(d.pc_col + kb + tb + gl);
+      ol = __ldg(d.pc_ol + kb + tb + gl);
+    }
+    const unsigned tn = npmax - tb < (unsigned)G ? npmax - tb : (unsigned)G;
+    for (unsigned t = 0; t < tn; t += 2) {
+      const int c0 = __shfl_sync(0xffffffffu, col, t, G), c1 = __shfl_sync(0xffffffffu, col, t + 1, G);
+      const unsigned o0 = __shfl_sync(0xffffffffu, ol, t, G), o1 = __shfl_sync(0xffffffffu, ol, t + 1, G);
+      const int len0 = (int)(o0 & 63u), len1 = t + 1 < tn ? (int)(o1 & 63u) : 0;
+      const int64_t e0 = rb + (int64_t)(o0 >> 6), e1 = rb + (int64_t)(o1 >> 6);
+#pragma unroll
+      for (int u = 0; u < kPiece / G; ++u) {
+        const int j = gl + u * G;
+        if (j < len0) f(e0 + j, c0 + j);
+        if (j < len1) f(e1 + j, c1 + j);
+      }
+    }
+  }
 }
 
 // Launch geometry shared by the host code and the final reduction kernel.
@@ -162,9 +201,9 @@ cudaError_t launch_df_split(const Dev& d, int* out_of_range, cudaStream_t st);  
 cudaError_t launch_mirror_df(const Dev& d, const Geo& g, cudaStream_t st);        // p_df from p
 cudaError_t launch_op_rows_df(const Dev& d, const Geo& g, int mode, cudaStream_t st);
 cudaError_t launch_op_cols_df(const Dev& d, const Geo& g, int mode, cudaStream_t st);
-// ---- runs of R's rows (df.cu) ----
-cudaError_t launch_runs_count(const Dev& d, int32_t* count, cudaStream_t st);     // runs per row
-cudaError_t launch_runs_fill(const Dev& d, cudaStream_t st);                      // run_col, run_beg
+// ---- pieces of the runs of R's rows (df.cu) ----
+cudaError_t launch_runs_count(const Dev& d, int32_t* runs, int32_t* pieces, cudaStream_t st);  // per row
+cudaError_t launch_runs_fill(const Dev& d, cudaStream_t st);                      // pc_col, pc_ol
 cudaError_t launch_op_rows_runs(const Dev& d, const Geo& g, int mode, cudaStream_t st);   // FP64 (kernels.cu)
 cudaError_t launch_op_rows_lp_runs(const Dev& d, const Geo& g, int standalone, cudaStream_t st);  // lowp.cu
 cudaError_t launch_refine_start(const Dev& d, const Geo& g, cudaStream_t st);

@@ -117,12 +117,24 @@ def test_double_float_refused_out_of_range():
         assert s.get_config()["op_arith"] == ipm.ARITH["df32"]
 
 
-def test_runs_auto_detection():
-    """AUTO takes runs for banded dose rows and keeps CSR for rows of scattered columns."""
-    p = W.rt_qp(n=700, seed=16)
+def _mean_run(ip, ix):
+    """Entries per run: a run starts at the first entry of a row or where the column is not one
+    more than the previous entry's."""
+    first = np.zeros(ix.size, bool)
+    first[ip[:-1][np.diff(ip) > 0]] = True
+    first[1:] |= ix[1:] != ix[:-1] + 1
+    return ix.size / max(first.sum(), 1)
+
+
+@pytest.mark.parametrize("n,density", [(2000, 0.02), (700, 0.005)])
+def test_runs_auto_detection(n, density):
+    """AUTO takes runs when they average at least 8 entries (banded dose rows at the RT
+    density) and keeps CSR otherwise (short rows, scattered columns)."""
+    p = W.rt_qp(n=n, seed=16, density=density)
+    want = int(_mean_run(p["D_indptr"], p["D_indices"]) >= 8.0)
     with ipm.Solver() as s:
         s.set_qp_rt(p)
-        assert s.get_config()["rows_runs"] == 1
+        assert s.get_config()["rows_runs"] == want
     rng = np.random.default_rng(3)
     n, m = 400, 300
     A = np.where(rng.random((m, n)) < 0.05, rng.normal(size=(m, n)), 0.0)
