@@ -237,6 +237,8 @@ def _operator_opts(args):
         o["op_arith"] = args.op_arith
     if args.rows_format:
         o["rows_format"] = args.rows_format
+    if args.rows_stage is not None:
+        o["rows_stage"] = args.rows_stage
     return o
 
 
@@ -791,6 +793,8 @@ def main():
                     help="PCG operator arithmetic with f64 storage (default: the preset's)")
     ap.add_argument("--rows-format", choices=["auto", "csr", "runs"], default=None,
                     help="format of the PCG rows pass (default: the preset's)")
+    ap.add_argument("--rows-stage", type=int, choices=[0, 1], default=None,
+                    help="0: rows pass staged through shared memory by bulk copies where available; 1: not")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every kernel directly (for per-kernel profilers; same kernels, slower)")
     args = ap.parse_args()

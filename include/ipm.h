@@ -146,6 +146,13 @@ typedef struct ipm_options {
                          /* from its average row length                                        */
   int op_arith;          /* enum ipm_arith: PCG operator arithmetic with F64 storage (F64)      */
   int rows_format;       /* enum ipm_rows_format of the PCG rows pass (AUTO)                    */
+  int rows_stage;        /* 0 (default): with RUNS, double-float or reduced storage, the rows   */
+                         /* pass streams R's values into shared memory by bulk copies (TMA),    */
+                         /* one three-stage pipeline per SM; 1: it reads global memory          */
+  double wait_limit_ms;  /* limit of every device-side wait (1000): when one runs out the solve */
+                         /* stops with IPM_ERR_TIMEOUT (the iterate is then not meaningful)     */
+  int wait_test;         /* test of the device watchdog (0): 1 arms the first staged tile's     */
+                         /* barrier for 16 bytes more than is copied, so its wait runs out      */
 } ipm_options;
 
 /* Fills *opt with the defaults listed above. */

@@ -344,6 +344,8 @@ int validate_options(const ipm_options& o) {
   if (o.system != IPM_SYSTEM_CONDENSED && o.system != IPM_SYSTEM_AUGMENTED) return IPM_ERR_ARG;
   if (o.op_arith != IPM_ARITH_F64 && o.op_arith != IPM_ARITH_DF32) return IPM_ERR_ARG;
   if (o.rows_format < IPM_ROWS_AUTO || o.rows_format > IPM_ROWS_RUNS) return IPM_ERR_ARG;
+  if (o.rows_stage < 0 || o.rows_stage > 1 || !(o.wait_limit_ms > 0 && o.wait_limit_ms <= 6e4)) return IPM_ERR_ARG;
+  if (o.wait_test < 0 || o.wait_test > 1) return IPM_ERR_ARG;
   if (o.system == IPM_SYSTEM_AUGMENTED &&
       (o.storage != IPM_STORAGE_F64 || (o.precond != IPM_PRECOND_JACOBI && o.precond != IPM_PRECOND_AUTO)))
     return IPM_ERR_ARG;   // the doubly augmented system runs FP64 with the Jacobi preconditioner
@@ -407,6 +409,10 @@ int prepare_operator_formats(ipm_handle* h) {
     d.df = bad ? 0 : 1;
   }
   d.runs = 0;
+  d.ntiles = 0;
+  d.tile_row = nullptr;
+  d.wait_ns = (uint64_t)(h->opt.wait_limit_ms * 1e6);
+  d.wait_test = h->opt.wait_test;
   d.npieces = 0;
   d.pc_ptr = nullptr;
   d.pc_col = nullptr;
@@ -432,10 +438,28 @@ int prepare_operator_formats(ipm_handle* h) {
   if (nruns == 0 || longest >= ((int64_t)1 << 26)) return IPM_OK;
   const bool use = h->opt.rows_format == IPM_ROWS_RUNS || (double)d.nnzR >= 8.0 * (double)nruns;
   if (!use) return IPM_OK;
+  // tiles of the staged rows pass (double-float or reduced storage): consecutive rows whose
+  // values take at most kStageBytes - 16 bytes (so their 16-byte-aligned span fits a stage);
+  // a longer row is a tile of its own, read from global memory
+  std::vector<int32_t> tiles;
+  const int vbytes = d.df ? 8 : (d.storage == ST_F32 ? 4 : d.storage == ST_BF16 ? 2 : d.storage == ST_FP8 ? 1 : 0);
+  if (vbytes && h->opt.rows_stage == 0) {
+    const int64_t cap = (kStageBytes - 16) / vbytes;
+    tiles.push_back(0);
+    int64_t r = 0;
+    while (r < d.nR) {
+      int64_t r1 = r + 1;
+      while (r1 < d.nR && rows[r1 + 1] - rows[r] <= cap) ++r1;
+      tiles.push_back((int32_t)r1);
+      r = r1;
+    }
+  }
+  const int64_t ntiles = tiles.empty() ? 0 : (int64_t)tiles.size() - 1;
   Carver cc(nullptr);
   cc.take<int64_t>(d.nR + 1);
   cc.take<int32_t>(npieces);
   cc.take<uint32_t>(npieces);
+  cc.take<int32_t>(ntiles + 1);
   const size_t bytes = cc.off + 256;
   if (h->opt.mem_budget > 0 && (double)(h->mat->bytes + h->arena_bytes + bytes) > h->opt.mem_budget)
     return IPM_OK;                                     // within the budget the rows pass stays CSR
@@ -446,10 +470,16 @@ int prepare_operator_formats(ipm_handle* h) {
   d.pc_ptr = cv.take<int64_t>(d.nR + 1);
   d.pc_col = cv.take<int32_t>(npieces);
   d.pc_ol = cv.take<uint32_t>(npieces);
+  d.tile_row = cv.take<int32_t>(ntiles + 1);
   d.npieces = npieces;
+  if (ntiles) {
+    CUDA_TRY(h, prepare_staged());
+    CUDA_TRY(h, cudaMemcpyAsync((void*)d.tile_row, tiles.data(), sizeof(int32_t) * tiles.size(), cudaMemcpyHostToDevice, h->st));
+  }
   CUDA_TRY(h, cudaMemcpyAsync((void*)d.pc_ptr, pp.data(), sizeof(int64_t) * pp.size(), cudaMemcpyHostToDevice, h->st));
   CUDA_TRY(h, launch_runs_fill(d, h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  d.ntiles = ntiles;
   d.runs = 1;
   return IPM_OK;
 }
@@ -818,6 +848,9 @@ void ipm_default_options(ipm_options* o) {
   o->lanes_at = 0;
   o->op_arith = IPM_ARITH_F64;
   o->rows_format = IPM_ROWS_AUTO;
+  o->rows_stage = 0;
+  o->wait_limit_ms = 1000.0;
+  o->wait_test = 0;
   o->warm_rho = 1e-5;
   o->u_cap = 0;
   o->ingest_host = 0;

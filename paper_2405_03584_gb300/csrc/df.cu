@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(256, 6) k_op_cols_df(Dev d) {
 
 cudaError_t launch_op_rows_df(const Dev& d, const Geo& g, int mode, cudaStream_t st) {
   if (!d.nR) return cudaSuccess;
+  if (d.ntiles) return launch_op_rows_staged(d, mode, st);
   if (d.runs) {
     if (mode == 0) { DISPATCH_GD(d.g_rows, k_op_rows_df<0, G, true><<<g.gRc, kBlock, 0, st>>>(d)); }
     else { DISPATCH_GD(d.g_rows, k_op_rows_df<1, G, true><<<g.gRc, kBlock, 0, st>>>(d)); }

@@ -296,6 +296,10 @@ __global__ void __launch_bounds__(256, 6) k_op_rows_lp_runs(Dev d, int standalon
 
 static void launch_rows_lp(const Dev& d, const Geo& g, int standalone, cudaStream_t st) {
   if (!d.nR) return;
+  if (d.ntiles) {
+    launch_op_rows_staged(d, standalone ? 1 : 0, st);
+    return;
+  }
   if (d.runs) DISPATCH_SG(d.storage, d.g_rows, k_op_rows_lp_runs<S, G><<<g.gRc, kBlock, 0, st>>>(d, standalone));
   else DISPATCH_SG(d.storage, d.g_rows, k_op_rows_lp<S, G><<<g.gR, kBlock, 0, st>>>(d, standalone));
 }

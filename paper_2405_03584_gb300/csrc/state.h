@@ -81,6 +81,12 @@ struct Dev {
   const int64_t* pc_ptr;       // nR + 1: pieces of row r are [pc_ptr[r], pc_ptr[r+1])
   const int32_t* pc_col;       // npieces: column of the piece's first entry
   const uint32_t* pc_ol;       // npieces: (entry offset within the row) << 6 | length
+  // tiles of the staged rows pass (staged.cu): consecutive rows [tile_row[t], tile_row[t+1])
+  // whose values fit one shared-memory stage; 0 tiles = the rows pass reads global memory
+  int64_t ntiles;
+  const int32_t* tile_row;     // ntiles + 1
+  uint64_t wait_ns;            // limit of every device-side wait (options.wait_limit_ms)
+  int wait_test;               // options.wait_test: the first staged tile's wait runs out
   // reduced-precision copy of the matrix values (storage != ST_F64): R~_ij = scaleR_i * q_ij
   int storage;
   void *Rq, *RTq;              // nnzR values each (float / bf16 / fp8-e4m3), indices shared with R, R^T
@@ -116,6 +122,12 @@ __device__ __forceinline__ double lr_row(const Dev& d, const int64_t j, const bo
 }
 
 constexpr int kPiece = 32;      // entries per piece of a run (at most)
+
+// Staged rows pass (staged.cu): stages of the copy pipeline and bytes of one tile's values.
+constexpr int kStages = 3;
+constexpr int kStageBytes = 64 * 1024;
+constexpr int kStageAlloc = kStageBytes + 32;   // a tile's values rounded out to 16-byte units
+constexpr int kStagedThreads = 512;
 
 // Calls f(e, c) for every stored entry e of row r of R, with its column c, by a group of G
 // lanes, walking the row's pieces: the group loads G piece descriptors at a time (one per
@@ -206,6 +218,9 @@ cudaError_t launch_runs_count(const Dev& d, int32_t* runs, int32_t* pieces, cuda
 cudaError_t launch_runs_fill(const Dev& d, cudaStream_t st);                      // pc_col, pc_ol
 cudaError_t launch_op_rows_runs(const Dev& d, const Geo& g, int mode, cudaStream_t st);   // FP64 (kernels.cu)
 cudaError_t launch_op_rows_lp_runs(const Dev& d, const Geo& g, int standalone, cudaStream_t st);  // lowp.cu
+// ---- staged rows pass (staged.cu): double-float or reduced storage, over pieces ----
+cudaError_t launch_op_rows_staged(const Dev& d, int mode, cudaStream_t st);
+cudaError_t prepare_staged();   // once per process: shared-memory limit of the staged kernels
 cudaError_t launch_refine_start(const Dev& d, const Geo& g, cudaStream_t st);
 cudaError_t launch_refine_inner(const Dev& d, const Geo& g, cudaGraphConditionalHandle hi, cudaStream_t st);
 cudaError_t launch_refine_tail(const Dev& d, const Geo& g, cudaGraphConditionalHandle h, cudaStream_t st);

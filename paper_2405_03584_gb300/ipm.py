@@ -48,7 +48,8 @@ class Options(C.Structure):
                 ("storage", C.c_int), ("refine_max", C.c_int), ("refine_eta", C.c_double),
                 ("lanes_rows", C.c_int), ("lanes_cols", C.c_int), ("warm_rho", C.c_double),
                 ("u_cap", C.c_int), ("ingest_host", C.c_int), ("system", C.c_int),
-                ("lanes_at", C.c_int), ("op_arith", C.c_int), ("rows_format", C.c_int)]
+                ("lanes_at", C.c_int), ("op_arith", C.c_int), ("rows_format", C.c_int),
+                ("rows_stage", C.c_int), ("wait_limit_ms", C.c_double), ("wait_test", C.c_int)]
 
 
 class QP(C.Structure):

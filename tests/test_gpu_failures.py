@@ -103,6 +103,28 @@ def test_host_timeout_then_collect():
         assert s.wait() == ipm.IPM_OK
 
 
+@pytest.mark.parametrize("storage,arith", [("f64", "df32"), ("bf16", "f64")])
+def test_device_wait_limit(storage, arith):
+    """The staged rows pass waits on mbarriers for its bulk copies; every wait is bounded.
+    wait_test arms the first tile's barrier for 16 bytes more than is copied, so that wait
+    runs out (after wait_limit_ms) with every copy landed: the block records the timeout and
+    stops the PCG loop, the solve ends with IPM_ERR_TIMEOUT after its first IPM iteration, and
+    the GPU context stays usable for the next solve."""
+    p = W.rt_qp(n=4000, seed=85)
+    opts = dict(tol_kkt=1e-7, storage=storage, op_arith=arith, rows_format="runs")
+    with ipm.Solver(wait_test=1, wait_limit_ms=5.0, **opts) as s:
+        s.set_qp_rt(p)
+        with pytest.raises(ipm.IpmError) as e:
+            s.solve()
+        assert e.value.status == ipm.IPM_ERR_TIMEOUT
+        assert s.info()["ipm_iters"] == 1
+    with ipm.Solver(**opts) as s:
+        s.set_qp_rt(p)
+        assert s.solve() == ipm.IPM_OK
+        out = s.get()
+        assert kkt_check.rel_kkt(kkt_check.rt_ops(p), out["x"], out["y"], out["zl"], out["zu"]) <= 1e-7
+
+
 def test_batch_refuses_changed_member():
     """A batch captures each member's buffers; after ipm_set_qp, ipm_share_qp or
     ipm_set_lowrank on a member, ipm_batch_solve refuses to launch (IPM_ERR_STATE)."""

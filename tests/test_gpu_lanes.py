@@ -14,7 +14,8 @@ width) and compared element by element with the oracle at the same iterate:
   at eta = 1e-10 against the oracle's exact direction (1e-6 relative).
 
 Each FP64-storage check runs for both operator arithmetics (float64, double-float) and both
-formats of the rows pass (CSR, runs); the reduced storages for both formats.
+formats of the rows pass (CSR, runs; double-float runs staged through shared memory and read
+from global memory); the reduced storages for every format.
 """
 import itertools
 
@@ -52,7 +53,13 @@ def _err(a, b):
     return np.abs(a - b).max() / (np.abs(b).max() + 1e-300)
 
 
-VARIANTS = [("f64", "csr"), ("f64", "runs"), ("df32", "csr"), ("df32", "runs")]
+VARIANTS = [("f64", "csr"), ("f64", "runs"), ("df32", "csr"), ("df32", "runs"), ("df32", "runs-unstaged")]
+
+
+def _fmt(fmt):
+    """rows_format and rows_stage of a variant name ("runs-unstaged": the pieces read from
+    global memory instead of the staged copy pipeline)."""
+    return dict(rows_format=fmt.split("-")[0], rows_stage=1 if fmt.endswith("unstaged") else 0)
 
 
 @pytest.mark.parametrize("arith,fmt", VARIANTS, ids=["%s-%s" % v for v in VARIANTS])
@@ -61,7 +68,7 @@ def test_fp64_kernels_every_width(case, lr, lc, arith, fmt):
     p, qp, it, (rd, rp, rs, rl, ru), K, ref_dir = case
     la = lr   # the A^T kernels take every width across the sweep as well
     with ipm.Solver(precond="jacobi_lr", lanes_rows=lr, lanes_cols=lc, lanes_at=la, max_cg=20000,
-                    op_arith=arith, rows_format=fmt) as s:
+                    op_arith=arith, **_fmt(fmt)) as s:
         s.set_qp_rt(p)
         s.set_iterate(it.x, it.s, it.y, it.zl, it.zu, MU)
         r = s.residuals()
@@ -75,19 +82,19 @@ def test_fp64_kernels_every_width(case, lr, lc, arith, fmt):
         d = s.newton_direction(eta=1e-12)
         assert d["report"]["converged"] == 1, d["report"]
         info = s.get()["info"]
-        assert info["op_arith"] == ipm.ARITH[arith] and info["rows_runs"] == (fmt == "runs")
+        assert info["op_arith"] == ipm.ARITH[arith] and info["rows_runs"] == fmt.startswith("runs")
         assert _err(d["dx"], ref_dir.x) <= 1e-7
         assert _err(d["dy"], ref_dir.y) <= 1e-7 and _err(d["ds"], ref_dir.s) <= 1e-7
         assert _err(d["dzl"], ref_dir.zl) <= 1e-7 and _err(d["dzu"], ref_dir.zu) <= 1e-7
 
 
-@pytest.mark.parametrize("fmt", ["csr", "runs"])
+@pytest.mark.parametrize("fmt", ["csr", "runs", "runs-unstaged"])
 @pytest.mark.parametrize("storage", ["f32", "bf16", "fp8"])
 @pytest.mark.parametrize("lr,lc", PAIRS, ids=["rows%d-cols%d" % pc for pc in PAIRS])
 def test_reduced_precision_kernels_every_width(case, storage, lr, lc, fmt):
     p, qp, it, _, _, ref_dir = case
     with ipm.Solver(precond="jacobi_lr", storage=storage, lanes_rows=lr, lanes_cols=lc, lanes_at=lc,
-                    max_cg=5000, refine_max=30, rows_format=fmt) as s:
+                    max_cg=5000, refine_max=30, **_fmt(fmt)) as s:
         s.set_qp_rt(p)
         s.set_iterate(it.x, it.s, it.y, it.zl, it.zu, MU)
         d = s.newton_direction(eta=1e-10)

@@ -13,7 +13,13 @@ from paper_2405_03584_gb300 import ipm, workloads as W
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = [("f64", "runs"), ("df32", "csr"), ("df32", "runs")]
+VARIANTS = [("f64", "runs"), ("df32", "csr"), ("df32", "runs"), ("df32", "runs-unstaged")]
+
+
+def _fmt(fmt):
+    """rows_format and rows_stage options of a variant name ("runs-unstaged": pieces read from
+    global memory instead of the staged copy pipeline)."""
+    return dict(rows_format=fmt.split("-")[0], rows_stage=1 if fmt.endswith("unstaged") else 0)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -37,11 +43,11 @@ def _check(p, qp, st, out, tol, ops):
 @pytest.mark.parametrize("precond", ["jacobi_lr", "jacobi"])
 def test_rt_solves(arith, fmt, precond):
     p = W.rt_qp(n=1500, seed=9)
-    with ipm.Solver(tol_kkt=1e-7, precond=precond, op_arith=arith, rows_format=fmt, max_cg=20000) as s:
+    with ipm.Solver(tol_kkt=1e-7, precond=precond, op_arith=arith, **_fmt(fmt), max_cg=20000) as s:
         s.set_qp_rt(p)
         st = s.solve()
         out = s.get()
-    assert out["info"]["op_arith"] == ipm.ARITH[arith] and out["info"]["rows_runs"] == (fmt == "runs")
+    assert out["info"]["op_arith"] == ipm.ARITH[arith] and out["info"]["rows_runs"] == fmt.startswith("runs")
     _check(p, O.from_rt(p), st, out, 1e-7, kkt_check.rt_ops(p))
 
 
@@ -49,7 +55,7 @@ def test_rt_solves(arith, fmt, precond):
 def test_dense_h_block_solves(arith, fmt):
     """A dense H block (its FP64 part of the column pass) and dense rows of A (one run each)."""
     p = W.dense_qp(n=300, m=700, seed=2)
-    with ipm.Solver(tol_kkt=1e-8, precond="jacobi_lr", op_arith=arith, rows_format=fmt, max_cg=20000) as s:
+    with ipm.Solver(tol_kkt=1e-8, precond="jacobi_lr", op_arith=arith, **_fmt(fmt), max_cg=20000) as s:
         s.set_qp_dense(p["H"], p["c"], p["A"], p["b"], p["l"], p["u"])
         st = s.solve()
         out = s.get()
@@ -60,7 +66,7 @@ def test_dense_h_block_solves(arith, fmt):
 def test_lowrank_hessian_solves(arith, fmt):
     """The quasi-Newton term U W U^T (FP64 inside the double-float column pass) with CSR rows."""
     q = W.bfgs_qp(n=3000, k=20, m_ub=900, m_lb=300, density=0.01, seed=6, c_mode="target", ub_fac=1.1, lb_fac=0.9)
-    with ipm.Solver(tol_kkt=1e-7, precond="jacobi_lr", op_arith=arith, rows_format=fmt, stiff_max=1024) as s:
+    with ipm.Solver(tol_kkt=1e-7, precond="jacobi_lr", op_arith=arith, **_fmt(fmt), stiff_max=1024) as s:
         s.set_qp_bfgs(q)
         st = s.solve()
         out = s.get()
@@ -73,13 +79,13 @@ def test_augmented_and_two_sided_solves(arith, fmt):
     """The paper's doubly augmented system (the rows pass also forms its bottom block) and
     two-sided rows (negated copies of rows appended to R)."""
     p = W.rt_qp(n=900, seed=13)
-    with ipm.Solver(tol_kkt=1e-8, system="augmented", op_arith=arith, rows_format=fmt, max_cg=50000) as s:
+    with ipm.Solver(tol_kkt=1e-8, system="augmented", op_arith=arith, **_fmt(fmt), max_cg=50000) as s:
         s.set_qp_rt(p)
         st = s.solve()
         out = s.get()
     _check(p, O.from_rt(p), st, out, 1e-8, kkt_check.rt_ops(p))
     t = W.rt_two_sided(W.rt_qp(n=1100, seed=5), n_window=40)
-    with ipm.Solver(tol_kkt=1e-8, precond="jacobi_lr", op_arith=arith, rows_format=fmt, stiff_max=1024) as s:
+    with ipm.Solver(tol_kkt=1e-8, precond="jacobi_lr", op_arith=arith, **_fmt(fmt), stiff_max=1024) as s:
         s.set_qp_rt(t)
         st = s.solve()
         out = s.get()
@@ -96,11 +102,52 @@ def test_bitwise_reproducible_and_direct_launches(arith, fmt):
     p = W.rt_qp(n=900, seed=14)
     xs = []
     for ug in (1, 1, 0):
-        with ipm.Solver(tol_kkt=1e-8, precond="jacobi_lr", op_arith=arith, rows_format=fmt, use_graphs=ug) as s:
+        with ipm.Solver(tol_kkt=1e-8, precond="jacobi_lr", op_arith=arith, **_fmt(fmt), use_graphs=ug) as s:
             s.set_qp_rt(p)
             assert s.solve() == ipm.IPM_OK
             xs.append(s.get()["x"])
     assert np.array_equal(xs[0], xs[1]) and np.array_equal(xs[0], xs[2])
+
+
+@pytest.mark.parametrize("arith,storage", [("df32", "f64"), ("f64", "bf16"), ("f64", "fp8")])
+def test_rows_longer_than_a_stage(arith, storage):
+    """Rows whose values do not fit one shared-memory stage of the staged rows pass (64 KB:
+    more than 8190 double-float or 32760 BF16 entries) are tiles of their own, read from
+    global memory, between ordinary staged tiles.  Against the definition: sampled entries of
+    one operator apply (double-float) and a solve certified by the checker (every storage)."""
+    p = W.rt_qp(n=40000, V=3000, seed=17, n_organ=300)
+    ip, ix, dv = p["D_indptr"], p["D_indices"], p["D_data"]
+    rng = np.random.default_rng(2)
+    long_rows = {5: (100, 36000), 1700: (2000, 35000), 2999: (0, 40000)}   # row: (first column, length)
+    rows_i, rows_d = [], []
+    for r in range(p["V"]):
+        if r in long_rows:
+            c0, ln = long_rows[r]
+            rows_i.append(np.arange(c0, c0 + ln, dtype=np.int32))
+            rows_d.append(rng.lognormal(0.0, 1.0, ln) * 0.01)
+        else:
+            rows_i.append(ix[ip[r]:ip[r + 1]])
+            rows_d.append(dv[ip[r]:ip[r + 1]])
+    q = dict(p)
+    q["D_indptr"] = np.concatenate([[0], np.cumsum([len(a) for a in rows_i])]).astype(np.int64)
+    q["D_indices"] = np.concatenate(rows_i).astype(np.int32)
+    q["D_data"] = np.concatenate(rows_d)
+    # the cost keeps its definition c = -D^T W d with the new rows
+    rowid = np.repeat(np.arange(q["V"]), np.diff(q["D_indptr"]))
+    q["c"] = -np.bincount(q["D_indices"], weights=q["D_data"] * (q["w"] * q["d"])[rowid], minlength=q["n"])
+    with ipm.Solver(tol_kkt=1e-6, op_arith=arith, storage=storage, rows_format="runs", max_cg=5000) as s:
+        s.set_qp_rt(q)
+        if storage == "f64":
+            x, sl, y, zl, zu = W.random_iterate(q["n"], q["m"], q["l"], q["u"], 3, 1.0)
+            s.set_iterate(x, sl, y, zl, zu, 0.1)
+            pv = rng.normal(size=q["n"])
+            qv = s.apply_kkt(pv)
+            cols = np.concatenate([[0, 100, 2000, 39999], rng.choice(q["n"], 60, replace=False)])
+            ref = kkt_check.rt_condensed_entries(q, x, sl, y, zl, zu, pv, cols)
+            np.testing.assert_allclose(qv[cols], ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+        assert s.solve() == ipm.IPM_OK
+        out = s.get()
+    assert kkt_check.rel_kkt(kkt_check.rt_ops(q), out["x"], out["y"], out["zl"], out["zu"]) <= 1e-6
 
 
 def test_double_float_refused_out_of_range():
