@@ -438,18 +438,21 @@ int prepare_operator_formats(ipm_handle* h) {
   if (nruns == 0 || longest >= ((int64_t)1 << 26)) return IPM_OK;
   const bool use = h->opt.rows_format == IPM_ROWS_RUNS || (double)d.nnzR >= 8.0 * (double)nruns;
   if (!use) return IPM_OK;
-  // tiles of the staged rows pass (double-float or reduced storage): consecutive rows whose
-  // values take at most kStageBytes - 16 bytes (so their 16-byte-aligned span fits a stage);
-  // a longer row is a tile of its own, read from global memory
+  // tiles of the staged rows pass (double-float or reduced storage): consecutive rows, at most
+  // one per lane group (32 rows for double-float, 64 otherwise), whose values take at most
+  // kStageValBytes - 16 bytes and whose pieces number at most kStagePieces (so the
+  // 16-byte-aligned spans fit a stage); a row beyond that is a tile of its own, read from
+  // global memory
   std::vector<int32_t> tiles;
   const int vbytes = d.df ? 8 : (d.storage == ST_F32 ? 4 : d.storage == ST_BF16 ? 2 : d.storage == ST_FP8 ? 1 : 0);
   if (vbytes && h->opt.rows_stage == 0) {
-    const int64_t cap = (kStageBytes - 16) / vbytes;
+    const int64_t cap = (kStageValBytes - 16) / vbytes;
+    const int64_t max_rows = d.df ? kStagedThreads / 16 : kStagedThreads / 8;
     tiles.push_back(0);
     int64_t r = 0;
     while (r < d.nR) {
       int64_t r1 = r + 1;
-      while (r1 < d.nR && rows[r1 + 1] - rows[r] <= cap) ++r1;
+      while (r1 < d.nR && r1 - r < max_rows && rows[r1 + 1] - rows[r] <= cap && pp[r1 + 1] - pp[r] <= kStagePieces) ++r1;
       tiles.push_back((int32_t)r1);
       r = r1;
     }

@@ -100,16 +100,53 @@ template <> struct Val<ST_FP8> {
   }
 };
 
-// Bytes [lo, hi) of the tile's values: whole 16-byte units around its entries.
-template <int K>
-__device__ __forceinline__ void tile_span(const Dev& d, int64_t t, int64_t& r0, int64_t& r1, uint64_t& lo,
-                                          uint64_t& hi) {
-  r0 = d.tile_row[t];
-  r1 = d.tile_row[t + 1];
-  const uint64_t e0 = (uint64_t)d.R_ptr[r0], e1 = (uint64_t)d.R_ptr[r1];
-  lo = (e0 * Val<K>::B) & ~(uint64_t)15;
-  hi = (e1 * Val<K>::B + 15) & ~(uint64_t)15;
+// Layout of one stage: the tile's values, its pieces' descriptors (columns, offset/length
+// words) and the row and piece pointers of its rows, each copied as whole 16-byte units.
+constexpr int al16(int x) { return (x + 15) & ~15; }
+struct StageLayout {
+  static constexpr int kVal = 0;
+  static constexpr int kCol = kVal + al16(kStageValBytes + 16);
+  static constexpr int kOl = kCol + al16(4 * kStagePieces + 16);
+  static constexpr int kRp = kOl + al16(4 * kStagePieces + 16);
+  static constexpr int kPp = kRp + al16(8 * (kStageRows + 1) + 16);
+  static constexpr int kEnd = kPp + al16(8 * (kStageRows + 1) + 16);
+};
+static_assert(StageLayout::kEnd <= kStageAlloc, "stage layout exceeds the stage");
+static_assert(StageLayout::kCol % 16 == 0 && StageLayout::kOl % 16 == 0 && StageLayout::kRp % 16 == 0 &&
+              StageLayout::kPp % 16 == 0, "stage sections must start on 16-byte boundaries");
+
+// One staged array section: bytes [lo, hi) of the global array, rounded out to 16 bytes.
+struct Span {
+  uint64_t lo, hi;
+};
+__device__ __forceinline__ Span span_of(uint64_t first, uint64_t end, uint64_t elem) {
+  return Span{(first * elem) & ~(uint64_t)15, (end * elem + 15) & ~(uint64_t)15};
 }
+
+// The spans of tile t: values of its entries, descriptors of its pieces, pointers of its rows.
+template <int K>
+struct TileSpans {
+  int64_t r0, r1, k0, k1, e0, e1;
+  Span v, c, o, rp, pp;
+  bool direct;   // too large for a stage: read from global memory
+  __device__ __forceinline__ TileSpans(const Dev& d, int64_t t) {
+    r0 = d.tile_row[t];
+    r1 = d.tile_row[t + 1];
+    e0 = d.R_ptr[r0];
+    e1 = d.R_ptr[r1];
+    k0 = d.pc_ptr[r0];
+    k1 = d.pc_ptr[r1];
+    v = span_of(e0, e1, Val<K>::B);
+    c = span_of(k0, k1, 4);
+    o = span_of(k0, k1, 4);
+    rp = span_of(r0, r1 + 1, 8);
+    pp = span_of(r0, r1 + 1, 8);
+    direct = v.hi - v.lo > (uint64_t)kStageValBytes + 16 || (k1 - k0) > kStagePieces || (r1 - r0) > kStageRows;
+  }
+  __device__ __forceinline__ uint32_t bytes() const {
+    return (uint32_t)((v.hi - v.lo) + (c.hi - c.lo) + (o.hi - o.lo) + (rp.hi - rp.lo) + (pp.hi - pp.lo));
+  }
+};
 
 template <int K>
 __device__ __forceinline__ const char* values_of(const Dev& d) {
@@ -117,28 +154,41 @@ __device__ __forceinline__ const char* values_of(const Dev& d) {
 }
 
 // Thread 0: arms stage s for tile t and issues its copies (none for a tile read from global
-// memory, whose phase completes at the arrival).  Returns the bytes it asked for.
+// memory, whose phase completes at the arrival).  plant: 16 bytes more are expected than copied.
 template <int K>
 __device__ __forceinline__ void issue_tile(const Dev& d, int64_t t, char* stage, uint32_t bar, bool plant) {
-  int64_t r0, r1;
-  uint64_t lo, hi;
-  tile_span<K>(d, t, r0, r1, lo, hi);
-  const uint64_t nb = hi - lo;
-  if (nb > (uint64_t)kStageBytes + 16) {
+  const TileSpans<K> ts(d, t);
+  if (ts.direct) {
     mbar_expect(bar, 0);
     return;
   }
-  mbar_expect(bar, (uint32_t)nb + (plant ? 16u : 0u));
-  bulk_copy(smem_u32(stage), values_of<K>(d) + lo, (uint32_t)nb, bar);
+  mbar_expect(bar, ts.bytes() + (plant ? 16u : 0u));
+  const uint32_t st = smem_u32(stage);
+  bulk_copy(st + StageLayout::kVal, values_of<K>(d) + ts.v.lo, (uint32_t)(ts.v.hi - ts.v.lo), bar);
+  bulk_copy(st + StageLayout::kCol, reinterpret_cast<const char*>(d.pc_col) + ts.c.lo, (uint32_t)(ts.c.hi - ts.c.lo), bar);
+  bulk_copy(st + StageLayout::kOl, reinterpret_cast<const char*>(d.pc_ol) + ts.o.lo, (uint32_t)(ts.o.hi - ts.o.lo), bar);
+  bulk_copy(st + StageLayout::kRp, reinterpret_cast<const char*>(d.R_ptr) + ts.rp.lo, (uint32_t)(ts.rp.hi - ts.rp.lo), bar);
+  bulk_copy(st + StageLayout::kPp, reinterpret_cast<const char*>(d.pc_ptr) + ts.pp.lo, (uint32_t)(ts.pp.hi - ts.pp.lo), bar);
 }
+
+// Lanes per row of the staged passes: 16 for double-float (a tile holds up to 32 rows, one per
+// group of the 512 threads), 8 for the narrow storages (up to 64 rows).
+template <int K> struct StagedLanes { static constexpr int G = K == ST_F64 ? 16 : 8; };
 
 }  // namespace
 
 // Staged rows pass.  K = ST_F64: v = omega o (R p) in double-float (MODE 0 inside PCG, with
 // the doubly augmented bottom block; MODE 1 one apply).  K = reduced storage: w32 = s^2
 // (w_R + thR) o (R~ p32) (MODE 0 inside PCG, MODE 1 standalone).
-template <int K, int MODE, int G>
+//
+// Each group of G lanes takes one row of the tile; per chunk of NP pieces every lane first
+// issues its 16 gathers of the vector (and reads the 16 values from the stage), then does the
+// 16 multiply-adds in four independent chains, so the gathers of a lane are in flight together.
+template <int K, int MODE>
 __global__ void __launch_bounds__(kStagedThreads, 1) k_op_rows_staged(Dev d) {
+  constexpr int G = StagedLanes<K>::G;
+  constexpr int PP = kPiece / G;    // positions of a piece per lane
+  constexpr int NP = 16 / PP;       // pieces per chunk: 16 entries per lane
   extern __shared__ __align__(128) char smem[];
   __shared__ __align__(8) uint64_t bars[kStages];
   __shared__ int s_skip;
@@ -148,7 +198,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_op_rows_staged(Dev d) {
   if (tid == 0) s_skip = (MODE == 0) ? d.sc->cg_done : 0;
   __syncthreads();
   if (s_skip) return;
-  const int gl = tid & (G - 1), grp = tid / G, ngroups = kStagedThreads / G;
+  const int gl = tid & (G - 1), grp = tid / G;
   const int64_t nt = d.ntiles;
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) mbar_init(smem_u32(&bars[s]));
@@ -163,6 +213,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_op_rows_staged(Dev d) {
     }
   int64_t i = 0;
   bool bad = false;   // the same in every thread: decided by a block-wide vote
+  const char* gv = values_of<K>(d);
   for (;; ++i) {
     const int64_t t = blockIdx.x + i * gridDim.x;
     if (t >= nt) break;
@@ -173,23 +224,59 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_op_rows_staged(Dev d) {
       bad = true;
       break;
     }
-    int64_t r0, r1;
-    uint64_t lo, hi;
-    tile_span<K>(d, t, r0, r1, lo, hi);
-    const bool direct = hi - lo > (uint64_t)kStageBytes + 16;
-    const char* sv = stage_of(s);
-    const char* gv = values_of<K>(d);
-    for (int64_t k0 = 0; k0 < r1 - r0; k0 += ngroups) {
-      const int64_t r = r0 + k0 + grp;
-      const bool ok = r < r1;
+    const TileSpans<K> ts(d, t);
+    const char* st = stage_of(s);
+    const int32_t* scol = reinterpret_cast<const int32_t*>(st + StageLayout::kCol);
+    const uint32_t* sol = reinterpret_cast<const uint32_t*>(st + StageLayout::kOl);
+    const int64_t* srp = reinterpret_cast<const int64_t*>(st + StageLayout::kRp);
+    const int64_t* spp = reinterpret_cast<const int64_t*>(st + StageLayout::kPp);
+    const int64_t kc = (int64_t)(ts.c.lo / 4), kr = (int64_t)(ts.rp.lo / 8);   // first staged element
+    for (int64_t q0 = 0; q0 < ts.r1 - ts.r0; q0 += kStagedThreads / G) {
+      const int64_t r = ts.r0 + q0 + grp;
+      const bool ok = r < ts.r1;
+      int64_t rb = 0, kb = 0, ke = 0;
+      if (ok) {
+        rb = ts.direct ? d.R_ptr[r] : srp[r - kr];
+        kb = ts.direct ? d.pc_ptr[r] : spp[r - kr];
+        ke = ts.direct ? d.pc_ptr[r + 1] : spp[r + 1 - kr];
+      }
+      const unsigned np = (unsigned)(ke - kb);
+      const unsigned npmax = __reduce_max_sync(0xffffffffu, np);
       if constexpr (K == ST_F64) {
-        float th = 0.f, tl = 0.f;
-        for_row_pieces<G>(d, r, ok, gl, [&](int64_t e, int c) {
-          const uint64_t b = (uint64_t)e * 8;
-          const float2 a = direct ? __ldg(reinterpret_cast<const float2*>(gv + b))
-                                  : *reinterpret_cast<const float2*>(sv + (b - lo));
-          df_mac(a, __ldg(d.p_df + c), th, tl);
-        });
+        float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
+        for (unsigned c0 = 0; c0 < npmax; c0 += NP) {
+          float2 av[NP * PP], xv[NP * PP];
+#pragma unroll
+          for (int q = 0; q < NP; ++q) {
+            const int64_t k = kb + c0 + q;
+            const bool valid = c0 + q < np;
+            const int col = valid ? (ts.direct ? d.pc_col[k] : scol[k - kc]) : 0;
+            const uint32_t ol = valid ? (ts.direct ? d.pc_ol[k] : sol[k - kc]) : 0u;
+            const int len = (int)(ol & 63u);
+            const int64_t eb = rb + (int64_t)(ol >> 6);
+#pragma unroll
+            for (int u = 0; u < PP; ++u) {
+              const int j = gl + u * G;
+              const bool in = j < len;
+              const uint64_t b = (uint64_t)(eb + j) * 8;
+              xv[q * PP + u] = in ? __ldg(d.p_df + col + j) : make_float2(0.f, 0.f);
+              av[q * PP + u] = !in ? make_float2(0.f, 0.f)
+                               : ts.direct ? __ldg(reinterpret_cast<const float2*>(gv + b))
+                                           : *reinterpret_cast<const float2*>(st + StageLayout::kVal + (b - ts.v.lo));
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < NP * PP; ++u) df_mac(av[u], xv[u], h[u & 3], l[u & 3]);
+        }
+        // the four chains, then the group, in a fixed order
+        float th = h[0], tl = l[0];
+#pragma unroll
+        for (int c = 1; c < 4; ++c) {
+          float s2, e2;
+          two_sum(th, h[c], s2, e2);
+          th = s2;
+          tl = __fadd_rn(__fadd_rn(tl, l[c]), e2);
+        }
         df_group_pair<G>(th, tl);
         if (ok && gl == 0) {
           if (MODE == 0 && d.aug) {
@@ -212,12 +299,30 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_op_rows_staged(Dev d) {
           }
         }
       } else {
-        float a = 0.f;
-        for_row_pieces<G>(d, r, ok, gl, [&](int64_t e, int c) {
-          const uint64_t b = (uint64_t)e * Val<K>::B;
-          const float v = Val<K>::dec(direct ? gv + b : sv + (b - lo));
-          a = fmaf(v, __ldg(d.p32 + c), a);
-        });
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (unsigned c0 = 0; c0 < npmax; c0 += NP) {
+          float av[NP * PP], xv[NP * PP];
+#pragma unroll
+          for (int q = 0; q < NP; ++q) {
+            const int64_t k = kb + c0 + q;
+            const bool valid = c0 + q < np;
+            const int col = valid ? (ts.direct ? d.pc_col[k] : scol[k - kc]) : 0;
+            const uint32_t ol = valid ? (ts.direct ? d.pc_ol[k] : sol[k - kc]) : 0u;
+            const int len = (int)(ol & 63u);
+            const int64_t eb = rb + (int64_t)(ol >> 6);
+#pragma unroll
+            for (int u = 0; u < PP; ++u) {
+              const int j = gl + u * G;
+              const bool in = j < len;
+              const uint64_t b = (uint64_t)(eb + j) * Val<K>::B;
+              xv[q * PP + u] = in ? __ldg(d.p32 + col + j) : 0.f;
+              av[q * PP + u] = !in ? 0.f : Val<K>::dec(ts.direct ? gv + b : st + StageLayout::kVal + (b - ts.v.lo));
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < NP * PP; ++u) acc[u & 3] = fmaf(av[u], xv[u], acc[u & 3]);
+        }
+        float a = (acc[0] + acc[1]) + (acc[2] + acc[3]);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
         if (ok && gl == 0) {
@@ -250,13 +355,6 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_op_rows_staged(Dev d) {
   }
 }
 
-#define DISPATCH_GS(g, ...)                                  \
-  switch (g) {                                               \
-    case 8: { constexpr int G = 8; __VA_ARGS__; } break;     \
-    case 16: { constexpr int G = 16; __VA_ARGS__; } break;   \
-    default: { constexpr int G = 32; __VA_ARGS__; } break;   \
-  }
-
 static int staged_grid(const Dev& d) {
   const int64_t sm = d.sm_count > 0 ? d.sm_count : 148;
   return (int)std::max<int64_t>(1, std::min<int64_t>(d.ntiles, sm));
@@ -266,10 +364,8 @@ template <int K>
 static void launch_staged_k(const Dev& d, int mode, cudaStream_t st) {
   const int grid = staged_grid(d);
   const size_t smem = (size_t)kStages * kStageAlloc;
-  // lanes per row: 8, 16 or 32 (the staged tiles hold 1-4 rows per group; 4 lanes are not offered)
-  const int g = d.g_rows < 8 ? 8 : d.g_rows;
-  if (mode == 0) { DISPATCH_GS(g, k_op_rows_staged<K, 0, G><<<grid, kStagedThreads, smem, st>>>(d)); }
-  else { DISPATCH_GS(g, k_op_rows_staged<K, 1, G><<<grid, kStagedThreads, smem, st>>>(d)); }
+  if (mode == 0) k_op_rows_staged<K, 0><<<grid, kStagedThreads, smem, st>>>(d);
+  else k_op_rows_staged<K, 1><<<grid, kStagedThreads, smem, st>>>(d);
 }
 
 cudaError_t launch_op_rows_staged(const Dev& d, int mode, cudaStream_t st) {
@@ -288,10 +384,8 @@ cudaError_t prepare_staged() {
     const cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (r != cudaSuccess && e == cudaSuccess) e = r;
   };
-#define IPMK_SET_STAGED(K)                                                                              \
-  set((const void*)k_op_rows_staged<K, 0, 8>); set((const void*)k_op_rows_staged<K, 0, 16>);            \
-  set((const void*)k_op_rows_staged<K, 0, 32>); set((const void*)k_op_rows_staged<K, 1, 8>);            \
-  set((const void*)k_op_rows_staged<K, 1, 16>); set((const void*)k_op_rows_staged<K, 1, 32>);
+#define IPMK_SET_STAGED(K) \
+  set((const void*)k_op_rows_staged<K, 0>); set((const void*)k_op_rows_staged<K, 1>);
   IPMK_SET_STAGED(ST_F64)
   IPMK_SET_STAGED(ST_F32)
   IPMK_SET_STAGED(ST_BF16)

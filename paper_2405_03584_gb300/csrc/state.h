@@ -123,10 +123,14 @@ __device__ __forceinline__ double lr_row(const Dev& d, const int64_t j, const bo
 
 constexpr int kPiece = 32;      // entries per piece of a run (at most)
 
-// Staged rows pass (staged.cu): stages of the copy pipeline and bytes of one tile's values.
+// Staged rows pass (staged.cu): stages of the copy pipeline; a tile holds at most
+// kStageValBytes of values, kStagePieces pieces and kStageRows rows (32 for double-float and
+// 64 for the narrow storages: one row per lane group of the kStagedThreads threads).
 constexpr int kStages = 3;
-constexpr int kStageBytes = 64 * 1024;
-constexpr int kStageAlloc = kStageBytes + 32;   // a tile's values rounded out to 16-byte units
+constexpr int kStageValBytes = 60 * 1024;
+constexpr int kStagePieces = 1024;
+constexpr int kStageRows = 64;
+constexpr int kStageAlloc = 72 * 1024;
 constexpr int kStagedThreads = 512;
 
 // Calls f(e, c) for every stored entry e of row r of R, with its column c, by a group of G
