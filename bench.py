@@ -794,7 +794,7 @@ def main():
     ap.add_argument("--rows-format", choices=["auto", "csr", "runs"], default=None,
                     help="format of the PCG rows pass (default: the preset's)")
     ap.add_argument("--rows-stage", type=int, choices=[0, 1], default=None,
-                    help="0: rows pass staged through shared memory by bulk copies where available; 1: not")
+                    help="1: rows pass staged through shared memory by bulk copies where available; 0: not")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every kernel directly (for per-kernel profilers; same kernels, slower)")
     args = ap.parse_args()

@@ -96,8 +96,10 @@ enum ipm_arith { IPM_ARITH_F64 = 0, IPM_ARITH_DF32 = 1 };
 
 /* Format of R's rows in the PCG rows pass.  CSR: one int32 column index per entry.  RUNS: the
  * maximal stretches of consecutive entries with consecutive columns (a dose row's contiguous
- * spot bands) as (first column, first entry) pairs, so no per-entry index is read.  AUTO: RUNS
- * when R has at least 8 entries per run on average (the row order is the caller's). */
+ * spot bands), cut into pieces of at most 32 entries with one 8-byte descriptor each, so no
+ * per-entry index is read.  AUTO: RUNS for the reduced storages when R has at least 8 entries
+ * per run on average (the row order is the caller's), CSR otherwise (with float64 or
+ * double-float arithmetic the CSR pass measured as fast or faster on the RT workload). */
 enum ipm_rows_format { IPM_ROWS_AUTO = 0, IPM_ROWS_CSR = 1, IPM_ROWS_RUNS = 2 };
 
 /* ipm_solve flags. */
@@ -146,13 +148,16 @@ typedef struct ipm_options {
                          /* from its average row length                                        */
   int op_arith;          /* enum ipm_arith: PCG operator arithmetic with F64 storage (F64)      */
   int rows_format;       /* enum ipm_rows_format of the PCG rows pass (AUTO)                    */
-  int rows_stage;        /* 0 (default): with RUNS, double-float or reduced storage, the rows   */
-                         /* pass streams R's values into shared memory by bulk copies (TMA),    */
-                         /* one three-stage pipeline per SM; 1: it reads global memory          */
+  int rows_stage;        /* 1: with RUNS and double-float or reduced storage, the rows pass     */
+                         /* streams R's values, piece descriptors and row pointers into shared  */
+                         /* memory by bulk copies (TMA), one three-stage pipeline per SM;       */
+                         /* 0 (default): it reads global memory (measured faster on the RT     */
+                         /* workload)                                                           */
   double wait_limit_ms;  /* limit of every device-side wait (1000): when one runs out the solve */
                          /* stops with IPM_ERR_TIMEOUT (the iterate is then not meaningful)     */
   int wait_test;         /* test of the device watchdog (0): 1 arms the first staged tile's     */
                          /* barrier for 16 bytes more than is copied, so its wait runs out      */
+                         /* (needs rows_stage = 1)                                              */
 } ipm_options;
 
 /* Fills *opt with the defaults listed above. */

@@ -436,7 +436,8 @@ int prepare_operator_formats(ipm_handle* h) {
   const int64_t npieces = pp[d.nR];
   // a piece records its offset in the row in 26 bits
   if (nruns == 0 || longest >= ((int64_t)1 << 26)) return IPM_OK;
-  const bool use = h->opt.rows_format == IPM_ROWS_RUNS || (double)d.nnzR >= 8.0 * (double)nruns;
+  const bool use = h->opt.rows_format == IPM_ROWS_RUNS ||
+                   (d.storage != ST_F64 && (double)d.nnzR >= 8.0 * (double)nruns);
   if (!use) return IPM_OK;
   // tiles of the staged rows pass (double-float or reduced storage): consecutive rows, at most
   // one per lane group (32 rows for double-float, 64 otherwise), whose values take at most
@@ -445,7 +446,7 @@ int prepare_operator_formats(ipm_handle* h) {
   // global memory
   std::vector<int32_t> tiles;
   const int vbytes = d.df ? 8 : (d.storage == ST_F32 ? 4 : d.storage == ST_BF16 ? 2 : d.storage == ST_FP8 ? 1 : 0);
-  if (vbytes && h->opt.rows_stage == 0) {
+  if (vbytes && h->opt.rows_stage == 1) {
     const int64_t cap = (kStageValBytes - 16) / vbytes;
     const int64_t max_rows = d.df ? kStagedThreads / 16 : kStagedThreads / 8;
     tiles.push_back(0);

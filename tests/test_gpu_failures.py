@@ -111,7 +111,7 @@ def test_device_wait_limit(storage, arith):
     stops the PCG loop, the solve ends with IPM_ERR_TIMEOUT after its first IPM iteration, and
     the GPU context stays usable for the next solve."""
     p = W.rt_qp(n=4000, seed=85)
-    opts = dict(tol_kkt=1e-7, storage=storage, op_arith=arith, rows_format="runs")
+    opts = dict(tol_kkt=1e-7, storage=storage, op_arith=arith, rows_format="runs", rows_stage=1)
     with ipm.Solver(wait_test=1, wait_limit_ms=5.0, **opts) as s:
         s.set_qp_rt(p)
         with pytest.raises(ipm.IpmError) as e:

@@ -14,8 +14,8 @@ width) and compared element by element with the oracle at the same iterate:
   at eta = 1e-10 against the oracle's exact direction (1e-6 relative).
 
 Each FP64-storage check runs for both operator arithmetics (float64, double-float) and both
-formats of the rows pass (CSR, runs; double-float runs staged through shared memory and read
-from global memory); the reduced storages for every format.
+formats of the rows pass (CSR, runs; double-float runs also staged through shared memory by
+bulk copies); the reduced storages for every format.
 """
 import itertools
 
@@ -53,13 +53,13 @@ def _err(a, b):
     return np.abs(a - b).max() / (np.abs(b).max() + 1e-300)
 
 
-VARIANTS = [("f64", "csr"), ("f64", "runs"), ("df32", "csr"), ("df32", "runs"), ("df32", "runs-unstaged")]
+VARIANTS = [("f64", "csr"), ("f64", "runs"), ("df32", "csr"), ("df32", "runs"), ("df32", "runs-staged")]
 
 
 def _fmt(fmt):
-    """rows_format and rows_stage of a variant name ("runs-unstaged": the pieces read from
-    global memory instead of the staged copy pipeline)."""
-    return dict(rows_format=fmt.split("-")[0], rows_stage=1 if fmt.endswith("unstaged") else 0)
+    """rows_format and rows_stage of a variant name ("runs-staged": the pieces
+    streamed through the shared-memory copy pipeline instead of read from global memory)."""
+    return dict(rows_format=fmt.split("-")[0], rows_stage=1 if fmt.endswith("-staged") else 0)
 
 
 @pytest.mark.parametrize("arith,fmt", VARIANTS, ids=["%s-%s" % v for v in VARIANTS])
@@ -88,7 +88,7 @@ def test_fp64_kernels_every_width(case, lr, lc, arith, fmt):
         assert _err(d["dzl"], ref_dir.zl) <= 1e-7 and _err(d["dzu"], ref_dir.zu) <= 1e-7
 
 
-@pytest.mark.parametrize("fmt", ["csr", "runs", "runs-unstaged"])
+@pytest.mark.parametrize("fmt", ["csr", "runs", "runs-staged"])
 @pytest.mark.parametrize("storage", ["f32", "bf16", "fp8"])
 @pytest.mark.parametrize("lr,lc", PAIRS, ids=["rows%d-cols%d" % pc for pc in PAIRS])
 def test_reduced_precision_kernels_every_width(case, storage, lr, lc, fmt):

@@ -13,13 +13,13 @@ from paper_2405_03584_gb300 import ipm, workloads as W
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = [("f64", "runs"), ("df32", "csr"), ("df32", "runs"), ("df32", "runs-unstaged")]
+VARIANTS = [("f64", "runs"), ("df32", "csr"), ("df32", "runs"), ("df32", "runs-staged")]
 
 
 def _fmt(fmt):
-    """rows_format and rows_stage options of a variant name ("runs-unstaged": pieces read from
-    global memory instead of the staged copy pipeline)."""
-    return dict(rows_format=fmt.split("-")[0], rows_stage=1 if fmt.endswith("unstaged") else 0)
+    """rows_format and rows_stage options of a variant name ("runs-staged": the
+    pieces streamed through the shared-memory copy pipeline instead of read from global memory)."""
+    return dict(rows_format=fmt.split("-")[0], rows_stage=1 if fmt.endswith("-staged") else 0)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -135,7 +135,8 @@ def test_rows_longer_than_a_stage(arith, storage):
     # the cost keeps its definition c = -D^T W d with the new rows
     rowid = np.repeat(np.arange(q["V"]), np.diff(q["D_indptr"]))
     q["c"] = -np.bincount(q["D_indices"], weights=q["D_data"] * (q["w"] * q["d"])[rowid], minlength=q["n"])
-    with ipm.Solver(tol_kkt=1e-6, op_arith=arith, storage=storage, rows_format="runs", max_cg=5000) as s:
+    with ipm.Solver(tol_kkt=1e-6, op_arith=arith, storage=storage, rows_format="runs", rows_stage=1,
+                    max_cg=5000) as s:
         s.set_qp_rt(q)
         if storage == "f64":
             x, sl, y, zl, zu = W.random_iterate(q["n"], q["m"], q["l"], q["u"], 3, 1.0)
@@ -174,18 +175,20 @@ def _mean_run(ip, ix):
 
 
 @pytest.mark.parametrize("n,density", [(2000, 0.02), (700, 0.005)])
-def test_runs_auto_detection(n, density):
-    """AUTO takes runs when they average at least 8 entries (banded dose rows at the RT
-    density) and keeps CSR otherwise (short rows, scattered columns)."""
+@pytest.mark.parametrize("storage", ["f64", "bf16"])
+def test_runs_auto_detection(n, density, storage):
+    """AUTO takes runs for the reduced storages when they average at least 8 entries (banded
+    dose rows at the RT density) and keeps CSR otherwise (short rows, scattered columns, or
+    FP64 storage, where the CSR pass is as fast)."""
     p = W.rt_qp(n=n, seed=16, density=density)
-    want = int(_mean_run(p["D_indptr"], p["D_indices"]) >= 8.0)
-    with ipm.Solver() as s:
+    want = int(storage != "f64" and _mean_run(p["D_indptr"], p["D_indices"]) >= 8.0)
+    with ipm.Solver(storage=storage) as s:
         s.set_qp_rt(p)
         assert s.get_config()["rows_runs"] == want
     rng = np.random.default_rng(3)
     n, m = 400, 300
     A = np.where(rng.random((m, n)) < 0.05, rng.normal(size=(m, n)), 0.0)
-    with ipm.Solver() as s:
+    with ipm.Solver(storage="bf16") as s:
         s.set_qp(n, m, rng.normal(size=n), np.abs(A).sum(1) + 1.0, np.zeros(n), np.ones(n), h0=np.ones(n),
                  A=_csr(A))
         assert s.get_config()["rows_runs"] == 0
