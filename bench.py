@@ -418,7 +418,7 @@ def run_bfgs(args):
     torch.cuda.set_device(0)
     build.build()
     p = _bfgs_problem(args.bfgs)
-    s = ipm.Solver(tol_kkt=TOL, precond="jacobi_lr", storage=args.storage,
+    s = ipm.Solver(tol_kkt=TOL, precond=args.precond or "jacobi_lr", storage=args.storage,
                    stiff_max=1024 if args.bfgs == "vmat" else 256)
     s.set_qp_bfgs(p)
     for _ in range(args.warmup):
@@ -636,6 +636,8 @@ def run_ours(args):
     dev = torch.cuda.current_device()
     p = W.rt_qp(n=N_FULL, seed=SEED)
     opts = presets.rt(args.storage, **_operator_opts(args))
+    if args.precond:
+        opts["precond"] = args.precond
     if args.system != "condensed":
         opts.update(system=args.system, precond="jacobi")
     s = ipm.Solver(use_graphs=0 if args.no_graphs else 1, **opts)
@@ -742,7 +744,7 @@ def run_ours(args):
                         "%s operator storage, f32 accumulate, f64 refinement and reductions" % args.storage,
                "data": "synthetic",
                "config": {"workload": WORKLOAD, "storage": args.storage, "system": args.system, "n": p["n"], "V": p["V"], "m": p["m"], "nnz_D": int(p["D_indptr"][-1]),
-                          "tol_kkt": TOL, "precond": "jacobi_lr", "parallelism": "replicas" if world > 1 else "single",
+                          "tol_kkt": TOL, "precond": opts["precond"], "parallelism": "replicas" if world > 1 else "single",
                           "l2": "no flush: operator working set (~1.2 GB) > 129 MB L2"},
                "latency_ms": {"p50": statistics.median(lat), "p99": p99, "mean": statistics.mean(lat)},
                "solve": {"status": [int(x) for x in statuses], "ipm_iters": [i["ipm_iters"] for i in infos],
@@ -789,6 +791,8 @@ def main():
                     help="the linear system of the Newton step (augmented: the paper's eq:2x2_augmented, Jacobi PCG)")
     ap.add_argument("--storage", choices=["f64", "f32", "bf16", "fp8"], default="f64",
                     help="operator storage of the single RT QP (reduced ones add FP64 refinement)")
+    ap.add_argument("--precond", choices=["jacobi", "jacobi_lr", "block32"], default=None,
+                    help="preconditioner of the RT and quasi-Newton modes (default: jacobi_lr)")
     ap.add_argument("--op-arith", choices=["f64", "df32"], default=None,
                     help="PCG operator arithmetic with f64 storage (default: the preset's)")
     ap.add_argument("--rows-format", choices=["auto", "csr", "runs"], default=None,

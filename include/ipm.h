@@ -63,13 +63,17 @@ enum ipm_mem_space { IPM_MEM_HOST = 0, IPM_MEM_DEVICE = 1 };
 
 /* Preconditioner of the PCG solve (Section 4.1.2 computes the Jacobi diagonal).
  *  JACOBI    : M = diag(H + A^T Theta A + Sigma), the paper's choice.
+ *  BLOCK32   : M = the 32 x 32 diagonal blocks of H + A^T Theta A + Sigma (blocks of consecutive
+ *              variables), each Cholesky-factored on the device every IPM iteration; the part of
+ *              the blocks that does not change with the iterate is formed once per QP.  Needs
+ *              the columns of every row of F and A in increasing order (IPM_ERR_ARG otherwise).
  *  JACOBI_LR : Jacobi on the rows whose theta is moderate, plus an exact low-rank correction
  *              (Woodbury) for the "stiff" rows whose theta_i sum_j a_ij^2 / M0_j > stiff_gamma;
  *              keeps PCG iteration counts bounded as mu -> 0 (default).
  *  DENSE     : the whole matrix, formed and Cholesky-factored on the device (one diagonal
  *              block of size n); for n <= dense_max_n and FP64 storage.                      */
 enum ipm_precond { IPM_PRECOND_JACOBI = 0, IPM_PRECOND_JACOBI_LR = 1, IPM_PRECOND_DENSE = 2,
-                   IPM_PRECOND_AUTO = 3 };
+                   IPM_PRECOND_AUTO = 3, IPM_PRECOND_BLOCK32 = 4 };
 
 /* Storage of the matrix values inside PCG.  F64 (default): the FP64 operator throughout.
  * F32 / BF16 / FP8_E4M3: a second copy of the values of R = [F; A] and R^T in that type with

@@ -66,6 +66,7 @@ int count_kernel_nodes(cudaGraph_t g) {
 struct MatStore {
   void* ptr = nullptr;
   void* aux = nullptr;              // runs of R's rows (sized only once R is on the device)
+  void* blk = nullptr;              // segments of the block-Jacobi preconditioner
   size_t bytes = 0;
   int device = 0;
   int storage = 0;
@@ -77,6 +78,7 @@ struct MatStore {
       cudaSetDevice(device);
       cudaFree(ptr);
       if (aux) cudaFree(aux);
+      if (blk) cudaFree(blk);
       cudaSetDevice(cur);
     }
   }
@@ -97,7 +99,7 @@ struct ipm_handle {
   Scal* hs = nullptr;               // pinned host copy of the device scalars
   bool loaded = false, have_iterate = false;
   int precond = PC_JACOBI_LR;
-  Graphs graphs[3];
+  Graphs graphs[kPrecondKinds];
   std::string err;
   ipm_info info{};
   double cnorm = 0, bnorm = 0;
@@ -247,7 +249,7 @@ void carve_matrix(Carver& cv, Dev& d, int64_t n, int64_t m, int64_t nR, int64_t 
 
 // Per-handle part: problem vectors (costs may change per handle), iterate and work space.
 void carve_state(Carver& cv, Dev& d, int64_t n, int64_t m, int64_t nR, int stiff_cap, int64_t sc_cap, bool dense,
-                 int storage, int trace_cap, bool df) {
+                 int storage, int trace_cap, bool df, int64_t nblk) {
   d.wR = cv.take<double>(nR); d.h0 = cv.take<double>(n); d.c = cv.take<double>(n); d.b = cv.take<double>(m);
   d.l = cv.take<double>(n); d.u = cv.take<double>(n);
   d.fl = cv.take<unsigned char>(n); d.fu = cv.take<unsigned char>(n);
@@ -299,6 +301,12 @@ void carve_state(Carver& cv, Dev& d, int64_t n, int64_t m, int64_t nR, int stiff
   } else {
     d.U = d.uw = d.lrs = d.upart = d.lrq = nullptr;
   }
+  if (nblk) {
+    d.blkC = cv.take<double>(nblk * 1024);
+    d.blkL = cv.take<double>(nblk * 1024);
+  } else {
+    d.blkC = d.blkL = nullptr;
+  }
   d.trace = cv.take<double>((int64_t)trace_cap * kTraceCols);
   d.partials = cv.take<double>(32 * (int64_t)kMaxRedBlocks);
   d.sc = cv.take<Scal>(1);
@@ -336,7 +344,7 @@ int alloc_trace(ipm_handle* h) {
 int validate_options(const ipm_options& o) {
   if (!(o.tol_kkt > 0) || !(o.tau > 0 && o.tau < 1) || o.max_ipm < 1 || o.max_cg < 1) return IPM_ERR_ARG;
   if (!(o.cg_eta_min > 0) || !(o.cg_eta_max >= o.cg_eta_min) || !(o.cg_eta_factor > 0)) return IPM_ERR_ARG;
-  if (o.precond < 0 || o.precond > 3 || o.stiff_max < 0 || o.stiff_max > 1024) return IPM_ERR_ARG;
+  if (o.precond < 0 || o.precond > 4 || o.stiff_max < 0 || o.stiff_max > 1024) return IPM_ERR_ARG;
   if (o.dense_max_n < 0 || o.dense_max_n > 2048 || !(o.stiff_gamma > 0)) return IPM_ERR_ARG;
   if (o.storage < 0 || o.storage > 3 || o.refine_max < 1 || !(o.refine_eta > 0 && o.refine_eta < 1)) return IPM_ERR_ARG;
   if (!(o.warm_rho >= 0 && o.warm_rho < 1)) return IPM_ERR_ARG;
@@ -485,6 +493,80 @@ int prepare_operator_formats(ipm_handle* h) {
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
   d.ntiles = ntiles;
   d.runs = 1;
+  return IPM_OK;
+}
+
+// Segments of the block-Jacobi preconditioner: for every row of R, the maximal stretches of its
+// entries whose columns fall into one block of 32 variables (the columns of a row must
+// increase), listed block by block in row order (a stable counting sort by block), once for
+// every row and once for the constraint rows; then the part of the blocks fixed for the QP.
+int prepare_block_segments(ipm_handle* h, const std::vector<int64_t>& Rp, const std::vector<int32_t>& arow) {
+  Dev& d = h->d;
+  d.nblk = (d.n + 31) / 32;
+  std::vector<int32_t> ri((size_t)d.nnzR);
+  if (d.nnzR) {
+    CUDA_TRY(h, cudaMemcpyAsync(ri.data(), d.R_idx, sizeof(int32_t) * ri.size(), cudaMemcpyDeviceToHost, h->st));
+    CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  }
+  std::vector<unsigned char> is_con((size_t)std::max<int64_t>(d.nR, 1), 0);
+  for (int32_t r : arow) is_con[r] = 1;
+  // count segments per block (all rows, constraint rows)
+  std::vector<int64_t> cs(d.nblk + 1, 0), cc(d.nblk + 1, 0);
+  for (int64_t r = 0; r < d.nR; ++r)
+    for (int64_t e = Rp[r]; e < Rp[r + 1]; ++e) {
+      if (e > Rp[r] && ri[e] <= ri[e - 1])
+        return fail(h, IPM_ERR_ARG, "BLOCK32 needs the columns of every row in increasing order");
+      if (e == Rp[r] || ri[e] / 32 != ri[e - 1] / 32) {
+        cs[ri[e] / 32 + 1]++;
+        if (is_con[r]) cc[ri[e] / 32 + 1]++;
+      }
+    }
+  for (int64_t b = 0; b < d.nblk; ++b) {
+    cs[b + 1] += cs[b];
+    cc[b + 1] += cc[b];
+  }
+  const int64_t ns = cs[d.nblk], nc = cc[d.nblk];
+  std::vector<int32_t> srow(ns), scnt(ns), crow(nc), ccnt(nc);
+  std::vector<int64_t> sbeg(ns), cbeg(nc);
+  std::vector<int64_t> fs(cs.begin(), cs.end() - 1), fc(cc.begin(), cc.end() - 1);
+  for (int64_t r = 0; r < d.nR; ++r) {
+    int64_t e = Rp[r];
+    while (e < Rp[r + 1]) {
+      const int32_t b = ri[e] / 32;
+      int64_t f = e + 1;
+      while (f < Rp[r + 1] && ri[f] / 32 == b) ++f;
+      const int64_t k = fs[b]++;
+      srow[k] = (int32_t)r; sbeg[k] = e; scnt[k] = (int32_t)(f - e);
+      if (is_con[r]) {
+        const int64_t kc = fc[b]++;
+        crow[kc] = (int32_t)r; cbeg[kc] = e; ccnt[kc] = (int32_t)(f - e);
+      }
+      e = f;
+    }
+  }
+  Carver cc0(nullptr);
+  cc0.take<int64_t>(d.nblk + 1); cc0.take<int64_t>(ns); cc0.take<int32_t>(ns); cc0.take<int32_t>(ns);
+  cc0.take<int64_t>(d.nblk + 1); cc0.take<int64_t>(nc); cc0.take<int32_t>(nc); cc0.take<int32_t>(nc);
+  const size_t bytes = cc0.off + 256;
+  int rc;
+  if ((rc = dev_alloc(h, &h->mat->blk, bytes, "block-Jacobi segments"))) return rc;
+  h->mat->bytes += bytes;
+  Carver cv((char*)h->mat->blk);
+  d.bs_ptr = cv.take<int64_t>(d.nblk + 1); d.bs_beg = cv.take<int64_t>(ns);
+  d.bs_row = cv.take<int32_t>(ns); d.bs_cnt = cv.take<int32_t>(ns);
+  d.bc_ptr = cv.take<int64_t>(d.nblk + 1); d.bc_beg = cv.take<int64_t>(nc);
+  d.bc_row = cv.take<int32_t>(nc); d.bc_cnt = cv.take<int32_t>(nc);
+  auto up = [&](const void* dst, const void* src, size_t nb) -> int {
+    if (nb) CUDA_TRY(h, cudaMemcpyAsync((void*)dst, src, nb, cudaMemcpyHostToDevice, h->st));
+    return IPM_OK;
+  };
+  if ((rc = up(d.bs_ptr, cs.data(), 8 * cs.size())) || (rc = up(d.bs_beg, sbeg.data(), 8 * sbeg.size())) ||
+      (rc = up(d.bs_row, srow.data(), 4 * srow.size())) || (rc = up(d.bs_cnt, scnt.data(), 4 * scnt.size())) ||
+      (rc = up(d.bc_ptr, cc.data(), 8 * cc.size())) || (rc = up(d.bc_beg, cbeg.data(), 8 * cbeg.size())) ||
+      (rc = up(d.bc_row, crow.data(), 4 * crow.size())) || (rc = up(d.bc_cnt, ccnt.data(), 4 * ccnt.size())))
+    return rc;
+  CUDA_TRY(h, launch_block_const(d, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));   // host staging buffers go out of scope
   return IPM_OK;
 }
 
@@ -773,6 +855,7 @@ int choose_precond(const ipm_handle* h) {
   const ipm_options& o = h->opt;
   int pc = o.precond;
   if (o.system == IPM_SYSTEM_AUGMENTED) return PC_JACOBI;   // the paper's Jacobi PCG on eq:2x2_augmented
+  if (pc == IPM_PRECOND_BLOCK32) return h->d.nblk ? PC_BLOCK32 : PC_JACOBI_LR;   // segments come from ipm_set_qp
   if (pc == IPM_PRECOND_AUTO) pc = (h->d.Kd && h->d.n <= 1024) ? PC_DENSE : PC_JACOBI_LR;
   if (pc == PC_DENSE && !h->d.Kd) pc = PC_JACOBI_LR;
   return pc;
@@ -931,6 +1014,7 @@ int ipm_update_costs(ipm_handle* h, const double* f_w, const double* c, int mem,
   if (f_w && fr) CUDA_TRY(h, cudaMemcpyAsync((void*)d.wR, hw.data(), 8 * fr, cudaMemcpyHostToDevice, h->st));
   if (c) CUDA_TRY(h, cudaMemcpyAsync((void*)d.c, hc.data(), 8 * d.n, cudaMemcpyHostToDevice, h->st));
   if (f_w) CUDA_TRY(h, launch_diagH(d, h->st));
+  if (f_w && d.nblk) CUDA_TRY(h, launch_block_const(d, h->st));   // the blocks' fixed part has w in it
   CUDA_TRY(h, cudaStreamSynchronize(h->st));   // host staging buffers go out of scope
   h->cnorm = cn;
   return leave(h, stream);
@@ -963,6 +1047,7 @@ int ipm_set_lowrank(ipm_handle* h, int64_t u_cols, const double* U, const double
   d.ucols = u_cols;
   destroy_graphs(h);                    // the captured kernels carry the old column count
   CUDA_TRY(h, launch_diagH(d, h->st));
+  if (d.nblk) CUDA_TRY(h, launch_block_const(d, h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));   // host staging buffers go out of scope
   return leave(h, stream);
 }
@@ -1178,7 +1263,8 @@ static int load_qp(ipm_handle* h, const ipm_qp* qp, int64_t m_ar, void* stream) 
   Carver cm(nullptr), cs(nullptr);
   const bool want_df = h->opt.op_arith == IPM_ARITH_DF32 && h->opt.storage == IPM_STORAGE_F64;
   carve_matrix(cm, dv, n, m, q.nR, nnzR, nnzAT, nnzHs, h->opt.storage, want_df);
-  carve_state(cs, dv, n, m, q.nR, stiff_cap, sc_cap, dense, h->opt.storage, h->opt.max_ipm, want_df);
+  const int64_t nblk = h->opt.precond == IPM_PRECOND_BLOCK32 ? (n + 31) / 32 : 0;
+  carve_state(cs, dv, n, m, q.nR, stiff_cap, sc_cap, dense, h->opt.storage, h->opt.max_ipm, want_df, nblk);
   const size_t mbytes = cm.off + 256, sbytes = cs.off + 256;
   if (h->opt.mem_budget > 0 && (double)(mbytes + sbytes) > h->opt.mem_budget)
     return fail(h, IPM_ERR_OOM, "QP needs " + std::to_string(mbytes + sbytes) + " bytes, over mem_budget");
@@ -1189,7 +1275,7 @@ static int load_qp(ipm_handle* h, const ipm_qp* qp, int64_t m_ar, void* stream) 
   h->mat = store;
   Carver cvm((char*)store->ptr), cvs((char*)h->arena);
   carve_matrix(cvm, dv, n, m, q.nR, nnzR, nnzAT, nnzHs, h->opt.storage, want_df);
-  carve_state(cvs, dv, n, m, q.nR, stiff_cap, sc_cap, dense, h->opt.storage, h->opt.max_ipm, want_df);
+  carve_state(cvs, dv, n, m, q.nR, stiff_cap, sc_cap, dense, h->opt.storage, h->opt.max_ipm, want_df, nblk);
   dv.n = n; dv.m = m; dv.nR = q.nR; dv.nnzR = nnzR; dv.nnzHs = nnzHs; dv.nnzA = nnzAT;
   dv.g_rows = heuristic_group(q.nR ? (double)nnzR / (double)q.nR : 0.0);
   dv.g_cols = heuristic_group((double)nnzR / (double)n);
@@ -1290,6 +1376,7 @@ static int load_qp(ipm_handle* h, const ipm_qp* qp, int64_t m_ar, void* stream) 
   CUDA_TRY(h, launch_quantize(d, h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));   // host staging buffers go out of scope
   if ((rc = prepare_operator_formats(h))) return rc;
+  if (nblk && (rc = prepare_block_segments(h, q.Rp, q.arow))) return rc;
   if (h->opt.autotune && !h->opt.lanes_rows && !h->opt.lanes_cols && (rc = autotune_groups(h))) return rc;
   h->loaded = true;
   h->have_iterate = false;
@@ -1474,7 +1561,8 @@ int ipm_share_qp(ipm_handle* h, ipm_handle* src, void* stream) {
   free_arena(h);
   Dev dv = sd;                      // sizes, lane choices and matrix pointers of the source
   Carver cs(nullptr);
-  carve_state(cs, dv, n, m, nR, stiff_cap, sc_cap, use_dense, h->opt.storage, h->opt.max_ipm, sd.R_df != nullptr);
+  carve_state(cs, dv, n, m, nR, stiff_cap, sc_cap, use_dense, h->opt.storage, h->opt.max_ipm, sd.R_df != nullptr,
+              sd.nblk);
   const size_t sbytes = cs.off + 256;
   if (h->opt.mem_budget > 0 && (double)sbytes > h->opt.mem_budget)
     return fail(h, IPM_ERR_OOM, "state needs " + std::to_string(sbytes) + " bytes, over mem_budget");
@@ -1482,7 +1570,8 @@ int ipm_share_qp(ipm_handle* h, ipm_handle* src, void* stream) {
   h->arena_bytes = sbytes;
   h->mat = store;
   Carver cvs((char*)h->arena);
-  carve_state(cvs, dv, n, m, nR, stiff_cap, sc_cap, use_dense, h->opt.storage, h->opt.max_ipm, sd.R_df != nullptr);
+  carve_state(cvs, dv, n, m, nR, stiff_cap, sc_cap, use_dense, h->opt.storage, h->opt.max_ipm, sd.R_df != nullptr,
+              sd.nblk);
   if (h->opt.lanes_rows) dv.g_rows = h->opt.lanes_rows;
   if (h->opt.lanes_cols) dv.g_cols = h->opt.lanes_cols;
   if (h->opt.lanes_at) dv.g_at = h->opt.lanes_at;
@@ -1523,6 +1612,7 @@ int ipm_share_qp(ipm_handle* h, ipm_handle* src, void* stream) {
   CUDA_TRY(h, launch_fill_rowk(d, h->st));
   CUDA_TRY(h, launch_densify_R(d, h->st));
   if (d.ucap) CUDA_TRY(h, cudaMemsetAsync(d.lrs, 0, sizeof(double) * d.ucap, h->st));
+  if (d.nblk) CUDA_TRY(h, launch_block_const(d, h->st));
   std::memset(h->hs, 0, sizeof(Scal));
   push_options(h);
   h->hs->mu = h->hs->mu0 = 1.0;
@@ -1641,7 +1731,7 @@ static int fill_info(ipm_handle* h, int64_t direct_launches) {
   in.cg_iters = s.cg_total;
   in.max_cg_step = s.max_cg_step;
   in.max_stiff_rows = s.max_stiff_seen;
-  in.precond = pc;
+  in.precond = pc == PC_BLOCK32 ? IPM_PRECOND_BLOCK32 : pc;
   in.rel_kkt = s.rel_kkt;
   in.primal_res = s.res_primal;
   in.dual_res = s.res_dual;

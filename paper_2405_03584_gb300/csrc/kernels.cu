@@ -1379,6 +1379,7 @@ __global__ void k_cg_p(Dev d, cudaGraphConditionalHandle h, int set_cond) {
 }
 
 cudaError_t launch_cg_init(const Dev& d, const Geo& g, int precond, cudaStream_t st) {
+  if (precond == PC_BLOCK32) return launch_block_apply(d, 1, st);
   if (precond == PC_DENSE) {
     k_dense_trsv<<<1, 1024, sizeof(double) * d.n, st>>>(d, 1);
   } else if (precond == PC_JACOBI_LR) {
@@ -1408,7 +1409,10 @@ cudaError_t launch_cg_body(const Dev& d, const Geo& g, int precond, cudaGraphCon
     launch_lr(d, d.p, 0, st);
     DISPATCH_G(d.g_cols, k_op_cols<0, G><<<g.gNc, kBlock, 0, st>>>(d));
   }
-  if (precond == PC_DENSE) {
+  if (precond == PC_BLOCK32) {
+    k_cg_update<2><<<g.eN, kBlock, 0, st>>>(d);
+    launch_block_apply(d, 0, st);
+  } else if (precond == PC_DENSE) {
     k_cg_update<2><<<g.eN, kBlock, 0, st>>>(d);
     k_dense_trsv<<<1, 1024, sizeof(double) * d.n, st>>>(d, 0);
   } else if (precond == PC_JACOBI_LR) {
@@ -1596,6 +1600,7 @@ cudaError_t launch_precond_build(const Dev& d, const Geo& g, int precond, cudaSt
 // (JACOBI_LR) or the dense factor (DENSE).
 cudaError_t launch_precond_finish(const Dev& d, const Geo& g, int precond, cudaStream_t st) {
   if (precond == PC_DENSE) return launch_dense_build(d, st);
+  if (precond == PC_BLOCK32) return launch_block_factor(d, st);
   if (precond == PC_JACOBI_LR && d.m) {
     k_sc_count<<<g.gN, kBlock, 0, st>>>(d);
     k_sc_scan<<<1, 1024, 0, st>>>(d);

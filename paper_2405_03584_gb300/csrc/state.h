@@ -87,6 +87,13 @@ struct Dev {
   const int32_t* tile_row;     // ntiles + 1
   uint64_t wait_ns;            // limit of every device-side wait (options.wait_limit_ms)
   int wait_test;               // options.wait_test: the first staged tile's wait runs out
+  // block-Jacobi preconditioner (block.cu): blocks of 32 variables, "segments" = the entries
+  // of one row of R in one block (bs_*: every row, bc_*: the constraint rows), ordered by
+  // block then row; C_b (blkC, fixed per QP) and the factor of M_b (blkL), 32 x 32 each
+  int64_t nblk;
+  const int64_t *bs_ptr, *bs_beg, *bc_ptr, *bc_beg;   // nblk + 1 pointers; first entry of a segment
+  const int32_t *bs_row, *bs_cnt, *bc_row, *bc_cnt;   // row of R and entries (<= 32) of a segment
+  double *blkC, *blkL;
   // reduced-precision copy of the matrix values (storage != ST_F64): R~_ij = scaleR_i * q_ij
   int storage;
   void *Rq, *RTq;              // nnzR values each (float / bf16 / fp8-e4m3), indices shared with R, R^T
@@ -242,6 +249,12 @@ cudaError_t launch_op_cols_only(const Dev& d, const Geo& g, cudaStream_t st);
 // ---- full Jacobi diagonal into Minv's storage as M (not inverted) ----
 cudaError_t launch_jacobi_full(const Dev& d, const Geo& g, double* out, cudaStream_t st);
 
-enum Precond { PC_JACOBI = 0, PC_JACOBI_LR = 1, PC_DENSE = 2 };
+enum Precond { PC_JACOBI = 0, PC_JACOBI_LR = 1, PC_DENSE = 2, PC_BLOCK32 = 3 };
+constexpr int kPrecondKinds = 4;
+
+// ---- block-Jacobi preconditioner (block.cu) ----
+cudaError_t launch_block_const(const Dev& d, cudaStream_t st);          // C_b (once per QP / cost update)
+cudaError_t launch_block_factor(const Dev& d, cudaStream_t st);         // M_b and its factor (per IPM iteration)
+cudaError_t launch_block_apply(const Dev& d, int init, cudaStream_t st);  // z = M^{-1} r, rz / beta
 
 }  // namespace ipmk

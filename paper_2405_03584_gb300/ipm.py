@@ -22,7 +22,7 @@ IPM_OK, IPM_ERR_ARG, IPM_ERR_OOM, IPM_MAX_ITER, IPM_CG_STALL, IPM_NUMERICAL, \
     IPM_INFEASIBLE_SUSPECTED, IPM_ERR_TIMEOUT, IPM_ERR_CUDA, IPM_ERR_STATE, IPM_ERR_TOO_LARGE, IPM_BUSY = range(12)
 STATIC_SCRATCH_ROWS = 262144
 MEM_HOST, MEM_DEVICE = 0, 1
-PRECOND = {"jacobi": 0, "jacobi_lr": 1, "dense": 2, "auto": 3}
+PRECOND = {"jacobi": 0, "jacobi_lr": 1, "dense": 2, "auto": 3, "block32": 4}
 STORAGE = {"f64": 0, "f32": 1, "bf16": 2, "fp8": 3, "fp8_e4m3": 3}
 ARITH = {"f64": 0, "df32": 1}
 ROWS_FORMAT = {"auto": 0, "csr": 1, "runs": 2}

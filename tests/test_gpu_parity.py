@@ -88,7 +88,7 @@ def test_residuals_operator_diag(name, make):
     s.close()
 
 
-@pytest.mark.parametrize("precond", ["jacobi", "jacobi_lr", "dense"])
+@pytest.mark.parametrize("precond", ["jacobi", "jacobi_lr", "dense", "block32"])
 @pytest.mark.parametrize("name,make", CASES[:3], ids=[c[0] for c in CASES[:3]])
 def test_newton_direction_and_steps(name, make, precond):
     p = make()
@@ -148,7 +148,7 @@ def test_solve_dense_c0_shape(precond):
     _check_solution(p, qp, st, out, ref, 1e-8)
 
 
-@pytest.mark.parametrize("precond", ["jacobi_lr", "dense", "jacobi"])
+@pytest.mark.parametrize("precond", ["jacobi_lr", "dense", "jacobi", "block32"])
 def test_solve_rt_small(precond):
     p = W.rt_qp(n=1500, seed=9)
     st, out, ref, qp = _solve_both(p, 1e-7, precond=precond, max_cg=20000)
