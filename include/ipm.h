@@ -66,7 +66,8 @@ enum ipm_mem_space { IPM_MEM_HOST = 0, IPM_MEM_DEVICE = 1 };
  *  BLOCK32   : M = the 32 x 32 diagonal blocks of H + A^T Theta A + Sigma (blocks of consecutive
  *              variables), each Cholesky-factored on the device every IPM iteration; the part of
  *              the blocks that does not change with the iterate is formed once per QP.  Needs
- *              the columns of every row of F and A in increasing order (IPM_ERR_ARG otherwise).
+ *              the columns of every row of F and A in increasing order and F64 storage
+ *              (IPM_ERR_ARG otherwise).
  *  JACOBI_LR : Jacobi on the rows whose theta is moderate, plus an exact low-rank correction
  *              (Woodbury) for the "stiff" rows whose theta_i sum_j a_ij^2 / M0_j > stiff_gamma;
  *              keeps PCG iteration counts bounded as mu -> 0 (default).

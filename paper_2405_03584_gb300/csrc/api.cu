@@ -360,6 +360,8 @@ int validate_options(const ipm_options& o) {
   // the dense factor is an FP64 preconditioner for the FP64 operator: with a reduced-precision
   // operator the refinement's inner PCG under it stalled near convergence (RT n = 900, FP8)
   if (o.precond == IPM_PRECOND_DENSE && o.storage != IPM_STORAGE_F64) return IPM_ERR_ARG;
+  // likewise the block factors (RT n = 900 with BF16 storage ended in IPM_NUMERICAL)
+  if (o.precond == IPM_PRECOND_BLOCK32 && o.storage != IPM_STORAGE_F64) return IPM_ERR_ARG;
   auto lanes_ok = [](int g) { return g == 0 || g == 4 || g == 8 || g == 16 || g == 32; };
   if (!lanes_ok(o.lanes_rows) || !lanes_ok(o.lanes_cols) || !lanes_ok(o.lanes_at)) return IPM_ERR_ARG;
   return IPM_OK;

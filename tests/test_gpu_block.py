@@ -110,13 +110,15 @@ def test_direction_and_solve_match_oracle(case):
     assert abs(f - f0) / (1 + abs(f0)) <= 1e-6
 
 
-@pytest.mark.parametrize("storage", ["f64", "bf16"])
-def test_shared_plan_and_cost_update(storage):
+def test_shared_plan_and_cost_update():
     """A slot sharing the plan forms its own fixed block part (from its own weights): the same
-    bits as the plan; after ipm_update_costs both solve the new QP alike."""
+    bits as the plan; after ipm_update_costs both solve the new QP alike.  Reduced storage is
+    refused with the block factors (as with the dense factor)."""
+    for storage in ("bf16", "fp8", "f32"):
+        with pytest.raises(ipm.IpmError):
+            ipm.Solver(precond="block32", storage=storage)
     p = W.rt_qp(n=900, seed=7)
-    with ipm.Solver(precond="block32", tol_kkt=1e-8, storage=storage) as plan, \
-            ipm.Solver(precond="block32", tol_kkt=1e-8, storage=storage) as slot:
+    with ipm.Solver(precond="block32", tol_kkt=1e-8) as plan, ipm.Solver(precond="block32", tol_kkt=1e-8) as slot:
         plan.set_qp_rt(p)
         slot.share_qp(plan)
         assert plan.solve() == ipm.IPM_OK and slot.solve() == ipm.IPM_OK
