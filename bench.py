@@ -239,6 +239,10 @@ def _operator_opts(args):
         o["rows_format"] = args.rows_format
     if args.rows_stage is not None:
         o["rows_stage"] = args.rows_stage
+    if args.cols_format is not None:
+        o["cols_format"] = args.cols_format
+    if args.refine_eta is not None:
+        o["refine_eta"] = args.refine_eta
     return o
 
 
@@ -751,7 +755,8 @@ def run_ours(args):
                          "cg_iters": [i["cg_iters"] for i in infos], "rel_kkt_device": infos[-1]["rel_kkt"],
                          "max_stiff_rows": infos[-1]["max_stiff_rows"],
                          "lanes_per_row": [infos[-1]["lanes_rows"], infos[-1]["lanes_cols"]],
-                         "op_arith": ["f64", "df32"][infos[-1]["op_arith"]], "rows_runs": infos[-1]["rows_runs"]},
+                         "op_arith": ["f64", "df32"][infos[-1]["op_arith"]], "rows_runs": infos[-1]["rows_runs"],
+                         "cols_gap": infos[-1]["cols_gap"], "refine_passes": infos[-1]["refine_passes"]},
                "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk}
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -799,6 +804,10 @@ def main():
                     help="format of the PCG rows pass (default: the preset's)")
     ap.add_argument("--rows-stage", type=int, choices=[0, 1], default=None,
                     help="1: rows pass staged through shared memory by bulk copies where available; 0: not")
+    ap.add_argument("--cols-format", type=int, choices=[0, 1], default=None,
+                    help="reduced storages: 0 column pass on 16-bit row gaps (default), 1 on int32 indices")
+    ap.add_argument("--refine-eta", type=float, default=None,
+                    help="reduced storages: inner PCG tolerance of each refinement pass (default 0.1)")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every kernel directly (for per-kernel profilers; same kernels, slower)")
     args = ap.parse_args()

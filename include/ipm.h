@@ -163,6 +163,9 @@ typedef struct ipm_options {
   int wait_test;         /* test of the device watchdog (0): 1 arms the first staged tile's     */
                          /* barrier for 16 bytes more than is copied, so its wait runs out      */
                          /* (needs rows_stage = 1)                                              */
+  int cols_format;       /* reduced storages: 0 (default) the column pass reads R^T's row       */
+                         /* indices as 16-bit gaps (a base row per column, filler slots for     */
+                         /* wider gaps, columns padded to 8 slots); 1: int32 indices (CSR)      */
 } ipm_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -230,6 +233,7 @@ typedef struct ipm_info {
   int64_t fallback_steps;    /* Newton steps finished by FP64 PCG after refinement stalled */
   int op_arith;              /* enum ipm_arith the F64-storage PCG operator ran in         */
   int rows_runs;             /* 1 if the PCG rows pass read R's rows as runs               */
+  int cols_gap;              /* 1 if the reduced-precision column pass reads 16-bit gaps   */
 } ipm_info;
 
 /* Per-step result of ipm_newton_direction. */

@@ -67,6 +67,7 @@ struct MatStore {
   void* ptr = nullptr;
   void* aux = nullptr;              // runs of R's rows (sized only once R is on the device)
   void* blk = nullptr;              // segments of the block-Jacobi preconditioner
+  void* gap = nullptr;              // gap layout of R^T (reduced-precision column pass)
   size_t bytes = 0;
   int device = 0;
   int storage = 0;
@@ -79,6 +80,7 @@ struct MatStore {
       cudaFree(ptr);
       if (aux) cudaFree(aux);
       if (blk) cudaFree(blk);
+      if (gap) cudaFree(gap);
       cudaSetDevice(cur);
     }
   }
@@ -353,7 +355,7 @@ int validate_options(const ipm_options& o) {
   if (o.op_arith != IPM_ARITH_F64 && o.op_arith != IPM_ARITH_DF32) return IPM_ERR_ARG;
   if (o.rows_format < IPM_ROWS_AUTO || o.rows_format > IPM_ROWS_RUNS) return IPM_ERR_ARG;
   if (o.rows_stage < 0 || o.rows_stage > 1 || !(o.wait_limit_ms > 0 && o.wait_limit_ms <= 6e4)) return IPM_ERR_ARG;
-  if (o.wait_test < 0 || o.wait_test > 1) return IPM_ERR_ARG;
+  if (o.wait_test < 0 || o.wait_test > 1 || o.cols_format < 0 || o.cols_format > 1) return IPM_ERR_ARG;
   if (o.system == IPM_SYSTEM_AUGMENTED &&
       (o.storage != IPM_STORAGE_F64 || (o.precond != IPM_PRECOND_JACOBI && o.precond != IPM_PRECOND_AUTO)))
     return IPM_ERR_ARG;   // the doubly augmented system runs FP64 with the Jacobi preconditioner
@@ -406,9 +408,57 @@ std::map<std::tuple<int64_t, int64_t, int64_t>, std::pair<int, int>> g_tune_cach
 // values (asked for by options.op_arith, kept only when every value is in the float32 range
 // the pairs need) and the runs of R's rows (options.rows_format; AUTO takes them when they
 // average at least 8 entries).  The runs get a device allocation of their own, sized here.
+// The gap layout of R^T for the reduced-precision column pass (options.cols_format = 0): slots
+// per column counted on the device, their offsets scanned here, then filled on the device.
+int prepare_gap_layout(ipm_handle* h) {
+  Dev& d = h->d;
+  d.gap = 0;
+  d.nslots = 0;
+  if (d.storage == ST_F64 || h->opt.cols_format != 0 || d.nnzR == 0) return IPM_OK;
+  int32_t* cnt = reinterpret_cast<int32_t*>(d.tR);     // nR doubles of iteration work space
+  std::vector<int32_t> hc((size_t)d.n);
+  if (d.nR * 2 >= d.n) {
+    CUDA_TRY(h, launch_gap_count(d, cnt, h->st));
+  } else {
+    return IPM_OK;                                     // no room for the counts (fewer rows than n / 2)
+  }
+  CUDA_TRY(h, cudaMemcpyAsync(hc.data(), cnt, sizeof(int32_t) * hc.size(), cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  std::vector<int64_t> gp((size_t)d.n + 1, 0);
+  for (int64_t j = 0; j < d.n; ++j) gp[j + 1] = gp[j] + hc[j];
+  const int64_t ns = gp[d.n];
+  const int vb = d.storage == ST_F32 ? 4 : d.storage == ST_BF16 ? 2 : 1;
+  Carver cc(nullptr);
+  cc.take<int64_t>(d.n + 1);
+  cc.take<int32_t>(d.n);
+  cc.take<uint16_t>(ns);
+  cc.take<unsigned char>((int64_t)vb * ns);
+  const size_t bytes = cc.off + 256;
+  if (h->opt.mem_budget > 0 && (double)(h->mat->bytes + h->arena_bytes + bytes) > h->opt.mem_budget)
+    return IPM_OK;                                     // within the budget the column pass stays CSR
+  int rc;
+  if ((rc = dev_alloc(h, &h->mat->gap, bytes, "gap layout of R^T"))) return rc;
+  h->mat->bytes += bytes;
+  Carver cv((char*)h->mat->gap);
+  d.gp_ptr = cv.take<int64_t>(d.n + 1);
+  d.gp_base = cv.take<int32_t>(d.n);
+  d.gp_d = cv.take<uint16_t>(ns);
+  d.gp_q = cv.take<unsigned char>((int64_t)vb * ns);
+  d.nslots = ns;
+  CUDA_TRY(h, cudaMemcpyAsync((void*)d.gp_ptr, gp.data(), sizeof(int64_t) * gp.size(), cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, launch_gap_fill(d, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  d.gap = 1;
+  return IPM_OK;
+}
+
 int prepare_operator_formats(ipm_handle* h) {
   Dev& d = h->d;
   d.df = 0;
+  {
+    const int rc0 = prepare_gap_layout(h);
+    if (rc0) return rc0;
+  }
   if (d.R_df) {
     int* flag = reinterpret_cast<int*>(d.partials);   // reduction scratch, free at set-up
     CUDA_TRY(h, cudaMemsetAsync(flag, 0, sizeof(int), h->st));
@@ -938,6 +988,7 @@ void ipm_default_options(ipm_options* o) {
   o->op_arith = IPM_ARITH_F64;
   o->rows_format = IPM_ROWS_AUTO;
   o->rows_stage = 0;
+  o->cols_format = 0;
   o->wait_limit_ms = 1000.0;
   o->wait_test = 0;
   o->warm_rho = 1e-5;
@@ -1749,6 +1800,7 @@ static int fill_info(ipm_handle* h, int64_t direct_launches) {
   in.fallback_steps = h->d.storage != ST_F64 ? s.fallback_total : 0;
   in.op_arith = h->d.df ? IPM_ARITH_DF32 : IPM_ARITH_F64;
   in.rows_runs = h->d.runs;
+  in.cols_gap = h->d.gap;
   return status;
 }
 
@@ -1807,6 +1859,7 @@ int ipm_get_info(ipm_handle* h, ipm_info* info) {
   // the operator's configuration is known from ipm_set_qp on, solved or not
   h->info.op_arith = h->d.df ? IPM_ARITH_DF32 : IPM_ARITH_F64;
   h->info.rows_runs = h->d.runs;
+  h->info.cols_gap = h->d.gap;
   h->info.lanes_rows = h->d.g_rows;
   h->info.lanes_cols = h->d.g_cols;
   *info = h->info;
@@ -2204,8 +2257,10 @@ int ipm_profile_operator(ipm_handle* h, int reps, double* ms_rows, double* ms_co
     const double vb = d.storage == ST_F32 ? 4.0 : (d.storage == ST_BF16 ? 2.0 : 1.0);
     // rows: narrow values, the index data, scale, w_R, thR read, w32 written, p32 read once
     if (bytes_rows) *bytes_rows = vb * nnz + row_index + 24.0 * nR + 4.0 * n + lr_b;
-    // cols: narrow values + indices, row pointers, w32 read once, p, h0, sigma read, q written
-    if (bytes_cols) *bytes_cols = (vb + 4.0) * nnz + 8.0 * (n + 1) + 4.0 * nR + 32.0 * n + hs_b + lr_b;
+    // cols: narrow values + indices (CSR: 4 bytes an entry; gap layout: 2 bytes a slot and a base
+    // row per column), column pointers, w32 read once, p, h0, sigma read, q written
+    const double col_data = d.gap ? (vb + 2.0) * (double)d.nslots + 4.0 * n : (vb + 4.0) * nnz;
+    if (bytes_cols) *bytes_cols = col_data + 8.0 * (n + 1) + 4.0 * nR + 32.0 * n + hs_b + lr_b;
     if (flops_rows) *flops_rows = 2.0 * nnz + 4.0 * nR + lr_f;
     if (flops_cols) *flops_cols = 2.0 * nnz + 2.0 * nnzh + 4.0 * n + lr_f;
     return IPM_OK;

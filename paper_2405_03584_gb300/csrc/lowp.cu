@@ -210,8 +210,140 @@ __global__ void k_op_rows_lp(Dev d, int standalone) {
   }
 }
 
-// q_j = sum_i q_ij w_i + Hs p + (h0 + sigma) p;  p^T q -> alpha (last block), as k_op_cols.
+// ---------------------------------------------------------------- gap layout of R^T
+//
+// The reduced-precision column pass reads R^T's row indices as 16-bit gaps: within a column
+// the rows ascend, so slot s holds g_s = row_s - row_{s-1} (the column's first row is kept in
+// gp_base, its gap is 0).  A gap above 65535 is bridged by filler slots of gap 65535 and value
+// 0; every column is padded with slots of gap 0 and value 0 to a whole number of 8-slot
+// chunks.  Index bytes per entry: 2 instead of 4.  A lane decodes a chunk of 8 slots by a
+// running sum, the group adds the lane totals by a shuffle scan, and a carry moves from one
+// trip of chunks to the next.
+
+// Slots of column j: its entries, the fillers of its wide gaps, padding to a multiple of 8.
+__global__ void k_gap_count(Dev d, int32_t* __restrict__ slots) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t j = gwarp_l(); j < d.n; j += nwarps_l()) {
+    const int64_t beg = d.RT_ptr[j], end = d.RT_ptr[j + 1];
+    int64_t f = 0;
+    for (int64_t e = beg + 1 + lane; e < end; e += 32) f += (int64_t)(d.RT_idx[e] - d.RT_idx[e - 1] - 1) / 65535;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+    if (lane == 0) slots[j] = (int32_t)(((end - beg) + f + 7) & ~(int64_t)7);
+  }
+}
+
+// Fills the gap layout of column j (one warp per column): each entry's slot is its position
+// plus the fillers before it (a ballot-free prefix over the warp's 32 entries, then a carry).
+template <int S>
+__global__ void k_gap_fill(Dev d) {
+  using T = typename StorageT<S>::T;
+  const int lane = threadIdx.x & 31;
+  T* q = static_cast<T*>(const_cast<void*>(d.gp_q));
+  uint16_t* g = const_cast<uint16_t*>(d.gp_d);
+  for (int64_t j = gwarp_l(); j < d.n; j += nwarps_l()) {
+    const int64_t beg = d.RT_ptr[j], end = d.RT_ptr[j + 1];
+    const int64_t s0 = d.gp_ptr[j], s1 = d.gp_ptr[j + 1];
+    if (lane == 0) const_cast<int32_t*>(d.gp_base)[j] = end > beg ? d.RT_idx[beg] : 0;
+    int64_t next = s0;   // first slot after the entries placed so far
+    for (int64_t e0 = beg; e0 < end; e0 += 32) {
+      const int64_t e = e0 + lane;
+      const bool in = e < end;
+      const int64_t gap = (in && e > beg) ? (int64_t)(d.RT_idx[e] - d.RT_idx[e - 1]) : 0;
+      const int64_t f = gap > 0 ? (gap - 1) / 65535 : 0;
+      int64_t c = in ? f + 1 : 0;              // slots this entry takes (fillers + itself)
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(0xffffffffu, c, o);
+        if (lane >= o) c += t;
+      }
+      const int64_t pos = next + c - 1;        // the entry's own slot
+      if (in) {
+        for (int64_t k = 0; k < f; ++k) {
+          g[pos - f + k] = 65535;
+          q[pos - f + k] = StorageT<S>::enc(0.f);
+        }
+        g[pos] = (uint16_t)(gap - f * 65535);
+        q[pos] = StorageT<S>::enc((float)(d.RT_val[e] / (double)d.scaleR[d.RT_idx[e]]));
+      }
+      next += __shfl_sync(0xffffffffu, c, 31);
+    }
+    for (int64_t s = next + lane; s < s1; s += 32) {
+      g[s] = 0;
+      q[s] = StorageT<S>::enc(0.f);
+    }
+  }
+}
+
+// Eight consecutive stored values from one aligned load.
+template <int S> struct Chunk8;
+template <> struct Chunk8<ST_F32> {
+  static __device__ __forceinline__ void load(const float* p, float* v) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p)), b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  }
+};
+template <> struct Chunk8<ST_BF16> {
+  static __device__ __forceinline__ void load(const __nv_bfloat16* p, float* v) { Chunk<ST_BF16>::load(p, v); }
+};
+template <> struct Chunk8<ST_FP8> {
+  static __device__ __forceinline__ void load(const __nv_fp8_e4m3* p, float* v) { Chunk<ST_FP8>::load(p, v); }
+};
+
+// FP32 dot of column j (gap layout) with w32 by a group of G lanes: lane gl takes chunks
+// gl, gl + G, ... (8 slots each); trip counts are uniform over the warp.
 template <int S, int G>
+__device__ __forceinline__ float group_gap_dot_lp(const Dev& d, const int64_t j, const bool ok, const int gl) {
+  using T = typename StorageT<S>::T;
+  const T* q = static_cast<const T*>(d.gp_q);
+  const int64_t s0 = ok ? d.gp_ptr[j] : 0, s1 = ok ? d.gp_ptr[j + 1] : 0;
+  const unsigned nch = (unsigned)((s1 - s0) >> 3);
+  const unsigned trips = (__reduce_max_sync(0xffffffffu, nch) + G - 1) / G;
+  int64_t carry = ok ? d.gp_base[j] : 0;     // row of the slot before the trip's first chunk
+  float a = 0.f;
+  for (unsigned t = 0; t < trips; ++t) {
+    const unsigned c = t * G + gl;
+    const bool valid = c < nch;
+    const int64_t sb = s0 + 8 * (int64_t)c;
+    uint4 gd = make_uint4(0, 0, 0, 0);
+    float v[8];
+    if (valid) {
+      gd = __ldg(reinterpret_cast<const uint4*>(d.gp_d + sb));
+      Chunk8<S>::load(q + sb, v);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = 0.f;
+    }
+    const unsigned w[4] = {gd.x, gd.y, gd.z, gd.w};
+    int run[8];
+    int acc = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      acc += (int)(w[k] & 0xffffu);
+      run[2 * k] = acc;
+      acc += (int)(w[k] >> 16);
+      run[2 * k + 1] = acc;
+    }
+    // exclusive scan of the lane totals over the group (width G)
+    int incl = acc;
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {
+      const int t2 = __shfl_up_sync(0xffffffffu, incl, o, G);
+      if ((gl & (G - 1)) >= o) incl += t2;
+    }
+    const int64_t base = carry + (incl - acc);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a = fmaf(v[k], __ldg(d.w32 + (base + run[k])), a);
+    carry += __shfl_sync(0xffffffffu, incl, G - 1, G);
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  return a;
+}
+
+// q_j = sum_i q_ij w_i + Hs p + (h0 + sigma) p;  p^T q -> alpha (last block), as k_op_cols.
+// GAP: R^T read in the gap layout (16-bit row gaps) instead of CSR.
+template <int S, int G, bool GAP>
 __global__ void __launch_bounds__(256, 6) k_op_cols_lp(Dev d, int standalone) {
   __shared__ double sh[32];
   if (!standalone && d.sc->cg_done) return;
@@ -221,8 +353,13 @@ __global__ void __launch_bounds__(256, 6) k_op_cols_lp(Dev d, int standalone) {
   const bool stiff = d.sc->n_stiff > 0;
   double pq = 0.0;
   FOR_GROUP_ROWS_L(G, j, ok, d.n) {
-    const int64_t beg = ok ? d.RT_ptr[j] : 0, end = ok ? d.RT_ptr[j + 1] : 0;
-    const float acc = group_row_dot_lp<S, G>(beg, end, gl, d.RT_idx, q, d.w32);
+    float acc;
+    if (GAP) {
+      acc = group_gap_dot_lp<S, G>(d, j, ok, gl);
+    } else {
+      const int64_t beg = ok ? d.RT_ptr[j] : 0, end = ok ? d.RT_ptr[j + 1] : 0;
+      acc = group_row_dot_lp<S, G>(beg, end, gl, d.RT_idx, q, d.w32);
+    }
     double hs = 0.0;
     if (d.Hs_ptr) {
       const int64_t hb = ok ? d.Hs_ptr[j] : 0, he = ok ? d.Hs_ptr[j + 1] : 0;
@@ -313,7 +450,8 @@ cudaError_t launch_op_lp(const Dev& d, const Geo& g, cudaStream_t st) {
   k_stiff_op_u<<<(d.stiff_cap + 7) / 8, kBlock, 0, st>>>(d);
   launch_lr(d, d.p, 0, st);
   launch_rows_lp(d, g, 0, st);
-  DISPATCH_SG(d.storage, d.g_cols, k_op_cols_lp<S, G><<<g.gNc, kBlock, 0, st>>>(d, 0));
+  if (d.gap) DISPATCH_SG(d.storage, d.g_cols, k_op_cols_lp<S, G, true><<<g.gNc, kBlock, 0, st>>>(d, 0));
+  else DISPATCH_SG(d.storage, d.g_cols, k_op_cols_lp<S, G, false><<<g.gNc, kBlock, 0, st>>>(d, 0));
   return cudaGetLastError();
 }
 
@@ -325,13 +463,28 @@ cudaError_t launch_op_rows_lp_only(const Dev& d, const Geo& g, cudaStream_t st) 
 }
 
 cudaError_t launch_op_cols_lp_only(const Dev& d, const Geo& g, cudaStream_t st) {
-  DISPATCH_SG(d.storage, d.g_cols, k_op_cols_lp<S, G><<<g.gNc, kBlock, 0, st>>>(d, 1));
+  if (d.gap) DISPATCH_SG(d.storage, d.g_cols, k_op_cols_lp<S, G, true><<<g.gNc, kBlock, 0, st>>>(d, 1));
+  else DISPATCH_SG(d.storage, d.g_cols, k_op_cols_lp<S, G, false><<<g.gNc, kBlock, 0, st>>>(d, 1));
   return cudaGetLastError();
 }
 
 __global__ void k_mirror_p32(Dev d) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x)
     d.p32[j] = (float)d.p[j];
+}
+
+cudaError_t launch_gap_count(const Dev& d, int32_t* slots, cudaStream_t st) {
+  const int gb = (int)std::min<int64_t>((d.n + 7) / 8, 8 * (int64_t)(d.sm_count > 0 ? d.sm_count : 148));
+  k_gap_count<<<gb, 256, 0, st>>>(d, slots);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gap_fill(const Dev& d, cudaStream_t st) {
+  const int gb = (int)std::min<int64_t>((d.n + 7) / 8, 8 * (int64_t)(d.sm_count > 0 ? d.sm_count : 148));
+  if (d.storage == ST_F32) k_gap_fill<ST_F32><<<gb, 256, 0, st>>>(d);
+  else if (d.storage == ST_BF16) k_gap_fill<ST_BF16><<<gb, 256, 0, st>>>(d);
+  else k_gap_fill<ST_FP8><<<gb, 256, 0, st>>>(d);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_mirror_p32(const Dev& d, const Geo& g, cudaStream_t st) {

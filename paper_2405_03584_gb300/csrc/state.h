@@ -87,6 +87,14 @@ struct Dev {
   const int32_t* tile_row;     // ntiles + 1
   uint64_t wait_ns;            // limit of every device-side wait (options.wait_limit_ms)
   int wait_test;               // options.wait_test: the first staged tile's wait runs out
+  // gap layout of R^T for the reduced-precision column pass (lowp.cu): per column a base row
+  // and 16-bit row gaps, slots padded to multiples of 8
+  int gap;
+  int64_t nslots;
+  const int64_t* gp_ptr;       // n + 1
+  const int32_t* gp_base;      // n: the column's first row
+  const uint16_t* gp_d;        // nslots: row gaps
+  const void* gp_q;            // nslots: narrow values (0 at fillers and padding)
   // block-Jacobi preconditioner (block.cu): blocks of 32 variables, "segments" = the entries
   // of one row of R in one block (bs_*: every row, bc_*: the constraint rows), ordered by
   // block then row; C_b (blkC, fixed per QP) and the factor of M_b (blkL), 32 x 32 each
@@ -219,6 +227,8 @@ cudaError_t launch_op_lp(const Dev& d, const Geo& g, cudaStream_t st);
 cudaError_t launch_op_rows_lp_only(const Dev& d, const Geo& g, cudaStream_t st);   // measurement
 cudaError_t launch_op_cols_lp_only(const Dev& d, const Geo& g, cudaStream_t st);
 cudaError_t launch_mirror_p32(const Dev& d, const Geo& g, cudaStream_t st);
+cudaError_t launch_gap_count(const Dev& d, int32_t* slots, cudaStream_t st);   // slots per column of R^T
+cudaError_t launch_gap_fill(const Dev& d, cudaStream_t st);                    // gp_base, gp_d, gp_q
 // ---- double-float operator (df.cu) ----
 cudaError_t launch_df_split(const Dev& d, int* out_of_range, cudaStream_t st);   // R_df, RT_df from the FP64 values
 cudaError_t launch_mirror_df(const Dev& d, const Geo& g, cudaStream_t st);        // p_df from p

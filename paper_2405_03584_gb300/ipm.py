@@ -49,7 +49,8 @@ class Options(C.Structure):
                 ("lanes_rows", C.c_int), ("lanes_cols", C.c_int), ("warm_rho", C.c_double),
                 ("u_cap", C.c_int), ("ingest_host", C.c_int), ("system", C.c_int),
                 ("lanes_at", C.c_int), ("op_arith", C.c_int), ("rows_format", C.c_int),
-                ("rows_stage", C.c_int), ("wait_limit_ms", C.c_double), ("wait_test", C.c_int)]
+                ("rows_stage", C.c_int), ("wait_limit_ms", C.c_double), ("wait_test", C.c_int),
+                ("cols_format", C.c_int)]
 
 
 class QP(C.Structure):
@@ -68,7 +69,7 @@ class Info(C.Structure):
                 ("primal_obj", C.c_double), ("dual_obj", C.c_double), ("mu", C.c_double), ("solve_ms", C.c_double),
                 ("kernel_launches", C.c_int64), ("lanes_rows", C.c_int), ("lanes_cols", C.c_int),
                 ("refine_passes", C.c_int64), ("fallback_steps", C.c_int64), ("op_arith", C.c_int),
-                ("rows_runs", C.c_int)]
+                ("rows_runs", C.c_int), ("cols_gap", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -372,9 +373,9 @@ class Solver:
         return info.as_dict()
 
     def get_config(self):
-        """The operator configuration chosen at set_qp: op_arith, rows_runs, lanes_rows, lanes_cols."""
+        """The operator configuration chosen at set_qp: op_arith, rows_runs, cols_gap, lanes."""
         i = self.info()
-        return {k: i[k] for k in ("op_arith", "rows_runs", "lanes_rows", "lanes_cols")}
+        return {k: i[k] for k in ("op_arith", "rows_runs", "cols_gap", "lanes_rows", "lanes_cols")}
 
     def get(self, stream=None, out=None):
         """Returns dict(x, y, zl, zu, s, info).  ``out`` may give preallocated device tensors."""

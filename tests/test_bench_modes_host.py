@@ -60,7 +60,7 @@ class StandInSolver:
     def get(self):
         info = dict(status=0, ipm_iters=20, cg_iters=200, max_cg_step=10, max_stiff_rows=5, precond=1, rel_kkt=1e-7,
                     kernel_launches=1000, lanes_rows=8, lanes_cols=16, refine_passes=0, fallback_steps=0,
-                    op_arith=1, rows_runs=1)
+                    op_arith=1, rows_runs=1, cols_gap=0)
         return dict(x=np.zeros(self.n), y=np.zeros(self.m), zl=np.zeros(self.n), zu=np.zeros(self.n),
                     s=np.zeros(self.m), info=info)
     def profile_operator(self, reps=20):

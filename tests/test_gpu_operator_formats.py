@@ -151,6 +151,41 @@ def test_rows_longer_than_a_stage(arith, storage):
     assert kkt_check.rel_kkt(kkt_check.rt_ops(q), out["x"], out["y"], out["zl"], out["zu"]) <= 1e-6
 
 
+@pytest.mark.parametrize("storage", ["bf16", "fp8", "f32"])
+def test_gap_layout_wide_gaps_and_ragged_columns(storage):
+    """The reduced-precision column pass on 16-bit row gaps: V = 150000 voxel rows with one to
+    three entries each over n = 3000 spots, so the columns of R^T jump over more than 65535
+    rows (filler slots) and end in padding; some columns are empty.  Solved to the checker's
+    tolerance, and against the same solve on int32 indices."""
+    rng = np.random.default_rng(4)
+    n, V = 3000, 150000
+    k = rng.integers(1, 4, size=V)
+    ip = np.concatenate([[0], np.cumsum(k)]).astype(np.int64)
+    ix = np.concatenate([np.sort(rng.choice(n - 40, size=kk, replace=False)) for kk in k]).astype(np.int32)
+    dv = rng.lognormal(0.0, 1.0, ix.size)
+    w = rng.uniform(0.1, 10.0, V)
+    d = (rng.random(V) < 0.3).astype(float)
+    rowid = np.repeat(np.arange(V), k)
+    c = -np.bincount(ix, weights=dv * (w * d)[rowid], minlength=n)
+    a_rows = np.sort(rng.choice(np.flatnonzero(d == 0), size=500, replace=False)).astype(np.int32)
+    p = dict(kind="rt", n=n, V=V, m=a_rows.size, D_indptr=ip, D_indices=ix, D_data=dv, w=w, d=d,
+             h0=np.full(n, 1e-4), eps=1e-4, c=c, a_rows=a_rows, b=np.full(a_rows.size, 0.6), l=np.zeros(n),
+             u=np.full(n, 5.0))
+    col = np.sort(ix[np.argsort(ix, kind="stable")])
+    rows_by_col = np.split(rowid[np.argsort(ix, kind="stable")], np.searchsorted(col, np.arange(1, n)))
+    assert max(np.diff(r).max(initial=0) for r in rows_by_col) > 65535
+    xs = []
+    for cf in (0, 1):
+        with ipm.Solver(tol_kkt=1e-6, storage=storage, cols_format=cf, max_cg=5000) as s:
+            s.set_qp_rt(p)
+            assert s.get_config()["cols_gap"] == (cf == 0)
+            assert s.solve() == ipm.IPM_OK
+            out = s.get()
+        assert kkt_check.rel_kkt(kkt_check.rt_ops(p), out["x"], out["y"], out["zl"], out["zu"]) <= 1e-6
+        xs.append(out["x"])
+    assert np.abs(xs[0] - xs[1]).max() <= 1e-3 * (1 + np.abs(xs[1]).max())
+
+
 def test_double_float_refused_out_of_range():
     """Values beyond 2^90 would lose bits in a float32 pair: the handle keeps float64."""
     p = W.rt_qp(n=400, seed=15)
