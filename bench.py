@@ -805,7 +805,7 @@ def main():
     ap.add_argument("--rows-stage", type=int, choices=[0, 1], default=None,
                     help="1: rows pass staged through shared memory by bulk copies where available; 0: not")
     ap.add_argument("--cols-format", type=int, choices=[0, 1], default=None,
-                    help="reduced storages: 0 column pass on 16-bit row gaps (default), 1 on int32 indices")
+                    help="reduced storages: 0 column pass on int32 indices (default), 1 on 16-bit row gaps")
     ap.add_argument("--refine-eta", type=float, default=None,
                     help="reduced storages: inner PCG tolerance of each refinement pass (default 0.1)")
     ap.add_argument("--no-graphs", action="store_true",

@@ -163,9 +163,11 @@ typedef struct ipm_options {
   int wait_test;         /* test of the device watchdog (0): 1 arms the first staged tile's     */
                          /* barrier for 16 bytes more than is copied, so its wait runs out      */
                          /* (needs rows_stage = 1)                                              */
-  int cols_format;       /* reduced storages: 0 (default) the column pass reads R^T's row       */
-                         /* indices as 16-bit gaps (a base row per column, filler slots for     */
-                         /* wider gaps, columns padded to 8 slots); 1: int32 indices (CSR)      */
+  int cols_format;       /* reduced storages: 0 (default) the column pass reads R^T's int32     */
+                         /* row indices (CSR); 1: as 16-bit gaps (a base row per column, filler */
+                         /* slots for wider gaps, columns padded to 8 slots: 2 index bytes an   */
+                         /* entry instead of 4, measured slower on the RT workload: the decode  */
+                         /* costs more than the bytes it saves)                                 */
 } ipm_options;
 
 /* Fills *opt with the defaults listed above. */

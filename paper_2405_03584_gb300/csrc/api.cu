@@ -408,13 +408,13 @@ std::map<std::tuple<int64_t, int64_t, int64_t>, std::pair<int, int>> g_tune_cach
 // values (asked for by options.op_arith, kept only when every value is in the float32 range
 // the pairs need) and the runs of R's rows (options.rows_format; AUTO takes them when they
 // average at least 8 entries).  The runs get a device allocation of their own, sized here.
-// The gap layout of R^T for the reduced-precision column pass (options.cols_format = 0): slots
+// The gap layout of R^T for the reduced-precision column pass (options.cols_format = 1): slots
 // per column counted on the device, their offsets scanned here, then filled on the device.
 int prepare_gap_layout(ipm_handle* h) {
   Dev& d = h->d;
   d.gap = 0;
   d.nslots = 0;
-  if (d.storage == ST_F64 || h->opt.cols_format != 0 || d.nnzR == 0) return IPM_OK;
+  if (d.storage == ST_F64 || h->opt.cols_format != 1 || d.nnzR == 0) return IPM_OK;
   int32_t* cnt = reinterpret_cast<int32_t*>(d.tR);     // nR doubles of iteration work space
   std::vector<int32_t> hc((size_t)d.n);
   if (d.nR * 2 >= d.n) {

@@ -15,8 +15,8 @@ width) and compared element by element with the oracle at the same iterate:
 
 Each FP64-storage check runs for both operator arithmetics (float64, double-float) and both
 formats of the rows pass (CSR, runs; double-float runs also staged through shared memory by
-bulk copies); the reduced storages for every rows format, with the column pass on 16-bit row
-gaps (the default) and on int32 indices.
+bulk copies); the reduced storages for every rows format, with the column pass on int32
+indices (the default) and on 16-bit row gaps.
 """
 import itertools
 
@@ -60,10 +60,10 @@ VARIANTS = [("f64", "csr"), ("f64", "runs"), ("df32", "csr"), ("df32", "runs"), 
 def _fmt(fmt):
     """Options of a variant name: the rows format first ("csr", "runs"), then "-staged" (the
     pieces streamed through the shared-memory copy pipeline instead of read from global
-    memory) or "-colscsr" (the reduced-precision column pass on int32 indices instead of the
-    16-bit gap layout)."""
+    memory) or "-colsgap" (the reduced-precision column pass on the 16-bit row-gap layout
+    instead of int32 indices)."""
     return dict(rows_format=fmt.split("-")[0], rows_stage=1 if fmt.endswith("-staged") else 0,
-                cols_format=1 if fmt.endswith("-colscsr") else 0)
+                cols_format=1 if fmt.endswith("-colsgap") else 0)
 
 
 @pytest.mark.parametrize("arith,fmt", VARIANTS, ids=["%s-%s" % v for v in VARIANTS])
@@ -92,7 +92,7 @@ def test_fp64_kernels_every_width(case, lr, lc, arith, fmt):
         assert _err(d["dzl"], ref_dir.zl) <= 1e-7 and _err(d["dzu"], ref_dir.zu) <= 1e-7
 
 
-@pytest.mark.parametrize("fmt", ["csr", "runs", "runs-staged", "csr-colscsr"])
+@pytest.mark.parametrize("fmt", ["csr", "runs", "runs-staged", "runs-colsgap"])
 @pytest.mark.parametrize("storage", ["f32", "bf16", "fp8"])
 @pytest.mark.parametrize("lr,lc", PAIRS, ids=["rows%d-cols%d" % pc for pc in PAIRS])
 def test_reduced_precision_kernels_every_width(case, storage, lr, lc, fmt):

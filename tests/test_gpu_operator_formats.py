@@ -153,15 +153,21 @@ def test_rows_longer_than_a_stage(arith, storage):
 
 @pytest.mark.parametrize("storage", ["bf16", "fp8", "f32"])
 def test_gap_layout_wide_gaps_and_ragged_columns(storage):
-    """The reduced-precision column pass on 16-bit row gaps: V = 150000 voxel rows with one to
-    three entries each over n = 3000 spots, so the columns of R^T jump over more than 65535
-    rows (filler slots) and end in padding; some columns are empty.  Solved to the checker's
-    tolerance, and against the same solve on int32 indices."""
+    """The reduced-precision column pass on 16-bit row gaps (cols_format = 1): V = 150000 voxel
+    rows with one to three entries each over n = 3000 spots; some columns of R^T jump over more
+    than 65535 rows (filler slots), every column ends in padding, some are empty.  Solved to
+    the checker's tolerance, and against the same solve on int32 indices."""
     rng = np.random.default_rng(4)
     n, V = 3000, 150000
     k = rng.integers(1, 4, size=V)
+    rows = [np.sort(rng.choice(n - 40, size=kk, replace=False)) for kk in k]
+    # the last 40 columns: 20 hit only by rows 5, 70000 and 140000 (gaps of more than 65535
+    # rows: filler slots), 20 by none (empty columns)
+    for r in (5, 70000, 140000):
+        rows[r] = np.concatenate([rows[r], np.arange(n - 40, n - 20)])
+    k = np.array([len(a) for a in rows])
     ip = np.concatenate([[0], np.cumsum(k)]).astype(np.int64)
-    ix = np.concatenate([np.sort(rng.choice(n - 40, size=kk, replace=False)) for kk in k]).astype(np.int32)
+    ix = np.concatenate(rows).astype(np.int32)
     dv = rng.lognormal(0.0, 1.0, ix.size)
     w = rng.uniform(0.1, 10.0, V)
     d = (rng.random(V) < 0.3).astype(float)
@@ -175,10 +181,10 @@ def test_gap_layout_wide_gaps_and_ragged_columns(storage):
     rows_by_col = np.split(rowid[np.argsort(ix, kind="stable")], np.searchsorted(col, np.arange(1, n)))
     assert max(np.diff(r).max(initial=0) for r in rows_by_col) > 65535
     xs = []
-    for cf in (0, 1):
+    for cf in (1, 0):
         with ipm.Solver(tol_kkt=1e-6, storage=storage, cols_format=cf, max_cg=5000) as s:
             s.set_qp_rt(p)
-            assert s.get_config()["cols_gap"] == (cf == 0)
+            assert s.get_config()["cols_gap"] == (cf == 1)
             assert s.solve() == ipm.IPM_OK
             out = s.get()
         assert kkt_check.rel_kkt(kkt_check.rt_ops(p), out["x"], out["y"], out["zl"], out["zu"]) <= 1e-6
