@@ -35,7 +35,7 @@ METRIC = "QP solves/sec & p50/p99 latency at rel. KKT <=1e-6; PCG SpMV HBM GB/s"
 N_FULL, SEED, TOL = 50_000, 1, 1e-6
 WORKLOAD = ("RT-shaped QP: D 200000 voxels x 50000 spots, 0.5% banded lognormal, H = D^T W D + 1e-4 I "
             "matrix-free, A = 20000 organ rows (b = 0.6), 0 <= x <= 5, FP64, seed 1")
-SAMPLE_SIZES = (2000, 3000, 4000)   # oracle samples: the same generator at these n (V = 4n)
+SAMPLE_SIZES = (2000, 4000, 6000)   # oracle samples: the same generator at these n (V = 4n)
 FALLBACK_HBM_GBS = 6800.0
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 (non-tensor) nominal rate
 
@@ -682,14 +682,17 @@ def run_ours(args):
     lanes = infos[-1]["lanes_rows"] if kern == "k_op_rows" else infos[-1]["lanes_cols"]
     lp = args.storage != "f64"
     df = infos[-1]["op_arith"] == 1
+    mx = infos[-1]["op_arith"] == 2
     runs = infos[-1]["rows_runs"] == 1 and kern == "k_op_rows"
-    base = kern + ("_lp" if lp else "") + ("_df" if df and not lp else "") + ("_runs" if runs else "")
+    base = kern + ("_lp" if lp else "") + ("_df" if df and not lp else "") + ("_mx" if mx and not lp else "") + \
+        ("_runs" if runs else "")
     kname = "%s<%s%d lanes/row>" % (base, (args.storage + ", ") if lp else "", lanes)
     roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "traffic": _ncu_traffic(base, lanes),
             "peak_kind": peak_kind + " hbm_gbs",
             "algorithmic_bytes": byts, "ms_per_launch": ms,
             ("fp32_tflops" if lp or df else "fp64_tflops"): flops / (ms / 1000.0) / 1e12,
+            "arith": "f32" if lp else ("double-float" if df else ("split f64 / double-float" if mx else "f64")),
             "fp64_nominal_tflops": FP64_NOMINAL_TFLOPS,
             "other_kernel": {"ms_per_launch": prof["ms_" + ("cols" if key == "rows" else "rows")],
                              "gbs": prof["bytes_" + ("cols" if key == "rows" else "rows")] /
@@ -755,7 +758,7 @@ def run_ours(args):
                          "cg_iters": [i["cg_iters"] for i in infos], "rel_kkt_device": infos[-1]["rel_kkt"],
                          "max_stiff_rows": infos[-1]["max_stiff_rows"],
                          "lanes_per_row": [infos[-1]["lanes_rows"], infos[-1]["lanes_cols"]],
-                         "op_arith": ["f64", "df32"][infos[-1]["op_arith"]], "rows_runs": infos[-1]["rows_runs"],
+                         "op_arith": ["f64", "df32", "mixed"][infos[-1]["op_arith"]], "rows_runs": infos[-1]["rows_runs"],
                          "cols_gap": infos[-1]["cols_gap"], "refine_passes": infos[-1]["refine_passes"]},
                "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk}
         print(json.dumps(out), flush=True)
@@ -798,7 +801,7 @@ def main():
                     help="operator storage of the single RT QP (reduced ones add FP64 refinement)")
     ap.add_argument("--precond", choices=["jacobi", "jacobi_lr", "block32"], default=None,
                     help="preconditioner of the RT and quasi-Newton modes (default: jacobi_lr)")
-    ap.add_argument("--op-arith", choices=["f64", "df32"], default=None,
+    ap.add_argument("--op-arith", choices=["f64", "df32", "mixed"], default=None,
                     help="PCG operator arithmetic with f64 storage (default: the preset's)")
     ap.add_argument("--rows-format", choices=["auto", "csr", "runs"], default=None,
                     help="format of the PCG rows pass (default: the preset's)")

@@ -90,6 +90,9 @@ enum ipm_storage { IPM_STORAGE_F64 = 0, IPM_STORAGE_F32 = 1, IPM_STORAGE_BF16 = 
 
 /* Arithmetic of the PCG operator with F64 storage (not part of the paper, which uses FP64).
  *  F64  : float64 multiply-adds (GB300 issues two per SM per clock, which bounds the passes).
+ *  MIXED: half of every lane's products as float64 multiply-adds, half in double-float (as
+ *         DF32), so the float64 and float32 pipes work at once; each entry is still read once.
+ *         Keeps both copies of R and R^T; the same range condition as DF32.  Rows as CSR.
  *  DF32 : double-float: every value of R, R^T and of the vectors the operator reads is carried
  *         as a (hi, lo) pair of float32 (48 significant bits, the same 8 bytes), products and
  *         sums by error-free transformations on the float32 pipe; row sums within about 1e-13
@@ -97,7 +100,7 @@ enum ipm_storage { IPM_STORAGE_F64 = 0, IPM_STORAGE_F32 = 1, IPM_STORAGE_BF16 = 
  *         Needs the non-zero values of R within [2^-90, 2^90]; otherwise ipm_set_qp keeps F64
  *         (ipm_info.op_arith tells which ran).  An extra copy of R and R^T (8 bytes per entry
  *         each) is stored. */
-enum ipm_arith { IPM_ARITH_F64 = 0, IPM_ARITH_DF32 = 1 };
+enum ipm_arith { IPM_ARITH_F64 = 0, IPM_ARITH_DF32 = 1, IPM_ARITH_MIXED = 2 };
 
 /* Format of R's rows in the PCG rows pass.  CSR: one int32 column index per entry.  RUNS: the
  * maximal stretches of consecutive entries with consecutive columns (a dose row's contiguous

@@ -352,7 +352,7 @@ int validate_options(const ipm_options& o) {
   if (!(o.warm_rho >= 0 && o.warm_rho < 1)) return IPM_ERR_ARG;
   if (o.u_cap < 0 || o.u_cap > (1 << 16)) return IPM_ERR_ARG;
   if (o.system != IPM_SYSTEM_CONDENSED && o.system != IPM_SYSTEM_AUGMENTED) return IPM_ERR_ARG;
-  if (o.op_arith != IPM_ARITH_F64 && o.op_arith != IPM_ARITH_DF32) return IPM_ERR_ARG;
+  if (o.op_arith < IPM_ARITH_F64 || o.op_arith > IPM_ARITH_MIXED) return IPM_ERR_ARG;
   if (o.rows_format < IPM_ROWS_AUTO || o.rows_format > IPM_ROWS_RUNS) return IPM_ERR_ARG;
   if (o.rows_stage < 0 || o.rows_stage > 1 || !(o.wait_limit_ms > 0 && o.wait_limit_ms <= 6e4)) return IPM_ERR_ARG;
   if (o.wait_test < 0 || o.wait_test > 1 || o.cols_format < 0 || o.cols_format > 1) return IPM_ERR_ARG;
@@ -455,6 +455,7 @@ int prepare_gap_layout(ipm_handle* h) {
 int prepare_operator_formats(ipm_handle* h) {
   Dev& d = h->d;
   d.df = 0;
+  d.mx = 0;
   {
     const int rc0 = prepare_gap_layout(h);
     if (rc0) return rc0;
@@ -466,7 +467,8 @@ int prepare_operator_formats(ipm_handle* h) {
     int bad = 0;
     CUDA_TRY(h, cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     CUDA_TRY(h, cudaStreamSynchronize(h->st));
-    d.df = bad ? 0 : 1;
+    d.df = (!bad && h->opt.op_arith == IPM_ARITH_DF32) ? 1 : 0;
+    d.mx = (!bad && h->opt.op_arith == IPM_ARITH_MIXED) ? 1 : 0;
   }
   d.runs = 0;
   d.ntiles = 0;
@@ -477,7 +479,8 @@ int prepare_operator_formats(ipm_handle* h) {
   d.pc_ptr = nullptr;
   d.pc_col = nullptr;
   d.pc_ol = nullptr;
-  if (h->opt.rows_format == IPM_ROWS_CSR || d.nR == 0 || d.nnzR == 0) return IPM_OK;
+  // (the split-pipe passes read R's rows as CSR)
+  if (h->opt.rows_format == IPM_ROWS_CSR || d.mx || d.nR == 0 || d.nnzR == 0) return IPM_OK;
   // per row: runs and pieces (two int32 per row in the nR doubles of iteration work space tR)
   int32_t* cnt = reinterpret_cast<int32_t*>(d.tR);
   CUDA_TRY(h, launch_runs_count(d, cnt, cnt + d.nR, h->st));
@@ -1314,7 +1317,7 @@ static int load_qp(ipm_handle* h, const ipm_qp* qp, int64_t m_ar, void* stream) 
   dv.ublocks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * (int64_t)dv.sm_count, n / 32));
   const int64_t nnzHs = (int64_t)q.Hv.size();
   Carver cm(nullptr), cs(nullptr);
-  const bool want_df = h->opt.op_arith == IPM_ARITH_DF32 && h->opt.storage == IPM_STORAGE_F64;
+  const bool want_df = h->opt.op_arith != IPM_ARITH_F64 && h->opt.storage == IPM_STORAGE_F64;
   carve_matrix(cm, dv, n, m, q.nR, nnzR, nnzAT, nnzHs, h->opt.storage, want_df);
   const int64_t nblk = h->opt.precond == IPM_PRECOND_BLOCK32 ? (n + 31) / 32 : 0;
   carve_state(cs, dv, n, m, q.nR, stiff_cap, sc_cap, dense, h->opt.storage, h->opt.max_ipm, want_df, nblk);
@@ -1798,7 +1801,7 @@ static int fill_info(ipm_handle* h, int64_t direct_launches) {
   in.lanes_cols = h->d.g_cols;
   in.refine_passes = h->d.storage != ST_F64 ? s.refine_total : 0;
   in.fallback_steps = h->d.storage != ST_F64 ? s.fallback_total : 0;
-  in.op_arith = h->d.df ? IPM_ARITH_DF32 : IPM_ARITH_F64;
+  in.op_arith = h->d.mx ? IPM_ARITH_MIXED : h->d.df ? IPM_ARITH_DF32 : IPM_ARITH_F64;
   in.rows_runs = h->d.runs;
   in.cols_gap = h->d.gap;
   return status;
@@ -1857,7 +1860,7 @@ int ipm_get_info(ipm_handle* h, ipm_info* info) {
   if (!h || !info) return IPM_ERR_ARG;
   if (!h->loaded) return fail(h, IPM_ERR_STATE, "no QP loaded");
   // the operator's configuration is known from ipm_set_qp on, solved or not
-  h->info.op_arith = h->d.df ? IPM_ARITH_DF32 : IPM_ARITH_F64;
+  h->info.op_arith = h->d.mx ? IPM_ARITH_MIXED : h->d.df ? IPM_ARITH_DF32 : IPM_ARITH_F64;
   h->info.rows_runs = h->d.runs;
   h->info.cols_gap = h->d.gap;
   h->info.lanes_rows = h->d.g_rows;
@@ -2214,7 +2217,7 @@ int ipm_profile_operator(ipm_handle* h, int reps, double* ms_rows, double* ms_co
   // the passes the handle's PCG runs: FP64, or the reduced-precision ones of its storage
   const bool lp = d.storage != ST_F64;
   if (lp) CUDA_TRY(h, launch_mirror_p32(d, g, h->st));
-  if (d.df) CUDA_TRY(h, launch_mirror_df(d, g, h->st));
+  if (d.df || d.mx) CUDA_TRY(h, launch_mirror_df(d, g, h->st));
   auto rows = [&]() {
     cudaError_t e = lp ? launch_op_rows_lp_only(d, g, h->st) : launch_op_rows_only(d, g, h->st);
     if (e == cudaSuccess && d.ucols) e = launch_lr(d, d.p, 0, h->st);   // U^T p belongs to the first half

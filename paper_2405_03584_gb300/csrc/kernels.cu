@@ -1399,6 +1399,10 @@ cudaError_t launch_cg_body(const Dev& d, const Geo& g, int precond, cudaGraphCon
   if (lowp) {
     cudaError_t e = launch_op_lp(d, g, st);
     if (e != cudaSuccess) return e;
+  } else if (d.mx) {
+    launch_op_rows_mx(d, g, 0, st);
+    launch_lr(d, d.p, 0, st);
+    launch_op_cols_mx(d, g, 0, st);
   } else if (d.df) {
     launch_op_rows_df(d, g, 0, st);
     launch_lr(d, d.p, 0, st);
@@ -1431,6 +1435,7 @@ cudaError_t launch_cg_body(const Dev& d, const Geo& g, int precond, cudaGraphCon
 // The rows and the column pass of the handle's FP64-storage PCG operator alone (measurement,
 // autotuning); the double-float passes read p_df, which the caller keeps current.
 cudaError_t launch_op_rows_only(const Dev& d, const Geo& g, cudaStream_t st) {
+  if (d.mx) return launch_op_rows_mx(d, g, 1, st);
   if (d.df) return launch_op_rows_df(d, g, 1, st);
   if (d.runs) return launch_op_rows_runs(d, g, 1, st);
   if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<1, G><<<g.gRc, kBlock, 0, st>>>(d));
@@ -1439,6 +1444,7 @@ cudaError_t launch_op_rows_only(const Dev& d, const Geo& g, cudaStream_t st) {
 
 cudaError_t launch_op_cols_only(const Dev& d, const Geo& g, cudaStream_t st) {
   // (the low-rank term uses us from the last launch_lr; the measurement does not re-run it)
+  if (d.mx) return launch_op_cols_mx(d, g, 1, st);
   if (d.df) return launch_op_cols_df(d, g, 1, st);
   DISPATCH_G(d.g_cols, k_op_cols<1, G><<<g.gNc, kBlock, 0, st>>>(d));
   return cudaGetLastError();
@@ -1446,6 +1452,13 @@ cudaError_t launch_op_cols_only(const Dev& d, const Geo& g, cudaStream_t st) {
 
 // q = K p, one apply of the handle's FP64-storage PCG operator (FP64 or double-float).
 cudaError_t launch_apply(const Dev& d, const Geo& g, cudaStream_t st) {
+  if (d.mx) {
+    launch_mirror_df(d, g, st);
+    launch_op_rows_mx(d, g, 1, st);
+    launch_lr(d, d.p, 0, st);
+    launch_op_cols_mx(d, g, 1, st);
+    return cudaGetLastError();
+  }
   if (d.df) {
     launch_mirror_df(d, g, st);
     launch_op_rows_df(d, g, 1, st);

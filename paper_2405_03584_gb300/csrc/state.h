@@ -70,6 +70,8 @@ struct Dev {
   // R^T as (hi, lo) float32 pairs, the PCG direction p and the rows-pass result v likewise;
   // the FP64 copies stay for the residuals, the start point and the stiff-row correction
   int df;
+  int mx;                      // the FP64-storage passes split their products between the float64
+                               // pipe (FP64 copies) and double-float (pair copies): mixed.cu
   const float2 *R_df, *RT_df;  // nnzR each
   float2 *p_df, *v_df;         // n, nR
   // runs of R's rows: maximal stretches of consecutive entries whose columns increase by one
@@ -234,6 +236,9 @@ cudaError_t launch_df_split(const Dev& d, int* out_of_range, cudaStream_t st);  
 cudaError_t launch_mirror_df(const Dev& d, const Geo& g, cudaStream_t st);        // p_df from p
 cudaError_t launch_op_rows_df(const Dev& d, const Geo& g, int mode, cudaStream_t st);
 cudaError_t launch_op_cols_df(const Dev& d, const Geo& g, int mode, cudaStream_t st);
+// ---- split-pipe operator passes (mixed.cu) ----
+cudaError_t launch_op_rows_mx(const Dev& d, const Geo& g, int mode, cudaStream_t st);
+cudaError_t launch_op_cols_mx(const Dev& d, const Geo& g, int mode, cudaStream_t st);
 // ---- pieces of the runs of R's rows (df.cu) ----
 cudaError_t launch_runs_count(const Dev& d, int32_t* runs, int32_t* pieces, cudaStream_t st);  // per row
 cudaError_t launch_runs_fill(const Dev& d, cudaStream_t st);                      // pc_col, pc_ol

@@ -24,7 +24,7 @@ STATIC_SCRATCH_ROWS = 262144
 MEM_HOST, MEM_DEVICE = 0, 1
 PRECOND = {"jacobi": 0, "jacobi_lr": 1, "dense": 2, "auto": 3, "block32": 4}
 STORAGE = {"f64": 0, "f32": 1, "bf16": 2, "fp8": 3, "fp8_e4m3": 3}
-ARITH = {"f64": 0, "df32": 1}
+ARITH = {"f64": 0, "df32": 1, "mixed": 2}
 ROWS_FORMAT = {"auto": 0, "csr": 1, "runs": 2}
 COLD, WARM = 0, 1
 

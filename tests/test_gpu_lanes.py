@@ -54,7 +54,7 @@ def _err(a, b):
     return np.abs(a - b).max() / (np.abs(b).max() + 1e-300)
 
 
-VARIANTS = [("f64", "csr"), ("f64", "runs"), ("df32", "csr"), ("df32", "runs"), ("df32", "runs-staged")]
+VARIANTS = [("f64", "csr"), ("f64", "runs"), ("df32", "csr"), ("df32", "runs"), ("df32", "runs-staged"), ("mixed", "csr")]
 
 
 def _fmt(fmt):

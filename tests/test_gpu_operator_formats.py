@@ -13,7 +13,7 @@ from paper_2405_03584_gb300 import ipm, workloads as W
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = [("f64", "runs"), ("df32", "csr"), ("df32", "runs"), ("df32", "runs-staged")]
+VARIANTS = [("f64", "runs"), ("df32", "csr"), ("df32", "runs"), ("df32", "runs-staged"), ("mixed", "csr")]
 
 
 def _fmt(fmt):
