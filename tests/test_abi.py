@@ -58,7 +58,7 @@ def test_null_arguments_rejected(lib):
 
 @pytest.mark.parametrize("field,value", [
     ("precond", 2), ("precond", 4), ("precond", 5), ("system", 1), ("stiff_max", 1025), ("lanes_rows", 12),
-    ("lanes_at", 3), ("op_arith", 2), ("rows_format", 3), ("rows_stage", 2), ("wait_limit_ms", 0.0),
+    ("lanes_at", 3), ("op_arith", 3), ("rows_format", 3), ("rows_stage", 2), ("wait_limit_ms", 0.0),
     ("dense_max_n", 4096),
     ("refine_eta", 1.0), ("warm_rho", 1.0), ("u_cap", 1 << 17), ("storage", 4)])
 def test_invalid_option_combinations_rejected(lib, field, value):
