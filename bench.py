@@ -243,6 +243,8 @@ def _operator_opts(args):
         o["cols_format"] = args.cols_format
     if args.refine_eta is not None:
         o["refine_eta"] = args.refine_eta
+    if args.refine_mode is not None:
+        o["refine_mode"] = args.refine_mode
     return o
 
 
@@ -811,6 +813,8 @@ def main():
                     help="reduced storages: 0 column pass on int32 indices (default), 1 on 16-bit row gaps")
     ap.add_argument("--refine-eta", type=float, default=None,
                     help="reduced storages: inner PCG tolerance of each refinement pass (default 0.1)")
+    ap.add_argument("--refine-mode", type=int, choices=[0, 1], default=None,
+                    help="reduced storages: 0 restarted refinement passes, 1 one PCG with residual replacement")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every kernel directly (for per-kernel profilers; same kernels, slower)")
     args = ap.parse_args()

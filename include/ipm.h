@@ -171,6 +171,11 @@ typedef struct ipm_options {
                          /* slots for wider gaps, columns padded to 8 slots: 2 index bytes an   */
                          /* entry instead of 4, measured slower on the RT workload: the decode  */
                          /* costs more than the bytes it saves)                                 */
+  int refine_mode;       /* reduced storages: 0 (default) refinement passes, each a PCG on the  */
+                         /* current FP64 residual to refine_eta; 1: one PCG per Newton step     */
+                         /* whose recursive residual is replaced by the FP64 residual rhs - K dx */
+                         /* each time it falls by refine_eta (the search direction is kept),    */
+                         /* ending when a replaced residual meets the step's tolerance          */
 } ipm_options;
 
 /* Fills *opt with the defaults listed above. */

@@ -38,6 +38,7 @@ struct LoopCounts {
   int pcg = 0;       // one PCG trip
   int refine = 0;    // refinement body, outside its PCG loop
   int fallback = 0;  // one trip of the FP64 fallback loop
+  int ru = 0;        // reduced precision with residual replacement: one PCG loop per step
 };
 
 struct Graphs {
@@ -356,6 +357,7 @@ int validate_options(const ipm_options& o) {
   if (o.rows_format < IPM_ROWS_AUTO || o.rows_format > IPM_ROWS_RUNS) return IPM_ERR_ARG;
   if (o.rows_stage < 0 || o.rows_stage > 1 || !(o.wait_limit_ms > 0 && o.wait_limit_ms <= 6e4)) return IPM_ERR_ARG;
   if (o.wait_test < 0 || o.wait_test > 1 || o.cols_format < 0 || o.cols_format > 1) return IPM_ERR_ARG;
+  if (o.refine_mode < 0 || o.refine_mode > 1) return IPM_ERR_ARG;
   if (o.system == IPM_SYSTEM_AUGMENTED &&
       (o.storage != IPM_STORAGE_F64 || (o.precond != IPM_PRECOND_JACOBI && o.precond != IPM_PRECOND_AUTO)))
     return IPM_ERR_ARG;   // the doubly augmented system runs FP64 with the Jacobi preconditioner
@@ -764,6 +766,28 @@ cudaError_t emit_step(ipm_handle* h, int pc, bool full, cudaStream_t st, cudaStr
       chk(add_while(st, s2, [&](cudaGraphConditionalHandle ch, cudaStream_t bs) {
             return launch_cg_body(d, g, pc, ch, bs, true, false);
           }, &c->pcg, &hp));
+  } else if (h->opt.refine_mode == 1) {
+    // one reduced-precision PCG with residual replacement, then the FP64 fallback
+    cudaGraphConditionalHandle hp = 0, hf = 0;
+    chk(new_handle(st, &hp));
+    chk(new_handle(st, &hf));
+    chk(launch_ru_start(d, st));
+    chk(launch_set_cond(hp, 1u, st));
+    chk(launch_cg_init(d, g, pc, st));
+    c->ru = 1;
+    if (e == cudaSuccess)
+      chk(add_while(st, s2, [&](cudaGraphConditionalHandle ch, cudaStream_t bs) {
+            return launch_ru_body(d, g, pc, ch, bs, true);
+          }, &c->pcg, &hp));
+    chk(launch_ru_end(d, g, st));
+    chk(launch_refine_fallback(d, g, st));
+    chk(launch_set_cond(hf, 1u, st));
+    chk(launch_cg_init(d, g, pc, st));
+    if (e == cudaSuccess)
+      chk(add_while(st, s2, [&](cudaGraphConditionalHandle ch, cudaStream_t bs) {
+            return launch_cg_body(d, g, pc, ch, bs, true, false);
+          }, &c->fallback, &hf));
+    chk(launch_refine_finish(d, g, st));
   } else {
     cudaGraphConditionalHandle hr = 0, hf = 0;
     chk(new_handle(st, &hr));
@@ -880,6 +904,22 @@ int run_iteration_direct(ipm_handle* h, int pc, int64_t* launches) {
   if (d.storage == ST_F64) {
     CUDA_TRY(h, launch_cg_init(d, g, pc, st));
     if ((rc = pcg(false))) return rc;
+  } else if (h->opt.refine_mode == 1) {
+    CUDA_TRY(h, launch_ru_start(d, st));
+    CUDA_TRY(h, launch_cg_init(d, g, pc, st));
+    int done = 0;
+    for (int k = 0; k < h->opt.max_cg + 1 && !done; ++k) {
+      CUDA_TRY(h, launch_ru_body(d, g, pc, 0, st, false));
+      CUDA_TRY(h, cudaMemcpyAsync(&h->hs->cg_done, &d.sc->cg_done, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(h, cudaStreamSynchronize(st));
+      done = h->hs->cg_done;
+      *launches += lc.pcg;
+    }
+    CUDA_TRY(h, launch_ru_end(d, g, st));
+    CUDA_TRY(h, launch_refine_fallback(d, g, st));
+    CUDA_TRY(h, launch_cg_init(d, g, pc, st));
+    if ((rc = pcg(false))) return rc;
+    CUDA_TRY(h, launch_refine_finish(d, g, st));
   } else {
     CUDA_TRY(h, launch_refine_start(d, g, st));
     for (int it = 0; it < h->opt.refine_max; ++it) {
@@ -992,6 +1032,7 @@ void ipm_default_options(ipm_options* o) {
   o->rows_format = IPM_ROWS_AUTO;
   o->rows_stage = 0;
   o->cols_format = 0;
+  o->refine_mode = 0;
   o->wait_limit_ms = 1000.0;
   o->wait_test = 0;
   o->warm_rho = 1e-5;
@@ -1772,6 +1813,8 @@ static int fill_info(ipm_handle* h, int64_t direct_launches) {
       launches += lc.ipm + 1;  // + the loop re-arm kernel counted in ipm
       if (!lowp) {
         launches += std::max<int64_t>(1, cg) * lc.pcg;
+      } else if (lc.ru) {
+        launches += std::max<int64_t>(1, cg) * lc.pcg + lc.fallback;
       } else {
         launches += (cg + ref) * lc.pcg + ref * lc.refine + lc.fallback;
       }

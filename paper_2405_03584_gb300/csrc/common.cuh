@@ -45,6 +45,10 @@ struct Scal {
   double mu0_cold, warm_rho;
   int refine_it, refine_max, cg_step_total, cg_conv_outer, fallback, fallback_total;
   int cg_fail_run;                   // consecutive Newton steps whose PCG ended unconverged
+  // reduced-precision PCG with residual replacement: the true residual's norm^2 at the last
+  // replacement and the flag asking for the next one
+  double rr_ref;
+  int ru_do;
   // totals of one solve (device-side IPM loop)
   long long cg_total;
   int refine_total, max_cg_step, trace_rows, trace_cap;

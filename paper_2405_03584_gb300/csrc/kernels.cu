@@ -1048,10 +1048,12 @@ cudaError_t launch_rhs(const Dev& d, const Geo& g, int precond, cudaStream_t st)
 
 // ------------------------------------------------------------------------------ PCG
 
-// v = omega o (R p).  MODE 0: inside PCG (skips once converged); MODE 1: single apply.
+// v = omega o (R p).  MODE 0: inside PCG (skips once converged); MODE 1: single apply;
+// MODE 2: single apply when the reduced-precision PCG asks for a residual replacement.
 template <int MODE, int G>
 __global__ void __launch_bounds__(256, 6) k_op_rows(Dev d) {
   if (MODE == 0 && d.sc->cg_done) return;
+  if (MODE == 2 && !d.sc->ru_do) return;
   FOR_GROUP_ROWS(G, ri, ok, d.nR) {
     // rows in windows ordered by length (rperm), so the groups of one warp run equal trips
     const int64_t r = (ok && d.rperm) ? (int64_t)d.rperm[ri] : ri;
@@ -1108,11 +1110,13 @@ cudaError_t launch_op_rows_runs(const Dev& d, const Geo& g, int mode, cudaStream
 }
 
 // q = R^T v + Hs p + (h0 + sigma) o p; p^T q -> alpha = rz / p^T q (last block).
-// MODE 0: inside PCG; MODE 1: a single operator apply (no scalars touched).
+// MODE 0: inside PCG; MODE 1: a single operator apply (no scalars touched); MODE 2: as 1,
+// when the reduced-precision PCG asks for a residual replacement.
 template <int MODE, int G>
 __global__ void __launch_bounds__(256, 6) k_op_cols(Dev d) {
   __shared__ double sh[32];
   if (MODE == 0 && d.sc->cg_done) return;
+  if (MODE == 2 && !d.sc->ru_do) return;
   double pq = 0.0;
   FOR_GROUP_ROWS(G, j, ok, d.n) {
     const int64_t beg = ok ? d.RT_ptr[j] : 0, end = ok ? d.RT_ptr[j + 1] : 0;
@@ -1129,7 +1133,7 @@ __global__ void __launch_bounds__(256, 6) k_op_cols(Dev d) {
       pq = fma(pj, qj, pq);
     }
   }
-  if (MODE == 1) return;
+  if (MODE != 0) return;
   if (d.aug)   // p^T q over the bottom block too (q's bottom written by the rows pass)
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.m; k += (int64_t)gridDim.x * blockDim.x)
       pq = fma(d.p[d.n + k], d.q[d.n + k], pq);
@@ -1434,6 +1438,21 @@ cudaError_t launch_cg_body(const Dev& d, const Geo& g, int precond, cudaGraphCon
 
 // The rows and the column pass of the handle's FP64-storage PCG operator alone (measurement,
 // autotuning); the double-float passes read p_df, which the caller keeps current.
+// The low-rank correction of the preconditioner after z0 = r / M (loop form) and the next
+// search direction (with the loop condition), for the replacement PCG of lowp.cu.
+cudaError_t launch_stiff_apply(const Dev& d, const Geo& g, cudaStream_t st) {
+  const int gs = (d.stiff_cap + 7) / 8;
+  k_stiff_u<<<gs, kBlock, 0, st>>>(d, 0);
+  k_stiff_t<<<gs, kBlock, 0, st>>>(d, 0);
+  k_stiff_corr<<<g.eN, kBlock, 0, st>>>(d, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_p(const Dev& d, const Geo& g, cudaGraphConditionalHandle h, bool in_graph, cudaStream_t st) {
+  k_cg_p<<<g.eN, kBlock, 0, st>>>(d, h, in_graph ? 1 : 0);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_op_rows_only(const Dev& d, const Geo& g, cudaStream_t st) {
   if (d.mx) return launch_op_rows_mx(d, g, 1, st);
   if (d.df) return launch_op_rows_df(d, g, 1, st);
@@ -1466,10 +1485,23 @@ cudaError_t launch_apply(const Dev& d, const Geo& g, cudaStream_t st) {
     launch_op_cols_df(d, g, 1, st);
     return cudaGetLastError();
   }
-  if (d.runs) launch_op_rows_runs(d, g, 1, st);
+  // (a reduced-storage handle keeps runs for its narrow rows pass; its FP64 applies read CSR,
+  // the faster FP64 form)
+  if (d.runs && d.storage == ST_F64) launch_op_rows_runs(d, g, 1, st);
   else if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<1, G><<<g.gRc, kBlock, 0, st>>>(d));
   launch_lr(d, d.p, 0, st);
   DISPATCH_G(d.g_cols, k_op_cols<1, G><<<g.gNc, kBlock, 0, st>>>(d));
+  return cudaGetLastError();
+}
+
+// q = K dx when the reduced-precision PCG asks for a residual replacement (ru_do), else
+// nothing: the FP64 operator over the accumulated step (a copy of the bundle with p -> dx).
+cudaError_t launch_apply_ru(const Dev& d, const Geo& g, cudaStream_t st) {
+  Dev d2 = d;
+  d2.p = d.dx;
+  if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<2, G><<<g.gRc, kBlock, 0, st>>>(d2));
+  if (d.ucols) launch_lr(d2, d2.p, 0, st);
+  DISPATCH_G(d.g_cols, k_op_cols<2, G><<<g.gNc, kBlock, 0, st>>>(d2));
   return cudaGetLastError();
 }
 

@@ -596,6 +596,162 @@ __global__ void k_refine_finish(Dev d) {
   }
 }
 
+// ------------------------------------------------- reduced-precision PCG with replacement
+//
+// One PCG per Newton step on the reduced-precision operator K~ (FP64 vectors), whose
+// recursive residual r is replaced by the true residual rhs - K dx (FP64 operator) whenever it
+// has fallen by refine_eta since the last replacement, when it meets the step's tolerance, or
+// at the iteration limit; the search direction is kept across replacements (a "reliable
+// update" of the residual, Sleijpen and van der Vorst 1996), so the Krylov space built on K~
+// is not thrown away as the restarted refinement does.  The step is done when a replaced
+// (true) residual meets the tolerance; otherwise the FP64 fallback PCG finishes it.
+
+// Start: tolerance of the step, reference norm = ||rhs||^2 (r = rhs, dx = 0 from the rhs pass).
+__global__ void k_ru_start(Dev d) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    Scal* sc = d.sc;
+    sc->tol2_outer = sc->tol2;
+    sc->rr_outer = sc->rhs2;
+    sc->rr_ref = sc->rhs2;
+    sc->refine_it = 0;
+    sc->cg_step_total = 0;
+    sc->cg_conv_outer = sc->cg_done;   // rhs == 0: nothing to solve
+    sc->ru_do = 0;
+  }
+}
+
+// dx += alpha p; r -= alpha q; ||r||^2; a replacement is asked for when ||r|| fell by
+// refine_eta since the last one, met the tolerance, or the iteration limit is reached.
+__global__ void k_ru_update(Dev d) {
+  __shared__ double sh[32];
+  if (d.sc->cg_done) return;
+  const double alpha = d.sc->alpha;
+  double rr = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x) {
+    d.dx[j] = fma(alpha, d.p[j], d.dx[j]);
+    const double rj = fma(-alpha, d.q[j], d.r[j]);
+    d.r[j] = rj;
+    rr = fma(rj, rj, rr);
+  }
+  double v[1] = {rr};
+  const int ops[1] = {0};
+  double out[1];
+  if (grid_reduce<1>(v, ops, d.partials + 17 * kMaxRedBlocks, &d.sc->ticket[T_UPD], out, sh)) {
+    if (threadIdx.x == 0) {
+      Scal* sc = d.sc;
+      sc->cg_iter += 1;
+      sc->rr = out[0];
+      if (!isfinite(out[0])) {
+        sc->cg_done = 1;
+        sc->status = DS_NUMERICAL;
+        sc->ru_do = 0;
+      } else {
+        sc->ru_do = (out[0] <= sc->tol2_outer || out[0] <= sc->refine_eta * sc->refine_eta * sc->rr_ref ||
+                     sc->cg_iter >= sc->cg_max) ? 1 : 0;
+      }
+    }
+  }
+}
+
+// On a replacement (q = K dx from the FP64 operator): r = rhs - q, the new reference norm; the
+// step ends when it meets the tolerance (converged) or at the iteration limit.
+__global__ void k_ru_resid(Dev d) {
+  __shared__ double sh[32];
+  if (!d.sc->ru_do) return;
+  double rr = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x) {
+    const double rj = d.rhs[j] - d.q[j];
+    d.r[j] = rj;
+    rr = fma(rj, rj, rr);
+  }
+  double v[1] = {rr};
+  const int ops[1] = {0};
+  double out[1];
+  if (grid_reduce<1>(v, ops, d.partials + 27 * kMaxRedBlocks, &d.sc->ticket[T_REF], out, sh)) {
+    if (threadIdx.x == 0) {
+      Scal* sc = d.sc;
+      sc->refine_it += 1;
+      sc->rr = out[0];
+      sc->rr_ref = out[0];
+      sc->rr_outer = out[0];
+      if (!isfinite(out[0])) {
+        sc->status = DS_NUMERICAL;
+        sc->cg_done = 1;
+      } else if (out[0] <= sc->tol2_outer) {
+        sc->cg_done = 1;
+        sc->cg_conv = 1;
+        sc->cg_conv_outer = 1;
+      } else if (sc->cg_iter >= sc->cg_max) {
+        sc->cg_done = 1;
+      }
+    }
+  }
+}
+
+// Preconditioned residual after the (possibly replaced) r.  ZM 0 (Jacobi): z = r / M, r^T z,
+// beta.  ZM 1 (Jacobi + low rank): z0 = r / M, the low-rank correction follows.
+template <int ZM>
+__global__ void k_ru_z(Dev d) {
+  __shared__ double sh[32];
+  if (d.sc->cg_done) return;
+  double rz = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x) {
+    const double zj = d.r[j] * d.Minv[j];
+    d.z[j] = zj;
+    rz = fma(d.r[j], zj, rz);
+  }
+  if (ZM == 1) return;
+  double v[1] = {rz};
+  const int ops[1] = {0};
+  double out[1];
+  if (grid_reduce<1>(v, ops, d.partials + 29 * kMaxRedBlocks, &d.sc->ticket[T_CORR], out, sh)) {
+    if (threadIdx.x == 0) {
+      Scal* sc = d.sc;
+      sc->beta = out[0] / sc->rz;
+      sc->rz = out[0];
+    }
+  }
+}
+
+// End: the step so far in dxr (the FP64 fallback adds its correction to it), PCG totals.
+__global__ void k_ru_end(Dev d) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x)
+    d.dxr[j] = d.dx[j];
+  if (blockIdx.x == 0 && threadIdx.x == 0) d.sc->cg_step_total = d.sc->cg_iter;
+}
+
+cudaError_t launch_ru_start(const Dev& d, cudaStream_t st) {
+  k_ru_start<<<1, 32, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_ru(const Dev& d, const Geo& g, cudaStream_t st);   // kernels.cu
+
+// One trip of the replacement PCG: q = K~ p, the update, the FP64 replacement when asked for,
+// the preconditioner, the next direction (k_cg_p sets the loop condition).
+cudaError_t launch_ru_body(const Dev& d, const Geo& g, int precond, cudaGraphConditionalHandle h, cudaStream_t st,
+                           bool in_graph) {
+  cudaError_t e = launch_op_lp(d, g, st);
+  if (e != cudaSuccess) return e;
+  k_ru_update<<<g.eN, kBlock, 0, st>>>(d);
+  e = launch_apply_ru(d, g, st);
+  if (e != cudaSuccess) return e;
+  k_ru_resid<<<g.eN, kBlock, 0, st>>>(d);
+  if (precond == PC_JACOBI_LR) {
+    k_ru_z<1><<<g.eN, kBlock, 0, st>>>(d);
+    e = launch_stiff_apply(d, g, st);
+    if (e != cudaSuccess) return e;
+  } else {
+    k_ru_z<0><<<g.eN, kBlock, 0, st>>>(d);
+  }
+  return launch_cg_p(d, g, h, in_graph, st);
+}
+
+cudaError_t launch_ru_end(const Dev& d, const Geo& g, cudaStream_t st) {
+  k_ru_end<<<g.eN, kBlock, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_refine_start(const Dev& d, const Geo& g, cudaStream_t st) {
   k_refine_start<<<g.eN, kBlock, 0, st>>>(d);
   return cudaGetLastError();

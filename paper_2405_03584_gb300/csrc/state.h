@@ -248,6 +248,13 @@ cudaError_t launch_op_rows_lp_runs(const Dev& d, const Geo& g, int standalone, c
 cudaError_t launch_op_rows_staged(const Dev& d, int mode, cudaStream_t st);
 cudaError_t prepare_staged();   // once per process: shared-memory limit of the staged kernels
 cudaError_t launch_refine_start(const Dev& d, const Geo& g, cudaStream_t st);
+// ---- reduced-precision PCG with residual replacement (lowp.cu) ----
+cudaError_t launch_ru_start(const Dev& d, cudaStream_t st);
+cudaError_t launch_ru_body(const Dev& d, const Geo& g, int precond, cudaGraphConditionalHandle h, cudaStream_t st,
+                           bool in_graph);
+cudaError_t launch_ru_end(const Dev& d, const Geo& g, cudaStream_t st);
+cudaError_t launch_stiff_apply(const Dev& d, const Geo& g, cudaStream_t st);   // kernels.cu
+cudaError_t launch_cg_p(const Dev& d, const Geo& g, cudaGraphConditionalHandle h, bool in_graph, cudaStream_t st);
 cudaError_t launch_refine_inner(const Dev& d, const Geo& g, cudaGraphConditionalHandle hi, cudaStream_t st);
 cudaError_t launch_refine_tail(const Dev& d, const Geo& g, cudaGraphConditionalHandle h, cudaStream_t st);
 cudaError_t launch_refine_fallback(const Dev& d, const Geo& g, cudaStream_t st);

@@ -50,7 +50,7 @@ class Options(C.Structure):
                 ("u_cap", C.c_int), ("ingest_host", C.c_int), ("system", C.c_int),
                 ("lanes_at", C.c_int), ("op_arith", C.c_int), ("rows_format", C.c_int),
                 ("rows_stage", C.c_int), ("wait_limit_ms", C.c_double), ("wait_test", C.c_int),
-                ("cols_format", C.c_int)]
+                ("cols_format", C.c_int), ("refine_mode", C.c_int)]
 
 
 class QP(C.Structure):

@@ -32,13 +32,14 @@ def test_max_iter():
         assert s.solve() == ipm.IPM_OK
 
 
-@pytest.mark.parametrize("storage", ["f64", "bf16"])
-def test_cg_stall(storage):
+@pytest.mark.parametrize("storage,refine_mode", [("f64", 0), ("bf16", 0), ("bf16", 1)])
+def test_cg_stall(storage, refine_mode):
     """One PCG iteration per Newton step against a tolerance of 1e-12: the first direction
     (residual far above 1e-2 of its right-hand side) is tolerated, the second ends the solve
     with IPM_CG_STALL."""
     p = W.rt_qp(n=1200, seed=82)
-    with ipm.Solver(tol_kkt=1e-8, max_cg=1, cg_eta_min=1e-12, cg_eta_max=1e-12, storage=storage, refine_max=1) as s:
+    with ipm.Solver(tol_kkt=1e-8, max_cg=1, cg_eta_min=1e-12, cg_eta_max=1e-12, storage=storage, refine_max=1,
+                    refine_mode=refine_mode) as s:
         s.set_qp_rt(p)
         assert s.solve() == ipm.IPM_CG_STALL
         info = s.get()["info"]

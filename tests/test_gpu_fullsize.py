@@ -78,15 +78,16 @@ def test_mid_size_matches_oracle(mid):
     assert np.abs(out["x"] - ref.x).max() / (1 + np.abs(ref.x).max()) <= 1e-3
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32", "bf16", "fp8"])
-def test_mid_size_error_per_storage(mid, storage):
+@pytest.mark.parametrize("storage,refine_mode", [("f64", 0), ("f32", 0), ("bf16", 0), ("fp8", 0), ("bf16", 1),
+                                                 ("fp8", 1)])
+def test_mid_size_error_per_storage(mid, storage, refine_mode):
     """Each operator storage in the benchmark's option set, against the FP64 oracle: the
     error in x, in the objective and the relative KKT residual of the returned point (the
     precision configuration reports these per dtype).  Bars: rel. KKT <= 1e-6 and relative
     objective error <= 1e-6; the x error is printed (x* is unique, its distance follows the
     KKT residual through the conditioning of the problem)."""
     p, qp, ref = mid
-    with ipm.Solver(**presets.rt(storage)) as s:
+    with ipm.Solver(**presets.rt(storage, refine_mode=refine_mode)) as s:
         s.set_qp_rt(p)
         assert s.solve() == ipm.IPM_OK
         out = s.get()
@@ -95,7 +96,7 @@ def test_mid_size_error_per_storage(mid, storage):
     ex = np.abs(out["x"] - ref.x).max() / np.abs(ref.x).max()
     e2 = np.linalg.norm(out["x"] - ref.x) / np.linalg.norm(ref.x)
     ef = abs(f - f_ref) / abs(f_ref)
-    print("\nstorage-accuracy %s: x_err_inf=%.3e x_err_2=%.3e obj_rel_err=%.3e rel_kkt=%.3e ipm=%d pcg=%d refine=%d"
-          % (storage, ex, e2, ef, rk, out["info"]["ipm_iters"], out["info"]["cg_iters"], out["info"]["refine_passes"]))
+    print("\nstorage-accuracy %s refine_mode %d: x_err_inf=%.3e x_err_2=%.3e obj_rel_err=%.3e rel_kkt=%.3e ipm=%d pcg=%d refine=%d"
+          % (storage, refine_mode, ex, e2, ef, rk, out["info"]["ipm_iters"], out["info"]["cg_iters"], out["info"]["refine_passes"]))
     assert rk <= 1e-6
     assert ef <= 1e-6

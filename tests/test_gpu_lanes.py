@@ -60,10 +60,11 @@ VARIANTS = [("f64", "csr"), ("f64", "runs"), ("df32", "csr"), ("df32", "runs"), 
 def _fmt(fmt):
     """Options of a variant name: the rows format first ("csr", "runs"), then "-staged" (the
     pieces streamed through the shared-memory copy pipeline instead of read from global
-    memory) or "-colsgap" (the reduced-precision column pass on the 16-bit row-gap layout
-    instead of int32 indices)."""
+    memory), "-colsgap" (the reduced-precision column pass on the 16-bit row-gap layout
+    instead of int32 indices) or "-ru" (one PCG with residual replacement per Newton step
+    instead of restarted refinement passes)."""
     return dict(rows_format=fmt.split("-")[0], rows_stage=1 if fmt.endswith("-staged") else 0,
-                cols_format=1 if fmt.endswith("-colsgap") else 0)
+                cols_format=1 if fmt.endswith("-colsgap") else 0, refine_mode=1 if fmt.endswith("-ru") else 0)
 
 
 @pytest.mark.parametrize("arith,fmt", VARIANTS, ids=["%s-%s" % v for v in VARIANTS])
@@ -92,7 +93,7 @@ def test_fp64_kernels_every_width(case, lr, lc, arith, fmt):
         assert _err(d["dzl"], ref_dir.zl) <= 1e-7 and _err(d["dzu"], ref_dir.zu) <= 1e-7
 
 
-@pytest.mark.parametrize("fmt", ["csr", "runs", "runs-staged", "runs-colsgap"])
+@pytest.mark.parametrize("fmt", ["csr", "runs", "runs-staged", "runs-colsgap", "runs-ru"])
 @pytest.mark.parametrize("storage", ["f32", "bf16", "fp8"])
 @pytest.mark.parametrize("lr,lc", PAIRS, ids=["rows%d-cols%d" % pc for pc in PAIRS])
 def test_reduced_precision_kernels_every_width(case, storage, lr, lc, fmt):

@@ -267,22 +267,26 @@ def test_bad_inputs_rejected():
     s.close()
 
 
+@pytest.mark.parametrize("refine_mode", [0, 1])
 @pytest.mark.parametrize("storage", ["f32", "bf16", "fp8"])
-def test_reduced_precision_operator_refined_to_fp64(storage):
+def test_reduced_precision_operator_refined_to_fp64(storage, refine_mode):
     """D and A stored in FP32 / BF16 / FP8-E4M3 with per-row scales, FP32-accumulating PCG,
-    FP64 iterative refinement of each Newton step: the solve must still match the FP64
+    FP64 accuracy of each Newton step by refinement passes (refine_mode 0) or by one PCG
+    whose residual is replaced by the FP64 one (1): the solve must still match the FP64
     oracle at the accuracy bar (rel KKT <= tol, rel objective difference <= 1e-6)."""
     p = W.rt_qp(n=1400, seed=19)
-    st, out, ref, qp = _solve_both(p, 1e-7, precond="jacobi_lr", storage=storage, max_cg=5000)
+    st, out, ref, qp = _solve_both(p, 1e-7, precond="jacobi_lr", storage=storage, max_cg=5000,
+                                   refine_mode=refine_mode)
     _check_solution(p, qp, st, out, ref, 1e-7)
     assert out["info"]["refine_passes"] >= out["info"]["ipm_iters"]
 
 
+@pytest.mark.parametrize("refine_mode", [0, 1])
 @pytest.mark.parametrize("storage", ["bf16", "fp8"])
-def test_reduced_precision_direction(storage):
+def test_reduced_precision_direction(storage, refine_mode):
     """One refined Newton direction at a random iterate against the oracle's exact one."""
     p = W.rt_qp(n=900, seed=21)
-    s, qp = _load(p, precond="jacobi_lr", storage=storage, max_cg=5000, refine_max=30)
+    s, qp = _load(p, precond="jacobi_lr", storage=storage, max_cg=5000, refine_max=30, refine_mode=refine_mode)
     it = _iterate(p, qp, 13, spread=1.0)
     s.set_iterate(it.x, it.s, it.y, it.zl, it.zu, 0.05)
     d = s.newton_direction(eta=1e-10)
