@@ -138,8 +138,9 @@ typedef struct ipm_options {
                          /* launched one by one from host loops (for per-kernel profilers)     */
   int storage;           /* enum ipm_storage (default IPM_STORAGE_F64)                          */
   int refine_max;        /* reduced precision: at most this many refinement passes per step (8) */
-  double refine_eta;     /* reduced precision: inner PCG tolerance relative to the current      */
-                         /* FP64 residual (0.1)                                                */
+  double refine_eta;     /* reduced precision: the factor by which the residual falls between  */
+                         /* two FP64 residual evaluations (0.01): refine_mode 1 replaces the   */
+                         /* PCG residual then, refine_mode 0 ends a refinement pass there      */
   int lanes_rows;        /* lanes per row of the kernels over R (4, 8, 16, 32; 0 = automatic)   */
   int lanes_cols;        /* lanes per row of the kernels over R^T (same; overrides autotune)    */
   double warm_rho;       /* IPM_WARM: complementarity pairs raised to >= warm_rho * mu0 of the  */
@@ -171,11 +172,11 @@ typedef struct ipm_options {
                          /* slots for wider gaps, columns padded to 8 slots: 2 index bytes an   */
                          /* entry instead of 4, measured slower on the RT workload: the decode  */
                          /* costs more than the bytes it saves)                                 */
-  int refine_mode;       /* reduced storages: 0 (default) refinement passes, each a PCG on the  */
-                         /* current FP64 residual to refine_eta; 1: one PCG per Newton step     */
-                         /* whose recursive residual is replaced by the FP64 residual rhs - K dx */
-                         /* each time it falls by refine_eta (the search direction is kept),    */
-                         /* ending when a replaced residual meets the step's tolerance          */
+  int refine_mode;       /* reduced storages: 1 (default) one PCG per Newton step whose         */
+                         /* recursive residual is replaced by the FP64 residual rhs - K dx each */
+                         /* time it falls by refine_eta (the search direction is kept), ending  */
+                         /* when a replaced residual meets the step's tolerance; 0: refinement  */
+                         /* passes, each a PCG restarted on the current FP64 residual           */
 } ipm_options;
 
 /* Fills *opt with the defaults listed above. */

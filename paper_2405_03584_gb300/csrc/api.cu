@@ -1024,7 +1024,7 @@ void ipm_default_options(ipm_options* o) {
   o->use_graphs = 1;
   o->storage = IPM_STORAGE_F64;
   o->refine_max = 8;
-  o->refine_eta = 0.1;
+  o->refine_eta = 0.01;
   o->lanes_rows = 0;
   o->lanes_cols = 0;
   o->lanes_at = 0;
@@ -1032,7 +1032,7 @@ void ipm_default_options(ipm_options* o) {
   o->rows_format = IPM_ROWS_AUTO;
   o->rows_stage = 0;
   o->cols_format = 0;
-  o->refine_mode = 0;
+  o->refine_mode = 1;
   o->wait_limit_ms = 1000.0;
   o->wait_test = 0;
   o->warm_rho = 1e-5;
