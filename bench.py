@@ -812,9 +812,10 @@ def main():
     ap.add_argument("--cols-format", type=int, choices=[0, 1], default=None,
                     help="reduced storages: 0 column pass on int32 indices (default), 1 on 16-bit row gaps")
     ap.add_argument("--refine-eta", type=float, default=None,
-                    help="reduced storages: inner PCG tolerance of each refinement pass (default 0.1)")
-    ap.add_argument("--refine-mode", type=int, choices=[0, 1], default=None,
-                    help="reduced storages: 0 restarted refinement passes, 1 one PCG with residual replacement")
+                    help="reduced storages: factor between FP64 residual evaluations (default: automatic)")
+    ap.add_argument("--refine-mode", type=int, choices=[0, 1, 2], default=None,
+                    help="reduced storages: 0 restarted refinement passes, 1 one PCG with residual replacement, "
+                         "2 automatic (the default)")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every kernel directly (for per-kernel profilers; same kernels, slower)")
     args = ap.parse_args()

@@ -139,8 +139,9 @@ typedef struct ipm_options {
   int storage;           /* enum ipm_storage (default IPM_STORAGE_F64)                          */
   int refine_max;        /* reduced precision: at most this many refinement passes per step (8) */
   double refine_eta;     /* reduced precision: the factor by which the residual falls between  */
-                         /* two FP64 residual evaluations (0.01): refine_mode 1 replaces the   */
-                         /* PCG residual then, refine_mode 0 ends a refinement pass there      */
+                         /* two FP64 residual evaluations: refine_mode 1 replaces the PCG      */
+                         /* residual then, refine_mode 0 ends a refinement pass there; 0      */
+                         /* (default) = 0.01 with replacement, 0.1 with passes                 */
   int lanes_rows;        /* lanes per row of the kernels over R (4, 8, 16, 32; 0 = automatic)   */
   int lanes_cols;        /* lanes per row of the kernels over R^T (same; overrides autotune)    */
   double warm_rho;       /* IPM_WARM: complementarity pairs raised to >= warm_rho * mu0 of the  */
@@ -172,11 +173,13 @@ typedef struct ipm_options {
                          /* slots for wider gaps, columns padded to 8 slots: 2 index bytes an   */
                          /* entry instead of 4, measured slower on the RT workload: the decode  */
                          /* costs more than the bytes it saves)                                 */
-  int refine_mode;       /* reduced storages: 1 (default) one PCG per Newton step whose         */
-                         /* recursive residual is replaced by the FP64 residual rhs - K dx each */
-                         /* time it falls by refine_eta (the search direction is kept), ending  */
-                         /* when a replaced residual meets the step's tolerance; 0: refinement  */
-                         /* passes, each a PCG restarted on the current FP64 residual           */
+  int refine_mode;       /* reduced storages: 1 one PCG per Newton step whose recursive         */
+                         /* residual is replaced by the FP64 residual rhs - K dx each time it   */
+                         /* falls by refine_eta (the search direction is kept), ending when a   */
+                         /* replaced residual meets the step's tolerance; 0 refinement passes,  */
+                         /* each a PCG restarted on the current FP64 residual; 2 (default) = 1  */
+                         /* for F32 and BF16, 0 for FP8 (whose coarse values make the kept      */
+                         /* direction drift: 688 against 240 PCG iterations on an RT QP)        */
 } ipm_options;
 
 /* Fills *opt with the defaults listed above. */

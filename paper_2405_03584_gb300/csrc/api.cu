@@ -349,7 +349,7 @@ int validate_options(const ipm_options& o) {
   if (!(o.cg_eta_min > 0) || !(o.cg_eta_max >= o.cg_eta_min) || !(o.cg_eta_factor > 0)) return IPM_ERR_ARG;
   if (o.precond < 0 || o.precond > 4 || o.stiff_max < 0 || o.stiff_max > 1024) return IPM_ERR_ARG;
   if (o.dense_max_n < 0 || o.dense_max_n > 2048 || !(o.stiff_gamma > 0)) return IPM_ERR_ARG;
-  if (o.storage < 0 || o.storage > 3 || o.refine_max < 1 || !(o.refine_eta > 0 && o.refine_eta < 1)) return IPM_ERR_ARG;
+  if (o.storage < 0 || o.storage > 3 || o.refine_max < 1 || !(o.refine_eta >= 0 && o.refine_eta < 1)) return IPM_ERR_ARG;
   if (!(o.warm_rho >= 0 && o.warm_rho < 1)) return IPM_ERR_ARG;
   if (o.u_cap < 0 || o.u_cap > (1 << 16)) return IPM_ERR_ARG;
   if (o.system != IPM_SYSTEM_CONDENSED && o.system != IPM_SYSTEM_AUGMENTED) return IPM_ERR_ARG;
@@ -357,7 +357,7 @@ int validate_options(const ipm_options& o) {
   if (o.rows_format < IPM_ROWS_AUTO || o.rows_format > IPM_ROWS_RUNS) return IPM_ERR_ARG;
   if (o.rows_stage < 0 || o.rows_stage > 1 || !(o.wait_limit_ms > 0 && o.wait_limit_ms <= 6e4)) return IPM_ERR_ARG;
   if (o.wait_test < 0 || o.wait_test > 1 || o.cols_format < 0 || o.cols_format > 1) return IPM_ERR_ARG;
-  if (o.refine_mode < 0 || o.refine_mode > 1) return IPM_ERR_ARG;
+  if (o.refine_mode < 0 || o.refine_mode > 2) return IPM_ERR_ARG;
   if (o.system == IPM_SYSTEM_AUGMENTED &&
       (o.storage != IPM_STORAGE_F64 || (o.precond != IPM_PRECOND_JACOBI && o.precond != IPM_PRECOND_AUTO)))
     return IPM_ERR_ARG;   // the doubly augmented system runs FP64 with the Jacobi preconditioner
@@ -739,6 +739,20 @@ cudaError_t add_while(cudaStream_t st, cudaStream_t body_st, Fill fill, int* bod
   return cudaSuccess;
 }
 
+// Reduced storage: whether a Newton step runs one PCG with residual replacement (refine_mode 1,
+// or 2 = automatic: replacement for F32 and BF16; FP8's coarse values let the kept direction
+// drift, so it takes restarted passes) and the factor between FP64 residual evaluations
+// (refine_eta, 0 = automatic: 0.01 with replacement, 0.1 with passes).
+bool refine_replaces(const ipm_handle* h) {
+  const int m = h->opt.refine_mode;
+  return m == 1 || (m == 2 && h->opt.storage != IPM_STORAGE_FP8_E4M3);
+}
+
+double refine_factor(const ipm_handle* h) {
+  if (h->opt.refine_eta > 0) return h->opt.refine_eta;
+  return refine_replaces(h) ? 0.01 : 0.1;
+}
+
 // Emits (into the capture running on `st`) one Newton step -- diagonal update, preconditioner,
 // right-hand side, PCG (nested while loops; with a reduced-precision store the PCG loop sits in
 // an FP64 refinement loop followed by an FP64 fallback loop) and direction recovery -- and,
@@ -766,7 +780,7 @@ cudaError_t emit_step(ipm_handle* h, int pc, bool full, cudaStream_t st, cudaStr
       chk(add_while(st, s2, [&](cudaGraphConditionalHandle ch, cudaStream_t bs) {
             return launch_cg_body(d, g, pc, ch, bs, true, false);
           }, &c->pcg, &hp));
-  } else if (h->opt.refine_mode == 1) {
+  } else if (refine_replaces(h)) {
     // one reduced-precision PCG with residual replacement, then the FP64 fallback
     cudaGraphConditionalHandle hp = 0, hf = 0;
     chk(new_handle(st, &hp));
@@ -904,7 +918,7 @@ int run_iteration_direct(ipm_handle* h, int pc, int64_t* launches) {
   if (d.storage == ST_F64) {
     CUDA_TRY(h, launch_cg_init(d, g, pc, st));
     if ((rc = pcg(false))) return rc;
-  } else if (h->opt.refine_mode == 1) {
+  } else if (refine_replaces(h)) {
     CUDA_TRY(h, launch_ru_start(d, st));
     CUDA_TRY(h, launch_cg_init(d, g, pc, st));
     int done = 0;
@@ -970,7 +984,7 @@ int push_options(ipm_handle* h) {
   s.stiff_max = std::min(h->opt.stiff_max, h->d.stiff_cap);
   s.equal_steps = h->opt.equal_steps;
   s.refine_max = h->opt.refine_max;
-  s.refine_eta = h->opt.refine_eta;
+  s.refine_eta = refine_factor(h);
   s.warm_rho = h->opt.warm_rho;
   s.cnorm = h->cnorm;
   s.bnorm = h->bnorm;
@@ -1024,7 +1038,7 @@ void ipm_default_options(ipm_options* o) {
   o->use_graphs = 1;
   o->storage = IPM_STORAGE_F64;
   o->refine_max = 8;
-  o->refine_eta = 0.01;
+  o->refine_eta = 0.0;
   o->lanes_rows = 0;
   o->lanes_cols = 0;
   o->lanes_at = 0;
@@ -1032,7 +1046,7 @@ void ipm_default_options(ipm_options* o) {
   o->rows_format = IPM_ROWS_AUTO;
   o->rows_stage = 0;
   o->cols_format = 0;
-  o->refine_mode = 1;
+  o->refine_mode = 2;
   o->wait_limit_ms = 1000.0;
   o->wait_test = 0;
   o->warm_rho = 1e-5;

@@ -48,7 +48,7 @@ struct Scal {
   // reduced-precision PCG with residual replacement: the true residual's norm^2 at the last
   // replacement and the flag asking for the next one
   double rr_ref;
-  int ru_do;
+  int ru_do, ru_restart;
   // totals of one solve (device-side IPM loop)
   long long cg_total;
   int refine_total, max_cg_step, trace_rows, trace_cap;

@@ -617,6 +617,7 @@ __global__ void k_ru_start(Dev d) {
     sc->cg_step_total = 0;
     sc->cg_conv_outer = sc->cg_done;   // rhs == 0: nothing to solve
     sc->ru_do = 0;
+    sc->ru_restart = 0;
   }
 }
 
@@ -672,6 +673,10 @@ __global__ void k_ru_resid(Dev d) {
       Scal* sc = d.sc;
       sc->refine_it += 1;
       sc->rr = out[0];
+      // no progress since the last replacement (the true residual fell by less than a tenth:
+      // the kept direction has lost conjugacy to the coarse operator's drift): restart the
+      // Krylov process from this residual
+      sc->ru_restart = out[0] > 0.81 * sc->rr_outer ? 1 : 0;
       sc->rr_ref = out[0];
       sc->rr_outer = out[0];
       if (!isfinite(out[0])) {
@@ -713,6 +718,15 @@ __global__ void k_ru_z(Dev d) {
   }
 }
 
+// After a replacement that made no progress: p = z (beta = 0), a fresh Krylov start.
+__global__ void k_ru_restart(Dev d) {
+  Scal* sc = d.sc;
+  if (sc->ru_restart) {
+    sc->beta = 0.0;
+    sc->ru_restart = 0;
+  }
+}
+
 // End: the step so far in dxr (the FP64 fallback adds its correction to it), PCG totals.
 __global__ void k_ru_end(Dev d) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n; j += (int64_t)gridDim.x * blockDim.x)
@@ -744,6 +758,7 @@ cudaError_t launch_ru_body(const Dev& d, const Geo& g, int precond, cudaGraphCon
   } else {
     k_ru_z<0><<<g.eN, kBlock, 0, st>>>(d);
   }
+  k_ru_restart<<<1, 1, 0, st>>>(d);
   return launch_cg_p(d, g, h, in_graph, st);
 }
 

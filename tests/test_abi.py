@@ -60,7 +60,7 @@ def test_null_arguments_rejected(lib):
     ("precond", 2), ("precond", 4), ("precond", 5), ("system", 1), ("stiff_max", 1025), ("lanes_rows", 12),
     ("lanes_at", 3), ("op_arith", 3), ("rows_format", 3), ("rows_stage", 2), ("wait_limit_ms", 0.0),
     ("dense_max_n", 4096),
-    ("refine_eta", 1.0), ("warm_rho", 1.0), ("u_cap", 1 << 17), ("storage", 4)])
+    ("refine_eta", 1.0), ("refine_eta", -0.1), ("refine_mode", 3), ("warm_rho", 1.0), ("u_cap", 1 << 17), ("storage", 4)])
 def test_invalid_option_combinations_rejected(lib, field, value):
     """ipm_create validates the options before touching the device: with BF16 storage the
     DENSE preconditioner and the doubly augmented system are refused, and so are values
