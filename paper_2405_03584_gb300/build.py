@@ -3,6 +3,9 @@
 Each ``csrc/*.cu`` translation unit is compiled in parallel (one ``-gencode`` for sm_103a),
 then linked with the CUDA runtime linked statically, so the library carries no dependency
 beyond the driver.  Rebuilds only when a source or header is newer than the library.
+``IPM_NVCC_FLAGS`` (space-separated) adds compile flags, e.g. ``-DIPM_OP_ROWS_MINB=8`` for the
+resident blocks per SM the float64 operator rows pass is compiled for; pass ``force=True``
+when changing it.
 """
 from __future__ import annotations
 
@@ -53,7 +56,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *os.environ.get("IPM_NVCC_FLAGS", "").split(), "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s%s" % (src, r.stdout, r.stderr))

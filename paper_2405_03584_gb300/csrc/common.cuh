@@ -18,6 +18,15 @@ namespace ipmk {
 
 constexpr int kWarp = 32;
 constexpr int kBlock = 256;          // threads per block of the streaming kernels
+#ifndef IPM_OP_ROWS_MINB
+#define IPM_OP_ROWS_MINB 6
+#endif
+#ifndef IPM_OP_COLS_MINB
+#define IPM_OP_COLS_MINB 6
+#endif
+// resident blocks per SM the float64 operator passes are compiled for (one wave of blocks)
+constexpr int kOpRowsMinBlocks = IPM_OP_ROWS_MINB;
+constexpr int kOpColsMinBlocks = IPM_OP_COLS_MINB;
 constexpr int kMaxRedBlocks = 2048;  // upper bound of blocks that write reduction partials
 constexpr int kHistBins = 64;        // stiff-row ratio histogram bins (two per octave)
 

@@ -61,6 +61,8 @@ Geo make_geo(const Dev& d) {
   // the PCG column kernels are limited to 40 registers (6 blocks per SM): one full wave
   g.gNc = (int)std::min<int64_t>(g.gN, 6 * (int64_t)(d.sm_count > 0 ? d.sm_count : 148));
   g.gRc = (int)std::min<int64_t>(g.gR, 6 * (int64_t)(d.sm_count > 0 ? d.sm_count : 148));
+  g.gR64 = (int)std::min<int64_t>(g.gR, kOpRowsMinBlocks * (int64_t)(d.sm_count > 0 ? d.sm_count : 148));
+  g.gN64 = (int)std::min<int64_t>(g.gN, kOpColsMinBlocks * (int64_t)(d.sm_count > 0 ? d.sm_count : 148));
   // the residual and right-hand-side column kernels are limited to 64 registers (4 per SM)
   g.gNr = (int)std::min<int64_t>(g.gN, 4 * (int64_t)(d.sm_count > 0 ? d.sm_count : 148));
   return g;
@@ -1051,7 +1053,7 @@ cudaError_t launch_rhs(const Dev& d, const Geo& g, int precond, cudaStream_t st)
 // v = omega o (R p).  MODE 0: inside PCG (skips once converged); MODE 1: single apply;
 // MODE 2: single apply when the reduced-precision PCG asks for a residual replacement.
 template <int MODE, int G>
-__global__ void __launch_bounds__(256, 6) k_op_rows(Dev d) {
+__global__ void __launch_bounds__(256, kOpRowsMinBlocks) k_op_rows(Dev d) {
   if (MODE == 0 && d.sc->cg_done) return;
   if (MODE == 2 && !d.sc->ru_do) return;
   FOR_GROUP_ROWS(G, ri, ok, d.nR) {
@@ -1113,7 +1115,7 @@ cudaError_t launch_op_rows_runs(const Dev& d, const Geo& g, int mode, cudaStream
 // MODE 0: inside PCG; MODE 1: a single operator apply (no scalars touched); MODE 2: as 1,
 // when the reduced-precision PCG asks for a residual replacement.
 template <int MODE, int G>
-__global__ void __launch_bounds__(256, 6) k_op_cols(Dev d) {
+__global__ void __launch_bounds__(256, kOpColsMinBlocks) k_op_cols(Dev d) {
   __shared__ double sh[32];
   if (MODE == 0 && d.sc->cg_done) return;
   if (MODE == 2 && !d.sc->ru_do) return;
@@ -1413,9 +1415,9 @@ cudaError_t launch_cg_body(const Dev& d, const Geo& g, int precond, cudaGraphCon
     launch_op_cols_df(d, g, 0, st);
   } else {
     if (d.runs) launch_op_rows_runs(d, g, 0, st);
-    else if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<0, G><<<g.gRc, kBlock, 0, st>>>(d));
+    else if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<0, G><<<g.gR64, kBlock, 0, st>>>(d));
     launch_lr(d, d.p, 0, st);
-    DISPATCH_G(d.g_cols, k_op_cols<0, G><<<g.gNc, kBlock, 0, st>>>(d));
+    DISPATCH_G(d.g_cols, k_op_cols<0, G><<<g.gN64, kBlock, 0, st>>>(d));
   }
   if (precond == PC_BLOCK32) {
     k_cg_update<2><<<g.eN, kBlock, 0, st>>>(d);
@@ -1457,7 +1459,7 @@ cudaError_t launch_op_rows_only(const Dev& d, const Geo& g, cudaStream_t st) {
   if (d.mx) return launch_op_rows_mx(d, g, 1, st);
   if (d.df) return launch_op_rows_df(d, g, 1, st);
   if (d.runs) return launch_op_rows_runs(d, g, 1, st);
-  if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<1, G><<<g.gRc, kBlock, 0, st>>>(d));
+  if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<1, G><<<g.gR64, kBlock, 0, st>>>(d));
   return cudaGetLastError();
 }
 
@@ -1465,7 +1467,7 @@ cudaError_t launch_op_cols_only(const Dev& d, const Geo& g, cudaStream_t st) {
   // (the low-rank term uses us from the last launch_lr; the measurement does not re-run it)
   if (d.mx) return launch_op_cols_mx(d, g, 1, st);
   if (d.df) return launch_op_cols_df(d, g, 1, st);
-  DISPATCH_G(d.g_cols, k_op_cols<1, G><<<g.gNc, kBlock, 0, st>>>(d));
+  DISPATCH_G(d.g_cols, k_op_cols<1, G><<<g.gN64, kBlock, 0, st>>>(d));
   return cudaGetLastError();
 }
 
@@ -1488,9 +1490,9 @@ cudaError_t launch_apply(const Dev& d, const Geo& g, cudaStream_t st) {
   // (a reduced-storage handle keeps runs for its narrow rows pass; its FP64 applies read CSR,
   // the faster FP64 form)
   if (d.runs && d.storage == ST_F64) launch_op_rows_runs(d, g, 1, st);
-  else if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<1, G><<<g.gRc, kBlock, 0, st>>>(d));
+  else if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<1, G><<<g.gR64, kBlock, 0, st>>>(d));
   launch_lr(d, d.p, 0, st);
-  DISPATCH_G(d.g_cols, k_op_cols<1, G><<<g.gNc, kBlock, 0, st>>>(d));
+  DISPATCH_G(d.g_cols, k_op_cols<1, G><<<g.gN64, kBlock, 0, st>>>(d));
   return cudaGetLastError();
 }
 
@@ -1499,9 +1501,9 @@ cudaError_t launch_apply(const Dev& d, const Geo& g, cudaStream_t st) {
 cudaError_t launch_apply_ru(const Dev& d, const Geo& g, cudaStream_t st) {
   Dev d2 = d;
   d2.p = d.dx;
-  if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<2, G><<<g.gRc, kBlock, 0, st>>>(d2));
+  if (d.nR) DISPATCH_G(d.g_rows, k_op_rows<2, G><<<g.gR64, kBlock, 0, st>>>(d2));
   if (d.ucols) launch_lr(d2, d2.p, 0, st);
-  DISPATCH_G(d.g_cols, k_op_cols<2, G><<<g.gNc, kBlock, 0, st>>>(d2));
+  DISPATCH_G(d.g_cols, k_op_cols<2, G><<<g.gN64, kBlock, 0, st>>>(d2));
   return cudaGetLastError();
 }
 

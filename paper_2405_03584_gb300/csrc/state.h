@@ -191,6 +191,7 @@ struct Geo {
   int gR, gM, gN;              // blocks of the row-group kernels over R rows, constraint rows, R^T rows
   int gNc;                     // blocks of the PCG column kernels (6 resident per SM: one wave)
   int gRc;                     // blocks of the PCG row kernel (6 resident per SM: one wave)
+  int gR64, gN64;              // blocks of the float64 operator passes (one wave at their occupancy)
   int gNr;                     // blocks of the residual and right-hand-side column kernels (4 per SM)
   int eM, eN;                  // blocks of the one-thread-per-element kernels over m and n
 };
