@@ -280,6 +280,7 @@ void carve_state(Carver& cv, Dev& d, int64_t n, int64_t m, int64_t nR, int stiff
   // copy stays below 256 MB (else it scans R's rows)
   d.Rd = (dense && nR * n <= (int64_t)(32 << 20)) ? cv.take<double>(nR * n) : nullptr;
   d.chol_diag = cv.take<double>(std::max<int64_t>(dense ? n : 0, stiff_cap));
+  d.chol_rinv = cv.take<double>(std::max<int64_t>(dense ? n : 0, stiff_cap));
   d.storage = storage;
   if (df) {
     d.p_df = cv.take<float2>(n);

@@ -2,7 +2,8 @@
 //   * k_gram_tiles / k_gram_diag_hs : K = Hs + R^T diag(omega) R + U W U^T + diag(h0 + sigma) as a
 //                  dense n x n matrix
 //                  (the DENSE preconditioner: one diagonal block covering all variables);
-//   * k_chol_*   : in-place blocked Cholesky factor (lower) with pivot flooring;
+//   * k_chol_*   : in-place blocked Cholesky factor (lower) with pivot flooring, and the
+//                  reciprocal pivots;
 //   * k_mirror   : copies L into the upper triangle so both triangular sweeps read rows;
 //   * k_inv      : explicit inverse from the factor, columns spread over blocks.
 // The low-rank correction's G (up to 1024 rows) is inverted explicitly, so each of the many
@@ -18,13 +19,21 @@ namespace ipmk {
 
 
 // Blocked right-looking Cholesky (lower, row-major, leading dimension ld) of the leading
-// nn x nn block of A, on 32 x 32 tiles spread over many blocks:
-//   for each tile column kb:  factor the diagonal tile (one block), solve the tiles below it
-//   (one block per tile), update the trailing lower triangle (one block per tile pair).
-// nn is read on the device (it may be the number of stiff rows).  A pivot below
-// floor_rel * (original diagonal) is raised to that floor (a modified factor; still symmetric
-// positive definite, which is all a preconditioner needs); the count goes to *nfloor.
+// nn x nn block of A on 32 x 32 tiles, two launches per tile column kb:
+//   * the panel: every block factors the diagonal tile in shared memory (the same code on the
+//     same data, so each gets the same factor; block 0 writes it back), then the others each
+//     solve 8 rows of the tiles below, X = A_ib,kb L_kb,kb^{-T}, one warp per row;
+//   * the trailing update A_ib,jb -= L_ib,kb L_jb,kb^T (kb < jb <= ib) on 16 x 16 quarter tiles.
+// GB300's float64 pipe issues two fused multiply-adds per SM per clock, so a 32-step chain
+// of float64 operations on one warp costs tens of microseconds: each pivot takes one rsqrt
+// and the rest multiplies by it (no division on the chain), and the arithmetic of a tile
+// column is spread over as many SMs as it has row blocks.  The reciprocal pivots go to
+// rinv[] for the triangular solves.  nn is read on the device (it may be the number of stiff
+// rows).  A pivot below floor_rel * (original diagonal) is raised to that floor (a modified
+// factor; still symmetric positive definite, which is all a preconditioner needs); the count
+// goes to *nfloor.
 constexpr int kT = 32;
+constexpr int kPanelRows = 8;   // rows of the panel below the diagonal tile per block
 
 __device__ __forceinline__ int dev_nn(const int* nn_dev, int nn_fixed) { return nn_dev ? *nn_dev : nn_fixed; }
 
@@ -34,13 +43,11 @@ __global__ void k_chol_save_diag(const double* A, int64_t ld, const int* nn_dev,
   if (blockIdx.x == 0 && threadIdx.x == 0 && nfloor) *nfloor = 0;
 }
 
-// Diagonal tile kb: unblocked Cholesky in shared memory (rows/cols >= nn padded by identity).
-__global__ void k_chol_potrf(double* A, int64_t ld, const int* nn_dev, int nn_fixed, int kb, const double* diag0,
-                             double floor_rel, int* nfloor) {
-  const int nn = dev_nn(nn_dev, nn_fixed);
-  const int base = kb * kT;
-  if (base >= nn) return;
-  __shared__ double t[kT][kT + 1];
+// Unblocked Cholesky of diagonal tile kb in shared memory by 256 threads (rows/cols >= nn
+// padded by identity): rs[k] = 1 / L_kk.  Pivots are floored as above; nfloor (may be null)
+// counts the floored ones.
+__device__ void tile_potrf(double (*t)[kT + 1], double* rs, const double* A, int64_t ld, int nn, int base,
+                           const double* diag0, double floor_rel, int* nfloor) {
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
   for (int r = ty; r < kT; r += 8) {
     const int gi = base + r, gj = base + tx;
@@ -48,107 +55,117 @@ __global__ void k_chol_potrf(double* A, int64_t ld, const int* nn_dev, int nn_fi
   }
   __syncthreads();
   for (int k = 0; k < kT; ++k) {
-    if (threadIdx.x == 0) {
-      double akk = t[k][k];
+    if (ty == 0) {   // column k by warp 0
+      double piv = t[k][k];
+      __syncwarp();
       if (base + k < nn) {
         const double fl = floor_rel * fabs(diag0[base + k]) + 1e-300;
-        if (!(akk > fl)) { akk = fl; atomicAdd(nfloor, 1); }
+        if (!(piv > fl)) {
+          piv = fl;
+          if (nfloor && tx == 0) atomicAdd(nfloor, 1);
+        }
       }
-      t[k][k] = sqrt(akk);
+      const double r = rsqrt(piv);
+      if (tx == k) {
+        t[k][k] = piv * r;
+        rs[k] = r;
+      } else if (tx > k) {
+        t[tx][k] *= r;
+      }
     }
     __syncthreads();
-    const double lkk = t[k][k];
-    if (threadIdx.x > k && threadIdx.x < kT) t[threadIdx.x][k] /= lkk;
+    for (int i = k + 1 + ty; i < kT; i += 8)
+      if (tx > k && tx <= i) t[i][tx] = fma(-t[i][k], t[tx][k], t[i][tx]);
     __syncthreads();
-    for (int r = k + 1 + ty; r < kT; r += 8)
-      if (tx > k && tx <= r) t[r][tx] = fma(-t[r][k], t[tx][k], t[r][tx]);
-    __syncthreads();
-  }
-  for (int r = ty; r < kT; r += 8) {
-    const int gi = base + r, gj = base + tx;
-    if (gi < nn && gj < nn && tx <= r) A[(int64_t)gi * ld + gj] = t[r][tx];
   }
 }
 
-// Tiles (ib, kb), ib > kb: X = A_ib,kb L_kb,kb^{-T} (one block per tile, one thread per row).
-__global__ void k_chol_trsm(double* A, int64_t ld, const int* nn_dev, int nn_fixed, int kb) {
+// Panel of tile column kb: block 0 the diagonal tile, block b >= 1 rows
+// [base + 32 + 8 (b - 1), + 8) below it.
+__global__ void __launch_bounds__(256) k_chol_panel(double* A, int64_t ld, const int* nn_dev, int nn_fixed, int kb,
+                                                    const double* diag0, double floor_rel, int* nfloor, double* rinv) {
   const int nn = dev_nn(nn_dev, nn_fixed);
-  const int nt = (nn + kT - 1) / kT;
-  const int ib = kb + 1 + blockIdx.x;
-  if (ib >= nt) return;
-  __shared__ double L[kT][kT + 1];
-  __shared__ double X[kT][kT + 1];
+  const int base = kb * kT;
+  if (base >= nn) return;
+  const int64_t row0 = base + kT + (int64_t)(blockIdx.x - 1) * kPanelRows;
+  if (blockIdx.x > 0 && row0 >= nn) return;   // whole block: before any barrier
+  __shared__ double t[kT][kT + 1];
+  __shared__ double rs[kT];
+  tile_potrf(t, rs, A, ld, nn, base, diag0, floor_rel, blockIdx.x == 0 ? nfloor : nullptr);
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int kbase = kb * kT, ibase = ib * kT;
-  for (int r = ty; r < kT; r += 8) {
-    const int gk = kbase + r, gc = kbase + tx;
-    L[r][tx] = (gk < nn && gc < nn) ? (tx <= r ? A[(int64_t)gk * ld + gc] : 0.0) : (r == tx ? 1.0 : 0.0);
-    const int gi = ibase + r;
-    X[r][tx] = (gi < nn && gc < nn) ? A[(int64_t)gi * ld + gc] : 0.0;
-  }
-  __syncthreads();
-  if (threadIdx.x < kT) {
-    const int r = threadIdx.x;
-    for (int j = 0; j < kT; ++j) {
-      double v = X[r][j];
-      for (int c = 0; c < j; ++c) v = fma(-X[r][c], L[j][c], v);
-      X[r][j] = v / L[j][j];
+  if (blockIdx.x == 0) {
+    for (int r = ty; r < kT; r += 8) {
+      const int gi = base + r, gj = base + tx;
+      if (gi < nn && gj < nn && tx <= r) A[(int64_t)gi * ld + gj] = t[r][tx];
     }
+    if (ty == 0 && base + tx < nn) rinv[base + tx] = rs[tx];
+    return;
   }
-  __syncthreads();
-  for (int r = ty; r < kT; r += 8) {
-    const int gi = ibase + r, gc = kbase + tx;
-    if (gi < nn && gc < nn) A[(int64_t)gi * ld + gc] = X[r][tx];
+  // row gi by warp ty: lane j holds x_j; x_c is final once scaled by 1 / L_cc
+  const int64_t gi = row0 + ty;
+  if (gi < nn) {
+    const bool in = base + tx < nn;
+    double x = in ? A[gi * ld + base + tx] : 0.0;
+#pragma unroll 8
+    for (int c = 0; c < kT; ++c) {
+      if (tx == c) x *= rs[c];
+      const double xc = __shfl_sync(0xffffffffu, x, c);
+      if (tx > c) x = fma(-xc, t[tx][c], x);
+    }
+    if (in) A[gi * ld + base + tx] = x;
   }
 }
 
-// Trailing update A_ib,jb -= L_ib,kb L_jb,kb^T for kb < jb <= ib (one block per tile pair).
-__global__ void k_chol_update(double* A, int64_t ld, const int* nn_dev, int nn_fixed, int kb) {
+// Trailing update A_ib,jb -= L_ib,kb L_jb,kb^T for kb < jb <= ib: four blocks per tile pair,
+// each a 16 x 16 quarter (one output per thread, a 32-term dot from shared memory).
+__global__ void __launch_bounds__(256) k_chol_update(double* A, int64_t ld, const int* nn_dev, int nn_fixed, int kb) {
   const int nn = dev_nn(nn_dev, nn_fixed);
   const int nt = (nn + kT - 1) / kT;
   const int mrem = nt - kb - 1;
   const int64_t npairs = (int64_t)mrem * (mrem + 1) / 2;
-  if ((int64_t)blockIdx.x >= npairs) return;
-  // blockIdx -> (a, b), 0 <= b <= a < mrem, row-major over the lower triangle
-  int a = (int)((sqrt(8.0 * blockIdx.x + 1.0) - 1.0) * 0.5);
-  while ((int64_t)(a + 1) * (a + 2) / 2 <= (int64_t)blockIdx.x) ++a;
-  while ((int64_t)a * (a + 1) / 2 > (int64_t)blockIdx.x) --a;
-  const int b = (int)(blockIdx.x - (int64_t)a * (a + 1) / 2);
-  const int ib = kb + 1 + a, jb = kb + 1 + b;
-  __shared__ double Li[kT][kT + 1];
-  __shared__ double Lj[kT][kT + 1];
+  const int64_t pair = blockIdx.x >> 2;
+  if (pair >= npairs) return;
+  // pair -> (a, b), 0 <= b <= a < mrem, row-major over the lower triangle
+  int a = (int)((sqrt(8.0 * (double)pair + 1.0) - 1.0) * 0.5);
+  while ((int64_t)(a + 1) * (a + 2) / 2 <= pair) ++a;
+  while ((int64_t)a * (a + 1) / 2 > pair) --a;
+  const int b = (int)(pair - (int64_t)a * (a + 1) / 2);
+  const int qi = (blockIdx.x >> 1) & 1, qj = blockIdx.x & 1;
+  if (a == b && qj > qi) return;   // strictly upper quarter of a diagonal tile
+  const int kbase = kb * kT;
+  const int ibase = (kb + 1 + a) * kT + 16 * qi, jbase = (kb + 1 + b) * kT + 16 * qj;
+  if (ibase >= nn || jbase >= nn) return;
+  __shared__ double Li[16][kT + 1];
+  __shared__ double Lj[16][kT + 1];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int kbase = kb * kT, ibase = ib * kT, jbase = jb * kT;
-  for (int r = ty; r < kT; r += 8) {
-    const int gc = kbase + tx;
-    Li[r][tx] = (ibase + r < nn && gc < nn) ? A[(int64_t)(ibase + r) * ld + gc] : 0.0;
-    Lj[r][tx] = (jbase + r < nn && gc < nn) ? A[(int64_t)(jbase + r) * ld + gc] : 0.0;
+  const bool cin = kbase + tx < nn;
+  for (int r = ty; r < 16; r += 8) {
+    Li[r][tx] = (ibase + r < nn && cin) ? A[(int64_t)(ibase + r) * ld + kbase + tx] : 0.0;
+    Lj[r][tx] = (jbase + r < nn && cin) ? A[(int64_t)(jbase + r) * ld + kbase + tx] : 0.0;
   }
   __syncthreads();
-  for (int r = ty; r < kT; r += 8) {
-    const int gi = ibase + r, gj = jbase + tx;
-    if (gi < nn && gj < nn && gj <= gi) {
-      double acc = 0.0;
+  const int r = threadIdx.x >> 4, c = threadIdx.x & 15;
+  const int gi = ibase + r, gj = jbase + c;
+  if (gi < nn && gj < nn && gj <= gi) {
+    double acc = 0.0;
 #pragma unroll 8
-      for (int c = 0; c < kT; ++c) acc = fma(Li[r][c], Lj[tx][c], acc);
-      A[(int64_t)gi * ld + gj] -= acc;
-    }
+    for (int k = 0; k < kT; ++k) acc = fma(Li[r][k], Lj[c][k], acc);
+    A[(int64_t)gi * ld + gj] -= acc;
   }
 }
 
-// Captures the whole factorisation for an nn of at most cap (tile columns beyond the device
-// nn exit immediately).
+// Captures the whole factorisation for an nn of at most cap (tile columns and panel rows
+// beyond the device nn exit immediately).
 static cudaError_t launch_chol(double* A, int64_t ld, const int* nn_dev, int nn_fixed, int cap, double* diag0,
-                               int* nfloor, cudaStream_t st) {
+                               double* rinv, int* nfloor, cudaStream_t st) {
   const int nt = (cap + kT - 1) / kT;
   k_chol_save_diag<<<std::max(1, std::min(64, (cap + 255) / 256)), 256, 0, st>>>(A, ld, nn_dev, nn_fixed, diag0, nfloor);
   for (int kb = 0; kb < nt; ++kb) {
-    k_chol_potrf<<<1, 256, 0, st>>>(A, ld, nn_dev, nn_fixed, kb, diag0, 1e-13, nfloor);
+    const int rows_below = std::max(0, cap - (kb + 1) * kT);
+    k_chol_panel<<<1 + (rows_below + kPanelRows - 1) / kPanelRows, 256, 0, st>>>(A, ld, nn_dev, nn_fixed, kb, diag0,
+                                                                                   1e-13, nfloor, rinv);
     const int below = nt - kb - 1;
-    if (below > 0) {
-      k_chol_trsm<<<below, 256, 0, st>>>(A, ld, nn_dev, nn_fixed, kb);
-      k_chol_update<<<below * (below + 1) / 2, 256, 0, st>>>(A, ld, nn_dev, nn_fixed, kb);
-    }
+    if (below > 0) k_chol_update<<<4 * below * (below + 1) / 2, 256, 0, st>>>(A, ld, nn_dev, nn_fixed, kb);
   }
   return cudaGetLastError();
 }
@@ -164,14 +181,15 @@ __global__ void k_mirror(double* A, int64_t ld, const int* nn_dev, int nn_fixed)
 
 // Column c of A^{-1} = L^{-T} L^{-1} e_c: forward sweep reads row p of the upper part (= column
 // p of L), backward sweep reads row q of L; both contiguous.  One block per column at a time.
-__global__ void k_inv(const double* A, int64_t ld, const int* nn_dev, int nn_fixed, double* Ainv, int64_t ldi) {
+__global__ void k_inv(const double* A, int64_t ld, const int* nn_dev, int nn_fixed, const double* rinv, double* Ainv,
+                      int64_t ldi) {
   extern __shared__ double y[];
   const int nn = nn_dev ? *nn_dev : nn_fixed;
   for (int c = blockIdx.x; c < nn; c += gridDim.x) {
     for (int i = threadIdx.x; i < nn; i += blockDim.x) y[i] = (i == c) ? 1.0 : 0.0;
     __syncthreads();
     for (int p = c; p < nn; ++p) {
-      const double yp = y[p] / A[(int64_t)p * ld + p];
+      const double yp = y[p] * rinv[p];
       __syncthreads();
       if (threadIdx.x == 0) y[p] = yp;
       const double* up = A + (int64_t)p * ld;
@@ -179,7 +197,7 @@ __global__ void k_inv(const double* A, int64_t ld, const int* nn_dev, int nn_fix
       __syncthreads();
     }
     for (int q = nn - 1; q >= 0; --q) {
-      const double xq = y[q] / A[(int64_t)q * ld + q];
+      const double xq = y[q] * rinv[q];
       __syncthreads();
       if (threadIdx.x == 0) y[q] = xq;
       const double* lq = A + (int64_t)q * ld;
@@ -352,7 +370,7 @@ cudaError_t launch_dense_build(const Dev& d, cudaStream_t st) {
   else
     k_gram_tiles<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, st>>>(d);
   k_gram_diag_hs<<<(int)std::min<int64_t>(d.n, 4 * 152), 256, 0, st>>>(d);
-  cudaError_t e = launch_chol(d.Kd, d.n, nullptr, n, n, d.chol_diag, &d.sc->chol_fail, st);
+  cudaError_t e = launch_chol(d.Kd, d.n, nullptr, n, n, d.chol_diag, d.chol_rinv, &d.sc->chol_fail, st);
   if (e != cudaSuccess) return e;
   k_mirror<<<256, 256, 0, st>>>(d.Kd, d.n, nullptr, n);
   (void)rowbytes;   // applied by triangular solves (k_dense_trsv), no explicit inverse
@@ -363,10 +381,10 @@ cudaError_t launch_stiff_factor(const Dev& d, cudaStream_t st) {
   const int cap = d.stiff_cap;
   const size_t rowbytes = sizeof(double) * (size_t)cap;
   const int* ns = &d.sc->n_stiff;
-  cudaError_t e = launch_chol(d.G, cap, ns, 0, cap, d.chol_diag, &d.sc->chol_fail, st);
+  cudaError_t e = launch_chol(d.G, cap, ns, 0, cap, d.chol_diag, d.chol_rinv, &d.sc->chol_fail, st);
   if (e != cudaSuccess) return e;
   k_mirror<<<64, 256, 0, st>>>(d.G, cap, ns, 0);
-  k_inv<<<std::min(cap, 4 * 152), 256, rowbytes, st>>>(d.G, cap, ns, 0, d.Ginv, cap);
+  k_inv<<<std::min(cap, 4 * 152), 256, rowbytes, st>>>(d.G, cap, ns, 0, d.chol_rinv, d.Ginv, cap);
   return cudaGetLastError();
 }
 

@@ -1271,29 +1271,37 @@ __global__ void k_stiff_corr(Dev d, int init) {
 
 // Dense preconditioner apply by triangular solves: z = K^{-1} r with K = L L^T (L in the
 // lower triangle of Kd, L^T mirrored into the upper triangle, both row-major), forward
-// L y = r then backward L^T z = y, in blocks of 32 rows: warp 0 solves the diagonal block
-// (lane i holds y_i, one shuffle per row), then all threads update the remaining rows with
-// the block's 32 columns.  One block of 1024 threads; y in shared memory (n <= 2048).
+// L y = r then backward L^T z = y, in blocks of 32 rows: the block's diagonal tile is staged
+// in shared memory by all threads, warp 0 solves it (lane i holds y_i, one shuffle per row,
+// multiplying by the saved reciprocal pivots), then all threads update the remaining rows
+// with the block's 32 columns.  One block of 1024 threads; y in shared memory (n <= 2048).
 // r^T z -> rz / beta; init: p = z.  (PCG with the exact factor converges in one or two
 // iterations, so this replaces forming K^{-1} once per IPM iteration.)
 __global__ void __launch_bounds__(1024) k_dense_trsv(Dev d, int init) {
   extern __shared__ double y[];
   __shared__ double sh[32];
+  __shared__ double Lt[32][33];
+  __shared__ double rs[32];
   if (!init && d.sc->cg_done) return;
   const int n = (int)d.n;
   const double* K = d.Kd;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < n; i += blockDim.x) y[i] = d.r[i];
-  __syncthreads();
   // forward: L y = r
   for (int kb = 0; kb < n; kb += 32) {
     const int bs = min(32, n - kb);
+    // tile rows kb + warp (lower part; identity padding past n), reciprocal pivots
+    Lt[warp][lane] = (warp < bs && lane < bs) ? (lane <= warp ? K[(int64_t)(kb + warp) * n + kb + lane] : 0.0)
+                                              : (warp == lane ? 1.0 : 0.0);
+    if (warp == 0) rs[lane] = lane < bs ? d.chol_rinv[kb + lane] : 1.0;
+    __syncthreads();
     if (warp == 0) {
       double yl = lane < bs ? y[kb + lane] : 0.0;
-      for (int c = 0; c < bs; ++c) {
-        if (lane == c) yl = yl / K[(int64_t)(kb + c) * n + kb + c];
+#pragma unroll 8
+      for (int c = 0; c < 32; ++c) {
+        if (lane == c) yl *= rs[c];
         const double v = __shfl_sync(0xffffffffu, yl, c);
-        if (lane > c && lane < bs) yl = fma(-K[(int64_t)(kb + lane) * n + kb + c], v, yl);
+        if (lane > c) yl = fma(-Lt[lane][c], v, yl);
       }
       if (lane < bs) y[kb + lane] = yl;
     }
@@ -1309,12 +1317,17 @@ __global__ void __launch_bounds__(1024) k_dense_trsv(Dev d, int init) {
   // backward: L^T z = y, with L^T row i in the upper triangle of row i
   for (int kb = ((n - 1) / 32) * 32; kb >= 0; kb -= 32) {
     const int bs = min(32, n - kb);
+    Lt[warp][lane] = (warp < bs && lane < bs) ? (lane <= warp ? K[(int64_t)(kb + warp) * n + kb + lane] : 0.0)
+                                              : (warp == lane ? 1.0 : 0.0);
+    if (warp == 0) rs[lane] = lane < bs ? d.chol_rinv[kb + lane] : 1.0;
+    __syncthreads();
     if (warp == 0) {
       double yl = lane < bs ? y[kb + lane] : 0.0;
-      for (int c = bs - 1; c >= 0; --c) {
-        if (lane == c) yl = yl / K[(int64_t)(kb + c) * n + kb + c];
+#pragma unroll 8
+      for (int c = 31; c >= 0; --c) {
+        if (lane == c) yl *= rs[c];
         const double v = __shfl_sync(0xffffffffu, yl, c);
-        if (lane < c) yl = fma(-K[(int64_t)(kb + lane) * n + kb + c], v, yl);
+        if (lane < c) yl = fma(-Lt[c][lane], v, yl);
       }
       if (lane < bs) y[kb + lane] = yl;
     }

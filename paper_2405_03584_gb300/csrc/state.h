@@ -66,6 +66,7 @@ struct Dev {
   double* Kd;                  // n x n: the condensed matrix, then its Cholesky factor (L and L^T)
   double* Rd;                  // nR x n: R as a dense matrix (when it is small enough), or nullptr
   double* chol_diag;           // max(n_dense, stiff_cap): original diagonal during a factorisation
+  double* chol_rinv;           // max(n_dense, stiff_cap): 1 / L_kk of the last factor
   // double-float operator (storage ST_F64 with options.op_arith = DF32): the values of R and
   // R^T as (hi, lo) float32 pairs, the PCG direction p and the rows-pass result v likewise;
   // the FP64 copies stay for the residuals, the start point and the stiff-row correction
