@@ -275,12 +275,16 @@ void carve_state(Carver& cv, Dev& d, int64_t n, int64_t m, int64_t nR, int stiff
   d.us = cv.take<double>(stiff_cap); d.ts = cv.take<double>(stiff_cap); d.stiff_cap = stiff_cap;
   d.us2 = cv.take<double>(stiff_cap);
   d.hist = cv.take<unsigned int>(kHistBins);
-  d.Kd = dense ? cv.take<double>(n * n) : nullptr;
+  d.Kd = dense ? cv.take<float2>(n * n) : nullptr;
   // the dense preconditioner forms K by a tiled product over R stored densely when that
   // copy stays below 256 MB (else it scans R's rows)
-  d.Rd = (dense && nR * n <= (int64_t)(32 << 20)) ? cv.take<double>(nR * n) : nullptr;
+  d.Rd = (dense && nR * n <= (int64_t)(32 << 20)) ? cv.take<float2>(nR * n) : nullptr;
+  d.wdf = dense ? cv.take<float2>(std::max<int64_t>(nR, 1)) : nullptr;
+  d.dense_aux = dense ? cv.take<double>(4) : nullptr;
   d.chol_diag = cv.take<double>(std::max<int64_t>(dense ? n : 0, stiff_cap));
   d.chol_rinv = cv.take<double>(std::max<int64_t>(dense ? n : 0, stiff_cap));
+  d.chol_rdf = dense ? cv.take<float2>(n) : nullptr;
+  d.chol_tinv = dense ? cv.take<float2>((n + 31) / 32 * 1024) : nullptr;
   d.storage = storage;
   if (df) {
     d.p_df = cv.take<float2>(n);

@@ -337,6 +337,20 @@ __device__ __forceinline__ void df_mac(const float2 a, const float2 x, float& h,
   l = __fadd_rn(l, __fadd_rn(t, e));
 }
 
+// (h, l) -> a normalised pair h' + l' = h + l (|l| small against |h|: Dekker's fast two-sum)
+__device__ __forceinline__ float2 df_fast_sum(float h, float l) {
+  const float s = __fadd_rn(h, l);
+  return make_float2(s, __fsub_rn(l, __fsub_rn(s, h)));
+}
+
+// a - (h + l) for a normalised pair a and an accumulated pair (h, l), normalised
+__device__ __forceinline__ float2 df_sub_sum(float2 a, float h, float l) {
+  float s, t;
+  two_sum(a.x, -h, s, t);
+  t = __fadd_rn(t, __fsub_rn(a.y, l));
+  return df_fast_sum(s, t);
+}
+
 // Sum of the pairs of a group of G lanes in place (fixed butterfly order; every lane of the
 // group gets the total pair).
 template <int G>

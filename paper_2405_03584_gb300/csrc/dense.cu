@@ -1,15 +1,25 @@
-// Dense pieces of the preconditioners (sm_103a, float64):
-//   * k_gram_tiles / k_gram_diag_hs : K = Hs + R^T diag(omega) R + U W U^T + diag(h0 + sigma) as a
-//                  dense n x n matrix
-//                  (the DENSE preconditioner: one diagonal block covering all variables);
+// Dense pieces of the preconditioners (sm_103a):
+//   * k_dense_prep / k_gram_gemm / k_gram_tiles / k_gram_diag_hs : K = Hs + R^T diag(omega) R +
+//                  U W U^T + diag(h0 + sigma), scaled by a power of two, as a dense n x n
+//                  matrix (the DENSE preconditioner: one diagonal block covering all variables);
 //   * k_chol_*   : in-place blocked Cholesky factor (lower) with pivot flooring, and the
 //                  reciprocal pivots;
+//   * k_chol_tile_inv : inverses of the factor's 32 x 32 diagonal tiles;
 //   * k_mirror   : copies L into the upper triangle so both triangular sweeps read rows;
 //   * k_inv      : explicit inverse from the factor, columns spread over blocks.
-// The low-rank correction's G (up to 1024 rows) is inverted explicitly, so each of the many
-// PCG applies is a parallel matvec; the DENSE preconditioner, whose PCG takes one or two
-// iterations, is applied by triangular solves with the factor instead.  The factorisation
-// runs once per IPM iteration.
+// The low-rank correction's G (up to 1024 rows) is factored in float64 and inverted
+// explicitly, so each of the many PCG applies is a parallel matvec.  The DENSE
+// preconditioner, whose PCG takes one or two iterations, is formed, factored and applied
+// (triangular solves, k_dense_trsv) in double-float arithmetic: values are pairs of float32
+// (hi + lo, about 48 bits) computed on the float32 pipe.  On GB300 a dependent float64
+// multiply-add takes 64 cycles, a float64 rsqrt or division over 400, and the SM retires one
+// float64 warp instruction per ~19 cycles, against 4.5 cycles and 128 lanes per clock for
+// float32: the factorisation is a chain of dependent steps and the Gram product is bound by
+// arithmetic, so both run several times faster in pairs.  A preconditioner needs no more than
+// the pairs' precision; PCG on the float64 operator carries the solve to its tolerance.
+// Pairs keep float32's exponent range, so K is scaled by 2^-2e (exact, e chosen each IPM
+// iteration from float64 bounds on its entries) before it is formed; the solve undoes it.
+// The factorisation runs once per IPM iteration.
 #include <algorithm>
 #include <cmath>
 
@@ -17,81 +27,150 @@
 
 namespace ipmk {
 
+// ------------------------------------------------------------------ scalar policies
+// float64 (the stiff-row G) and double-float pairs in a float2 (x + y, |y| <= ulp(x) / 2
+// after each operation; the dense K).
 
+__device__ __forceinline__ double r_mul(double a, double b) { return a * b; }
+__device__ __forceinline__ double r_fms(double c, double a, double b) { return fma(-a, b, c); }   // c - a b
+__device__ __forceinline__ double r_rsqrt(double p) { return rsqrt(p); }
+__device__ __forceinline__ bool r_above(double a, double b) { return a > b; }
+__device__ __forceinline__ double r_shfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ double r_to_double(double v) { return v; }
+__device__ __forceinline__ double r_floor(double fl) { return fl + 1e-300; }
+template <class R> __device__ __forceinline__ R r_const(double v);
+template <> __device__ __forceinline__ double r_const<double>(double v) { return v; }
+template <> __device__ __forceinline__ float2 r_const<float2>(double v) { return make_float2((float)v, 0.f); }
+
+// a b: the high product, its exact error (fma) and the two cross terms
+__device__ __forceinline__ float2 r_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  return df_fast_sum(p, e);
+}
+// c - a b
+__device__ __forceinline__ float2 r_fms(float2 c, float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  float s, t;
+  two_sum(c.x, -p, s, t);
+  t = __fadd_rn(t, __fsub_rn(c.y, e));
+  return df_fast_sum(s, t);
+}
+// 1 / sqrt(p): the float32 estimate r0, then one Newton step r0 + r0 (1 - p r0^2) / 2 with
+// the residual 1 - p r0^2 formed in pairs (r0^2 exact by fma)
+__device__ __forceinline__ float2 r_rsqrt(float2 p) {
+  const float r0 = rsqrtf(p.x);
+  const float q = __fmul_rn(r0, r0);
+  const float2 w = r_mul(p, make_float2(q, __fmaf_rn(r0, r0, -q)));
+  const float e = __fsub_rn(__fsub_rn(1.f, w.x), w.y);
+  return df_fast_sum(r0, __fmul_rn(__fmul_rn(0.5f, r0), e));
+}
+__device__ __forceinline__ bool r_above(float2 a, float2 b) { return a.x > b.x; }
+__device__ __forceinline__ float2 r_shfl(float2 v, int src) {
+  return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+__device__ __forceinline__ double r_to_double(float2 v) { return df_value(v.x, v.y); }
+__device__ __forceinline__ float2 r_floor(float2 fl) { return make_float2(fmaxf(fl.x, 1e-30f), 0.f); }
+
+// ------------------------------------------------------------------ blocked Cholesky
 // Blocked right-looking Cholesky (lower, row-major, leading dimension ld) of the leading
 // nn x nn block of A on 32 x 32 tiles, two launches per tile column kb:
 //   * the panel: every block factors the diagonal tile in shared memory (the same code on the
 //     same data, so each gets the same factor; block 0 writes it back), then the others each
 //     solve 8 rows of the tiles below, X = A_ib,kb L_kb,kb^{-T}, one warp per row;
 //   * the trailing update A_ib,jb -= L_ib,kb L_jb,kb^T (kb < jb <= ib) on 16 x 16 quarter tiles.
-// GB300's float64 pipe issues two fused multiply-adds per SM per clock, so a 32-step chain
-// of float64 operations on one warp costs tens of microseconds: each pivot takes one rsqrt
-// and the rest multiplies by it (no division on the chain), and the arithmetic of a tile
-// column is spread over as many SMs as it has row blocks.  The reciprocal pivots go to
-// rinv[] for the triangular solves.  nn is read on the device (it may be the number of stiff
-// rows).  A pivot below floor_rel * (original diagonal) is raised to that floor (a modified
-// factor; still symmetric positive definite, which is all a preconditioner needs); the count
-// goes to *nfloor.
+// Each pivot takes one reciprocal square root and the rest multiplies by it (no division on
+// the chain), and the arithmetic of a tile column is spread over as many SMs as it has row
+// blocks.  The reciprocal pivots go to rinv[] for the triangular solves.  nn is read on the
+// device (it may be the number of stiff rows).  A pivot below floor_rel * (original diagonal)
+// is raised to that floor (a modified factor; still symmetric positive definite, which is all
+// a preconditioner needs); the count goes to *nfloor.
 constexpr int kT = 32;
 constexpr int kPanelRows = 8;   // rows of the panel below the diagonal tile per block
+constexpr double kFloorRel = 1e-13;
 
 __device__ __forceinline__ int dev_nn(const int* nn_dev, int nn_fixed) { return nn_dev ? *nn_dev : nn_fixed; }
 
-__global__ void k_chol_save_diag(const double* A, int64_t ld, const int* nn_dev, int nn_fixed, double* diag0, int* nfloor) {
+template <class R>
+__global__ void k_chol_save_diag(const R* A, int64_t ld, const int* nn_dev, int nn_fixed, double* diag0, int* nfloor) {
   const int nn = dev_nn(nn_dev, nn_fixed);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) diag0[i] = A[(int64_t)i * ld + i];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x)
+    diag0[i] = r_to_double(A[(int64_t)i * ld + i]);
   if (blockIdx.x == 0 && threadIdx.x == 0 && nfloor) *nfloor = 0;
 }
 
 // Unblocked Cholesky of diagonal tile kb in shared memory by 256 threads (rows/cols >= nn
 // padded by identity): rs[k] = 1 / L_kk.  Pivots are floored as above; nfloor (may be null)
-// counts the floored ones.
-__device__ void tile_potrf(double (*t)[kT + 1], double* rs, const double* A, int64_t ld, int nn, int base,
-                           const double* diag0, double floor_rel, int* nfloor) {
+// counts the floored ones.  The trailing update of step k touches the entries (i, j),
+// k < j <= i; listed by j descending (then i), they are the first (31 - k)(32 - k) / 2 of one
+// table of pairs, so the 256 threads take them densely (at most two each) instead of one
+// row per warp with most lanes idle.
+constexpr int kTriPairs = kT * (kT - 1) / 2;   // 496 pairs (i, j), 1 <= j <= i < 32
+
+template <class R>
+__device__ void tile_potrf(R (*t)[kT + 1], R* rs, const R* A, int64_t ld, int nn, int base, const double* diag0,
+                           int* nfloor) {
+  __shared__ unsigned short pairs[kTriPairs];
+  __shared__ R fl[kT];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
   for (int r = ty; r < kT; r += 8) {
     const int gi = base + r, gj = base + tx;
-    t[r][tx] = (gi < nn && gj < nn) ? A[(int64_t)gi * ld + gj] : (r == tx ? 1.0 : 0.0);
+    t[r][tx] = (gi < nn && gj < nn) ? A[(int64_t)gi * ld + gj] : r_const<R>(r == tx ? 1.0 : 0.0);
+  }
+  if (ty == 0) fl[tx] = r_floor(r_const<R>(base + tx < nn ? kFloorRel * fabs(diag0[base + tx]) : 0.0));
+  for (int e = threadIdx.x; e < kTriPairs; e += blockDim.x) {
+    int j = kT - 1, rem = e;
+    while (rem >= kT - j) {
+      rem -= kT - j;
+      --j;
+    }
+    pairs[e] = (unsigned short)((j + rem) * kT + j);
   }
   __syncthreads();
   for (int k = 0; k < kT; ++k) {
     if (ty == 0) {   // column k by warp 0
-      double piv = t[k][k];
+      R piv = t[k][k];
       __syncwarp();
-      if (base + k < nn) {
-        const double fl = floor_rel * fabs(diag0[base + k]) + 1e-300;
-        if (!(piv > fl)) {
-          piv = fl;
-          if (nfloor && tx == 0) atomicAdd(nfloor, 1);
-        }
+      if (base + k < nn && !r_above(piv, fl[k])) {
+        piv = fl[k];
+        if (nfloor && tx == 0) atomicAdd(nfloor, 1);
       }
-      const double r = rsqrt(piv);
+      const R r = r_rsqrt(piv);
       if (tx == k) {
-        t[k][k] = piv * r;
+        t[k][k] = r_mul(piv, r);
         rs[k] = r;
       } else if (tx > k) {
-        t[tx][k] *= r;
+        t[tx][k] = r_mul(t[tx][k], r);
       }
     }
     __syncthreads();
-    for (int i = k + 1 + ty; i < kT; i += 8)
-      if (tx > k && tx <= i) t[i][tx] = fma(-t[i][k], t[tx][k], t[i][tx]);
+    const int cnt = (kT - 1 - k) * (kT - k) / 2;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int i = pairs[e] / kT, j = pairs[e] % kT;
+      t[i][j] = r_fms(t[i][j], t[i][k], t[j][k]);
+    }
     __syncthreads();
   }
 }
 
 // Panel of tile column kb: block 0 the diagonal tile, block b >= 1 rows
 // [base + 32 + 8 (b - 1), + 8) below it.
-__global__ void __launch_bounds__(256) k_chol_panel(double* A, int64_t ld, const int* nn_dev, int nn_fixed, int kb,
-                                                    const double* diag0, double floor_rel, int* nfloor, double* rinv) {
+template <class R>
+__global__ void __launch_bounds__(256) k_chol_panel(R* A, int64_t ld, const int* nn_dev, int nn_fixed, int kb,
+                                                    const double* diag0, int* nfloor, R* rinv) {
   const int nn = dev_nn(nn_dev, nn_fixed);
   const int base = kb * kT;
   if (base >= nn) return;
   const int64_t row0 = base + kT + (int64_t)(blockIdx.x - 1) * kPanelRows;
   if (blockIdx.x > 0 && row0 >= nn) return;   // whole block: before any barrier
-  __shared__ double t[kT][kT + 1];
-  __shared__ double rs[kT];
-  tile_potrf(t, rs, A, ld, nn, base, diag0, floor_rel, blockIdx.x == 0 ? nfloor : nullptr);
+  __shared__ R t[kT][kT + 1];
+  __shared__ R rs[kT];
+  tile_potrf<R>(t, rs, A, ld, nn, base, diag0, blockIdx.x == 0 ? nfloor : nullptr);
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   if (blockIdx.x == 0) {
     for (int r = ty; r < kT; r += 8) {
@@ -105,20 +184,36 @@ __global__ void __launch_bounds__(256) k_chol_panel(double* A, int64_t ld, const
   const int64_t gi = row0 + ty;
   if (gi < nn) {
     const bool in = base + tx < nn;
-    double x = in ? A[gi * ld + base + tx] : 0.0;
+    R x = in ? A[gi * ld + base + tx] : r_const<R>(0.0);
 #pragma unroll 8
     for (int c = 0; c < kT; ++c) {
-      if (tx == c) x *= rs[c];
-      const double xc = __shfl_sync(0xffffffffu, x, c);
-      if (tx > c) x = fma(-xc, t[tx][c], x);
+      if (tx == c) x = r_mul(x, rs[c]);
+      const R xc = r_shfl(x, c);
+      if (tx > c) x = r_fms(x, xc, t[tx][c]);
     }
     if (in) A[gi * ld + base + tx] = x;
   }
 }
 
+// 32-term dot of shared-memory rows, subtracted from a: float64 by fma; pairs accumulated
+// unnormalised (high parts by two-sum, every error term into the low part), then subtracted.
+__device__ __forceinline__ double dot_sub(double a, const double* x, const double* y) {
+  double acc = 0.0;
+#pragma unroll 8
+  for (int k = 0; k < kT; ++k) acc = fma(x[k], y[k], acc);
+  return a - acc;
+}
+__device__ __forceinline__ float2 dot_sub(float2 a, const float2* x, const float2* y) {
+  float h = 0.f, l = 0.f;
+#pragma unroll 8
+  for (int k = 0; k < kT; ++k) df_mac(x[k], y[k], h, l);
+  return df_sub_sum(a, h, l);
+}
+
 // Trailing update A_ib,jb -= L_ib,kb L_jb,kb^T for kb < jb <= ib: four blocks per tile pair,
 // each a 16 x 16 quarter (one output per thread, a 32-term dot from shared memory).
-__global__ void __launch_bounds__(256) k_chol_update(double* A, int64_t ld, const int* nn_dev, int nn_fixed, int kb) {
+template <class R>
+__global__ void __launch_bounds__(256) k_chol_update(R* A, int64_t ld, const int* nn_dev, int nn_fixed, int kb) {
   const int nn = dev_nn(nn_dev, nn_fixed);
   const int nt = (nn + kT - 1) / kT;
   const int mrem = nt - kb - 1;
@@ -135,43 +230,76 @@ __global__ void __launch_bounds__(256) k_chol_update(double* A, int64_t ld, cons
   const int kbase = kb * kT;
   const int ibase = (kb + 1 + a) * kT + 16 * qi, jbase = (kb + 1 + b) * kT + 16 * qj;
   if (ibase >= nn || jbase >= nn) return;
-  __shared__ double Li[16][kT + 1];
-  __shared__ double Lj[16][kT + 1];
+  __shared__ R Li[16][kT + 1];
+  __shared__ R Lj[16][kT + 1];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const bool cin = kbase + tx < nn;
   for (int r = ty; r < 16; r += 8) {
-    Li[r][tx] = (ibase + r < nn && cin) ? A[(int64_t)(ibase + r) * ld + kbase + tx] : 0.0;
-    Lj[r][tx] = (jbase + r < nn && cin) ? A[(int64_t)(jbase + r) * ld + kbase + tx] : 0.0;
+    Li[r][tx] = (ibase + r < nn && cin) ? A[(int64_t)(ibase + r) * ld + kbase + tx] : r_const<R>(0.0);
+    Lj[r][tx] = (jbase + r < nn && cin) ? A[(int64_t)(jbase + r) * ld + kbase + tx] : r_const<R>(0.0);
   }
   __syncthreads();
   const int r = threadIdx.x >> 4, c = threadIdx.x & 15;
   const int gi = ibase + r, gj = jbase + c;
   if (gi < nn && gj < nn && gj <= gi) {
-    double acc = 0.0;
-#pragma unroll 8
-    for (int k = 0; k < kT; ++k) acc = fma(Li[r][k], Lj[c][k], acc);
-    A[(int64_t)gi * ld + gj] -= acc;
+    R* ap = A + (int64_t)gi * ld + gj;
+    *ap = dot_sub(*ap, Li[r], Lj[c]);
   }
 }
 
 // Captures the whole factorisation for an nn of at most cap (tile columns and panel rows
 // beyond the device nn exit immediately).
-static cudaError_t launch_chol(double* A, int64_t ld, const int* nn_dev, int nn_fixed, int cap, double* diag0,
-                               double* rinv, int* nfloor, cudaStream_t st) {
+template <class R>
+static cudaError_t launch_chol(R* A, int64_t ld, const int* nn_dev, int nn_fixed, int cap, double* diag0, R* rinv,
+                               int* nfloor, cudaStream_t st) {
   const int nt = (cap + kT - 1) / kT;
-  k_chol_save_diag<<<std::max(1, std::min(64, (cap + 255) / 256)), 256, 0, st>>>(A, ld, nn_dev, nn_fixed, diag0, nfloor);
+  k_chol_save_diag<R><<<std::max(1, std::min(64, (cap + 255) / 256)), 256, 0, st>>>(A, ld, nn_dev, nn_fixed, diag0,
+                                                                                     nfloor);
   for (int kb = 0; kb < nt; ++kb) {
     const int rows_below = std::max(0, cap - (kb + 1) * kT);
-    k_chol_panel<<<1 + (rows_below + kPanelRows - 1) / kPanelRows, 256, 0, st>>>(A, ld, nn_dev, nn_fixed, kb, diag0,
-                                                                                   1e-13, nfloor, rinv);
+    k_chol_panel<R><<<1 + (rows_below + kPanelRows - 1) / kPanelRows, 256, 0, st>>>(A, ld, nn_dev, nn_fixed, kb, diag0,
+                                                                                     nfloor, rinv);
     const int below = nt - kb - 1;
-    if (below > 0) k_chol_update<<<4 * below * (below + 1) / 2, 256, 0, st>>>(A, ld, nn_dev, nn_fixed, kb);
+    if (below > 0) k_chol_update<R><<<4 * below * (below + 1) / 2, 256, 0, st>>>(A, ld, nn_dev, nn_fixed, kb);
   }
   return cudaGetLastError();
 }
 
+// Inverse of every diagonal tile of the (pair) factor, L_kk^{-1} (lower, 32 x 32, row-major,
+// padded by identity past nn), one block per tile: forward substitution on the identity, row c
+// final once scaled by 1 / L_cc, then eliminated from the rows below.  The dense
+// preconditioner's triangular solves multiply by these instead of substituting row by row.
+__global__ void __launch_bounds__(256) k_chol_tile_inv(const float2* A, int64_t ld, int nn, const float2* rinv,
+                                                       float2* tinv) {
+  __shared__ float2 L[kT][kT + 1];
+  __shared__ float2 X[kT][kT + 1];
+  __shared__ float2 rs[kT];
+  const int base = blockIdx.x * kT;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < kT; r += 8) {
+    const int gi = base + r, gj = base + tx;
+    L[r][tx] = (gi < nn && gj < nn) ? (tx <= r ? A[(int64_t)gi * ld + gj] : make_float2(0.f, 0.f))
+                                    : make_float2(r == tx ? 1.f : 0.f, 0.f);
+    X[r][tx] = make_float2(r == tx ? 1.f : 0.f, 0.f);
+  }
+  if (ty == 0) rs[tx] = base + tx < nn ? rinv[base + tx] : make_float2(1.f, 0.f);
+  __syncthreads();
+  for (int c = 0; c < kT; ++c) {
+    if (ty == 0 && tx <= c) X[c][tx] = r_mul(X[c][tx], rs[c]);
+    __syncthreads();
+    const int w = c + 1, cnt = (kT - 1 - c) * w;   // rows i > c, columns j <= c
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int i = c + 1 + e / w, j = e % w;
+      X[i][j] = r_fms(X[i][j], L[i][c], X[c][j]);
+    }
+    __syncthreads();
+  }
+  for (int r = ty; r < kT; r += 8) tinv[(int64_t)blockIdx.x * kT * kT + r * kT + tx] = X[r][tx];
+}
+
 // Upper triangle <- L^T so that column p of L is row p of the upper part.
-__global__ void k_mirror(double* A, int64_t ld, const int* nn_dev, int nn_fixed) {
+template <class R>
+__global__ void k_mirror(R* A, int64_t ld, const int* nn_dev, int nn_fixed) {
   const int nn = nn_dev ? *nn_dev : nn_fixed;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)nn * nn; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = t / nn, i = t % nn;
@@ -179,8 +307,9 @@ __global__ void k_mirror(double* A, int64_t ld, const int* nn_dev, int nn_fixed)
   }
 }
 
-// Column c of A^{-1} = L^{-T} L^{-1} e_c: forward sweep reads row p of the upper part (= column
-// p of L), backward sweep reads row q of L; both contiguous.  One block per column at a time.
+// Column c of A^{-1} = L^{-T} L^{-1} e_c (float64): forward sweep reads row p of the upper part
+// (= column p of L), backward sweep reads row q of L; both contiguous.  One block per column at
+// a time.
 __global__ void k_inv(const double* A, int64_t ld, const int* nn_dev, int nn_fixed, const double* rinv, double* Ainv,
                       int64_t ldi) {
   extern __shared__ double y[];
@@ -209,35 +338,135 @@ __global__ void k_inv(const double* A, int64_t ld, const int* nn_dev, int nn_fix
   }
 }
 
-// K = R^T diag(omega) R + U W U^T + Hs + diag(h0 + sigma) by 32 x 32 tiles: one block per
-// tile of the lower triangle; for every row i of R (in order) the block gathers the row's
-// entries that fall in its two column ranges (scaled by omega_i on one side) and adds their
-// outer product (2 x 2 outputs per thread); the columns of U likewise.  Each output is a sum
-// in row order, so K is deterministic; off-diagonal tiles are written to both triangles.
+// ------------------------------------------------------------------ forming the scaled K
+// dense_aux[0] = max_ij R_ij^2 and dense_aux[1] = max |Hs| (set with the QP, as the bit
+// patterns of non-negative doubles, whose unsigned order is their numeric order, so the
+// atomic maximum is exact and independent of order); dense_aux[2] = the scale 2^-2e of the
+// current iteration's K.
+
+__global__ void k_dense_maxima(Dev d) {
+  unsigned long long mr = 0, mh = 0;
+  const int64_t nnzR = d.nR ? d.R_ptr[d.nR] : 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnzR; e += (int64_t)gridDim.x * blockDim.x) {
+    const double v = d.R_val[e] * d.R_val[e];
+    mr = max(mr, (unsigned long long)__double_as_longlong(v));
+  }
+  const int64_t nnzH = d.Hs_ptr ? d.Hs_ptr[d.n] : 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnzH; e += (int64_t)gridDim.x * blockDim.x)
+    mh = max(mh, (unsigned long long)__double_as_longlong(fabs(d.Hs_val[e])));
+  unsigned long long* aux = reinterpret_cast<unsigned long long*>(d.dense_aux);
+  if (mr) atomicMax(aux + 0, mr);
+  if (mh) atomicMax(aux + 1, mh);
+}
+
+// One block: B = nR max_i omega_i max R^2 + max_j |h0_j + sigma_j| + max |Hs| + (a bound on
+// the low-rank term) bounds every |K_ij|; s = 2^-2e with 2^2e > B puts K's entries below 1 in
+// magnitude.  Then the scaled row weights as pairs, wdf_i = s omega_i.
+__global__ void __launch_bounds__(1024) k_dense_prep(Dev d) {
+  __shared__ double sh[32];
+  __shared__ double s_scale;
+  double mw = 0.0, md = 0.0, ml = 0.0;
+  for (int64_t i = threadIdx.x; i < d.nR; i += blockDim.x) mw = fmax(mw, fabs(d.omega[i]));
+  for (int64_t j = threadIdx.x; j < d.n; j += blockDim.x) md = fmax(md, fabs(d.h0[j] + d.sigma[j]));
+  if (d.ucols)
+    for (int64_t e = threadIdx.x; e < d.n * d.ucols; e += blockDim.x) {
+      const double u = d.U[e];
+      ml = fmax(ml, u * u * fabs(d.uw[e % d.ucols]) * (double)d.ucols);
+    }
+  mw = block_reduce<1>(mw, sh);
+  md = block_reduce<1>(md, sh);
+  ml = block_reduce<1>(ml, sh);
+  if (threadIdx.x == 0) {
+    const unsigned long long* aux = reinterpret_cast<const unsigned long long*>(d.dense_aux);
+    const double rmax2 = __longlong_as_double((long long)aux[0]);
+    const double hmax = __longlong_as_double((long long)aux[1]);
+    const double B = mw * rmax2 * (double)(d.nR > 0 ? d.nR : 1) + md + hmax + ml;
+    int e = 0;
+    if (B > 0.0 && isfinite(B)) {
+      frexp(B, &e);   // B < 2^e
+      e += e & 1;     // even: the factor's scale 2^-e/2 is exact too
+    }
+    s_scale = ldexp(1.0, -e);
+    d.dense_aux[2] = s_scale;
+  }
+  __syncthreads();
+  const double s = s_scale;
+  for (int64_t i = threadIdx.x; i < d.nR; i += blockDim.x) d.wdf[i] = df_split(s * d.omega[i]);
+}
+
+// K = R^T diag(omega) R + U W U^T (scaled, as pairs) by 32 x 32 tiles: one block per tile of
+// the lower triangle, 2 x 2 outputs per thread, each a sum in row order, so K is
+// deterministic; off-diagonal tiles are written to both triangles.
 constexpr int kGT = 32;
 
-__global__ void __launch_bounds__(256) k_gram_tiles(Dev d) {
-  __shared__ double sJ[kGT], sL[kGT];
-  const int64_t n = d.n;
-  const int64_t b = blockIdx.x;
-  int64_t tj = (int64_t)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+__device__ __forceinline__ void tile_of_block(int64_t b, int64_t& tj, int64_t& tl) {
+  tj = (int64_t)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
   while ((tj + 1) * (tj + 2) / 2 <= b) ++tj;
   while (tj * (tj + 1) / 2 > b) --tj;
-  const int64_t tl = b - tj * (tj + 1) / 2;
+  tl = b - tj * (tj + 1) / 2;
+}
+
+// the low-rank term's columns into the 2 x 2 accumulators (sJ, sL: 32 pairs of shared
+// memory each), then the tile's stores
+__device__ __forceinline__ void gram_lowrank_store(const Dev& d, int64_t J0, int64_t L0, int64_t tj, int64_t tl,
+                                                   float2* sJ, float2* sL, float (&h)[2][2], float (&l)[2][2]) {
+  const int64_t n = d.n;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const double s = d.dense_aux[2];
+  for (int64_t r = 0; r < d.ucols; ++r) {
+    __syncthreads();
+    if (tid < kGT) {
+      sJ[tid] = J0 + tid < n ? df_split(d.U[(J0 + tid) * d.ucols + r] * d.uw[r] * s) : make_float2(0.f, 0.f);
+      sL[tid] = L0 + tid < n ? df_split(d.U[(L0 + tid) * d.ucols + r]) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) df_mac(sJ[2 * ty + a], sL[2 * tx + c], h[a][c], l[a][c]);
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int64_t j = J0 + 2 * ty + a, lc = L0 + 2 * tx + c;
+      if (j < n && lc < n) {
+        const float2 v = df_fast_sum(h[a][c], l[a][c]);
+        d.Kd[j * n + lc] = v;
+        if (tj != tl) d.Kd[lc * n + j] = v;
+      }
+    }
+}
+
+// From the CSR rows of R (when R is too large to keep densely): for every row i the block
+// gathers the row's entries that fall in its two column ranges (one side scaled by the row
+// weight) and adds their outer product.
+__global__ void __launch_bounds__(256) k_gram_tiles(Dev d) {
+  __shared__ float2 sJ[kGT], sL[kGT];
+  int64_t tj, tl;
+  tile_of_block(blockIdx.x, tj, tl);
   const int64_t J0 = tj * kGT, L0 = tl * kGT;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  float h[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, l[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
   for (int64_t i = 0; i < d.nR; ++i) {
-    if (tid < kGT) { sJ[tid] = 0.0; sL[tid] = 0.0; }
+    if (tid < kGT) {
+      sJ[tid] = make_float2(0.f, 0.f);
+      sL[tid] = make_float2(0.f, 0.f);
+    }
     __syncthreads();
-    const double w = d.omega[i];
+    const float2 w = d.wdf[i];
     int hj = 0, hl = 0;
-    if (w != 0.0) {
+    if (w.x != 0.f) {
       for (int64_t e = d.R_ptr[i] + tid; e < d.R_ptr[i + 1]; e += blockDim.x) {
         const int64_t c = d.R_idx[e];
-        const double v = d.R_val[e];
-        if (c >= J0 && c < J0 + kGT) { sJ[c - J0] = w * v; hj = 1; }
-        if (c >= L0 && c < L0 + kGT) { sL[c - L0] = v; hl = 1; }
+        if (c >= J0 && c < J0 + kGT) {
+          sJ[c - J0] = r_mul(w, df_split(d.R_val[e]));
+          hj = 1;
+        }
+        if (c >= L0 && c < L0 + kGT) {
+          sL[c - L0] = df_split(d.R_val[e]);
+          hl = 1;
+        }
       }
     }
     hj = __syncthreads_or(hj);
@@ -246,116 +475,82 @@ __global__ void __launch_bounds__(256) k_gram_tiles(Dev d) {
 #pragma unroll
       for (int a = 0; a < 2; ++a)
 #pragma unroll
-        for (int c = 0; c < 2; ++c) acc[a][c] = fma(sJ[2 * ty + a], sL[2 * tx + c], acc[a][c]);
+        for (int c = 0; c < 2; ++c) df_mac(sJ[2 * ty + a], sL[2 * tx + c], h[a][c], l[a][c]);
     }
     __syncthreads();
   }
-  for (int64_t r = 0; r < d.ucols; ++r) {
-    if (tid < kGT) {
-      sJ[tid] = J0 + tid < n ? d.U[(J0 + tid) * d.ucols + r] * d.uw[r] : 0.0;
-      sL[tid] = L0 + tid < n ? d.U[(L0 + tid) * d.ucols + r] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int c = 0; c < 2; ++c) acc[a][c] = fma(sJ[2 * ty + a], sL[2 * tx + c], acc[a][c]);
-    __syncthreads();
-  }
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const int64_t j = J0 + 2 * ty + a, l = L0 + 2 * tx + c;
-      if (j < n && l < n) {
-        d.Kd[j * n + l] = acc[a][c];
-        if (tj != tl) d.Kd[l * n + j] = acc[a][c];
-      }
-    }
+  gram_lowrank_store(d, J0, L0, tj, tl, sJ, sL, h, l);
 }
 
-// The same tiles from the dense copy of R: chunks of 32 rows of Rd staged in shared memory
-// (one side scaled by omega), 2 x 2 outputs per thread, rows summed in order; plus U W U^T.
+// From the dense copy of R (pairs): chunks of 32 rows of Rd staged in shared memory (one side
+// scaled by the row weight), rows summed in order.
 __global__ void __launch_bounds__(256) k_gram_gemm(Dev d) {
-  __shared__ double sA[kGT][kGT + 1], sB[kGT][kGT + 1];
+  __shared__ float2 sA[kGT][kGT + 1], sB[kGT][kGT + 1];
   const int64_t n = d.n;
-  const int64_t b = blockIdx.x;
-  int64_t tj = (int64_t)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
-  while ((tj + 1) * (tj + 2) / 2 <= b) ++tj;
-  while (tj * (tj + 1) / 2 > b) --tj;
-  const int64_t tl = b - tj * (tj + 1) / 2;
+  int64_t tj, tl;
+  tile_of_block(blockIdx.x, tj, tl);
   const int64_t J0 = tj * kGT, L0 = tl * kGT;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  float h[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, l[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
   for (int64_t i0 = 0; i0 < d.nR; i0 += kGT) {
     for (int t = tid; t < kGT * kGT; t += blockDim.x) {
       const int ii = t >> 5, cc = t & 31;
       const int64_t i = i0 + ii;
       const bool in = i < d.nR;
-      sA[ii][cc] = (in && J0 + cc < n) ? d.Rd[i * n + J0 + cc] * d.omega[i] : 0.0;
-      sB[ii][cc] = (in && L0 + cc < n) ? d.Rd[i * n + L0 + cc] : 0.0;
+      sA[ii][cc] = (in && J0 + cc < n) ? r_mul(d.Rd[i * n + J0 + cc], d.wdf[i]) : make_float2(0.f, 0.f);
+      sB[ii][cc] = (in && L0 + cc < n) ? d.Rd[i * n + L0 + cc] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
     for (int ii = 0; ii < kGT; ++ii) {
-      const double a0 = sA[ii][2 * ty], a1 = sA[ii][2 * ty + 1];
-      const double b0 = sB[ii][2 * tx], b1 = sB[ii][2 * tx + 1];
-      acc[0][0] = fma(a0, b0, acc[0][0]);
-      acc[0][1] = fma(a0, b1, acc[0][1]);
-      acc[1][0] = fma(a1, b0, acc[1][0]);
-      acc[1][1] = fma(a1, b1, acc[1][1]);
+      const float2 a0 = sA[ii][2 * ty], a1 = sA[ii][2 * ty + 1];
+      const float2 b0 = sB[ii][2 * tx], b1 = sB[ii][2 * tx + 1];
+      df_mac(a0, b0, h[0][0], l[0][0]);
+      df_mac(a0, b1, h[0][1], l[0][1]);
+      df_mac(a1, b0, h[1][0], l[1][0]);
+      df_mac(a1, b1, h[1][1], l[1][1]);
     }
     __syncthreads();
   }
-  for (int64_t r = 0; r < d.ucols; ++r) {
-    if (tid < kGT) {
-      sA[0][tid] = J0 + tid < n ? d.U[(J0 + tid) * d.ucols + r] * d.uw[r] : 0.0;
-      sB[0][tid] = L0 + tid < n ? d.U[(L0 + tid) * d.ucols + r] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int c = 0; c < 2; ++c) acc[a][c] = fma(sA[0][2 * ty + a], sB[0][2 * tx + c], acc[a][c]);
-    __syncthreads();
-  }
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const int64_t j = J0 + 2 * ty + a, l = L0 + 2 * tx + c;
-      if (j < n && l < n) {
-        d.Kd[j * n + l] = acc[a][c];
-        if (tj != tl) d.Kd[l * n + j] = acc[a][c];
-      }
-    }
+  gram_lowrank_store(d, J0, L0, tj, tl, &sA[0][0], &sB[0][0], h, l);
 }
 
-__global__ void k_densify_zero(double* Rd, int64_t total) {
+__global__ void k_densify_zero(float2* Rd, int64_t total) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
-    Rd[t] = 0.0;
+    Rd[t] = make_float2(0.f, 0.f);
 }
 
 __global__ void k_densify_fill(Dev d) {
   for (int64_t r = blockIdx.x; r < d.nR; r += gridDim.x)
-    for (int64_t e = d.R_ptr[r] + threadIdx.x; e < d.R_ptr[r + 1]; e += blockDim.x) d.Rd[r * d.n + d.R_idx[e]] = d.R_val[e];
+    for (int64_t e = d.R_ptr[r] + threadIdx.x; e < d.R_ptr[r + 1]; e += blockDim.x)
+      d.Rd[r * d.n + d.R_idx[e]] = df_split(d.R_val[e]);
 }
 
 cudaError_t launch_densify_R(const Dev& d, cudaStream_t st) {
-  if (!d.Rd || !d.nR) return cudaSuccess;
+  if (!d.Kd) return cudaSuccess;
+  cudaMemsetAsync(d.dense_aux, 0, 4 * sizeof(double), st);
+  k_dense_maxima<<<4 * 152, 256, 0, st>>>(d);
+  if (!d.Rd || !d.nR) return cudaGetLastError();
   k_densify_zero<<<1024, 256, 0, st>>>(d.Rd, d.nR * d.n);
   k_densify_fill<<<(int)std::min<int64_t>(d.nR, 4096), 256, 0, st>>>(d);
   return cudaGetLastError();
 }
 
-// Adds diag(h0 + sigma) and the explicit block Hs (each entry once: no conflicts).
+// Adds s (diag(h0 + sigma) + Hs) (each entry once: no conflicts), in float64 on the pair.
 __global__ void k_gram_diag_hs(Dev d) {
   const int64_t n = d.n;
+  const double s = d.dense_aux[2];
   for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
-    if (threadIdx.x == 0) d.Kd[j * n + j] += d.h0[j] + d.sigma[j];
+    if (threadIdx.x == 0) {
+      float2* kp = d.Kd + j * n + j;
+      *kp = df_split(df_value(kp->x, kp->y) + s * (d.h0[j] + d.sigma[j]));
+    }
     if (d.Hs_ptr) {
       __syncthreads();
-      for (int64_t e = d.Hs_ptr[j] + threadIdx.x; e < d.Hs_ptr[j + 1]; e += blockDim.x) d.Kd[j * n + d.Hs_idx[e]] += d.Hs_val[e];
+      for (int64_t e = d.Hs_ptr[j] + threadIdx.x; e < d.Hs_ptr[j + 1]; e += blockDim.x) {
+        float2* kp = d.Kd + j * n + d.Hs_idx[e];
+        *kp = df_split(df_value(kp->x, kp->y) + s * d.Hs_val[e]);
+      }
     }
     __syncthreads();
   }
@@ -363,17 +558,17 @@ __global__ void k_gram_diag_hs(Dev d) {
 
 cudaError_t launch_dense_build(const Dev& d, cudaStream_t st) {
   const int n = (int)d.n;
-  const size_t rowbytes = sizeof(double) * (size_t)n;
   const int64_t nt = (d.n + kGT - 1) / kGT;
+  k_dense_prep<<<1, 1024, 0, st>>>(d);
   if (d.Rd)
     k_gram_gemm<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, st>>>(d);
   else
     k_gram_tiles<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, st>>>(d);
   k_gram_diag_hs<<<(int)std::min<int64_t>(d.n, 4 * 152), 256, 0, st>>>(d);
-  cudaError_t e = launch_chol(d.Kd, d.n, nullptr, n, n, d.chol_diag, d.chol_rinv, &d.sc->chol_fail, st);
+  cudaError_t e = launch_chol<float2>(d.Kd, d.n, nullptr, n, n, d.chol_diag, d.chol_rdf, &d.sc->chol_fail, st);
   if (e != cudaSuccess) return e;
-  k_mirror<<<256, 256, 0, st>>>(d.Kd, d.n, nullptr, n);
-  (void)rowbytes;   // applied by triangular solves (k_dense_trsv), no explicit inverse
+  if (nt > 0) k_chol_tile_inv<<<(unsigned)nt, 256, 0, st>>>(d.Kd, d.n, n, d.chol_rdf, d.chol_tinv);
+  k_mirror<float2><<<256, 256, 0, st>>>(d.Kd, d.n, nullptr, n);
   return cudaGetLastError();
 }
 
@@ -381,9 +576,9 @@ cudaError_t launch_stiff_factor(const Dev& d, cudaStream_t st) {
   const int cap = d.stiff_cap;
   const size_t rowbytes = sizeof(double) * (size_t)cap;
   const int* ns = &d.sc->n_stiff;
-  cudaError_t e = launch_chol(d.G, cap, ns, 0, cap, d.chol_diag, d.chol_rinv, &d.sc->chol_fail, st);
+  cudaError_t e = launch_chol<double>(d.G, cap, ns, 0, cap, d.chol_diag, d.chol_rinv, &d.sc->chol_fail, st);
   if (e != cudaSuccess) return e;
-  k_mirror<<<64, 256, 0, st>>>(d.G, cap, ns, 0);
+  k_mirror<double><<<64, 256, 0, st>>>(d.G, cap, ns, 0);
   k_inv<<<std::min(cap, 4 * 152), 256, rowbytes, st>>>(d.G, cap, ns, 0, d.chol_rinv, d.Ginv, cap);
   return cudaGetLastError();
 }

@@ -1269,80 +1269,76 @@ __global__ void k_stiff_corr(Dev d, int init) {
   }
 }
 
-// Dense preconditioner apply by triangular solves: z = K^{-1} r with K = L L^T (L in the
-// lower triangle of Kd, L^T mirrored into the upper triangle, both row-major), forward
-// L y = r then backward L^T z = y, in blocks of 32 rows: the block's diagonal tile is staged
-// in shared memory by all threads, warp 0 solves it (lane i holds y_i, one shuffle per row,
-// multiplying by the saved reciprocal pivots), then all threads update the remaining rows
-// with the block's 32 columns.  One block of 1024 threads; y in shared memory (n <= 2048).
-// r^T z -> rz / beta; init: p = z.  (PCG with the exact factor converges in one or two
-// iterations, so this replaces forming K^{-1} once per IPM iteration.)
+// Dense preconditioner apply by triangular solves in double-float pairs: z = K^{-1} r with
+// s K = L L^T (the scaled K factored in pairs: L in the lower triangle of Kd, L^T mirrored
+// into the upper triangle, both row-major), forward L y = r' then backward L^T z' = y, where
+// r' = 2^-e r (2^e >= max |r|, exact) and z = s 2^e z'.  In blocks of 32 rows: the block's
+// 32 values come from the inverse of its diagonal tile (one warp per row, a shuffle-tree sum
+// of pairs: no row-by-row chain), then all threads update the remaining rows with the block's
+// 32 columns while the next tile's inverse is staged in shared memory.  One block of 1024
+// threads; y in shared memory (n <= 2048).  r^T z -> rz / beta; init: p = z.  (PCG with the
+// factor converges in one or two iterations, so this replaces forming K^{-1} once per IPM
+// iteration.)
 __global__ void __launch_bounds__(1024) k_dense_trsv(Dev d, int init) {
-  extern __shared__ double y[];
+  extern __shared__ float2 y[];
   __shared__ double sh[32];
-  __shared__ double Lt[32][33];
-  __shared__ double rs[32];
+  __shared__ float2 Li[2][32][33];
+  __shared__ float2 yk[32];
   if (!init && d.sc->cg_done) return;
   const int n = (int)d.n;
-  const double* K = d.Kd;
+  const int nt = (n + 31) / 32;
+  const float2* K = d.Kd;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int i = tid; i < n; i += blockDim.x) y[i] = d.r[i];
-  // forward: L y = r
-  for (int kb = 0; kb < n; kb += 32) {
-    const int bs = min(32, n - kb);
-    // tile rows kb + warp (lower part; identity padding past n), reciprocal pivots
-    Lt[warp][lane] = (warp < bs && lane < bs) ? (lane <= warp ? K[(int64_t)(kb + warp) * n + kb + lane] : 0.0)
-                                              : (warp == lane ? 1.0 : 0.0);
-    if (warp == 0) rs[lane] = lane < bs ? d.chol_rinv[kb + lane] : 1.0;
+  double rmax = 0.0;
+  for (int i = tid; i < n; i += blockDim.x) rmax = fmax(rmax, fabs(d.r[i]));
+  rmax = block_reduce<1>(rmax, sh);
+  int er = 0;
+  if (rmax > 0.0 && isfinite(rmax)) frexp(rmax, &er);
+  const double rs = ldexp(1.0, -er);
+  for (int i = tid; i < n; i += blockDim.x) y[i] = df_split(d.r[i] * rs);
+  if (nt > 0) Li[0][warp][lane] = d.chol_tinv[warp * 32 + lane];
+  __syncthreads();
+  // forward: L y = r'
+  for (int t = 0; t < nt; ++t) {
+    const int kb = t * 32, bs = min(32, n - kb), cur = t & 1;
+    float h = 0.f, l = 0.f;
+    if (lane < bs) df_mac(Li[cur][warp][lane], y[kb + lane], h, l);
+    df_group_pair<32>(h, l);
+    if (lane == 0) yk[warp] = df_fast_sum(h, l);
     __syncthreads();
-    if (warp == 0) {
-      double yl = lane < bs ? y[kb + lane] : 0.0;
-#pragma unroll 8
-      for (int c = 0; c < 32; ++c) {
-        if (lane == c) yl *= rs[c];
-        const double v = __shfl_sync(0xffffffffu, yl, c);
-        if (lane > c) yl = fma(-Lt[lane][c], v, yl);
-      }
-      if (lane < bs) y[kb + lane] = yl;
-    }
-    __syncthreads();
+    if (t + 1 < nt) Li[cur ^ 1][warp][lane] = d.chol_tinv[(int64_t)(t + 1) * 1024 + warp * 32 + lane];
+    if (tid < bs) y[kb + tid] = yk[tid];
     for (int r = kb + bs + tid; r < n; r += blockDim.x) {
-      const double* Lr = K + (int64_t)r * n + kb;
-      double acc = 0.0;
-      for (int c = 0; c < bs; ++c) acc = fma(Lr[c], y[kb + c], acc);
-      y[r] -= acc;
+      const float2* Lr = K + (int64_t)r * n + kb;
+      float ah = 0.f, al = 0.f;
+      for (int c = 0; c < bs; ++c) df_mac(Lr[c], yk[c], ah, al);
+      y[r] = df_sub_sum(y[r], ah, al);
     }
     __syncthreads();
   }
-  // backward: L^T z = y, with L^T row i in the upper triangle of row i
-  for (int kb = ((n - 1) / 32) * 32; kb >= 0; kb -= 32) {
-    const int bs = min(32, n - kb);
-    Lt[warp][lane] = (warp < bs && lane < bs) ? (lane <= warp ? K[(int64_t)(kb + warp) * n + kb + lane] : 0.0)
-                                              : (warp == lane ? 1.0 : 0.0);
-    if (warp == 0) rs[lane] = lane < bs ? d.chol_rinv[kb + lane] : 1.0;
+  // backward: L^T z' = y, with L^T row i in the upper triangle of row i; tile nt - 1's
+  // inverse is still staged
+  for (int t = nt - 1; t >= 0; --t) {
+    const int kb = t * 32, bs = min(32, n - kb), cur = t & 1;
+    float h = 0.f, l = 0.f;
+    if (lane < bs) df_mac(Li[cur][lane][warp], y[kb + lane], h, l);
+    df_group_pair<32>(h, l);
+    if (lane == 0) yk[warp] = df_fast_sum(h, l);
     __syncthreads();
-    if (warp == 0) {
-      double yl = lane < bs ? y[kb + lane] : 0.0;
-#pragma unroll 8
-      for (int c = 31; c >= 0; --c) {
-        if (lane == c) yl *= rs[c];
-        const double v = __shfl_sync(0xffffffffu, yl, c);
-        if (lane < c) yl = fma(-Lt[c][lane], v, yl);
-      }
-      if (lane < bs) y[kb + lane] = yl;
-    }
-    __syncthreads();
+    if (t > 0) Li[cur ^ 1][warp][lane] = d.chol_tinv[(int64_t)(t - 1) * 1024 + warp * 32 + lane];
+    if (tid < bs) y[kb + tid] = yk[tid];
     for (int r = tid; r < kb; r += blockDim.x) {
-      const double* Ur = K + (int64_t)r * n + kb;
-      double acc = 0.0;
-      for (int c = 0; c < bs; ++c) acc = fma(Ur[c], y[kb + c], acc);
-      y[r] -= acc;
+      const float2* Ur = K + (int64_t)r * n + kb;
+      float ah = 0.f, al = 0.f;
+      for (int c = 0; c < bs; ++c) df_mac(Ur[c], yk[c], ah, al);
+      y[r] = df_sub_sum(y[r], ah, al);
     }
     __syncthreads();
   }
+  const double zs = d.dense_aux[2] * ldexp(1.0, er);
   double rz = 0.0;
   for (int j = tid; j < n; j += blockDim.x) {
-    const double zj = y[j];
+    const double zj = df_value(y[j].x, y[j].y) * zs;
     d.z[j] = zj;
     if (init) {
       d.p[j] = zj;
@@ -1400,7 +1396,7 @@ __global__ void k_cg_p(Dev d, cudaGraphConditionalHandle h, int set_cond) {
 cudaError_t launch_cg_init(const Dev& d, const Geo& g, int precond, cudaStream_t st) {
   if (precond == PC_BLOCK32) return launch_block_apply(d, 1, st);
   if (precond == PC_DENSE) {
-    k_dense_trsv<<<1, 1024, sizeof(double) * d.n, st>>>(d, 1);
+    k_dense_trsv<<<1, 1024, sizeof(float2) * d.n, st>>>(d, 1);
   } else if (precond == PC_JACOBI_LR) {
     k_cg_init_diag<<<g.eN, kBlock, 0, st>>>(d);
     const int gs = (d.stiff_cap + 7) / 8;
@@ -1437,7 +1433,7 @@ cudaError_t launch_cg_body(const Dev& d, const Geo& g, int precond, cudaGraphCon
     launch_block_apply(d, 0, st);
   } else if (precond == PC_DENSE) {
     k_cg_update<2><<<g.eN, kBlock, 0, st>>>(d);
-    k_dense_trsv<<<1, 1024, sizeof(double) * d.n, st>>>(d, 0);
+    k_dense_trsv<<<1, 1024, sizeof(float2) * d.n, st>>>(d, 0);
   } else if (precond == PC_JACOBI_LR) {
     k_cg_update<1><<<g.eN, kBlock, 0, st>>>(d);
     const int gs = (d.stiff_cap + 7) / 8;

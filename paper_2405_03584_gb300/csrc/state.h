@@ -63,10 +63,14 @@ struct Dev {
   int stiff_cap;
   unsigned int* hist;          // kHistBins
   // dense preconditioner (n x n), nullptr if not allocated
-  double* Kd;                  // n x n: the condensed matrix, then its Cholesky factor (L and L^T)
-  double* Rd;                  // nR x n: R as a dense matrix (when it is small enough), or nullptr
+  float2* Kd;                  // n x n pairs: the scaled condensed matrix, then its Cholesky factor (L and L^T)
+  float2* Rd;                  // nR x n pairs: R as a dense matrix (when it is small enough), or nullptr
+  float2* wdf;                 // nR pairs: the scaled row weights of the current dense K
+  double* dense_aux;           // 4: max R^2, max |Hs| (bit patterns), the scale of K
   double* chol_diag;           // max(n_dense, stiff_cap): original diagonal during a factorisation
   double* chol_rinv;           // max(n_dense, stiff_cap): 1 / L_kk of the last factor
+  float2* chol_rdf;            // dense only: 1 / L_kk of the dense factor (pairs)
+  float2* chol_tinv;           // dense only: inverses of the dense factor's 32 x 32 diagonal tiles
   // double-float operator (storage ST_F64 with options.op_arith = DF32): the values of R and
   // R^T as (hi, lo) float32 pairs, the PCG direction p and the rows-pass result v likewise;
   // the FP64 copies stay for the residuals, the start point and the stiff-row correction

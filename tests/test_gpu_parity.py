@@ -100,6 +100,10 @@ def test_newton_direction_and_steps(name, make, precond):
     ref = O.newton_direction(qp, it, mu)
     rep = d["report"]
     assert rep["converged"] == 1, rep
+    if precond == "dense":
+        # the factor of the whole condensed matrix (double-float pairs, about 48 bits) leaves
+        # PCG a few iterations to 1e-12; more would mean a broken factor or solve
+        assert rep["iters"] <= 4, rep
     # dx: PCG stops at ||r|| <= 1e-12 ||rhs||; the error is bounded by cond(K) times that
     K, rhs, _, _ = O.condensed_system(qp, it, O.residuals(qp, it, mu))
     res = np.linalg.norm(K @ d["dx"] - rhs) / np.linalg.norm(rhs)
@@ -115,6 +119,25 @@ def test_newton_direction_and_steps(name, make, precond):
         ap, ad = s.step_lengths(ref.x, ref.s, ref.y, ref.zl, ref.zu, tau)
         ap0, ad0 = O.step_lengths(qp, it, ref, tau)
         assert ap == pytest.approx(ap0, rel=1e-13) and ad == pytest.approx(ad0, rel=1e-13)
+    s.close()
+
+
+def test_dense_preconditioner_from_csr_rows():
+    """R too large to keep densely (nR n above 2^25 entries): the dense preconditioner forms
+    K from R's CSR rows (one pass over the rows per tile) instead of the dense copy; the
+    Newton direction and its PCG iteration count as with the dense copy."""
+    p = W.rt_qp(n=300, V=120_000, density=0.02, seed=8)
+    assert p["V"] * p["n"] > (32 << 20)
+    s, qp = _load(p, precond="dense", max_cg=20000)
+    it = _iterate(p, qp, 12, spread=1.0)
+    mu = 0.05
+    s.set_iterate(it.x, it.s, it.y, it.zl, it.zu, mu)
+    d = s.newton_direction(eta=1e-12)
+    rep = d["report"]
+    assert rep["converged"] == 1 and rep["iters"] <= 4, rep
+    ref = O.newton_direction(qp, it, mu)
+    err = lambda a, b: np.abs(a - b).max() / (np.abs(b).max() + 1e-300)
+    assert err(d["dx"], ref.x) <= 1e-7 and err(d["dy"], ref.y) <= 1e-7
     s.close()
 
 
