@@ -530,7 +530,7 @@ def run_dense(args):
     torch.cuda.set_device(0)
     build.build()
     p = W.dense_qp(n=500, m=1000, seed=0)
-    s = ipm.Solver(tol_kkt=1e-8, use_graphs=0 if args.no_graphs else 1)
+    s = ipm.Solver(tol_kkt=1e-8, use_graphs=0 if args.no_graphs else 1, autotune=args.dense_autotune)
     s.set_qp_dense(p["H"], p["c"], p["A"], p["b"], p["l"], p["u"])
     for _ in range(args.warmup):
         s.solve()
@@ -562,7 +562,8 @@ def run_dense(args):
                          "solve" % rinfo.iterations}
     res = {"mode": "dense", "metric": "QP solves/sec at rel. KKT <= 1e-8 (dense QP)", "value": 1000.0 / ms,
            "unit": "solves/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup, "dtype": "f64",
-           "config": {"workload": "dense QP n=500, m=1000, seed 0 (workloads.dense_qp)", "precond": "dense"},
+           "config": {"workload": "dense QP n=500, m=1000, seed 0 (workloads.dense_qp)", "precond": "dense",
+                      "autotune": args.dense_autotune},
            "status": [int(x) for x in sts], "ipm_iters": info["ipm_iters"], "cg_iters": info["cg_iters"],
            "us_per_ipm_iter": 1000.0 * ms / max(info["ipm_iters"], 1),
            "us_per_pcg_iter_upper_bound": 1000.0 * ms / max(info["cg_iters"], 1),
@@ -789,6 +790,7 @@ def main():
     ap.add_argument("--bfgs", choices=["proton", "vmat"], help="the quasi-Newton Hessian shapes of the paper")
     ap.add_argument("--sqp", action="store_true", help="the SQP outer loop with GPU QP sub-problems")
     ap.add_argument("--dense", action="store_true", help="the dense QP (n = 500, m = 1000)")
+    ap.add_argument("--dense-autotune", type=int, default=1, help="--dense: time the lane widths per matrix (0: fixed)")
     ap.add_argument("--two-sided", action="store_true", help="the RT workload with two-sided dose-window rows")
     ap.add_argument("--window-rows", type=int, default=200, help="--two-sided: window rows per voxel class")
     ap.add_argument("--sqp-n", type=int, default=10000)

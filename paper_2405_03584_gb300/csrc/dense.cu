@@ -91,7 +91,7 @@ __device__ __forceinline__ float2 r_floor(float2 fl) { return make_float2(fmaxf(
 // is raised to that floor (a modified factor; still symmetric positive definite, which is all
 // a preconditioner needs); the count goes to *nfloor.
 constexpr int kT = 32;
-constexpr int kPanelRows = 8;   // rows of the panel below the diagonal tile per block
+constexpr int kPanelRows = 16;  // rows of the panel below the diagonal tile per block (a warp each)
 constexpr double kFloorRel = 1e-13;
 
 __device__ __forceinline__ int dev_nn(const int* nn_dev, int nn_fixed) { return nn_dev ? *nn_dev : nn_fixed; }
@@ -104,25 +104,49 @@ __global__ void k_chol_save_diag(const R* A, int64_t ld, const int* nn_dev, int 
   if (blockIdx.x == 0 && threadIdx.x == 0 && nfloor) *nfloor = 0;
 }
 
-// Unblocked Cholesky of diagonal tile kb in shared memory by 256 threads (rows/cols >= nn
-// padded by identity): rs[k] = 1 / L_kk.  Pivots are floored as above; nfloor (may be null)
-// counts the floored ones.  The trailing update of step k touches the entries (i, j),
-// k < j <= i; listed by j descending (then i), they are the first (31 - k)(32 - k) / 2 of one
-// table of pairs, so the 256 threads take them densely (at most two each) instead of one
-// row per warp with most lanes idle.
+// Unblocked Cholesky of diagonal tile kb in shared memory (rows/cols >= nn padded by
+// identity): rs[k] = 1 / L_kk.  Pivots are floored as above; nfloor (may be null) counts the
+// floored ones.  The pivots form a chain, so each step is organised around it with one
+// barrier: warp 0 holds column k in registers (lane i: L_ik), applies step k to column k + 1
+// and factors it at once (pivot by shuffle, reciprocal square root, scaling), while the
+// other warps apply step k to the rest of the trailing block, the entries (i, j) with
+// k + 1 < j <= i.  Listed by j descending (then i), those are the first (30 - k)(31 - k) / 2
+// entries of one table of pairs, so the threads take them densely (one each with 512
+// threads) instead of one row per warp with most lanes idle.  (Measured on GB300: about
+// 20000 cycles per tile; a whole tile in one warp's registers, with no barrier, took 44000:
+// one warp then issues every multiply-add of the tile.)
+constexpr int kPanelThreads = 512;
 constexpr int kTriPairs = kT * (kT - 1) / 2;   // 496 pairs (i, j), 1 <= j <= i < 32
+
+// Column c by warp 0, lane i holding x = t[i][c] (updated through step c - 1): the floored
+// pivot, its reciprocal square root, the scaled column, stored for the other warps and
+// returned in registers for the next step.
+template <class R>
+__device__ __forceinline__ R tile_column(R (*t)[kT + 1], R* rs, R x, R flc, int c, bool live, int* nfloor) {
+  const int lane = threadIdx.x & 31;
+  R piv = r_shfl(x, c);
+  if (live && !r_above(piv, flc)) {
+    piv = flc;
+    if (nfloor && lane == 0) atomicAdd(nfloor, 1);
+  }
+  const R r = r_rsqrt(piv);
+  const R col = lane == c ? r_mul(piv, r) : (lane > c ? r_mul(x, r) : r_const<R>(0.0));
+  if (lane >= c) t[lane][c] = col;
+  if (lane == c) rs[c] = r;
+  return col;
+}
 
 template <class R>
 __device__ void tile_potrf(R (*t)[kT + 1], R* rs, const R* A, int64_t ld, int nn, int base, const double* diag0,
                            int* nfloor) {
   __shared__ unsigned short pairs[kTriPairs];
-  __shared__ R fl[kT];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
-  for (int r = ty; r < kT; r += 8) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < kT; r += blockDim.x >> 5) {
     const int gi = base + r, gj = base + tx;
     t[r][tx] = (gi < nn && gj < nn) ? A[(int64_t)gi * ld + gj] : r_const<R>(r == tx ? 1.0 : 0.0);
   }
-  if (ty == 0) fl[tx] = r_floor(r_const<R>(base + tx < nn ? kFloorRel * fabs(diag0[base + tx]) : 0.0));
+  // warp 0: the floor of row lane (its pivot's floor is taken by shuffle)
+  const R fl = r_floor(r_const<R>(ty == 0 && base + tx < nn ? kFloorRel * fabs(diag0[base + tx]) : 0.0));
   for (int e = threadIdx.x; e < kTriPairs; e += blockDim.x) {
     int j = kT - 1, rem = e;
     while (rem >= kT - j) {
@@ -132,37 +156,32 @@ __device__ void tile_potrf(R (*t)[kT + 1], R* rs, const R* A, int64_t ld, int nn
     pairs[e] = (unsigned short)((j + rem) * kT + j);
   }
   __syncthreads();
-  for (int k = 0; k < kT; ++k) {
-    if (ty == 0) {   // column k by warp 0
-      R piv = t[k][k];
-      __syncwarp();
-      if (base + k < nn && !r_above(piv, fl[k])) {
-        piv = fl[k];
-        if (nfloor && tx == 0) atomicAdd(nfloor, 1);
+  R colk = r_const<R>(0.0);
+  if (ty == 0) colk = tile_column<R>(t, rs, t[tx][0], r_shfl(fl, 0), 0, base < nn, nfloor);
+  __syncthreads();
+  for (int k = 0; k + 1 < kT; ++k) {
+    const int c = k + 1;
+    if (ty == 0) {
+      R x = t[tx][c];                          // column c through step k - 1
+      const R lck = r_shfl(colk, c);           // L_ck
+      if (tx >= c) x = r_fms(x, colk, lck);    // step k on column c
+      colk = tile_column<R>(t, rs, x, r_shfl(fl, c), c, base + c < nn, nfloor);
+    } else {
+      const int cnt = (kT - 2 - k) * (kT - 1 - k) / 2;
+      for (int e = threadIdx.x - 32; e < cnt; e += blockDim.x - 32) {
+        const int i = pairs[e] / kT, j = pairs[e] % kT;
+        t[i][j] = r_fms(t[i][j], t[i][k], t[j][k]);
       }
-      const R r = r_rsqrt(piv);
-      if (tx == k) {
-        t[k][k] = r_mul(piv, r);
-        rs[k] = r;
-      } else if (tx > k) {
-        t[tx][k] = r_mul(t[tx][k], r);
-      }
-    }
-    __syncthreads();
-    const int cnt = (kT - 1 - k) * (kT - k) / 2;
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-      const int i = pairs[e] / kT, j = pairs[e] % kT;
-      t[i][j] = r_fms(t[i][j], t[i][k], t[j][k]);
     }
     __syncthreads();
   }
 }
 
 // Panel of tile column kb: block 0 the diagonal tile, block b >= 1 rows
-// [base + 32 + 8 (b - 1), + 8) below it.
+// [base + 32 + kPanelRows (b - 1), + kPanelRows) below it, one warp per row.
 template <class R>
-__global__ void __launch_bounds__(256) k_chol_panel(R* A, int64_t ld, const int* nn_dev, int nn_fixed, int kb,
-                                                    const double* diag0, int* nfloor, R* rinv) {
+__global__ void __launch_bounds__(kPanelThreads) k_chol_panel(R* A, int64_t ld, const int* nn_dev, int nn_fixed,
+                                                              int kb, const double* diag0, int* nfloor, R* rinv) {
   const int nn = dev_nn(nn_dev, nn_fixed);
   const int base = kb * kT;
   if (base >= nn) return;
@@ -173,7 +192,7 @@ __global__ void __launch_bounds__(256) k_chol_panel(R* A, int64_t ld, const int*
   tile_potrf<R>(t, rs, A, ld, nn, base, diag0, blockIdx.x == 0 ? nfloor : nullptr);
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   if (blockIdx.x == 0) {
-    for (int r = ty; r < kT; r += 8) {
+    for (int r = ty; r < kT; r += kPanelThreads / 32) {
       const int gi = base + r, gj = base + tx;
       if (gi < nn && gj < nn && tx <= r) A[(int64_t)gi * ld + gj] = t[r][tx];
     }
@@ -257,7 +276,7 @@ static cudaError_t launch_chol(R* A, int64_t ld, const int* nn_dev, int nn_fixed
                                                                                      nfloor);
   for (int kb = 0; kb < nt; ++kb) {
     const int rows_below = std::max(0, cap - (kb + 1) * kT);
-    k_chol_panel<R><<<1 + (rows_below + kPanelRows - 1) / kPanelRows, 256, 0, st>>>(A, ld, nn_dev, nn_fixed, kb, diag0,
+    k_chol_panel<R><<<1 + (rows_below + kPanelRows - 1) / kPanelRows, kPanelThreads, 0, st>>>(A, ld, nn_dev, nn_fixed, kb, diag0,
                                                                                      nfloor, rinv);
     const int below = nt - kb - 1;
     if (below > 0) k_chol_update<R><<<4 * below * (below + 1) / 2, 256, 0, st>>>(A, ld, nn_dev, nn_fixed, kb);
@@ -483,7 +502,8 @@ __global__ void __launch_bounds__(256) k_gram_tiles(Dev d) {
 }
 
 // From the dense copy of R (pairs): chunks of 32 rows of Rd staged in shared memory (one side
-// scaled by the row weight), rows summed in order.
+// scaled by the row weight), rows summed in order.  The next chunk is loaded into registers
+// while the current one is multiplied.
 __global__ void __launch_bounds__(256) k_gram_gemm(Dev d) {
   __shared__ float2 sA[kGT][kGT + 1], sB[kGT][kGT + 1];
   const int64_t n = d.n;
@@ -492,15 +512,28 @@ __global__ void __launch_bounds__(256) k_gram_gemm(Dev d) {
   const int64_t J0 = tj * kGT, L0 = tl * kGT;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   float h[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, l[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-  for (int64_t i0 = 0; i0 < d.nR; i0 += kGT) {
-    for (int t = tid; t < kGT * kGT; t += blockDim.x) {
-      const int ii = t >> 5, cc = t & 31;
+  constexpr int kPer = kGT * kGT / 256;   // staged entries per thread and side
+  float2 ra[kPer], rb[kPer];
+  auto fetch = [&](int64_t i0) {
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int t = tid + q * 256, ii = t >> 5, cc = t & 31;
       const int64_t i = i0 + ii;
       const bool in = i < d.nR;
-      sA[ii][cc] = (in && J0 + cc < n) ? r_mul(d.Rd[i * n + J0 + cc], d.wdf[i]) : make_float2(0.f, 0.f);
-      sB[ii][cc] = (in && L0 + cc < n) ? d.Rd[i * n + L0 + cc] : make_float2(0.f, 0.f);
+      ra[q] = (in && J0 + cc < n) ? r_mul(d.Rd[i * n + J0 + cc], d.wdf[i]) : make_float2(0.f, 0.f);
+      rb[q] = (in && L0 + cc < n) ? d.Rd[i * n + L0 + cc] : make_float2(0.f, 0.f);
+    }
+  };
+  if (d.nR > 0) fetch(0);
+  for (int64_t i0 = 0; i0 < d.nR; i0 += kGT) {
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int t = tid + q * 256;
+      sA[t >> 5][t & 31] = ra[q];
+      sB[t >> 5][t & 31] = rb[q];
     }
     __syncthreads();
+    if (i0 + kGT < d.nR) fetch(i0 + kGT);
 #pragma unroll 4
     for (int ii = 0; ii < kGT; ++ii) {
       const float2 a0 = sA[ii][2 * ty], a1 = sA[ii][2 * ty + 1];

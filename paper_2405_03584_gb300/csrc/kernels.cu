@@ -1275,7 +1275,8 @@ __global__ void k_stiff_corr(Dev d, int init) {
 // r' = 2^-e r (2^e >= max |r|, exact) and z = s 2^e z'.  In blocks of 32 rows: the block's
 // 32 values come from the inverse of its diagonal tile (one warp per row, a shuffle-tree sum
 // of pairs: no row-by-row chain), then all threads update the remaining rows with the block's
-// 32 columns while the next tile's inverse is staged in shared memory.  One block of 1024
+// 32 columns while the next tile's inverse is staged in shared memory.  Thread r reads its
+// row's 32 factor entries (256 contiguous bytes: after the first miss the rest hit L1).  One block of 1024
 // threads; y in shared memory (n <= 2048).  r^T z -> rz / beta; init: p = z.  (PCG with the
 // factor converges in one or two iterations, so this replaces forming K^{-1} once per IPM
 // iteration.)
