@@ -283,6 +283,7 @@ void carve_state(Carver& cv, Dev& d, int64_t n, int64_t m, int64_t nR, int stiff
   d.dense_aux = dense ? cv.take<double>(4) : nullptr;
   d.chol_diag = cv.take<double>(std::max<int64_t>(dense ? n : 0, stiff_cap));
   d.chol_rinv = cv.take<double>(std::max<int64_t>(dense ? n : 0, stiff_cap));
+  d.chol_tiles = cv.take<double>(std::max<int64_t>(dense ? (n + 31) / 32 : 0, (stiff_cap + 31) / 32) * 1024);
   d.chol_rdf = dense ? cv.take<float2>(n) : nullptr;
   d.chol_tinv = dense ? cv.take<float2>((n + 31) / 32 * 1024) : nullptr;
   d.storage = storage;

@@ -178,10 +178,14 @@ __device__ void tile_potrf(R (*t)[kT + 1], R* rs, const R* A, int64_t ld, int nn
 }
 
 // Panel of tile column kb: block 0 the diagonal tile, block b >= 1 rows
-// [base + 32 + kPanelRows (b - 1), + kPanelRows) below it, one warp per row.
+// [base + 32 + kPanelRows (b - 1), + kPanelRows) below it, one warp per row.  Every block loads
+// the diagonal tile from A, and a block may start after block 0 has finished (when other
+// kernels hold SMs), so block 0 leaves A's diagonal tile alone: its factor goes to tiles[kb]
+// and the last pass (k_mirror) installs it.
 template <class R>
 __global__ void __launch_bounds__(kPanelThreads) k_chol_panel(R* A, int64_t ld, const int* nn_dev, int nn_fixed,
-                                                              int kb, const double* diag0, int* nfloor, R* rinv) {
+                                                              int kb, const double* diag0, int* nfloor, R* rinv,
+                                                              R* tiles) {
   const int nn = dev_nn(nn_dev, nn_fixed);
   const int base = kb * kT;
   if (base >= nn) return;
@@ -192,10 +196,8 @@ __global__ void __launch_bounds__(kPanelThreads) k_chol_panel(R* A, int64_t ld, 
   tile_potrf<R>(t, rs, A, ld, nn, base, diag0, blockIdx.x == 0 ? nfloor : nullptr);
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   if (blockIdx.x == 0) {
-    for (int r = ty; r < kT; r += kPanelThreads / 32) {
-      const int gi = base + r, gj = base + tx;
-      if (gi < nn && gj < nn && tx <= r) A[(int64_t)gi * ld + gj] = t[r][tx];
-    }
+    for (int r = ty; r < kT; r += kPanelThreads / 32)
+      tiles[(int64_t)kb * kT * kT + r * kT + tx] = tx <= r ? t[r][tx] : r_const<R>(0.0);
     if (ty == 0 && base + tx < nn) rinv[base + tx] = rs[tx];
     return;
   }
@@ -266,21 +268,41 @@ __global__ void __launch_bounds__(256) k_chol_update(R* A, int64_t ld, const int
   }
 }
 
+// Last pass of the factorisation: the factored diagonal tiles from tiles[] (L below and on
+// the diagonal, L^T above), and the upper triangle <- L^T elsewhere, so that column p of L is
+// row p of the upper part.  Only diagonal tiles and the upper triangle are written; the lower
+// triangle outside the diagonal tiles is only read.
+template <class R>
+__global__ void k_mirror(R* A, int64_t ld, const int* nn_dev, int nn_fixed, const R* tiles) {
+  const int nn = nn_dev ? *nn_dev : nn_fixed;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)nn * nn; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = t / nn, i = t % nn;
+    if (p / kT == i / kT) {
+      const R* tile = tiles + (p / kT) * kT * kT;
+      const int a = (int)(p % kT), b = (int)(i % kT);
+      A[p * ld + i] = b <= a ? tile[a * kT + b] : tile[b * kT + a];
+    } else if (i > p) {
+      A[p * ld + i] = A[i * ld + p];
+    }
+  }
+}
+
 // Captures the whole factorisation for an nn of at most cap (tile columns and panel rows
 // beyond the device nn exit immediately).
 template <class R>
 static cudaError_t launch_chol(R* A, int64_t ld, const int* nn_dev, int nn_fixed, int cap, double* diag0, R* rinv,
-                               int* nfloor, cudaStream_t st) {
+                               R* tiles, int* nfloor, cudaStream_t st) {
   const int nt = (cap + kT - 1) / kT;
   k_chol_save_diag<R><<<std::max(1, std::min(64, (cap + 255) / 256)), 256, 0, st>>>(A, ld, nn_dev, nn_fixed, diag0,
                                                                                      nfloor);
   for (int kb = 0; kb < nt; ++kb) {
     const int rows_below = std::max(0, cap - (kb + 1) * kT);
-    k_chol_panel<R><<<1 + (rows_below + kPanelRows - 1) / kPanelRows, kPanelThreads, 0, st>>>(A, ld, nn_dev, nn_fixed, kb, diag0,
-                                                                                     nfloor, rinv);
+    k_chol_panel<R><<<1 + (rows_below + kPanelRows - 1) / kPanelRows, kPanelThreads, 0, st>>>(
+        A, ld, nn_dev, nn_fixed, kb, diag0, nfloor, rinv, tiles);
     const int below = nt - kb - 1;
     if (below > 0) k_chol_update<R><<<4 * below * (below + 1) / 2, 256, 0, st>>>(A, ld, nn_dev, nn_fixed, kb);
   }
+  k_mirror<R><<<cap > 256 ? 256 : 64, 256, 0, st>>>(A, ld, nn_dev, nn_fixed, tiles);
   return cudaGetLastError();
 }
 
@@ -314,16 +336,6 @@ __global__ void __launch_bounds__(256) k_chol_tile_inv(const float2* A, int64_t 
     __syncthreads();
   }
   for (int r = ty; r < kT; r += 8) tinv[(int64_t)blockIdx.x * kT * kT + r * kT + tx] = X[r][tx];
-}
-
-// Upper triangle <- L^T so that column p of L is row p of the upper part.
-template <class R>
-__global__ void k_mirror(R* A, int64_t ld, const int* nn_dev, int nn_fixed) {
-  const int nn = nn_dev ? *nn_dev : nn_fixed;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)nn * nn; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = t / nn, i = t % nn;
-    if (i > p) A[p * ld + i] = A[i * ld + p];
-  }
 }
 
 // Column c of A^{-1} = L^{-T} L^{-1} e_c (float64): forward sweep reads row p of the upper part
@@ -598,10 +610,10 @@ cudaError_t launch_dense_build(const Dev& d, cudaStream_t st) {
   else
     k_gram_tiles<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, st>>>(d);
   k_gram_diag_hs<<<(int)std::min<int64_t>(d.n, 4 * 152), 256, 0, st>>>(d);
-  cudaError_t e = launch_chol<float2>(d.Kd, d.n, nullptr, n, n, d.chol_diag, d.chol_rdf, &d.sc->chol_fail, st);
+  cudaError_t e = launch_chol<float2>(d.Kd, d.n, nullptr, n, n, d.chol_diag, d.chol_rdf,
+                                      reinterpret_cast<float2*>(d.chol_tiles), &d.sc->chol_fail, st);
   if (e != cudaSuccess) return e;
   if (nt > 0) k_chol_tile_inv<<<(unsigned)nt, 256, 0, st>>>(d.Kd, d.n, n, d.chol_rdf, d.chol_tinv);
-  k_mirror<float2><<<256, 256, 0, st>>>(d.Kd, d.n, nullptr, n);
   return cudaGetLastError();
 }
 
@@ -609,9 +621,9 @@ cudaError_t launch_stiff_factor(const Dev& d, cudaStream_t st) {
   const int cap = d.stiff_cap;
   const size_t rowbytes = sizeof(double) * (size_t)cap;
   const int* ns = &d.sc->n_stiff;
-  cudaError_t e = launch_chol<double>(d.G, cap, ns, 0, cap, d.chol_diag, d.chol_rinv, &d.sc->chol_fail, st);
+  cudaError_t e = launch_chol<double>(d.G, cap, ns, 0, cap, d.chol_diag, d.chol_rinv, d.chol_tiles,
+                                      &d.sc->chol_fail, st);
   if (e != cudaSuccess) return e;
-  k_mirror<double><<<64, 256, 0, st>>>(d.G, cap, ns, 0);
   k_inv<<<std::min(cap, 4 * 152), 256, rowbytes, st>>>(d.G, cap, ns, 0, d.chol_rinv, d.Ginv, cap);
   return cudaGetLastError();
 }

@@ -69,6 +69,8 @@ struct Dev {
   double* dense_aux;           // 4: max R^2, max |Hs| (bit patterns), the scale of K
   double* chol_diag;           // max(n_dense, stiff_cap): original diagonal during a factorisation
   double* chol_rinv;           // max(n_dense, stiff_cap): 1 / L_kk of the last factor
+  double* chol_tiles;          // factored 32 x 32 diagonal tiles of the last factor (pairs for the dense K),
+                               // installed into the factor by its last pass
   float2* chol_rdf;            // dense only: 1 / L_kk of the dense factor (pairs)
   float2* chol_tinv;           // dense only: inverses of the dense factor's 32 x 32 diagonal tiles
   // double-float operator (storage ST_F64 with options.op_arith = DF32): the values of R and

@@ -128,3 +128,53 @@ def test_serving_mix_equals_alone(storage):
             ref, info = O.solve(qp, tol=1e-10)
             assert info.status == "optimal"
             assert abs(O.objective(qp, x) - O.objective(qp, ref.x)) <= 1e-6 * (1 + abs(O.objective(qp, ref.x)))
+
+
+@pytest.mark.parametrize("storage", ["f64", "bf16"])
+def test_concurrent_slots_bitwise_equal(storage):
+    """Many solves in flight at once on their own streams: slots of one RT plan (low-rank
+    stiff-row correction factored on the device) and of a dense plan (the DENSE
+    preconditioner), three rounds.  Contention delays some blocks of every launch past others
+    of the same launch, so a kernel whose blocks read what another block of it writes gives
+    different results here; every solve must equal the solve alone, bitwise."""
+    import torch
+    rt = W.rt_qp(n=6000, seed=41)
+    dn = W.dense_qp(n=400, m=800, seed=42)
+    opts = dict(tol_kkt=1e-6, storage=storage)
+
+    def load(kind, s):
+        if kind == "rt":
+            s.set_qp_rt(rt)
+        else:
+            s.set_qp_dense(dn["H"], dn["c"], dn["A"], dn["b"], dn["l"], dn["u"])
+        return s
+
+    ref = {}
+    for kind in ("rt", "dense") if storage == "f64" else ("rt",):
+        with load(kind, ipm.Solver(**opts)) as s:
+            assert s.solve() == ipm.IPM_OK
+            out = s.get()
+            ref[kind] = (out["x"].copy(), out["info"]["ipm_iters"], out["info"]["cg_iters"])
+    plans = {k: load(k, ipm.Solver(**opts)) for k in ref}
+    slots = []
+    for kind in ref:
+        for _ in range(6 if kind == "rt" else 4):
+            st = torch.cuda.Stream()
+            slots.append((kind, ipm.Solver(**opts).share_qp(plans[kind], stream=st.cuda_stream), st))
+    if "rt" in ref:
+        stiff = plans["rt"]
+        stiff.solve()
+        assert stiff.get()["info"]["max_stiff_rows"] > 32    # the stiff factor spans several tiles
+    for _ in range(3):
+        for kind, s, st in slots:
+            s.solve_async(stream=st.cuda_stream)
+        for kind, s, st in slots:
+            assert s.wait() == ipm.IPM_OK
+            out = s.get(stream=st.cuda_stream)
+            x, it, cg = ref[kind]
+            assert out["info"]["ipm_iters"] == it and out["info"]["cg_iters"] == cg, (kind, out["info"])
+            assert np.array_equal(out["x"], x), kind
+    for _, s, _ in slots:
+        s.close()
+    for s in plans.values():
+        s.close()
