@@ -5,7 +5,8 @@
 //   * k_chol_*   : in-place blocked Cholesky factor (lower) with pivot flooring, and the
 //                  reciprocal pivots;
 //   * k_chol_tile_inv : inverses of the factor's 32 x 32 diagonal tiles;
-//   * k_mirror   : copies L into the upper triangle so both triangular sweeps read rows;
+//   * k_mirror   : last pass of a factorisation: installs the factored diagonal tiles and copies
+//                  L^T into the upper triangle, so both triangular sweeps read rows;
 //   * k_inv      : explicit inverse from the factor, columns spread over blocks.
 // The low-rank correction's G (up to 1024 rows) is factored in float64 and inverted
 // explicitly, so each of the many PCG applies is a parallel matvec.  The DENSE
@@ -81,8 +82,9 @@ __device__ __forceinline__ float2 r_floor(float2 fl) { return make_float2(fmaxf(
 // Blocked right-looking Cholesky (lower, row-major, leading dimension ld) of the leading
 // nn x nn block of A on 32 x 32 tiles, two launches per tile column kb:
 //   * the panel: every block factors the diagonal tile in shared memory (the same code on the
-//     same data, so each gets the same factor; block 0 writes it back), then the others each
-//     solve 8 rows of the tiles below, X = A_ib,kb L_kb,kb^{-T}, one warp per row;
+//     same data, so each gets the same factor; block 0 stores it in tiles[kb], which the last
+//     pass installs), then the others each solve 16 rows of the tiles below,
+//     X = A_ib,kb L_kb,kb^{-T}, one warp per row;
 //   * the trailing update A_ib,jb -= L_ib,kb L_jb,kb^T (kb < jb <= ib) on 16 x 16 quarter tiles.
 // Each pivot takes one reciprocal square root and the rest multiplies by it (no division on
 // the chain), and the arithmetic of a tile column is spread over as many SMs as it has row
