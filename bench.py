@@ -503,7 +503,7 @@ def run_sqp(args):
             "qp_ipm_iters_first": h[0]["qp_ipm_iters"],
             "qp_ipm_iters_mean_after_first": float(np.mean([r["qp_ipm_iters"] for r in h[1:]])) if len(h) > 1 else None,
             "qp_cg_iters_mean": float(np.mean([r["qp_cg_iters"] for r in h])),
-            "max_u_cols": max(r["u_cols"] for r in h), "qp_not_ok": int(sum(r["qp_status"] != 0 for r in h)),
+            "max_u_cols": max(r["u_cols"] for r in h), "qp_not_ok": int(sum(r["qp_status"] != 0 for r in h)), "qp_cold_retries": int(sum(r.get("qp_cold_retry", False) for r in h)),
             "objective_evals": obj.evals}
     clk = clocks.stop()
     w, c = runs["warm"], runs["cold"]

@@ -111,6 +111,13 @@ def sqp_solve(obj: DoseObjective, A, b, l, u, x0, solver, max_iter=50, tol=1e-6,
     for k in range(max_iter):
         t0 = time.perf_counter()
         st = solver.solve(warm=warm and k > 0)
+        retried = False
+        if st != 0 and warm and k > 0:
+            # a warm start from the previous solution can stall the interior point method (its
+            # complementarity products start far from the central path of the new QP): the
+            # sub-problem is solved again from the cold start point before its step is taken
+            st = solver.solve(warm=False)
+            retried = True
         out = solver.get()
         t_qp = time.perf_counter() - t0
         xs = out["x"]
@@ -119,7 +126,7 @@ def sqp_solve(obj: DoseObjective, A, b, l, u, x0, solver, max_iter=50, tol=1e-6,
         dn = float(np.abs(d).max())
         rec = dict(k=k, f=f, step_inf=dn, qp_status=int(st), qp_ipm_iters=out["info"]["ipm_iters"],
                    qp_cg_iters=out["info"]["cg_iters"], qp_rel_kkt=out["info"]["rel_kkt"], qp_s=t_qp,
-                   u_cols=int(U.shape[1]), warm=bool(warm and k > 0))
+                   u_cols=int(U.shape[1]), warm=bool(warm and k > 0), qp_cold_retry=retried)
         if dn <= tol * (1.0 + float(np.abs(x).max())):
             hist.append(rec)
             converged = True

@@ -167,3 +167,27 @@ def test_sqp_two_sided_rows_match_slsqp(seed):
     _, g = obj.value_grad(res.x)
     r = g + A2.T @ res.y - res.zl + res.zu
     assert np.abs(r).max() <= 1e-4 * (1 + np.abs(g).max())
+
+
+def test_failed_warm_start_is_solved_again_cold():
+    """A warm-started sub-problem that ends without converging (a stalled warm start) is solved
+    again from the cold start point before its step is taken; the loop then reaches the same
+    point as with cold starts throughout."""
+    p = W.sqp_problem(n=40, density=0.08, seed=4)
+    obj, A = _objective(p)
+    calls = []
+
+    class WarmFails(OracleQP):
+        def solve(self, warm=False):
+            calls.append(warm)
+            st = super().solve(warm)
+            return 3 if warm else st          # every warm start "stalls" (IPM_MAX_ITER)
+
+    res = sqp.sqp_solve(obj, A, p["b"], p["l"], p["u"], np.zeros(p["n"]), WarmFails(), max_iter=200, tol=1e-6)
+    ref = sqp.sqp_solve(obj, A, p["b"], p["l"], p["u"], np.zeros(p["n"]), OracleQP(), max_iter=200, tol=1e-6,
+                        warm=False)
+    assert res.converged and ref.converged
+    assert all(r["qp_status"] == 0 for r in res.history)
+    assert all(r["qp_cold_retry"] == (r["k"] > 0) for r in res.history)
+    assert calls[0] is False and calls[1:3] == [True, False]
+    assert abs(res.f - ref.f) <= 1e-10 * (1 + abs(ref.f))
