@@ -278,8 +278,14 @@ void carve_state(Carver& cv, Dev& d, int64_t n, int64_t m, int64_t nR, int stiff
   d.Kd = dense ? cv.take<float2>(n * n) : nullptr;
   // the dense preconditioner forms K by a tiled product over R stored densely when that
   // copy stays below 256 MB (else it scans R's rows)
-  d.Rd = (dense && nR * n <= (int64_t)(32 << 20)) ? cv.take<float2>(nR * n) : nullptr;
+  const bool dense_rd = dense && nR * n <= (int64_t)(32 << 20);   // decided from sizes: a counting
+                                                                 // pass returns null pointers
+  d.Rd = dense_rd ? cv.take<float2>(nR * n) : nullptr;
   d.wdf = dense ? cv.take<float2>(std::max<int64_t>(nR, 1)) : nullptr;
+  {
+    const int64_t nt = (n + 31) / 32, splits = gram_splits(n);
+    d.gram_part = (dense_rd && splits > 1) ? cv.take<float2>(splits * (nt * (nt + 1) / 2) * 1024) : nullptr;
+  }
   d.dense_aux = dense ? cv.take<double>(4) : nullptr;
   d.chol_diag = cv.take<double>(std::max<int64_t>(dense ? n : 0, stiff_cap));
   d.chol_rinv = cv.take<double>(std::max<int64_t>(dense ? n : 0, stiff_cap));

@@ -440,9 +440,9 @@ __device__ __forceinline__ void tile_of_block(int64_t b, int64_t& tj, int64_t& t
 }
 
 // the low-rank term's columns into the 2 x 2 accumulators (sJ, sL: 32 pairs of shared
-// memory each), then the tile's stores
-__device__ __forceinline__ void gram_lowrank_store(const Dev& d, int64_t J0, int64_t L0, int64_t tj, int64_t tl,
-                                                   float2* sJ, float2* sL, float (&h)[2][2], float (&l)[2][2]) {
+// memory each)
+__device__ __forceinline__ void gram_lowrank_acc(const Dev& d, int64_t J0, int64_t L0, float2* sJ, float2* sL,
+                                                 float (&h)[2][2], float (&l)[2][2]) {
   const int64_t n = d.n;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   const double s = d.dense_aux[2];
@@ -458,6 +458,13 @@ __device__ __forceinline__ void gram_lowrank_store(const Dev& d, int64_t J0, int
 #pragma unroll
       for (int c = 0; c < 2; ++c) df_mac(sJ[2 * ty + a], sL[2 * tx + c], h[a][c], l[a][c]);
   }
+}
+
+// the tile's stores (both triangles off the diagonal)
+__device__ __forceinline__ void gram_store(const Dev& d, int64_t J0, int64_t L0, int64_t tj, int64_t tl,
+                                           const float (&h)[2][2], const float (&l)[2][2]) {
+  const int64_t n = d.n;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -512,17 +519,23 @@ __global__ void __launch_bounds__(256) k_gram_tiles(Dev d) {
     }
     __syncthreads();
   }
-  gram_lowrank_store(d, J0, L0, tj, tl, sJ, sL, h, l);
+  gram_lowrank_acc(d, J0, L0, sJ, sL, h, l);
+  gram_store(d, J0, L0, tj, tl, h, l);
 }
 
 // From the dense copy of R (pairs): chunks of 32 rows of Rd staged in shared memory (one side
 // scaled by the row weight), rows summed in order.  The next chunk is loaded into registers
 // while the current one is multiplied.
+// With row splits (gridDim.y > 1) block (t, s) sums the rows of chunk range s of tile t and
+// writes its unnormalised pairs to gram_part[s][t] (split 0 also takes the low-rank term);
+// k_gram_sum adds the splits in order.
 __global__ void __launch_bounds__(256) k_gram_gemm(Dev d) {
   __shared__ float2 sA[kGT][kGT + 1], sB[kGT][kGT + 1];
   const int64_t n = d.n;
   int64_t tj, tl;
   tile_of_block(blockIdx.x, tj, tl);
+  const int64_t chunks = (d.nR + kGT - 1) / kGT, per = (chunks + gridDim.y - 1) / gridDim.y;
+  const int64_t r_beg = blockIdx.y * per * kGT, r_end = min(d.nR, (int64_t)(blockIdx.y + 1) * per * kGT);
   const int64_t J0 = tj * kGT, L0 = tl * kGT;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   float h[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, l[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
@@ -533,13 +546,13 @@ __global__ void __launch_bounds__(256) k_gram_gemm(Dev d) {
     for (int q = 0; q < kPer; ++q) {
       const int t = tid + q * 256, ii = t >> 5, cc = t & 31;
       const int64_t i = i0 + ii;
-      const bool in = i < d.nR;
+      const bool in = i < r_end;
       ra[q] = (in && J0 + cc < n) ? r_mul(d.Rd[i * n + J0 + cc], d.wdf[i]) : make_float2(0.f, 0.f);
       rb[q] = (in && L0 + cc < n) ? d.Rd[i * n + L0 + cc] : make_float2(0.f, 0.f);
     }
   };
-  if (d.nR > 0) fetch(0);
-  for (int64_t i0 = 0; i0 < d.nR; i0 += kGT) {
+  if (r_beg < r_end) fetch(r_beg);
+  for (int64_t i0 = r_beg; i0 < r_end; i0 += kGT) {
 #pragma unroll
     for (int q = 0; q < kPer; ++q) {
       const int t = tid + q * 256;
@@ -547,7 +560,7 @@ __global__ void __launch_bounds__(256) k_gram_gemm(Dev d) {
       sB[t >> 5][t & 31] = rb[q];
     }
     __syncthreads();
-    if (i0 + kGT < d.nR) fetch(i0 + kGT);
+    if (i0 + kGT < r_end) fetch(i0 + kGT);
 #pragma unroll 4
     for (int ii = 0; ii < kGT; ++ii) {
       const float2 a0 = sA[ii][2 * ty], a1 = sA[ii][2 * ty + 1];
@@ -559,7 +572,42 @@ __global__ void __launch_bounds__(256) k_gram_gemm(Dev d) {
     }
     __syncthreads();
   }
-  gram_lowrank_store(d, J0, L0, tj, tl, &sA[0][0], &sB[0][0], h, l);
+  if (blockIdx.y == 0) gram_lowrank_acc(d, J0, L0, &sA[0][0], &sB[0][0], h, l);
+  if (gridDim.y == 1) {
+    gram_store(d, J0, L0, tj, tl, h, l);
+    return;
+  }
+  float2* part = d.gram_part + ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * kGT * kGT;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) part[(2 * ty + a) * kGT + 2 * tx + c] = make_float2(h[a][c], l[a][c]);
+}
+
+// The row splits' partial tiles added in split order (two-sum of the high parts, the low parts
+// and errors summed), one thread per tile entry; the tile stores as k_gram_gemm's.
+__global__ void k_gram_sum(Dev d, int splits, int64_t tiles) {
+  const int64_t n = d.n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tiles * kGT * kGT;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t tile = t / (kGT * kGT);
+    const int e = (int)(t % (kGT * kGT)), a = e / kGT, c = e % kGT;
+    int64_t tj, tl;
+    tile_of_block(tile, tj, tl);
+    const int64_t j = tj * kGT + a, lc = tl * kGT + c;
+    if (j >= n || lc >= n) continue;
+    float h = 0.f, l = 0.f;
+    for (int s = 0; s < splits; ++s) {
+      const float2 p = d.gram_part[((int64_t)s * tiles + tile) * kGT * kGT + e];
+      float sum, err;
+      two_sum(h, p.x, sum, err);
+      h = sum;
+      l = __fadd_rn(l, __fadd_rn(err, p.y));
+    }
+    const float2 v = df_fast_sum(h, l);
+    d.Kd[j * n + lc] = v;
+    if (tj != tl) d.Kd[lc * n + j] = v;
+  }
 }
 
 __global__ void k_densify_zero(float2* Rd, int64_t total) {
@@ -607,9 +655,12 @@ cudaError_t launch_dense_build(const Dev& d, cudaStream_t st) {
   const int n = (int)d.n;
   const int64_t nt = (d.n + kGT - 1) / kGT;
   k_dense_prep<<<1, 1024, 0, st>>>(d);
-  if (d.Rd)
-    k_gram_gemm<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, st>>>(d);
-  else
+  if (d.Rd) {
+    const int splits = d.gram_part ? gram_splits(d.n) : 1;
+    const int64_t tiles = nt * (nt + 1) / 2;
+    k_gram_gemm<<<dim3((unsigned)tiles, (unsigned)splits), 256, 0, st>>>(d);
+    if (splits > 1) k_gram_sum<<<(unsigned)std::min<int64_t>((tiles * 1024 + 255) / 256, 4 * 152), 256, 0, st>>>(d, splits, tiles);
+  } else
     k_gram_tiles<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, st>>>(d);
   k_gram_diag_hs<<<(int)std::min<int64_t>(d.n, 4 * 152), 256, 0, st>>>(d);
   cudaError_t e = launch_chol<float2>(d.Kd, d.n, nullptr, n, n, d.chol_diag, d.chol_rdf,

@@ -71,6 +71,7 @@ struct Dev {
   double* chol_rinv;           // max(n_dense, stiff_cap): 1 / L_kk of the last factor
   double* chol_tiles;          // factored 32 x 32 diagonal tiles of the last factor (pairs for the dense K),
                                // installed into the factor by its last pass
+  float2* gram_part;           // dense only, small n: partial Gram tiles of the row splits (gram_splits)
   float2* chol_rdf;            // dense only: 1 / L_kk of the dense factor (pairs)
   float2* chol_tinv;           // dense only: inverses of the dense factor's 32 x 32 diagonal tiles
   // double-float operator (storage ST_F64 with options.op_arith = DF32): the values of R and
@@ -204,6 +205,14 @@ struct Geo {
 };
 
 Geo make_geo(const Dev& d);
+
+// Row splits of the dense Gram product: a problem with fewer 32 x 32 tiles of the lower
+// triangle than about one or two per SM splits each tile's rows over 4 or 2 blocks (partial
+// sums added in a fixed order), so the SMs hold more than one block each.
+inline int gram_splits(int64_t n) {
+  const int64_t nt = (n + 31) / 32, tiles = nt * (nt + 1) / 2;
+  return tiles < 152 ? 4 : (tiles < 304 ? 2 : 1);
+}
 
 // ---- low-rank Hessian term: lrs = uw o (U^T v); quad: also v^T U W U^T v into the scalars ----
 cudaError_t launch_lr(const Dev& d, const double* v, int quad, cudaStream_t st);
